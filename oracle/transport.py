@@ -1,0 +1,88 @@
+"""Theta / Crank-Nicolson transport step (oracle; test infrastructure only).
+
+Section 3.2, eq. (3.11) transport_cn: T_2(dt) = (I + dt/2 L_h)(I - dt/2 L_h)^{-1}.
+Section 5.1 uses the theta-weighted form of the same step; with weight theta
+and sub-step delta the new state solves
+
+    (I - theta delta L_h) F^new = (I + (1 - theta) delta L_h) F^old,      (*)
+
+theta = 1/2 being eq. (3.11).  Reading: eq. (4.2) crank_nicolson prints the
+same system without the factors 1/2; (*) is used (it is eq. (3.11) for
+theta = 1/2).  The periodic system is cyclic (the paper treats inflow
+boundaries only, Section 2); (*) is solved exactly as the linear system it is.
+
+Two independent routes:
+  DirectTransport  sparse LU of (*) with the L_h assembled from eq. (3.7)
+                   (the plain definition; tiny and medium meshes);
+  bloch_transport  per-line Fourier (Bloch) closed form of (*) for an
+                   axis-aligned velocity, derived by hand from eq. (3.7) on a
+                   Cartesian cell (any size).  Derivation: with
+                   K = Dm + w_0^{-1} e_0 e_0^T (Dm[j,i] = l_i'(x_j)), the
+                   summation-by-parts identity of GL quadrature reduces
+                   eq. (3.7) for v = +lambda e_a on line cell c to
+                   d/dt f_c = -(2 lambda / h)(K f_c - w_0^{-1} e_0 f_{c-1,d});
+                   for the Fourier mode exp(i kappa c), f_{c-1} -> exp(-i kappa) f_c.
+                   v = -lambda e_a is the mirror image (points reversed).
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .dg import assemble_transport
+from .quadrature import gauss_lobatto, lagrange_derivative
+
+
+class DirectTransport:
+    """Solve (*) for one velocity v and sub-step delta with a sparse LU (SuperLU)."""
+
+    def __init__(self, mesh, v, delta, theta=0.5):
+        self.mesh = mesh
+        L = assemble_transport(mesh, v)
+        I = sp.identity(mesh.npoints, format="csr")
+        self.A = (I - theta * delta * L).tocsc()
+        self.B = (I + (1.0 - theta) * delta * L).tocsr()
+        self.lu = spla.splu(self.A)
+
+    def __call__(self, field):
+        rhs = self.B @ np.asarray(field, dtype=np.float64).reshape(-1)
+        return self.lu.solve(rhs).reshape(np.shape(field))
+
+
+def line_K(d):
+    """K = Dm + w_0^{-1} e_0 e_0^T of the reduced 1-D cell operator (see module doc)."""
+    x, w = gauss_lobatto(d)
+    K = lagrange_derivative(x).copy()
+    K[0, 0] += 1.0 / w[0]
+    return K, w
+
+
+def bloch_transport(field, axis_np, sign, d, nu, theta=0.5):
+    """Solve (*) for v = sign * lambda e_a along numpy axis ``axis_np`` by Fourier modes.
+
+    nu = 2 lambda delta / h.  For mode m (kappa = 2 pi m / N) the cell block obeys
+      [I + theta nu (K - w0^{-1} e^{-i kappa} e_0 e_d^T)] f^new
+          = [I - (1-theta) nu (K - w0^{-1} e^{-i kappa} e_0 e_d^T)] f^old.
+    """
+    n = d + 1
+    K, w = line_K(d)
+    f = np.moveaxis(np.asarray(field, dtype=np.float64), axis_np, -1)
+    if sign < 0:
+        f = f[..., ::-1]
+    P = f.shape[-1]
+    N = P // n
+    assert N * n == P
+    fc = f.reshape(f.shape[:-1] + (N, n))
+    kappa = 2.0 * np.pi * np.arange(N) / N
+    e0ed = np.zeros((n, n))
+    e0ed[0, n - 1] = 1.0 / w[0]
+    Kk = K[None, :, :] - np.exp(-1j * kappa)[:, None, None] * e0ed[None, :, :]
+    I = np.eye(n)[None]
+    Am = I + theta * nu * Kk
+    Bm = I - (1.0 - theta) * nu * Kk
+    Tm = np.linalg.solve(Am, Bm)                      # (N, n, n)
+    Fh = np.fft.fft(fc, axis=-2)
+    Fh = np.einsum("mij,...mj->...mi", Tm, Fh)
+    fnew = np.real(np.fft.ifft(Fh, axis=-2)).reshape(f.shape)
+    if sign < 0:
+        fnew = fnew[..., ::-1]
+    return np.ascontiguousarray(np.moveaxis(fnew, -1, axis_np))

@@ -1,0 +1,174 @@
+"""Seeded synthetic workloads (configurations and initial macroscopic states).
+
+This module holds no arithmetic of the scheme: only problem sizes and the
+recipes of the initial states w^0, evaluated at point coordinates that the
+caller supplies (each side computes its own Gauss-Lobatto coordinates).  It
+is shared by the tests (which feed the same arrays to the oracle and to the
+CUDA library) and by ``bench.py``.
+
+Recipes (the paper prints no data for these workloads; all inputs are
+synthetic and drawn from ``numpy.random.default_rng(seed)``):
+
+* advection: a periodised Gaussian bump (sigma = 0.1, centre (1/2, ..., 1/2),
+  3^D periodic images) plus 8 Fourier modes of amplitude 1e-2 with wave vectors
+  drawn from {-4..4}^D minus 0 and phases from U[0, 2 pi).
+* shallow water: h = 1 + 0.1 F, hu = hv = 0, F a sum of 16 Fourier modes
+  (|k|_inf <= 4, N(0,1) amplitudes, U[0,2 pi) phases) scaled so that
+  max |F| = 1 on a fixed uniform reference grid.
+* Euler: rho = 1 + 0.05 F_rho, u_a = 0.1 F_a, p = 1, with independent fields
+  built like F above (|k|_inf <= 2 in 3-D); w = (rho, rho u, E) with
+  E = p/(gamma-1) + rho |u|^2 / 2.
+"""
+import math
+from dataclasses import dataclass, field
+from typing import Tuple
+
+import numpy as np
+
+KINDS = ("advection", "shallow_water", "euler")
+
+
+@dataclass
+class Config:
+    name: str
+    kind: str
+    dim: int
+    n_macro: Tuple[int, ...]
+    n_sub: Tuple[int, ...]
+    order: int
+    lam: float
+    steps: int
+    seed: int
+    a: Tuple[float, ...] = (0.0, 0.0, 0.0)
+    gravity: float = 9.81
+    gamma: float = 1.4
+    theta: float = 0.5
+    omega: float = 2.0
+    cfl: float = 1.0
+    lengths: Tuple[float, ...] = (1.0, 1.0, 1.0)
+
+    @property
+    def m(self):
+        return {"advection": 1, "shallow_water": 3, "euler": self.dim + 2}[self.kind]
+
+    @property
+    def ncells(self):
+        return tuple(self.n_macro[a] * self.n_sub[a] for a in range(self.dim))
+
+    @property
+    def npoints_axis(self):
+        return tuple(c * (self.order + 1) for c in self.ncells)
+
+    @property
+    def npoints(self):
+        return int(np.prod(self.npoints_axis))
+
+    @property
+    def nfields(self):
+        return self.m * 2 * self.dim
+
+    @property
+    def dofs(self):
+        """Kinetic degrees of freedom: one f value at one GL point."""
+        return self.nfields * self.npoints
+
+    @property
+    def h(self):
+        """Sub-cell edge (all axes have the same edge in these workloads)."""
+        return min(self.lengths[a] / self.ncells[a] for a in range(self.dim))
+
+    @property
+    def dt(self):
+        """Time step dt = cfl * h / lambda."""
+        return self.cfl * self.h / self.lam
+
+    def scaled(self, n_macro=None, n_sub=None, steps=None, name=None):
+        import dataclasses
+        return dataclasses.replace(
+            self, n_macro=tuple(n_macro or self.n_macro), n_sub=tuple(n_sub or self.n_sub),
+            steps=self.steps if steps is None else steps, name=name or self.name)
+
+
+ADVECTION_D2Q4 = Config("advection_d2q4_8x8x4x4_d2", "advection", 2, (8, 8), (4, 4), 2,
+                        lam=2.0, steps=10, seed=1, a=(1.0, 0.5, 0.0))
+SW_D2Q4 = Config("shallow_water_d2q4_64x64x8x8_d3", "shallow_water", 2, (64, 64), (8, 8), 3,
+                 lam=8.0, steps=100, seed=2)
+EULER_D3Q6 = Config("euler_d3q6_32c3x4c3_d2", "euler", 3, (32, 32, 32), (4, 4, 4), 2,
+                    lam=5.0, steps=10, seed=3)
+
+CONFIGS = {c.name: c for c in (ADVECTION_D2Q4, SW_D2Q4, EULER_D3Q6)}
+
+
+def _grid(coords):
+    """Broadcastable coordinate arrays, numpy axis order (z, y, x) i.e. x last."""
+    D = len(coords)
+    out = []
+    for a in range(D):
+        shape = [1] * D
+        shape[D - 1 - a] = len(coords[a])
+        out.append(np.asarray(coords[a], dtype=np.float64).reshape(shape))
+    return out
+
+
+def _modes(rng, D, count, kmax):
+    ks = []
+    while len(ks) < count:
+        k = rng.integers(-kmax, kmax + 1, size=D)
+        if np.any(k != 0):
+            ks.append(k)
+    return np.array(ks, dtype=np.float64)
+
+
+def _mode_sum(X, ks, amps, phases):
+    out = 0.0
+    for k, c, ph in zip(ks, amps, phases):
+        arg = 0.0
+        for a in range(len(X)):
+            arg = arg + k[a] * X[a]
+        out = out + c * np.cos(2.0 * math.pi * arg + ph)
+    return out
+
+
+def _normalised_field(rng, D, count, kmax, ref_pts):
+    ks = _modes(rng, D, count, kmax)
+    amps = rng.standard_normal(count)
+    phases = rng.uniform(0.0, 2.0 * math.pi, count)
+    ref = _grid([np.arange(ref_pts) / ref_pts] * D)
+    scale = np.max(np.abs(_mode_sum(ref, ks, amps, phases)))
+    return lambda X: _mode_sum(X, ks, amps / scale, phases)
+
+
+def initial_w(cfg, coords):
+    """w^0 of shape (m, *grid) (x last) at the tensor grid ``coords`` = [x, y(, z)]."""
+    D = cfg.dim
+    X = _grid(coords)
+    shape = tuple(len(coords[a]) for a in reversed(range(D)))
+    rng = np.random.default_rng(cfg.seed)
+    if cfg.kind == "advection":
+        sigma = 0.1
+        g = 0.0
+        for shift in np.ndindex(*(3,) * D):
+            r2 = 0.0
+            for a in range(D):
+                r2 = r2 + (X[a] - 0.5 - (shift[a] - 1)) ** 2
+            g = g + np.exp(-r2 / (2.0 * sigma * sigma))
+        ks = _modes(rng, D, 8, 4)
+        phases = rng.uniform(0.0, 2.0 * math.pi, 8)
+        w = g + _mode_sum(X, ks, np.full(8, 1e-2), phases)
+        return np.broadcast_to(w, shape)[None].astype(np.float64).copy()
+    if cfg.kind == "shallow_water":
+        F = _normalised_field(rng, D, 16, 4, 256)
+        h = np.broadcast_to(1.0 + 0.1 * F(X), shape)
+        z = np.zeros(shape)
+        return np.stack([h, z, z.copy()]).astype(np.float64)
+    if cfg.kind == "euler":
+        kmax = 4 if D == 2 else 2
+        ref = 256 if D == 2 else 48
+        Fr = _normalised_field(rng, D, 16, kmax, ref)
+        Fu = [_normalised_field(rng, D, 16, kmax, ref) for _ in range(D)]
+        rho = np.broadcast_to(1.0 + 0.05 * Fr(X), shape)
+        u = [np.broadcast_to(0.1 * Fu[a](X), shape) for a in range(D)]
+        p = 1.0
+        E = p / (cfg.gamma - 1.0) + 0.5 * rho * sum(ua * ua for ua in u)
+        return np.stack([rho] + [rho * ua for ua in u] + [E]).astype(np.float64)
+    raise ValueError(cfg.kind)
