@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Benchmark of the PDG hot path: kinetic DOF-updates/s on the shallow-water D2Q4 workload.
+
+Workload (one GPU): 2-D shallow water (g = 9.81) through the vectorial D2Q4 kinetic
+model (12 populations), periodic unit square, 64x64 macrocells x 8x8 subcells,
+DG degree 3 (4 GL points per cell and axis: 2048 x 2048 points), theta = 1/2,
+omega = 2, dt = h / lambda, lambda = 8; seeded smooth initial height, zero velocity.
+One benchmark step = one palindromic step M2(dt) = T(dt/2) C(dt) T(dt/2) over the
+whole state (50,331,648 kinetic DOF).  DOF-update = one population value at one GL
+point advanced through one full step.
+
+Output: ONE JSON line (rank 0).  `value` is measured with the state resident in
+HBM; `e2e` times the same run through the C ABI with host buffers (pdg_set_w from
+pinned host memory, pdg_step, pdg_get_w to host).  The state (403 MB) is larger
+than L2 (126 MB), so no L2 flush is needed between steps.
+
+`--impl reference` times the FP64 CPU oracle (the only reference this method has:
+the paper ships no code) on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no
+collective on the data path); value = sum over ranks / max time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "kinetic DOF-updates/s"
+UNIT = "DOF-updates/s"
+
+# Algorithmic per-unit figures of the dominant kernel (the last-axis pass:
+# T(dt/2), collision, T(dt/2)); see the design doc for the derivation.
+#   bytes: every population of every point read once and written once = 16 B per DOF.
+#   flops per transported DOF per sub-step (degree d, n = d+1): E row (n FMA) + inflow
+#     term (1 FMA) + per cell the z combination (2 flops) -> 2n + 2 + 2/n flops.
+#   collision flops per point (shallow water): see collision_flops().
+
+
+def transport_flops_per_dof(n):
+    return 2.0 * n + 2.0 + 2.0 / n
+
+
+def collision_flops_sw():
+    # moments 12 adds->9 adds; 1/h (1 div), u, v (2 mul), p = 0.5 g h h (2 mul), 4 flux
+    # products (2 FMA + 2 mul = 6 flops); c0 w_k (3 mul); per population fma + mul + add (4 flops) x 12
+    return 9 + 1 + 2 + 2 + 6 + 3 + 4 * 12
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="pdg", choices=["pdg", "reference"])
+    ap.add_argument("--scheme", default="M2", choices=["M2", "M2_collapsed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and self.uuid not in parts[1]:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[6 + k].lower() == "active":
+                    reasons.add(nm)
+        out.update(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def cpu_baseline(cfg_name, sample_steps):
+    """Time the FP64 oracle (single thread) on a bounded sample of the workload, in a
+    fresh process (no CUDA there; BLAS/OpenMP pinned to one thread)."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from paper_1702_00169_gb300 import workloads as W
+from oracle import models as OM, scheme as OS
+from oracle.dg import CartesianMesh
+cfg = W.CONFIGS[{cfg_name!r}].scaled(n_macro=(8, 8))
+mesh = CartesianMesh(cfg.dim, cfg.ncells, cfg.order)
+model = OM.Model(OM.SHALLOW_WATER, cfg.dim, cfg.lam, gravity=cfg.gravity)
+w0 = W.initial_w(cfg, [mesh.coords1d(a) for a in range(cfg.dim)])
+tr = OS.Transporter(mesh, model, theta=cfg.theta, method="bloch")
+f = OS.initial_state(model, w0)
+f = OS.m2_step(f, tr, model, cfg.dt, cfg.omega)
+t0 = time.perf_counter()
+for _ in range({sample_steps}):
+    f = OS.m2_step(f, tr, model, cfg.dt, cfg.omega)
+el = time.perf_counter() - t0
+print(json.dumps({{"value": cfg.dofs * {sample_steps} / el, "dofs": cfg.dofs, "steps": {sample_steps},
+                  "seconds": el, "mesh": "%dx%d macrocells x 8x8 subcells, d=3" % cfg.n_macro}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-500:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 numpy oracle (Bloch/FFT transport), {d['steps']} M2 steps of the same model "
+                       f"on {d['mesh']} ({d['dofs']} DOF), {d['seconds']:.1f} s, 1 thread")}
+
+
+def run_reference(args, cfg):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    # each reference step = one M2 step of the oracle on a bounded sample of the workload
+    sample_steps = max(1, args.steps)
+    warm = max(0, args.warmup)
+    res = cpu_baseline(cfg.name, sample_steps if sample_steps <= 200 else 200) if warm >= 0 else None
+    value = res["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": cfg.name, "reference": "FP64 CPU oracle (the paper ships no code)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": res.get("cores"), "kind": "oracle",
+                             "sample": res.get("sample")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if value:
+        line["ms_per_step"] = 1e3 * cfg.dofs / value
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    from paper_1702_00169_gb300 import workloads as W
+    cfg = W.SW_D2Q4
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    assert torch.cuda.is_available(), "bench.py needs a GPU"
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1702_00169_gb300 import pdg
+
+    stream = torch.cuda.Stream()
+    s = pdg.solver_for(cfg, scheme=args.scheme, stream=stream.cuda_stream)
+    info = s.info()
+    coords = [s.points(a) for a in range(cfg.dim)]
+    w0 = np.ascontiguousarray(W.initial_w(cfg, coords).reshape(-1))
+    w0_dev = torch.from_numpy(w0).cuda()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident run ----
+    s.set_w(w0_dev)
+    s.step(cfg.dt, args.warmup)
+    s.synchronize()
+    dev_uuid = None
+    try:
+        dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(dev_uuid)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.4)
+    s.timing_enable(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(cfg.dt, args.steps)
+    ev1.record(stream)
+    s.synchronize()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches, kms = s.timing_read()
+    s.timing_enable(False)
+    w_end = s.get_w()
+    finite = bool(np.all(np.isfinite(w_end)))
+
+    ms_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    dofs = cfg.dofs
+    value = dofs * args.steps * ws / (ms_max * 1e-3)
+
+    # ---- end-to-end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        w_host = torch.from_numpy(w0).pin_memory()
+        w_out = torch.empty_like(w_host).pin_memory()
+        s2 = pdg.solver_for(cfg, scheme=args.scheme, stream=stream.cuda_stream)
+        s2.set_w(w_host)
+        s2.step(cfg.dt, 2)
+        s2.get_w(w_out)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2.set_w(w_host)
+        s2.step(cfg.dt, args.steps)
+        s2.get_w(w_out)
+        t1 = time.perf_counter()
+        el = t1 - t0
+        if ws > 1:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        s2.close()
+        nbytes = w0.nbytes
+        e2e = {"value": dofs * args.steps * ws / el, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+               "note": "one pdg_set_w (host) + pdg_step(K) + pdg_get_w (host) per timed run; bytes amortised over K"}
+    s.close()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (from the live CUDA-event timing) ----
+    n = cfg.order + 1
+    P = info.npoints
+    F = info.nfields
+    kinds = {0: "transport pass (T T on +-x populations)", 1: "last-axis pass (T, collision, T)"}
+    k_dom = int(np.argmax(kms[:2]))
+    avg_ms = kms[k_dom] / max(1, launches[k_dom])
+    if k_dom == 1:
+        bytes_launch = 16.0 * F * P
+        flops_launch = 2 * (F // 2) * P * transport_flops_per_dof(n) + P * collision_flops_sw()
+    else:
+        bytes_launch = 16.0 * (F // 2) * P
+        flops_launch = 2 * (F // 2) * P * transport_flops_per_dof(n)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # FP64 pipe: 2 DFMA per SM per clock (GB300 nominal 1.25 TFLOP/s at 2.07 GHz, 152 SMs)
+    fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    achieved_tflops = flops_launch / (avg_ms * 1e-3) / 1e12
+    achieved_gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved_tflops / fp64_peak_tflops, "traffic": None,
+            "kernel": kinds[k_dom], "avg_launch_ms": avg_ms, "launches": launches[k_dom],
+            "algorithmic_flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
+            "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": achieved_gbs / hbm_peak,
+            "peak_note": "FP64 pipe peak = 152 SMs x 2 DFMA/clk x 2 flop x median SM clock under load"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg.name, args.cpu_sample_steps)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.name, "model": "shallow water via vectorial D2Q4 (12 populations)",
+                       "mesh": "64x64 macrocells x 8x8 subcells, d=3, 2048x2048 GL points, periodic",
+                       "dof": dofs, "scheme": args.scheme, "theta": cfg.theta, "omega": cfg.omega,
+                       "dt": cfg.dt, "lambda": cfg.lam, "precision": "FP64",
+                       "l2": "state 403 MB > 126 MB L2: inputs larger than L2, no flush",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "gpu_launches": int(sum(launches)), "roofline": roof, "clocks": clocks,
+            "e2e": e2e, "cpu_baseline": cpu, "state_finite": finite}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

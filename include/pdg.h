@@ -1,0 +1,246 @@
+/*
+ * pdg.h -- C ABI of the GB300 (sm_103a) Palindromic Discontinuous Galerkin solver.
+ *
+ * The library advances the kinetic BGK system of Badwaik et al., "Task-based
+ * parallelization of an implicit kinetic scheme" (arXiv:1702.00169):
+ *   - Section 2, eq. (2.1) kin_bgk: n_v = 2D transport equations at constant
+ *     velocities +-lambda e_a, coupled by the relaxation towards f^eq(P f);
+ *   - Section 3.1, eq. (3.7) DG_reduit: upwind nodal DG on Gauss-Lobatto points;
+ *   - Section 3.2, eq. (3.11) transport_cn and eq. (3.12) collision_cn, composed
+ *     as the palindrome M2(dt) = T(dt/2) C(dt) T(dt/2).
+ * Meshes are periodic Cartesian boxes split into n_macro x n_sub cells per axis
+ * (the macrocell / subcell structure of Section 4.3).
+ *
+ * Conventions common to every entry point
+ *   - Every call returns a pdg_status (0 = PDG_OK, negative = error).  No C++
+ *     exception crosses the ABI.  On error the context is left unchanged
+ *     (except for the text returned by pdg_last_error) unless stated.
+ *   - The caller owns every buffer it passes; the library never keeps a
+ *     caller pointer after the call returns.  The context owns its device
+ *     state (allocated with cudaMalloc on the current device).
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - Work is issued on the context's CUDA stream.  Calls with host buffers
+ *     synchronise that stream before returning; calls with device buffers and
+ *     pdg_step are asynchronous with respect to the host.
+ *
+ * Data layout (both host and device buffers, FP64, C order):
+ *   point index along axis a:  g_a = cell_a * (d+1) + node_a  (face points are
+ *     duplicated, as in any DG method; P_a = N_a (d+1) with N_a = n_macro_a n_sub_a);
+ *   one scalar field:          [P_z][P_y][P_x]  (x fastest; absent axes have P = 1);
+ *   macroscopic state w:       [m][P_z][P_y][P_x];
+ *   kinetic state f:           [m][2D][P_z][P_y][P_x], population i in the order
+ *                              +x, -x, +y, -y, +z, -z.
+ */
+#ifndef PDG_H
+#define PDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdg_ctx pdg_ctx;
+
+/* Status codes. */
+enum {
+  PDG_OK = 0,
+  PDG_ERR_ARG = -1,         /* invalid argument (null pointer, size, range) */
+  PDG_ERR_OOM = -2,         /* device or host allocation failed */
+  PDG_ERR_CUDA = -3,        /* a CUDA runtime call failed (text in pdg_last_error) */
+  PDG_ERR_STATE = -4,       /* call out of order (e.g. pdg_step before pdg_set_w) */
+  PDG_ERR_TIMEOUT = -5,     /* a bounded device wait ran out */
+  PDG_ERR_UNSUPPORTED = -6  /* valid request that this build does not implement */
+};
+
+/* Kinetic model kinds (vectorial DnQ2n: each conserved variable has 2D populations). */
+enum {
+  PDG_MODEL_ADVECTION = 0,     /* m = 1, flux q^a = a_a w                          */
+  PDG_MODEL_SHALLOW_WATER = 1, /* D = 2, m = 3, w = (h, hu, hv), gravity g          */
+  PDG_MODEL_EULER = 2          /* D = 2 or 3, m = D + 2, w = (rho, rho u, E), gamma */
+};
+
+/* Time schemes (Section 3.2 and Section 5.1). */
+enum {
+  PDG_SCHEME_M2 = 0,          /* T(dt/2) C(dt) T(dt/2) per step                   */
+  PDG_SCHEME_M2_COLLAPSED = 1 /* consecutive half transports merged into T(dt)    */
+};
+
+/* Arithmetic of the transport sweep. */
+enum {
+  PDG_PREC_FP64 = 0 /* FP64 storage and FP64 arithmetic on every step */
+};
+
+/*
+ * Model description.  Equilibrium (Section 2; the paper gives no DnQ2n formula,
+ * reading): f^eq_{k,i} = w_k/(2D) + (v_i . q_k(w)) / (2 lambda^2), which satisfies
+ * P f^eq = w and P V^a f^eq = q^a(w).
+ *   kind       PDG_MODEL_*
+ *   scheme     PDG_SCHEME_*
+ *   precision  PDG_PREC_*
+ *   lambda     lattice speed (> 0): velocities are +-lambda e_a
+ *   a[3]       advection velocity (PDG_MODEL_ADVECTION)
+ *   gravity    g (PDG_MODEL_SHALLOW_WATER)
+ *   gamma      ratio of specific heats (PDG_MODEL_EULER)
+ *   omega      relaxation weight of eq. (3.12): omega = 2 dt/(2 tau + dt); finite, != 0
+ *              (physical range (0, 2]; a negative dt gives a negative omega)
+ *   theta      implicit weight of the transport step, 0 <= theta <= 1 (1/2 = eq. (3.11))
+ */
+typedef struct pdg_model_desc {
+  int kind;
+  int scheme;
+  int precision;
+  int reserved;
+  double lambda;
+  double a[3];
+  double gravity;
+  double gamma;
+  double omega;
+  double theta;
+} pdg_model_desc;
+
+/* Sizes of a context (filled by pdg_get_info). */
+typedef struct pdg_info {
+  int dim;            /* D */
+  int order;          /* d (d+1 GL points per cell and axis) */
+  int m;              /* conserved variables (0 before pdg_set_model) */
+  int nv;             /* populations per variable, 2D */
+  int ncell[3];       /* N_a = n_macro_a n_sub_a (1 for absent axes) */
+  int npts[3];        /* P_a = N_a (d+1) (1 for absent axes) */
+  long long npoints;  /* prod_a P_a */
+  long long nfields;  /* m * 2D */
+  long long w_len;    /* m * npoints: doubles in w */
+  long long f_len;    /* nfields * npoints: doubles in f */
+  double h[3];        /* cell edge per axis */
+} pdg_info;
+
+/*
+ * pdg_create_mesh -- create a context on a periodic Cartesian mesh.
+ * Defines the mesh of Section 3.1 (cells L with the affine map tau_L, GL points
+ * eq. (3.3)) grouped as in Section 4.3 (macrocells split into regular subcells).
+ *   out            receives the new context (set to NULL on error)
+ *   dim            D in {1, 2, 3}
+ *   n_macro, n_sub macrocells and subcells per macrocell along x, y, z (first
+ *                  dim entries read; each >= 1)
+ *   order          DG degree d in {1, 2, 3, 4}
+ *   length         box edge lengths (> 0; first dim entries read); NULL = unit box
+ *   periodic_mask  bit a set = axis a periodic; all dim bits must be set (inflow
+ *                  boundaries return PDG_ERR_UNSUPPORTED)
+ *   cuda_stream    cudaStream_t for all work of this context; NULL = legacy default stream
+ * Allocates no device memory.  Errors: PDG_ERR_ARG, PDG_ERR_UNSUPPORTED, PDG_ERR_OOM.
+ */
+int pdg_create_mesh(pdg_ctx** out, int dim, const int n_macro[3], const int n_sub[3], int order,
+                    const double length[3], unsigned periodic_mask, void* cuda_stream);
+
+/*
+ * pdg_set_model -- choose the kinetic model and time scheme (Section 2, Section 3.2).
+ * Allocates nothing.  If the number of conserved variables changes, the previous
+ * state is discarded and pdg_set_w or pdg_set_f must follow before pdg_step.
+ * Errors: PDG_ERR_ARG, PDG_ERR_UNSUPPORTED (e.g. shallow water with D != 2).
+ */
+int pdg_set_model(pdg_ctx* ctx, const pdg_model_desc* desc);
+
+/*
+ * pdg_set_w -- set f := f^eq(w) at every GL point (equilibrium start; the paper
+ * is silent on the initial kinetic data).
+ *   w          macroscopic state, layout [m][P_z][P_y][P_x], len = m * npoints doubles
+ *   on_device  1: w is a device pointer (read on the context stream, asynchronous);
+ *              0: w is host memory (copied, then the stream is synchronised)
+ * The first pdg_set_w / pdg_set_f after a model change allocates the device state
+ * f (f_len doubles, cudaMalloc).
+ * Errors: PDG_ERR_STATE (no model), PDG_ERR_ARG (len mismatch, NULL), PDG_ERR_OOM, PDG_ERR_CUDA.
+ */
+int pdg_set_w(pdg_ctx* ctx, const double* w, size_t len, int on_device);
+
+/*
+ * pdg_step -- advance nsteps palindromic steps of size dt (Section 3.2):
+ * M2(dt) = T(dt/2) C(dt) T(dt/2), with T the theta step
+ * (I - theta delta L_h) F^new = (I + (1-theta) delta L_h) F^old of eq. (3.11),
+ * solved exactly on the periodic mesh, and C eq. (3.12).  With
+ * PDG_SCHEME_M2_COLLAPSED the interior half transports are merged into T(dt)
+ * (collapsed Strang of Section 5.1).  Asynchronous on the context stream.
+ * dt may be negative (time-symmetric use).  nsteps = 0 is a no-op.
+ * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_CUDA.
+ */
+int pdg_step(pdg_ctx* ctx, double dt, int nsteps);
+
+/*
+ * pdg_get_w -- moments w_k = sum_i f_{k,i} (eq. (2.2) micro_to_macro), FP64.
+ *   out        layout [m][P_z][P_y][P_x], len = m * npoints doubles
+ *   on_device  1: out is a device pointer (written on the context stream, asynchronous);
+ *              0: host memory (the stream is synchronised before returning)
+ * A host read uses a device staging buffer of len doubles, allocated on first use.
+ * Errors: PDG_ERR_STATE, PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA.
+ */
+int pdg_get_w(pdg_ctx* ctx, double* out, size_t len, int on_device);
+
+/*
+ * pdg_get_f / pdg_set_f -- read or overwrite the kinetic state f (the only state
+ * the scheme keeps, the "low-storage" property of Section 4.4); a get/set pair
+ * is a checkpoint / restore.  Layout [m][2D][P_z][P_y][P_x], len = f_len doubles.
+ * on_device as for pdg_get_w / pdg_set_w.  Errors: PDG_ERR_STATE, PDG_ERR_ARG, PDG_ERR_CUDA.
+ */
+int pdg_get_f(pdg_ctx* ctx, double* out, size_t len, int on_device);
+int pdg_set_f(pdg_ctx* ctx, const double* f, size_t len, int on_device);
+
+/*
+ * pdg_get_points -- physical GL coordinates along one axis (eq. (3.3) map_GL:
+ * x = c h + (h/2)(1 + x^_j)), computed by the library's own quadrature.
+ *   axis  0..dim-1;  out: host buffer of len = P_axis doubles.
+ * Errors: PDG_ERR_ARG.
+ */
+int pdg_get_points(const pdg_ctx* ctx, int axis, double* out, size_t len);
+
+/* pdg_get_info -- sizes of the context (see pdg_info).  Errors: PDG_ERR_ARG. */
+int pdg_get_info(const pdg_ctx* ctx, pdg_info* info);
+
+/*
+ * pdg_get_line_coefs -- the per-cell transport coefficients the sweep uses for
+ * axis-aligned velocity +lambda e_axis and sub-step delta (host, for inspection
+ * and tests): E = B^{-1}(I - (1-theta) nu K) (n x n, row-major), the inflow
+ * vector q, and the ratio beta of the periodic inflow recurrence, where
+ * nu = 2 lambda delta / h_axis, K = Dm + w_0^{-1} e_0 e_0^T, B = I + theta nu K.
+ *   E: n*n doubles, q: n doubles, beta: 1 double (n = order + 1).
+ * Errors: PDG_ERR_STATE (no model), PDG_ERR_ARG.
+ */
+int pdg_get_line_coefs(const pdg_ctx* ctx, int axis, double delta, double* E, double* q, double* beta);
+
+/* pdg_synchronize -- wait for all work issued on the context stream.  Errors: PDG_ERR_CUDA. */
+int pdg_synchronize(pdg_ctx* ctx);
+
+/*
+ * Kernel timing.  When enabled, pdg_step records CUDA events on the context
+ * stream around every launch and accumulates, per kernel kind, the number of
+ * launches and their summed duration (read back after a synchronisation).
+ *   kind 0 = transport pass (axes before the last; T or T T, no collision)
+ *   kind 1 = last-axis pass (T, fused collision, T)
+ *   kind 2 = state kernels (set_w / get_w)
+ * pdg_timing_enable(ctx, 1) resets the counters.  pdg_timing_read fills up to
+ * max_kinds entries of launches[] and ms[] and synchronises the stream.
+ */
+int pdg_timing_enable(pdg_ctx* ctx, int enable);
+int pdg_timing_read(pdg_ctx* ctx, long long* launches, double* ms, int max_kinds);
+
+/*
+ * pdg_set_launch -- override the launch shape of one pass kind (0 or 1 as above):
+ *   lpb    lines per thread block (>= 1), nseg: segments per line (>= 1),
+ *   ngroup field groups per block (>= 1); lpb*nseg*ngroup <= 512.
+ * All zeros restores the built-in heuristic.  Used by the autotuner.
+ * Errors: PDG_ERR_ARG.
+ */
+int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
+
+/* pdg_destroy -- free the context and its device memory (NULL is a no-op). */
+int pdg_destroy(pdg_ctx* ctx);
+
+/* pdg_last_error -- text of the last error of ctx (never NULL; "" if none). */
+const char* pdg_last_error(const pdg_ctx* ctx);
+
+/* pdg_status_string -- static text of a status code. */
+const char* pdg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDG_H */

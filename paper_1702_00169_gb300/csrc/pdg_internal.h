@@ -1,0 +1,80 @@
+// Internal declarations shared by the host plan, the kernels and the C ABI layer.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#define PDG_MAXN 5          // GL points per cell and axis (degree <= 4)
+#define PDG_MAXM 5          // conserved variables (3-D Euler)
+#define PDG_MAXF 30         // fields m * 2D
+#define PDG_MAXOPS 4        // operations fused in one pass
+
+// Per-cell coefficients of one theta transport sub-step along one axis, for the
+// traversal direction of the velocity (negative velocities traverse the line
+// backwards, which maps them onto the positive case: the GL nodes are symmetric).
+//
+// For cell c (traversal order) with old values f_c and new values fn_c:
+//   fn_c = E f_c + q z_{c-1},   z_{c-1} = za x_{c-1} + zb u_{c-1},
+// where x_{c-1} is the NEW and u_{c-1} the OLD value at the last node of the
+// upwind cell.  The last node obeys the scalar periodic recurrence
+//   x_c = alpha_c + beta x_{c-1},  alpha_c = (E f_c)_{n-1} + q_{n-1} zb u_{c-1},
+//   beta = q_{n-1} za.
+struct PdgCoef {
+  double E[PDG_MAXN * PDG_MAXN];  // row-major n x n
+  double q[PDG_MAXN];
+  double za, zb, beta;
+  double betaL0, betaL1;  // beta^Lbase, beta^(Lbase+1): segment lengths of the launch
+  double inv_ring;        // 1 / (1 - beta^N)
+  int W;                  // window (cells) when truncated
+  int full;               // 1: aggregate whole segments and close the ring exactly
+};
+
+struct PdgModel {
+  int kind;      // PDG_MODEL_*
+  int dim;       // D
+  int m;         // conserved variables
+  int nv;        // 2D
+  double lambda;
+  double omega;
+  double a[3];
+  double gravity;
+  double gamma;
+  double cadv[6];  // advection: 1/(2D) + s_i a_axis / (2 lambda) per population (f^eq_i / w)
+};
+
+enum { PDG_OP_NONE = 0, PDG_OP_T = 1, PDG_OP_C = 2 };
+
+struct PdgPass {
+  double* f;
+  long long field_stride;  // points per field
+  long long stride;        // point stride along the line
+  long long lineA, s1, s2; // base(l) = (l % lineA) * s1 + (l / lineA) * s2
+  int nlines;              // line positions in the pass
+  int npl;                 // points per line, P = ncell * n
+  int ncell;               // cells per line
+  int nseg, lpb, ngroup;   // launch shape
+  int nops;
+  int op[PDG_MAXOPS];
+  int opcoef[PDG_MAXOPS];
+  int ntf;                     // transported fields
+  int tfield[2 * PDG_MAXM];    // field index (k * 2D + i)
+  int tdir[2 * PDG_MAXM];      // +1 / -1
+  PdgCoef coef[2];
+  PdgModel model;
+};
+
+// ---- host plan (pdg_plan.cpp) ----
+// Gauss-Lobatto nodes/weights of degree d (ascending) and Dm[j*n+i] = l_i'(x_j).
+int pdg_plan_gl(int d, double* x, double* w);
+void pdg_plan_dmat(int n, const double* x, double* Dm);
+// Transport coefficients for degree d, nu = 2 lambda delta / h, weight theta.
+// Fills E, q, za, zb, beta (not the launch-dependent fields).  Returns 0 on success.
+int pdg_plan_coef(int d, double nu, double theta, PdgCoef* c);
+// Smallest K >= 1 with |beta|^K <= 2^-60 (window that makes truncation exact to rounding).
+int pdg_plan_window(double beta);
+
+// ---- kernels (pdg_kernels.cu) ----
+// All return a cudaError_t cast to int.
+int pdg_launch_pass(const PdgPass& p, void* stream);
+int pdg_launch_set_feq(double* f, long long npoints, const PdgModel& m, void* stream);
+int pdg_launch_get_w(const double* f, double* w, long long npoints, const PdgModel& m, void* stream);

@@ -1,0 +1,164 @@
+// Host plan: Gauss-Lobatto quadrature and the per-cell transport coefficients.
+//
+// Section 3.1: nodal DG on the (d+1) Gauss-Lobatto points of [-1, 1] with the
+// Lagrange basis; eq. (3.7) DG_reduit on an affine Cartesian cell of edge h
+// reduces, for v = +lambda e_a, to the line system
+//     d/dt f_c = -(2 lambda / h) [K f_c - w_0^{-1} e_0 f_{c-1, d}],
+//     K = Dm + w_0^{-1} e_0 e_0^T,  Dm[j][i] = l_i'(x_j),
+// using the summation-by-parts identity W Dm + Dm^T W = e_d e_d^T - e_0 e_0^T of
+// GL quadrature.  The theta step of eq. (3.11) (theta = 1/2) with nu = 2 lambda delta / h:
+//     B fn_c - theta nu w_0^{-1} e_0 x_{c-1} = (I - (1-theta) nu K) f_c + (1-theta) nu w_0^{-1} e_0 u_{c-1}
+// with B = I + theta nu K, hence fn_c = E f_c + g (x_{c-1} + ((1-theta)/theta) u_{c-1}),
+// E = B^{-1}(I - (1-theta) nu K), g = B^{-1} theta nu w_0^{-1} e_0.
+//
+// Everything is computed in double with FP contraction disabled (build flag), so
+// the x86-64 and aarch64 builds produce identical coefficients.
+#include <cmath>
+#include <cstring>
+
+#include "pdg_internal.h"
+
+// Legendre P_k(x) and its derivative by the three-term recurrence.
+static void legendre(int k, double x, double* p, double* dp) {
+  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  if (k == 0) { *p = 1.0; *dp = 0.0; return; }
+  for (int j = 2; j <= k; ++j) {
+    double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+    double d2 = d0 + (2.0 * j - 1.0) * p1;  // P_j' = P_{j-2}' + (2j-1) P_{j-1}
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+  }
+  *p = p1; *dp = d1;
+}
+
+// GL nodes: x_0 = -1, x_d = +1 and the roots of P_d' (Newton on P_d' with
+// P_d'' = (2x P_d' - d(d+1) P_d) / (1 - x^2), started from Chebyshev-Lobatto points);
+// weights w_j = 2 / (d (d+1) P_d(x_j)^2).
+int pdg_plan_gl(int d, double* x, double* w) {
+  if (d < 1 || d > 16) return -1;
+  const double pi = 3.14159265358979323846;
+  for (int j = 0; j <= d; ++j) {
+    if (j == 0) { x[j] = -1.0; continue; }
+    if (j == d) { x[j] = 1.0; continue; }
+    double t = -std::cos(pi * j / d);
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(d, t, &p, &dp);
+      double ddp = (2.0 * t * dp - d * (d + 1.0) * p) / (1.0 - t * t);
+      double step = dp / ddp;
+      t -= step;
+      if (std::fabs(step) < 1e-17) break;
+    }
+    x[j] = t;
+  }
+  // exact symmetry of the node set
+  for (int j = 0; j <= d / 2; ++j) {
+    double s = 0.5 * (x[d - j] - x[j]);
+    x[j] = -s; x[d - j] = s;
+  }
+  if (d % 2 == 0) x[d / 2] = 0.0;
+  for (int j = 0; j <= d; ++j) {
+    double p, dp;
+    legendre(d, x[j], &p, &dp);
+    w[j] = 2.0 / (d * (d + 1.0) * p * p);
+  }
+  return 0;
+}
+
+// Dm[j*n + i] = l_i'(x_j) by the barycentric formula (Berrut & Trefethen, SIAM Review 2004):
+// with b_i = 1 / prod_{k != i} (x_i - x_k): l_i'(x_j) = (b_i / b_j) / (x_j - x_i), j != i,
+// and the diagonal from sum_i l_i' = 0.
+void pdg_plan_dmat(int n, const double* x, double* Dm) {
+  double b[16];
+  for (int i = 0; i < n; ++i) {
+    double p = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != i) p *= (x[i] - x[k]);
+    b[i] = 1.0 / p;
+  }
+  for (int j = 0; j < n; ++j) {
+    double diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      if (i == j) continue;
+      double v = (b[i] / b[j]) / (x[j] - x[i]);
+      Dm[j * n + i] = v;
+      diag -= v;
+    }
+    Dm[j * n + j] = diag;
+  }
+}
+
+// Solve A X = R (n x n, k right-hand sides, row-major) by Gaussian elimination
+// with partial pivoting; A and R are overwritten.  Returns 0 on success.
+static int solve(int n, int k, double* A, double* R) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) return -1;
+    if (piv != c) {
+      for (int j = 0; j < n; ++j) { double t = A[c * n + j]; A[c * n + j] = A[piv * n + j]; A[piv * n + j] = t; }
+      for (int j = 0; j < k; ++j) { double t = R[c * k + j]; R[c * k + j] = R[piv * k + j]; R[piv * k + j] = t; }
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double fct = A[r * n + c] / A[c * n + c];
+      if (fct == 0.0) continue;
+      for (int j = c; j < n; ++j) A[r * n + j] -= fct * A[c * n + j];
+      for (int j = 0; j < k; ++j) R[r * k + j] -= fct * R[c * k + j];
+    }
+  }
+  for (int r = 0; r < n; ++r) {
+    double inv = A[r * n + r];
+    for (int j = 0; j < k; ++j) R[r * k + j] /= inv;
+  }
+  return 0;
+}
+
+int pdg_plan_coef(int d, double nu, double theta, PdgCoef* c) {
+  const int n = d + 1;
+  if (n > PDG_MAXN || !(theta >= 0.0 && theta <= 1.0) || !std::isfinite(nu)) return -1;
+  double x[PDG_MAXN], w[PDG_MAXN], Dm[PDG_MAXN * PDG_MAXN];
+  if (pdg_plan_gl(d, x, w)) return -1;
+  pdg_plan_dmat(n, x, Dm);
+  double K[PDG_MAXN * PDG_MAXN];
+  std::memcpy(K, Dm, sizeof(double) * n * n);
+  K[0] += 1.0 / w[0];
+  // A = B = I + theta nu K ; right-hand sides: [I - (1-theta) nu K | theta nu/w0 e0 | (1-theta) nu/w0 e0]
+  double A[PDG_MAXN * PDG_MAXN];
+  const int k = n + 2;
+  double R[PDG_MAXN * (PDG_MAXN + 2)];
+  for (int r = 0; r < n; ++r) {
+    for (int j = 0; j < n; ++j) {
+      double id = (r == j) ? 1.0 : 0.0;
+      A[r * n + j] = id + theta * nu * K[r * n + j];
+      R[r * k + j] = id - (1.0 - theta) * nu * K[r * n + j];
+    }
+    R[r * k + n] = (r == 0) ? theta * nu / w[0] : 0.0;
+    R[r * k + n + 1] = (r == 0) ? (1.0 - theta) * nu / w[0] : 0.0;
+  }
+  if (solve(n, k, A, R)) return -1;
+  std::memset(c, 0, sizeof(*c));
+  for (int r = 0; r < n; ++r)
+    for (int j = 0; j < n; ++j) c->E[r * n + j] = R[r * k + j];
+  if (theta > 0.0) {
+    for (int r = 0; r < n; ++r) c->q[r] = R[r * k + n];  // g
+    c->za = 1.0;
+    c->zb = (1.0 - theta) / theta;
+  } else {
+    for (int r = 0; r < n; ++r) c->q[r] = R[r * k + n + 1];  // p (explicit step)
+    c->za = 0.0;
+    c->zb = 1.0;
+  }
+  c->beta = c->q[n - 1] * c->za;
+  return 0;
+}
+
+int pdg_plan_window(double beta) {
+  double a = std::fabs(beta);
+  if (a == 0.0) return 1;
+  if (a >= 1.0) return 1 << 30;
+  double K = std::ceil(-60.0 * std::log(2.0) / std::log(a));
+  if (K < 1.0) K = 1.0;
+  if (K > (double)(1 << 30)) return 1 << 30;
+  return (int)K;
+}

@@ -1,0 +1,210 @@
+"""Thin ctypes binding of libpdg.so (include/pdg.h).  Argument marshalling only.
+
+Every function of the C ABI is exposed under the same name with the same
+arguments (pointers given as integers, numpy arrays or torch tensors).  The
+class :class:`Solver` is a small convenience wrapper used by the tests and
+``bench.py``.  There is no CPU fallback: importing this module raises if the
+CUDA library has not been built (``__graft_entry__.build()``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpdg.so")
+
+PDG_OK = 0
+PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA, PDG_ERR_STATE, PDG_ERR_TIMEOUT, PDG_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+PDG_MODEL_ADVECTION, PDG_MODEL_SHALLOW_WATER, PDG_MODEL_EULER = 0, 1, 2
+PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED = 0, 1
+PDG_PREC_FP64 = 0
+
+KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER}
+SCHEME = {"M2": PDG_SCHEME_M2, "M2_collapsed": PDG_SCHEME_M2_COLLAPSED}
+
+
+class pdg_model_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("scheme", ctypes.c_int), ("precision", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("lambda_", ctypes.c_double), ("a", ctypes.c_double * 3),
+                ("gravity", ctypes.c_double), ("gamma", ctypes.c_double), ("omega", ctypes.c_double),
+                ("theta", ctypes.c_double)]
+
+
+class pdg_info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("order", ctypes.c_int), ("m", ctypes.c_int), ("nv", ctypes.c_int),
+                ("ncell", ctypes.c_int * 3), ("npts", ctypes.c_int * 3), ("npoints", ctypes.c_longlong),
+                ("nfields", ctypes.c_longlong), ("w_len", ctypes.c_longlong), ("f_len", ctypes.c_longlong),
+                ("h", ctypes.c_double * 3)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libpdg.so not built at {LIB_PATH}; run __graft_entry__.build()")
+lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+_D = ctypes.c_double
+_SIGS = {
+    "pdg_create_mesh": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _I,
+                             ctypes.POINTER(_D), ctypes.c_uint, _P]),
+    "pdg_set_model": (_I, [_P, ctypes.POINTER(pdg_model_desc)]),
+    "pdg_set_w": (_I, [_P, _P, _SZ, _I]),
+    "pdg_step": (_I, [_P, _D, _I]),
+    "pdg_get_w": (_I, [_P, _P, _SZ, _I]),
+    "pdg_get_f": (_I, [_P, _P, _SZ, _I]),
+    "pdg_set_f": (_I, [_P, _P, _SZ, _I]),
+    "pdg_get_points": (_I, [_P, _I, _P, _SZ]),
+    "pdg_get_info": (_I, [_P, ctypes.POINTER(pdg_info)]),
+    "pdg_get_line_coefs": (_I, [_P, _I, _D, _P, _P, _P]),
+    "pdg_synchronize": (_I, [_P]),
+    "pdg_timing_enable": (_I, [_P, _I]),
+    "pdg_timing_read": (_I, [_P, _P, _P, _I]),
+    "pdg_set_launch": (_I, [_P, _I, _I, _I, _I]),
+    "pdg_destroy": (_I, [_P]),
+    "pdg_last_error": (ctypes.c_char_p, [_P]),
+    "pdg_status_string": (ctypes.c_char_p, [_I]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+    globals()[_name] = _fn
+
+EXPORTED = tuple(_SIGS)
+
+
+class PdgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{pdg_status_string(status).decode()}: {msg}")
+        self.status = status
+
+
+def _ptr(x, want_device):
+    """(pointer, on_device, length) of a numpy array or torch tensor (FP64, contiguous)."""
+    if isinstance(x, np.ndarray):
+        if want_device is True:
+            raise ValueError("numpy array given where a device buffer is required")
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("numpy buffers must be contiguous float64")
+        return x.ctypes.data, 0, x.size
+    import torch  # device memory and streams come from torch
+
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(type(x))
+    if x.dtype != torch.float64 or not x.is_contiguous():
+        raise ValueError("tensors must be contiguous float64")
+    return x.data_ptr(), 1 if x.is_cuda else 0, x.numel()
+
+
+class Solver:
+    """Owns one pdg_ctx.  Methods map one-to-one onto the C ABI."""
+
+    def __init__(self, dim, n_macro, n_sub, order, lengths=None, stream=None):
+        self.ctx = _P()
+        nm = (_I * 3)(*(list(n_macro) + [1] * (3 - len(n_macro))))
+        ns = (_I * 3)(*(list(n_sub) + [1] * (3 - len(n_sub))))
+        ln = None if lengths is None else (_D * 3)(*(list(lengths) + [1.0] * (3 - len(lengths))))
+        st = _P(stream) if stream else None
+        r = pdg_create_mesh(ctypes.byref(self.ctx), dim, nm, ns, order, ln, (1 << dim) - 1, st)
+        if r != PDG_OK:
+            raise PdgError(r, "pdg_create_mesh")
+        self.dim = dim
+
+    def _check(self, r, what):
+        if r != PDG_OK:
+            raise PdgError(r, f"{what}: {pdg_last_error(self.ctx).decode()}")
+
+    def close(self):
+        if self.ctx:
+            pdg_destroy(self.ctx)
+            self.ctx = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        i = pdg_info()
+        self._check(pdg_get_info(self.ctx, ctypes.byref(i)), "pdg_get_info")
+        return i
+
+    def set_model(self, kind, lam, a=(0.0, 0.0, 0.0), gravity=9.81, gamma=1.4, omega=2.0, theta=0.5,
+                  scheme="M2", precision=PDG_PREC_FP64):
+        d = pdg_model_desc()
+        d.kind = KIND[kind] if isinstance(kind, str) else int(kind)
+        d.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
+        d.precision = precision
+        d.lambda_ = lam
+        for i in range(3):
+            d.a[i] = float(a[i]) if i < len(a) else 0.0
+        d.gravity, d.gamma, d.omega, d.theta = gravity, gamma, omega, theta
+        self._check(pdg_set_model(self.ctx, ctypes.byref(d)), "pdg_set_model")
+
+    def points(self, axis):
+        n = self.info().npts[axis]
+        out = np.empty(n, dtype=np.float64)
+        self._check(pdg_get_points(self.ctx, axis, out.ctypes.data, n), "pdg_get_points")
+        return out
+
+    def set_w(self, w):
+        p, dev, n = _ptr(w, None)
+        self._check(pdg_set_w(self.ctx, p, n, dev), "pdg_set_w")
+
+    def set_f(self, f):
+        p, dev, n = _ptr(f, None)
+        self._check(pdg_set_f(self.ctx, p, n, dev), "pdg_set_f")
+
+    def step(self, dt, nsteps):
+        self._check(pdg_step(self.ctx, dt, nsteps), "pdg_step")
+
+    def get_w(self, out=None):
+        i = self.info()
+        if out is None:
+            out = np.empty(i.w_len, dtype=np.float64)
+        p, dev, n = _ptr(out, None)
+        self._check(pdg_get_w(self.ctx, p, n, dev), "pdg_get_w")
+        return out
+
+    def get_f(self, out=None):
+        i = self.info()
+        if out is None:
+            out = np.empty(i.f_len, dtype=np.float64)
+        p, dev, n = _ptr(out, None)
+        self._check(pdg_get_f(self.ctx, p, n, dev), "pdg_get_f")
+        return out
+
+    def line_coefs(self, axis, delta):
+        n = self.info().order + 1
+        E = np.empty(n * n)
+        q = np.empty(n)
+        b = np.empty(1)
+        self._check(pdg_get_line_coefs(self.ctx, axis, delta, E.ctypes.data, q.ctypes.data, b.ctypes.data),
+                    "pdg_get_line_coefs")
+        return E.reshape(n, n), q, float(b[0])
+
+    def synchronize(self):
+        self._check(pdg_synchronize(self.ctx), "pdg_synchronize")
+
+    def timing_enable(self, on=True):
+        self._check(pdg_timing_enable(self.ctx, 1 if on else 0), "pdg_timing_enable")
+
+    def timing_read(self):
+        la = (ctypes.c_longlong * 3)()
+        ms = (ctypes.c_double * 3)()
+        self._check(pdg_timing_read(self.ctx, ctypes.addressof(la), ctypes.addressof(ms), 3), "pdg_timing_read")
+        return list(la), list(ms)
+
+    def set_launch(self, kind, lpb, nseg, ngroup):
+        self._check(pdg_set_launch(self.ctx, kind, lpb, nseg, ngroup), "pdg_set_launch")
+
+
+def solver_for(cfg, scheme="M2", stream=None):
+    """Create a Solver with mesh and model of a workloads.Config."""
+    s = Solver(cfg.dim, cfg.n_macro, cfg.n_sub, cfg.order, lengths=cfg.lengths[:cfg.dim], stream=stream)
+    s.set_model(cfg.kind, cfg.lam, a=cfg.a, gravity=cfg.gravity, gamma=cfg.gamma, omega=cfg.omega,
+                theta=cfg.theta, scheme=scheme)
+    return s

@@ -1,0 +1,51 @@
+"""Helpers shared by the GPU parity tests: run a problem through the C ABI and
+through the oracle on identical seeded inputs."""
+import numpy as np
+
+from oracle import models as OM
+from oracle import scheme as OS
+from oracle.dg import CartesianMesh
+
+ORACLE_KIND = {"advection": OM.ADVECTION, "shallow_water": OM.SHALLOW_WATER, "euler": OM.EULER}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def oracle_mesh(cfg):
+    return CartesianMesh(cfg.dim, cfg.ncells, cfg.order, lengths=cfg.lengths[:cfg.dim])
+
+
+def oracle_model(cfg):
+    return OM.Model(ORACLE_KIND[cfg.kind], cfg.dim, cfg.lam, a=cfg.a[:cfg.dim], gravity=cfg.gravity,
+                    gamma=cfg.gamma)
+
+
+def oracle_w0(cfg):
+    from paper_1702_00169_gb300 import workloads as W
+    mesh = oracle_mesh(cfg)
+    return W.initial_w(cfg, [mesh.coords1d(a) for a in range(cfg.dim)])
+
+
+def run_oracle(cfg, w0, dt, nsteps, scheme="M2", method="bloch", omega=None):
+    mesh = oracle_mesh(cfg)
+    model = oracle_model(cfg)
+    tr = OS.Transporter(mesh, model, theta=cfg.theta, method=method)
+    om = cfg.omega if omega is None else omega
+    return OS.run(OS.initial_state(model, w0), tr, model, dt, nsteps, om, scheme)
+
+
+def run_gpu(cfg, w0, dt, nsteps, scheme="M2", launch=None, omega=None, stream=None):
+    from paper_1702_00169_gb300 import pdg
+    import dataclasses
+    c = cfg if omega is None else dataclasses.replace(cfg, omega=omega)
+    s = pdg.solver_for(c, scheme=scheme, stream=stream)
+    if launch:
+        for kind, shape in launch.items():
+            s.set_launch(kind, *shape)
+    s.set_w(np.ascontiguousarray(w0.reshape(-1)))
+    s.step(dt, nsteps)
+    f = s.get_f().reshape((cfg.m, 2 * cfg.dim) + tuple(reversed(cfg.npoints_axis)))
+    s.close()
+    return f

@@ -1,0 +1,133 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+entry point declared in include/pdg.h, and validates arguments before touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from golden_util import expr, rows
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pdg():
+    from paper_1702_00169_gb300 import build as B
+    if not os.path.exists(B.LIB):
+        B.build()
+    from paper_1702_00169_gb300 import pdg as P
+    return P
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pdg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pdg_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(pdg):
+    names = _declared()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(pdg.lib, n), n
+        assert n in pdg.EXPORTED, n
+
+
+def test_create_mesh_validation(pdg):
+    ctx = ctypes.c_void_p()
+    nm = (ctypes.c_int * 3)(4, 4, 1)
+    ns = (ctypes.c_int * 3)(2, 2, 1)
+    assert pdg.pdg_create_mesh(ctypes.byref(ctx), 4, nm, ns, 2, None, 15, None) == pdg.PDG_ERR_ARG
+    assert pdg.pdg_create_mesh(ctypes.byref(ctx), 2, nm, ns, 0, None, 3, None) == pdg.PDG_ERR_ARG
+    assert pdg.pdg_create_mesh(ctypes.byref(ctx), 2, nm, ns, 5, None, 3, None) == pdg.PDG_ERR_ARG
+    assert pdg.pdg_create_mesh(ctypes.byref(ctx), 2, nm, ns, 2, None, 1, None) == pdg.PDG_ERR_UNSUPPORTED
+    bad = (ctypes.c_int * 3)(0, 4, 1)
+    assert pdg.pdg_create_mesh(ctypes.byref(ctx), 2, bad, ns, 2, None, 3, None) == pdg.PDG_ERR_ARG
+    assert pdg.pdg_create_mesh(None, 2, nm, ns, 2, None, 3, None) == pdg.PDG_ERR_ARG
+    assert pdg.pdg_create_mesh(ctypes.byref(ctx), 2, nm, ns, 2, None, 3, None) == pdg.PDG_OK
+    assert pdg.pdg_destroy(ctx) == pdg.PDG_OK
+    assert pdg.pdg_destroy(None) == pdg.PDG_OK
+
+
+def test_model_validation_and_state_order(pdg):
+    s = pdg.Solver(3, (2, 2, 2), (2, 2, 2), 2)
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_model("shallow_water", 8.0)
+    assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
+    for kw in ({"omega": 0.0}, {"omega": float("nan")}, {"theta": 1.5}):
+        with pytest.raises(pdg.PdgError) as e:
+            s.set_model("euler", 5.0, **kw)
+        assert e.value.status == pdg.PDG_ERR_ARG
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_model("euler", -1.0)
+    assert e.value.status == pdg.PDG_ERR_ARG
+    with pytest.raises(pdg.PdgError) as e:
+        s.step(0.01, 1)
+    assert e.value.status == pdg.PDG_ERR_STATE
+    s.set_model("euler", 5.0)
+    info = s.info()
+    assert (info.m, info.nv, info.nfields) == (5, 6, 30)
+    assert list(info.npts) == [12, 12, 12] and info.npoints == 12 ** 3
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_w(np.zeros(7))
+    assert e.value.status == pdg.PDG_ERR_ARG
+    with pytest.raises(pdg.PdgError) as e:
+        s.get_w()
+    assert e.value.status == pdg.PDG_ERR_STATE
+    s.close()
+
+
+def test_points_match_gl_closed_form(pdg):
+    """Library GL coordinates (its own quadrature) = cell h + (h/2)(1 + x^) with the
+    textbook nodes of tests/golden/gauss_lobatto.txt."""
+    for d in (1, 2, 3, 4):
+        s = pdg.Solver(2, (3, 2), (2, 1), d, lengths=(1.5, 0.5))
+        s.set_model("advection", 2.0, a=(1.0, 0.5))
+        nodes = [expr(x) for dd, x, w in rows("gauss_lobatto.txt") if int(dd) == d]
+        for a, (L, N) in enumerate(((1.5, 6), (0.5, 2))):
+            h = L / N
+            ref = np.array([c * h + 0.5 * h * (1 + x) for c in range(N) for x in nodes])
+            np.testing.assert_allclose(s.points(a), ref, rtol=0, atol=4e-16 * L)
+        s.close()
+
+
+def test_line_coefficients_d1_golden(pdg):
+    """E, q, beta computed by the library for d = 1, theta = 1/2, nu = 1 equal the hand
+    derivation of tests/golden/line_d1_theta_half_nu1.txt."""
+    g = {k: expr(v) for k, v in rows("line_d1_theta_half_nu1.txt")}
+    s = pdg.Solver(1, (7,), (1,), 1)
+    s.set_model("advection", 2.0, a=(0.5,))
+    h = 1.0 / 7
+    E, q, beta = s.line_coefs(0, h / (2 * 2.0))
+    np.testing.assert_allclose(E, [[g["E00"], g["E01"]], [g["E10"], g["E11"]]], rtol=0, atol=2e-16)
+    np.testing.assert_allclose(q, [g["g0"], g["g1"]], rtol=0, atol=2e-16)
+    assert abs(beta - g["beta"]) < 2e-16
+    s.close()
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("nu,theta", [(1.0, 0.5), (2.0, 0.5), (5.0, 0.75), (1.0, 1.0)])
+def test_line_coefficients_vs_oracle_bloch_zero_mode(pdg, d, nu, theta):
+    """The per-cell operator of one CN step applied to one isolated periodic cell (N = 1,
+    so x_{c-1} is the cell itself) equals the oracle's Bloch step at kappa = 0."""
+    from oracle.transport import bloch_transport
+    s = pdg.Solver(1, (1,), (1,), d)
+    lam = 2.0
+    s.set_model("advection", lam, a=(0.5,), theta=theta)
+    delta = nu * 1.0 / (2 * lam)
+    E, q, beta = s.line_coefs(0, delta)
+    n = d + 1
+    f = np.random.default_rng(d).standard_normal(n)
+    # one cell ring: x = fn[n-1] solves x = alpha + beta x
+    if theta > 0:
+        za, zb = 1.0, (1 - theta) / theta
+    else:
+        za, zb = 0.0, 1.0
+    alpha = (E @ f)[n - 1] + q[n - 1] * zb * f[n - 1]
+    x = alpha / (1 - beta)
+    fn = E @ f + q * (za * x + zb * f[n - 1])
+    ref = bloch_transport(f, -1, +1, d, nu, theta)
+    np.testing.assert_allclose(fn, ref, rtol=0, atol=1e-13)
+    s.close()
