@@ -52,7 +52,7 @@ def transport_flops_per_dof(n):
 def collision_flops_sw():
     # moments 12 adds->9 adds; 1/h (1 div), u, v (2 mul), p = 0.5 g h h (2 mul), 4 flux
     # products (2 FMA + 2 mul = 6 flops); c0 w_k (3 mul); per population fma + mul + add (4 flops) x 12
-    return 9 + 1 + 2 + 2 + 6 + 3 + 4 * 12
+    return 9 + 1 + 2 + 2 + 6 + 3 + 4 * 12 + 9  # = 80
 
 
 def parse_args():

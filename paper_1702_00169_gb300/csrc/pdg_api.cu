@@ -128,16 +128,30 @@ void choose_shape(const pdg_ctx* c, int kind, int nlines, int ncell, int ntf, in
   *ngroup = G;
 }
 
-// Fill the launch-dependent fields of a coefficient set for segments of a line of N cells.
-void finish_coef(PdgCoef* C, int N, int S) {
+// Fill the launch-dependent fields of a coefficient set for segments of a line of
+// N cells.  Returns 0, or -1 when the periodic system is singular (|beta| = 1 with
+// beta^N = 1).
+int finish_coef(PdgCoef* C, int N, int S) {
   const int Lbase = N / S;
-  const int W = pdg_plan_window(C->beta);
+  const double ab = std::fabs(C->beta);
+  C->rev = ab > 1.0 ? 1 : 0;
+  C->gamma = C->rev ? 1.0 / C->beta : 0.0;
+  const double r = C->rev ? C->gamma : C->beta;
+  const int W = pdg_plan_window(r);
   C->W = W;
   C->full = (W > Lbase) ? 1 : 0;
-  C->betaL0 = std::pow(C->beta, (double)Lbase);
-  C->betaL1 = std::pow(C->beta, (double)(Lbase + 1));
-  const double bN = std::pow(C->beta, (double)N);
-  C->inv_ring = 1.0 / (1.0 - bN);
+  C->betaL0 = std::pow(r, (double)Lbase);
+  C->betaL1 = std::pow(r, (double)(Lbase + 1));
+  const double rN = std::pow(r, (double)N);
+  if (!(std::fabs(1.0 - rN) > 1e-12)) return -1;
+  C->inv_ring = 1.0 / (1.0 - rN);
+  return 0;
+}
+
+// Window of a coefficient set in the stable direction.
+int stable_window(const PdgCoef& C) {
+  const double ab = std::fabs(C.beta);
+  return pdg_plan_window(ab > 1.0 ? 1.0 / C.beta : C.beta);
 }
 
 int plan_line_coef(const pdg_ctx* c, int axis, double delta, PdgCoef* C) {
@@ -193,13 +207,14 @@ int issue_pass(pdg_ctx* c, int axis, int nops, const int* ops, const int* coefid
   const int kind = has_c ? 1 : 0;
   int Wmax = 1;
   for (int i = 0; i < ncs; ++i) {
-    int W = pdg_plan_window(cs[i].beta);
+    int W = stable_window(cs[i]);
     if (W > Wmax) Wmax = W;
   }
   choose_shape(c, kind, p.nlines, p.ncell, p.ntf, Wmax, &p.lpb, &p.nseg, &p.ngroup);
   for (int i = 0; i < ncs && i < 2; ++i) {
     p.coef[i] = cs[i];
-    finish_coef(&p.coef[i], p.ncell, p.nseg);
+    if (finish_coef(&p.coef[i], p.ncell, p.nseg))
+      return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
   }
   p.model = c->model;
   (void)D;
@@ -415,6 +430,10 @@ int pdg_step(pdg_ctx* c, double dt, int nsteps) {
   for (int a = 0; a < D; ++a) {
     if (plan_line_coef(c, a, 0.5 * dt, &half[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
     if (plan_line_coef(c, a, dt, &full[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
+    // validate the periodic closure of every coefficient set before issuing any pass
+    PdgCoef t0 = half[a], t1 = full[a];
+    if (finish_coef(&t0, c->N[a], 1) || (c->scheme == PDG_SCHEME_M2_COLLAPSED && finish_coef(&t1, c->N[a], 1)))
+      return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
   }
   const int T = PDG_OP_T, C = PDG_OP_C;
   int r;

@@ -23,10 +23,16 @@ struct PdgCoef {
   double E[PDG_MAXN * PDG_MAXN];  // row-major n x n
   double q[PDG_MAXN];
   double za, zb, beta;
-  double betaL0, betaL1;  // beta^Lbase, beta^(Lbase+1): segment lengths of the launch
-  double inv_ring;        // 1 / (1 - beta^N)
+  // Launch-dependent fields.  With |beta| < 1 the recurrence runs downwind with
+  // ratio r = beta; with |beta| > 1 (negative time steps) it runs upwind,
+  // x_{c-1} = gamma (x_c - alpha_c) with r = gamma = 1/beta (rev = 1), which is
+  // the stable direction.
+  double gamma;           // 1 / beta when rev
+  double betaL0, betaL1;  // r^Lbase, r^(Lbase+1): segment lengths of the launch
+  double inv_ring;        // 1 / (1 - r^N)
   int W;                  // window (cells) when truncated
   int full;               // 1: aggregate whole segments and close the ring exactly
+  int rev;                // 1: upwind recurrence (|beta| > 1)
 };
 
 struct PdgModel {

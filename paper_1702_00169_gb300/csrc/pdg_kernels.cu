@@ -66,10 +66,10 @@ __device__ __forceinline__ void collide<MV_SW>(double* v, const PdgModel& M) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const double b = c0 * w[k];
-    v[4 * k + 0] = fma(c1, qx[k], b) + om1 * v[4 * k + 0];
-    v[4 * k + 1] = fma(-c1, qx[k], b) + om1 * v[4 * k + 1];
-    v[4 * k + 2] = fma(c1, qy[k], b) + om1 * v[4 * k + 2];
-    v[4 * k + 3] = fma(-c1, qy[k], b) + om1 * v[4 * k + 3];
+    v[4 * k + 0] = fma(om1, v[4 * k + 0], fma(c1, qx[k], b));
+    v[4 * k + 1] = fma(om1, v[4 * k + 1], fma(-c1, qx[k], b));
+    v[4 * k + 2] = fma(om1, v[4 * k + 2], fma(c1, qy[k], b));
+    v[4 * k + 3] = fma(om1, v[4 * k + 3], fma(-c1, qy[k], b));
   }
 }
 
@@ -107,8 +107,8 @@ __device__ __forceinline__ void collide_euler(double* v, const PdgModel& M) {
 #pragma unroll
     for (int k = 0; k < m; ++k) {
       const double bse = c0 * w[k];
-      v[k * nv + 2 * a] = fma(c1, q[k], bse) + om1 * v[k * nv + 2 * a];
-      v[k * nv + 2 * a + 1] = fma(-c1, q[k], bse) + om1 * v[k * nv + 2 * a + 1];
+      v[k * nv + 2 * a] = fma(om1, v[k * nv + 2 * a], fma(c1, q[k], bse));
+      v[k * nv + 2 * a + 1] = fma(om1, v[k * nv + 2 * a + 1], fma(-c1, q[k], bse));
     }
   }
 }
@@ -188,6 +188,53 @@ __device__ __forceinline__ void phase_sweep(double* lp, long long dstep, int c0,
   }
 }
 
+// Reverse mode (|beta| > 1): x_{c-1} = gamma (x_c - alpha_c).
+// Phase 1: y = x_{c0-1} from the first cells [c0, cend) of the segment, given the
+// old last-node value u0 of cell c0 - 1.
+template <int NP>
+__device__ __forceinline__ void phase_aggregate_rev(const double* lp, long long dstep, int c0, int cend,
+                                                    double u0, const PdgCoef& C, double* Y) {
+  double y = 0.0;
+  const double qz = C.q[NP - 1] * C.zb;
+  for (int c = cend - 1; c >= c0; --c) {
+    double v[NP];
+    load_cell<NP>(lp, dstep, c, v);
+    const double u = (c > c0) ? lp[((long long)(c - 1) * NP + (NP - 1)) * dstep] : u0;
+    double alpha = qz * u;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) alpha = fma(C.E[(NP - 1) * NP + j], v[j], alpha);
+    y = C.gamma * (y - alpha);
+  }
+  *Y = y;
+}
+
+// Phase 2 (reverse): sweep cells c1-1 down to c0 from x = x_{c1-1}; u0 = old value of
+// the last node of cell c0 - 1 (saved before any write).
+template <int NP>
+__device__ __forceinline__ void phase_sweep_rev(double* lp, long long dstep, int c0, int c1, double x,
+                                                double u0, const PdgCoef& C) {
+  const double qz = C.q[NP - 1] * C.zb;
+  for (int c = c1 - 1; c >= c0; --c) {
+    double v[NP];
+    load_cell<NP>(lp, dstep, c, v);
+    const double u = (c > c0) ? lp[((long long)(c - 1) * NP + (NP - 1)) * dstep] : u0;
+    double alpha = qz * u;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) alpha = fma(C.E[(NP - 1) * NP + j], v[j], alpha);
+    const double xm = C.gamma * (x - alpha);
+    const double z = fma(C.za, xm, C.zb * u);
+    double* p0 = lp + (long long)c * NP * dstep;
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      double acc = C.q[r] * z;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc = fma(C.E[r * NP + j], v[j], acc);
+      p0[r * dstep] = acc;
+    }
+    x = xm;
+  }
+}
+
 __device__ __forceinline__ long long line_base(const PdgPass& p, int line) {
   return (long long)(line % p.lineA) * p.s1 + (long long)(line / p.lineA) * p.s2;
 }
@@ -207,9 +254,15 @@ __device__ void transport_op(const PdgPass& p, const PdgCoef& C, double* smY, do
       double* fl = p.f + (long long)p.tfield[phi] * p.field_stride + base;
       const long long dstep = dir > 0 ? p.stride : -p.stride;
       double* lp = dir > 0 ? fl : fl + (long long)(p.npl - 1) * p.stride;
-      const int wstart = C.full ? c0 : c1 - C.W;
       double Y, U;
-      phase_aggregate<NP>(lp, dstep, N, wstart, c1, C, &Y, &U);
+      if (!C.rev) {
+        const int wstart = C.full ? c0 : c1 - C.W;
+        phase_aggregate<NP>(lp, dstep, N, wstart, c1, C, &Y, &U);
+      } else {
+        const int cp = (c0 == 0) ? N - 1 : c0 - 1;
+        U = lp[((long long)cp * NP + (NP - 1)) * dstep];
+        phase_aggregate_rev<NP>(lp, dstep, c0, C.full ? c1 : c0 + C.W, U, C, &Y);
+      }
       const int o = (phi * S + s) * LPB + l_in;
       smY[o] = Y;
       smU[o] = U;
@@ -223,23 +276,45 @@ __device__ void transport_op(const PdgPass& p, const PdgCoef& C, double* smY, do
       double* fl = p.f + (long long)p.tfield[phi] * p.field_stride + base;
       const long long dstep = dir > 0 ? p.stride : -p.stride;
       double* lp = dir > 0 ? fl : fl + (long long)(p.npl - 1) * p.stride;
-      const int sp = (s == 0) ? S - 1 : s - 1;
-      const double u = smU[(phi * S + sp) * LPB + l_in];
-      double x;
-      if (!C.full) {
-        x = smY[(phi * S + sp) * LPB + l_in];
-      } else {
-        double acc = 0.0, cf = 1.0;
-        int t = sp;
-        for (int j = 0; j < S; ++j) {
-          acc = fma(cf, smY[(phi * S + t) * LPB + l_in], acc);
-          const int len = seg_begin(t + 1, N, S) - seg_begin(t, N, S);
-          cf *= (len == Lbase) ? C.betaL0 : C.betaL1;
-          t = (t == 0) ? S - 1 : t - 1;
+      if (!C.rev) {
+        // inflow from the upwind segment s-1 (ring)
+        const int sp = (s == 0) ? S - 1 : s - 1;
+        const double u = smU[(phi * S + sp) * LPB + l_in];
+        double x;
+        if (!C.full) {
+          x = smY[(phi * S + sp) * LPB + l_in];
+        } else {
+          double acc = 0.0, cf = 1.0;
+          int t = sp;
+          for (int j = 0; j < S; ++j) {
+            acc = fma(cf, smY[(phi * S + t) * LPB + l_in], acc);
+            const int len = seg_begin(t + 1, N, S) - seg_begin(t, N, S);
+            cf *= (len == Lbase) ? C.betaL0 : C.betaL1;
+            t = (t == 0) ? S - 1 : t - 1;
+          }
+          x = acc * C.inv_ring;
         }
-        x = acc * C.inv_ring;
+        phase_sweep<NP>(lp, dstep, c0, c1, x, u, C);
+      } else {
+        // outflow value of the own segment from the downwind segment s+1 (ring)
+        const int sn = (s == S - 1) ? 0 : s + 1;
+        const double u0 = smU[(phi * S + s) * LPB + l_in];
+        double x;
+        if (!C.full) {
+          x = smY[(phi * S + sn) * LPB + l_in];
+        } else {
+          double acc = 0.0, cf = 1.0;
+          int t = sn;
+          for (int j = 0; j < S; ++j) {
+            acc = fma(cf, smY[(phi * S + t) * LPB + l_in], acc);
+            const int len = seg_begin(t + 1, N, S) - seg_begin(t, N, S);
+            cf *= (len == Lbase) ? C.betaL0 : C.betaL1;
+            t = (t == S - 1) ? 0 : t + 1;
+          }
+          x = acc * C.inv_ring;
+        }
+        phase_sweep_rev<NP>(lp, dstep, c0, c1, x, u0, C);
       }
-      phase_sweep<NP>(lp, dstep, c0, c1, x, u, C);
     }
   }
 }
