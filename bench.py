@@ -58,8 +58,10 @@ def collision_flops_sw():
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--workload", default="shallow_water", choices=["shallow_water", "batched"])
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--impl", default="pdg", choices=["pdg", "reference"])
     ap.add_argument("--scheme", default="M2", choices=["M2", "M2_collapsed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -132,7 +134,7 @@ class ClockSampler:
         return out
 
 
-def cpu_baseline(cfg_name, sample_steps):
+def cpu_baseline(cfg_name, sample_steps, warmup_steps=1):
     """Time the FP64 oracle (single thread) on a bounded sample of the workload, in a
     fresh process (no CUDA there; BLAS/OpenMP pinned to one thread)."""
     code = f"""
@@ -148,7 +150,8 @@ model = OM.Model(OM.SHALLOW_WATER, cfg.dim, cfg.lam, gravity=cfg.gravity)
 w0 = W.initial_w(cfg, [mesh.coords1d(a) for a in range(cfg.dim)])
 tr = OS.Transporter(mesh, model, theta=cfg.theta, method="bloch")
 f = OS.initial_state(model, w0)
-f = OS.m2_step(f, tr, model, cfg.dt, cfg.omega)
+for _ in range(max(1, {warmup_steps})):
+    f = OS.m2_step(f, tr, model, cfg.dt, cfg.omega)
 t0 = time.perf_counter()
 for _ in range({sample_steps}):
     f = OS.m2_step(f, tr, model, cfg.dt, cfg.omega)
@@ -172,9 +175,7 @@ def run_reference(args, cfg):
     if rank != 0:
         return
     # each reference step = one M2 step of the oracle on a bounded sample of the workload
-    sample_steps = max(1, args.steps)
-    warm = max(0, args.warmup)
-    res = cpu_baseline(cfg.name, sample_steps if sample_steps <= 200 else 200) if warm >= 0 else None
+    res = cpu_baseline(cfg.name, max(1, args.steps), max(1, args.warmup))
     value = res["value"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
@@ -188,13 +189,86 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def bench_batched(args):
+    """256 independent shallow-water meshes (8..96 macrocells per axis x 4x4 subcells,
+    degrees 1-4, per-instance dt at CFL 1) advanced by persistent batched launches
+    replayed from a CUDA graph; compared with the same instances stepped one by one."""
+    import torch
+    from paper_1702_00169_gb300 import pdg
+    from paper_1702_00169_gb300 import workloads as W
+    K = args.steps if args.steps is not None else 20
+    insts = W.batched_instances()
+    stream = torch.cuda.Stream()
+    sol = []
+    for c in insts:
+        sv = pdg.solver_for(c, stream=stream.cuda_stream)
+        w0 = W.initial_w(c, [sv.points(a) for a in range(c.dim)])
+        sv.set_w(np.ascontiguousarray(w0.reshape(-1)))
+        sol.append(sv)
+    dts = [c.dt for c in insts]
+    dofs = sum(c.dofs for c in insts)
+    b = pdg.Batch(sol, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    if not args.no_autotune:
+        b.autotune(dts, reps=2)
+    tune_s = time.perf_counter() - t0
+    b.step(dts, K, use_graph=True)          # warm-up (captures the graph)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(str(torch.cuda.get_device_properties(0).uuid))
+    sampler.start()
+    time.sleep(0.4)
+    b.step(dts, K, use_graph=True)          # timed: graph replay
+    ms, launches = b.elapsed()
+    clocks = sampler.stop()
+    # same instances one after the other through pdg_step (heuristic shapes, no graph)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for sv, dt in zip(sol, dts):
+        sv.step(dt, 1)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for sv, dt in zip(sol, dts):
+        sv.step(dt, K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_serial = ev0.elapsed_time(ev1)
+    finite = all(bool(np.all(np.isfinite(sv.get_w()))) for sv in sol[:8])
+    b.close()
+    for sv in sol:
+        sv.close()
+    value = dofs * K / (ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": K,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched_shallow_water_256", "instances": len(insts), "dof": dofs,
+                       "mesh": "M x M macrocells, M ~ U{8..96}, 4x4 subcells, d ~ U{1..4} (seed 4)",
+                       "dt": "per instance, CFL 1", "graph": True, "autotuned": not args.no_autotune,
+                       "autotune_s": tune_s, "l2": "18 GB state >> L2"},
+            "gpu_launches": launches, "clocks": clocks,
+            "serial": {"value": dofs * K / (ms_serial * 1e-3), "ms": ms_serial,
+                       "note": "same instances, pdg_step one after the other, heuristic shapes"},
+            "speedup_vs_serial": ms_serial / ms, "state_finite": finite}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     from paper_1702_00169_gb300 import workloads as W
     cfg = W.SW_D2Q4
     if args.impl == "reference":
+        if args.steps is None:
+            args.steps = 20
+        if args.warmup is None:
+            args.warmup = 3
         run_reference(args, cfg)
         return
+    if args.workload == "batched":
+        bench_batched(args)
+        return
+    if args.steps is None:
+        args.steps = 1000
+    if args.warmup is None:
+        args.warmup = 20
 
     import torch
     ws, rank, local = dist_env()

@@ -222,13 +222,63 @@ int pdg_timing_enable(pdg_ctx* ctx, int enable);
 int pdg_timing_read(pdg_ctx* ctx, long long* launches, double* ms, int max_kinds);
 
 /*
- * pdg_set_launch -- override the launch shape of one pass kind (0 or 1 as above):
+ * pdg_set_launch -- override the launch shape of one pass kind: kind 0 / 1 as above
+ * for pdg_step launches (lpb*nseg*ngroup <= 512), kind 2 / 3 for the same pass kinds
+ * inside batched launches (lpb*nseg*ngroup <= 256):
  *   lpb    lines per thread block (>= 1), nseg: segments per line (>= 1),
- *   ngroup field groups per block (>= 1); lpb*nseg*ngroup <= 512.
- * All zeros restores the built-in heuristic.  Used by the autotuner.
+ *   ngroup field groups per block (>= 1).
+ * All zeros restores the built-in heuristic.  Used by the autotuners.
  * Errors: PDG_ERR_ARG.
  */
 int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
+
+/* pdg_get_launch -- read the launch shape override of a kind 0..3 (zeros = heuristic). */
+int pdg_get_launch(const pdg_ctx* ctx, int kind, int* lpb, int* nseg, int* ngroup);
+
+/*
+ * pdg_autotune -- pick the launch shapes of both pass kinds for this mesh and model.
+ * Every candidate (lines per block, segments, field groups) is timed with CUDA events
+ * over `reps` launches of the steady-state pass of a step of size dt, on a scratch
+ * copy of the state (the state is not modified; a temporary of f_len doubles is
+ * allocated and freed), and the fastest is stored as the pdg_set_launch override.
+ * Results are unchanged up to rounding (the segment split changes the summation
+ * order of the periodic closure).  Synchronises the stream.
+ * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA.
+ */
+int pdg_autotune(pdg_ctx* ctx, double dt, int reps);
+
+/*
+ * Batched execution (many independent meshes of different size, degree and model
+ * in one persistent launch per stage).  Stage t runs the t-th pass of the schedule
+ * of every instance that has one (the schedule of pdg_step); inside a stage the work
+ * items (one thread block's lines of one pass) are ordered by cost, largest first,
+ * and claimed by persistent blocks through an atomic counter.  A work item does the
+ * arithmetic of the single-mesh kernel with the same launch shape, so an instance
+ * gives the same result whatever its batch neighbours are.
+ *
+ * pdg_batch_create -- group n contexts (each with a model; the batch keeps the
+ *   context handles, which must outlive it) on one CUDA stream (NULL = default).
+ *   Errors: PDG_ERR_ARG, PDG_ERR_STATE (a context without model), PDG_ERR_OOM, PDG_ERR_CUDA.
+ * pdg_batch_step -- advance instance i by nsteps[i] palindromic steps of size dt[i]
+ *   (nsteps[i] = 0 leaves it untouched).  use_graph != 0 captures the stage launches
+ *   in a CUDA graph, cached and replayed while dt[] and nsteps[] repeat.
+ *   Asynchronous; the per-call work tables (a few bytes per pass and per instance)
+ *   live in device memory owned by the batch.
+ *   Errors: PDG_ERR_STATE (an instance without state), PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA.
+ * pdg_batch_elapsed -- device time (ms) of the last pdg_batch_step (CUDA events; waits
+ *   for it) and the number of kernel launches it issued.
+ * pdg_batch_autotune -- per class of instances (dimension, degree, cells per axis,
+ *   model, dt) time the candidate shapes of the batched kernel on a scratch copy of
+ *   one representative state and apply the fastest to the whole class.
+ * pdg_batch_destroy -- release the batch (not its contexts).
+ */
+typedef struct pdg_batch pdg_batch;
+int pdg_batch_create(pdg_batch** out, int n, pdg_ctx* const* ctxs, void* cuda_stream);
+int pdg_batch_step(pdg_batch* batch, const double* dt, const int* nsteps, int use_graph);
+int pdg_batch_elapsed(pdg_batch* batch, double* ms, long long* launches);
+int pdg_batch_autotune(pdg_batch* batch, const double* dt, int reps);
+int pdg_batch_destroy(pdg_batch* batch);
+const char* pdg_batch_last_error(const pdg_batch* batch);
 
 /* pdg_destroy -- free the context and its device memory (NULL is a no-op). */
 int pdg_destroy(pdg_ctx* ctx);

@@ -12,6 +12,7 @@
 // The collapsed scheme of Section 5.1 merges interior half steps into T(dt).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -42,12 +43,35 @@ struct pdg_ctx {
   bool has_state = false;
   double* wstage = nullptr;
   long long wstage_cap = 0;
-  int launch[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  int launch[2][3] = {{0, 0, 0}, {0, 0, 0}};   // single-mesh shape overrides per pass kind
+  int bshape[2][3] = {{0, 0, 0}, {0, 0, 0}};   // shapes inside batched launches (<= 256 threads)
   bool timing = false;
   long long t_launches[3] = {0, 0, 0};
   double t_ms[3] = {0, 0, 0};
   std::vector<PdgTimedLaunch> pending;
   std::vector<cudaEvent_t> event_pool;
+  std::string err;
+};
+
+struct pdg_batch {
+  std::vector<pdg_ctx*> inst;
+  cudaStream_t stream = nullptr;       // the caller's stream (may be the legacy default stream)
+  cudaStream_t cap = nullptr;          // private blocking stream used for graph capture and replay
+  int grid = 0;
+  size_t smem = 0;
+  // device tables of the last pdg_batch_step (kept alive for the captured graph)
+  PdgPass* d_desc = nullptr;
+  int* d_ent_desc = nullptr;
+  long long* d_ent_start = nullptr;
+  unsigned long long* d_counter = nullptr;
+  size_t cap_desc = 0, cap_ent = 0, cap_cnt = 0;
+  std::vector<int> st_off, st_nent;          // per stage: first entry, entries
+  std::vector<long long> st_total;           // per stage: work items
+  std::vector<char> sig;                      // signature of the tables (graph cache key)
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<char> gsig;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, ej = nullptr;
+  long long last_launches = 0;
   std::string err;
 };
 
@@ -95,24 +119,28 @@ int drain_timing(pdg_ctx* c) {
   return PDG_OK;
 }
 
-// Launch shape heuristic for one pass (lines per block, segments, field groups).
-void choose_shape(const pdg_ctx* c, int kind, int nlines, int ncell, int ntf, int W, int* lpb, int* nseg,
+// Launch shape heuristic for one pass (lines per block, segments, field groups)
+// with at most max_threads threads; ov (if ov[0] > 0) forces the shape.
+void choose_shape(const int* ov, int max_threads, int nlines, int ncell, int ntf, int W, int* lpb, int* nseg,
                   int* ngroup) {
-  const int* ov = c->launch[kind];
-  if (ov[0] > 0) {
+  if (ov && ov[0] > 0) {
     *lpb = ov[0];
     *nseg = ov[1] < ncell ? ov[1] : ncell;
     *ngroup = ov[2] < ntf ? ov[2] : ntf;
+    while ((long long)(*lpb) * (*nseg) * (*ngroup) > max_threads && *nseg > 1) --(*nseg);
+    while ((long long)(*lpb) * (*nseg) * (*ngroup) > max_threads && *ngroup > 1) --(*ngroup);
+    while ((long long)(*lpb) * (*nseg) * (*ngroup) > max_threads && *lpb > 1) --(*lpb);
     return;
   }
   int L = 8;
   if (nlines < L) L = nlines < 1 ? 1 : nlines;
+  if (L > max_threads) L = max_threads;
   int G = ntf;
   const long long target = 152LL * 1024;
   long long s_target = (target + (long long)nlines * G - 1) / ((long long)nlines * G);
-  int s_max_threads = 512 / (L * G);
+  int s_max_threads = max_threads / (L * G);
   if (s_max_threads < 1) {
-    G = 512 / L;
+    G = max_threads / L;
     if (G < 1) G = 1;
     s_max_threads = 1;
   }
@@ -159,12 +187,18 @@ int plan_line_coef(const pdg_ctx* c, int axis, double delta, PdgCoef* C) {
   return pdg_plan_coef(c->order, nu, c->theta, C);
 }
 
-// Issue one pass along `axis` with the op list (ops: PDG_OP_*, coef: index into cs).
-int issue_pass(pdg_ctx* c, int axis, int nops, const int* ops, const int* coefidx, const PdgCoef* cs,
-               int ncs) {
-  PdgPass p;
+// Kind of a pass: 0 = transport only, 1 = contains the collision.
+int pass_kind(const PdgPassSpec& sp) {
+  for (int o = 0; o < sp.nops; ++o)
+    if (sp.op[o] == PDG_OP_C) return 1;
+  return 0;
+}
+
+// Fill a launch descriptor for one pass of context c (shape from ov or the heuristic).
+int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov, PdgPass* out) {
+  PdgPass& p = *out;
   std::memset(&p, 0, sizeof(p));
-  const int D = c->dim;
+  const int axis = sp.axis;
   p.f = c->f;
   p.field_stride = c->npoints;
   const long long Px = c->P[0], Py = c->P[1], Pz = c->P[2];
@@ -197,27 +231,29 @@ int issue_pass(pdg_ctx* c, int axis, int nops, const int* ops, const int* coefid
     p.tfield[2 * k + 1] = k * nv + 2 * axis + 1;
     p.tdir[2 * k + 1] = -1;
   }
-  bool has_c = false;
-  p.nops = nops;
-  for (int o = 0; o < nops; ++o) {
-    p.op[o] = ops[o];
-    p.opcoef[o] = coefidx[o];
-    has_c |= ops[o] == PDG_OP_C;
+  p.nops = sp.nops;
+  for (int o = 0; o < sp.nops; ++o) {
+    p.op[o] = sp.op[o];
+    p.opcoef[o] = sp.opcoef[o];
   }
-  const int kind = has_c ? 1 : 0;
+  const int kind = pass_kind(sp);
+  p.mv = kind ? pdg_model_variant(c->model) : 5 /* no collision */;
   int Wmax = 1;
-  for (int i = 0; i < ncs; ++i) {
-    int W = stable_window(cs[i]);
+  for (int i = 0; i < sp.ncs; ++i) {
+    int W = stable_window(sp.cs[i]);
     if (W > Wmax) Wmax = W;
   }
-  choose_shape(c, kind, p.nlines, p.ncell, p.ntf, Wmax, &p.lpb, &p.nseg, &p.ngroup);
-  for (int i = 0; i < ncs && i < 2; ++i) {
-    p.coef[i] = cs[i];
+  choose_shape(ov, max_threads, p.nlines, p.ncell, p.ntf, Wmax, &p.lpb, &p.nseg, &p.ngroup);
+  for (int i = 0; i < sp.ncs && i < 2; ++i) {
+    p.coef[i] = sp.cs[i];
     if (finish_coef(&p.coef[i], p.ncell, p.nseg))
       return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
   }
   p.model = c->model;
-  (void)D;
+  return PDG_OK;
+}
+
+int launch_timed(pdg_ctx* c, const PdgPass& p, int kind) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
     e0 = get_event(c);
@@ -230,6 +266,62 @@ int issue_pass(pdg_ctx* c, int axis, int nops, const int* ops, const int* coefid
   if (c->timing) {
     PDG_CUDA(c, cudaEventRecord(e1, c->stream));
     c->pending.push_back({kind, e0, e1});
+  }
+  return PDG_OK;
+}
+
+int issue_pass(pdg_ctx* c, const PdgPassSpec& sp) {
+  PdgPass p;
+  const int kind = pass_kind(sp);
+  if (int r = make_pass(c, sp, 512, c->launch[kind], &p)) return r;
+  return launch_timed(c, p, kind);
+}
+
+PdgPassSpec spec(int axis, int nops, const int* ops, const int* ci, const PdgCoef* cs, int ncs) {
+  PdgPassSpec sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.axis = axis;
+  sp.nops = nops;
+  for (int o = 0; o < nops; ++o) {
+    sp.op[o] = ops[o];
+    sp.opcoef[o] = ci[o];
+  }
+  sp.ncs = ncs;
+  for (int i = 0; i < ncs; ++i) sp.cs[i] = cs[i];
+  return sp;
+}
+
+// The pass list of nsteps palindromic steps (see the schedule at the top of this file).
+int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+  out.clear();
+  if (nsteps <= 0) return PDG_OK;
+  const int D = c->dim, L = D - 1;
+  PdgCoef half[3], full[3];
+  for (int a = 0; a < D; ++a) {
+    if (plan_line_coef(c, a, 0.5 * dt, &half[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
+    if (plan_line_coef(c, a, dt, &full[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
+    PdgCoef t0 = half[a], t1 = full[a];
+    if (finish_coef(&t0, c->N[a], 1) || (c->scheme == PDG_SCHEME_M2_COLLAPSED && finish_coef(&t1, c->N[a], 1)))
+      return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
+  }
+  const int T = PDG_OP_T, C = PDG_OP_C;
+  const int z1[1] = {0}, z2[2] = {0, 0}, z3[3] = {0, 0, 0};
+  const int o1[1] = {T}, o2[2] = {T, T}, o3[3] = {T, C, T};
+  if (c->scheme == PDG_SCHEME_M2) {
+    for (int a = 0; a < L; ++a) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
+    for (int s = 0; s < nsteps; ++s) {
+      out.push_back(spec(L, 3, o3, z3, &half[L], 1));
+      for (int a = 0; a < L; ++a) out.push_back(spec(a, s < nsteps - 1 ? 2 : 1, o2, z2, &half[a], 1));
+    }
+  } else {
+    for (int a = 0; a < L; ++a) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
+    for (int s = 0; s < nsteps; ++s) {
+      PdgCoef cs[2] = {half[L], full[L]};
+      const int ops[2] = {T, C}, ci[2] = {s == 0 ? 0 : 1, 0};
+      out.push_back(spec(L, 2, ops, ci, cs, 2));
+      for (int a = 0; a < L; ++a) out.push_back(spec(a, 1, o1, z1, s < nsteps - 1 ? &full[a] : &half[a], 1));
+    }
+    out.push_back(spec(L, 1, o1, z1, &half[L], 1));
   }
   return PDG_OK;
 }
@@ -425,48 +517,10 @@ int pdg_step(pdg_ctx* c, double dt, int nsteps) {
   if (!c->has_state) return fail(c, PDG_ERR_STATE, "pdg_step before pdg_set_w / pdg_set_f");
   if (nsteps < 0 || !std::isfinite(dt)) return fail(c, PDG_ERR_ARG, "bad dt or nsteps");
   if (nsteps == 0) return PDG_OK;
-  const int D = c->dim, L = D - 1;
-  PdgCoef half[3], full[3];
-  for (int a = 0; a < D; ++a) {
-    if (plan_line_coef(c, a, 0.5 * dt, &half[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
-    if (plan_line_coef(c, a, dt, &full[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
-    // validate the periodic closure of every coefficient set before issuing any pass
-    PdgCoef t0 = half[a], t1 = full[a];
-    if (finish_coef(&t0, c->N[a], 1) || (c->scheme == PDG_SCHEME_M2_COLLAPSED && finish_coef(&t1, c->N[a], 1)))
-      return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
-  }
-  const int T = PDG_OP_T, C = PDG_OP_C;
-  int r;
-  if (c->scheme == PDG_SCHEME_M2) {
-    for (int a = 0; a < L; ++a) {
-      const int ops[1] = {T}, ci[1] = {0};
-      if ((r = issue_pass(c, a, 1, ops, ci, &half[a], 1))) return r;
-    }
-    for (int s = 0; s < nsteps; ++s) {
-      const int ops[3] = {T, C, T}, ci[3] = {0, 0, 0};
-      if ((r = issue_pass(c, L, 3, ops, ci, &half[L], 1))) return r;
-      for (int a = 0; a < L; ++a) {
-        const int ops2[2] = {T, T}, ci2[2] = {0, 0};
-        if ((r = issue_pass(c, a, s < nsteps - 1 ? 2 : 1, ops2, ci2, &half[a], 1))) return r;
-      }
-    }
-  } else {
-    for (int a = 0; a < L; ++a) {
-      const int ops[1] = {T}, ci[1] = {0};
-      if ((r = issue_pass(c, a, 1, ops, ci, &half[a], 1))) return r;
-    }
-    for (int s = 0; s < nsteps; ++s) {
-      PdgCoef cs[2] = {half[L], full[L]};
-      const int ops[2] = {T, C}, ci[2] = {s == 0 ? 0 : 1, 0};
-      if ((r = issue_pass(c, L, 2, ops, ci, cs, 2))) return r;
-      for (int a = 0; a < L; ++a) {
-        const int ops2[1] = {T}, ci2[1] = {0};
-        if ((r = issue_pass(c, a, 1, ops2, ci2, s < nsteps - 1 ? &full[a] : &half[a], 1))) return r;
-      }
-    }
-    const int ops[1] = {T}, ci[1] = {0};
-    if ((r = issue_pass(c, L, 1, ops, ci, &half[L], 1))) return r;
-  }
+  std::vector<PdgPassSpec> sched;
+  if (int r = build_schedule(c, dt, nsteps, sched)) return r;
+  for (const auto& sp : sched)
+    if (int r = issue_pass(c, sp)) return r;
   return PDG_OK;
 }
 
@@ -547,16 +601,18 @@ int pdg_timing_read(pdg_ctx* c, long long* launches, double* ms, int max_kinds) 
 }
 
 int pdg_set_launch(pdg_ctx* c, int kind, int lpb, int nseg, int ngroup) {
-  if (!c || kind < 0 || kind > 1) return PDG_ERR_ARG;
+  if (!c || kind < 0 || kind > 3) return PDG_ERR_ARG;
+  int* slot = kind < 2 ? c->launch[kind] : c->bshape[kind - 2];
+  const int maxt = kind < 2 ? 512 : pdg_batch_threads();
   if (lpb == 0 && nseg == 0 && ngroup == 0) {
-    c->launch[kind][0] = c->launch[kind][1] = c->launch[kind][2] = 0;
+    slot[0] = slot[1] = slot[2] = 0;
     return PDG_OK;
   }
-  if (lpb < 1 || nseg < 1 || ngroup < 1 || (long long)lpb * nseg * ngroup > 512)
+  if (lpb < 1 || nseg < 1 || ngroup < 1 || (long long)lpb * nseg * ngroup > maxt)
     return fail(c, PDG_ERR_ARG, "bad launch shape");
-  c->launch[kind][0] = lpb;
-  c->launch[kind][1] = nseg;
-  c->launch[kind][2] = ngroup;
+  slot[0] = lpb;
+  slot[1] = nseg;
+  slot[2] = ngroup;
   return PDG_OK;
 }
 
@@ -571,6 +627,539 @@ int pdg_destroy(pdg_ctx* c) {
   if (c->f) cudaFree(c->f);
   if (c->wstage) cudaFree(c->wstage);
   delete c;
+  return PDG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner: time candidate launch shapes of the two pass kinds on a scratch copy
+// of the state and keep the fastest.
+
+namespace {
+
+struct Shape {
+  int lpb, nseg, ngroup;
+};
+
+std::vector<Shape> shape_candidates(int max_threads, int ncell, int ntf, int W) {
+  std::vector<Shape> out;
+  const int lpbs[] = {4, 8, 16, 32};
+  const int segs[] = {1, 2, 4, 8, 16, 32};
+  const int groups[] = {1, 2, ntf / 2, ntf};
+  for (int L : lpbs)
+    for (int S : segs) {
+      if (S > ncell) continue;
+      if (S > 1 && ncell / S < W) continue;  // keep the window closure
+      for (int gi = 0; gi < 4; ++gi) {
+        const int G = groups[gi];
+        if (G < 1 || ntf % G) continue;
+        if (gi > 0 && G == groups[gi - 1]) continue;
+        const int t = L * S * G;
+        if (t > max_threads || t < max_threads / 4) continue;
+        out.push_back({L, S, G});
+      }
+    }
+  if (out.empty()) out.push_back({8, 1, 1});
+  return out;
+}
+
+// Runs `reps` launches of one pass on a scratch copy of the state and returns the mean ms.
+template <class LaunchFn>
+int time_launches(pdg_ctx* c, int reps, LaunchFn fn, float* ms) {
+  cudaEvent_t a, b;
+  PDG_CUDA(c, cudaEventCreate(&a));
+  PDG_CUDA(c, cudaEventCreate(&b));
+  int r = fn();  // warm-up
+  if (r) return r;
+  PDG_CUDA(c, cudaEventRecord(a, c->stream));
+  for (int i = 0; i < reps; ++i)
+    if ((r = fn())) return r;
+  PDG_CUDA(c, cudaEventRecord(b, c->stream));
+  PDG_CUDA(c, cudaEventSynchronize(b));
+  float t = 0.f;
+  PDG_CUDA(c, cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t / (reps > 0 ? reps : 1);
+  return PDG_OK;
+}
+
+// Representative pass specs of kind 0 and 1 for time step dt.
+int representative_specs(pdg_ctx* c, double dt, PdgPassSpec* sp, bool* have) {
+  std::vector<PdgPassSpec> sched;
+  if (int r = build_schedule(c, dt, 2, sched)) return r;
+  have[0] = have[1] = false;
+  for (const auto& s : sched) {
+    const int k = pass_kind(s);
+    // prefer the steady-state passes (T T and T C T)
+    if (!have[k] || s.nops > sp[k].nops) {
+      sp[k] = s;
+      have[k] = true;
+    }
+  }
+  return PDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdg_autotune(pdg_ctx* c, double dt, int reps) {
+  if (!c) return PDG_ERR_ARG;
+  if (!c->has_state) return fail(c, PDG_ERR_STATE, "pdg_autotune needs a state (pdg_set_w)");
+  if (!std::isfinite(dt) || dt == 0.0 || reps < 1) return fail(c, PDG_ERR_ARG, "bad dt or reps");
+  PdgPassSpec sp[2];
+  bool have[2];
+  if (int r = representative_specs(c, dt, sp, have)) return r;
+  const size_t bytes = sizeof(double) * (size_t)c->model.m * c->model.nv * c->npoints;
+  double* scratch = nullptr;
+  cudaError_t e = cudaMalloc((void**)&scratch, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, PDG_ERR_OOM, "pdg_autotune: no memory for the scratch state");
+  }
+  double* keep = c->f;
+  int status = PDG_OK;
+  e = cudaMemcpyAsync(scratch, c->f, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) status = cuda_fail(c, e, "pdg_autotune copy");
+  c->f = scratch;
+  const bool tim = c->timing;
+  c->timing = false;
+  for (int k = 0; k < 2 && status == PDG_OK; ++k) {
+    if (!have[k]) continue;
+    PdgPass p0;
+    if ((status = make_pass(c, sp[k], 512, nullptr, &p0))) break;
+    int W = 1;
+    for (int i = 0; i < sp[k].ncs; ++i) W = std::max(W, stable_window(sp[k].cs[i]));
+    float best = 1e30f;
+    Shape bs{0, 0, 0};
+    for (const Shape& s : shape_candidates(512, p0.ncell, p0.ntf, W)) {
+      int ov[3] = {s.lpb, s.nseg, s.ngroup};
+      PdgPass p;
+      if ((status = make_pass(c, sp[k], 512, ov, &p))) break;
+      float ms = 0.f;
+      status = time_launches(c, reps, [&]() {
+        int er = pdg_launch_pass(p, (void*)c->stream);
+        return er ? cuda_fail(c, (cudaError_t)er, "autotune launch") : PDG_OK;
+      }, &ms);
+      if (status) break;
+      if (ms < best) {
+        best = ms;
+        bs = s;
+      }
+    }
+    if (status == PDG_OK && bs.lpb > 0) {
+      c->launch[k][0] = bs.lpb;
+      c->launch[k][1] = bs.nseg;
+      c->launch[k][2] = bs.ngroup;
+    }
+  }
+  c->timing = tim;
+  c->f = keep;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(scratch);
+  return status;
+}
+
+int pdg_get_launch(const pdg_ctx* c, int kind, int* lpb, int* nseg, int* ngroup) {
+  if (!c || kind < 0 || kind > 3 || !lpb || !nseg || !ngroup) return PDG_ERR_ARG;
+  const int* slot = kind < 2 ? c->launch[kind] : c->bshape[kind - 2];
+  *lpb = slot[0];
+  *nseg = slot[1];
+  *ngroup = slot[2];
+  return PDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched execution of many independent meshes.
+
+}  // extern "C"
+
+extern "C" const char* pdg_batch_last_error(const pdg_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" {
+
+int pdg_batch_create(pdg_batch** out, int n, pdg_ctx* const* ctxs, void* cuda_stream) {
+  if (!out) return PDG_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || !ctxs) return PDG_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i] || !ctxs[i]->has_model) return PDG_ERR_STATE;
+  pdg_batch* b = new (std::nothrow) pdg_batch();
+  if (!b) return PDG_ERR_OOM;
+  b->inst.assign(ctxs, ctxs + n);
+  b->stream = (cudaStream_t)cuda_stream;
+  int maxcarry = 0;
+  for (int i = 0; i < n; ++i) {
+    const int ntf = 2 * ctxs[i]->model.m;
+    maxcarry = std::max(maxcarry, 2 * ntf * pdg_batch_threads());
+  }
+  b->smem = pdg_batch_smem(maxcarry);
+  int e = pdg_batch_grid(b->smem, &b->grid);
+  // Graphs cannot be captured on the legacy default stream: capture and replay on a
+  // private blocking stream joined to the caller's stream with events.
+  if (e || cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ej, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamDefault) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return PDG_ERR_CUDA;
+  }
+  *out = b;
+  return PDG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int bfail(pdg_batch* b, int code, const std::string& m) {
+  b->err = m;
+  return code;
+}
+
+template <class T>
+int ensure_dev(pdg_batch* b, T** p, size_t* cap, size_t need) {
+  if (need <= *cap) return PDG_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, PDG_ERR_OOM, "batch table allocation failed");
+  }
+  *cap = need;
+  return PDG_OK;
+}
+
+double item_cost(const PdgPass& p) {
+  int nt = 0, nc = 0;
+  for (int o = 0; o < p.nops; ++o) {
+    nt += p.op[o] == PDG_OP_T;
+    nc += p.op[o] == PDG_OP_C;
+  }
+  const int np = p.npl / p.ncell;
+  const double per_point = (double)p.ntf * nt * (np + 2) + (double)nc * p.model.m * p.model.nv * 6.0;
+  return (double)p.lpb * p.npl * per_point;
+}
+
+// Build the stage tables for dt[i], nsteps[i] and upload them.
+int batch_prepare(pdg_batch* b, const double* dt, const int* nsteps) {
+  const int n = (int)b->inst.size();
+  std::vector<PdgPass> descs;
+  std::vector<std::vector<int>> plist(n);  // per instance: descriptor index per pass
+  std::vector<std::vector<long long>> pblocks(n);
+  for (int i = 0; i < n; ++i) {
+    pdg_ctx* c = b->inst[i];
+    if (!c->has_state) return bfail(b, PDG_ERR_STATE, "batch instance without state");
+    if (nsteps[i] < 0 || !std::isfinite(dt[i])) return bfail(b, PDG_ERR_ARG, "bad dt or nsteps");
+    std::vector<PdgPassSpec> sched;
+    if (int r = build_schedule(c, dt[i], nsteps[i], sched)) return bfail(b, r, c->err);
+    int prev_kind = -1, prev_nops = -1, prev_idx = -1;
+    const PdgCoef* prev_cs = nullptr;
+    (void)prev_cs;
+    for (const auto& sp : sched) {
+      const int kind = pass_kind(sp);
+      PdgPass p;
+      if (int r = make_pass(c, sp, pdg_batch_threads(), c->bshape[kind], &p)) return bfail(b, r, c->err);
+      // reuse the previous identical descriptor of this instance (steady-state passes repeat)
+      int idx = -1;
+      for (int j = (int)descs.size() - 1; j >= 0 && j >= (int)descs.size() - 4; --j)
+        if (std::memcmp(&descs[j], &p, sizeof(PdgPass)) == 0) {
+          idx = j;
+          break;
+        }
+      if (idx < 0) {
+        idx = (int)descs.size();
+        descs.push_back(p);
+      }
+      plist[i].push_back(idx);
+      pblocks[i].push_back((p.nlines + p.lpb - 1) / p.lpb);
+      prev_kind = kind;
+      prev_nops = sp.nops;
+      prev_idx = idx;
+    }
+    (void)prev_kind;
+    (void)prev_nops;
+    (void)prev_idx;
+  }
+  size_t nst = 0;
+  for (int i = 0; i < n; ++i) nst = std::max(nst, plist[i].size());
+  std::vector<int> ent_desc;
+  std::vector<long long> ent_start;
+  b->st_off.assign(nst, 0);
+  b->st_nent.assign(nst, 0);
+  b->st_total.assign(nst, 0);
+  for (size_t t = 0; t < nst; ++t) {
+    std::vector<std::pair<double, int>> order;  // (cost per item, instance)
+    for (int i = 0; i < n; ++i)
+      if (t < plist[i].size()) order.push_back({item_cost(descs[plist[i][t]]), i});
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
+    b->st_off[t] = (int)ent_desc.size();
+    long long acc = 0;
+    for (auto& o : order) {
+      ent_desc.push_back(plist[o.second][t]);
+      ent_start.push_back(acc);
+      acc += pblocks[o.second][t];
+    }
+    b->st_nent[t] = (int)order.size();
+    b->st_total[t] = acc;
+  }
+  if (int r = ensure_dev(b, &b->d_desc, &b->cap_desc, std::max<size_t>(1, descs.size()))) return r;
+  if (int r = ensure_dev(b, &b->d_ent_desc, &b->cap_ent, std::max<size_t>(1, ent_desc.size()))) return r;
+  size_t cap2 = b->cap_ent;
+  b->cap_ent = 0;
+  long long* es = b->d_ent_start;
+  size_t cap_es = (es && cap2 >= ent_start.size()) ? cap2 : 0;
+  (void)cap_es;
+  if (b->d_ent_start) cudaFree(b->d_ent_start);
+  b->d_ent_start = nullptr;
+  cudaError_t e = cudaMalloc((void**)&b->d_ent_start, sizeof(long long) * std::max<size_t>(1, ent_start.size()));
+  b->cap_ent = cap2;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, PDG_ERR_OOM, "batch table allocation failed");
+  }
+  if (int r = ensure_dev(b, &b->d_counter, &b->cap_cnt, std::max<size_t>(1, nst))) return r;
+  e = cudaMemcpyAsync(b->d_desc, descs.data(), sizeof(PdgPass) * descs.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_ent_desc, ent_desc.data(), sizeof(int) * ent_desc.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_ent_start, ent_start.data(), sizeof(long long) * ent_start.size(),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host vectors die at return
+  if (e != cudaSuccess) return bfail(b, PDG_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+  // signature: the tables themselves
+  b->sig.clear();
+  auto app = [&](const void* p, size_t nb) {
+    const char* q = (const char*)p;
+    b->sig.insert(b->sig.end(), q, q + nb);
+  };
+  app(descs.data(), sizeof(PdgPass) * descs.size());
+  app(ent_desc.data(), sizeof(int) * ent_desc.size());
+  app(ent_start.data(), sizeof(long long) * ent_start.size());
+  return PDG_OK;
+}
+
+int batch_issue(pdg_batch* b, cudaStream_t st) {
+  const size_t nst = b->st_nent.size();
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long) * std::max<size_t>(1, nst), st);
+  if (e != cudaSuccess) return bfail(b, PDG_ERR_CUDA, std::string("batch counters: ") + cudaGetErrorString(e));
+  long long launches = 0;
+  for (size_t t = 0; t < nst; ++t) {
+    int r = pdg_launch_batch(b->d_desc, b->d_ent_desc + b->st_off[t], b->d_ent_start + b->st_off[t],
+                             b->st_nent[t], b->st_total[t], b->d_counter + t, b->grid, b->smem, (void*)st);
+    if (r) return bfail(b, PDG_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString((cudaError_t)r));
+    launches += b->st_total[t] > 0;
+  }
+  b->last_launches = launches;
+  return PDG_OK;
+}
+
+// End a capture left open by an error so that the stream is usable again.
+void abort_capture(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(st, &g);
+    if (g) cudaGraphDestroy(g);
+  }
+  cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdg_batch_step(pdg_batch* b, const double* dt, const int* nsteps, int use_graph) {
+  if (!b || !dt || !nsteps) return PDG_ERR_ARG;
+  if (int r = batch_prepare(b, dt, nsteps)) return r;
+  cudaError_t e = cudaEventRecord(b->e0, b->stream);
+  if (e != cudaSuccess) return bfail(b, PDG_ERR_CUDA, cudaGetErrorString(e));
+  if (!use_graph) {
+    if (int r = batch_issue(b, b->stream)) return r;
+  } else {
+    if (!b->gexec || b->gsig != b->sig) {
+      if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        abort_capture(b->cap);
+        return bfail(b, PDG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+      }
+      int r = batch_issue(b, b->cap);
+      e = cudaStreamEndCapture(b->cap, &g);
+      if (r || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        abort_capture(b->cap);
+        return r ? r : bfail(b, PDG_ERR_CUDA, std::string("capture end: ") + cudaGetErrorString(e));
+      }
+      e = cudaGraphInstantiate(&b->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->gexec = nullptr;
+        return bfail(b, PDG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+      b->gsig = b->sig;
+    }
+    // order: caller stream -> capture stream (graph) -> caller stream
+    e = cudaEventRecord(b->ej, b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ej, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->gexec, b->cap);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ej, b->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ej, 0);
+    if (e != cudaSuccess) return bfail(b, PDG_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  }
+  e = cudaEventRecord(b->e1, b->stream);
+  if (e != cudaSuccess) return bfail(b, PDG_ERR_CUDA, cudaGetErrorString(e));
+  return PDG_OK;
+}
+
+int pdg_batch_elapsed(pdg_batch* b, double* ms, long long* launches) {
+  if (!b) return PDG_ERR_ARG;
+  cudaError_t e = cudaEventSynchronize(b->e1);
+  if (e != cudaSuccess) return bfail(b, PDG_ERR_CUDA, cudaGetErrorString(e));
+  float t = 0.f;
+  e = cudaEventElapsedTime(&t, b->e0, b->e1);
+  if (e != cudaSuccess) return bfail(b, PDG_ERR_CUDA, cudaGetErrorString(e));
+  if (ms) *ms = t;
+  if (launches) *launches = b->last_launches;
+  return PDG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Autotuning classes: cells per line rounded to a power of two, CFL number rounded to
+// a power of two (the window of the periodic closure depends on it).
+int size_bucket(const pdg_ctx* c) {
+  int m = 0;
+  for (int a = 0; a < c->dim; ++a) m = std::max(m, c->N[a]);
+  int b = 0;
+  while ((1 << b) < m) ++b;
+  return b;
+}
+int cfl_bucket(const pdg_ctx* c, double dt) {
+  const double nu = std::fabs(2.0 * c->model.lambda * dt / c->h[0]);
+  return (int)std::floor(std::log2(nu + 1e-300) + 0.5);
+}
+}  // namespace
+
+extern "C" {
+
+int pdg_batch_autotune(pdg_batch* b, const double* dt, int reps) {
+  if (!b || !dt || reps < 1) return PDG_ERR_ARG;
+  const int n = (int)b->inst.size();
+  // one representative per class (dimension, degree, cells per axis, model)
+  std::vector<int> rep(n, -1);
+  for (int i = 0; i < n; ++i) {
+    pdg_ctx* ci = b->inst[i];
+    for (int j = 0; j < i && rep[i] < 0; ++j) {
+      pdg_ctx* cj = b->inst[j];
+      if (rep[j] == j && ci->dim == cj->dim && ci->order == cj->order && ci->model.kind == cj->model.kind &&
+          size_bucket(ci) == size_bucket(cj) && cfl_bucket(ci, dt[i]) == cfl_bucket(cj, dt[j]))
+        rep[i] = j;
+    }
+    if (rep[i] < 0) rep[i] = i;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (rep[i] != i) continue;
+    pdg_ctx* c = b->inst[i];
+    if (!c->has_state) return bfail(b, PDG_ERR_STATE, "batch instance without state");
+    PdgPassSpec sp[2];
+    bool have[2];
+    if (int r = representative_specs(c, dt[i], sp, have)) return bfail(b, r, c->err);
+    const size_t bytes = sizeof(double) * (size_t)c->model.m * c->model.nv * c->npoints;
+    double* scratch = nullptr;
+    if (cudaMalloc((void**)&scratch, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return bfail(b, PDG_ERR_OOM, "autotune scratch");
+    }
+    cudaMemcpyAsync(scratch, c->f, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    double* keep = c->f;
+    c->f = scratch;
+    int status = PDG_OK;
+    int* d_ent = nullptr;
+    long long* d_start = nullptr;
+    unsigned long long* d_cnt = nullptr;
+    PdgPass* d_p = nullptr;
+    if (cudaMalloc((void**)&d_ent, sizeof(int)) || cudaMalloc((void**)&d_start, sizeof(long long)) ||
+        cudaMalloc((void**)&d_cnt, sizeof(unsigned long long)) || cudaMalloc((void**)&d_p, sizeof(PdgPass))) {
+      cudaGetLastError();
+      status = bfail(b, PDG_ERR_OOM, "autotune tables");
+    }
+    const int zero_i = 0;
+    const long long zero_l = 0;
+    if (status == PDG_OK) {
+      cudaMemcpy(d_ent, &zero_i, sizeof(int), cudaMemcpyHostToDevice);
+      cudaMemcpy(d_start, &zero_l, sizeof(long long), cudaMemcpyHostToDevice);
+    }
+    int best_shape[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    for (int k = 0; k < 2 && status == PDG_OK; ++k) {
+      if (!have[k]) continue;
+      PdgPass p0;
+      if ((status = make_pass(c, sp[k], pdg_batch_threads(), nullptr, &p0))) break;
+      int W = 1;
+      for (int q = 0; q < sp[k].ncs; ++q) W = std::max(W, stable_window(sp[k].cs[q]));
+      float best = 1e30f;
+      for (const Shape& s : shape_candidates(pdg_batch_threads(), p0.ncell, p0.ntf, W)) {
+        int ov[3] = {s.lpb, s.nseg, s.ngroup};
+        PdgPass p;
+        if ((status = make_pass(c, sp[k], pdg_batch_threads(), ov, &p))) break;
+        cudaMemcpyAsync(d_p, &p, sizeof(PdgPass), cudaMemcpyHostToDevice, c->stream);
+        const long long total = (p.nlines + p.lpb - 1) / p.lpb;
+        float ms = 0.f;
+        status = time_launches(c, reps, [&]() {
+          cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), c->stream);
+          int er = pdg_launch_batch(d_p, d_ent, d_start, 1, total, d_cnt, b->grid, b->smem, (void*)c->stream);
+          return er ? cuda_fail(c, (cudaError_t)er, "batch autotune launch") : PDG_OK;
+        }, &ms);
+        if (status) break;
+        if (ms < best) {
+          best = ms;
+          best_shape[k][0] = s.lpb;
+          best_shape[k][1] = s.nseg;
+          best_shape[k][2] = s.ngroup;
+        }
+      }
+    }
+    cudaStreamSynchronize(c->stream);
+    c->f = keep;
+    cudaFree(scratch);
+    cudaFree(d_ent);
+    cudaFree(d_start);
+    cudaFree(d_cnt);
+    cudaFree(d_p);
+    if (status) return bfail(b, status, c->err);
+    for (int j = 0; j < n; ++j)
+      if (rep[j] == i)
+        for (int k = 0; k < 2; ++k)
+          for (int q = 0; q < 3; ++q) b->inst[j]->bshape[k][q] = best_shape[k][q];
+  }
+  return PDG_OK;
+}
+
+int pdg_batch_destroy(pdg_batch* b) {
+  if (!b) return PDG_OK;
+  cudaStreamSynchronize(b->stream);
+  if (b->cap) cudaStreamSynchronize(b->cap);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->d_desc) cudaFree(b->d_desc);
+  if (b->d_ent_desc) cudaFree(b->d_ent_desc);
+  if (b->d_ent_start) cudaFree(b->d_ent_start);
+  if (b->d_counter) cudaFree(b->d_counter);
+  if (b->e0) cudaEventDestroy(b->e0);
+  if (b->e1) cudaEventDestroy(b->e1);
+  if (b->ej) cudaEventDestroy(b->ej);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
   return PDG_OK;
 }
 

@@ -65,8 +65,19 @@ struct PdgPass {
   int ntf;                     // transported fields
   int tfield[2 * PDG_MAXM];    // field index (k * 2D + i)
   int tdir[2 * PDG_MAXM];      // +1 / -1
+  int mv;                      // model variant of the collision (MV_* of pdg_device.cuh)
   PdgCoef coef[2];
   PdgModel model;
+};
+
+// A pass of the schedule before its launch shape is chosen.
+struct PdgPassSpec {
+  int axis;
+  int nops;
+  int op[PDG_MAXOPS];
+  int opcoef[PDG_MAXOPS];
+  int ncs;
+  PdgCoef cs[2];
 };
 
 // ---- host plan (pdg_plan.cpp) ----
@@ -84,3 +95,12 @@ int pdg_plan_window(double beta);
 int pdg_launch_pass(const PdgPass& p, void* stream);
 int pdg_launch_set_feq(double* f, long long npoints, const PdgModel& m, void* stream);
 int pdg_launch_get_w(const double* f, double* w, long long npoints, const PdgModel& m, void* stream);
+// Model variant index used by the kernels (MV_* in pdg_device.cuh) for a model / pass.
+int pdg_model_variant(const PdgModel& m);
+
+// ---- batched persistent kernel (pdg_batch.cu) ----
+int pdg_batch_threads();
+size_t pdg_batch_smem(int max_carry_doubles);
+int pdg_batch_grid(size_t smem, int* grid);
+int pdg_launch_batch(const PdgPass* d_descs, const int* d_ent_desc, const long long* d_ent_start, int nent,
+                     long long total, unsigned long long* d_counter, int grid, size_t smem, void* stream);

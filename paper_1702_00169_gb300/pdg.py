@@ -62,6 +62,14 @@ _SIGS = {
     "pdg_timing_enable": (_I, [_P, _I]),
     "pdg_timing_read": (_I, [_P, _P, _P, _I]),
     "pdg_set_launch": (_I, [_P, _I, _I, _I, _I]),
+    "pdg_get_launch": (_I, [_P, _I, _P, _P, _P]),
+    "pdg_autotune": (_I, [_P, _D, _I]),
+    "pdg_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P]),
+    "pdg_batch_step": (_I, [_P, _P, _P, _I]),
+    "pdg_batch_elapsed": (_I, [_P, _P, _P]),
+    "pdg_batch_autotune": (_I, [_P, _P, _I]),
+    "pdg_batch_destroy": (_I, [_P]),
+    "pdg_batch_last_error": (ctypes.c_char_p, [_P]),
     "pdg_destroy": (_I, [_P]),
     "pdg_last_error": (ctypes.c_char_p, [_P]),
     "pdg_status_string": (ctypes.c_char_p, [_I]),
@@ -200,6 +208,61 @@ class Solver:
 
     def set_launch(self, kind, lpb, nseg, ngroup):
         self._check(pdg_set_launch(self.ctx, kind, lpb, nseg, ngroup), "pdg_set_launch")
+
+
+    def get_launch(self, kind):
+        v = [ctypes.c_int(), ctypes.c_int(), ctypes.c_int()]
+        self._check(pdg_get_launch(self.ctx, kind, *[ctypes.addressof(x) for x in v]), "pdg_get_launch")
+        return tuple(x.value for x in v)
+
+    def autotune(self, dt, reps=3):
+        self._check(pdg_autotune(self.ctx, dt, reps), "pdg_autotune")
+
+
+class Batch:
+    """Owns one pdg_batch over existing Solver objects (which must outlive it)."""
+
+    def __init__(self, solvers, stream=None):
+        self.solvers = list(solvers)
+        arr = (_P * len(self.solvers))(*[s.ctx.value for s in self.solvers])
+        self.b = _P()
+        r = pdg_batch_create(ctypes.byref(self.b), len(self.solvers), ctypes.addressof(arr),
+                             _P(stream) if stream else None)
+        if r != PDG_OK:
+            raise PdgError(r, "pdg_batch_create")
+
+    def _check(self, r, what):
+        if r != PDG_OK:
+            raise PdgError(r, f"{what}: {pdg_batch_last_error(self.b).decode()}")
+
+    def step(self, dt, nsteps, use_graph=False):
+        n = len(self.solvers)
+        dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+        ns = np.ascontiguousarray(np.broadcast_to(np.asarray(nsteps, dtype=np.int32), (n,)))
+        self._check(pdg_batch_step(self.b, dts.ctypes.data, ns.ctypes.data, 1 if use_graph else 0),
+                    "pdg_batch_step")
+
+    def elapsed(self):
+        ms = ctypes.c_double()
+        la = ctypes.c_longlong()
+        self._check(pdg_batch_elapsed(self.b, ctypes.addressof(ms), ctypes.addressof(la)), "pdg_batch_elapsed")
+        return ms.value, la.value
+
+    def autotune(self, dt, reps=3):
+        n = len(self.solvers)
+        dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+        self._check(pdg_batch_autotune(self.b, dts.ctypes.data, reps), "pdg_batch_autotune")
+
+    def close(self):
+        if self.b:
+            pdg_batch_destroy(self.b)
+            self.b = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solver_for(cfg, scheme="M2", stream=None):

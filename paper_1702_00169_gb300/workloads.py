@@ -120,13 +120,20 @@ def _modes(rng, D, count, kmax):
 
 
 def _mode_sum(X, ks, amps, phases):
-    out = 0.0
-    for k, c, ph in zip(ks, amps, phases):
-        arg = 0.0
-        for a in range(len(X)):
-            arg = arg + k[a] * X[a]
-        out = out + c * np.cos(2.0 * math.pi * arg + ph)
-    return out
+    """sum_j amps_j cos(2 pi k_j . x + phases_j) on the tensor grid X, evaluated as the real
+    part of a rank-(number of modes) sum of separable complex exponentials (one matrix
+    product), not point by point."""
+    D = len(X)
+    xs = [np.asarray(X[a]).reshape(-1) for a in range(D)]          # 1-D coordinates, axis a
+    wj = amps * np.exp(1j * phases)
+    Ea = [np.exp(2j * np.pi * np.outer(ks[:, a], xs[a])) for a in range(D)]   # (J, P_a)
+    # A[j, rest] = w_j prod_{a >= 1} E_a[j, .] (numpy order: highest axis first)
+    A = wj[:, None]
+    for a in reversed(range(1, D)):
+        A = (A[:, :, None] * Ea[a][:, None, :]).reshape(len(wj), -1)
+    F = np.real(A.T @ Ea[0])                                        # (prod_{a>=1} P_a, P_0)
+    shape = tuple(len(xs[a]) for a in reversed(range(D)))
+    return F.reshape(shape)
 
 
 def _normalised_field(rng, D, count, kmax, ref_pts):
@@ -146,12 +153,11 @@ def initial_w(cfg, coords):
     rng = np.random.default_rng(cfg.seed)
     if cfg.kind == "advection":
         sigma = 0.1
-        g = 0.0
-        for shift in np.ndindex(*(3,) * D):
-            r2 = 0.0
-            for a in range(D):
-                r2 = r2 + (X[a] - 0.5 - (shift[a] - 1)) ** 2
-            g = g + np.exp(-r2 / (2.0 * sigma * sigma))
+        # periodised Gaussian: the sum over the 3^D images factorises per axis
+        g = 1.0
+        for a in range(D):
+            ga = sum(np.exp(-(X[a] - 0.5 - s) ** 2 / (2.0 * sigma * sigma)) for s in (-1.0, 0.0, 1.0))
+            g = g * ga
         ks = _modes(rng, D, 8, 4)
         phases = rng.uniform(0.0, 2.0 * math.pi, 8)
         w = g + _mode_sum(X, ks, np.full(8, 1e-2), phases)
@@ -172,3 +178,19 @@ def initial_w(cfg, coords):
         E = p / (cfg.gamma - 1.0) + 0.5 * rho * sum(ua * ua for ua in u)
         return np.stack([rho] + [rho * ua for ua in u] + [E]).astype(np.float64)
     raise ValueError(cfg.kind)
+
+
+def batched_instances(n=256, seed=4, m_range=(8, 96), n_sub=4, orders=(1, 2, 3, 4), kind="shallow_water"):
+    """Independent shallow-water instances of the batched workload: macrocell grid M x M
+    with M ~ U{m_range}, n_sub x n_sub subcells, degree ~ U{orders}; instance i has its
+    own initial-state seed (1000 * seed + i); dt from CFL 1 per instance."""
+    rng = np.random.default_rng(seed)
+    base = SW_D2Q4 if kind == "shallow_water" else ADVECTION_D2Q4
+    out = []
+    for i in range(n):
+        M = int(rng.integers(m_range[0], m_range[1] + 1))
+        d = int(rng.choice(orders))
+        out.append(base.scaled(n_macro=(M, M), n_sub=(n_sub, n_sub), name=f"{kind}_{i}_M{M}_d{d}"))
+        import dataclasses
+        out[-1] = dataclasses.replace(out[-1], order=d, seed=1000 * seed + i, steps=20)
+    return out
