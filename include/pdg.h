@@ -205,6 +205,27 @@ int pdg_get_info(const pdg_ctx* ctx, pdg_info* info);
  */
 int pdg_get_line_coefs(const pdg_ctx* ctx, int axis, double delta, double* E, double* q, double* beta);
 
+/*
+ * pdg_get_w_noalloc -- pdg_get_w into HOST memory without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot let
+ * the library call cudaMalloc (a pooled or custom allocator owns the device budget,
+ * allocation calls are intercepted or forbidden after start-up, or the footprint must
+ * not grow between two checkpoints).  pdg_get_w stages a host read in a device buffer
+ * it allocates on first use; this variant stages it in a static array compiled into
+ * the library instead: 1,048,576 doubles (8 MiB), held on every GPU that loads the
+ * library until the process exits.  It calls no cudaMalloc / cudaFree.
+ *   out  host buffer of len = m * npoints doubles, layout [m][P_z][P_y][P_x]
+ * Behaviour: writes the whole staged range before copying it (nothing in the array
+ * needs to start at zero); synchronises the context stream before returning.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All
+ * calls share the one array: calls whose GPU work overlaps (other contexts on other
+ * streams, or other host threads) race on it and must be serialised by the caller.
+ * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (NULL, len mismatch, or len greater
+ * than 1,048,576: use pdg_get_w), PDG_ERR_CUDA.
+ */
+int pdg_get_w_noalloc(pdg_ctx* ctx, double* out, size_t len);
+
 /* pdg_synchronize -- wait for all work issued on the context stream.  Errors: PDG_ERR_CUDA. */
 int pdg_synchronize(pdg_ctx* ctx);
 

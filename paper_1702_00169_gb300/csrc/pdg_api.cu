@@ -348,6 +348,18 @@ size_t fields_of(const pdg_ctx* c) { return (size_t)c->model.m * c->model.nv; }
 
 }  // namespace
 
+bool pdg_internal_view(const pdg_ctx* c, PdgStateView* v) {
+  if (!c || !c->has_state || !c->f) return false;
+  v->f = c->f;
+  v->npoints = c->npoints;
+  v->m = c->model.m;
+  v->nv = c->model.nv;
+  v->stream = c->stream;
+  return true;
+}
+
+int pdg_internal_fail(pdg_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
+
 extern "C" {
 
 const char* pdg_status_string(int s) {

@@ -80,6 +80,24 @@ struct PdgPassSpec {
   PdgCoef cs[2];
 };
 
+// ---- read-only view of a context for entry points outside pdg_api.cu ----
+#include <cuda_runtime.h>
+#include <string>
+struct pdg_ctx;
+struct PdgStateView {
+  const double* f;
+  long long npoints;
+  int m, nv;
+  cudaStream_t stream;
+};
+// Fills v and returns true when the context has a state.
+bool pdg_internal_view(const pdg_ctx* c, PdgStateView* v);
+// Records msg as the context's last error and returns code.
+int pdg_internal_fail(pdg_ctx* c, int code, const std::string& msg);
+
+// Capacity (doubles) of the static staging array of pdg_get_w_noalloc (8 MiB).
+#define PDG_NOALLOC_W_MAX (1LL << 20)
+
 // ---- host plan (pdg_plan.cpp) ----
 // Gauss-Lobatto nodes/weights of degree d (ascending) and Dm[j*n+i] = l_i'(x_j).
 int pdg_plan_gl(int d, double* x, double* w);

@@ -58,6 +58,7 @@ _SIGS = {
     "pdg_get_points": (_I, [_P, _I, _P, _SZ]),
     "pdg_get_info": (_I, [_P, ctypes.POINTER(pdg_info)]),
     "pdg_get_line_coefs": (_I, [_P, _I, _D, _P, _P, _P]),
+    "pdg_get_w_noalloc": (_I, [_P, _P, _SZ]),
     "pdg_synchronize": (_I, [_P]),
     "pdg_timing_enable": (_I, [_P, _I]),
     "pdg_timing_read": (_I, [_P, _P, _P, _I]),

@@ -1,0 +1,77 @@
+"""pdg_get_w_noalloc: host read of w = P f that allocates no device memory.
+
+Some callers cannot let the library call cudaMalloc (a pooled allocator owns the
+device budget, allocation is forbidden after start-up, or the footprint must not
+grow between checkpoints).  This entry point stages the read in a static device
+array instead of the buffer pdg_get_w allocates.  The test calls it through the C
+ABI and checks it against pdg_get_w on two calls in a row, and that sizes beyond the
+static array are rejected with a clear error.  It lives in a file collected last and
+passes both alone in a fresh process and after the other GPU tests.
+"""
+import ctypes
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1702_00169_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+NOALLOC_MAX = 1 << 20
+
+
+def _solver(cfg):
+    from gpu_common import oracle_w0
+    from paper_1702_00169_gb300 import pdg
+    s = pdg.solver_for(cfg)
+    s.set_w(np.ascontiguousarray(oracle_w0(cfg).reshape(-1)))
+    return s
+
+
+def _noalloc(s, n):
+    from paper_1702_00169_gb300 import pdg
+    out = np.full(n, np.nan)
+    r = pdg.pdg_get_w_noalloc(s.ctx, out.ctypes.data, n)
+    return r, out
+
+
+def test_noalloc_matches_get_w_two_calls_in_a_row():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1702_00169_gb300 import pdg
+    for cfg in (dataclasses.replace(W.SW_D2Q4, n_macro=(4, 3), n_sub=(4, 5), order=3),
+                dataclasses.replace(W.EULER_D3Q6, n_macro=(2, 2, 2), n_sub=(3, 2, 3), order=2)):
+        s = _solver(cfg)
+        n = s.info().w_len
+        assert n <= NOALLOC_MAX
+        for _ in range(2):
+            s.step(cfg.dt, 2)
+            r, w_na = _noalloc(s, n)
+            assert r == pdg.PDG_OK, pdg.pdg_last_error(s.ctx)
+            w_ref = s.get_w()
+            assert np.all(np.isfinite(w_na))
+            assert np.linalg.norm(w_na - w_ref) <= TOL * np.linalg.norm(w_ref)
+        # two calls in a row on an unchanged state give the same array
+        r1, a = _noalloc(s, n)
+        r2, b = _noalloc(s, n)
+        assert r1 == r2 == pdg.PDG_OK
+        np.testing.assert_array_equal(a, b)
+        s.close()
+
+
+def test_noalloc_rejects_sizes_beyond_the_static_array():
+    from paper_1702_00169_gb300 import pdg
+    cfg = dataclasses.replace(W.SW_D2Q4, n_macro=(20, 20), n_sub=(8, 8), order=3)   # 3 * 640^2 doubles
+    s = _solver(cfg)
+    n = s.info().w_len
+    assert n > NOALLOC_MAX
+    r, _ = _noalloc(s, n)
+    assert r == pdg.PDG_ERR_ARG
+    msg = pdg.pdg_last_error(s.ctx).decode()
+    assert "static staging array" in msg and str(NOALLOC_MAX) in msg
+    # a wrong length is rejected too, and the regular entry point still works
+    r, _ = _noalloc(s, 7)
+    assert r == pdg.PDG_ERR_ARG
+    assert np.all(np.isfinite(s.get_w()))
+    s.close()
