@@ -301,6 +301,64 @@ int pdg_batch_autotune(pdg_batch* batch, const double* dt, int reps);
 int pdg_batch_destroy(pdg_batch* batch);
 const char* pdg_batch_last_error(const pdg_batch* batch);
 
+/*
+ * Serving with continuous batching.  A server owns a FIFO of submitted solves and a
+ * set of resident ones.  pdg_server_iterate (1) admits waiting requests, first come
+ * first served, while the sum of the resident states stays within the memory budget
+ * (each admitted request gets its own context; its state comes from the CUDA
+ * stream-ordered pool, so admission and retirement do not synchronise the device),
+ * (2) advances every resident solve by min(remaining, chunk_steps) palindromic steps
+ * through one pdg_batch_step (all their launches overlap on the device), then (3)
+ * retires the finished ones: their moments w are copied to a host result and their
+ * device state is freed, which lets the next waiting requests in.  A solve's
+ * arithmetic does not depend on the other solves in flight, on when it was admitted
+ * or on the chunking (chunk boundaries only split fused transport passes).
+ * Times are seconds on the server clock (pdg_server_now, a monotonic clock).
+ *
+ * pdg_request:  mesh (dim, n_macro, n_sub, order; unit box, periodic), model,
+ *   dt and nsteps, w0 = initial macroscopic state in host memory (m * npoints doubles,
+ *   copied at submission), t_arrival = arrival time on the server clock.
+ * pdg_server_create -- budget in bytes of resident kinetic state, chunk of steps per
+ *   iteration (>= 1), use_graph as in pdg_batch_step, CUDA stream (NULL = default).
+ * pdg_server_submit -- validate and enqueue a request; *id receives its id (> 0).
+ *   Errors: PDG_ERR_ARG (bad request, w0 length, larger than the budget), PDG_ERR_OOM.
+ * pdg_server_iterate -- one admission / batched chunk / retirement round (synchronous).
+ * pdg_server_pending -- waiting and resident counts.
+ * pdg_server_poll -- up to max finished requests not yet polled: ids, arrival,
+ *   admission and completion times; *count receives how many were written.
+ * pdg_server_result -- copy the final w of a finished request (once; then released).
+ *   Errors: PDG_ERR_STATE (unknown, unfinished or already fetched id), PDG_ERR_ARG.
+ * pdg_server_stats -- iterations, DOF-updates done, requests completed, peak resident bytes.
+ * pdg_server_destroy -- free everything, including unfinished requests.
+ */
+typedef struct pdg_request {
+  int dim;
+  int n_macro[3];
+  int n_sub[3];
+  int order;
+  pdg_model_desc model;
+  double dt;
+  int nsteps;
+  int reserved;
+  const double* w0;
+  size_t w0_len;
+  double t_arrival;
+} pdg_request;
+typedef struct pdg_server pdg_server;
+int pdg_server_create(pdg_server** out, size_t mem_budget_bytes, int chunk_steps, int use_graph,
+                      void* cuda_stream);
+double pdg_server_now(const pdg_server* server);
+int pdg_server_submit(pdg_server* server, const pdg_request* req, long long* id);
+int pdg_server_iterate(pdg_server* server, int* n_resident, int* n_done);
+int pdg_server_pending(const pdg_server* server, int* n_waiting, int* n_resident);
+int pdg_server_poll(pdg_server* server, long long* ids, double* t_arrival, double* t_admit, double* t_done,
+                    int max, int* count);
+int pdg_server_result(pdg_server* server, long long id, double* w, size_t len);
+int pdg_server_stats(const pdg_server* server, long long* iterations, long long* dof_updates,
+                     long long* completed, size_t* peak_bytes);
+int pdg_server_destroy(pdg_server* server);
+const char* pdg_server_last_error(const pdg_server* server);
+
 /* pdg_destroy -- free the context and its device memory (NULL is a no-op). */
 int pdg_destroy(pdg_ctx* ctx);
 

@@ -43,6 +43,7 @@ struct pdg_ctx {
   bool has_state = false;
   double* wstage = nullptr;
   long long wstage_cap = 0;
+  bool async_alloc = false;   // state from the stream-ordered pool (cudaMallocAsync / cudaFreeAsync)
   int launch[2][3] = {{0, 0, 0}, {0, 0, 0}};   // single-mesh shape overrides per pass kind
   int bshape[2][3] = {{0, 0, 0}, {0, 0, 0}};   // shapes inside batched launches (<= 256 threads)
   bool timing = false;
@@ -331,13 +332,17 @@ int ensure_state(pdg_ctx* c) {
   const long long need = (long long)c->model.m * c->model.nv * c->npoints;
   if (need <= c->f_cap) return PDG_OK;
   double* nf = nullptr;
-  cudaError_t e = cudaMalloc((void**)&nf, sizeof(double) * (size_t)need);
+  cudaError_t e = c->async_alloc ? cudaMallocAsync((void**)&nf, sizeof(double) * (size_t)need, c->stream)
+                                 : cudaMalloc((void**)&nf, sizeof(double) * (size_t)need);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, e == cudaErrorMemoryAllocation ? PDG_ERR_OOM : PDG_ERR_CUDA,
                 std::string("cudaMalloc(f): ") + cudaGetErrorString(e));
   }
-  if (c->f) cudaFree(c->f);
+  if (c->f) {
+    if (c->async_alloc) cudaFreeAsync(c->f, c->stream);
+    else cudaFree(c->f);
+  }
   c->f = nf;
   c->f_cap = need;
   c->has_state = false;
@@ -359,6 +364,25 @@ bool pdg_internal_view(const pdg_ctx* c, PdgStateView* v) {
 }
 
 int pdg_internal_fail(pdg_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
+
+void pdg_internal_set_async_alloc(pdg_ctx* c, bool on) { c->async_alloc = on; }
+
+int pdg_internal_set_w_async(pdg_ctx* c, const double* w_host_pinned) {
+  if (!c || !c->has_model || !w_host_pinned) return PDG_ERR_ARG;
+  if (int r = ensure_state(c)) return r;
+  const size_t need = (size_t)c->model.m * c->npoints;
+  PDG_CUDA(c, cudaMemcpyAsync(c->f, w_host_pinned, sizeof(double) * need, cudaMemcpyHostToDevice, c->stream));
+  int e = pdg_launch_set_feq(c->f, c->npoints, c->model, (void*)c->stream);
+  if (e) return cuda_fail(c, (cudaError_t)e, "set_feq launch");
+  c->has_state = true;
+  return PDG_OK;
+}
+
+int pdg_internal_batch_set(pdg_batch* b, int n, pdg_ctx* const* ctxs) {
+  if (!b || n < 0 || (n > 0 && !ctxs)) return PDG_ERR_ARG;
+  b->inst.assign(ctxs, ctxs + n);
+  return PDG_OK;
+}
 
 extern "C" {
 
@@ -630,13 +654,16 @@ int pdg_set_launch(pdg_ctx* c, int kind, int lpb, int nseg, int ngroup) {
 
 int pdg_destroy(pdg_ctx* c) {
   if (!c) return PDG_OK;
-  if (c->stream || c->f) cudaStreamSynchronize(c->stream);
+  if (!c->async_alloc && (c->stream || c->f)) cudaStreamSynchronize(c->stream);
   for (auto& t : c->pending) {
     cudaEventDestroy(t.e0);
     cudaEventDestroy(t.e1);
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
-  if (c->f) cudaFree(c->f);
+  if (c->f) {
+    if (c->async_alloc) cudaFreeAsync(c->f, c->stream);
+    else cudaFree(c->f);
+  }
   if (c->wstage) cudaFree(c->wstage);
   delete c;
   return PDG_OK;
@@ -802,11 +829,8 @@ int pdg_batch_create(pdg_batch** out, int n, pdg_ctx* const* ctxs, void* cuda_st
   if (!b) return PDG_ERR_OOM;
   b->inst.assign(ctxs, ctxs + n);
   b->stream = (cudaStream_t)cuda_stream;
-  int maxcarry = 0;
-  for (int i = 0; i < n; ++i) {
-    const int ntf = 2 * ctxs[i]->model.m;
-    maxcarry = std::max(maxcarry, 2 * ntf * pdg_batch_threads());
-  }
+  // carry arrays sized for the largest population count (any instance list fits)
+  const int maxcarry = 2 * (2 * PDG_MAXM) * pdg_batch_threads();
   b->smem = pdg_batch_smem(maxcarry);
   int e = pdg_batch_grid(b->smem, &b->grid);
   // Graphs cannot be captured on the legacy default stream: capture and replay on a

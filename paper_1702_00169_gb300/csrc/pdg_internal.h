@@ -94,6 +94,14 @@ struct PdgStateView {
 bool pdg_internal_view(const pdg_ctx* c, PdgStateView* v);
 // Records msg as the context's last error and returns code.
 int pdg_internal_fail(pdg_ctx* c, int code, const std::string& msg);
+// Take the state of c from the stream-ordered pool (no device-wide synchronisation on free).
+void pdg_internal_set_async_alloc(pdg_ctx* c, bool on);
+// pdg_set_w without the final stream synchronisation (pageable sources are staged
+// by the copy call itself; pinned sources must stay valid until the stream passes).
+int pdg_internal_set_w_async(pdg_ctx* c, const double* w_host_pinned);
+// Replace the instance list of a batch (the contexts must have models).
+struct pdg_batch;
+int pdg_internal_batch_set(pdg_batch* b, int n, pdg_ctx* const* ctxs);
 
 // Capacity (doubles) of the static staging array of pdg_get_w_noalloc (8 MiB).
 #define PDG_NOALLOC_W_MAX (1LL << 20)

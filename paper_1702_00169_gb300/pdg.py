@@ -38,6 +38,13 @@ class pdg_info(ctypes.Structure):
                 ("h", ctypes.c_double * 3)]
 
 
+class pdg_request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n_macro", ctypes.c_int * 3), ("n_sub", ctypes.c_int * 3),
+                ("order", ctypes.c_int), ("model", pdg_model_desc), ("dt", ctypes.c_double),
+                ("nsteps", ctypes.c_int), ("reserved", ctypes.c_int), ("w0", ctypes.c_void_p),
+                ("w0_len", ctypes.c_size_t), ("t_arrival", ctypes.c_double)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libpdg.so not built at {LIB_PATH}; run __graft_entry__.build()")
 lib = ctypes.CDLL(LIB_PATH)
@@ -71,6 +78,16 @@ _SIGS = {
     "pdg_batch_autotune": (_I, [_P, _P, _I]),
     "pdg_batch_destroy": (_I, [_P]),
     "pdg_batch_last_error": (ctypes.c_char_p, [_P]),
+    "pdg_server_create": (_I, [ctypes.POINTER(_P), _SZ, _I, _I, _P]),
+    "pdg_server_now": (_D, [_P]),
+    "pdg_server_submit": (_I, [_P, ctypes.POINTER(pdg_request), _P]),
+    "pdg_server_iterate": (_I, [_P, _P, _P]),
+    "pdg_server_pending": (_I, [_P, _P, _P]),
+    "pdg_server_poll": (_I, [_P, _P, _P, _P, _P, _I, _P]),
+    "pdg_server_result": (_I, [_P, ctypes.c_longlong, _P, _SZ]),
+    "pdg_server_stats": (_I, [_P, _P, _P, _P, _P]),
+    "pdg_server_destroy": (_I, [_P]),
+    "pdg_server_last_error": (ctypes.c_char_p, [_P]),
     "pdg_destroy": (_I, [_P]),
     "pdg_last_error": (ctypes.c_char_p, [_P]),
     "pdg_status_string": (ctypes.c_char_p, [_I]),
@@ -272,3 +289,96 @@ def solver_for(cfg, scheme="M2", stream=None):
     s.set_model(cfg.kind, cfg.lam, a=cfg.a, gravity=cfg.gravity, gamma=cfg.gamma, omega=cfg.omega,
                 theta=cfg.theta, scheme=scheme)
     return s
+
+
+def model_desc(kind, lam, a=(0.0, 0.0, 0.0), gravity=9.81, gamma=1.4, omega=2.0, theta=0.5, scheme="M2",
+               precision=PDG_PREC_FP64):
+    d = pdg_model_desc()
+    d.kind = KIND[kind] if isinstance(kind, str) else int(kind)
+    d.scheme = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
+    d.precision = precision
+    d.lambda_ = lam
+    for i in range(3):
+        d.a[i] = float(a[i]) if i < len(a) else 0.0
+    d.gravity, d.gamma, d.omega, d.theta = gravity, gamma, omega, theta
+    return d
+
+
+class Server:
+    """Owns one pdg_server (continuous batching of independent solves)."""
+
+    def __init__(self, budget_bytes, chunk_steps=10, use_graph=False, stream=None):
+        self.s = _P()
+        r = pdg_server_create(ctypes.byref(self.s), int(budget_bytes), int(chunk_steps), 1 if use_graph else 0,
+                              _P(stream) if stream else None)
+        if r != PDG_OK:
+            raise PdgError(r, "pdg_server_create")
+
+    def _check(self, r, what):
+        if r != PDG_OK:
+            raise PdgError(r, f"{what}: {pdg_server_last_error(self.s).decode()}")
+
+    def now(self):
+        return pdg_server_now(self.s)
+
+    def submit(self, cfg, w0, nsteps, t_arrival=None, dt=None, scheme="M2"):
+        """Enqueue a solve of workloads.Config `cfg` from w0 (host array)."""
+        w0 = np.ascontiguousarray(np.asarray(w0, dtype=np.float64).reshape(-1))
+        q = pdg_request()
+        q.dim = cfg.dim
+        for a in range(3):
+            q.n_macro[a] = cfg.n_macro[a] if a < cfg.dim else 1
+            q.n_sub[a] = cfg.n_sub[a] if a < cfg.dim else 1
+        q.order = cfg.order
+        q.model = model_desc(cfg.kind, cfg.lam, a=cfg.a, gravity=cfg.gravity, gamma=cfg.gamma, omega=cfg.omega,
+                             theta=cfg.theta, scheme=scheme)
+        q.dt = cfg.dt if dt is None else dt
+        q.nsteps = int(nsteps)
+        q.w0 = w0.ctypes.data
+        q.w0_len = w0.size
+        q.t_arrival = self.now() if t_arrival is None else t_arrival
+        rid = ctypes.c_longlong()
+        self._check(pdg_server_submit(self.s, ctypes.byref(q), ctypes.addressof(rid)), "pdg_server_submit")
+        return rid.value
+
+    def iterate(self):
+        nr, nd = ctypes.c_int(), ctypes.c_int()
+        self._check(pdg_server_iterate(self.s, ctypes.addressof(nr), ctypes.addressof(nd)), "pdg_server_iterate")
+        return nr.value, nd.value
+
+    def pending(self):
+        nw, nr = ctypes.c_int(), ctypes.c_int()
+        self._check(pdg_server_pending(self.s, ctypes.addressof(nw), ctypes.addressof(nr)), "pdg_server_pending")
+        return nw.value, nr.value
+
+    def poll(self, max_n=4096):
+        ids = np.zeros(max_n, dtype=np.int64)
+        ta, tb, tc = (np.zeros(max_n) for _ in range(3))
+        cnt = ctypes.c_int()
+        self._check(pdg_server_poll(self.s, ids.ctypes.data, ta.ctypes.data, tb.ctypes.data, tc.ctypes.data, max_n,
+                                    ctypes.addressof(cnt)), "pdg_server_poll")
+        n = cnt.value
+        return [(int(ids[i]), ta[i], tb[i], tc[i]) for i in range(n)]
+
+    def result(self, rid, w_len):
+        out = np.empty(w_len)
+        self._check(pdg_server_result(self.s, rid, out.ctypes.data, w_len), "pdg_server_result")
+        return out
+
+    def stats(self):
+        it, du, co = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        pk = ctypes.c_size_t()
+        self._check(pdg_server_stats(self.s, ctypes.addressof(it), ctypes.addressof(du), ctypes.addressof(co),
+                                     ctypes.addressof(pk)), "pdg_server_stats")
+        return {"iterations": it.value, "dof_updates": du.value, "completed": co.value, "peak_bytes": pk.value}
+
+    def close(self):
+        if self.s:
+            pdg_server_destroy(self.s)
+            self.s = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

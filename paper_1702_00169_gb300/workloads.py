@@ -194,3 +194,27 @@ def batched_instances(n=256, seed=4, m_range=(8, 96), n_sub=4, orders=(1, 2, 3, 
         import dataclasses
         out[-1] = dataclasses.replace(out[-1], order=d, seed=1000 * seed + i, steps=20)
     return out
+
+
+def serving_requests(n=1000, seed=5, rate=200.0, m_range=(16, 128), n_sub=4, orders=(1, 2, 3, 4),
+                     steps_range=(10, 1000)):
+    """Seeded Poisson request stream of the serving workload: arrival times (s) with mean
+    rate `rate`, each request a 2-D advection or shallow-water solve (50/50) on M x M
+    macrocells (M ~ U{m_range}) x n_sub^2 subcells, degree ~ U{orders}, steps
+    log-uniform in steps_range, dt at CFL 1.  Returns [(t_arrival, Config, nsteps)]."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        kind = "advection" if rng.random() < 0.5 else "shallow_water"
+        M = int(rng.integers(m_range[0], m_range[1] + 1))
+        d = int(rng.choice(orders))
+        lo, hi = np.log(steps_range[0]), np.log(steps_range[1])
+        ns = int(round(float(np.exp(rng.uniform(lo, hi)))))
+        base = ADVECTION_D2Q4 if kind == "advection" else SW_D2Q4
+        cfg = dataclasses.replace(base.scaled(n_macro=(M, M), n_sub=(n_sub, n_sub), name=f"req{i}_{kind}_M{M}_d{d}"),
+                                  order=d, seed=100000 * seed + i, steps=ns)
+        out.append((t, cfg, ns))
+    return out
