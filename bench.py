@@ -71,6 +71,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=20)
+    ap.add_argument("--no-mixed", action="store_true", help="skip the double-float measurement")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df32"],
+                    help="precision of the headline run (profiling of the double-float kernels)")
     return ap.parse_args()
 
 
@@ -394,45 +397,49 @@ def main():
     from paper_1702_00169_gb300 import pdg
 
     stream = torch.cuda.Stream()
-    s = pdg.solver_for(cfg, scheme=args.scheme, stream=stream.cuda_stream)
+    s = pdg.solver_for(cfg, scheme=args.scheme, stream=stream.cuda_stream, precision=args.precision)
     info = s.info()
     coords = [s.points(a) for a in range(cfg.dim)]
     w0 = np.ascontiguousarray(W.initial_w(cfg, coords).reshape(-1))
     w0_dev = torch.from_numpy(w0).cuda()
     torch.cuda.synchronize()
-
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
-
-    # ---- device-resident run ----
-    s.set_w(w0_dev)
-    s.step(cfg.dt, args.warmup)
-    s.synchronize()
     dev_uuid = None
     try:
         dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
         pass
-    sampler = ClockSampler(dev_uuid)
-    barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.4)
-    s.timing_enable(True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    s.step(cfg.dt, args.steps)
-    ev1.record(stream)
-    s.synchronize()
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    launches, kms = s.timing_read()
-    s.timing_enable(False)
-    w_end = s.get_w()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def timed_run(sv):
+        """W untimed steps, then K steps between CUDA events on the context stream, with
+        per-kernel event timing and clock sampling inside the timed region."""
+        sv.set_w(w0_dev)
+        sv.step(cfg.dt, args.warmup)
+        sv.synchronize()
+        sampler = ClockSampler(dev_uuid)
+        barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        time.sleep(0.4)
+        sv.timing_enable(True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sv.step(cfg.dt, args.steps)
+        ev1.record(stream)
+        sv.synchronize()
+        torch.cuda.synchronize()
+        clk = sampler.stop()
+        barrier()
+        launches, kms = sv.timing_read()
+        sv.timing_enable(False)
+        return ev0.elapsed_time(ev1), launches, kms, clk, sv.get_w()
+
+    # ---- device-resident run (FP64) ----
+    ms, launches, kms, clocks, w_end = timed_run(s)
     finite = bool(np.all(np.isfinite(w_end)))
 
     ms_max = ms
@@ -442,6 +449,23 @@ def main():
         ms_max = float(t.item())
     dofs = cfg.dofs
     value = dofs * args.steps * ws / (ms_max * 1e-3)
+
+    # ---- the same run in double-float precision (FP32-pair state and arithmetic) ----
+    mixed = None
+    if not args.no_mixed and args.precision == "fp64":
+        sd = pdg.solver_for(cfg, scheme=args.scheme, stream=stream.cuda_stream, precision="df32")
+        ms_d, launches_d, kms_d, clocks_d, w_end_d = timed_run(sd)
+        sd.close()
+        k_d = int(np.argmax(kms_d[:2]))
+        avg_d = kms_d[k_d] / max(1, launches_d[k_d])
+        bytes_d = 16.0 * info.nfields * info.npoints if k_d == 1 else 8.0 * info.nfields * info.npoints
+        mixed = {"precision": "df32 (FP32-pair state and double-word arithmetic on the FP32 pipes)",
+                 "value": dofs * args.steps * ws / (ms_d * 1e-3), "ms_per_step": ms_d / args.steps,
+                 "speedup_vs_fp64": ms / ms_d,
+                 "rel_l2_w_vs_fp64_after_steps": float(np.linalg.norm(w_end_d - w_end) / np.linalg.norm(w_end)),
+                 "dominant_kernel_avg_ms": avg_d,
+                 "hbm_achieved_gbs": bytes_d / (avg_d * 1e-3) / 1e9, "clocks": clocks_d,
+                 "gpu_launches": int(sum(launches_d))}
 
     # ---- end-to-end through the C ABI with host buffers ----
     e2e = None
@@ -521,7 +545,7 @@ def main():
                        "l2": "state 403 MB > 126 MB L2: inputs larger than L2, no flush",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "gpu_launches": int(sum(launches)), "roofline": roof, "clocks": clocks,
-            "e2e": e2e, "cpu_baseline": cpu, "state_finite": finite}
+            "e2e": e2e, "cpu_baseline": cpu, "mixed": mixed, "state_finite": finite}
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

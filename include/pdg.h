@@ -66,9 +66,19 @@ enum {
   PDG_SCHEME_M2_COLLAPSED = 1 /* consecutive half transports merged into T(dt)    */
 };
 
-/* Arithmetic of the transport sweep. */
+/* State format and arithmetic. */
 enum {
-  PDG_PREC_FP64 = 0 /* FP64 storage and FP64 arithmetic on every step */
+  PDG_PREC_FP64 = 0, /* FP64 storage and FP64 arithmetic on every step */
+  PDG_PREC_DF32 = 1  /* double-float: the state is stored as a pair of FP32 values
+                        (hi + lo, about 48 significant bits, same 8 bytes per value) and
+                        every step -- transport, moments, equilibrium, relaxation -- uses
+                        double-word arithmetic built from error-free FP32 transformations
+                        (GB300 runs FP32 at 61x its FP64 rate).  The ABI still exchanges
+                        FP64 buffers: states are converted on pdg_set_w / pdg_set_f /
+                        pdg_get_w / pdg_get_f (pair -> FP64 is exact).  Not a paper
+                        feature: an accuracy/speed trade-off of this implementation
+                        (relative L2 vs the FP64 reference <= 1e-12 on the tested
+                        workloads). */
 };
 
 /*
@@ -222,7 +232,7 @@ int pdg_get_line_coefs(const pdg_ctx* ctx, int axis, double delta, double* E, do
  * calls share the one array: calls whose GPU work overlaps (other contexts on other
  * streams, or other host threads) race on it and must be serialised by the caller.
  * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (NULL, len mismatch, or len greater
- * than 1,048,576: use pdg_get_w), PDG_ERR_CUDA.
+ * than 1,048,576: use pdg_get_w), PDG_ERR_UNSUPPORTED (a PDG_PREC_DF32 state), PDG_ERR_CUDA.
  */
 int pdg_get_w_noalloc(pdg_ctx* ctx, double* out, size_t len);
 

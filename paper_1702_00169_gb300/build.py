@@ -18,7 +18,8 @@ LIBDIR = os.path.join(PKG, "lib")
 OBJDIR = os.path.join(ROOT, "_build", "obj")
 LIB = os.path.join(LIBDIR, "libpdg.so")
 
-SOURCES = ["pdg_api.cu", "pdg_kernels.cu", "pdg_batch.cu", "pdg_noalloc.cu", "pdg_server.cu", "pdg_plan.cpp"]
+SOURCES = ["pdg_batch_df.cu", "pdg_batch.cu", "pdg_kernels_df.cu", "pdg_kernels.cu", "pdg_api.cu",
+           "pdg_noalloc.cu", "pdg_server.cu", "pdg_plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I", os.path.join(ROOT, "include")]

@@ -58,7 +58,8 @@ struct pdg_batch {
   std::vector<pdg_ctx*> inst;
   cudaStream_t stream = nullptr;       // the caller's stream (may be the legacy default stream)
   cudaStream_t cap = nullptr;          // private blocking stream used for graph capture and replay
-  int grid = 0;
+  int grid = 0;                        // persistent grid, FP64 kernel
+  int grid_df = 0;                     // persistent grid, double-float kernel
   size_t smem = 0;
   // device tables of the last pdg_batch_step (kept alive for the captured graph)
   PdgPass* d_desc = nullptr;
@@ -66,8 +67,9 @@ struct pdg_batch {
   long long* d_ent_start = nullptr;
   unsigned long long* d_counter = nullptr;
   size_t cap_desc = 0, cap_ent = 0, cap_cnt = 0;
-  std::vector<int> st_off, st_nent;          // per stage: first entry, entries
-  std::vector<long long> st_total;           // per stage: work items
+  // per launch (one per stage and precision present): first entry, entries, work items, precision
+  std::vector<int> st_off, st_nent, st_prec;
+  std::vector<long long> st_total;
   std::vector<char> sig;                      // signature of the tables (graph cache key)
   cudaGraphExec_t gexec = nullptr;
   std::vector<char> gsig;
@@ -174,6 +176,7 @@ int finish_coef(PdgCoef* C, int N, int S) {
   const double rN = std::pow(r, (double)N);
   if (!(std::fabs(1.0 - rN) > 1e-12)) return -1;
   C->inv_ring = 1.0 / (1.0 - rN);
+  pdg_coef_split(C);
   return 0;
 }
 
@@ -239,6 +242,7 @@ int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov,
   }
   const int kind = pass_kind(sp);
   p.mv = kind ? pdg_model_variant(c->model) : 5 /* no collision */;
+  p.prec = c->model.prec;
   int Wmax = 1;
   for (int i = 0; i < sp.ncs; ++i) {
     int W = stable_window(sp.cs[i]);
@@ -359,6 +363,7 @@ bool pdg_internal_view(const pdg_ctx* c, PdgStateView* v) {
   v->npoints = c->npoints;
   v->m = c->model.m;
   v->nv = c->model.nv;
+  v->prec = c->model.prec;
   v->stream = c->stream;
   return true;
 }
@@ -446,7 +451,8 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
     return fail(c, PDG_ERR_ARG, "unknown model kind");
   if (d->scheme != PDG_SCHEME_M2 && d->scheme != PDG_SCHEME_M2_COLLAPSED)
     return fail(c, PDG_ERR_ARG, "unknown scheme");
-  if (d->precision != PDG_PREC_FP64) return fail(c, PDG_ERR_UNSUPPORTED, "precision not available");
+  if (d->precision != PDG_PREC_FP64 && d->precision != PDG_PREC_DF32)
+    return fail(c, PDG_ERR_UNSUPPORTED, "precision not available");
   if (!(d->lambda > 0.0 && std::isfinite(d->lambda))) return fail(c, PDG_ERR_ARG, "lambda must be > 0");
   if (!std::isfinite(d->omega) || d->omega == 0.0) return fail(c, PDG_ERR_ARG, "omega must be finite and != 0");
   if (!(d->theta >= 0.0 && d->theta <= 1.0)) return fail(c, PDG_ERR_ARG, "theta must be in [0, 1]");
@@ -466,7 +472,10 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
     const double s = (i % 2 == 0) ? 1.0 : -1.0;
     M.cadv[i] = 1.0 / (2.0 * c->dim) + s * d->a[i / 2] / (2.0 * d->lambda);
   }
-  if (c->has_model && c->model.m != M.m) c->has_state = false;
+  M.prec = d->precision;
+  pdg_model_constants(&M);
+  // a different number of fields or a different state format invalidates the state
+  if (c->has_model && (c->model.m != M.m || c->model.prec != M.prec)) c->has_state = false;
   c->model = M;
   c->scheme = d->scheme;
   c->precision = d->precision;
@@ -501,6 +510,10 @@ int pdg_set_f(pdg_ctx* c, const double* f, size_t len, int on_device) {
   if (int r = ensure_state(c)) return r;
   PDG_CUDA(c, cudaMemcpyAsync(c->f, f, sizeof(double) * need,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  if (c->model.prec == PDG_PREC_DF32) {
+    int e = pdg_launch_convert(c->f, (long long)need, 1, (void*)c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e, "convert launch");
+  }
   if (!on_device) PDG_CUDA(c, cudaStreamSynchronize(c->stream));
   c->has_state = true;
   return PDG_OK;
@@ -512,8 +525,19 @@ int pdg_get_f(pdg_ctx* c, double* out, size_t len, int on_device) {
   if (!out) return fail(c, PDG_ERR_ARG, "out is NULL");
   const size_t need = fields_of(c) * c->npoints;
   if (len != need) return fail(c, PDG_ERR_ARG, "f length mismatch");
+  const bool df = c->model.prec == PDG_PREC_DF32;
+  // double-float state: convert to FP64 in place, copy, convert back (the round trip
+  // pair -> double -> pair is exact)
+  if (df) {
+    int e = pdg_launch_convert(c->f, (long long)need, 0, (void*)c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e, "convert launch");
+  }
   PDG_CUDA(c, cudaMemcpyAsync(out, c->f, sizeof(double) * need,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  if (df) {
+    int e = pdg_launch_convert(c->f, (long long)need, 1, (void*)c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e, "convert launch");
+  }
   if (!on_device) PDG_CUDA(c, cudaStreamSynchronize(c->stream));
   return PDG_OK;
 }
@@ -832,7 +856,8 @@ int pdg_batch_create(pdg_batch** out, int n, pdg_ctx* const* ctxs, void* cuda_st
   // carry arrays sized for the largest population count (any instance list fits)
   const int maxcarry = 2 * (2 * PDG_MAXM) * pdg_batch_threads();
   b->smem = pdg_batch_smem(maxcarry);
-  int e = pdg_batch_grid(b->smem, &b->grid);
+  int e = pdg_batch_grid(b->smem, PDG_PREC_FP64, &b->grid);
+  if (!e) e = pdg_batch_grid(b->smem, PDG_PREC_DF32, &b->grid_df);
   // Graphs cannot be captured on the legacy default stream: capture and replay on a
   // private blocking stream joined to the caller's stream with events.
   if (e || cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess ||
@@ -925,25 +950,32 @@ int batch_prepare(pdg_batch* b, const double* dt, const int* nsteps) {
   for (int i = 0; i < n; ++i) nst = std::max(nst, plist[i].size());
   std::vector<int> ent_desc;
   std::vector<long long> ent_start;
-  b->st_off.assign(nst, 0);
-  b->st_nent.assign(nst, 0);
-  b->st_total.assign(nst, 0);
+  b->st_off.clear();
+  b->st_nent.clear();
+  b->st_total.clear();
+  b->st_prec.clear();
   for (size_t t = 0; t < nst; ++t) {
-    std::vector<std::pair<double, int>> order;  // (cost per item, instance)
-    for (int i = 0; i < n; ++i)
-      if (t < plist[i].size()) order.push_back({item_cost(descs[plist[i][t]]), i});
-    std::stable_sort(order.begin(), order.end(),
-                     [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
-    b->st_off[t] = (int)ent_desc.size();
-    long long acc = 0;
-    for (auto& o : order) {
-      ent_desc.push_back(plist[o.second][t]);
-      ent_start.push_back(acc);
-      acc += pblocks[o.second][t];
+    for (int prec = 0; prec < 2; ++prec) {
+      std::vector<std::pair<double, int>> order;  // (cost per item, instance)
+      for (int i = 0; i < n; ++i)
+        if (t < plist[i].size() && descs[plist[i][t]].prec == prec)
+          order.push_back({item_cost(descs[plist[i][t]]), i});
+      if (order.empty()) continue;
+      std::stable_sort(order.begin(), order.end(), [](const std::pair<double, int>& x,
+                                                      const std::pair<double, int>& y) { return x.first > y.first; });
+      b->st_off.push_back((int)ent_desc.size());
+      long long acc = 0;
+      for (auto& o : order) {
+        ent_desc.push_back(plist[o.second][t]);
+        ent_start.push_back(acc);
+        acc += pblocks[o.second][t];
+      }
+      b->st_nent.push_back((int)order.size());
+      b->st_total.push_back(acc);
+      b->st_prec.push_back(prec);
     }
-    b->st_nent[t] = (int)order.size();
-    b->st_total[t] = acc;
   }
+  nst = b->st_off.size();
   if (int r = ensure_dev(b, &b->d_desc, &b->cap_desc, std::max<size_t>(1, descs.size()))) return r;
   if (int r = ensure_dev(b, &b->d_ent_desc, &b->cap_ent, std::max<size_t>(1, ent_desc.size()))) return r;
   size_t cap2 = b->cap_ent;
@@ -987,8 +1019,10 @@ int batch_issue(pdg_batch* b, cudaStream_t st) {
   if (e != cudaSuccess) return bfail(b, PDG_ERR_CUDA, std::string("batch counters: ") + cudaGetErrorString(e));
   long long launches = 0;
   for (size_t t = 0; t < nst; ++t) {
+    const int prec = b->st_prec[t];
     int r = pdg_launch_batch(b->d_desc, b->d_ent_desc + b->st_off[t], b->d_ent_start + b->st_off[t],
-                             b->st_nent[t], b->st_total[t], b->d_counter + t, b->grid, b->smem, (void*)st);
+                             b->st_nent[t], b->st_total[t], b->d_counter + t,
+                             prec == PDG_PREC_DF32 ? b->grid_df : b->grid, b->smem, prec, (void*)st);
     if (r) return bfail(b, PDG_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString((cudaError_t)r));
     launches += b->st_total[t] > 0;
   }
@@ -1154,7 +1188,9 @@ int pdg_batch_autotune(pdg_batch* b, const double* dt, int reps) {
         float ms = 0.f;
         status = time_launches(c, reps, [&]() {
           cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), c->stream);
-          int er = pdg_launch_batch(d_p, d_ent, d_start, 1, total, d_cnt, b->grid, b->smem, (void*)c->stream);
+          const int prec = c->model.prec;
+          int er = pdg_launch_batch(d_p, d_ent, d_start, 1, total, d_cnt,
+                                    prec == PDG_PREC_DF32 ? b->grid_df : b->grid, b->smem, prec, (void*)c->stream);
           return er ? cuda_fail(c, (cudaError_t)er, "batch autotune launch") : PDG_OK;
         }, &ms);
         if (status) break;

@@ -1,6 +1,13 @@
-// Device code shared by the single-instance kernels (pdg_kernels.cu) and the
-// batched persistent kernel (pdg_batch.cu): collision of eq. (3.12), the two-phase
+// Device code shared by the single-instance kernels (pdg_kernels*.cu) and the
+// batched persistent kernels (pdg_batch*.cu): collision of eq. (3.12), the two-phase
 // exact periodic transport sweep of eq. (3.11), and the pass body.
+//
+// Everything is templated on the number type T of the state and of the arithmetic:
+//   T = double : FP64 storage and FP64 arithmetic;
+//   T = dd     : double-float numbers (an unevaluated sum hi + lo of two FP32 values,
+//                about 48 significant bits) stored as a float pair in the same 8 bytes,
+//                with arithmetic built from error-free transformations on the FP32
+//                pipes (GB300 executes FP32 FMAs at 61x its FP64 rate).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -12,98 +19,238 @@ namespace pdgdev {
 enum { MV_ADV = 0, MV_SW = 1, MV_EU1 = 2, MV_EU2 = 3, MV_EU3 = 4, MV_NONE = 5 };
 
 // ---------------------------------------------------------------------------
+// Double-float arithmetic.  Error-free transformations (all with explicit
+// round-to-nearest intrinsics so that no FMA contraction can alter them):
+//   two_sum  (Knuth):  a + b = s + e exactly;
+//   fast_two_sum (Dekker, |a| >= |b|): a + b = s + e exactly;
+//   two_prod (with FMA): a * b = p + e exactly.
+// Double-word operations follow Joldes, Muller & Popescu, "Tight and rigorous error
+// bounds for basic building blocks of double-word arithmetic", ACM TOMS 44 (2017):
+//   add = AccurateDWPlusDW (relative error <= 3u^2 + 13u^3),
+//   mul = DWTimesDW with FMA (relative error <= 5u^2), u = 2^-24.
+struct __align__(8) dd {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dd dd_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dd dd_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dd dd_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ dd operator+(dd x, dd y) {
+  const dd s = dd_two_sum(x.hi, y.hi);
+  const dd t = dd_two_sum(x.lo, y.lo);
+  const dd v = dd_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return dd_fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+__device__ __forceinline__ dd operator-(dd x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dd operator-(dd x, dd y) { return x + (-y); }
+__device__ __forceinline__ dd operator*(dd x, dd y) {
+  const dd c = dd_two_prod(x.hi, y.hi);
+  const float tl = __fmul_rn(x.lo, y.lo);
+  const float cl = __fmaf_rn(x.lo, y.hi, __fmaf_rn(x.hi, y.lo, tl));
+  return dd_fast_two_sum(c.hi, __fadd_rn(c.lo, cl));
+}
+__device__ __forceinline__ dd fma(dd a, dd b, dd c) { return a * b + c; }
+// keep the FP64 fma visible next to the double-float overload
+__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+// 1/x: FP32 reciprocal seed refined by one Newton step in double-word arithmetic.
+__device__ __forceinline__ dd recip(dd x) {
+  const float r0 = __frcp_rn(x.hi);
+  const dd one = {1.0f, 0.0f};
+  const dd e = one - x * dd{r0, 0.0f};          // ~2^-23
+  return dd{r0, 0.0f} + dd{r0, 0.0f} * e;
+}
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+template <class T> __device__ __forceinline__ T zero();
+template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ dd zero<dd>() { return {0.0f, 0.0f}; }
+
+// loads / stores of the state (the same 8-byte slots in both modes)
+template <class T> __device__ __forceinline__ T ld(const double* p);
+template <> __device__ __forceinline__ double ld<double>(const double* p) { return *p; }
+template <> __device__ __forceinline__ dd ld<dd>(const double* p) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st(double* p, dd v) { *reinterpret_cast<float2*>(p) = make_float2(v.hi, v.lo); }
+
+// FP64 <-> double-float conversion (only at the API boundary)
+__device__ __forceinline__ dd dd_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double dd_to_double(dd x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(dd x) { return dd_to_double(x); }
+template <class T> __device__ __forceinline__ T from_double(double x);
+template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ dd from_double<dd>(double x) { return dd_from_double(x); }
+
+// coefficient accessors: value i of a (double array, float-pair array) couple
+template <class T> __device__ __forceinline__ T cval(const double* d, const float (*f)[2], int i);
+template <> __device__ __forceinline__ double cval<double>(const double* d, const float (*)[2], int i) {
+  return d[i];
+}
+template <> __device__ __forceinline__ dd cval<dd>(const double*, const float (*f)[2], int i) {
+  return {f[i][0], f[i][1]};
+}
+#define PDG_C(T, C, name, i) cval<T>((C).name, (C).name##_f, (i))
+#define PDG_S(T, C, name) cval<T>(&(C).name, (C).name##_f, 0)
+#define PDG_K(T, M, i) cval<T>((M).k, (M).k_f, (i))
+
+// Dot product acc + sum_j a_j b_j.  FP64: an FMA chain.  Double-float: compensated
+// accumulation in the spirit of Ogita, Rump & Oishi ("Accurate sum and dot product",
+// SIAM J. Sci. Comput. 2005): exact products of the high parts (two_prod), the
+// high sum kept exactly with two_sum, every rounding error and the cross terms
+// a.hi b.lo + a.lo b.hi collected in one FP32 accumulator, then renormalised.
+template <int K>
+__device__ __forceinline__ double dot_acc(const double* a, const double* b, double acc) {
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc = fma(a[j], b[j], acc);
+  return acc;
+}
+template <int K>
+__device__ __forceinline__ dd dot_acc(const dd* a, const dd* b, dd acc) {
+  float S = acc.hi, L = acc.lo;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const dd p = dd_two_prod(a[j].hi, b[j].hi);
+    const float cross = __fmaf_rn(a[j].hi, b[j].lo, __fmul_rn(a[j].lo, b[j].hi));
+    const dd s = dd_two_sum(S, p.hi);
+    S = s.hi;
+    L = __fadd_rn(L, __fadd_rn(s.lo, __fadd_rn(p.lo, cross)));
+  }
+  return dd_fast_two_sum(S, L);
+}
+
+// ---------------------------------------------------------------------------
 // Collision at one point (eq. (3.12)); v holds the m * 2D populations.
 // f^eq_{k,i} = w_k/(2D) + (v_i . q_k(w))/(2 lambda^2) = w_k/(2D) + s_i q^a_k / (2 lambda)
-// for v_i = s_i lambda e_a.
-template <int MV>
-__device__ __forceinline__ void collide(double* v, const PdgModel& M);
+// for v_i = s_i lambda e_a.  Model constants (index PDG_K_*) come precomputed from
+// the host in FP64 and as float pairs.
+template <int MV, class T>
+__device__ __forceinline__ void collide(T* v, const PdgModel& M);
 
-template <>
-__device__ __forceinline__ void collide<MV_ADV>(double* v, const PdgModel& M) {
-  const int nv = M.nv;
-  double w = 0.0;
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-    if (i < nv) w += v[i];
-  const double om = M.omega, om1 = 1.0 - M.omega;
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-    if (i < nv) v[i] = fma(om * M.cadv[i], w, om1 * v[i]);
-}
+template <int MV, class T>
+struct Collide;
 
-template <>
-__device__ __forceinline__ void collide<MV_SW>(double* v, const PdgModel& M) {
-  // w = (h, hu, hv), populations k*4 + {+x, -x, +y, -y}
-  double w[3];
+template <class T>
+struct Collide<MV_ADV, T> {
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) {
+    const int nv = M.nv;
+    T w = zero<T>();
 #pragma unroll
-  for (int k = 0; k < 3; ++k) w[k] = (v[4 * k] + v[4 * k + 1]) + (v[4 * k + 2] + v[4 * k + 3]);
-  const double h = w[0], hu = w[1], hv = w[2];
-  const double ih = 1.0 / h;
-  const double u = hu * ih, vv = hv * ih;
-  const double p = 0.5 * M.gravity * h * h;
-  const double qx[3] = {hu, fma(hu, u, p), hv * u};
-  const double qy[3] = {hv, hu * vv, fma(hv, vv, p)};
-  const double om = M.omega, om1 = 1.0 - M.omega;
-  const double c0 = 0.25 * om;                 // omega / (2D)
-  const double c1 = om / (2.0 * M.lambda);     // omega / (2 lambda)
+    for (int i = 0; i < 6; ++i)
+      if (i < nv) w = w + v[i];
+    const T om1 = PDG_K(T, M, PDG_K_OM1);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double b = c0 * w[k];
-    v[4 * k + 0] = fma(om1, v[4 * k + 0], fma(c1, qx[k], b));
-    v[4 * k + 1] = fma(om1, v[4 * k + 1], fma(-c1, qx[k], b));
-    v[4 * k + 2] = fma(om1, v[4 * k + 2], fma(c1, qy[k], b));
-    v[4 * k + 3] = fma(om1, v[4 * k + 3], fma(-c1, qy[k], b));
+    for (int i = 0; i < 6; ++i)
+      if (i < nv) v[i] = fma(PDG_K(T, M, PDG_K_CADV + i), w, om1 * v[i]);
   }
-}
+};
 
-template <int D>
-__device__ __forceinline__ void collide_euler(double* v, const PdgModel& M) {
+template <class T>
+struct Collide<MV_SW, T> {
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) {
+    // w = (h, hu, hv), populations k*4 + {+x, -x, +y, -y}
+    T w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w[k] = (v[4 * k] + v[4 * k + 1]) + (v[4 * k + 2] + v[4 * k + 3]);
+    const T h = w[0], hu = w[1], hv = w[2];
+    const T ih = recip(h);
+    const T u = hu * ih, vv = hv * ih;
+    const T p = (PDG_K(T, M, PDG_K_HALFG) * h) * h;
+    const T qx[3] = {hu, fma(hu, u, p), hv * u};
+    const T qy[3] = {hv, hu * vv, fma(hv, vv, p)};
+    const T om1 = PDG_K(T, M, PDG_K_OM1);
+    const T c0 = PDG_K(T, M, PDG_K_C0);   // omega / (2D)
+    const T c1 = PDG_K(T, M, PDG_K_C1);   // omega / (2 lambda)
+    const T mc1 = -c1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const T b = c0 * w[k];
+      v[4 * k + 0] = fma(om1, v[4 * k + 0], fma(c1, qx[k], b));
+      v[4 * k + 1] = fma(om1, v[4 * k + 1], fma(mc1, qx[k], b));
+      v[4 * k + 2] = fma(om1, v[4 * k + 2], fma(c1, qy[k], b));
+      v[4 * k + 3] = fma(om1, v[4 * k + 3], fma(mc1, qy[k], b));
+    }
+  }
+};
+
+template <int D, class T>
+__device__ __forceinline__ void collide_euler(T* v, const PdgModel& M) {
   constexpr int m = D + 2, nv = 2 * D;
-  double w[m];
+  T w[m];
 #pragma unroll
   for (int k = 0; k < m; ++k) {
-    double s = 0.0;
+    T s = zero<T>();
 #pragma unroll
-    for (int i = 0; i < nv; ++i) s += v[k * nv + i];
+    for (int i = 0; i < nv; ++i) s = s + v[k * nv + i];
     w[k] = s;
   }
-  const double rho = w[0], E = w[D + 1];
-  const double ir = 1.0 / rho;
-  double u[D];
-  double ke = 0.0;
+  const T rho = w[0], E = w[D + 1];
+  const T ir = recip(rho);
+  T u[D];
+  T ke = zero<T>();
 #pragma unroll
   for (int b = 0; b < D; ++b) {
     u[b] = w[1 + b] * ir;
     ke = fma(w[1 + b], u[b], ke);
   }
-  const double p = (M.gamma - 1.0) * (E - 0.5 * ke);
-  const double om = M.omega, om1 = 1.0 - M.omega;
-  const double c0 = om / (2.0 * D);
-  const double c1 = om / (2.0 * M.lambda);
+  const T p = PDG_K(T, M, PDG_K_GM1) * (E - PDG_K(T, M, PDG_K_HALF) * ke);
+  const T om1 = PDG_K(T, M, PDG_K_OM1);
+  const T c0 = PDG_K(T, M, PDG_K_C0);
+  const T c1 = PDG_K(T, M, PDG_K_C1);
+  const T mc1 = -c1;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    double q[m];
+    T q[m];
     q[0] = w[1 + a];
 #pragma unroll
     for (int b = 0; b < D; ++b) q[1 + b] = (a == b) ? fma(w[1 + b], u[a], p) : w[1 + b] * u[a];
     q[D + 1] = (E + p) * u[a];
 #pragma unroll
     for (int k = 0; k < m; ++k) {
-      const double bse = c0 * w[k];
+      const T bse = c0 * w[k];
       v[k * nv + 2 * a] = fma(om1, v[k * nv + 2 * a], fma(c1, q[k], bse));
-      v[k * nv + 2 * a + 1] = fma(om1, v[k * nv + 2 * a + 1], fma(-c1, q[k], bse));
+      v[k * nv + 2 * a + 1] = fma(om1, v[k * nv + 2 * a + 1], fma(mc1, q[k], bse));
     }
   }
 }
 
-template <>
-__device__ __forceinline__ void collide<MV_EU1>(double* v, const PdgModel& M) { collide_euler<1>(v, M); }
-template <>
-__device__ __forceinline__ void collide<MV_EU2>(double* v, const PdgModel& M) { collide_euler<2>(v, M); }
-template <>
-__device__ __forceinline__ void collide<MV_EU3>(double* v, const PdgModel& M) { collide_euler<3>(v, M); }
-template <>
-__device__ __forceinline__ void collide<MV_NONE>(double*, const PdgModel&) {}
+template <class T>
+struct Collide<MV_EU1, T> {
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) { collide_euler<1, T>(v, M); }
+};
+template <class T>
+struct Collide<MV_EU2, T> {
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) { collide_euler<2, T>(v, M); }
+};
+template <class T>
+struct Collide<MV_EU3, T> {
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) { collide_euler<3, T>(v, M); }
+};
+template <class T>
+struct Collide<MV_NONE, T> {
+  static __device__ __forceinline__ void run(T*, const PdgModel&) {}
+};
+
+template <int MV, class T>
+__device__ __forceinline__ void collide(T* v, const PdgModel& M) {
+  Collide<MV, T>::run(v, M);
+}
 
 template <int MV>
 struct NFields { static constexpr int value = PDG_MAXF; };
@@ -118,30 +265,37 @@ template <> struct NFields<MV_NONE> { static constexpr int value = 1; };
 // Transport phases for one population along one line.  lp points at traversal
 // index 0 of the line, dstep is the signed stride between traversal indices.
 
-template <int NP>
-__device__ __forceinline__ void load_cell(const double* lp, long long dstep, int c, double* v) {
+template <int NP, class T>
+__device__ __forceinline__ void load_cell(const double* lp, long long dstep, int c, T* v) {
   const double* p0 = lp + (long long)c * NP * dstep;
 #pragma unroll
-  for (int j = 0; j < NP; ++j) v[j] = p0[j * dstep];
+  for (int j = 0; j < NP; ++j) v[j] = ld<T>(p0 + j * dstep);
+}
+
+template <int NP, class T>
+__device__ __forceinline__ void load_row(const PdgCoef& C, int r, T* row) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) row[j] = PDG_C(T, C, E, r * NP + j);
 }
 
 // Phase 1: aggregate Y of the recurrence over cells [wstart, c1) starting from 0,
 // and the old last-node value of cell c1 - 1.
-template <int NP>
-__device__ __forceinline__ void phase_aggregate(const double* lp, long long dstep, int N, int wstart,
-                                                int c1, const PdgCoef& C, double* Y, double* U) {
+template <int NP, class T>
+__device__ __forceinline__ void phase_aggregate(const double* lp, long long dstep, int N, int wstart, int c1,
+                                                const PdgCoef& C, T* Y, T* U) {
   int cp = wstart - 1;
   if (cp < 0) cp += N;
-  double u = lp[((long long)cp * NP + (NP - 1)) * dstep];
-  double y = 0.0;
-  const double qz = C.q[NP - 1] * C.zb;
+  T u = ld<T>(lp + ((long long)cp * NP + (NP - 1)) * dstep);
+  T y = zero<T>();
+  const T qz = PDG_C(T, C, q, NP - 1) * PDG_S(T, C, zb);
+  const T beta = PDG_S(T, C, beta);
+  T row[NP];
+  load_row<NP, T>(C, NP - 1, row);
   for (int c = wstart; c < c1; ++c) {
-    double v[NP];
-    load_cell<NP>(lp, dstep, c, v);
-    double alpha = qz * u;
-#pragma unroll
-    for (int j = 0; j < NP; ++j) alpha = fma(C.E[(NP - 1) * NP + j], v[j], alpha);
-    y = fma(C.beta, y, alpha);
+    T v[NP];
+    load_cell<NP, T>(lp, dstep, c, v);
+    const T alpha = dot_acc<NP>(row, v, qz * u);
+    y = fma(beta, y, alpha);
     u = v[NP - 1];
   }
   *Y = y;
@@ -149,21 +303,22 @@ __device__ __forceinline__ void phase_aggregate(const double* lp, long long dste
 }
 
 // Phase 2: sweep cells [c0, c1) with inflow (x, u) and write the new values in place.
-template <int NP>
-__device__ __forceinline__ void phase_sweep(double* lp, long long dstep, int c0, int c1, double x,
-                                            double u, const PdgCoef& C) {
+template <int NP, class T>
+__device__ __forceinline__ void phase_sweep(double* lp, long long dstep, int c0, int c1, T x, T u,
+                                            const PdgCoef& C) {
+  const T za = PDG_S(T, C, za), zb = PDG_S(T, C, zb);
   for (int c = c0; c < c1; ++c) {
-    double v[NP];
-    load_cell<NP>(lp, dstep, c, v);
-    const double z = fma(C.za, x, C.zb * u);
+    T v[NP];
+    load_cell<NP, T>(lp, dstep, c, v);
+    const T z = fma(za, x, zb * u);
     double* p0 = lp + (long long)c * NP * dstep;
-    double last = 0.0;
+    T last = zero<T>();
 #pragma unroll
     for (int r = 0; r < NP; ++r) {
-      double acc = C.q[r] * z;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) acc = fma(C.E[r * NP + j], v[j], acc);
-      p0[r * dstep] = acc;
+      T row[NP];
+      load_row<NP, T>(C, r, row);
+      const T acc = dot_acc<NP>(row, v, PDG_C(T, C, q, r) * z);
+      st(p0 + r * dstep, acc);
       if (r == NP - 1) last = acc;
     }
     x = last;
@@ -174,45 +329,47 @@ __device__ __forceinline__ void phase_sweep(double* lp, long long dstep, int c0,
 // Reverse mode (|beta| > 1): x_{c-1} = gamma (x_c - alpha_c).
 // Phase 1: y = x_{c0-1} from the first cells [c0, cend) of the segment, given the
 // old last-node value u0 of cell c0 - 1.
-template <int NP>
-__device__ __forceinline__ void phase_aggregate_rev(const double* lp, long long dstep, int c0, int cend,
-                                                    double u0, const PdgCoef& C, double* Y) {
-  double y = 0.0;
-  const double qz = C.q[NP - 1] * C.zb;
+template <int NP, class T>
+__device__ __forceinline__ void phase_aggregate_rev(const double* lp, long long dstep, int c0, int cend, T u0,
+                                                    const PdgCoef& C, T* Y) {
+  T y = zero<T>();
+  const T qz = PDG_C(T, C, q, NP - 1) * PDG_S(T, C, zb);
+  const T gamma = PDG_S(T, C, gamma);
+  T row[NP];
+  load_row<NP, T>(C, NP - 1, row);
   for (int c = cend - 1; c >= c0; --c) {
-    double v[NP];
-    load_cell<NP>(lp, dstep, c, v);
-    const double u = (c > c0) ? lp[((long long)(c - 1) * NP + (NP - 1)) * dstep] : u0;
-    double alpha = qz * u;
-#pragma unroll
-    for (int j = 0; j < NP; ++j) alpha = fma(C.E[(NP - 1) * NP + j], v[j], alpha);
-    y = C.gamma * (y - alpha);
+    T v[NP];
+    load_cell<NP, T>(lp, dstep, c, v);
+    const T u = (c > c0) ? ld<T>(lp + ((long long)(c - 1) * NP + (NP - 1)) * dstep) : u0;
+    const T alpha = dot_acc<NP>(row, v, qz * u);
+    y = gamma * (y - alpha);
   }
   *Y = y;
 }
 
 // Phase 2 (reverse): sweep cells c1-1 down to c0 from x = x_{c1-1}; u0 = old value of
 // the last node of cell c0 - 1 (saved before any write).
-template <int NP>
-__device__ __forceinline__ void phase_sweep_rev(double* lp, long long dstep, int c0, int c1, double x,
-                                                double u0, const PdgCoef& C) {
-  const double qz = C.q[NP - 1] * C.zb;
+template <int NP, class T>
+__device__ __forceinline__ void phase_sweep_rev(double* lp, long long dstep, int c0, int c1, T x, T u0,
+                                                const PdgCoef& C) {
+  const T qz = PDG_C(T, C, q, NP - 1) * PDG_S(T, C, zb);
+  const T gamma = PDG_S(T, C, gamma);
+  const T za = PDG_S(T, C, za), zb = PDG_S(T, C, zb);
   for (int c = c1 - 1; c >= c0; --c) {
-    double v[NP];
-    load_cell<NP>(lp, dstep, c, v);
-    const double u = (c > c0) ? lp[((long long)(c - 1) * NP + (NP - 1)) * dstep] : u0;
-    double alpha = qz * u;
-#pragma unroll
-    for (int j = 0; j < NP; ++j) alpha = fma(C.E[(NP - 1) * NP + j], v[j], alpha);
-    const double xm = C.gamma * (x - alpha);
-    const double z = fma(C.za, xm, C.zb * u);
+    T v[NP];
+    load_cell<NP, T>(lp, dstep, c, v);
+    const T u = (c > c0) ? ld<T>(lp + ((long long)(c - 1) * NP + (NP - 1)) * dstep) : u0;
+    T rowl[NP];
+    load_row<NP, T>(C, NP - 1, rowl);
+    const T alpha = dot_acc<NP>(rowl, v, qz * u);
+    const T xm = gamma * (x - alpha);
+    const T z = fma(za, xm, zb * u);
     double* p0 = lp + (long long)c * NP * dstep;
 #pragma unroll
     for (int r = 0; r < NP; ++r) {
-      double acc = C.q[r] * z;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) acc = fma(C.E[r * NP + j], v[j], acc);
-      p0[r * dstep] = acc;
+      T row[NP];
+      load_row<NP, T>(C, r, row);
+      st(p0 + r * dstep, dot_acc<NP>(row, v, PDG_C(T, C, q, r) * z));
     }
     x = xm;
   }
@@ -224,9 +381,9 @@ __device__ __forceinline__ long long line_base(const PdgPass& p, int line) {
 
 __device__ __forceinline__ int seg_begin(int s, int N, int S) { return (int)(((long long)s * N) / S); }
 
-template <int NP>
-__device__ void transport_op(const PdgPass& p, const PdgCoef& C, double* smY, double* smU, int l_in,
-                             int s, int grp, bool active, int line, int bid) {
+template <int NP, class T>
+__device__ void transport_op(const PdgPass& p, const PdgCoef& C, T* smY, T* smU, int l_in, int s, int grp,
+                             bool active, int line, int bid) {
   const int N = p.ncell, S = p.nseg, LPB = p.lpb, G = p.ngroup;
   const int c0 = seg_begin(s, N, S), c1 = seg_begin(s + 1, N, S);
   const long long base = active ? line_base(p, line) : 0;
@@ -237,14 +394,14 @@ __device__ void transport_op(const PdgPass& p, const PdgCoef& C, double* smY, do
       double* fl = p.f + (long long)p.tfield[phi] * p.field_stride + base;
       const long long dstep = dir > 0 ? p.stride : -p.stride;
       double* lp = dir > 0 ? fl : fl + (long long)(p.npl - 1) * p.stride;
-      double Y, U;
+      T Y, U;
       if (!C.rev) {
         const int wstart = C.full ? c0 : c1 - C.W;
-        phase_aggregate<NP>(lp, dstep, N, wstart, c1, C, &Y, &U);
+        phase_aggregate<NP, T>(lp, dstep, N, wstart, c1, C, &Y, &U);
       } else {
         const int cp = (c0 == 0) ? N - 1 : c0 - 1;
-        U = lp[((long long)cp * NP + (NP - 1)) * dstep];
-        phase_aggregate_rev<NP>(lp, dstep, c0, C.full ? c1 : c0 + C.W, U, C, &Y);
+        U = ld<T>(lp + ((long long)cp * NP + (NP - 1)) * dstep);
+        phase_aggregate_rev<NP, T>(lp, dstep, c0, C.full ? c1 : c0 + C.W, U, C, &Y);
       }
       const int o = (phi * S + s) * LPB + l_in;
       smY[o] = Y;
@@ -254,6 +411,7 @@ __device__ void transport_op(const PdgPass& p, const PdgCoef& C, double* smY, do
   __syncthreads();
   if (active) {
     const int Lbase = N / S;
+    const T bL0 = PDG_S(T, C, betaL0), bL1 = PDG_S(T, C, betaL1);
     for (int phi = grp; phi < p.ntf; phi += G) {
       const int dir = p.tdir[phi];
       double* fl = p.f + (long long)p.tfield[phi] * p.field_stride + base;
@@ -262,47 +420,47 @@ __device__ void transport_op(const PdgPass& p, const PdgCoef& C, double* smY, do
       if (!C.rev) {
         // inflow from the upwind segment s-1 (ring)
         const int sp = (s == 0) ? S - 1 : s - 1;
-        const double u = smU[(phi * S + sp) * LPB + l_in];
-        double x;
+        const T u = smU[(phi * S + sp) * LPB + l_in];
+        T x;
         if (!C.full) {
           x = smY[(phi * S + sp) * LPB + l_in];
         } else {
-          double acc = 0.0, cf = 1.0;
+          T acc = zero<T>(), cf = from_double<T>(1.0);
           int t = sp;
           for (int j = 0; j < S; ++j) {
             acc = fma(cf, smY[(phi * S + t) * LPB + l_in], acc);
             const int len = seg_begin(t + 1, N, S) - seg_begin(t, N, S);
-            cf *= (len == Lbase) ? C.betaL0 : C.betaL1;
+            cf = cf * ((len == Lbase) ? bL0 : bL1);
             t = (t == 0) ? S - 1 : t - 1;
           }
-          x = acc * C.inv_ring;
+          x = acc * PDG_S(T, C, inv_ring);
         }
-        phase_sweep<NP>(lp, dstep, c0, c1, x, u, C);
+        phase_sweep<NP, T>(lp, dstep, c0, c1, x, u, C);
       } else {
         // outflow value of the own segment from the downwind segment s+1 (ring)
         const int sn = (s == S - 1) ? 0 : s + 1;
-        const double u0 = smU[(phi * S + s) * LPB + l_in];
-        double x;
+        const T u0 = smU[(phi * S + s) * LPB + l_in];
+        T x;
         if (!C.full) {
           x = smY[(phi * S + sn) * LPB + l_in];
         } else {
-          double acc = 0.0, cf = 1.0;
+          T acc = zero<T>(), cf = from_double<T>(1.0);
           int t = sn;
           for (int j = 0; j < S; ++j) {
             acc = fma(cf, smY[(phi * S + t) * LPB + l_in], acc);
             const int len = seg_begin(t + 1, N, S) - seg_begin(t, N, S);
-            cf *= (len == Lbase) ? C.betaL0 : C.betaL1;
+            cf = cf * ((len == Lbase) ? bL0 : bL1);
             t = (t == S - 1) ? 0 : t + 1;
           }
-          x = acc * C.inv_ring;
+          x = acc * PDG_S(T, C, inv_ring);
         }
-        phase_sweep_rev<NP>(lp, dstep, c0, c1, x, u0, C);
+        phase_sweep_rev<NP, T>(lp, dstep, c0, c1, x, u0, C);
       }
     }
   }
 }
 
-template <int MV>
+template <int MV, class T>
 __device__ void collision_op(const PdgPass& p, int bid) {
   __syncthreads();
   constexpr int NF = NFields<MV>::value;
@@ -315,22 +473,21 @@ __device__ void collision_op(const PdgPass& p, int bid) {
     if (line >= p.nlines) continue;
     const long long off = line_base(p, line) + tpos * p.stride;
     const int nf = p.model.m * p.model.nv;
-    double v[NF];
+    T v[NF];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) v[k] = (k < nf) ? p.f[(long long)k * p.field_stride + off] : 0.0;
-    collide<MV>(v, p.model);
+    for (int k = 0; k < NF; ++k) v[k] = (k < nf) ? ld<T>(p.f + (long long)k * p.field_stride + off) : zero<T>();
+    collide<MV, T>(v, p.model);
 #pragma unroll
     for (int k = 0; k < NF; ++k)
-      if (k < nf) p.f[(long long)k * p.field_stride + off] = v[k];
+      if (k < nf) st(p.f + (long long)k * p.field_stride + off, v[k]);
   }
 }
 
-
 // One pass over block `bid` of a pass descriptor: the op list of p applied to the
-// lpb lines owned by the block.  sm: 2 * ntf * nseg * lpb doubles.  All threads of
-// the block must call it (it contains __syncthreads); threads with index >=
+// lpb lines owned by the block.  sm: 2 * ntf * nseg * lpb 8-byte words.  All threads
+// of the block must call it (it contains __syncthreads); threads with index >=
 // lpb * nseg * ngroup take part in the barriers and in the collision phase only.
-template <int NP, int MV>
+template <int NP, int MV, class T>
 __device__ __forceinline__ void pass_body(const PdgPass& p, int bid, double* sm) {
   const int LPB = p.lpb, S = p.nseg;
   const int t = threadIdx.x;
@@ -341,16 +498,16 @@ __device__ __forceinline__ void pass_body(const PdgPass& p, int bid, double* sm)
   const int line = bid * LPB + l_in;
   const bool active = (t < nthr) && line < p.nlines;
   const int cap = p.ntf * S * LPB;
-  double* smY = sm;
-  double* smU = sm + cap;
+  T* smY = reinterpret_cast<T*>(sm);
+  T* smU = smY + cap;
   for (int o = 0; o < p.nops; ++o) {
     if (p.op[o] == PDG_OP_T) {
       if (p.opcoef[o] == 0)
-        transport_op<NP>(p, p.coef[0], smY, smU, l_in, s, grp, active, line, bid);
+        transport_op<NP, T>(p, p.coef[0], smY, smU, l_in, s, grp, active, line, bid);
       else
-        transport_op<NP>(p, p.coef[1], smY, smU, l_in, s, grp, active, line, bid);
+        transport_op<NP, T>(p, p.coef[1], smY, smU, l_in, s, grp, active, line, bid);
     } else if (p.op[o] == PDG_OP_C) {
-      if constexpr (MV != MV_NONE) collision_op<MV>(p, bid);
+      if constexpr (MV != MV_NONE) collision_op<MV, T>(p, bid);
     }
   }
 }

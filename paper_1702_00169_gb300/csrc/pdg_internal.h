@@ -33,6 +33,24 @@ struct PdgCoef {
   int W;                  // window (cells) when truncated
   int full;               // 1: aggregate whole segments and close the ring exactly
   int rev;                // 1: upwind recurrence (|beta| > 1)
+  int pad_;
+  // the same values as double-float pairs (hi, lo) for the double-float kernels
+  float E_f[PDG_MAXN * PDG_MAXN][2];
+  float q_f[PDG_MAXN][2];
+  float za_f[1][2], zb_f[1][2], beta_f[1][2], gamma_f[1][2];
+  float betaL0_f[1][2], betaL1_f[1][2], inv_ring_f[1][2];
+};
+
+// Model constants precomputed on the host (FP64 and as float pairs).
+enum {
+  PDG_K_OM1 = 0,    // 1 - omega
+  PDG_K_C0 = 1,     // omega / (2D)
+  PDG_K_C1 = 2,     // omega / (2 lambda)
+  PDG_K_HALFG = 3,  // gravity / 2
+  PDG_K_GM1 = 4,    // gamma - 1
+  PDG_K_HALF = 5,   // 1/2
+  PDG_K_CADV = 6,   // omega (1/(2D) + s_i a_axis / (2 lambda)), 6 entries
+  PDG_K_N = 12
 };
 
 struct PdgModel {
@@ -40,12 +58,16 @@ struct PdgModel {
   int dim;       // D
   int m;         // conserved variables
   int nv;        // 2D
+  int prec;      // PDG_PREC_*
+  int pad_;
   double lambda;
   double omega;
   double a[3];
   double gravity;
   double gamma;
   double cadv[6];  // advection: 1/(2D) + s_i a_axis / (2 lambda) per population (f^eq_i / w)
+  double k[PDG_K_N];
+  float k_f[PDG_K_N][2];
 };
 
 enum { PDG_OP_NONE = 0, PDG_OP_T = 1, PDG_OP_C = 2 };
@@ -66,6 +88,7 @@ struct PdgPass {
   int tfield[2 * PDG_MAXM];    // field index (k * 2D + i)
   int tdir[2 * PDG_MAXM];      // +1 / -1
   int mv;                      // model variant of the collision (MV_* of pdg_device.cuh)
+  int prec;                    // PDG_PREC_* of the state and arithmetic
   PdgCoef coef[2];
   PdgModel model;
 };
@@ -88,6 +111,7 @@ struct PdgStateView {
   const double* f;
   long long npoints;
   int m, nv;
+  int prec;
   cudaStream_t stream;
 };
 // Fills v and returns true when the context has a state.
@@ -116,17 +140,30 @@ int pdg_plan_coef(int d, double nu, double theta, PdgCoef* c);
 // Smallest K >= 1 with |beta|^K <= 2^-60 (window that makes truncation exact to rounding).
 int pdg_plan_window(double beta);
 
+// Split a double into a double-float pair (hi = nearest float, lo = nearest float of the rest).
+inline void pdg_split(double x, float out[2]) {
+  const float h = (float)x;
+  out[0] = h;
+  out[1] = (float)(x - (double)h);
+}
+// Fill the float-pair copies of a coefficient set / of the model constants.
+void pdg_coef_split(PdgCoef* c);
+void pdg_model_constants(PdgModel* m);
+
 // ---- kernels (pdg_kernels.cu) ----
 // All return a cudaError_t cast to int.
 int pdg_launch_pass(const PdgPass& p, void* stream);
 int pdg_launch_set_feq(double* f, long long npoints, const PdgModel& m, void* stream);
 int pdg_launch_get_w(const double* f, double* w, long long npoints, const PdgModel& m, void* stream);
+// In-place conversion of n state values between FP64 and double-float (to_df != 0: FP64 -> pair).
+int pdg_launch_convert(double* f, long long n, int to_df, void* stream);
 // Model variant index used by the kernels (MV_* in pdg_device.cuh) for a model / pass.
 int pdg_model_variant(const PdgModel& m);
 
 // ---- batched persistent kernel (pdg_batch.cu) ----
 int pdg_batch_threads();
 size_t pdg_batch_smem(int max_carry_doubles);
-int pdg_batch_grid(size_t smem, int* grid);
+int pdg_batch_grid(size_t smem, int prec, int* grid);
 int pdg_launch_batch(const PdgPass* d_descs, const int* d_ent_desc, const long long* d_ent_start, int nent,
-                     long long total, unsigned long long* d_counter, int grid, size_t smem, void* stream);
+                     long long total, unsigned long long* d_counter, int grid, size_t smem, int prec,
+                     void* stream);

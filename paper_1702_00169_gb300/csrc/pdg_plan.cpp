@@ -162,3 +162,28 @@ int pdg_plan_window(double beta) {
   if (K > (double)(1 << 30)) return 1 << 30;
   return (int)K;
 }
+
+void pdg_coef_split(PdgCoef* c) {
+  for (int i = 0; i < PDG_MAXN * PDG_MAXN; ++i) pdg_split(c->E[i], c->E_f[i]);
+  for (int i = 0; i < PDG_MAXN; ++i) pdg_split(c->q[i], c->q_f[i]);
+  pdg_split(c->za, c->za_f[0]);
+  pdg_split(c->zb, c->zb_f[0]);
+  pdg_split(c->beta, c->beta_f[0]);
+  pdg_split(c->gamma, c->gamma_f[0]);
+  pdg_split(c->betaL0, c->betaL0_f[0]);
+  pdg_split(c->betaL1, c->betaL1_f[0]);
+  pdg_split(c->inv_ring, c->inv_ring_f[0]);
+}
+
+void pdg_model_constants(PdgModel* m) {
+  const double om = m->omega;
+  for (int i = 0; i < PDG_K_N; ++i) m->k[i] = 0.0;
+  m->k[PDG_K_OM1] = 1.0 - om;
+  m->k[PDG_K_C0] = m->kind == 1 ? 0.25 * om : om / (2.0 * m->dim);
+  m->k[PDG_K_C1] = om / (2.0 * m->lambda);
+  m->k[PDG_K_HALFG] = 0.5 * m->gravity;
+  m->k[PDG_K_GM1] = m->gamma - 1.0;
+  m->k[PDG_K_HALF] = 0.5;
+  for (int i = 0; i < 6; ++i) m->k[PDG_K_CADV + i] = om * m->cadv[i];
+  for (int i = 0; i < PDG_K_N; ++i) pdg_split(m->k[i], m->k_f[i]);
+}

@@ -19,6 +19,8 @@ PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA, PDG_ERR_STATE, PDG_ERR_TIMEOUT, PDG_ERR_
 PDG_MODEL_ADVECTION, PDG_MODEL_SHALLOW_WATER, PDG_MODEL_EULER = 0, 1, 2
 PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED = 0, 1
 PDG_PREC_FP64 = 0
+PDG_PREC_DF32 = 1
+PRECISION = {"fp64": PDG_PREC_FP64, "df32": PDG_PREC_DF32}
 
 KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER}
 SCHEME = {"M2": PDG_SCHEME_M2, "M2_collapsed": PDG_SCHEME_M2_COLLAPSED}
@@ -283,11 +285,12 @@ class Batch:
             pass
 
 
-def solver_for(cfg, scheme="M2", stream=None):
+def solver_for(cfg, scheme="M2", stream=None, precision=PDG_PREC_FP64):
     """Create a Solver with mesh and model of a workloads.Config."""
     s = Solver(cfg.dim, cfg.n_macro, cfg.n_sub, cfg.order, lengths=cfg.lengths[:cfg.dim], stream=stream)
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
     s.set_model(cfg.kind, cfg.lam, a=cfg.a, gravity=cfg.gravity, gamma=cfg.gamma, omega=cfg.omega,
-                theta=cfg.theta, scheme=scheme)
+                theta=cfg.theta, scheme=scheme, precision=prec)
     return s
 
 
@@ -321,7 +324,7 @@ class Server:
     def now(self):
         return pdg_server_now(self.s)
 
-    def submit(self, cfg, w0, nsteps, t_arrival=None, dt=None, scheme="M2"):
+    def submit(self, cfg, w0, nsteps, t_arrival=None, dt=None, scheme="M2", precision=PDG_PREC_FP64):
         """Enqueue a solve of workloads.Config `cfg` from w0 (host array)."""
         w0 = np.ascontiguousarray(np.asarray(w0, dtype=np.float64).reshape(-1))
         q = pdg_request()
@@ -331,7 +334,8 @@ class Server:
             q.n_sub[a] = cfg.n_sub[a] if a < cfg.dim else 1
         q.order = cfg.order
         q.model = model_desc(cfg.kind, cfg.lam, a=cfg.a, gravity=cfg.gravity, gamma=cfg.gamma, omega=cfg.omega,
-                             theta=cfg.theta, scheme=scheme)
+                             theta=cfg.theta, scheme=scheme,
+                             precision=PRECISION[precision] if isinstance(precision, str) else int(precision))
         q.dt = cfg.dt if dt is None else dt
         q.nsteps = int(nsteps)
         q.w0 = w0.ctypes.data

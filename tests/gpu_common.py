@@ -36,11 +36,11 @@ def run_oracle(cfg, w0, dt, nsteps, scheme="M2", method="bloch", omega=None):
     return OS.run(OS.initial_state(model, w0), tr, model, dt, nsteps, om, scheme)
 
 
-def run_gpu(cfg, w0, dt, nsteps, scheme="M2", launch=None, omega=None, stream=None):
+def run_gpu(cfg, w0, dt, nsteps, scheme="M2", launch=None, omega=None, stream=None, precision=0):
     from paper_1702_00169_gb300 import pdg
     import dataclasses
     c = cfg if omega is None else dataclasses.replace(cfg, omega=omega)
-    s = pdg.solver_for(c, scheme=scheme, stream=stream)
+    s = pdg.solver_for(c, scheme=scheme, stream=stream, precision=precision)
     if launch:
         for kind, shape in launch.items():
             s.set_launch(kind, *shape)
