@@ -263,6 +263,18 @@ int pdg_timing_read(pdg_ctx* ctx, long long* launches, double* ms, int max_kinds
  */
 int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
 
+/*
+ * pdg_set_option -- implementation switches of a context.
+ *   PDG_OPT_COMPOSE_TT (default 1): two consecutive transport sub-steps with the same
+ *     coefficients (the T(dt/2) T(dt/2) of consecutive palindromic steps) run as one
+ *     composed sweep, fn = E^2 f + (E q) z + q z', with a 2x2 inflow recurrence; the
+ *     same operator, about 27 % fewer operations per cell at degree 3, results equal
+ *     up to rounding.  0 runs them as two sweeps.
+ * Errors: PDG_ERR_ARG (unknown option).
+ */
+enum { PDG_OPT_COMPOSE_TT = 1 };
+int pdg_set_option(pdg_ctx* ctx, int option, int value);
+
 /* pdg_get_launch -- read the launch shape override of a kind 0..3 (zeros = heuristic). */
 int pdg_get_launch(const pdg_ctx* ctx, int kind, int* lpb, int* nseg, int* ngroup);
 

@@ -44,6 +44,7 @@ struct pdg_ctx {
   double* wstage = nullptr;
   long long wstage_cap = 0;
   bool async_alloc = false;   // state from the stream-ordered pool (cudaMallocAsync / cudaFreeAsync)
+  bool compose = true;        // compose consecutive equal transports into one T T sweep
   int launch[2][3] = {{0, 0, 0}, {0, 0, 0}};   // single-mesh shape overrides per pass kind
   int bshape[2][3] = {{0, 0, 0}, {0, 0, 0}};   // shapes inside batched launches (<= 256 threads)
   bool timing = false;
@@ -253,6 +254,23 @@ int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov,
     p.coef[i] = sp.cs[i];
     if (finish_coef(&p.coef[i], p.ncell, p.nseg))
       return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
+  }
+  // Two consecutive transports with the same coefficients become one composed T T
+  // op when the pair recurrence can use the window closure on these segments.
+  for (int o = 0; o + 1 < p.nops; ++o) {
+    if (p.op[o] != PDG_OP_T || p.op[o + 1] != PDG_OP_T || p.opcoef[o] != p.opcoef[o + 1]) continue;
+    PdgCoef& cf = p.coef[p.opcoef[o]];
+    if (cf.rev || cf.full || !c->compose) continue;
+    const int W2 = pdg_plan_compose(c->n, &cf);
+    if (W2 <= 0 || W2 > p.ncell / p.nseg) continue;
+    cf.W2 = W2;
+    pdg_coef_split(&cf);
+    p.op[o] = PDG_OP_TT;
+    for (int q = o + 1; q + 1 < p.nops; ++q) {
+      p.op[q] = p.op[q + 1];
+      p.opcoef[q] = p.opcoef[q + 1];
+    }
+    p.nops -= 1;
   }
   p.model = c->model;
   return PDG_OK;
@@ -825,6 +843,16 @@ int pdg_autotune(pdg_ctx* c, double dt, int reps) {
   return status;
 }
 
+int pdg_set_option(pdg_ctx* c, int option, int value) {
+  if (!c) return PDG_ERR_ARG;
+  switch (option) {
+    case PDG_OPT_COMPOSE_TT:
+      c->compose = value != 0;
+      return PDG_OK;
+  }
+  return fail(c, PDG_ERR_ARG, "unknown option");
+}
+
 int pdg_get_launch(const pdg_ctx* c, int kind, int* lpb, int* nseg, int* ngroup) {
   if (!c || kind < 0 || kind > 3 || !lpb || !nseg || !ngroup) return PDG_ERR_ARG;
   const int* slot = kind < 2 ? c->launch[kind] : c->bshape[kind - 2];
@@ -854,7 +882,7 @@ int pdg_batch_create(pdg_batch** out, int n, pdg_ctx* const* ctxs, void* cuda_st
   b->inst.assign(ctxs, ctxs + n);
   b->stream = (cudaStream_t)cuda_stream;
   // carry arrays sized for the largest population count (any instance list fits)
-  const int maxcarry = 2 * (2 * PDG_MAXM) * pdg_batch_threads();
+  const int maxcarry = 3 * (2 * PDG_MAXM) * pdg_batch_threads();
   b->smem = pdg_batch_smem(maxcarry);
   int e = pdg_batch_grid(b->smem, PDG_PREC_FP64, &b->grid);
   if (!e) e = pdg_batch_grid(b->smem, PDG_PREC_DF32, &b->grid_df);

@@ -265,11 +265,66 @@ template <> struct NFields<MV_NONE> { static constexpr int value = 1; };
 // Transport phases for one population along one line.  lp points at traversal
 // index 0 of the line, dstep is the signed stride between traversal indices.
 
+// 16-byte vector access to two consecutive state slots (x-axis lines are contiguous).
+__device__ __forceinline__ void ld2(const double* p, double* a, double* b) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  *a = v.x;
+  *b = v.y;
+}
+__device__ __forceinline__ void ld2(const double* p, dd* a, dd* b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  *a = dd{v.x, v.y};
+  *b = dd{v.z, v.w};
+}
+__device__ __forceinline__ void st2(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void st2(double* p, dd a, dd b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
+// Cell c of a line: NP values in traversal order.  On unit-stride lines (dstep = +-1)
+// with an even NP the cell is one 16-byte aligned block (lines start on 16-byte
+// boundaries and every cell holds NP * 8 bytes): vector loads, reversed in registers
+// for the backward direction.
 template <int NP, class T>
 __device__ __forceinline__ void load_cell(const double* lp, long long dstep, int c, T* v) {
   const double* p0 = lp + (long long)c * NP * dstep;
+  if constexpr (NP % 2 == 0) {
+    if (dstep == 1) {
+#pragma unroll
+      for (int j = 0; j < NP; j += 2) ld2(p0 + j, &v[j], &v[j + 1]);
+      return;
+    }
+    if (dstep == -1) {
+      const double* b = p0 - (NP - 1);
+#pragma unroll
+      for (int j = 0; j < NP; j += 2) ld2(b + j, &v[NP - 1 - j], &v[NP - 2 - j]);
+      return;
+    }
+  }
 #pragma unroll
   for (int j = 0; j < NP; ++j) v[j] = ld<T>(p0 + j * dstep);
+}
+
+template <int NP, class T>
+__device__ __forceinline__ void store_cell(double* lp, long long dstep, int c, const T* v) {
+  double* p0 = lp + (long long)c * NP * dstep;
+  if constexpr (NP % 2 == 0) {
+    if (dstep == 1) {
+#pragma unroll
+      for (int j = 0; j < NP; j += 2) st2(p0 + j, v[j], v[j + 1]);
+      return;
+    }
+    if (dstep == -1) {
+      double* b = p0 - (NP - 1);
+#pragma unroll
+      for (int j = 0; j < NP; j += 2) st2(b + j, v[NP - 1 - j], v[NP - 2 - j]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NP; ++j) st(p0 + j * dstep, v[j]);
 }
 
 template <int NP, class T>
@@ -303,10 +358,35 @@ __device__ __forceinline__ void phase_aggregate(const double* lp, long long dste
 }
 
 // Phase 2: sweep cells [c0, c1) with inflow (x, u) and write the new values in place.
+// On unit-stride lines the next cell is loaded before the current one is stored (they
+// never alias), so its memory latency overlaps the arithmetic; strided lines are
+// coalesced across the warp and keep the lighter loop.
 template <int NP, class T>
 __device__ __forceinline__ void phase_sweep(double* lp, long long dstep, int c0, int c1, T x, T u,
                                             const PdgCoef& C) {
   const T za = PDG_S(T, C, za), zb = PDG_S(T, C, zb);
+  if (dstep == 1 || dstep == -1) {
+    T v[NP];
+    if (c0 < c1) load_cell<NP, T>(lp, dstep, c0, v);
+    for (int c = c0; c < c1; ++c) {
+      T vn[NP];
+      if (c + 1 < c1) load_cell<NP, T>(lp, dstep, c + 1, vn);
+      const T z = fma(za, x, zb * u);
+      T out[NP];
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        T row[NP];
+        load_row<NP, T>(C, r, row);
+        out[r] = dot_acc<NP>(row, v, PDG_C(T, C, q, r) * z);
+      }
+      store_cell<NP, T>(lp, dstep, c, out);
+      x = out[NP - 1];
+      u = v[NP - 1];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) v[j] = vn[j];
+    }
+    return;
+  }
   for (int c = c0; c < c1; ++c) {
     T v[NP];
     load_cell<NP, T>(lp, dstep, c, v);
@@ -372,6 +452,70 @@ __device__ __forceinline__ void phase_sweep_rev(double* lp, long long dstep, int
       st(p0 + r * dstep, dot_acc<NP>(row, v, PDG_C(T, C, q, r) * z));
     }
     x = xm;
+  }
+}
+
+// Composed double sub-step T T (forward recurrence, window mode; see PdgCoef):
+// phase 1 aggregates the pair recurrence X_c = A_c + [[beta, 0], [gamma1, beta]] X_{c-1}
+// over the last cells [wstart, c1) of the segment, from X = 0.
+template <int NP, class T>
+__device__ __forceinline__ void phase_aggregate_tt(const double* lp, long long dstep, int N, int wstart, int c1,
+                                                   const PdgCoef& C, T* Y1, T* Y2, T* U) {
+  int cp = wstart - 1;
+  if (cp < 0) cp += N;
+  T u = ld<T>(lp + ((long long)cp * NP + (NP - 1)) * dstep);
+  T y1 = zero<T>(), y2 = zero<T>();
+  const T zb = PDG_S(T, C, zb);
+  const T qz = PDG_C(T, C, q, NP - 1) * zb;
+  const T eqz = PDG_C(T, C, Eq, NP - 1) * zb;
+  const T beta = PDG_S(T, C, beta), g1 = PDG_S(T, C, gamma1);
+  T rowE[NP], rowE2[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    rowE[j] = PDG_C(T, C, E, (NP - 1) * NP + j);
+    rowE2[j] = PDG_C(T, C, E2, (NP - 1) * NP + j);
+  }
+  for (int c = wstart; c < c1; ++c) {
+    T v[NP];
+    load_cell<NP, T>(lp, dstep, c, v);
+    const T a1 = dot_acc<NP>(rowE, v, qz * u);
+    const T a2 = dot_acc<NP>(rowE2, v, eqz * u);
+    y2 = fma(beta, y2, fma(g1, y1, a2));
+    y1 = fma(beta, y1, a1);
+    u = v[NP - 1];
+  }
+  *Y1 = y1;
+  *Y2 = y2;
+  *U = u;
+}
+
+// Phase 2 of T T: sweep [c0, c1) from the inflow pair (x, xp) and old value u.
+template <int NP, class T>
+__device__ __forceinline__ void phase_sweep_tt(double* lp, long long dstep, int c0, int c1, T x, T xp, T u,
+                                               const PdgCoef& C) {
+  const T za = PDG_S(T, C, za), zb = PDG_S(T, C, zb);
+  const T qn = PDG_C(T, C, q, NP - 1);
+  T rowE[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) rowE[j] = PDG_C(T, C, E, (NP - 1) * NP + j);
+  for (int c = c0; c < c1; ++c) {
+    T v[NP];
+    load_cell<NP, T>(lp, dstep, c, v);
+    const T z = fma(za, x, zb * u);
+    const T zp = fma(za, xp, zb * x);
+    T out[NP];
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      T row[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) row[j] = PDG_C(T, C, E2, r * NP + j);
+      out[r] = dot_acc<NP>(row, v, fma(PDG_C(T, C, Eq, r), z, PDG_C(T, C, q, r) * zp));
+    }
+    const T xn = dot_acc<NP>(rowE, v, qn * z);
+    store_cell<NP, T>(lp, dstep, c, out);
+    xp = out[NP - 1];
+    x = xn;
+    u = v[NP - 1];
   }
 }
 
@@ -460,6 +604,40 @@ __device__ void transport_op(const PdgPass& p, const PdgCoef& C, T* smY, T* smU,
   }
 }
 
+template <int NP, class T>
+__device__ void transport_op_tt(const PdgPass& p, const PdgCoef& C, T* smY, T* smY2, T* smU, int l_in, int s,
+                                int grp, bool active, int line) {
+  const int N = p.ncell, S = p.nseg, LPB = p.lpb, G = p.ngroup;
+  const int c0 = seg_begin(s, N, S), c1 = seg_begin(s + 1, N, S);
+  const long long base = active ? line_base(p, line) : 0;
+  __syncthreads();
+  if (active) {
+    for (int phi = grp; phi < p.ntf; phi += G) {
+      const int dir = p.tdir[phi];
+      double* fl = p.f + (long long)p.tfield[phi] * p.field_stride + base;
+      const long long dstep = dir > 0 ? p.stride : -p.stride;
+      double* lp = dir > 0 ? fl : fl + (long long)(p.npl - 1) * p.stride;
+      T Y1, Y2, U;
+      phase_aggregate_tt<NP, T>(lp, dstep, N, c1 - C.W2, c1, C, &Y1, &Y2, &U);
+      const int o = (phi * S + s) * LPB + l_in;
+      smY[o] = Y1;
+      smY2[o] = Y2;
+      smU[o] = U;
+    }
+  }
+  __syncthreads();
+  if (active) {
+    for (int phi = grp; phi < p.ntf; phi += G) {
+      const int dir = p.tdir[phi];
+      double* fl = p.f + (long long)p.tfield[phi] * p.field_stride + base;
+      const long long dstep = dir > 0 ? p.stride : -p.stride;
+      double* lp = dir > 0 ? fl : fl + (long long)(p.npl - 1) * p.stride;
+      const int o = (phi * S + ((s == 0) ? S - 1 : s - 1)) * LPB + l_in;
+      phase_sweep_tt<NP, T>(lp, dstep, c0, c1, smY[o], smY2[o], smU[o], C);
+    }
+  }
+}
+
 template <int MV, class T>
 __device__ void collision_op(const PdgPass& p, int bid) {
   __syncthreads();
@@ -484,7 +662,7 @@ __device__ void collision_op(const PdgPass& p, int bid) {
 }
 
 // One pass over block `bid` of a pass descriptor: the op list of p applied to the
-// lpb lines owned by the block.  sm: 2 * ntf * nseg * lpb 8-byte words.  All threads
+// lpb lines owned by the block.  sm: 3 * ntf * nseg * lpb 8-byte words.  All threads
 // of the block must call it (it contains __syncthreads); threads with index >=
 // lpb * nseg * ngroup take part in the barriers and in the collision phase only.
 template <int NP, int MV, class T>
@@ -500,12 +678,15 @@ __device__ __forceinline__ void pass_body(const PdgPass& p, int bid, double* sm)
   const int cap = p.ntf * S * LPB;
   T* smY = reinterpret_cast<T*>(sm);
   T* smU = smY + cap;
+  T* smY2 = smU + cap;
   for (int o = 0; o < p.nops; ++o) {
     if (p.op[o] == PDG_OP_T) {
       if (p.opcoef[o] == 0)
         transport_op<NP, T>(p, p.coef[0], smY, smU, l_in, s, grp, active, line, bid);
       else
         transport_op<NP, T>(p, p.coef[1], smY, smU, l_in, s, grp, active, line, bid);
+    } else if (p.op[o] == PDG_OP_TT) {
+      transport_op_tt<NP, T>(p, p.coef[p.opcoef[o]], smY, smY2, smU, l_in, s, grp, active, line);
     } else if (p.op[o] == PDG_OP_C) {
       if constexpr (MV != MV_NONE) collision_op<MV, T>(p, bid);
     }

@@ -33,12 +33,24 @@ struct PdgCoef {
   int W;                  // window (cells) when truncated
   int full;               // 1: aggregate whole segments and close the ring exactly
   int rev;                // 1: upwind recurrence (|beta| > 1)
-  int pad_;
+  int W2;                 // window of the composed double step (0: not composable)
+  // Two consecutive sub-steps T T with these coefficients, composed (forward, window mode):
+  //   gn_c = E2 f_c + Eq z_{c-1} + q z'_{c-1},  E2 = E E,  Eq = E q,
+  //   z = za x + zb u (first step), z' = za x' + zb x (second step),
+  //   (x, x') last-node values of the two steps: x_c = (E f_c)_{n-1} + q_{n-1} z_{c-1},
+  //   x'_c = (gn_c)_{n-1};  the pair obeys X_c = A_c + [[beta, 0], [gamma1, beta]] X_{c-1}
+  //   with gamma1 = Eq_{n-1} za + q_{n-1} zb.
+  double E2[PDG_MAXN * PDG_MAXN];
+  double Eq[PDG_MAXN];
+  double gamma1;
   // the same values as double-float pairs (hi, lo) for the double-float kernels
   float E_f[PDG_MAXN * PDG_MAXN][2];
   float q_f[PDG_MAXN][2];
   float za_f[1][2], zb_f[1][2], beta_f[1][2], gamma_f[1][2];
   float betaL0_f[1][2], betaL1_f[1][2], inv_ring_f[1][2];
+  float E2_f[PDG_MAXN * PDG_MAXN][2];
+  float Eq_f[PDG_MAXN][2];
+  float gamma1_f[1][2];
 };
 
 // Model constants precomputed on the host (FP64 and as float pairs).
@@ -70,7 +82,7 @@ struct PdgModel {
   float k_f[PDG_K_N][2];
 };
 
-enum { PDG_OP_NONE = 0, PDG_OP_T = 1, PDG_OP_C = 2 };
+enum { PDG_OP_NONE = 0, PDG_OP_T = 1, PDG_OP_C = 2, PDG_OP_TT = 3 };
 
 struct PdgPass {
   double* f;
@@ -139,6 +151,9 @@ void pdg_plan_dmat(int n, const double* x, double* Dm);
 int pdg_plan_coef(int d, double nu, double theta, PdgCoef* c);
 // Smallest K >= 1 with |beta|^K <= 2^-60 (window that makes truncation exact to rounding).
 int pdg_plan_window(double beta);
+// Fill E2, Eq, gamma1 of a coefficient set (n = order + 1) and return the window of the
+// composed recurrence (|beta|^K and K |gamma1| |beta|^(K-1) <= 2^-60), 0 if |beta| >= 1.
+int pdg_plan_compose(int n, PdgCoef* c);
 
 // Split a double into a double-float pair (hi = nearest float, lo = nearest float of the rest).
 inline void pdg_split(double x, float out[2]) {

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(512) pass_kernel(const __grid_constant__ PdgPa
 template <int NP, int MV, class T>
 int launch_pass_t(const PdgPass& p, cudaStream_t st) {
   const int threads = p.lpb * p.nseg * p.ngroup;
-  const size_t smem = sizeof(double) * 2 * (size_t)p.ntf * p.nseg * p.lpb;
+  const size_t smem = sizeof(double) * 3 * (size_t)p.ntf * p.nseg * p.lpb;
   auto kern = pass_kernel<NP, MV, T>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -163,6 +163,31 @@ int pdg_plan_window(double beta) {
   return (int)K;
 }
 
+int pdg_plan_compose(int n, PdgCoef* c) {
+  for (int r = 0; r < n; ++r) {
+    for (int j = 0; j < n; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc += c->E[r * n + k] * c->E[k * n + j];
+      c->E2[r * n + j] = acc;
+    }
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc += c->E[r * n + k] * c->q[k];
+    c->Eq[r] = acc;
+  }
+  c->gamma1 = c->Eq[n - 1] * c->za + c->q[n - 1] * c->zb;
+  const double b = std::fabs(c->beta), g = std::fabs(c->gamma1);
+  if (b >= 1.0) return 0;
+  const double tol = std::ldexp(1.0, -60);
+  double bk = 1.0;  // |beta|^(K-1)
+  for (int K = 1; K < (1 << 20); ++K) {
+    const double bK = bk * b;
+    if (bK <= tol && (double)K * g * bk <= tol) return K;
+    if (b == 0.0 && K >= 2) return K;
+    bk = bK;
+  }
+  return 0;
+}
+
 void pdg_coef_split(PdgCoef* c) {
   for (int i = 0; i < PDG_MAXN * PDG_MAXN; ++i) pdg_split(c->E[i], c->E_f[i]);
   for (int i = 0; i < PDG_MAXN; ++i) pdg_split(c->q[i], c->q_f[i]);
@@ -173,6 +198,9 @@ void pdg_coef_split(PdgCoef* c) {
   pdg_split(c->betaL0, c->betaL0_f[0]);
   pdg_split(c->betaL1, c->betaL1_f[0]);
   pdg_split(c->inv_ring, c->inv_ring_f[0]);
+  for (int i = 0; i < PDG_MAXN * PDG_MAXN; ++i) pdg_split(c->E2[i], c->E2_f[i]);
+  for (int i = 0; i < PDG_MAXN; ++i) pdg_split(c->Eq[i], c->Eq_f[i]);
+  pdg_split(c->gamma1, c->gamma1_f[0]);
 }
 
 void pdg_model_constants(PdgModel* m) {

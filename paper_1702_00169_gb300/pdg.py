@@ -21,6 +21,7 @@ PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED = 0, 1
 PDG_PREC_FP64 = 0
 PDG_PREC_DF32 = 1
 PRECISION = {"fp64": PDG_PREC_FP64, "df32": PDG_PREC_DF32}
+PDG_OPT_COMPOSE_TT = 1
 
 KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER}
 SCHEME = {"M2": PDG_SCHEME_M2, "M2_collapsed": PDG_SCHEME_M2_COLLAPSED}
@@ -73,6 +74,7 @@ _SIGS = {
     "pdg_timing_read": (_I, [_P, _P, _P, _I]),
     "pdg_set_launch": (_I, [_P, _I, _I, _I, _I]),
     "pdg_get_launch": (_I, [_P, _I, _P, _P, _P]),
+    "pdg_set_option": (_I, [_P, _I, _I]),
     "pdg_autotune": (_I, [_P, _D, _I]),
     "pdg_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P]),
     "pdg_batch_step": (_I, [_P, _P, _P, _I]),
@@ -229,6 +231,9 @@ class Solver:
     def set_launch(self, kind, lpb, nseg, ngroup):
         self._check(pdg_set_launch(self.ctx, kind, lpb, nseg, ngroup), "pdg_set_launch")
 
+
+    def set_option(self, option, value):
+        self._check(pdg_set_option(self.ctx, option, int(value)), "pdg_set_option")
 
     def get_launch(self, kind):
         v = [ctypes.c_int(), ctypes.c_int(), ctypes.c_int()]

@@ -224,3 +224,23 @@ def test_get_w_host_path_matches_moments():
                 ref = ref + f[:, i]
             np.testing.assert_allclose(w, ref, rtol=0, atol=1e-15 * np.max(np.abs(ref)))
         s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_composed_double_sweep_matches_two_sweeps(precision):
+    """PDG_OPT_COMPOSE_TT: the composed T T sweep and two single sweeps are the same
+    operator; both match the oracle (1e-12) and each other to rounding."""
+    from paper_1702_00169_gb300 import pdg
+    cfg = dataclasses.replace(W.SW_D2Q4, n_macro=(3, 4), n_sub=(5, 3), order=3)
+    w0 = oracle_w0(cfg)
+    out = []
+    for compose in (1, 0):
+        s = pdg.solver_for(cfg, precision=precision)
+        s.set_option(pdg.PDG_OPT_COMPOSE_TT, compose)
+        s.set_w(np.ascontiguousarray(w0.reshape(-1)))
+        s.step(cfg.dt, 7)
+        out.append(s.get_f().reshape((cfg.m, 4) + w0.shape[1:]))
+        s.close()
+    f_ref = run_oracle(cfg, w0, cfg.dt, 7)
+    assert rel_l2(out[0], f_ref) <= TOL and rel_l2(out[1], f_ref) <= TOL
+    assert rel_l2(out[0], out[1]) <= 1e-13

@@ -74,12 +74,15 @@ def test_mixed_results_equal_alone_and_oracle():
 
 
 def test_chunking_does_not_change_results():
+    """Chunk boundaries only split the transport passes of consecutive steps: the same
+    operator, evaluated as two sweeps instead of one composed sweep, so results agree
+    to rounding."""
     reqs = _requests()[:4]
     big = 1 << 34
     a, _ = _run(reqs, big, chunk=1, stagger=False)
     b, _ = _run(reqs, big, chunk=100, stagger=True)
     for i in range(len(reqs)):
-        np.testing.assert_array_equal(a[i], b[i])
+        assert np.linalg.norm(a[i] - b[i]) <= 1e-13 * np.linalg.norm(b[i])
 
 
 def test_request_larger_than_budget_rejected():
