@@ -55,10 +55,24 @@ def collision_flops_sw():
     return 9 + 1 + 2 + 2 + 6 + 3 + 4 * 12 + 9  # = 80
 
 
+def collision_flops(kind, dim):
+    """Algorithmic flops of the collision at one point (FMA = 2)."""
+    nv = 2 * dim
+    if kind == "shallow_water":
+        return collision_flops_sw()
+    if kind == "advection":
+        return (nv - 1) + 4 * nv
+    m = dim + 2
+    # moments; 1/rho; velocities; kinetic energy; pressure; per axis D momentum fluxes
+    # (one FMA, D-1 products) and the energy flux; c0 w_k per axis; 2 FMA per population
+    return m * (nv - 1) + 1 + dim + 2 * dim + 3 + dim * (2 + (dim - 1) + 2) + dim * m + 4 * m * nv
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--workload", default="shallow_water", choices=["shallow_water", "batched", "serving"])
+    ap.add_argument("--workload", default="shallow_water",
+                    choices=["shallow_water", "advection", "euler", "batched", "serving"])
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=64.0)
@@ -368,7 +382,7 @@ def bench_serving(args):
 def main():
     args = parse_args()
     from paper_1702_00169_gb300 import workloads as W
-    cfg = W.SW_D2Q4
+    cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6}.get(args.workload, W.SW_D2Q4)
     if args.impl == "reference":
         if args.steps is None:
             args.steps = 20
@@ -383,9 +397,9 @@ def main():
         bench_serving(args)
         return
     if args.steps is None:
-        args.steps = 1000
+        args.steps = {"euler": 20, "advection": 1000}.get(args.workload, 1000)
     if args.warmup is None:
-        args.warmup = 20
+        args.warmup = {"euler": 3}.get(args.workload, 20)
 
     import torch
     ws, rank, local = dist_env()
@@ -461,7 +475,7 @@ def main():
         sd.close()
         k_d = int(np.argmax(kms_d[:2]))
         avg_d = kms_d[k_d] / max(1, launches_d[k_d])
-        bytes_d = 16.0 * info.nfields * info.npoints if k_d == 1 else 8.0 * info.nfields * info.npoints
+        bytes_d = 16.0 * info.nfields * info.npoints if k_d == 1 else 16.0 * info.nfields * info.npoints / cfg.dim
         mixed = {"precision": "df32 (FP32-pair state and double-word arithmetic on the FP32 pipes)",
                  "value": dofs * args.steps * ws / (ms_d * 1e-3), "ms_per_step": ms_d / args.steps,
                  "speedup_vs_fp64": ms / ms_d,
@@ -507,15 +521,16 @@ def main():
     n = cfg.order + 1
     P = info.npoints
     F = info.nfields
-    kinds = {0: "transport pass (T T on +-x populations)", 1: "last-axis pass (T, collision, T)"}
+    kinds = {0: "transport pass (composed T T on the populations of the other axes)",
+             1: "last-axis pass (T, collision, T)"}
     k_dom = int(np.argmax(kms[:2]))
     avg_ms = kms[k_dom] / max(1, launches[k_dom])
     if k_dom == 1:
         bytes_launch = 16.0 * F * P
-        flops_launch = 2 * (F // 2) * P * transport_flops_per_dof(n) + P * collision_flops_sw()
+        flops_launch = 2 * (F // cfg.dim) * P * transport_flops_per_dof(n) + P * collision_flops(cfg.kind, cfg.dim)
     else:
-        bytes_launch = 16.0 * (F // 2) * P
-        flops_launch = 2 * (F // 2) * P * transport_flops_per_dof(n)
+        bytes_launch = 16.0 * (F // cfg.dim) * P
+        flops_launch = 2 * (F // cfg.dim) * P * transport_flops_per_dof(n)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -541,11 +556,15 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg.name, "model": "shallow water via vectorial D2Q4 (12 populations)",
-                       "mesh": "64x64 macrocells x 8x8 subcells, d=3, 2048x2048 GL points, periodic",
+            "config": {"workload": cfg.name,
+                       "model": f"{cfg.kind} via vectorial D{cfg.dim}Q{2 * cfg.dim} ({cfg.nfields} populations)",
+                       "mesh": (f"{'x'.join(map(str, cfg.n_macro))} macrocells x {'x'.join(map(str, cfg.n_sub))} "
+                                f"subcells, d={cfg.order}, {'x'.join(map(str, cfg.npoints_axis))} GL points, periodic"),
                        "dof": dofs, "scheme": args.scheme, "theta": cfg.theta, "omega": cfg.omega,
-                       "dt": cfg.dt, "lambda": cfg.lam, "precision": "FP64",
-                       "l2": "state 403 MB > 126 MB L2: inputs larger than L2, no flush",
+                       "dt": cfg.dt, "lambda": cfg.lam, "precision": args.precision.upper(),
+                       "l2": (f"state {cfg.dofs * 8 / 1e6:.0f} MB > 126 MB L2: inputs larger than L2, no flush"
+                              if cfg.dofs * 8 > 126e6 else
+                              f"state {cfg.dofs * 8 / 1e6:.1f} MB fits in L2: L2-resident (small parity workload)"),
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                        "launch_shapes": {"autotuned": not args.no_autotune, "transport_pass": list(shape0),
                                          "last_axis_pass": list(shape1)}},
