@@ -26,7 +26,8 @@ enum { MV_ADV = 0, MV_SW = 1, MV_EU1 = 2, MV_EU2 = 3, MV_EU3 = 4, MV_NONE = 5 };
 //   two_prod (with FMA): a * b = p + e exactly.
 // Double-word operations follow Joldes, Muller & Popescu, "Tight and rigorous error
 // bounds for basic building blocks of double-word arithmetic", ACM TOMS 44 (2017):
-//   add = AccurateDWPlusDW (relative error <= 3u^2 + 13u^3),
+//   add = SloppyDWPlusDW (Dekker) below, AccurateDWPlusDW (relative error
+//         <= 3u^2 + 13u^3) where cancellation must not cost relative accuracy,
 //   mul = DWTimesDW with FMA (relative error <= 5u^2), u = 2^-24.
 struct __align__(8) dd {
   float hi, lo;
@@ -46,7 +47,16 @@ __device__ __forceinline__ dd dd_two_prod(float a, float b) {
   const float p = __fmul_rn(a, b);
   return {p, __fmaf_rn(a, b, -p)};
 }
+// Addition: Dekker's double-word sum (SloppyDWPlusDW, 11 operations).  Its error is
+// bounded by about 2u^2 (|x| + |y|): relative to the operands rather than to the sum,
+// which on this scheme's O(1) populations is an absolute error of ~1e-15; the
+// accurate variant (AccurateDWPlusDW, 20 operations) is kept for the recurrences.
 __device__ __forceinline__ dd operator+(dd x, dd y) {
+  const dd s = dd_two_sum(x.hi, y.hi);
+  const float v = __fadd_rn(x.lo, y.lo);
+  return dd_fast_two_sum(s.hi, __fadd_rn(s.lo, v));
+}
+__device__ __forceinline__ dd dd_add_accurate(dd x, dd y) {
   const dd s = dd_two_sum(x.hi, y.hi);
   const dd t = dd_two_sum(x.lo, y.lo);
   const dd v = dd_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
@@ -71,6 +81,13 @@ __device__ __forceinline__ dd recip(dd x) {
   return dd{r0, 0.0f} + dd{r0, 0.0f} * e;
 }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// (1 - omega) f + omega f^eq for the double-float state: with omega = 2 the factor
+// 1 - omega = -1 is exact and the product is a sign flip.
+__device__ __forceinline__ dd relax(dd om1, dd v, dd e) {
+  if (om1.hi == -1.0f && om1.lo == 0.0f) return e - v;
+  return om1 * v + e;
+}
 
 template <class T> __device__ __forceinline__ T zero();
 template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
@@ -181,10 +198,19 @@ struct Collide<MV_SW, T> {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const T b = c0 * w[k];
-      v[4 * k + 0] = fma(om1, v[4 * k + 0], fma(c1, qx[k], b));
-      v[4 * k + 1] = fma(om1, v[4 * k + 1], fma(mc1, qx[k], b));
-      v[4 * k + 2] = fma(om1, v[4 * k + 2], fma(c1, qy[k], b));
-      v[4 * k + 3] = fma(om1, v[4 * k + 3], fma(mc1, qy[k], b));
+      if constexpr (sizeof(T) == sizeof(dd) && !__is_same(T, double)) {
+        // double-float: b +- c1 q shared by the two opposite populations
+        const T tx = c1 * qx[k], ty = c1 * qy[k];
+        v[4 * k + 0] = relax(om1, v[4 * k + 0], b + tx);
+        v[4 * k + 1] = relax(om1, v[4 * k + 1], b - tx);
+        v[4 * k + 2] = relax(om1, v[4 * k + 2], b + ty);
+        v[4 * k + 3] = relax(om1, v[4 * k + 3], b - ty);
+      } else {
+        v[4 * k + 0] = fma(om1, v[4 * k + 0], fma(c1, qx[k], b));
+        v[4 * k + 1] = fma(om1, v[4 * k + 1], fma(mc1, qx[k], b));
+        v[4 * k + 2] = fma(om1, v[4 * k + 2], fma(c1, qy[k], b));
+        v[4 * k + 3] = fma(om1, v[4 * k + 3], fma(mc1, qy[k], b));
+      }
     }
   }
 };
@@ -224,8 +250,14 @@ __device__ __forceinline__ void collide_euler(T* v, const PdgModel& M) {
 #pragma unroll
     for (int k = 0; k < m; ++k) {
       const T bse = c0 * w[k];
-      v[k * nv + 2 * a] = fma(om1, v[k * nv + 2 * a], fma(c1, q[k], bse));
-      v[k * nv + 2 * a + 1] = fma(om1, v[k * nv + 2 * a + 1], fma(mc1, q[k], bse));
+      if constexpr (!__is_same(T, double)) {
+        const T t = c1 * q[k];
+        v[k * nv + 2 * a] = relax(om1, v[k * nv + 2 * a], bse + t);
+        v[k * nv + 2 * a + 1] = relax(om1, v[k * nv + 2 * a + 1], bse - t);
+      } else {
+        v[k * nv + 2 * a] = fma(om1, v[k * nv + 2 * a], fma(c1, q[k], bse));
+        v[k * nv + 2 * a + 1] = fma(om1, v[k * nv + 2 * a + 1], fma(mc1, q[k], bse));
+      }
     }
   }
 }
