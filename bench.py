@@ -91,6 +91,21 @@ def parse_args():
     return ap.parse_args()
 
 
+def aggregate_ranks(ms_local, units_local):
+    """Whole-job figures of a replica run: the slowest rank's time and the sum of the
+    units all ranks processed (torch.distributed all_reduce, any backend)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms_local), float(units_local)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -459,13 +474,9 @@ def main():
     shape0, shape1 = s.get_launch(0), s.get_launch(1)
     finite = bool(np.all(np.isfinite(w_end)))
 
-    ms_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
     dofs = cfg.dofs
-    value = dofs * args.steps * ws / (ms_max * 1e-3)
+    ms_max, units = aggregate_ranks(ms, dofs * args.steps)
+    value = units / (ms_max * 1e-3)
 
     # ---- the same run in double-float precision (FP32-pair state and arithmetic) ----
     mixed = None
@@ -477,7 +488,8 @@ def main():
         avg_d = kms_d[k_d] / max(1, launches_d[k_d])
         bytes_d = 16.0 * info.nfields * info.npoints if k_d == 1 else 16.0 * info.nfields * info.npoints / cfg.dim
         mixed = {"precision": "df32 (FP32-pair state and double-word arithmetic on the FP32 pipes)",
-                 "value": dofs * args.steps * ws / (ms_d * 1e-3), "ms_per_step": ms_d / args.steps,
+                 "value": aggregate_ranks(ms_d, dofs * args.steps)[1] / (aggregate_ranks(ms_d, 0)[0] * 1e-3),
+                 "ms_per_step": ms_d / args.steps,
                  "speedup_vs_fp64": ms / ms_d,
                  "rel_l2_w_vs_fp64_after_steps": float(np.linalg.norm(w_end_d - w_end) / np.linalg.norm(w_end)),
                  "dominant_kernel_avg_ms": avg_d,
@@ -500,14 +512,10 @@ def main():
         s2.step(cfg.dt, args.steps)
         s2.get_w(w_out)
         t1 = time.perf_counter()
-        el = t1 - t0
-        if ws > 1:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            el = float(t.item())
+        el_max, units_e2e = aggregate_ranks(t1 - t0, dofs * args.steps)
         s2.close()
         nbytes = w0.nbytes
-        e2e = {"value": dofs * args.steps * ws / el, "unit": UNIT,
+        e2e = {"value": units_e2e / el_max, "unit": UNIT,
                "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
                "note": "one pdg_set_w (host) + pdg_step(K) + pdg_get_w (host) per timed run; bytes amortised over K"}
     s.close()
