@@ -8,6 +8,9 @@ Section 3.2:
       the method the paper retains for its results).
   Section 5.1, collapsed Strang: the last transport sub-step of a step and the
       first of the next are merged into one T_2(dt), except at the two ends.
+  M_2^kin(dt) = T_2(dt/4) C_2(dt/2) T_2(dt/2) C_2(dt/2) T_2(dt/4) (Section 3.2): the
+      composition that stays second order when tau -> 0; `omega` is then the weight of
+      each C_2(dt/2).
 
 The steps are applied in the naive order: every population is transported
 along its own velocity, then the collision acts on all populations, then every
@@ -67,7 +70,8 @@ def m2_step(f, transporter, model, dt, omega):
 
 
 def run(f0, transporter, model, dt, nsteps, omega, scheme="M2"):
-    """nsteps palindromic steps from f0.  scheme: "M2" or "M2_collapsed" (Section 5.1)."""
+    """nsteps palindromic steps from f0.  scheme: "M2", "M2_collapsed" (Section 5.1) or
+    "M2_kin" (Section 3.2)."""
     f = np.array(f0, dtype=np.float64, copy=True)
     if nsteps <= 0:
         return f
@@ -80,6 +84,14 @@ def run(f0, transporter, model, dt, nsteps, omega, scheme="M2"):
         for s in range(nsteps):
             f = collision(f, model, omega)
             f = transporter(f, dt if s < nsteps - 1 else 0.5 * dt)
+        return f
+    if scheme == "M2_kin":
+        for _ in range(nsteps):
+            f = transporter(f, 0.25 * dt)
+            f = collision(f, model, omega)
+            f = transporter(f, 0.5 * dt)
+            f = collision(f, model, omega)
+            f = transporter(f, 0.25 * dt)
         return f
     raise ValueError(scheme)
 

@@ -161,3 +161,37 @@ def test_collapsed_single_step_equals_m2():
     dt = mesh.h[0] / model.lam
     np.testing.assert_allclose(S.run(f0, tr, model, dt, 1, 2.0, "M2_collapsed"),
                                S.run(f0, tr, model, dt, 1, 2.0, "M2"), atol=0, rtol=0)
+
+
+def test_m2kin_zero_step_is_identity_unlike_m2():
+    """Section 3.2: with tau = 0, M2(0) F = 2 F^eq - F != F, while
+    M2^kin(0) = C_2 C_2 = I (the collision is an involution at omega = 2)."""
+    rng = np.random.default_rng(61)
+    model = M.Model(M.SHALLOW_WATER, 2, 8.0)
+    mesh = CartesianMesh(2, (2, 3), 2)
+    f = model.feq(_sw_state(mesh, rng)) + 1e-2 * rng.standard_normal((3, 4) + mesh.shape)
+    tr = S.Transporter(mesh, model, method="direct")
+    np.testing.assert_allclose(S.run(f, tr, model, 0.0, 1, 2.0, "M2_kin"), f, atol=1e-14)
+    assert np.max(np.abs(S.run(f, tr, model, 0.0, 1, 2.0, "M2") - f)) > 1e-3
+
+
+def test_m2kin_time_symmetric_for_positive_tau():
+    """The palindrome M2^kin with C_2(dt/2) weights omega(dt/2) = dt/(2 tau + dt/2):
+    M2^kin(-dt) M2^kin(dt) = I when tau > 0."""
+    rng = np.random.default_rng(62)
+    model = M.Model(M.SHALLOW_WATER, 2, 8.0)
+    mesh = CartesianMesh(2, (3, 2), 2)
+    f = model.feq(_sw_state(mesh, rng)) + 1e-3 * rng.standard_normal((3, 4) + mesh.shape)
+    tr = S.Transporter(mesh, model, method="direct")
+    tau, dt = 0.02, 0.01
+    om = lambda t: 2 * (t / 2) / (2 * tau + t / 2)
+    g = S.run(f, tr, model, dt, 1, om(dt), "M2_kin")
+    back = S.run(g, tr, model, -dt, 1, om(-dt), "M2_kin")
+    np.testing.assert_allclose(back, f, atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_m2kin_second_order(d):
+    errs = [_advection_error(d, N, "M2_kin") for N in (8, 16, 32)]
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(slopes > 1.8) and slopes[-1] > 1.9, (errs, slopes)
