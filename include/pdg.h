@@ -63,7 +63,10 @@ enum {
 /* Time schemes (Section 3.2 and Section 5.1). */
 enum {
   PDG_SCHEME_M2 = 0,          /* T(dt/2) C(dt) T(dt/2) per step                   */
-  PDG_SCHEME_M2_COLLAPSED = 1 /* consecutive half transports merged into T(dt)    */
+  PDG_SCHEME_M2_COLLAPSED = 1, /* consecutive half transports merged into T(dt)   */
+  PDG_SCHEME_M2KIN = 2         /* T(dt/4) C(dt/2) T(dt/2) C(dt/2) T(dt/4): second order
+                                  also as tau -> 0 (Section 3.2); omega is the weight of
+                                  each C(dt/2) */
 };
 
 /* State format and arithmetic. */
@@ -168,7 +171,8 @@ int pdg_set_w(pdg_ctx* ctx, const double* w, size_t len, int on_device);
  * (I - theta delta L_h) F^new = (I + (1-theta) delta L_h) F^old of eq. (3.11),
  * solved exactly on the periodic mesh, and C eq. (3.12).  With
  * PDG_SCHEME_M2_COLLAPSED the interior half transports are merged into T(dt)
- * (collapsed Strang of Section 5.1).  Asynchronous on the context stream.
+ * (collapsed Strang of Section 5.1); PDG_SCHEME_M2KIN advances M2^kin steps.
+ * Asynchronous on the context stream.
  * dt may be negative (time-symmetric use).  nsteps = 0 is a no-op.
  * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_CUDA.
  */

@@ -330,6 +330,45 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
   const int T = PDG_OP_T, C = PDG_OP_C;
   const int z1[1] = {0}, z2[2] = {0, 0}, z3[3] = {0, 0, 0};
   const int o1[1] = {T}, o2[2] = {T, T}, o3[3] = {T, C, T};
+  if (c->scheme == PDG_SCHEME_M2KIN) {
+    // T(dt/4) C T(dt/2) C T(dt/4) per step.  The collisions split the run into the
+    // transport segments seg_0 = T(q), then alternately T(h) and T(q) T(q) (the trailing
+    // quarter of a step and the leading quarter of the next), and seg_2n = T(q).  Each
+    // collision runs in a last-axis pass together with the last axis' transports around
+    // it; the other axes transport each segment in passes between the collisions.
+    PdgCoef qc[3], hc[3];
+    for (int a = 0; a < D; ++a) {
+      if (plan_line_coef(c, a, 0.25 * dt, &qc[a]) || plan_line_coef(c, a, 0.5 * dt, &hc[a]))
+        return fail(c, PDG_ERR_ARG, "singular transport step");
+      PdgCoef t0 = qc[a], t1 = hc[a];
+      if (finish_coef(&t0, c->N[a], 1) || finish_coef(&t1, c->N[a], 1))
+        return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
+    }
+    const int nseg = 2 * nsteps + 1;
+    // segment j: number of sub-steps and their coefficient index (0 = quarter, 1 = half)
+    auto seg_n = [&](int j) { return (j == 0 || j == nseg - 1) ? 1 : ((j % 2 == 1) ? 1 : 2); };
+    auto seg_ci = [&](int j) { return (j % 2 == 1) ? 1 : 0; };
+    auto other_axes = [&](int j) {
+      for (int a = 0; a < L; ++a) {
+        PdgCoef cs[2] = {qc[a], hc[a]};
+        const int ops[2] = {T, T}, ci[2] = {seg_ci(j), seg_ci(j)};
+        out.push_back(spec(a, seg_n(j), ops, ci, cs, 2));
+      }
+    };
+    PdgCoef csL[2] = {qc[L], hc[L]};
+    other_axes(0);
+    {
+      const int ops[3] = {T, C, T}, ci[3] = {seg_ci(0), 0, seg_ci(1)};
+      out.push_back(spec(L, 3, ops, ci, csL, 2));
+    }
+    for (int j = 1; j < nseg - 1; ++j) {
+      other_axes(j);
+      int ops[3] = {C, T, T}, ci[3] = {0, seg_ci(j + 1), seg_ci(j + 1)};
+      out.push_back(spec(L, 1 + seg_n(j + 1), ops, ci, csL, 2));
+    }
+    other_axes(nseg - 1);
+    return PDG_OK;
+  }
   if (c->scheme == PDG_SCHEME_M2) {
     for (int a = 0; a < L; ++a) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
     for (int s = 0; s < nsteps; ++s) {
@@ -467,7 +506,7 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   if (!c || !d) return PDG_ERR_ARG;
   if (d->kind < PDG_MODEL_ADVECTION || d->kind > PDG_MODEL_EULER)
     return fail(c, PDG_ERR_ARG, "unknown model kind");
-  if (d->scheme != PDG_SCHEME_M2 && d->scheme != PDG_SCHEME_M2_COLLAPSED)
+  if (d->scheme != PDG_SCHEME_M2 && d->scheme != PDG_SCHEME_M2_COLLAPSED && d->scheme != PDG_SCHEME_M2KIN)
     return fail(c, PDG_ERR_ARG, "unknown scheme");
   if (d->precision != PDG_PREC_FP64 && d->precision != PDG_PREC_DF32)
     return fail(c, PDG_ERR_UNSUPPORTED, "precision not available");

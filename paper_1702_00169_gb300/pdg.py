@@ -17,14 +17,14 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpdg.so")
 PDG_OK = 0
 PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA, PDG_ERR_STATE, PDG_ERR_TIMEOUT, PDG_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 PDG_MODEL_ADVECTION, PDG_MODEL_SHALLOW_WATER, PDG_MODEL_EULER = 0, 1, 2
-PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED = 0, 1
+PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED, PDG_SCHEME_M2KIN = 0, 1, 2
 PDG_PREC_FP64 = 0
 PDG_PREC_DF32 = 1
 PRECISION = {"fp64": PDG_PREC_FP64, "df32": PDG_PREC_DF32}
 PDG_OPT_COMPOSE_TT = 1
 
 KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER}
-SCHEME = {"M2": PDG_SCHEME_M2, "M2_collapsed": PDG_SCHEME_M2_COLLAPSED}
+SCHEME = {"M2": PDG_SCHEME_M2, "M2_collapsed": PDG_SCHEME_M2_COLLAPSED, "M2_kin": PDG_SCHEME_M2KIN}
 
 
 class pdg_model_desc(ctypes.Structure):

@@ -244,3 +244,15 @@ def test_composed_double_sweep_matches_two_sweeps(precision):
     f_ref = run_oracle(cfg, w0, cfg.dt, 7)
     assert rel_l2(out[0], f_ref) <= TOL and rel_l2(out[1], f_ref) <= TOL
     assert rel_l2(out[0], out[1]) <= 1e-13
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("nsteps", [1, 2, 5])
+def test_m2kin_scheme(precision, nsteps):
+    """M2^kin (Section 3.2) for shallow water and 3-D Euler against the oracle."""
+    for cfg in (dataclasses.replace(W.SW_D2Q4, n_macro=(2, 3), n_sub=(4, 3), order=3),
+                dataclasses.replace(W.EULER_D3Q6, n_macro=(2, 2, 2), n_sub=(2, 3, 2), order=2)):
+        w0 = oracle_w0(cfg)
+        f_ref = run_oracle(cfg, w0, cfg.dt, nsteps, scheme="M2_kin")
+        f = run_gpu(cfg, w0, cfg.dt, nsteps, scheme="M2_kin", precision=precision)
+        assert rel_l2(f, f_ref) <= TOL
