@@ -38,8 +38,9 @@ class CartesianMesh:
     N_a alone.
     """
 
-    def __init__(self, dim, ncells, d, lengths=None):
+    def __init__(self, dim, ncells, d, lengths=None, periodic=None):
         self.dim = int(dim)
+        self.periodic = tuple(bool(p) for p in (periodic if periodic is not None else (True,) * dim))
         self.N = tuple(int(v) for v in ncells)
         assert len(self.N) == self.dim
         self.d = int(d)
@@ -89,12 +90,18 @@ class CartesianMesh:
         return idx
 
 
-def assemble_transport(mesh, v):
+def assemble_transport(mesh, v, with_boundary=False):
     """Sparse L_h (npoints x npoints) for constant velocity v; eq. (3.7) DG_reduit.
 
     Every term of eq. (3.7) is added literally, for every local pair (i, j) and
     every face eps, vectorised over the cells (uniform affine cells share the
     coefficients).
+
+    Non-periodic axes (mesh.periodic[a] False) end at the domain boundary.  There the
+    neighbour value f_{R,i'} is the boundary datum f^b at the same face point (the
+    fictitious cell of eq. (3.8)); its coefficient - (1/omega_{L,i}) mu (v.c n^)^- is
+    returned, per point, in `bcoef` when with_boundary is True: the semi-discrete
+    system is d/dt f = L_h f + bcoef * f^b (only inflow face points have bcoef != 0).
     """
     D = mesh.dim
     n = mesh.n
@@ -114,6 +121,7 @@ def assemble_transport(mesh, v):
         return mesh.flat_index([cellc[a] * n + loc[a] for a in range(D)])
 
     rows, cols, vals = [], [], []
+    brows, bvals = [], []
     locs = list(itertools.product(range(n), repeat=D))   # loc[a] = i_a
     for i in locs:
         omega_i = float(np.prod([w1[i[a]] for a in range(D)]))
@@ -150,11 +158,24 @@ def assemble_transport(mesh, v):
                     ncell[a] = (cells[a] + s) % mesh.N[a]
                     ip = list(i)
                     ip[a] = 0 if s > 0 else n - 1   # matching point x_{L,i} = x_{R,i'}
-                    rows.append(row)
-                    cols.append(gidx(ncell, ip))
-                    vals.append(np.full(row.shape, -mu * vm / omega_Li))
+                    inside = np.ones(row.shape, dtype=bool)
+                    if not mesh.periodic[a]:
+                        inside = (cells[a] + s >= 0) & (cells[a] + s < mesh.N[a])
+                    coef = -mu * vm / omega_Li
+                    rows.append(row[inside])
+                    cols.append(gidx(ncell, ip)[inside])
+                    vals.append(np.full(int(inside.sum()), coef))
+                    if not inside.all():             # fictitious cell: f_R = f^b at the face point
+                        brows.append(row[~inside])
+                        bvals.append(np.full(int((~inside).sum()), coef))
     rows = np.concatenate(rows)
     cols = np.concatenate(cols)
     vals = np.concatenate(vals)
     N = mesh.npoints
-    return sp.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
+    L = sp.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
+    if not with_boundary:
+        return L
+    bcoef = np.zeros(N)
+    if brows:
+        np.add.at(bcoef, np.concatenate(brows), np.concatenate(bvals))
+    return L, bcoef.reshape(mesh.shape)

@@ -35,8 +35,11 @@ class Transporter:
     method = "bloch":  per-line Fourier closed form (any size).
     """
 
-    def __init__(self, mesh, model, theta=0.5, method="direct"):
+    def __init__(self, mesh, model, theta=0.5, method="direct", fb=None):
+        """fb: boundary data f^b, array (m, 2D, *grid) whose values at the inflow face
+        points of each population are used on non-periodic axes (direct method only)."""
         self.mesh, self.model, self.theta, self.method = mesh, model, theta, method
+        self.fb = fb
         self._cache = {}
 
     def _direct(self, i, delta):
@@ -46,10 +49,11 @@ class Transporter:
             self._cache[key] = DirectTransport(self.mesh, v, delta, self.theta)
         return self._cache[key]
 
-    def field(self, g, i, delta):
+    def field(self, g, i, delta, fb=None):
         """Transport one population array g (grid-shaped) with velocity v_i over delta."""
         if self.method == "direct":
-            return self._direct(i, delta)(g)
+            return self._direct(i, delta)(g, fb)
+        assert all(self.mesh.periodic), "the Bloch solver is periodic only"
         a, sign = i // 2, (+1 if i % 2 == 0 else -1)
         nu = 2.0 * self.model.lam * delta / self.mesh.h[a]
         return bloch_transport(g, self.mesh.axis_np(a), sign, self.mesh.d, nu, self.theta)
@@ -58,7 +62,7 @@ class Transporter:
         out = np.empty_like(f)
         for k in range(f.shape[0]):
             for i in range(f.shape[1]):
-                out[k, i] = self.field(f[k, i], i, delta)
+                out[k, i] = self.field(f[k, i], i, delta, None if self.fb is None else self.fb[k, i])
         return out
 
 
@@ -107,5 +111,5 @@ def weighted_total(mesh, w):
     return np.array([np.sum(M * w[k]) for k in range(w.shape[0])])
 
 
-def make_mesh(dim, ncells, d, lengths=None):
-    return CartesianMesh(dim, ncells, d, lengths)
+def make_mesh(dim, ncells, d, lengths=None, periodic=None):
+    return CartesianMesh(dim, ncells, d, lengths, periodic)

@@ -33,18 +33,27 @@ from .quadrature import gauss_lobatto, lagrange_derivative
 
 
 class DirectTransport:
-    """Solve (*) for one velocity v and sub-step delta with a sparse LU (SuperLU)."""
+    """Solve (*) for one velocity v and sub-step delta with a sparse LU (SuperLU).
+
+    On non-periodic axes the boundary data f^b enter through the fictitious cells of
+    eq. (3.8) (d/dt f_R = 0): with the augmented unknowns (f, f_R) the theta step
+    reduces to (I - theta delta L) f^new = (I + (1-theta) delta L) f^old
+    + delta * bcoef * f^b.
+    """
 
     def __init__(self, mesh, v, delta, theta=0.5):
         self.mesh = mesh
-        L = assemble_transport(mesh, v)
+        self.delta = delta
+        L, self.bcoef = assemble_transport(mesh, v, with_boundary=True)
         I = sp.identity(mesh.npoints, format="csr")
         self.A = (I - theta * delta * L).tocsc()
         self.B = (I + (1.0 - theta) * delta * L).tocsr()
         self.lu = spla.splu(self.A)
 
-    def __call__(self, field):
+    def __call__(self, field, fb=None):
         rhs = self.B @ np.asarray(field, dtype=np.float64).reshape(-1)
+        if fb is not None:
+            rhs = rhs + self.delta * (self.bcoef * np.asarray(fb, dtype=np.float64)).reshape(-1)
         return self.lu.solve(rhs).reshape(np.shape(field))
 
 
