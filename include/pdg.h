@@ -137,10 +137,12 @@ typedef struct pdg_info {
  *                  dim entries read; each >= 1)
  *   order          DG degree d in {1, 2, 3, 4}
  *   length         box edge lengths (> 0; first dim entries read); NULL = unit box
- *   periodic_mask  bit a set = axis a periodic; all dim bits must be set (inflow
- *                  boundaries return PDG_ERR_UNSUPPORTED)
+ *   periodic_mask  bit a set = axis a periodic; bit clear = the axis ends at inflow /
+ *                  outflow boundaries (eq. (2.6): each population takes the boundary
+ *                  datum f^b at its inflow face, through the fictitious cells of
+ *                  eq. (3.8); f^b = 0 until set with pdg_set_inflow)
  *   cuda_stream    cudaStream_t for all work of this context; NULL = legacy default stream
- * Allocates no device memory.  Errors: PDG_ERR_ARG, PDG_ERR_UNSUPPORTED, PDG_ERR_OOM.
+ * Allocates no device memory.  Errors: PDG_ERR_ARG, PDG_ERR_OOM.
  */
 int pdg_create_mesh(pdg_ctx** out, int dim, const int n_macro[3], const int n_sub[3], int order,
                     const double length[3], unsigned periodic_mask, void* cuda_stream);
@@ -196,6 +198,22 @@ int pdg_get_w(pdg_ctx* ctx, double* out, size_t len, int on_device);
  */
 int pdg_get_f(pdg_ctx* ctx, double* out, size_t len, int on_device);
 int pdg_set_f(pdg_ctx* ctx, const double* f, size_t len, int on_device);
+
+/*
+ * pdg_set_inflow -- boundary data f^b of a non-periodic axis (eq. (2.6) with the
+ * fictitious cells of eq. (3.8): f^b is constant in time).  On such an axis the upwind
+ * graph is acyclic (Section 4.1) and each line is swept from its inflow face with no
+ * cyclic closure.
+ *   fb   [2][m][lines] doubles: side 0 = the low face (x_a = 0), read by the +lambda e_a
+ *        populations; side 1 = the high face, read by the -lambda e_a populations; lines
+ *        are the points of the other axes in C order ([P_z][P_y] for axis 0, [P_z][P_x]
+ *        for axis 1, [P_y][P_x] for axis 2); len = 2 * m * lines.
+ *   on_device as for pdg_set_w.  Kept until the next pdg_set_inflow or a model change
+ *   (which resets it to zero).  Time steps that make |beta| > 1 (dt < 0) are not
+ *   supported on inflow axes (pdg_step returns PDG_ERR_UNSUPPORTED).
+ * Errors: PDG_ERR_STATE (no model), PDG_ERR_ARG (periodic axis, length), PDG_ERR_OOM, PDG_ERR_CUDA.
+ */
+int pdg_set_inflow(pdg_ctx* ctx, int axis, const double* fb, size_t len, int on_device);
 
 /*
  * pdg_get_points -- physical GL coordinates along one axis (eq. (3.3) map_GL:

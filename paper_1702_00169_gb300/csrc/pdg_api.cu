@@ -43,6 +43,8 @@ struct pdg_ctx {
   bool has_state = false;
   double* wstage = nullptr;
   long long wstage_cap = 0;
+  bool periodic[3] = {true, true, true};
+  double* fb[3] = {nullptr, nullptr, nullptr};  // inflow data per non-periodic axis: [2][m][lines]
   bool async_alloc = false;   // state from the stream-ordered pool (cudaMallocAsync / cudaFreeAsync)
   bool compose = true;        // compose consecutive equal transports into one T T sweep
   int launch[2][3] = {{0, 0, 0}, {0, 0, 0}};   // single-mesh shape overrides per pass kind
@@ -163,7 +165,7 @@ void choose_shape(const int* ov, int max_threads, int nlines, int ncell, int ntf
 // Fill the launch-dependent fields of a coefficient set for segments of a line of
 // N cells.  Returns 0, or -1 when the periodic system is singular (|beta| = 1 with
 // beta^N = 1).
-int finish_coef(PdgCoef* C, int N, int S) {
+int finish_coef(PdgCoef* C, int N, int S, bool periodic = true) {
   const int Lbase = N / S;
   const double ab = std::fabs(C->beta);
   C->rev = ab > 1.0 ? 1 : 0;
@@ -175,8 +177,8 @@ int finish_coef(PdgCoef* C, int N, int S) {
   C->betaL0 = std::pow(r, (double)Lbase);
   C->betaL1 = std::pow(r, (double)(Lbase + 1));
   const double rN = std::pow(r, (double)N);
-  if (!(std::fabs(1.0 - rN) > 1e-12)) return -1;
-  C->inv_ring = 1.0 / (1.0 - rN);
+  if (periodic && !(std::fabs(1.0 - rN) > 1e-12)) return -1;
+  C->inv_ring = periodic ? 1.0 / (1.0 - rN) : 0.0;
   pdg_coef_split(C);
   return 0;
 }
@@ -250,10 +252,14 @@ int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov,
     if (W > Wmax) Wmax = W;
   }
   choose_shape(ov, max_threads, p.nlines, p.ncell, p.ntf, Wmax, &p.lpb, &p.nseg, &p.ngroup);
+  p.periodic = c->periodic[axis] ? 1 : 0;
+  p.fb = c->periodic[axis] ? nullptr : c->fb[axis];
   for (int i = 0; i < sp.ncs && i < 2; ++i) {
     p.coef[i] = sp.cs[i];
-    if (finish_coef(&p.coef[i], p.ncell, p.nseg))
+    if (finish_coef(&p.coef[i], p.ncell, p.nseg, c->periodic[axis]))
       return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
+    if (!p.periodic && p.coef[i].rev)
+      return fail(c, PDG_ERR_UNSUPPORTED, "time steps with |beta| > 1 on an inflow (non-periodic) axis");
   }
   // Two consecutive transports with the same coefficients become one composed T T
   // op when the pair recurrence can use the window closure on these segments.
@@ -324,8 +330,11 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
     if (plan_line_coef(c, a, 0.5 * dt, &half[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
     if (plan_line_coef(c, a, dt, &full[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
     PdgCoef t0 = half[a], t1 = full[a];
-    if (finish_coef(&t0, c->N[a], 1) || (c->scheme == PDG_SCHEME_M2_COLLAPSED && finish_coef(&t1, c->N[a], 1)))
+    if (finish_coef(&t0, c->N[a], 1, c->periodic[a]) ||
+        (c->scheme == PDG_SCHEME_M2_COLLAPSED && finish_coef(&t1, c->N[a], 1, c->periodic[a])))
       return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
+    if (!c->periodic[a] && (t0.rev || (c->scheme == PDG_SCHEME_M2_COLLAPSED && t1.rev)))
+      return fail(c, PDG_ERR_UNSUPPORTED, "time steps with |beta| > 1 on an inflow (non-periodic) axis");
   }
   const int T = PDG_OP_T, C = PDG_OP_C;
   const int z1[1] = {0}, z2[2] = {0, 0}, z3[3] = {0, 0, 0};
@@ -341,8 +350,10 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
       if (plan_line_coef(c, a, 0.25 * dt, &qc[a]) || plan_line_coef(c, a, 0.5 * dt, &hc[a]))
         return fail(c, PDG_ERR_ARG, "singular transport step");
       PdgCoef t0 = qc[a], t1 = hc[a];
-      if (finish_coef(&t0, c->N[a], 1) || finish_coef(&t1, c->N[a], 1))
+      if (finish_coef(&t0, c->N[a], 1, c->periodic[a]) || finish_coef(&t1, c->N[a], 1, c->periodic[a]))
         return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
+      if (!c->periodic[a] && (t0.rev || t1.rev))
+        return fail(c, PDG_ERR_UNSUPPORTED, "time steps with |beta| > 1 on an inflow (non-periodic) axis");
     }
     const int nseg = 2 * nsteps + 1;
     // segment j: number of sub-steps and their coefficient index (0 = quarter, 1 = half)
@@ -412,6 +423,32 @@ int ensure_state(pdg_ctx* c) {
 
 size_t fields_of(const pdg_ctx* c) { return (size_t)c->model.m * c->model.nv; }
 
+// Lines of a pass along axis a (= points of the other axes).
+long long lines_of(const pdg_ctx* c, int a) { return c->npoints / c->P[a]; }
+
+// Allocate (zeroed) inflow data for every non-periodic axis of the current model.
+int ensure_inflow(pdg_ctx* c) {
+  for (int a = 0; a < c->dim; ++a) {
+    if (c->periodic[a] || c->fb[a]) continue;
+    const size_t n = 2 * (size_t)c->model.m * (size_t)lines_of(c, a);
+    cudaError_t e = cudaMalloc((void**)&c->fb[a], sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->fb[a], 0, sizeof(double) * n, c->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, PDG_ERR_OOM, std::string("inflow data: ") + cudaGetErrorString(e));
+    }
+  }
+  return PDG_OK;
+}
+
+void free_inflow(pdg_ctx* c) {
+  for (int a = 0; a < 3; ++a)
+    if (c->fb[a]) {
+      cudaFree(c->fb[a]);
+      c->fb[a] = nullptr;
+    }
+}
+
 }  // namespace
 
 bool pdg_internal_view(const pdg_ctx* c, PdgStateView* v) {
@@ -473,13 +510,12 @@ int pdg_create_mesh(pdg_ctx** out, int dim, const int n_macro[3], const int n_su
     if ((long long)n_macro[a] * n_sub[a] * (order + 1) > (1LL << 30)) return PDG_ERR_ARG;
     if (length && !(length[a] > 0.0 && std::isfinite(length[a]))) return PDG_ERR_ARG;
   }
-  const unsigned need = (1u << dim) - 1u;
-  if ((periodic_mask & need) != need) return PDG_ERR_UNSUPPORTED;
   pdg_ctx* c = new (std::nothrow) pdg_ctx();
   if (!c) return PDG_ERR_OOM;
   c->dim = dim;
   c->order = order;
   c->n = order + 1;
+  for (int a = 0; a < dim; ++a) c->periodic[a] = (periodic_mask >> a) & 1u;
   long long np = 1;
   for (int a = 0; a < 3; ++a) {
     if (a < dim) {
@@ -532,7 +568,10 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   M.prec = d->precision;
   pdg_model_constants(&M);
   // a different number of fields or a different state format invalidates the state
-  if (c->has_model && (c->model.m != M.m || c->model.prec != M.prec)) c->has_state = false;
+  if (c->has_model && (c->model.m != M.m || c->model.prec != M.prec)) {
+    c->has_state = false;
+    free_inflow(c);   // layout / format of the boundary data changes too (reset to zero)
+  }
   c->model = M;
   c->scheme = d->scheme;
   c->precision = d->precision;
@@ -548,6 +587,7 @@ int pdg_set_w(pdg_ctx* c, const double* w, size_t len, int on_device) {
   const size_t need = (size_t)c->model.m * c->npoints;
   if (len != need) return fail(c, PDG_ERR_ARG, "w length mismatch");
   if (int r = ensure_state(c)) return r;
+  if (int r = ensure_inflow(c)) return r;
   // w_k goes to field slot k; the kernel reads all w_k of a point before writing.
   PDG_CUDA(c, cudaMemcpyAsync(c->f, w, sizeof(double) * need,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
@@ -565,6 +605,7 @@ int pdg_set_f(pdg_ctx* c, const double* f, size_t len, int on_device) {
   const size_t need = fields_of(c) * c->npoints;
   if (len != need) return fail(c, PDG_ERR_ARG, "f length mismatch");
   if (int r = ensure_state(c)) return r;
+  if (int r = ensure_inflow(c)) return r;
   PDG_CUDA(c, cudaMemcpyAsync(c->f, f, sizeof(double) * need,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   if (c->model.prec == PDG_PREC_DF32) {
@@ -638,6 +679,24 @@ int pdg_step(pdg_ctx* c, double dt, int nsteps) {
   if (int r = build_schedule(c, dt, nsteps, sched)) return r;
   for (const auto& sp : sched)
     if (int r = issue_pass(c, sp)) return r;
+  return PDG_OK;
+}
+
+int pdg_set_inflow(pdg_ctx* c, int axis, const double* fb, size_t len, int on_device) {
+  if (!c) return PDG_ERR_ARG;
+  if (!c->has_model) return fail(c, PDG_ERR_STATE, "pdg_set_inflow before pdg_set_model");
+  if (axis < 0 || axis >= c->dim || c->periodic[axis]) return fail(c, PDG_ERR_ARG, "axis is not an inflow axis");
+  if (!fb) return fail(c, PDG_ERR_ARG, "fb is NULL");
+  const size_t need = 2 * (size_t)c->model.m * (size_t)lines_of(c, axis);
+  if (len != need) return fail(c, PDG_ERR_ARG, "inflow data length mismatch");
+  if (int r = ensure_inflow(c)) return r;
+  PDG_CUDA(c, cudaMemcpyAsync(c->fb[axis], fb, sizeof(double) * need,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  if (c->model.prec == PDG_PREC_DF32) {
+    int e = pdg_launch_convert(c->fb[axis], (long long)need, 1, (void*)c->stream);
+    if (e) return cuda_fail(c, (cudaError_t)e, "convert launch");
+  }
+  if (!on_device) PDG_CUDA(c, cudaStreamSynchronize(c->stream));
   return PDG_OK;
 }
 
@@ -746,6 +805,7 @@ int pdg_destroy(pdg_ctx* c) {
     else cudaFree(c->f);
   }
   if (c->wstage) cudaFree(c->wstage);
+  free_inflow(c);
   delete c;
   return PDG_OK;
 }

@@ -369,10 +369,10 @@ __device__ __forceinline__ void load_row(const PdgCoef& C, int r, T* row) {
 // and the old last-node value of cell c1 - 1.
 template <int NP, class T>
 __device__ __forceinline__ void phase_aggregate(const double* lp, long long dstep, int N, int wstart, int c1,
-                                                const PdgCoef& C, T* Y, T* U) {
+                                                const PdgCoef& C, T* Y, T* U, const T* inflow) {
   int cp = wstart - 1;
   if (cp < 0) cp += N;
-  T u = ld<T>(lp + ((long long)cp * NP + (NP - 1)) * dstep);
+  T u = (wstart == 0 && inflow) ? *inflow : ld<T>(lp + ((long long)cp * NP + (NP - 1)) * dstep);
   T y = zero<T>();
   const T qz = PDG_C(T, C, q, NP - 1) * PDG_S(T, C, zb);
   const T beta = PDG_S(T, C, beta);
@@ -492,10 +492,10 @@ __device__ __forceinline__ void phase_sweep_rev(double* lp, long long dstep, int
 // over the last cells [wstart, c1) of the segment, from X = 0.
 template <int NP, class T>
 __device__ __forceinline__ void phase_aggregate_tt(const double* lp, long long dstep, int N, int wstart, int c1,
-                                                   const PdgCoef& C, T* Y1, T* Y2, T* U) {
+                                                   const PdgCoef& C, T* Y1, T* Y2, T* U, const T* inflow) {
   int cp = wstart - 1;
   if (cp < 0) cp += N;
-  T u = ld<T>(lp + ((long long)cp * NP + (NP - 1)) * dstep);
+  T u = (wstart == 0 && inflow) ? *inflow : ld<T>(lp + ((long long)cp * NP + (NP - 1)) * dstep);
   T y1 = zero<T>(), y2 = zero<T>();
   const T zb = PDG_S(T, C, zb);
   const T qz = PDG_C(T, C, q, NP - 1) * zb;
@@ -557,6 +557,14 @@ __device__ __forceinline__ long long line_base(const PdgPass& p, int line) {
 
 __device__ __forceinline__ int seg_begin(int s, int N, int S) { return (int)(((long long)s * N) / S); }
 
+// Inflow boundary value of transported population phi on line `line` (non-periodic axes).
+template <class T>
+__device__ __forceinline__ T inflow_value(const PdgPass& p, int phi, int line) {
+  const int k = p.tfield[phi] / p.model.nv;
+  const int side = p.tdir[phi] > 0 ? 0 : 1;
+  return ld<T>(p.fb + ((long long)(side * p.model.m + k) * p.nlines + line));
+}
+
 template <int NP, class T>
 __device__ void transport_op(const PdgPass& p, const PdgCoef& C, T* smY, T* smU, int l_in, int s, int grp,
                              bool active, int line, int bid) {
@@ -573,7 +581,13 @@ __device__ void transport_op(const PdgPass& p, const PdgCoef& C, T* smY, T* smU,
       T Y, U;
       if (!C.rev) {
         const int wstart = C.full ? c0 : c1 - C.W;
-        phase_aggregate<NP, T>(lp, dstep, N, wstart, c1, C, &Y, &U);
+        T bval;
+        const T* inflow = nullptr;
+        if (!p.periodic) {
+          bval = inflow_value<T>(p, phi, line);
+          inflow = &bval;
+        }
+        phase_aggregate<NP, T>(lp, dstep, N, wstart, c1, C, &Y, &U, inflow);
       } else {
         const int cp = (c0 == 0) ? N - 1 : c0 - 1;
         U = ld<T>(lp + ((long long)cp * NP + (NP - 1)) * dstep);
@@ -593,7 +607,29 @@ __device__ void transport_op(const PdgPass& p, const PdgCoef& C, T* smY, T* smU,
       double* fl = p.f + (long long)p.tfield[phi] * p.field_stride + base;
       const long long dstep = dir > 0 ? p.stride : -p.stride;
       double* lp = dir > 0 ? fl : fl + (long long)(p.npl - 1) * p.stride;
-      if (!C.rev) {
+      if (!C.rev && !p.periodic) {
+        // open chain from the inflow boundary (fictitious cell value b, constant in time)
+        const T b = inflow_value<T>(p, phi, line);
+        T x, u;
+        if (s == 0) {
+          x = b;
+          u = b;
+        } else {
+          u = smU[(phi * S + s - 1) * LPB + l_in];
+          if (!C.full) {
+            x = smY[(phi * S + s - 1) * LPB + l_in];
+          } else {
+            T acc = zero<T>(), cf = from_double<T>(1.0);
+            for (int t = s - 1; t >= 0; --t) {
+              acc = fma(cf, smY[(phi * S + t) * LPB + l_in], acc);
+              const int len = seg_begin(t + 1, N, S) - seg_begin(t, N, S);
+              cf = cf * ((len == Lbase) ? bL0 : bL1);
+            }
+            x = fma(cf, b, acc);
+          }
+        }
+        phase_sweep<NP, T>(lp, dstep, c0, c1, x, u, C);
+      } else if (!C.rev) {
         // inflow from the upwind segment s-1 (ring)
         const int sp = (s == 0) ? S - 1 : s - 1;
         const T u = smU[(phi * S + sp) * LPB + l_in];
@@ -650,7 +686,13 @@ __device__ void transport_op_tt(const PdgPass& p, const PdgCoef& C, T* smY, T* s
       const long long dstep = dir > 0 ? p.stride : -p.stride;
       double* lp = dir > 0 ? fl : fl + (long long)(p.npl - 1) * p.stride;
       T Y1, Y2, U;
-      phase_aggregate_tt<NP, T>(lp, dstep, N, c1 - C.W2, c1, C, &Y1, &Y2, &U);
+      T bval;
+      const T* inflow = nullptr;
+      if (!p.periodic) {
+        bval = inflow_value<T>(p, phi, line);
+        inflow = &bval;
+      }
+      phase_aggregate_tt<NP, T>(lp, dstep, N, c1 - C.W2, c1, C, &Y1, &Y2, &U, inflow);
       const int o = (phi * S + s) * LPB + l_in;
       smY[o] = Y1;
       smY2[o] = Y2;
@@ -664,8 +706,13 @@ __device__ void transport_op_tt(const PdgPass& p, const PdgCoef& C, T* smY, T* s
       double* fl = p.f + (long long)p.tfield[phi] * p.field_stride + base;
       const long long dstep = dir > 0 ? p.stride : -p.stride;
       double* lp = dir > 0 ? fl : fl + (long long)(p.npl - 1) * p.stride;
-      const int o = (phi * S + ((s == 0) ? S - 1 : s - 1)) * LPB + l_in;
-      phase_sweep_tt<NP, T>(lp, dstep, c0, c1, smY[o], smY2[o], smU[o], C);
+      if (!p.periodic && s == 0) {
+        const T b = inflow_value<T>(p, phi, line);   // both sub-steps see the constant fictitious value
+        phase_sweep_tt<NP, T>(lp, dstep, c0, c1, b, b, b, C);
+      } else {
+        const int o = (phi * S + ((s == 0) ? S - 1 : s - 1)) * LPB + l_in;
+        phase_sweep_tt<NP, T>(lp, dstep, c0, c1, smY[o], smY2[o], smU[o], C);
+      }
     }
   }
 }

@@ -101,6 +101,9 @@ struct PdgPass {
   int tdir[2 * PDG_MAXM];      // +1 / -1
   int mv;                      // model variant of the collision (MV_* of pdg_device.cuh)
   int prec;                    // PDG_PREC_* of the state and arithmetic
+  int periodic;                // 1: periodic lines; 0: inflow boundary data fb
+  int pad2_;
+  const double* fb;            // non-periodic: inflow values [2 sides][m][nlines] (state format)
   PdgCoef coef[2];
   PdgModel model;
 };

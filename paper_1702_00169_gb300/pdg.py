@@ -66,6 +66,7 @@ _SIGS = {
     "pdg_get_f": (_I, [_P, _P, _SZ, _I]),
     "pdg_set_f": (_I, [_P, _P, _SZ, _I]),
     "pdg_get_points": (_I, [_P, _I, _P, _SZ]),
+    "pdg_set_inflow": (_I, [_P, _I, _P, _SZ, _I]),
     "pdg_get_info": (_I, [_P, ctypes.POINTER(pdg_info)]),
     "pdg_get_line_coefs": (_I, [_P, _I, _D, _P, _P, _P]),
     "pdg_get_w_noalloc": (_I, [_P, _P, _SZ]),
@@ -131,13 +132,14 @@ def _ptr(x, want_device):
 class Solver:
     """Owns one pdg_ctx.  Methods map one-to-one onto the C ABI."""
 
-    def __init__(self, dim, n_macro, n_sub, order, lengths=None, stream=None):
+    def __init__(self, dim, n_macro, n_sub, order, lengths=None, stream=None, periodic=None):
         self.ctx = _P()
         nm = (_I * 3)(*(list(n_macro) + [1] * (3 - len(n_macro))))
         ns = (_I * 3)(*(list(n_sub) + [1] * (3 - len(n_sub))))
         ln = None if lengths is None else (_D * 3)(*(list(lengths) + [1.0] * (3 - len(lengths))))
         st = _P(stream) if stream else None
-        r = pdg_create_mesh(ctypes.byref(self.ctx), dim, nm, ns, order, ln, (1 << dim) - 1, st)
+        mask = (1 << dim) - 1 if periodic is None else sum(1 << a for a in range(dim) if periodic[a])
+        r = pdg_create_mesh(ctypes.byref(self.ctx), dim, nm, ns, order, ln, mask, st)
         if r != PDG_OK:
             raise PdgError(r, "pdg_create_mesh")
         self.dim = dim
@@ -183,6 +185,10 @@ class Solver:
     def set_w(self, w):
         p, dev, n = _ptr(w, None)
         self._check(pdg_set_w(self.ctx, p, n, dev), "pdg_set_w")
+
+    def set_inflow(self, axis, fb):
+        p, dev, n = _ptr(fb, None)
+        self._check(pdg_set_inflow(self.ctx, axis, p, n, dev), "pdg_set_inflow")
 
     def set_f(self, f):
         p, dev, n = _ptr(f, None)

@@ -42,7 +42,8 @@ def test_create_mesh_validation(pdg):
     assert pdg.pdg_create_mesh(ctypes.byref(ctx), 4, nm, ns, 2, None, 15, None) == pdg.PDG_ERR_ARG
     assert pdg.pdg_create_mesh(ctypes.byref(ctx), 2, nm, ns, 0, None, 3, None) == pdg.PDG_ERR_ARG
     assert pdg.pdg_create_mesh(ctypes.byref(ctx), 2, nm, ns, 5, None, 3, None) == pdg.PDG_ERR_ARG
-    assert pdg.pdg_create_mesh(ctypes.byref(ctx), 2, nm, ns, 2, None, 1, None) == pdg.PDG_ERR_UNSUPPORTED
+    assert pdg.pdg_create_mesh(ctypes.byref(ctx), 2, nm, ns, 2, None, 1, None) == pdg.PDG_OK  # y: inflow axis
+    assert pdg.pdg_destroy(ctx) == pdg.PDG_OK
     bad = (ctypes.c_int * 3)(0, 4, 1)
     assert pdg.pdg_create_mesh(ctypes.byref(ctx), 2, bad, ns, 2, None, 3, None) == pdg.PDG_ERR_ARG
     assert pdg.pdg_create_mesh(None, 2, nm, ns, 2, None, 3, None) == pdg.PDG_ERR_ARG
@@ -130,4 +131,17 @@ def test_line_coefficients_vs_oracle_bloch_zero_mode(pdg, d, nu, theta):
     fn = E @ f + q * (za * x + zb * f[n - 1])
     ref = bloch_transport(f, -1, +1, d, nu, theta)
     np.testing.assert_allclose(fn, ref, rtol=0, atol=1e-13)
+    s.close()
+
+
+def test_inflow_validation_host(pdg):
+    s = pdg.Solver(2, (3, 2), (2, 2), 2, periodic=(False, True))
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_inflow(0, np.zeros(4))
+    assert e.value.status == pdg.PDG_ERR_STATE
+    s.set_model("shallow_water", 8.0)
+    for axis, n in ((1, 2 * 3 * 18), (0, 7)):   # periodic axis, wrong length
+        with pytest.raises(pdg.PdgError) as e:
+            s.set_inflow(axis, np.zeros(n))
+        assert e.value.status == pdg.PDG_ERR_ARG
     s.close()
