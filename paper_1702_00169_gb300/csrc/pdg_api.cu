@@ -61,17 +61,17 @@ struct pdg_batch {
   std::vector<pdg_ctx*> inst;
   cudaStream_t stream = nullptr;       // the caller's stream (may be the legacy default stream)
   cudaStream_t cap = nullptr;          // private blocking stream used for graph capture and replay
-  int grid = 0;                        // persistent grid, FP64 kernel
-  int grid_df = 0;                     // persistent grid, double-float kernel
   size_t smem = 0;
   // device tables of the last pdg_batch_step (kept alive for the captured graph)
   PdgPass* d_desc = nullptr;
   int* d_ent_desc = nullptr;
   long long* d_ent_start = nullptr;
   unsigned long long* d_counter = nullptr;
-  size_t cap_desc = 0, cap_ent = 0, cap_cnt = 0;
-  // per launch (one per stage and precision present): first entry, entries, work items, precision
-  std::vector<int> st_off, st_nent, st_prec;
+  size_t cap_desc = 0, cap_ent = 0, cap_es = 0, cap_cnt = 0;
+  bool realloc = false;                // a table moved: the cached graph must be recaptured
+  // per launch (one per stage and (precision, degree, model) group present): first entry,
+  // entries, work items, group
+  std::vector<int> st_off, st_nent, st_prec, st_np, st_mv;
   std::vector<long long> st_total;
   std::vector<char> sig;                      // signature of the tables (graph cache key)
   cudaGraphExec_t gexec = nullptr;
@@ -983,8 +983,7 @@ int pdg_batch_create(pdg_batch** out, int n, pdg_ctx* const* ctxs, void* cuda_st
   // carry arrays sized for the largest population count (any instance list fits)
   const int maxcarry = 3 * (2 * PDG_MAXM) * pdg_batch_threads();
   b->smem = pdg_batch_smem(maxcarry);
-  int e = pdg_batch_grid(b->smem, PDG_PREC_FP64, &b->grid);
-  if (!e) e = pdg_batch_grid(b->smem, PDG_PREC_DF32, &b->grid_df);
+  int e = 0;
   // Graphs cannot be captured on the legacy default stream: capture and replay on a
   // private blocking stream joined to the caller's stream with events.
   if (e || cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess ||
@@ -1010,6 +1009,13 @@ int bfail(pdg_batch* b, int code, const std::string& m) {
 template <class T>
 int ensure_dev(pdg_batch* b, T** p, size_t* cap, size_t need) {
   if (need <= *cap) return PDG_OK;
+  // the cached graph holds the old address: it is replayed no more (and freed first)
+  if (b->gexec) {
+    cudaStreamSynchronize(b->cap);
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  b->realloc = true;
   if (*p) cudaFree(*p);
   *p = nullptr;
   *cap = 0;
@@ -1081,13 +1087,25 @@ int batch_prepare(pdg_batch* b, const double* dt, const int* nsteps) {
   b->st_nent.clear();
   b->st_total.clear();
   b->st_prec.clear();
+  b->st_np.clear();
+  b->st_mv.clear();
   for (size_t t = 0; t < nst; ++t) {
-    for (int prec = 0; prec < 2; ++prec) {
+    // groups of this stage: one persistent launch per (precision, degree, model) variant
+    std::vector<int> keys;
+    for (int i = 0; i < n; ++i)
+      if (t < plist[i].size()) {
+        const PdgPass& d = descs[plist[i][t]];
+        const int key = (d.prec * 8 + d.npl / d.ncell) * 8 + d.mv;
+        if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+      }
+    std::sort(keys.begin(), keys.end());
+    for (int key : keys) {
       std::vector<std::pair<double, int>> order;  // (cost per item, instance)
       for (int i = 0; i < n; ++i)
-        if (t < plist[i].size() && descs[plist[i][t]].prec == prec)
-          order.push_back({item_cost(descs[plist[i][t]]), i});
-      if (order.empty()) continue;
+        if (t < plist[i].size()) {
+          const PdgPass& d = descs[plist[i][t]];
+          if ((d.prec * 8 + d.npl / d.ncell) * 8 + d.mv == key) order.push_back({item_cost(d), i});
+        }
       std::stable_sort(order.begin(), order.end(), [](const std::pair<double, int>& x,
                                                       const std::pair<double, int>& y) { return x.first > y.first; });
       b->st_off.push_back((int)ent_desc.size());
@@ -1099,26 +1117,17 @@ int batch_prepare(pdg_batch* b, const double* dt, const int* nsteps) {
       }
       b->st_nent.push_back((int)order.size());
       b->st_total.push_back(acc);
-      b->st_prec.push_back(prec);
+      b->st_prec.push_back(key / 64);
+      b->st_np.push_back((key / 8) % 8);
+      b->st_mv.push_back(key % 8);
     }
   }
   nst = b->st_off.size();
   if (int r = ensure_dev(b, &b->d_desc, &b->cap_desc, std::max<size_t>(1, descs.size()))) return r;
   if (int r = ensure_dev(b, &b->d_ent_desc, &b->cap_ent, std::max<size_t>(1, ent_desc.size()))) return r;
-  size_t cap2 = b->cap_ent;
-  b->cap_ent = 0;
-  long long* es = b->d_ent_start;
-  size_t cap_es = (es && cap2 >= ent_start.size()) ? cap2 : 0;
-  (void)cap_es;
-  if (b->d_ent_start) cudaFree(b->d_ent_start);
-  b->d_ent_start = nullptr;
-  cudaError_t e = cudaMalloc((void**)&b->d_ent_start, sizeof(long long) * std::max<size_t>(1, ent_start.size()));
-  b->cap_ent = cap2;
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return bfail(b, PDG_ERR_OOM, "batch table allocation failed");
-  }
+  if (int r = ensure_dev(b, &b->d_ent_start, &b->cap_es, std::max<size_t>(1, ent_start.size()))) return r;
   if (int r = ensure_dev(b, &b->d_counter, &b->cap_cnt, std::max<size_t>(1, nst))) return r;
+  cudaError_t e = cudaSuccess;
   e = cudaMemcpyAsync(b->d_desc, descs.data(), sizeof(PdgPass) * descs.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_ent_desc, ent_desc.data(), sizeof(int) * ent_desc.size(), cudaMemcpyHostToDevice,
@@ -1146,10 +1155,9 @@ int batch_issue(pdg_batch* b, cudaStream_t st) {
   if (e != cudaSuccess) return bfail(b, PDG_ERR_CUDA, std::string("batch counters: ") + cudaGetErrorString(e));
   long long launches = 0;
   for (size_t t = 0; t < nst; ++t) {
-    const int prec = b->st_prec[t];
     int r = pdg_launch_batch(b->d_desc, b->d_ent_desc + b->st_off[t], b->d_ent_start + b->st_off[t],
-                             b->st_nent[t], b->st_total[t], b->d_counter + t,
-                             prec == PDG_PREC_DF32 ? b->grid_df : b->grid, b->smem, prec, (void*)st);
+                             b->st_nent[t], b->st_total[t], b->d_counter + t, b->smem, b->st_prec[t],
+                             b->st_np[t], b->st_mv[t], (void*)st);
     if (r) return bfail(b, PDG_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString((cudaError_t)r));
     launches += b->st_total[t] > 0;
   }
@@ -1315,9 +1323,8 @@ int pdg_batch_autotune(pdg_batch* b, const double* dt, int reps) {
         float ms = 0.f;
         status = time_launches(c, reps, [&]() {
           cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), c->stream);
-          const int prec = c->model.prec;
-          int er = pdg_launch_batch(d_p, d_ent, d_start, 1, total, d_cnt,
-                                    prec == PDG_PREC_DF32 ? b->grid_df : b->grid, b->smem, prec, (void*)c->stream);
+          int er = pdg_launch_batch(d_p, d_ent, d_start, 1, total, d_cnt, b->smem, p.prec, p.npl / p.ncell, p.mv,
+                                    (void*)c->stream);
           return er ? cuda_fail(c, (cudaError_t)er, "batch autotune launch") : PDG_OK;
         }, &ms);
         if (status) break;

@@ -18,19 +18,7 @@ namespace pdgdev {
 constexpr int kBatchThreads = 256;
 constexpr int kDescWords = (int)((sizeof(PdgPass) + 7) / 8);
 
-template <int NP, class T>
-__device__ __forceinline__ void dispatch_mv(const PdgPass& p, int mv, int bid, double* sm) {
-  switch (mv) {
-    case MV_ADV: pass_body<NP, MV_ADV, T>(p, bid, sm); break;
-    case MV_SW: pass_body<NP, MV_SW, T>(p, bid, sm); break;
-    case MV_EU2: pass_body<NP, MV_EU2, T>(p, bid, sm); break;
-    case MV_EU3: pass_body<NP, MV_EU3, T>(p, bid, sm); break;
-    case MV_EU1: pass_body<NP, MV_EU1, T>(p, bid, sm); break;
-    default: pass_body<NP, MV_NONE, T>(p, bid, sm); break;
-  }
-}
-
-template <class T>
+template <int NP, int MV, class T>
 __global__ void __launch_bounds__(kBatchThreads)
     batch_kernel(const PdgPass* __restrict__ descs, const int* __restrict__ ent_desc,
                  const long long* __restrict__ ent_start, int nent, long long total,
@@ -65,44 +53,57 @@ __global__ void __launch_bounds__(kBatchThreads)
       loaded = di;
       __syncthreads();
     }
-    const int np = sp->npl / sp->ncell;
-    const int mv = sp->mv;
-    switch (np) {
-      case 2: dispatch_mv<2, T>(*sp, mv, bid, carry); break;
-      case 3: dispatch_mv<3, T>(*sp, mv, bid, carry); break;
-      case 4: dispatch_mv<4, T>(*sp, mv, bid, carry); break;
-      case 5: dispatch_mv<5, T>(*sp, mv, bid, carry); break;
-      default: break;
-    }
+    pass_body<NP, MV, T>(*sp, bid, carry);
     __syncthreads();  // s_item / s_desc / descriptor are rewritten by the next item
   }
 }
 
-template <class T>
-int batch_grid_t(size_t smem, int* grid) {
-  int dev = 0, sms = 0, per = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return (int)e;
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return (int)e;
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// Host side: the kernel of one (degree NP, model variant MV) and its persistent grid.
+template <int NP, int MV, class T>
+int launch_variant(const PdgPass* d_descs, const int* d_ent_desc, const long long* d_ent_start, int nent,
+                   long long total, unsigned long long* d_counter, size_t smem, cudaStream_t st) {
+  static int grid = 0;  // blocks per SM x SMs, computed once per process and variant
+  auto kern = batch_kernel<NP, MV, T>;
+  if (grid == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && smem > 48 * 1024)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kBatchThreads, smem);
     if (e != cudaSuccess) return (int)e;
+    grid = sms * (per < 1 ? 1 : per);
   }
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<T>, kBatchThreads, smem);
-  if (e != cudaSuccess) return (int)e;
-  if (per < 1) per = 1;
-  *grid = sms * per;
-  return 0;
+  kern<<<grid, kBatchThreads, smem, st>>>(d_descs, d_ent_desc, d_ent_start, nent, total, d_counter);
+  return (int)cudaGetLastError();
+}
+
+template <int NP, class T>
+int launch_np(int mv, const PdgPass* a, const int* b, const long long* c, int n, long long t,
+              unsigned long long* k, size_t smem, cudaStream_t st) {
+  switch (mv) {
+    case MV_ADV: return launch_variant<NP, MV_ADV, T>(a, b, c, n, t, k, smem, st);
+    case MV_SW: return launch_variant<NP, MV_SW, T>(a, b, c, n, t, k, smem, st);
+    case MV_EU1: return launch_variant<NP, MV_EU1, T>(a, b, c, n, t, k, smem, st);
+    case MV_EU2: return launch_variant<NP, MV_EU2, T>(a, b, c, n, t, k, smem, st);
+    case MV_EU3: return launch_variant<NP, MV_EU3, T>(a, b, c, n, t, k, smem, st);
+    case MV_NONE: return launch_variant<NP, MV_NONE, T>(a, b, c, n, t, k, smem, st);
+  }
+  return (int)cudaErrorInvalidValue;
 }
 
 template <class T>
-int launch_batch_t(const PdgPass* d_descs, const int* d_ent_desc, const long long* d_ent_start, int nent,
-                   long long total, unsigned long long* d_counter, int grid, size_t smem, void* stream) {
+int launch_batch_t(int np, int mv, const PdgPass* d_descs, const int* d_ent_desc, const long long* d_ent_start,
+                   int nent, long long total, unsigned long long* d_counter, size_t smem, void* stream) {
   if (nent <= 0 || total <= 0) return 0;
-  batch_kernel<T><<<grid, kBatchThreads, smem, (cudaStream_t)stream>>>(d_descs, d_ent_desc, d_ent_start, nent,
-                                                                        total, d_counter);
-  return (int)cudaGetLastError();
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (np) {
+    case 2: return launch_np<2, T>(mv, d_descs, d_ent_desc, d_ent_start, nent, total, d_counter, smem, st);
+    case 3: return launch_np<3, T>(mv, d_descs, d_ent_desc, d_ent_start, nent, total, d_counter, smem, st);
+    case 4: return launch_np<4, T>(mv, d_descs, d_ent_desc, d_ent_start, nent, total, d_counter, smem, st);
+    case 5: return launch_np<5, T>(mv, d_descs, d_ent_desc, d_ent_start, nent, total, d_counter, smem, st);
+  }
+  return (int)cudaErrorInvalidValue;
 }
 
 }  // namespace pdgdev

@@ -181,7 +181,7 @@ int pdg_model_variant(const PdgModel& m);
 // ---- batched persistent kernel (pdg_batch.cu) ----
 int pdg_batch_threads();
 size_t pdg_batch_smem(int max_carry_doubles);
-int pdg_batch_grid(size_t smem, int prec, int* grid);
+// One persistent launch over the entries of one (precision, degree NP, model variant) group.
 int pdg_launch_batch(const PdgPass* d_descs, const int* d_ent_desc, const long long* d_ent_start, int nent,
-                     long long total, unsigned long long* d_counter, int grid, size_t smem, int prec,
+                     long long total, unsigned long long* d_counter, size_t smem, int prec, int np, int mv,
                      void* stream);
