@@ -235,27 +235,46 @@ def bench_batched(args):
     K = args.steps if args.steps is not None else 20
     insts = W.batched_instances()
     stream = torch.cuda.Stream()
-    sol = []
-    for c in insts:
-        sv = pdg.solver_for(c, stream=stream.cuda_stream)
-        w0 = W.initial_w(c, [sv.points(a) for a in range(c.dim)])
-        sv.set_w(np.ascontiguousarray(w0.reshape(-1)))
-        sol.append(sv)
     dts = [c.dt for c in insts]
     dofs = sum(c.dofs for c in insts)
-    b = pdg.Batch(sol, stream=stream.cuda_stream)
-    t0 = time.perf_counter()
-    if not args.no_autotune:
-        b.autotune(dts, reps=2)
-    tune_s = time.perf_counter() - t0
-    b.step(dts, K, use_graph=True)          # warm-up (captures the graph)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(str(torch.cuda.get_device_properties(0).uuid))
-    sampler.start()
-    time.sleep(0.4)
-    b.step(dts, K, use_graph=True)          # timed: graph replay
-    ms, launches = b.elapsed()
-    clocks = sampler.stop()
+    w0s = []
+
+    def make(precision):
+        sol = []
+        for i, c in enumerate(insts):
+            sv = pdg.solver_for(c, stream=stream.cuda_stream, precision=precision)
+            if len(w0s) <= i:
+                w0s.append(np.ascontiguousarray(W.initial_w(c, [sv.points(a) for a in range(c.dim)]).reshape(-1)))
+            sv.set_w(w0s[i])
+            sol.append(sv)
+        return sol, pdg.Batch(sol, stream=stream.cuda_stream)
+
+    def timed(b, with_clocks):
+        t0 = time.perf_counter()
+        if not args.no_autotune:
+            b.autotune(dts, reps=2)
+        tune = time.perf_counter() - t0
+        b.step(dts, K, use_graph=True)          # warm-up (captures the graph)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(str(torch.cuda.get_device_properties(0).uuid)) if with_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.4)
+        b.step(dts, K, use_graph=True)          # timed: graph replay
+        ms, launches = b.elapsed()
+        return ms, launches, tune, (sampler.stop() if sampler else None)
+
+    # mixed-precision variant first (double-float state and arithmetic), then FP64
+    sol_d, b_d = make("df32")
+    ms_d, _, _, _ = timed(b_d, False)
+    w_d = [sv.get_w() for sv in sol_d[:16]]
+    b_d.close()
+    for sv in sol_d:
+        sv.close()
+    sol, b = make("fp64")
+    ms, launches, tune_s, clocks = timed(b, True)
+    err_d = float(np.sqrt(sum(np.sum((sv.get_w() - wd) ** 2) for sv, wd in zip(sol[:16], w_d))
+                          / sum(np.sum(sv.get_w() ** 2) for sv in sol[:16])))
     # same instances one after the other through pdg_step (heuristic shapes, no graph)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -283,7 +302,10 @@ def bench_batched(args):
             "gpu_launches": launches, "clocks": clocks,
             "serial": {"value": dofs * K / (ms_serial * 1e-3), "ms": ms_serial,
                        "note": "same instances, pdg_step one after the other, heuristic shapes"},
-            "speedup_vs_serial": ms_serial / ms, "state_finite": finite}
+            "speedup_vs_serial": ms_serial / ms, "state_finite": finite,
+            "mixed": {"precision": "df32", "value": dofs * K / (ms_d * 1e-3), "speedup_vs_fp64": ms / ms_d,
+                      "rel_l2_w_vs_fp64": err_d, "note": "same batch, double-float state and arithmetic; error over "
+                                                         "the first 16 instances after the 2 x K steps"}}
     print(json.dumps(line), flush=True)
 
 
