@@ -86,6 +86,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=20)
     ap.add_argument("--no-mixed", action="store_true", help="skip the double-float measurement")
+    ap.add_argument("--shapes", default=None,
+                    help="fixed launch shapes 'lpb,nseg,ngroup/lpb,nseg,ngroup' for the transport and "
+                         "last-axis passes instead of autotuning (reproduces a timed configuration)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df32"],
                     help="precision of the headline run (profiling of the double-float kernels)")
     return ap.parse_args()
@@ -468,7 +471,10 @@ def main():
         """W untimed steps, then K steps between CUDA events on the context stream, with
         per-kernel event timing and clock sampling inside the timed region."""
         sv.set_w(w0_dev)
-        if not args.no_autotune:
+        if args.shapes:
+            for kind, sh in enumerate(args.shapes.split("/")):
+                sv.set_launch(kind, *[int(x) for x in sh.split(",")])
+        elif not args.no_autotune:
             sv.autotune(cfg.dt, reps=3)     # launch shapes picked on a scratch copy (untimed)
         sv.step(cfg.dt, args.warmup)
         sv.synchronize()
@@ -596,7 +602,8 @@ def main():
                               if cfg.dofs * 8 > 126e6 else
                               f"state {cfg.dofs * 8 / 1e6:.1f} MB fits in L2: L2-resident (small parity workload)"),
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
-                       "launch_shapes": {"autotuned": not args.no_autotune, "transport_pass": list(shape0),
+                       "launch_shapes": {"autotuned": not args.no_autotune and not args.shapes,
+                                         "transport_pass": list(shape0),
                                          "last_axis_pass": list(shape1)}},
             "gpu_launches": int(sum(launches)), "roofline": roof, "clocks": clocks,
             "e2e": e2e, "cpu_baseline": cpu, "mixed": mixed, "state_finite": finite}
