@@ -81,7 +81,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--impl", default="pdg", choices=["pdg", "reference"])
-    ap.add_argument("--scheme", default="M2", choices=["M2", "M2_collapsed"])
+    ap.add_argument("--scheme", default="M2", choices=["M2", "M2_collapsed", "M2_kin"])
+    ap.add_argument("--inflow-x", action="store_true",
+                    help="x axis with inflow boundaries (f^b = f^eq of the initial state at the faces)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=20)
@@ -451,11 +453,29 @@ def main():
     from paper_1702_00169_gb300 import pdg
 
     stream = torch.cuda.Stream()
-    s = pdg.solver_for(cfg, scheme=args.scheme, stream=stream.cuda_stream, precision=args.precision)
+    periodic = [True] * cfg.dim
+    if args.inflow_x:
+        periodic[0] = False
+
+    def solver(precision):
+        sv = pdg.Solver(cfg.dim, cfg.n_macro, cfg.n_sub, cfg.order, lengths=cfg.lengths[:cfg.dim],
+                        stream=stream.cuda_stream, periodic=periodic)
+        sv.set_model(cfg.kind, cfg.lam, a=cfg.a, gravity=cfg.gravity, gamma=cfg.gamma, omega=cfg.omega,
+                     theta=cfg.theta, scheme=args.scheme, precision=pdg.PRECISION[precision])
+        return sv
+
+    s = solver(args.precision)
     info = s.info()
     coords = [s.points(a) for a in range(cfg.dim)]
     w0 = np.ascontiguousarray(W.initial_w(cfg, coords).reshape(-1))
     w0_dev = torch.from_numpy(w0).cuda()
+    fb = None
+    if args.inflow_x:
+        # inflow data: the initial equilibrium populations at the two x faces
+        s.set_w(w0_dev)
+        f0 = s.get_f().reshape((cfg.m, 2 * cfg.dim) + tuple(reversed(cfg.npoints_axis)))
+        fb = np.ascontiguousarray(np.stack([f0[:, 0, ..., 0].reshape(cfg.m, -1),
+                                            f0[:, 1, ..., -1].reshape(cfg.m, -1)]))
     torch.cuda.synchronize()
     dev_uuid = None
     try:
@@ -471,6 +491,8 @@ def main():
         """W untimed steps, then K steps between CUDA events on the context stream, with
         per-kernel event timing and clock sampling inside the timed region."""
         sv.set_w(w0_dev)
+        if fb is not None:
+            sv.set_inflow(0, fb)
         if args.shapes:
             for kind, sh in enumerate(args.shapes.split("/")):
                 sv.set_launch(kind, *[int(x) for x in sh.split(",")])
@@ -509,7 +531,7 @@ def main():
     # ---- the same run in double-float precision (FP32-pair state and arithmetic) ----
     mixed = None
     if not args.no_mixed and args.precision == "fp64":
-        sd = pdg.solver_for(cfg, scheme=args.scheme, stream=stream.cuda_stream, precision="df32")
+        sd = solver("df32")
         ms_d, launches_d, kms_d, clocks_d, w_end_d = timed_run(sd)
         sd.close()
         k_d = int(np.argmax(kms_d[:2]))
@@ -529,8 +551,10 @@ def main():
     if not args.no_e2e:
         w_host = torch.from_numpy(w0).pin_memory()
         w_out = torch.empty_like(w_host).pin_memory()
-        s2 = pdg.solver_for(cfg, scheme=args.scheme, stream=stream.cuda_stream)
+        s2 = solver("fp64")
         s2.set_w(w_host)
+        if fb is not None:
+            s2.set_inflow(0, fb)
         s2.step(cfg.dt, 2)
         s2.get_w(w_out)
         barrier()
@@ -597,6 +621,8 @@ def main():
                        "mesh": (f"{'x'.join(map(str, cfg.n_macro))} macrocells x {'x'.join(map(str, cfg.n_sub))} "
                                 f"subcells, d={cfg.order}, {'x'.join(map(str, cfg.npoints_axis))} GL points, periodic"),
                        "dof": dofs, "scheme": args.scheme, "theta": cfg.theta, "omega": cfg.omega,
+                       "boundaries": "x: inflow (f^b = initial equilibrium), others periodic" if args.inflow_x
+                       else "periodic",
                        "dt": cfg.dt, "lambda": cfg.lam, "precision": args.precision.upper(),
                        "l2": (f"state {cfg.dofs * 8 / 1e6:.0f} MB > 126 MB L2: inputs larger than L2, no flush"
                               if cfg.dofs * 8 > 126e6 else

@@ -16,6 +16,10 @@
 
 namespace pdgdev {
 
+#ifndef PDG_PREFETCH_DIST
+#define PDG_PREFETCH_DIST 2   // cells ahead prefetched into L2 on strided sweeps
+#endif
+
 enum { MV_ADV = 0, MV_SW = 1, MV_EU1 = 2, MV_EU2 = 3, MV_EU3 = 4, MV_NONE = 5 };
 
 // ---------------------------------------------------------------------------
@@ -359,6 +363,14 @@ __device__ __forceinline__ void store_cell(double* lp, long long dstep, int c, c
   for (int j = 0; j < NP; ++j) st(p0 + j * dstep, v[j]);
 }
 
+// L2 prefetch of the NP values of cell c (strided lines: no register is spent on it).
+template <int NP>
+__device__ __forceinline__ void prefetch_cell(const double* lp, long long dstep, int c) {
+  const double* p0 = lp + (long long)c * NP * dstep;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + j * dstep));
+}
+
 template <int NP, class T>
 __device__ __forceinline__ void load_row(const PdgCoef& C, int r, T* row) {
 #pragma unroll
@@ -420,6 +432,7 @@ __device__ __forceinline__ void phase_sweep(double* lp, long long dstep, int c0,
     return;
   }
   for (int c = c0; c < c1; ++c) {
+    if (c + PDG_PREFETCH_DIST < c1) prefetch_cell<NP>(lp, dstep, c + PDG_PREFETCH_DIST);
     T v[NP];
     load_cell<NP, T>(lp, dstep, c, v);
     const T z = fma(za, x, zb * u);
