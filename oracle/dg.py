@@ -168,10 +168,12 @@ def assemble_transport(mesh, v, with_boundary=False):
                     if not inside.all():             # fictitious cell: f_R = f^b at the face point
                         brows.append(row[~inside])
                         bvals.append(np.full(int((~inside).sum()), coef))
+    N = mesh.npoints
+    if not rows:                                   # v = 0: every term of eq. (3.7) vanishes
+        rows, cols, vals = [np.zeros(0, dtype=np.int64)], [np.zeros(0, dtype=np.int64)], [np.zeros(0)]
     rows = np.concatenate(rows)
     cols = np.concatenate(cols)
     vals = np.concatenate(vals)
-    N = mesh.npoints
     L = sp.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
     if not with_boundary:
         return L

@@ -19,7 +19,7 @@ population is transported again.
 import numpy as np
 
 from .dg import CartesianMesh
-from .transport import DirectTransport, bloch_transport
+from .transport import DirectTransport, bloch_transport, bloch_transport_2d
 
 
 def collision(f, model, omega):
@@ -32,7 +32,9 @@ class Transporter:
     """Applies T_theta(delta) to every population (each along its velocity).
 
     method = "direct": sparse LU of the assembled eq. (3.7) system (tiny meshes);
-    method = "bloch":  per-line Fourier closed form (any size).
+    method = "bloch":  Fourier closed form (any size): per line for axis-aligned
+                       velocities, per 2-D mode for the diagonal D2Q9 velocities;
+                       the rest velocity of D2Q9 is not transported.
     """
 
     def __init__(self, mesh, model, theta=0.5, method="direct", fb=None):
@@ -54,9 +56,17 @@ class Transporter:
         if self.method == "direct":
             return self._direct(i, delta)(g, fb)
         assert all(self.mesh.periodic), "the Bloch solver is periodic only"
-        a, sign = i // 2, (+1 if i % 2 == 0 else -1)
-        nu = 2.0 * self.model.lam * delta / self.mesh.h[a]
-        return bloch_transport(g, self.mesh.axis_np(a), sign, self.mesh.d, nu, self.theta)
+        v = self.model.velocities()[i]
+        nz = np.flatnonzero(v)
+        if nz.size == 0:
+            return np.array(g, dtype=np.float64, copy=True)
+        if nz.size == 1:
+            a = int(nz[0])
+            nu = 2.0 * abs(v[a]) * delta / self.mesh.h[a]
+            return bloch_transport(g, self.mesh.axis_np(a), 1 if v[a] > 0 else -1, self.mesh.d, nu,
+                                   self.theta)
+        assert self.mesh.dim == 2
+        return bloch_transport_2d(g, v, self.mesh.h, self.mesh.d, delta, self.theta)
 
     def __call__(self, f, delta):
         out = np.empty_like(f)

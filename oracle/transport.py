@@ -95,3 +95,57 @@ def bloch_transport(field, axis_np, sign, d, nu, theta=0.5):
     if sign < 0:
         fnew = fnew[..., ::-1]
     return np.ascontiguousarray(np.moveaxis(fnew, -1, axis_np))
+
+
+def bloch_transport_2d(field, v, h, d, delta, theta=0.5):
+    """Solve (*) on a periodic 2-D mesh for ANY constant velocity v = (v_x, v_y) by
+    2-D Fourier modes over the cells (field shape (P_y, P_x), x last; h = (h_x, h_y)).
+
+    On a Cartesian cell the terms of eq. (3.7) split by axis: the x part of the volume
+    term involves Dm along x only, the faces normal to x carry (v_x n_x)^+- only, and the
+    GL weight of the other direction cancels against omega_{L,i}.  Hence
+    L_h = v_x-line operator (acting along every row of nodes) + v_y-line operator
+    (along every column), each the 1-D reduction of ``bloch_transport``.  For the mode
+    exp(i (kappa_x c_x + kappa_y c_y)), in the traversal orientation of each axis
+    (negative components mirror that axis),
+      K2 = nu_x (I (x) K_x(kappa_x)) + nu_y (K_y(kappa_y) (x) I),
+      K_a(kappa) = K - w0^{-1} e^{-i kappa} e_0 e_d^T,  nu_a = 2 |v_a| delta / h_a,
+    on the node vector p = i_y n + i_x, and [I + theta K2] f^new = [I - (1-theta) K2] f^old.
+    A zero component drops its term; v = 0 is the identity.
+    """
+    n = d + 1
+    K, w = line_K(d)
+    f = np.asarray(field, dtype=np.float64)
+    if v[0] < 0:
+        f = f[:, ::-1]
+    if v[1] < 0:
+        f = f[::-1, :]
+    Py, Px = f.shape
+    Ny, Nx = Py // n, Px // n
+    assert Ny * n == Py and Nx * n == Px
+    nux = 2.0 * abs(v[0]) * delta / h[0]
+    nuy = 2.0 * abs(v[1]) * delta / h[1]
+    fc = f.reshape(Ny, n, Nx, n).transpose(0, 2, 1, 3).reshape(Ny, Nx, n * n)
+    Fh = np.fft.fft2(fc, axes=(0, 1))
+    e0ed = np.zeros((n, n))
+    e0ed[0, n - 1] = 1.0 / w[0]
+    I = np.eye(n)
+    kx = 2.0 * np.pi * np.arange(Nx) / Nx
+    ky = 2.0 * np.pi * np.arange(Ny) / Ny
+    Kx = K[None] - np.exp(-1j * kx)[:, None, None] * e0ed[None]            # (Nx, n, n)
+    Ky = K[None] - np.exp(-1j * ky)[:, None, None] * e0ed[None]            # (Ny, n, n)
+    out = np.empty_like(Fh)
+    Inn = np.eye(n * n)
+    for jy in range(Ny):
+        K2 = (nux * np.einsum("ab,mij->maibj", I, Kx).reshape(Nx, n * n, n * n)
+              + nuy * np.kron(Ky[jy], I)[None])
+        A = Inn[None] + theta * K2
+        B = Inn[None] - (1.0 - theta) * K2
+        out[jy] = np.linalg.solve(A, np.einsum("mpq,mq->mp", B, Fh[jy])[..., None])[..., 0]
+    fn = np.real(np.fft.ifft2(out, axes=(0, 1)))
+    fn = fn.reshape(Ny, Nx, n, n).transpose(0, 2, 1, 3).reshape(Py, Px)
+    if v[1] < 0:
+        fn = fn[::-1, :]
+    if v[0] < 0:
+        fn = fn[:, ::-1]
+    return np.ascontiguousarray(fn)
