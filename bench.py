@@ -55,9 +55,21 @@ def collision_flops_sw():
     return 9 + 1 + 2 + 2 + 6 + 3 + 4 * 12 + 9  # = 80
 
 
+def diag_flops_per_dof(n):
+    """D2Q9 diagonal transport, per DOF (n^2 nodes per cell): the dense Binv row (n^2 FMA),
+    r = f/theta (1 mul), the -c1 f term (1 FMA), the face injections and the two
+    published faces (4n FMA per cell)."""
+    return 2.0 * n * n + 1.0 + 2.0 + 8.0 / n
+
+
 def collision_flops(kind, dim):
     """Algorithmic flops of the collision at one point (FMA = 2)."""
     nv = 2 * dim
+    if kind == "isothermal_d2q9":
+        # rho, j_x, j_y (18 adds); 1/rho; s_x, s_y (4 mul); |s|^2/6 and base (4); the four
+        # quadratic bases (4 x 3); s_x + s_y, s_y - s_x (2); nine e_i (8 adds); W_i rho (3 mul);
+        # relaxation (9 x 3)
+        return 18 + 1 + 4 + 4 + 12 + 2 + 8 + 3 + 27
     if kind == "shallow_water":
         return collision_flops_sw()
     if kind == "advection":
@@ -72,7 +84,7 @@ def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--workload", default="shallow_water",
-                    choices=["shallow_water", "advection", "euler", "batched", "serving"])
+                    choices=["shallow_water", "advection", "euler", "d2q9", "batched", "serving"])
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=64.0)
@@ -185,9 +197,12 @@ import numpy as np
 from paper_1702_00169_gb300 import workloads as W
 from oracle import models as OM, scheme as OS
 from oracle.dg import CartesianMesh
-cfg = W.CONFIGS[{cfg_name!r}].scaled(n_macro=(8, 8))
-mesh = CartesianMesh(cfg.dim, cfg.ncells, cfg.order)
-model = OM.Model(OM.SHALLOW_WATER, cfg.dim, cfg.lam, gravity=cfg.gravity)
+cfg = W.CONFIGS[{cfg_name!r}]
+cfg = cfg.scaled(n_macro=tuple(min(8, x) for x in cfg.n_macro))
+mesh = CartesianMesh(cfg.dim, cfg.ncells, cfg.order, lengths=cfg.lengths[:cfg.dim])
+kind = {{"advection": OM.ADVECTION, "shallow_water": OM.SHALLOW_WATER, "euler": OM.EULER,
+        "isothermal_d2q9": OM.ISOTHERMAL_D2Q9}}[cfg.kind]
+model = OM.Model(kind, cfg.dim, cfg.lam, a=cfg.a[:cfg.dim], gravity=cfg.gravity, gamma=cfg.gamma)
 w0 = W.initial_w(cfg, [mesh.coords1d(a) for a in range(cfg.dim)])
 tr = OS.Transporter(mesh, model, theta=cfg.theta, method="bloch")
 f = OS.initial_state(model, w0)
@@ -198,7 +213,8 @@ for _ in range({sample_steps}):
     f = OS.m2_step(f, tr, model, cfg.dt, cfg.omega)
 el = time.perf_counter() - t0
 print(json.dumps({{"value": cfg.dofs * {sample_steps} / el, "dofs": cfg.dofs, "steps": {sample_steps},
-                  "seconds": el, "mesh": "%dx%d macrocells x 8x8 subcells, d=3" % cfg.n_macro}}))
+                  "seconds": el, "mesh": "%s macrocells x %s subcells, d=%d" % (
+                      "x".join(map(str, cfg.n_macro)), "x".join(map(str, cfg.n_sub)), cfg.order)}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -424,7 +440,9 @@ def bench_serving(args):
 def main():
     args = parse_args()
     from paper_1702_00169_gb300 import workloads as W
-    cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6}.get(args.workload, W.SW_D2Q4)
+    cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6, "d2q9": W.D2Q9_ISO}.get(args.workload, W.SW_D2Q4)
+    if args.inflow_x and cfg.kind == "isothermal_d2q9":
+        raise SystemExit("--inflow-x: the D2Q9 path runs on periodic meshes only")
     if args.impl == "reference":
         if args.steps is None:
             args.steps = 20
@@ -439,9 +457,9 @@ def main():
         bench_serving(args)
         return
     if args.steps is None:
-        args.steps = {"euler": 20, "advection": 1000}.get(args.workload, 1000)
+        args.steps = {"euler": 20, "advection": 1000, "d2q9": 100}.get(args.workload, 1000)
     if args.warmup is None:
-        args.warmup = {"euler": 3}.get(args.workload, 20)
+        args.warmup = {"euler": 3, "d2q9": 5}.get(args.workload, 20)
 
     import torch
     ws, rank, local = dist_env()
@@ -519,6 +537,24 @@ def main():
         sv.timing_enable(False)
         return ev0.elapsed_time(ev1), launches, kms, clk, sv.get_w()
 
+    n = cfg.order + 1
+    P = info.npoints
+    F = info.nfields
+    q9 = cfg.kind == "isothermal_d2q9"
+    pops_line = 2 if q9 else F // cfg.dim     # populations transported by one line pass
+
+    def dominant(kms):
+        """Kernel kind with the largest share of the timed region (0, 1 or 3)."""
+        return max((0, 1, 3), key=lambda k: kms[k])
+
+    def kernel_work(kind):
+        """(algorithmic bytes, algorithmic flops) of one launch of a kernel kind."""
+        if kind == 3:
+            return 16.0 * 4 * P, 4 * P * diag_flops_per_dof(n)
+        if kind == 1:
+            return 16.0 * F * P, 2 * pops_line * P * transport_flops_per_dof(n) + P * collision_flops(cfg.kind, cfg.dim)
+        return 16.0 * pops_line * P, 2 * pops_line * P * transport_flops_per_dof(n)
+
     # ---- device-resident run (FP64) ----
     ms, launches, kms, clocks, w_end = timed_run(s)
     shape0, shape1 = s.get_launch(0), s.get_launch(1)
@@ -534,9 +570,9 @@ def main():
         sd = solver("df32")
         ms_d, launches_d, kms_d, clocks_d, w_end_d = timed_run(sd)
         sd.close()
-        k_d = int(np.argmax(kms_d[:2]))
+        k_d = dominant(kms_d)
         avg_d = kms_d[k_d] / max(1, launches_d[k_d])
-        bytes_d = 16.0 * info.nfields * info.npoints if k_d == 1 else 16.0 * info.nfields * info.npoints / cfg.dim
+        bytes_d = kernel_work(k_d)[0]
         mixed = {"precision": "df32 (FP32-pair state and double-word arithmetic on the FP32 pipes)",
                  "value": aggregate_ranks(ms_d, dofs * args.steps)[1] / (aggregate_ranks(ms_d, 0)[0] * 1e-3),
                  "ms_per_step": ms_d / args.steps,
@@ -578,19 +614,12 @@ def main():
         return
 
     # ---- roofline of the dominant kernel (from the live CUDA-event timing) ----
-    n = cfg.order + 1
-    P = info.npoints
-    F = info.nfields
     kinds = {0: "transport pass (composed T T on the populations of the other axes)",
-             1: "last-axis pass (T, collision, T)"}
-    k_dom = int(np.argmax(kms[:2]))
+             1: "last-axis pass (T, collision, T)",
+             3: "D2Q9 diagonal transport pass (4 populations, tiled 2-D wavefront)"}
+    k_dom = dominant(kms)
     avg_ms = kms[k_dom] / max(1, launches[k_dom])
-    if k_dom == 1:
-        bytes_launch = 16.0 * F * P
-        flops_launch = 2 * (F // cfg.dim) * P * transport_flops_per_dof(n) + P * collision_flops(cfg.kind, cfg.dim)
-    else:
-        bytes_launch = 16.0 * (F // cfg.dim) * P
-        flops_launch = 2 * (F // cfg.dim) * P * transport_flops_per_dof(n)
+    bytes_launch, flops_launch = kernel_work(k_dom)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -617,7 +646,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg.name,
-                       "model": f"{cfg.kind} via vectorial D{cfg.dim}Q{2 * cfg.dim} ({cfg.nfields} populations)",
+                       "model": ("isothermal Euler via D2Q9 (9 populations, 4 diagonal)" if q9 else
+                                 f"{cfg.kind} via vectorial D{cfg.dim}Q{2 * cfg.dim} ({cfg.nfields} populations)"),
                        "mesh": (f"{'x'.join(map(str, cfg.n_macro))} macrocells x {'x'.join(map(str, cfg.n_sub))} "
                                 f"subcells, d={cfg.order}, {'x'.join(map(str, cfg.npoints_axis))} GL points, periodic"),
                        "dof": dofs, "scheme": args.scheme, "theta": cfg.theta, "omega": cfg.omega,

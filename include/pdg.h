@@ -29,7 +29,10 @@
  *   one scalar field:          [P_z][P_y][P_x]  (x fastest; absent axes have P = 1);
  *   macroscopic state w:       [m][P_z][P_y][P_x];
  *   kinetic state f:           [m][2D][P_z][P_y][P_x], population i in the order
- *                              +x, -x, +y, -y, +z, -z.
+ *                              +x, -x, +y, -y, +z, -z;
+ *                              D2Q9 (PDG_MODEL_ISOTHERMAL_D2Q9): [9][P_y][P_x] in the
+ *                              velocity order of Section 5.1, lambda (0,0), (1,0), (0,1),
+ *                              (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
  */
 #ifndef PDG_H
 #define PDG_H
@@ -53,11 +56,21 @@ enum {
   PDG_ERR_UNSUPPORTED = -6  /* valid request that this build does not implement */
 };
 
-/* Kinetic model kinds (vectorial DnQ2n: each conserved variable has 2D populations). */
+/* Kinetic model kinds.  0-2: vectorial DnQ2n, each conserved variable has 2D
+ * populations.  3: the D2Q9 lattice of Section 5.1 (Euler with gravity), one set of
+ * nine populations for the isothermal Euler variables. */
 enum {
   PDG_MODEL_ADVECTION = 0,     /* m = 1, flux q^a = a_a w                          */
   PDG_MODEL_SHALLOW_WATER = 1, /* D = 2, m = 3, w = (h, hu, hv), gravity g          */
-  PDG_MODEL_EULER = 2          /* D = 2 or 3, m = D + 2, w = (rho, rho u, E), gamma */
+  PDG_MODEL_EULER = 2,         /* D = 2 or 3, m = D + 2, w = (rho, rho u, E), gamma */
+  PDG_MODEL_ISOTHERMAL_D2Q9 = 3 /* D = 2, m = 3, w = (rho, rho u_x, rho u_y), nine
+                                  velocities lambda xi_i (xi in {-1,0,1}^2), equilibrium
+                                  f_i = W_i rho (1 + u.v_i/c^2 + (u.v_i)^2/(2c^4)
+                                  - u.u/(2c^2)), c = lambda/sqrt(3), W = 4/9, 1/9, 1/36
+                                  (Section 5.1).  The four diagonal velocities couple each
+                                  cell to two upwind faces: their transport is the 2-D
+                                  recurrence of pdg_step's documentation.  Periodic meshes
+                                  only; 0 < theta <= 1; dt > 0. */
 };
 
 /* Time schemes (Section 3.2 and Section 5.1). */
@@ -117,11 +130,11 @@ typedef struct pdg_info {
   int dim;            /* D */
   int order;          /* d (d+1 GL points per cell and axis) */
   int m;              /* conserved variables (0 before pdg_set_model) */
-  int nv;             /* populations per variable, 2D */
+  int nv;             /* populations per variable, 2D (D2Q9: 9 populations in all) */
   int ncell[3];       /* N_a = n_macro_a n_sub_a (1 for absent axes) */
   int npts[3];        /* P_a = N_a (d+1) (1 for absent axes) */
   long long npoints;  /* prod_a P_a */
-  long long nfields;  /* m * 2D */
+  long long nfields;  /* populations in f: m * 2D (D2Q9: 9) */
   long long w_len;    /* m * npoints: doubles in w */
   long long f_len;    /* nfields * npoints: doubles in f */
   double h[3];        /* cell edge per axis */
@@ -176,7 +189,19 @@ int pdg_set_w(pdg_ctx* ctx, const double* w, size_t len, int on_device);
  * (collapsed Strang of Section 5.1); PDG_SCHEME_M2KIN advances M2^kin steps.
  * Asynchronous on the context stream.
  * dt may be negative (time-symmetric use).  nsteps = 0 is a no-op.
- * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_CUDA.
+ * D2Q9 diagonal velocities v = lambda (s_x, s_y): on a Cartesian cell eq. (3.7) splits
+ * into one line operator per axis, and the theta step couples a cell to the NEW values
+ * on the faces of its two upwind neighbours,
+ *   f_c^new = B^-1 [f_c/theta + (nu_x/w_0) S_x Lt + (nu_y/w_0) S_y Bt] - ((1-theta)/theta) f_c,
+ *   B = I + theta (nu_x I (x) K + nu_y K (x) I),  Lt = (1-theta) L^old + theta L^new
+ * (L, B: downwind-face values of the upwind neighbours along x and y).  The periodic
+ * 2-D recurrence is solved on tiles swept as wavefronts; every tile starts W cells
+ * upwind along both axes, W chosen on the host so that the influence of the
+ * truncated start (bounded through the entrywise absolute transfer matrices of the
+ * face recurrence) is below 2^-56 of the state's magnitude.  dt must be > 0 there
+ * (PDG_ERR_UNSUPPORTED otherwise, or when no such W <= 128 exists).
+ * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_CUDA,
+ *         PDG_ERR_UNSUPPORTED.
  */
 int pdg_step(pdg_ctx* ctx, double dt, int nsteps);
 
@@ -268,6 +293,7 @@ int pdg_synchronize(pdg_ctx* ctx);
  *   kind 0 = transport pass (axes before the last; T or T T, no collision)
  *   kind 1 = last-axis pass (T, fused collision, T)
  *   kind 2 = state kernels (set_w / get_w)
+ *   kind 3 = D2Q9 diagonal transport pass
  * pdg_timing_enable(ctx, 1) resets the counters.  pdg_timing_read fills up to
  * max_kinds entries of launches[] and ms[] and synchronises the stream.
  */

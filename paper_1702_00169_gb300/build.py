@@ -1,6 +1,6 @@
 """Build libpdg.so in-tree with nvcc for sm_103a (GB300).
 
-Three translation units compiled in parallel, then linked into
+The translation units are compiled in parallel, then linked into
 ``paper_1702_00169_gb300/lib/libpdg.so``.  Host code is compiled with FP
 contraction disabled so the plan coefficients are identical on x86-64 and
 aarch64.
@@ -18,8 +18,8 @@ LIBDIR = os.path.join(PKG, "lib")
 OBJDIR = os.path.join(ROOT, "_build", "obj")
 LIB = os.path.join(LIBDIR, "libpdg.so")
 
-SOURCES = ["pdg_batch_df.cu", "pdg_batch.cu", "pdg_kernels_df.cu", "pdg_kernels.cu", "pdg_api.cu",
-           "pdg_noalloc.cu", "pdg_server.cu", "pdg_plan.cpp"]
+SOURCES = ["pdg_batch_df.cu", "pdg_batch.cu", "pdg_kernels_df.cu", "pdg_kernels.cu", "pdg_diag_df.cu",
+           "pdg_diag.cu", "pdg_api.cu", "pdg_noalloc.cu", "pdg_server.cu", "pdg_plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I", os.path.join(ROOT, "include")]

@@ -50,8 +50,8 @@ struct pdg_ctx {
   int launch[2][3] = {{0, 0, 0}, {0, 0, 0}};   // single-mesh shape overrides per pass kind
   int bshape[2][3] = {{0, 0, 0}, {0, 0, 0}};   // shapes inside batched launches (<= 256 threads)
   bool timing = false;
-  long long t_launches[3] = {0, 0, 0};
-  double t_ms[3] = {0, 0, 0};
+  long long t_launches[4] = {0, 0, 0, 0};
+  double t_ms[4] = {0, 0, 0, 0};
   std::vector<PdgTimedLaunch> pending;
   std::vector<cudaEvent_t> event_pool;
   std::string err;
@@ -231,13 +231,23 @@ int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov,
   p.npl = c->P[axis];
   p.ncell = c->N[axis];
   const int m = c->model.m, nv = c->model.nv;
-  p.ntf = 2 * m;
-  for (int k = 0; k < m; ++k) {
-    p.tfield[2 * k] = k * nv + 2 * axis;
-    p.tdir[2 * k] = +1;
-    p.tfield[2 * k + 1] = k * nv + 2 * axis + 1;
-    p.tdir[2 * k + 1] = -1;
+  if (c->model.kind == PDG_MODEL_ISOTHERMAL_D2Q9) {
+    // populations 1 + axis (+lambda e_axis) and 3 + axis (-lambda e_axis)
+    p.ntf = 2;
+    p.tfield[0] = 1 + axis;
+    p.tdir[0] = +1;
+    p.tfield[1] = 3 + axis;
+    p.tdir[1] = -1;
+  } else {
+    p.ntf = 2 * m;
+    for (int k = 0; k < m; ++k) {
+      p.tfield[2 * k] = k * nv + 2 * axis;
+      p.tdir[2 * k] = +1;
+      p.tfield[2 * k + 1] = k * nv + 2 * axis + 1;
+      p.tdir[2 * k + 1] = -1;
+    }
   }
+  p.dslot = sp.dslot;
   p.nops = sp.nops;
   for (int o = 0; o < sp.nops; ++o) {
     p.op[o] = sp.op[o];
@@ -299,7 +309,84 @@ int launch_timed(pdg_ctx* c, const PdgPass& p, int kind) {
   return PDG_OK;
 }
 
+// Launch descriptor of a D2Q9 diagonal pass (populations 5-8, slots dslot_in.. -> the
+// other slot set).  The tile counts minimise the swept region of one block (output
+// cells plus the upwind start) times the number of blocks per SM.
+int make_diag(pdg_ctx* c, const PdgPassSpec& sp, PdgDiagPass* out) {
+  PdgDiagPass& p = *out;
+  std::memset(&p, 0, sizeof(p));
+  const double nux = 2.0 * c->model.lambda * sp.ddelta / c->h[0];
+  const double nuy = 2.0 * c->model.lambda * sp.ddelta / c->h[1];
+  if (pdg_plan_diag(c->order, nux, nuy, c->theta, &p.c))
+    return fail(c, PDG_ERR_UNSUPPORTED,
+                "diagonal transport: no truncation width <= 128 cells for this time step (dt must be > 0)");
+  const int in = sp.dslot_in, outs = sp.dslot_in == PDG_Q9_DIAG ? PDG_Q9_SCRATCH : PDG_Q9_DIAG;
+  static const int sx[4] = {+1, -1, -1, +1}, sy[4] = {+1, +1, -1, -1};   // populations 5-8
+  p.npop = 4;
+  for (int i = 0; i < 4; ++i) {
+    p.fin[i] = c->f + (long long)(in + i) * c->npoints;
+    p.fout[i] = c->f + (long long)(outs + i) * c->npoints;
+    p.sx[i] = sx[i];
+    p.sy[i] = sy[i];
+  }
+  p.n = c->n;
+  p.ncx = c->N[0];
+  p.ncy = c->N[1];
+  p.row = c->P[0];
+  p.prec = c->model.prec;
+  const int NN = c->n * c->n;
+  p.kpar = std::max(1, 256 / NN);
+  const int slots = 152;   // one block per SM per wave (co-resident blocks share its FP64 pipe)
+  double best = 1e300;
+  for (int ntx = 1; ntx <= std::min(p.ncx, 64); ++ntx) {
+    const int tx = (p.ncx + ntx - 1) / ntx;
+    if ((long long)tx * (ntx - 1) >= p.ncx) continue;   // the last tile would be empty
+    for (int nty = 1; nty <= std::min(p.ncy, 64); ++nty) {
+      const int ty = (p.ncy + nty - 1) / nty;
+      if ((long long)ty * (nty - 1) >= p.ncy) continue;
+      const long long blocks = 4LL * ntx * nty;
+      const long long waves = (blocks + slots - 1) / slots;
+      const double cost = (double)waves * (double)(tx + p.c.wx) * (double)(ty + p.c.wy);
+      if (cost < best) {
+        best = cost;
+        p.tx = tx;
+        p.ty = ty;
+        p.ntx = ntx;
+        p.nty = nty;
+      }
+    }
+  }
+  if (pdg_diag_smem(p) > 200 * 1024) return fail(c, PDG_ERR_UNSUPPORTED, "diagonal tile too large");
+  return PDG_OK;
+}
+
+int issue_diag(pdg_ctx* c, const PdgPassSpec& sp) {
+  PdgDiagPass p;
+  if (int r = make_diag(c, sp, &p)) return r;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    e0 = get_event(c);
+    e1 = get_event(c);
+    if (!e0 || !e1) return fail(c, PDG_ERR_CUDA, "cudaEventCreate failed");
+    PDG_CUDA(c, cudaEventRecord(e0, c->stream));
+  }
+  int e = pdg_launch_diag(p, (void*)c->stream);
+  if (e != 0) return cuda_fail(c, (cudaError_t)e, "diag_kernel launch");
+  if (c->timing) {
+    PDG_CUDA(c, cudaEventRecord(e1, c->stream));
+    c->pending.push_back({3, e0, e1});
+  }
+  return PDG_OK;
+}
+
 int issue_pass(pdg_ctx* c, const PdgPassSpec& sp) {
+  if (sp.axis == -2) {
+    PDG_CUDA(c, cudaMemcpyAsync(c->f + (long long)PDG_Q9_DIAG * c->npoints,
+                                c->f + (long long)PDG_Q9_SCRATCH * c->npoints,
+                                sizeof(double) * 4 * (size_t)c->npoints, cudaMemcpyDeviceToDevice, c->stream));
+    return PDG_OK;
+  }
+  if (sp.axis < 0) return issue_diag(c, sp);
   PdgPass p;
   const int kind = pass_kind(sp);
   if (int r = make_pass(c, sp, 512, c->launch[kind], &p)) return r;
@@ -320,8 +407,8 @@ PdgPassSpec spec(int axis, int nops, const int* ops, const int* ci, const PdgCoe
   return sp;
 }
 
-// The pass list of nsteps palindromic steps (see the schedule at the top of this file).
-int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+// The line passes of nsteps palindromic steps (see the schedule at the top of this file).
+int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
   out.clear();
   if (nsteps <= 0) return PDG_OK;
   const int D = c->dim, L = D - 1;
@@ -399,9 +486,76 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
   return PDG_OK;
 }
 
+// The full pass list.  D2Q9 adds the diagonal transports: the sub-steps between two
+// collisions (and before the first / after the last) run as diagonal passes issued
+// just before the line pass that holds the next collision (transports of different
+// populations commute); each diagonal pass swaps the slot set of populations 5-8, the
+// collision reads them where they are, and a final copy returns them to slots 5-8.
+int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+  if (int r = build_line_schedule(c, dt, nsteps, out)) return r;
+  if (c->model.kind != PDG_MODEL_ISOTHERMAL_D2Q9 || nsteps <= 0) return PDG_OK;
+  if (!(dt > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 diagonal transport needs dt > 0");
+  // diagonal sub-steps of each transport segment, in order
+  std::vector<std::vector<double>> seg;
+  const double h = 0.5 * dt, q = 0.25 * dt;
+  if (c->scheme == PDG_SCHEME_M2) {
+    seg.push_back({h});
+    for (int s = 1; s < nsteps; ++s) seg.push_back({h, h});
+    seg.push_back({h});
+  } else if (c->scheme == PDG_SCHEME_M2_COLLAPSED) {
+    seg.push_back({h});
+    for (int s = 1; s < nsteps; ++s) seg.push_back({dt});
+    seg.push_back({h});
+  } else {
+    seg.push_back({q});
+    for (int s = 0; s < nsteps; ++s) {
+      seg.push_back({h});
+      if (s < nsteps - 1) seg.push_back({q, q});
+    }
+    seg.push_back({q});
+  }
+  std::vector<PdgPassSpec> res;
+  res.reserve(out.size() + 3 * seg.size() + 1);
+  int slot = PDG_Q9_DIAG;
+  size_t ci = 0;
+  auto diag = [&](double delta) {
+    PdgPassSpec d;
+    std::memset(&d, 0, sizeof(d));
+    d.axis = -1;
+    d.ddelta = delta;
+    d.dslot_in = slot;
+    res.push_back(d);
+    slot = (slot == PDG_Q9_DIAG) ? PDG_Q9_SCRATCH : PDG_Q9_DIAG;
+  };
+  for (auto sp : out) {
+    if (pass_kind(sp)) {
+      if (ci >= seg.size()) return fail(c, PDG_ERR_ARG, "internal: schedule segments");
+      for (double dl : seg[ci]) diag(dl);
+      ++ci;
+      sp.dslot = slot;
+    }
+    res.push_back(sp);
+  }
+  if (ci + 1 != seg.size()) return fail(c, PDG_ERR_ARG, "internal: schedule segments");
+  for (double dl : seg[ci]) diag(dl);
+  if (slot != PDG_Q9_DIAG) {
+    PdgPassSpec cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.axis = -2;   // copy slots 9-12 back to 5-8
+    res.push_back(cp);
+  }
+  out.swap(res);
+  return PDG_OK;
+}
+
+// State slots of the current model (D2Q9: nine populations and four scratch slots).
+long long state_slots(const pdg_ctx* c) {
+  return c->model.kind == PDG_MODEL_ISOTHERMAL_D2Q9 ? PDG_Q9_SLOTS : (long long)c->model.nf;
+}
+
 // Allocate the kinetic state for the current model if it does not fit yet.
 int ensure_state(pdg_ctx* c) {
-  const long long need = (long long)c->model.m * c->model.nv * c->npoints;
+  const long long need = state_slots(c) * c->npoints;
   if (need <= c->f_cap) return PDG_OK;
   double* nf = nullptr;
   cudaError_t e = c->async_alloc ? cudaMallocAsync((void**)&nf, sizeof(double) * (size_t)need, c->stream)
@@ -421,7 +575,7 @@ int ensure_state(pdg_ctx* c) {
   return PDG_OK;
 }
 
-size_t fields_of(const pdg_ctx* c) { return (size_t)c->model.m * c->model.nv; }
+size_t fields_of(const pdg_ctx* c) { return (size_t)c->model.nf; }
 
 // Lines of a pass along axis a (= points of the other axes).
 long long lines_of(const pdg_ctx* c, int a) { return c->npoints / c->P[a]; }
@@ -457,6 +611,7 @@ bool pdg_internal_view(const pdg_ctx* c, PdgStateView* v) {
   v->npoints = c->npoints;
   v->m = c->model.m;
   v->nv = c->model.nv;
+  v->nf = c->model.nf;
   v->prec = c->model.prec;
   v->stream = c->stream;
   return true;
@@ -540,7 +695,7 @@ int pdg_create_mesh(pdg_ctx** out, int dim, const int n_macro[3], const int n_su
 
 int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   if (!c || !d) return PDG_ERR_ARG;
-  if (d->kind < PDG_MODEL_ADVECTION || d->kind > PDG_MODEL_EULER)
+  if (d->kind < PDG_MODEL_ADVECTION || d->kind > PDG_MODEL_ISOTHERMAL_D2Q9)
     return fail(c, PDG_ERR_ARG, "unknown model kind");
   if (d->scheme != PDG_SCHEME_M2 && d->scheme != PDG_SCHEME_M2_COLLAPSED && d->scheme != PDG_SCHEME_M2KIN)
     return fail(c, PDG_ERR_ARG, "unknown scheme");
@@ -551,24 +706,30 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   if (!(d->theta >= 0.0 && d->theta <= 1.0)) return fail(c, PDG_ERR_ARG, "theta must be in [0, 1]");
   if (d->kind == PDG_MODEL_SHALLOW_WATER && c->dim != 2)
     return fail(c, PDG_ERR_UNSUPPORTED, "shallow water needs dim = 2");
+  const bool q9 = d->kind == PDG_MODEL_ISOTHERMAL_D2Q9;
+  if (q9 && c->dim != 2) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 needs dim = 2");
+  if (q9 && !(c->periodic[0] && c->periodic[1]))
+    return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 runs on periodic meshes only");
+  if (q9 && !(d->theta > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 needs theta > 0");
   PdgModel M{};
   M.kind = d->kind;
   M.dim = c->dim;
-  M.m = d->kind == PDG_MODEL_ADVECTION ? 1 : (d->kind == PDG_MODEL_SHALLOW_WATER ? 3 : c->dim + 2);
-  M.nv = 2 * c->dim;
+  M.m = d->kind == PDG_MODEL_ADVECTION ? 1 : ((d->kind == PDG_MODEL_SHALLOW_WATER || q9) ? 3 : c->dim + 2);
+  M.nv = q9 ? 9 : 2 * c->dim;
+  M.nf = q9 ? 9 : M.m * M.nv;
   M.lambda = d->lambda;
   M.omega = d->omega;
   for (int a = 0; a < 3; ++a) M.a[a] = d->a[a];
   M.gravity = d->gravity;
   M.gamma = d->gamma;
-  for (int i = 0; i < M.nv; ++i) {
+  for (int i = 0; i < M.nv && !q9; ++i) {
     const double s = (i % 2 == 0) ? 1.0 : -1.0;
     M.cadv[i] = 1.0 / (2.0 * c->dim) + s * d->a[i / 2] / (2.0 * d->lambda);
   }
   M.prec = d->precision;
   pdg_model_constants(&M);
   // a different number of fields or a different state format invalidates the state
-  if (c->has_model && (c->model.m != M.m || c->model.prec != M.prec)) {
+  if (c->has_model && (c->model.m != M.m || c->model.nf != M.nf || c->model.prec != M.prec)) {
     c->has_state = false;
     free_inflow(c);   // layout / format of the boundary data changes too (reset to zero)
   }
@@ -717,14 +878,14 @@ int pdg_get_info(const pdg_ctx* c, pdg_info* info) {
   info->dim = c->dim;
   info->order = c->order;
   info->m = c->has_model ? c->model.m : 0;
-  info->nv = 2 * c->dim;
+  info->nv = c->has_model ? c->model.nv : 2 * c->dim;
   for (int a = 0; a < 3; ++a) {
     info->ncell[a] = c->N[a];
     info->npts[a] = c->P[a];
     info->h[a] = a < c->dim ? c->h[a] : 0.0;
   }
   info->npoints = c->npoints;
-  info->nfields = (long long)info->m * info->nv;
+  info->nfields = c->has_model ? (long long)c->model.nf : 0;
   info->w_len = (long long)info->m * c->npoints;
   info->f_len = info->nfields * c->npoints;
   return PDG_OK;
@@ -757,7 +918,7 @@ int pdg_timing_enable(pdg_ctx* c, int enable) {
     if (r) return r;
   }
   c->timing = enable != 0;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     c->t_launches[k] = 0;
     c->t_ms[k] = 0.0;
   }
@@ -769,7 +930,7 @@ int pdg_timing_read(pdg_ctx* c, long long* launches, double* ms, int max_kinds) 
   PDG_CUDA(c, cudaStreamSynchronize(c->stream));
   int r = drain_timing(c);
   if (r) return r;
-  for (int k = 0; k < max_kinds && k < 3; ++k) {
+  for (int k = 0; k < max_kinds && k < 4; ++k) {
     if (launches) launches[k] = c->t_launches[k];
     if (ms) ms[k] = c->t_ms[k];
   }
@@ -871,6 +1032,7 @@ int representative_specs(pdg_ctx* c, double dt, PdgPassSpec* sp, bool* have) {
   if (int r = build_schedule(c, dt, 2, sched)) return r;
   have[0] = have[1] = false;
   for (const auto& s : sched) {
+    if (s.axis < 0) continue;   // diagonal passes and copies have no line shape
     const int k = pass_kind(s);
     // prefer the steady-state passes (T T and T C T)
     if (!have[k] || s.nops > sp[k].nops) {
@@ -892,7 +1054,7 @@ int pdg_autotune(pdg_ctx* c, double dt, int reps) {
   PdgPassSpec sp[2];
   bool have[2];
   if (int r = representative_specs(c, dt, sp, have)) return r;
-  const size_t bytes = sizeof(double) * (size_t)c->model.m * c->model.nv * c->npoints;
+  const size_t bytes = sizeof(double) * (size_t)state_slots(c) * c->npoints;
   double* scratch = nullptr;
   cudaError_t e = cudaMalloc((void**)&scratch, bytes);
   if (e != cudaSuccess) {
@@ -974,8 +1136,10 @@ int pdg_batch_create(pdg_batch** out, int n, pdg_ctx* const* ctxs, void* cuda_st
   if (!out) return PDG_ERR_ARG;
   *out = nullptr;
   if (n < 1 || !ctxs) return PDG_ERR_ARG;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (!ctxs[i] || !ctxs[i]->has_model) return PDG_ERR_STATE;
+    if (ctxs[i]->model.kind == PDG_MODEL_ISOTHERMAL_D2Q9) return PDG_ERR_UNSUPPORTED;
+  }
   pdg_batch* b = new (std::nothrow) pdg_batch();
   if (!b) return PDG_ERR_OOM;
   b->inst.assign(ctxs, ctxs + n);
@@ -1048,6 +1212,8 @@ int batch_prepare(pdg_batch* b, const double* dt, const int* nsteps) {
   for (int i = 0; i < n; ++i) {
     pdg_ctx* c = b->inst[i];
     if (!c->has_state) return bfail(b, PDG_ERR_STATE, "batch instance without state");
+    if (c->model.kind == PDG_MODEL_ISOTHERMAL_D2Q9)
+      return bfail(b, PDG_ERR_UNSUPPORTED, "D2Q9 instances run through pdg_step only");
     if (nsteps[i] < 0 || !std::isfinite(dt[i])) return bfail(b, PDG_ERR_ARG, "bad dt or nsteps");
     std::vector<PdgPassSpec> sched;
     if (int r = build_schedule(c, dt[i], nsteps[i], sched)) return bfail(b, r, c->err);

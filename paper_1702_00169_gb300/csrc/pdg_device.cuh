@@ -20,7 +20,7 @@ namespace pdgdev {
 #define PDG_PREFETCH_DIST 2   // cells ahead prefetched into L2 on strided sweeps
 #endif
 
-enum { MV_ADV = 0, MV_SW = 1, MV_EU1 = 2, MV_EU2 = 3, MV_EU3 = 4, MV_NONE = 5 };
+enum { MV_ADV = 0, MV_SW = 1, MV_EU1 = 2, MV_EU2 = 3, MV_EU3 = 4, MV_NONE = 5, MV_D2Q9 = 6 };
 
 // ---------------------------------------------------------------------------
 // Double-float arithmetic.  Error-free transformations (all with explicit
@@ -278,6 +278,51 @@ template <class T>
 struct Collide<MV_EU3, T> {
   static __device__ __forceinline__ void run(T* v, const PdgModel& M) { collide_euler<3, T>(v, M); }
 };
+// D2Q9 (Section 5.1): with j = sum_i f_i xi_i (lattice units, v_i = lambda xi_i) and
+// s = 3 j / rho = u . xi / c^2 per unit xi, the equilibrium is
+// f^eq_i = W_i rho e_i, e_i = 1 + s.xi_i + (s.xi_i)^2 / 2 - |s|^2 / 6.  v holds the nine
+// populations in the velocity order of Section 5.1; M carries omega W_i (omega = 1 gives
+// f^eq itself when 1 - omega = 0).
+template <class T>
+__device__ __forceinline__ void d2q9_relax(T* v, T rho, T jx, T jy, const PdgModel& M) {
+  const T three = from_double<T>(3.0);
+  const T ir = recip(rho);
+  const T sx = three * (jx * ir), sy = three * (jy * ir);
+  const T half = PDG_K(T, M, PDG_K_HALF);
+  const T base = from_double<T>(1.0) - PDG_K(T, M, PDG_K_SIXTH) * fma(sx, sx, sy * sy);
+  const T a0 = PDG_K(T, M, PDG_K_Q9W0) * rho, a1 = PDG_K(T, M, PDG_K_Q9W1) * rho;
+  const T a2 = PDG_K(T, M, PDG_K_Q9W2) * rho;
+  const T om1 = PDG_K(T, M, PDG_K_OM1);
+  const T sp = sx + sy, sm = sy - sx;
+  // e(+t) = base + t + t^2/2, e(-t) = base - t + t^2/2
+  const T bx = fma(half * sx, sx, base), by = fma(half * sy, sy, base);
+  const T bp = fma(half * sp, sp, base), bm = fma(half * sm, sm, base);
+  const T e[9] = {base, bx + sx, by + sy, bx - sx, by - sy, bp + sp, bm + sm, bp - sp, bm - sm};
+  if constexpr (!__is_same(T, double)) {
+    v[0] = relax(om1, v[0], a0 * e[0]);
+#pragma unroll
+    for (int i = 1; i < 5; ++i) v[i] = relax(om1, v[i], a1 * e[i]);
+#pragma unroll
+    for (int i = 5; i < 9; ++i) v[i] = relax(om1, v[i], a2 * e[i]);
+  } else {
+    v[0] = fma(om1, v[0], a0 * e[0]);
+#pragma unroll
+    for (int i = 1; i < 5; ++i) v[i] = fma(om1, v[i], a1 * e[i]);
+#pragma unroll
+    for (int i = 5; i < 9; ++i) v[i] = fma(om1, v[i], a2 * e[i]);
+  }
+}
+
+template <class T>
+struct Collide<MV_D2Q9, T> {
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) {
+    const T rho = (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
+    const T jx = (v[1] - v[3]) + ((v[5] - v[6]) + (v[8] - v[7]));
+    const T jy = (v[2] - v[4]) + ((v[5] + v[6]) - (v[7] + v[8]));
+    d2q9_relax<T>(v, rho, jx, jy, M);
+  }
+};
+
 template <class T>
 struct Collide<MV_NONE, T> {
   static __device__ __forceinline__ void run(T*, const PdgModel&) {}
@@ -296,6 +341,15 @@ template <> struct NFields<MV_EU2> { static constexpr int value = 16; };
 template <> struct NFields<MV_EU3> { static constexpr int value = 30; };
 template <> struct NFields<MV_ADV> { static constexpr int value = 6; };
 template <> struct NFields<MV_NONE> { static constexpr int value = 1; };
+template <> struct NFields<MV_D2Q9> { static constexpr int value = 9; };
+
+// State slot of population k at collision time (D2Q9: the diagonal populations 5-8 sit
+// in slots dslot..dslot+3, see PDG_Q9_SLOTS).
+template <int MV>
+__device__ __forceinline__ int coll_slot(int k, int dslot) {
+  if constexpr (MV == MV_D2Q9) return k < PDG_Q9_DIAG ? k : dslot + (k - PDG_Q9_DIAG);
+  return k;
+}
 
 // ---------------------------------------------------------------------------
 // Transport phases for one population along one line.  lp points at traversal
@@ -742,14 +796,15 @@ __device__ void collision_op(const PdgPass& p, int bid) {
     const int line = bid * LPB + l_in;
     if (line >= p.nlines) continue;
     const long long off = line_base(p, line) + tpos * p.stride;
-    const int nf = p.model.m * p.model.nv;
+    const int nf = p.model.nf;
     T v[NF];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) v[k] = (k < nf) ? ld<T>(p.f + (long long)k * p.field_stride + off) : zero<T>();
+    for (int k = 0; k < NF; ++k)
+      v[k] = (k < nf) ? ld<T>(p.f + (long long)coll_slot<MV>(k, p.dslot) * p.field_stride + off) : zero<T>();
     collide<MV, T>(v, p.model);
 #pragma unroll
     for (int k = 0; k < NF; ++k)
-      if (k < nf) st(p.f + (long long)k * p.field_stride + off, v[k]);
+      if (k < nf) st(p.f + (long long)coll_slot<MV>(k, p.dslot) * p.field_stride + off, v[k]);
   }
 }
 

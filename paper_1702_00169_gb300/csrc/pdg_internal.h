@@ -64,6 +64,16 @@ enum {
   PDG_K_CADV = 6,   // omega (1/(2D) + s_i a_axis / (2 lambda)), 6 entries
   PDG_K_N = 12
 };
+// D2Q9 reuses the advection slots: omega W_0, omega W_axis, omega W_diag, 1/6, 1/lambda, lambda.
+enum { PDG_K_Q9W0 = 6, PDG_K_Q9W1 = 7, PDG_K_Q9W2 = 8, PDG_K_SIXTH = 9, PDG_K_ILAM = 10, PDG_K_LAM = 11 };
+
+// D2Q9 state slots: populations 0-8 in the velocity order of Section 5.1, then four
+// scratch slots.  The diagonal transport (populations 5-8) is computed out of place,
+// so between the two diagonal sub-steps of a step the diagonal populations live in
+// slots 9-12 (PdgPass::dslot tells the collision where they are).
+#define PDG_Q9_SLOTS 13
+#define PDG_Q9_DIAG 5
+#define PDG_Q9_SCRATCH 9
 
 struct PdgModel {
   int kind;      // PDG_MODEL_*
@@ -71,7 +81,7 @@ struct PdgModel {
   int m;         // conserved variables
   int nv;        // 2D
   int prec;      // PDG_PREC_*
-  int pad_;
+  int nf;        // populations in f: m * nv (DnQ2n) or 9 (D2Q9)
   double lambda;
   double omega;
   double a[3];
@@ -102,20 +112,56 @@ struct PdgPass {
   int mv;                      // model variant of the collision (MV_* of pdg_device.cuh)
   int prec;                    // PDG_PREC_* of the state and arithmetic
   int periodic;                // 1: periodic lines; 0: inflow boundary data fb
-  int pad2_;
+  int dslot;                   // D2Q9 collision: state slot of population 5 (5 or 9)
   const double* fb;            // non-periodic: inflow values [2 sides][m][nlines] (state format)
   PdgCoef coef[2];
   PdgModel model;
 };
 
-// A pass of the schedule before its launch shape is chosen.
+// A pass of the schedule before its launch shape is chosen.  axis >= 0: a line pass
+// (ops on the populations along that axis, C on all); axis = -1: the D2Q9 diagonal
+// transport T(ddelta) of populations 5-8 from slots dslot_in.. to the other slot set.
 struct PdgPassSpec {
   int axis;
   int nops;
   int op[PDG_MAXOPS];
   int opcoef[PDG_MAXOPS];
   int ncs;
+  int dslot;      // line pass with C on D2Q9: slot of population 5
+  int dslot_in;   // diagonal pass: input slot of population 5 (output: the other set)
+  double ddelta;  // diagonal pass: sub-step
   PdgCoef cs[2];
+};
+
+// Coefficients of one diagonal theta sub-step on an n x n-node cell (node p = iy n + ix,
+// traversal orientation: the upwind neighbours are at -x and -y):
+//   fn = Binv r - c1 f,  r = f / theta + kx S_x Lt + ky S_y Bt,  c1 = (1 - theta) / theta,
+//   Lt = (1 - theta) L^old + theta L^new (values on the +x face of the -x neighbour,
+//   one per row iy, entering node (iy, 0)), Bt likewise from the -y neighbour (one per
+//   column ix, entering node (0, ix)); Binv = (I + theta (nu_x I(x)K + nu_y K(x)I))^-1,
+//   kx = nu_x / w_0, ky = nu_y / w_0.
+#define PDG_MAXNN (PDG_MAXN * PDG_MAXN)
+struct PdgDiagCoef {
+  double Binv[PDG_MAXNN * PDG_MAXNN];   // row-major NN x NN
+  double rtheta, c1, theta, omtheta, kx, ky;
+  int wx, wy;                            // halo columns / warm-up rows (cells)
+  float Binv_f[PDG_MAXNN * PDG_MAXNN][2];
+  float rtheta_f[1][2], c1_f[1][2], theta_f[1][2], omtheta_f[1][2], kx_f[1][2], ky_f[1][2];
+};
+
+// Launch descriptor of a diagonal pass: npop populations (traversal signs sx, sy) on an
+// ncx x ncy periodic cell grid; tiles of tx x ty output cells, each swept from wx
+// columns and wy rows upwind.
+struct PdgDiagPass {
+  const double* fin[4];
+  double* fout[4];
+  int sx[4], sy[4];
+  int npop, n, ncx, ncy;
+  long long row;          // points per row (P_x)
+  int tx, ty, ntx, nty;   // tile shape and counts
+  int kpar;               // cells processed in parallel per thread group (threads = kpar * n^2)
+  int prec;
+  PdgDiagCoef c;
 };
 
 // ---- read-only view of a context for entry points outside pdg_api.cu ----
@@ -125,7 +171,7 @@ struct pdg_ctx;
 struct PdgStateView {
   const double* f;
   long long npoints;
-  int m, nv;
+  int m, nv, nf;
   int prec;
   cudaStream_t stream;
 };
@@ -167,6 +213,15 @@ inline void pdg_split(double x, float out[2]) {
 // Fill the float-pair copies of a coefficient set / of the model constants.
 void pdg_coef_split(PdgCoef* c);
 void pdg_model_constants(PdgModel* m);
+// Diagonal sub-step coefficients for degree d, nu_x, nu_y > 0, 0 < theta <= 1, and the
+// halo / warm-up widths of the truncated tile start (influence <= 2^-56).  Returns 0, or
+// -1 when the theta system is singular or no width <= 128 meets the bound.
+int pdg_plan_diag(int d, double nux, double nuy, double theta, PdgDiagCoef* c);
+
+// ---- kernels (pdg_diag.cu) ----
+int pdg_launch_diag(const PdgDiagPass& p, void* stream);
+// dynamic shared memory (bytes) of one diagonal block
+size_t pdg_diag_smem(const PdgDiagPass& p);
 
 // ---- kernels (pdg_kernels.cu) ----
 // All return a cudaError_t cast to int.

@@ -48,6 +48,43 @@ __global__ void get_w_kernel(const double* __restrict__ f, double* __restrict__ 
   }
 }
 
+// D2Q9: w = (rho, rho u_x, rho u_y) in slots 0-2 -> f = f^eq(w) in slots 0-8 (M1 has
+// omega = 1, so the relaxation returns f^eq).
+template <class T>
+__global__ void set_feq_q9_kernel(double* __restrict__ f, long long P, const __grid_constant__ PdgModel M1) {
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+       pt += (long long)gridDim.x * blockDim.x) {
+    const T rho = from_double<T>(f[pt]);
+    const T ilam = PDG_K(T, M1, PDG_K_ILAM);
+    const T jx = from_double<T>(f[P + pt]) * ilam, jy = from_double<T>(f[2 * P + pt]) * ilam;
+    T v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = zero<T>();
+    d2q9_relax<T>(v, rho, jx, jy, M1);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st(f + (long long)i * P + pt, v[i]);
+  }
+}
+
+// D2Q9: w = P f = (sum f_i, lambda sum f_i xi_i).
+template <class T>
+__global__ void get_w_q9_kernel(const double* __restrict__ f, double* __restrict__ w, long long P,
+                                const __grid_constant__ PdgModel M) {
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+       pt += (long long)gridDim.x * blockDim.x) {
+    T v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = ld<T>(f + (long long)i * P + pt);
+    const T rho = (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
+    const T jx = (v[1] - v[3]) + ((v[5] - v[6]) + (v[8] - v[7]));
+    const T jy = (v[2] - v[4]) + ((v[5] + v[6]) - (v[7] + v[8]));
+    const T lam = PDG_K(T, M, PDG_K_LAM);
+    w[pt] = to_double(rho);
+    w[P + pt] = to_double(lam * jx);
+    w[2 * P + pt] = to_double(lam * jy);
+  }
+}
+
 __global__ void convert_kernel(double* __restrict__ f, long long n, int to_df) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -79,6 +116,7 @@ int pdg_model_variant(const PdgModel& m) {
     case PDG_MODEL_ADVECTION: return MV_ADV;
     case PDG_MODEL_SHALLOW_WATER: return MV_SW;
     case PDG_MODEL_EULER: return m.dim == 1 ? MV_EU1 : (m.dim == 2 ? MV_EU2 : MV_EU3);
+    case PDG_MODEL_ISOTHERMAL_D2Q9: return MV_D2Q9;
   }
   return -1;
 }
@@ -99,12 +137,25 @@ int pdg_launch_set_feq(double* f, long long P, const PdgModel& m, void* stream) 
     case MV_EU1: return launch_feq_t<MV_EU1>(f, P, m1, st);
     case MV_EU2: return launch_feq_t<MV_EU2>(f, P, m1, st);
     case MV_EU3: return launch_feq_t<MV_EU3>(f, P, m1, st);
+    case MV_D2Q9:
+      if (m1.prec == PDG_PREC_DF32)
+        set_feq_q9_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+      else
+        set_feq_q9_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+      return (int)cudaGetLastError();
   }
   return (int)cudaErrorInvalidValue;
 }
 
 int pdg_launch_get_w(const double* f, double* w, long long P, const PdgModel& m, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
+  if (m.kind == PDG_MODEL_ISOTHERMAL_D2Q9) {
+    if (m.prec == PDG_PREC_DF32)
+      get_w_q9_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+    else
+      get_w_q9_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+    return (int)cudaGetLastError();
+  }
   if (m.prec == PDG_PREC_DF32)
     get_w_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m.m, m.nv);
   else

@@ -69,6 +69,8 @@ extern "C" int pdg_get_w_noalloc(pdg_ctx* c, double* out, size_t len) {
   if (!out) return pdg_internal_fail(c, PDG_ERR_ARG, "out is NULL");
   if (v.prec != PDG_PREC_FP64)
     return pdg_internal_fail(c, PDG_ERR_UNSUPPORTED, "pdg_get_w_noalloc reads FP64 states only");
+  if (v.m * v.nv != v.nf)
+    return pdg_internal_fail(c, PDG_ERR_UNSUPPORTED, "pdg_get_w_noalloc reads vectorial (DnQ2n) states only");
   const size_t need = (size_t)v.m * (size_t)v.npoints;
   if (len != need) return pdg_internal_fail(c, PDG_ERR_ARG, "w length mismatch");
   if (need > (size_t)PDG_NOALLOC_W_MAX)

@@ -212,6 +212,124 @@ void pdg_model_constants(PdgModel* m) {
   m->k[PDG_K_HALFG] = 0.5 * m->gravity;
   m->k[PDG_K_GM1] = m->gamma - 1.0;
   m->k[PDG_K_HALF] = 0.5;
-  for (int i = 0; i < 6; ++i) m->k[PDG_K_CADV + i] = om * m->cadv[i];
+  if (m->kind == 3) {  // D2Q9: lattice weights of Section 5.1
+    m->k[PDG_K_Q9W0] = om * (4.0 / 9.0);
+    m->k[PDG_K_Q9W1] = om * (1.0 / 9.0);
+    m->k[PDG_K_Q9W2] = om * (1.0 / 36.0);
+    m->k[PDG_K_SIXTH] = 1.0 / 6.0;
+    m->k[PDG_K_ILAM] = 1.0 / m->lambda;
+    m->k[PDG_K_LAM] = m->lambda;
+  } else {
+    for (int i = 0; i < 6; ++i) m->k[PDG_K_CADV + i] = om * m->cadv[i];
+  }
   for (int i = 0; i < PDG_K_N; ++i) pdg_split(m->k[i], m->k_f[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal velocities (D2Q9).  On a Cartesian cell eq. (3.7) splits by axis, so for
+// v = lambda (s_x, s_y), in the traversal orientation (s = -1 mirrors that axis),
+//   B fn_c = (I - (1-theta) K2) f_c + (nu_x/w_0) S_x Lt + (nu_y/w_0) S_y Bt,
+//   K2 = nu_x I(x)K + nu_y K(x)I,  B = I + theta K2,
+// and B^-1 (I - (1-theta) K2) = B^-1 / theta - ((1-theta)/theta) I, which gives the form
+// of PdgDiagCoef (one dense NN x NN product per cell).
+//
+// Truncation width.  The new face values s_c = (R_c, T_c) (R: nodes (i, n-1), T: nodes
+// (n-1, i)) obey s_c = a_c + A s_{c-x} + B s_{c-y} with A, B the theta-weighted injection
+// columns of B^-1 restricted to the face rows.  A tile swept from W columns upwind starts
+// with the old face values instead of the new ones (error <= 2 max|f| per entry).  With
+// X = (I - |B|)^-1 |A| the error of the column j cells, taken over all rows, is bounded
+// entrywise by X^(j+1) applied to that start error (and likewise for the rows with
+// Y = (I - |A|)^-1 |B|); W is the smallest width whose bound, carried into the cell
+// values, is <= 2^-57 of max|f| for each of the two edges.
+static int diag_width(int m, const double* X, double g) {
+  double v[2 * PDG_MAXN], t[2 * PDG_MAXN];
+  for (int i = 0; i < m; ++i) v[i] = 1.0;
+  const double tol = std::ldexp(1.0, -57);
+  for (int W = 1; W <= 128; ++W) {
+    double mx = 0.0;
+    for (int i = 0; i < m; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < m; ++j) acc += X[i * m + j] * v[j];
+      t[i] = acc;
+      if (acc > mx) mx = acc;
+    }
+    for (int i = 0; i < m; ++i) v[i] = t[i];
+    if (!(mx < 1e300)) return -1;
+    if (2.0 * g * mx <= tol) return W;
+  }
+  return -1;
+}
+
+int pdg_plan_diag(int d, double nux, double nuy, double theta, PdgDiagCoef* c) {
+  const int n = d + 1, NN = n * n;
+  if (n > PDG_MAXN || !(theta > 0.0 && theta <= 1.0) || !(nux > 0.0) || !(nuy > 0.0) ||
+      !std::isfinite(nux) || !std::isfinite(nuy))
+    return -1;
+  double x[PDG_MAXN], w[PDG_MAXN], K[PDG_MAXN * PDG_MAXN];
+  if (pdg_plan_gl(d, x, w)) return -1;
+  pdg_plan_dmat(n, x, K);
+  K[0] += 1.0 / w[0];
+  static thread_local double A[PDG_MAXNN * PDG_MAXNN], R[PDG_MAXNN * PDG_MAXNN];
+  for (int p = 0; p < NN; ++p) {
+    const int iy = p / n, ix = p % n;
+    for (int q = 0; q < NN; ++q) {
+      const int jy = q / n, jx = q % n;
+      double k2 = 0.0;
+      if (iy == jy) k2 += nux * K[ix * n + jx];
+      if (ix == jx) k2 += nuy * K[iy * n + jy];
+      A[p * NN + q] = (p == q ? 1.0 : 0.0) + theta * k2;
+      R[p * NN + q] = (p == q ? 1.0 : 0.0);
+    }
+  }
+  if (solve(NN, NN, A, R)) return -1;
+  std::memset(c, 0, sizeof(*c));
+  for (int i = 0; i < NN * NN; ++i) c->Binv[i] = R[i];
+  c->theta = theta;
+  c->omtheta = 1.0 - theta;
+  c->rtheta = 1.0 / theta;
+  c->c1 = (1.0 - theta) / theta;
+  c->kx = nux / w[0];
+  c->ky = nuy / w[0];
+  // face transfer matrices (entrywise absolute values), state index s < n: R_s, s >= n: T_{s-n}
+  const int m = 2 * n;
+  auto fnode = [&](int s) { return s < n ? s * n + (n - 1) : (n - 1) * n + (s - n); };
+  double Ab[4 * PDG_MAXN * PDG_MAXN], Bb[4 * PDG_MAXN * PDG_MAXN];
+  for (int s = 0; s < m; ++s)
+    for (int t = 0; t < m; ++t) {
+      Ab[s * m + t] = t < n ? std::fabs(theta * c->kx * c->Binv[fnode(s) * NN + t * n]) : 0.0;
+      Bb[s * m + t] = t >= n ? std::fabs(theta * c->ky * c->Binv[fnode(s) * NN + (t - n)]) : 0.0;
+    }
+  double g = 0.0;   // largest cell value change per unit change of the inflow faces
+  for (int p = 0; p < NN; ++p) {
+    double acc = 0.0;
+    for (int q = 0; q < n; ++q)
+      acc += std::fabs(theta * c->kx * c->Binv[p * NN + q * n]) + std::fabs(theta * c->ky * c->Binv[p * NN + q]);
+    if (acc > g) g = acc;
+  }
+  double X[4 * PDG_MAXN * PDG_MAXN], Y[4 * PDG_MAXN * PDG_MAXN];
+  for (int pass = 0; pass < 2; ++pass) {
+    const double* P = pass == 0 ? Ab : Bb;   // the edge's own transfer
+    const double* Q = pass == 0 ? Bb : Ab;   // transfer along the edge
+    double IQ[4 * PDG_MAXN * PDG_MAXN], RHS[4 * PDG_MAXN * PDG_MAXN];
+    for (int i = 0; i < m * m; ++i) {
+      IQ[i] = ((i / m) == (i % m) ? 1.0 : 0.0) - Q[i];
+      RHS[i] = P[i];
+    }
+    if (solve(m, m, IQ, RHS)) return -1;
+    // (I - |Q|)^-1 must be entrywise >= 0 (spectral radius of |Q| below 1)
+    for (int i = 0; i < m * m; ++i)
+      if (RHS[i] < -1e-12) return -1;
+    std::memcpy(pass == 0 ? X : Y, RHS, sizeof(double) * m * m);
+  }
+  c->wx = diag_width(m, X, g);
+  c->wy = diag_width(m, Y, g);
+  if (c->wx < 0 || c->wy < 0) return -1;
+  for (int i = 0; i < NN * NN; ++i) pdg_split(c->Binv[i], c->Binv_f[i]);
+  pdg_split(c->rtheta, c->rtheta_f[0]);
+  pdg_split(c->c1, c->c1_f[0]);
+  pdg_split(c->theta, c->theta_f[0]);
+  pdg_split(c->omtheta, c->omtheta_f[0]);
+  pdg_split(c->kx, c->kx_f[0]);
+  pdg_split(c->ky, c->ky_f[0]);
+  return 0;
 }

@@ -16,14 +16,15 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpdg.so")
 
 PDG_OK = 0
 PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA, PDG_ERR_STATE, PDG_ERR_TIMEOUT, PDG_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
-PDG_MODEL_ADVECTION, PDG_MODEL_SHALLOW_WATER, PDG_MODEL_EULER = 0, 1, 2
+PDG_MODEL_ADVECTION, PDG_MODEL_SHALLOW_WATER, PDG_MODEL_EULER, PDG_MODEL_ISOTHERMAL_D2Q9 = 0, 1, 2, 3
 PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED, PDG_SCHEME_M2KIN = 0, 1, 2
 PDG_PREC_FP64 = 0
 PDG_PREC_DF32 = 1
 PRECISION = {"fp64": PDG_PREC_FP64, "df32": PDG_PREC_DF32}
 PDG_OPT_COMPOSE_TT = 1
 
-KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER}
+KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER,
+        "isothermal_d2q9": PDG_MODEL_ISOTHERMAL_D2Q9}
 SCHEME = {"M2": PDG_SCHEME_M2, "M2_collapsed": PDG_SCHEME_M2_COLLAPSED, "M2_kin": PDG_SCHEME_M2KIN}
 
 
@@ -229,9 +230,11 @@ class Solver:
         self._check(pdg_timing_enable(self.ctx, 1 if on else 0), "pdg_timing_enable")
 
     def timing_read(self):
-        la = (ctypes.c_longlong * 3)()
-        ms = (ctypes.c_double * 3)()
-        self._check(pdg_timing_read(self.ctx, ctypes.addressof(la), ctypes.addressof(ms), 3), "pdg_timing_read")
+        """Per kernel kind (0 line pass, 1 line pass with collision, 2 state kernels,
+        3 D2Q9 diagonal pass): launches and summed ms."""
+        la = (ctypes.c_longlong * 4)()
+        ms = (ctypes.c_double * 4)()
+        self._check(pdg_timing_read(self.ctx, ctypes.addressof(la), ctypes.addressof(ms), 4), "pdg_timing_read")
         return list(la), list(ms)
 
     def set_launch(self, kind, lpb, nseg, ngroup):

@@ -18,6 +18,9 @@ synthetic and drawn from ``numpy.random.default_rng(seed)``):
 * Euler: rho = 1 + 0.05 F_rho, u_a = 0.1 F_a, p = 1, with independent fields
   built like F above (|k|_inf <= 2 in 3-D); w = (rho, rho u, E) with
   E = p/(gamma-1) + rho |u|^2 / 2.
+* isothermal D2Q9 (the model of the paper's Euler-with-gravity test, without the
+  source): rho = 1 + 0.05 F_rho, u_a = 0.05 F_a with independent fields built like
+  F above; w = (rho, rho u_x, rho u_y); lambda = 1 (sound speed 1/sqrt(3), Mach <= 0.09).
 """
 import math
 from dataclasses import dataclass, field
@@ -25,7 +28,7 @@ from typing import Tuple
 
 import numpy as np
 
-KINDS = ("advection", "shallow_water", "euler")
+KINDS = ("advection", "shallow_water", "euler", "isothermal_d2q9")
 
 
 @dataclass
@@ -49,7 +52,17 @@ class Config:
 
     @property
     def m(self):
-        return {"advection": 1, "shallow_water": 3, "euler": self.dim + 2}[self.kind]
+        return {"advection": 1, "shallow_water": 3, "euler": self.dim + 2, "isothermal_d2q9": 3}[self.kind]
+
+    @property
+    def groups(self):
+        """Leading axis of f: conserved variables (DnQ2n) or one set of nine (D2Q9)."""
+        return 1 if self.kind == "isothermal_d2q9" else self.m
+
+    @property
+    def nv(self):
+        """Populations per group: 2D (DnQ2n) or 9 (D2Q9)."""
+        return 9 if self.kind == "isothermal_d2q9" else 2 * self.dim
 
     @property
     def ncells(self):
@@ -65,7 +78,7 @@ class Config:
 
     @property
     def nfields(self):
-        return self.m * 2 * self.dim
+        return self.groups * self.nv
 
     @property
     def dofs(self):
@@ -96,7 +109,10 @@ SW_D2Q4 = Config("shallow_water_d2q4_64x64x8x8_d3", "shallow_water", 2, (64, 64)
 EULER_D3Q6 = Config("euler_d3q6_32c3x4c3_d2", "euler", 3, (32, 32, 32), (4, 4, 4), 2,
                     lam=5.0, steps=10, seed=3)
 
-CONFIGS = {c.name: c for c in (ADVECTION_D2Q4, SW_D2Q4, EULER_D3Q6)}
+D2Q9_ISO = Config("isothermal_d2q9_64x64x8x8_d3", "isothermal_d2q9", 2, (64, 64), (8, 8), 3,
+                  lam=1.0, steps=20, seed=6)
+
+CONFIGS = {c.name: c for c in (ADVECTION_D2Q4, SW_D2Q4, EULER_D3Q6, D2Q9_ISO)}
 
 
 def _grid(coords):
@@ -177,6 +193,12 @@ def initial_w(cfg, coords):
         p = 1.0
         E = p / (cfg.gamma - 1.0) + 0.5 * rho * sum(ua * ua for ua in u)
         return np.stack([rho] + [rho * ua for ua in u] + [E]).astype(np.float64)
+    if cfg.kind == "isothermal_d2q9":
+        Fr = _normalised_field(rng, D, 16, 4, 256)
+        Fu = [_normalised_field(rng, D, 16, 4, 256) for _ in range(D)]
+        rho = np.broadcast_to(1.0 + 0.05 * Fr(X), shape)
+        u = [np.broadcast_to(0.05 * Fu[a](X), shape) for a in range(D)]
+        return np.stack([rho] + [rho * ua for ua in u]).astype(np.float64)
     raise ValueError(cfg.kind)
 
 

@@ -6,7 +6,8 @@ from oracle import models as OM
 from oracle import scheme as OS
 from oracle.dg import CartesianMesh
 
-ORACLE_KIND = {"advection": OM.ADVECTION, "shallow_water": OM.SHALLOW_WATER, "euler": OM.EULER}
+ORACLE_KIND = {"advection": OM.ADVECTION, "shallow_water": OM.SHALLOW_WATER, "euler": OM.EULER,
+               "isothermal_d2q9": OM.ISOTHERMAL_D2Q9}
 
 
 def rel_l2(a, b):
@@ -46,6 +47,6 @@ def run_gpu(cfg, w0, dt, nsteps, scheme="M2", launch=None, omega=None, stream=No
             s.set_launch(kind, *shape)
     s.set_w(np.ascontiguousarray(w0.reshape(-1)))
     s.step(dt, nsteps)
-    f = s.get_f().reshape((cfg.m, 2 * cfg.dim) + tuple(reversed(cfg.npoints_axis)))
+    f = s.get_f().reshape((cfg.groups, cfg.nv) + tuple(reversed(cfg.npoints_axis)))
     s.close()
     return f
