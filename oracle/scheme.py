@@ -11,6 +11,8 @@ Section 3.2:
   M_2^kin(dt) = T_2(dt/4) C_2(dt/2) T_2(dt/2) C_2(dt/2) T_2(dt/4) (Section 3.2): the
       composition that stays second order when tau -> 0; `omega` is then the weight of
       each C_2(dt/2).
+  With a source (oracle.source): M_2^s(dt) = T_2(dt/2) S_2(dt/2) C_2(dt) S_2(dt/2) T_2(dt/2)
+      (Section 3.2), also in the collapsed form of Section 5.1.
 
 The steps are applied in the naive order: every population is transported
 along its own velocity, then the collision acts on all populations, then every
@@ -19,6 +21,7 @@ population is transported again.
 import numpy as np
 
 from .dg import CartesianMesh
+from .source import source_step
 from .transport import DirectTransport, bloch_transport, bloch_transport_2d
 
 
@@ -76,29 +79,40 @@ class Transporter:
         return out
 
 
-def m2_step(f, transporter, model, dt, omega):
-    """M_2(dt) = T(dt/2) C(dt) T(dt/2), Section 3.2."""
+def m2_step(f, transporter, model, dt, omega, source=None):
+    """M_2(dt) = T(dt/2) C(dt) T(dt/2), Section 3.2; with a source M_2^s(dt)."""
     f = transporter(f, 0.5 * dt)
-    f = collision(f, model, omega)
+    f = source_collision(f, transporter, model, dt, omega, source)
     return transporter(f, 0.5 * dt)
 
 
-def run(f0, transporter, model, dt, nsteps, omega, scheme="M2"):
+def source_collision(f, transporter, model, dt, omega, source=None):
+    """C_2(dt), or S_2(dt/2) C_2(dt) S_2(dt/2) with a source."""
+    if source is None:
+        return collision(f, model, omega)
+    f = source_step(f, model, transporter.mesh, source, 0.5 * dt)
+    f = collision(f, model, omega)
+    return source_step(f, model, transporter.mesh, source, 0.5 * dt)
+
+
+def run(f0, transporter, model, dt, nsteps, omega, scheme="M2", source=None):
     """nsteps palindromic steps from f0.  scheme: "M2", "M2_collapsed" (Section 5.1) or
-    "M2_kin" (Section 3.2)."""
+    "M2_kin" (Section 3.2); source: an oracle.source.Source (M2 and M2_collapsed)."""
     f = np.array(f0, dtype=np.float64, copy=True)
     if nsteps <= 0:
         return f
     if scheme == "M2":
         for _ in range(nsteps):
-            f = m2_step(f, transporter, model, dt, omega)
+            f = m2_step(f, transporter, model, dt, omega, source)
         return f
     if scheme == "M2_collapsed":
         f = transporter(f, 0.5 * dt)
         for s in range(nsteps):
-            f = collision(f, model, omega)
+            f = source_collision(f, transporter, model, dt, omega, source)
             f = transporter(f, dt if s < nsteps - 1 else 0.5 * dt)
         return f
+    if source is not None:
+        raise ValueError("sources are defined for M2 and M2_collapsed (Section 3.2, Section 5.1)")
     if scheme == "M2_kin":
         for _ in range(nsteps):
             f = transporter(f, 0.25 * dt)
