@@ -80,6 +80,11 @@ def collision_flops(kind, dim):
     return m * (nv - 1) + 1 + dim + 2 * dim + 3 + dim * (2 + (dim - 1) + 2) + dim * m + 4 * m * nv
 
 
+SOURCES = {"gravity": dict(gravity=(0.0, -1.0)),
+           "penalization": dict(K_s=300.0, kappa=40.0, x_c=(0.25, 0.5), w_s=(1.0, 0.0, 0.0)),
+           "both": dict(gravity=(0.0, -1.0), K_s=300.0, kappa=40.0, x_c=(0.25, 0.5), w_s=(1.0, 0.0, 0.0))}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -93,6 +98,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--impl", default="pdg", choices=["pdg", "reference"])
+    ap.add_argument("--source", default="none", choices=["none", "gravity", "penalization", "both"],
+                    help="d2q9 workload: source stages S(dt/2) C S(dt/2) (gravity g = -1 e_y; "
+                         "penalisation K_s = 300, kappa = 40 at (0.25, 0.5), w_s = (1, 0, 0))")
     ap.add_argument("--scheme", default="M2", choices=["M2", "M2_collapsed", "M2_kin"])
     ap.add_argument("--inflow-x", action="store_true",
                     help="x axis with inflow boundaries (f^b = f^eq of the initial state at the faces)")
@@ -443,6 +451,8 @@ def main():
     cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6, "d2q9": W.D2Q9_ISO}.get(args.workload, W.SW_D2Q4)
     if args.inflow_x and cfg.kind == "isothermal_d2q9":
         raise SystemExit("--inflow-x: the D2Q9 path runs on periodic meshes only")
+    if args.source != "none" and cfg.kind != "isothermal_d2q9":
+        raise SystemExit("--source: sources run on the D2Q9 workload (--workload d2q9)")
     if args.impl == "reference":
         if args.steps is None:
             args.steps = 20
@@ -480,6 +490,8 @@ def main():
                         stream=stream.cuda_stream, periodic=periodic)
         sv.set_model(cfg.kind, cfg.lam, a=cfg.a, gravity=cfg.gravity, gamma=cfg.gamma, omega=cfg.omega,
                      theta=cfg.theta, scheme=args.scheme, precision=pdg.PRECISION[precision])
+        if args.source != "none":
+            sv.set_source(**SOURCES[args.source])
         return sv
 
     s = solver(args.precision)
@@ -651,6 +663,8 @@ def main():
                        "mesh": (f"{'x'.join(map(str, cfg.n_macro))} macrocells x {'x'.join(map(str, cfg.n_sub))} "
                                 f"subcells, d={cfg.order}, {'x'.join(map(str, cfg.npoints_axis))} GL points, periodic"),
                        "dof": dofs, "scheme": args.scheme, "theta": cfg.theta, "omega": cfg.omega,
+                       "source": (f"M2^s: S(dt/2) C S(dt/2), {args.source} {SOURCES[args.source]}"
+                                  if args.source != "none" else "none"),
                        "boundaries": "x: inflow (f^b = initial equilibrium), others periodic" if args.inflow_x
                        else "periodic",
                        "dt": cfg.dt, "lambda": cfg.lam, "precision": args.precision.upper(),

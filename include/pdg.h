@@ -181,6 +181,40 @@ int pdg_set_model(pdg_ctx* ctx, const pdg_model_desc* desc);
 int pdg_set_w(pdg_ctx* ctx, const double* w, size_t len, int on_device);
 
 /*
+ * Source terms of the split scheme M2^s(dt) = T(dt/2) S(dt/2) C(dt) S(dt/2) T(dt/2)
+ * (Section 3.2; collapsed form of Section 5.1 with PDG_SCHEME_M2_COLLAPSED).  S is a
+ * theta step of d/dt w = s(w) applied to the equilibrium part of f:
+ *   w' = w + delta [theta s(w') + (1 - theta) s(w)],   f' = f + f^eq(w') - f^eq(w)
+ * (reading: the paper applies the source "on the equilibrium part"; P f' = w').
+ *   PDG_SOURCE_GRAVITY       s = (0, rho g)            (Section 5.1; g = gravity[0..1])
+ *   PDG_SOURCE_PENALIZATION  s = -K(x) (w - w_s), K(x) = K_s exp(-kappa |x - x_c|^2) at the
+ *                            GL points (Section 5.2; the paper prints the opposite sign
+ *                            while describing a relaxation towards w_s)
+ * Both may be combined.  Available for PDG_MODEL_ISOTHERMAL_D2Q9 (the model of both
+ * source test cases of the paper) with PDG_SCHEME_M2 or PDG_SCHEME_M2_COLLAPSED.
+ */
+enum { PDG_SOURCE_GRAVITY = 1, PDG_SOURCE_PENALIZATION = 2 };
+typedef struct pdg_source_desc {
+  int flags;          /* PDG_SOURCE_* bits; 0 = no source */
+  int reserved;
+  double gravity[3];  /* g (x, y used) */
+  double K_s;         /* penalisation amplitude (>= 0) */
+  double kappa;       /* penalisation decay (>= 0) */
+  double x_c[3];      /* penalisation centre (box coordinates; x, y used) */
+  double w_s[5];      /* target state (rho, rho u_x, rho u_y) */
+  double theta;       /* implicit weight of S, 0 <= theta <= 1 (1/2 = second order) */
+} pdg_source_desc;
+
+/*
+ * pdg_set_source -- set (or, with desc NULL or flags 0, remove) the source of a context.
+ * The penalisation frequency K(x) is evaluated once here at every GL point and kept on
+ * the device (npoints doubles, cudaMalloc).  pdg_set_model removes the source.
+ * Errors: PDG_ERR_STATE (no model), PDG_ERR_UNSUPPORTED (model or scheme without
+ * sources), PDG_ERR_ARG (bad values), PDG_ERR_OOM, PDG_ERR_CUDA.
+ */
+int pdg_set_source(pdg_ctx* ctx, const pdg_source_desc* desc);
+
+/*
  * pdg_step -- advance nsteps palindromic steps of size dt (Section 3.2):
  * M2(dt) = T(dt/2) C(dt) T(dt/2), with T the theta step
  * (I - theta delta L_h) F^new = (I + (1-theta) delta L_h) F^old of eq. (3.11),
@@ -306,6 +340,8 @@ int pdg_timing_read(pdg_ctx* ctx, long long* launches, double* ms, int max_kinds
  * inside batched launches (lpb*nseg*ngroup <= 256):
  *   lpb    lines per thread block (>= 1), nseg: segments per line (>= 1),
  *   ngroup field groups per block (>= 1).
+ * kind 4 = D2Q9 diagonal pass: lpb = threads per block (a multiple of 32, 64..512),
+ *   nseg x ngroup = output cells per tile along x and y (>= 1; the tile counts follow).
  * All zeros restores the built-in heuristic.  Used by the autotuners.
  * Errors: PDG_ERR_ARG.
  */
@@ -323,7 +359,7 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
 enum { PDG_OPT_COMPOSE_TT = 1 };
 int pdg_set_option(pdg_ctx* ctx, int option, int value);
 
-/* pdg_get_launch -- read the launch shape override of a kind 0..3 (zeros = heuristic). */
+/* pdg_get_launch -- read the launch shape override of a kind 0..4 (zeros = heuristic). */
 int pdg_get_launch(const pdg_ctx* ctx, int kind, int* lpb, int* nseg, int* ngroup);
 
 /*

@@ -49,6 +49,9 @@ struct pdg_ctx {
   bool compose = true;        // compose consecutive equal transports into one T T sweep
   int launch[2][3] = {{0, 0, 0}, {0, 0, 0}};   // single-mesh shape overrides per pass kind
   int bshape[2][3] = {{0, 0, 0}, {0, 0, 0}};   // shapes inside batched launches (<= 256 threads)
+  int dshape[3] = {0, 0, 0};                   // D2Q9 diagonal pass: threads, tile x, tile y
+  PdgSrc src{};                                // source stage (flags 0 = none); delta set per pass
+  double* kfield = nullptr;                    // penalisation K at every point
   bool timing = false;
   long long t_launches[4] = {0, 0, 0, 0};
   double t_ms[4] = {0, 0, 0, 0};
@@ -255,6 +258,12 @@ int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov,
   }
   const int kind = pass_kind(sp);
   p.mv = kind ? pdg_model_variant(c->model) : 5 /* no collision */;
+  if (kind && c->src.flags && sp.sdelta != 0.0) {
+    p.src = c->src;
+    p.src.kfield = c->kfield;
+    p.src.delta = sp.sdelta;
+    pdg_split(p.src.delta, p.src.delta_f[0]);
+  }
   p.prec = c->model.prec;
   int Wmax = 1;
   for (int i = 0; i < sp.ncs; ++i) {
@@ -334,11 +343,19 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, PdgDiagPass* out) {
   p.ncy = c->N[1];
   p.row = c->P[0];
   p.prec = c->model.prec;
-  const int NN = c->n * c->n;
-  p.kpar = std::max(1, 256 / NN);
+  p.threads = c->dshape[0] ? c->dshape[0] : 512;
   const int slots = 152;   // one block per SM per wave (co-resident blocks share its FP64 pipe)
+  const double NN = (double)c->n * c->n, NF = 2.0 * c->n - 1.0;
   double best = 1e300;
-  for (int ntx = 1; ntx <= std::min(p.ncx, 64); ++ntx) {
+  if (c->dshape[0]) {
+    p.tx = std::min(c->dshape[1], p.ncx);
+    p.ty = std::min(c->dshape[2], p.ncy);
+    p.ntx = (p.ncx + p.tx - 1) / p.tx;
+    p.nty = (p.ncy + p.ty - 1) / p.ty;
+  }
+  // cost of one block: output cells, start cells at the face-node share of their work, and
+  // a per-step overhead of about 8 cells (two barriers per anti-diagonal)
+  for (int ntx = 1; ntx <= std::min(p.ncx, 64) && !c->dshape[0]; ++ntx) {
     const int tx = (p.ncx + ntx - 1) / ntx;
     if ((long long)tx * (ntx - 1) >= p.ncx) continue;   // the last tile would be empty
     for (int nty = 1; nty <= std::min(p.ncy, 64); ++nty) {
@@ -346,7 +363,8 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, PdgDiagPass* out) {
       if ((long long)ty * (nty - 1) >= p.ncy) continue;
       const long long blocks = 4LL * ntx * nty;
       const long long waves = (blocks + slots - 1) / slots;
-      const double cost = (double)waves * (double)(tx + p.c.wx) * (double)(ty + p.c.wy);
+      const double region = (double)(tx + p.c.wx) * (double)(ty + p.c.wy), out = (double)tx * ty;
+      const double cost = (double)waves * (out + (region - out) * NF / NN + 8.0 * (tx + p.c.wx + ty + p.c.wy));
       if (cost < best) {
         best = cost;
         p.tx = tx;
@@ -495,6 +513,8 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
   if (int r = build_line_schedule(c, dt, nsteps, out)) return r;
   if (c->model.kind != PDG_MODEL_ISOTHERMAL_D2Q9 || nsteps <= 0) return PDG_OK;
   if (!(dt > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 diagonal transport needs dt > 0");
+  if (c->src.flags && c->scheme == PDG_SCHEME_M2KIN)
+    return fail(c, PDG_ERR_UNSUPPORTED, "sources are defined for M2 and M2_collapsed");
   // diagonal sub-steps of each transport segment, in order
   std::vector<std::vector<double>> seg;
   const double h = 0.5 * dt, q = 0.25 * dt;
@@ -533,6 +553,7 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
       for (double dl : seg[ci]) diag(dl);
       ++ci;
       sp.dslot = slot;
+      sp.sdelta = c->src.flags ? 0.5 * dt : 0.0;   // S(dt/2) C(dt) S(dt/2)
     }
     res.push_back(sp);
   }
@@ -734,6 +755,7 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
     free_inflow(c);   // layout / format of the boundary data changes too (reset to zero)
   }
   c->model = M;
+  c->src.flags = 0;   // a new model starts without a source
   c->scheme = d->scheme;
   c->precision = d->precision;
   c->theta = d->theta;
@@ -828,6 +850,67 @@ int pdg_get_w(pdg_ctx* c, double* out, size_t len, int on_device) {
     PDG_CUDA(c, cudaMemcpyAsync(out, dst, sizeof(double) * need, cudaMemcpyDeviceToHost, c->stream));
     PDG_CUDA(c, cudaStreamSynchronize(c->stream));
   }
+  return PDG_OK;
+}
+
+int pdg_set_source(pdg_ctx* c, const pdg_source_desc* d) {
+  if (!c) return PDG_ERR_ARG;
+  if (!c->has_model) return fail(c, PDG_ERR_STATE, "pdg_set_source before pdg_set_model");
+  if (!d || d->flags == 0) {
+    c->src.flags = 0;
+    return PDG_OK;
+  }
+  if (c->model.kind != PDG_MODEL_ISOTHERMAL_D2Q9)
+    return fail(c, PDG_ERR_UNSUPPORTED, "sources are available for the D2Q9 model");
+  if (c->scheme == PDG_SCHEME_M2KIN)
+    return fail(c, PDG_ERR_UNSUPPORTED, "sources are defined for M2 and M2_collapsed");
+  if (d->flags & ~(PDG_SOURCE_GRAVITY | PDG_SOURCE_PENALIZATION)) return fail(c, PDG_ERR_ARG, "unknown source flag");
+  if (!(d->theta >= 0.0 && d->theta <= 1.0)) return fail(c, PDG_ERR_ARG, "source theta must be in [0, 1]");
+  const bool pen = d->flags & PDG_SOURCE_PENALIZATION;
+  for (int a = 0; a < 2; ++a)
+    if (!std::isfinite(d->gravity[a]) || !std::isfinite(d->x_c[a])) return fail(c, PDG_ERR_ARG, "non-finite source value");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(d->w_s[k])) return fail(c, PDG_ERR_ARG, "non-finite source value");
+  if (pen && !(d->K_s >= 0.0 && std::isfinite(d->K_s) && d->kappa >= 0.0 && std::isfinite(d->kappa)))
+    return fail(c, PDG_ERR_ARG, "penalisation needs finite K_s >= 0 and kappa >= 0");
+  PdgSrc S{};
+  S.flags = d->flags;
+  const bool grav = d->flags & PDG_SOURCE_GRAVITY;
+  for (int a = 0; a < 2; ++a) S.g[a] = grav ? d->gravity[a] : 0.0;
+  for (int k = 0; k < 3; ++k) S.ws[k] = d->w_s[k];
+  S.theta = d->theta;
+  S.omtheta = 1.0 - d->theta;
+  for (int a = 0; a < 2; ++a) pdg_split(S.g[a], S.g_f[a]);
+  for (int k = 0; k < 3; ++k) pdg_split(S.ws[k], S.ws_f[k]);
+  pdg_split(S.theta, S.theta_f[0]);
+  pdg_split(S.omtheta, S.omtheta_f[0]);
+  if (pen) {
+    // K(x) = K_s exp(-kappa |x - x_c|^2) at the GL points, computed on the host once
+    std::vector<double> xs[2];
+    for (int a = 0; a < 2; ++a) {
+      xs[a].resize(c->P[a]);
+      if (pdg_get_points(c, a, xs[a].data(), xs[a].size())) return fail(c, PDG_ERR_ARG, "points");
+    }
+    std::vector<double> K((size_t)c->npoints);
+    for (int y = 0; y < c->P[1]; ++y) {
+      const double dy = xs[1][y] - d->x_c[1];
+      for (int x = 0; x < c->P[0]; ++x) {
+        const double dx = xs[0][x] - d->x_c[0];
+        K[(size_t)y * c->P[0] + x] = d->K_s * std::exp(-d->kappa * (dx * dx + dy * dy));
+      }
+    }
+    if (!c->kfield) {
+      cudaError_t e = cudaMalloc((void**)&c->kfield, sizeof(double) * (size_t)c->npoints);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->kfield = nullptr;
+        return fail(c, PDG_ERR_OOM, std::string("cudaMalloc(K): ") + cudaGetErrorString(e));
+      }
+    }
+    PDG_CUDA(c, cudaMemcpyAsync(c->kfield, K.data(), sizeof(double) * K.size(), cudaMemcpyHostToDevice, c->stream));
+    PDG_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  c->src = S;
   return PDG_OK;
 }
 
@@ -938,7 +1021,19 @@ int pdg_timing_read(pdg_ctx* c, long long* launches, double* ms, int max_kinds) 
 }
 
 int pdg_set_launch(pdg_ctx* c, int kind, int lpb, int nseg, int ngroup) {
-  if (!c || kind < 0 || kind > 3) return PDG_ERR_ARG;
+  if (!c || kind < 0 || kind > 4) return PDG_ERR_ARG;
+  if (kind == 4) {
+    if (lpb == 0 && nseg == 0 && ngroup == 0) {
+      c->dshape[0] = c->dshape[1] = c->dshape[2] = 0;
+      return PDG_OK;
+    }
+    if (lpb < 64 || lpb > 512 || lpb % 32 || nseg < 1 || ngroup < 1)
+      return fail(c, PDG_ERR_ARG, "bad diagonal launch shape");
+    c->dshape[0] = lpb;
+    c->dshape[1] = nseg;
+    c->dshape[2] = ngroup;
+    return PDG_OK;
+  }
   int* slot = kind < 2 ? c->launch[kind] : c->bshape[kind - 2];
   const int maxt = kind < 2 ? 512 : pdg_batch_threads();
   if (lpb == 0 && nseg == 0 && ngroup == 0) {
@@ -966,6 +1061,7 @@ int pdg_destroy(pdg_ctx* c) {
     else cudaFree(c->f);
   }
   if (c->wstage) cudaFree(c->wstage);
+  if (c->kfield) cudaFree(c->kfield);
   free_inflow(c);
   delete c;
   return PDG_OK;
@@ -1115,8 +1211,8 @@ int pdg_set_option(pdg_ctx* c, int option, int value) {
 }
 
 int pdg_get_launch(const pdg_ctx* c, int kind, int* lpb, int* nseg, int* ngroup) {
-  if (!c || kind < 0 || kind > 3 || !lpb || !nseg || !ngroup) return PDG_ERR_ARG;
-  const int* slot = kind < 2 ? c->launch[kind] : c->bshape[kind - 2];
+  if (!c || kind < 0 || kind > 4 || !lpb || !nseg || !ngroup) return PDG_ERR_ARG;
+  const int* slot = kind < 2 ? c->launch[kind] : (kind < 4 ? c->bshape[kind - 2] : c->dshape);
   *lpb = slot[0];
   *nseg = slot[1];
   *ngroup = slot[2];

@@ -304,6 +304,13 @@ __device__ __forceinline__ void d2q9_relax(T* v, T rho, T jx, T jy, const PdgMod
     for (int i = 1; i < 5; ++i) v[i] = relax(om1, v[i], a1 * e[i]);
 #pragma unroll
     for (int i = 5; i < 9; ++i) v[i] = relax(om1, v[i], a2 * e[i]);
+  } else if (M.omega == 2.0) {
+    // omega = 2: (1 - omega) f + omega f^eq = W_i rho e_i (times 2) - f, one FMA
+    v[0] = fma(a0, e[0], -v[0]);
+#pragma unroll
+    for (int i = 1; i < 5; ++i) v[i] = fma(a1, e[i], -v[i]);
+#pragma unroll
+    for (int i = 5; i < 9; ++i) v[i] = fma(a2, e[i], -v[i]);
   } else {
     v[0] = fma(om1, v[0], a0 * e[0]);
 #pragma unroll
@@ -311,6 +318,66 @@ __device__ __forceinline__ void d2q9_relax(T* v, T rho, T jx, T jy, const PdgMod
 #pragma unroll
     for (int i = 5; i < 9; ++i) v[i] = fma(om1, v[i], a2 * e[i]);
   }
+}
+
+// D2Q9 equilibrium f^eq_i(rho, j) = W_i rho e_i (unscaled weights), j in lattice units.
+template <class T>
+__device__ __forceinline__ void d2q9_feq(T rho, T jx, T jy, const PdgModel& M, T* out) {
+  const T three = from_double<T>(3.0);
+  const T ir = recip(rho);
+  const T sx = three * (jx * ir), sy = three * (jy * ir);
+  const T half = PDG_K(T, M, PDG_K_HALF);
+  const T base = from_double<T>(1.0) - PDG_K(T, M, PDG_K_SIXTH) * fma(sx, sx, sy * sy);
+  const T sp = sx + sy, sm = sy - sx;
+  const T bx = fma(half * sx, sx, base), by = fma(half * sy, sy, base);
+  const T bp = fma(half * sp, sp, base), bm = fma(half * sm, sm, base);
+  const T a0 = from_double<T>(4.0 / 9.0) * rho, a1 = from_double<T>(1.0 / 9.0) * rho;
+  const T a2 = from_double<T>(1.0 / 36.0) * rho;
+  out[0] = a0 * base;
+  out[1] = a1 * (bx + sx);
+  out[2] = a1 * (by + sy);
+  out[3] = a1 * (bx - sx);
+  out[4] = a1 * (by - sy);
+  out[5] = a2 * (bp + sp);
+  out[6] = a2 * (bm + sm);
+  out[7] = a2 * (bp - sp);
+  out[8] = a2 * (bm - sm);
+}
+
+// Source stages around the collision, S(delta) C S(delta) (pdg_set_source).  S is the theta
+// step of d/dt w = s(w) for w = (rho, rho u), s = (0, rho g) - K (w - w_s), applied to the
+// equilibrium part: f' = f + f^eq(w') - f^eq(w).  Its theta system is lower triangular:
+// rho' first, then rho u' with the gravity term taken at both levels.  Composed:
+//   w -> w1 -> w2 (C keeps w),  f_out = f^eq(w2) + (1 - omega) (f - f^eq(w)),
+// since S keeps f - f^eq and C scales it by 1 - omega (f^eq(w1) cancels).
+template <class T>
+__device__ __forceinline__ void d2q9_source_collide(T* v, const PdgSrc& S, const PdgModel& M, long long off) {
+  const T rho = (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
+  const T jx = (v[1] - v[3]) + ((v[5] - v[6]) + (v[8] - v[7]));
+  const T jy = (v[2] - v[4]) + ((v[5] + v[6]) - (v[7] + v[8]));
+  const T lam = PDG_K(T, M, PDG_K_LAM), ilam = PDG_K(T, M, PDG_K_ILAM);
+  const T dl = PDG_S(T, S, delta), th = PDG_S(T, S, theta), omth = PDG_S(T, S, omtheta);
+  const T K = (S.flags & PDG_SOURCE_PENALIZATION) ? from_double<T>(S.kfield[off]) : zero<T>();
+  const T dK = dl * K;
+  const T ia = recip(fma(th, dK, from_double<T>(1.0)));
+  const T bb = from_double<T>(1.0) - omth * dK;
+  const T gx = PDG_C(T, S, g, 0), gy = PDG_C(T, S, g, 1);
+  const T kr = dK * PDG_C(T, S, ws, 0), kmx = dK * PDG_C(T, S, ws, 1), kmy = dK * PDG_C(T, S, ws, 2);
+  // S(delta) twice
+  const T rho1 = fma(bb, rho, kr) * ia;
+  const T rg1 = dl * fma(omth, rho, th * rho1);
+  const T mx1 = fma(bb, lam * jx, fma(rg1, gx, kmx)) * ia;
+  const T my1 = fma(bb, lam * jy, fma(rg1, gy, kmy)) * ia;
+  const T rho2 = fma(bb, rho1, kr) * ia;
+  const T rg2 = dl * fma(omth, rho1, th * rho2);
+  const T mx2 = fma(bb, mx1, fma(rg2, gx, kmx)) * ia;
+  const T my2 = fma(bb, my1, fma(rg2, gy, kmy)) * ia;
+  T e0[9], e2[9];
+  d2q9_feq<T>(rho, jx, jy, M, e0);
+  d2q9_feq<T>(rho2, mx2 * ilam, my2 * ilam, M, e2);
+  const T om1 = PDG_K(T, M, PDG_K_OM1);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) v[i] = fma(om1, v[i] - e0[i], e2[i]);
 }
 
 template <class T>
@@ -801,7 +868,14 @@ __device__ void collision_op(const PdgPass& p, int bid) {
 #pragma unroll
     for (int k = 0; k < NF; ++k)
       v[k] = (k < nf) ? ld<T>(p.f + (long long)coll_slot<MV>(k, p.dslot) * p.field_stride + off) : zero<T>();
-    collide<MV, T>(v, p.model);
+    bool done = false;
+    if constexpr (MV == MV_D2Q9) {
+      if (p.src.flags) {
+        d2q9_source_collide<T>(v, p.src, p.model, off);
+        done = true;
+      }
+    }
+    if (!done) collide<MV, T>(v, p.model);
 #pragma unroll
     for (int k = 0; k < NF; ++k)
       if (k < nf) st(p.f + (long long)coll_slot<MV>(k, p.dslot) * p.field_stride + off, v[k]);

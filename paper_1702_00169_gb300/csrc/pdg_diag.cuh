@@ -17,12 +17,12 @@
 // on another block.  Reads come from the input slots and writes go to the output slots,
 // so overlapping regions of neighbouring tiles never see a new value.
 //
-// Work split.  Each cell is computed by n^2 threads, thread q owning output node q; Binv
-// sits in shared memory transposed (column-major), so the threads of a cell read
-// consecutive words; kpar cells of an anti-diagonal are processed per round
-// (threads = kpar n^2).  A round: (A) every thread builds entry q of r_c in shared
-// memory; (B) every thread forms its output node as a dot product with r_c.  The next
-// round's state value is loaded before (B) so that its latency overlaps the arithmetic.
+// Work split.  One step of the wavefront = one anti-diagonal of cells: (A) the block
+// builds r_c for every cell of it in shared memory, (B) the block forms the output
+// nodes as dot products with r_c (Binv sits in shared memory transposed, so the threads
+// of a cell read consecutive words).  The cells of the upwind start only pass faces on,
+// so (B) computes just their 2n-1 face nodes.  The state of the next anti-diagonal is
+// copied into shared memory with cp.async while (B) runs (double-buffered by parity).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -44,41 +44,54 @@ struct DiagGeom {
   int sx, sy, ncx, ncy;
   long long row;
   int X0, Y0, wx, wy, ncol, nrow;
+  const int* colx;         // [ncol + 1]: x of traversal node 0 of region column j - 1
+  const long long* rowy;   // [nrow + 1]: offset of traversal node row 0 of region row r - 1
 };
 
-// Offset of node (iy, ix) (traversal orientation) of region cell (j, r).
+// Offset of node (iy, ix) (traversal orientation) of region cell (j, r), j, r >= -1.
 template <int NP>
 __device__ __forceinline__ long long diag_off(const DiagGeom& g, int j, int r, int iy, int ix) {
-  const int tc = wrap_cell(g.X0 - g.wx + j, g.ncx);
-  const int tr = wrap_cell(g.Y0 - g.wy + r, g.ncy);
-  const int pcx = g.sx > 0 ? tc : g.ncx - 1 - tc;
-  const int pcy = g.sy > 0 ? tr : g.ncy - 1 - tr;
-  const int x = pcx * NP + (g.sx > 0 ? ix : NP - 1 - ix);
-  const int y = pcy * NP + (g.sy > 0 ? iy : NP - 1 - iy);
-  return (long long)y * g.row + x;
+  return g.rowy[r + 1] + (long long)(g.sy * iy) * g.row + g.colx[j + 1] + g.sx * ix;
 }
 
-// Values a thread needs from memory for one round: its state value and, on the
-// region's upwind edges, the old face value entering its node.
-template <class T>
-struct DiagLoad {
-  T f, lb, bb;
-};
+// Asynchronous 8-byte copy global -> shared (cp.async, cached in L1) and its fences.
+__device__ __forceinline__ void cp_async8(void* smem, const double* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
+// Face node f of a cell: f < n: node (f, n-1) of the +x face; else node (n-1, f-n) of the
+// +y face (the corner belongs to the first set).
+template <int NP>
+__device__ __forceinline__ int face_node(int f) {
+  return f < NP ? f * NP + (NP - 1) : (NP - 1) * NP + (f - NP);
+}
+
+// Stage the state of every cell of anti-diagonal t (all n^2 nodes) and, on the region's
+// upwind edges, the old face values entering it, into buffer set `b`.
 template <int NP, class T>
-__device__ __forceinline__ void diag_fetch(const DiagGeom& g, int t, int j, int iy, int ix, bool act,
-                                          DiagLoad<T>& L) {
-  if (!act) return;
-  const int r = t - j;
-  L.f = ld<T>(g.fin + diag_off<NP>(g, j, r, iy, ix));
-  if (j == 0 && ix == 0) L.lb = ld<T>(g.fin + diag_off<NP>(g, -1, r, iy, NP - 1));
-  if (r == 0 && iy == 0) L.bb = ld<T>(g.fin + diag_off<NP>(g, j, -1, NP - 1, ix));
+__device__ __forceinline__ void diag_stage(const DiagGeom& g, int t, T* fb, T* lbnd, T* bbnd) {
+  constexpr int NN = NP * NP, RS = NN + 2;
+  const int jlo = max(0, t - g.nrow + 1), jhi = min(g.ncol - 1, t);
+  const int A = jhi - jlo + 1;
+  for (int i = threadIdx.x; i < A * NN; i += blockDim.x) {
+    const int c = i / NN, q = i % NN;
+    const int j = jlo + c;
+    cp_async8(fb + c * RS + q, g.fin + diag_off<NP>(g, j, t - j, q / NP, q % NP));
+  }
+  const int tid = threadIdx.x;
+  if (jlo == 0 && tid < NP)   // column 0 at row t: +x face of the cell upwind of it
+    cp_async8(lbnd + tid, g.fin + diag_off<NP>(g, -1, t, tid, NP - 1));
+  if (jhi == t && tid >= NP && tid < 2 * NP)   // row 0 at column t: +y face of the cell below
+    cp_async8(bbnd + (tid - NP), g.fin + diag_off<NP>(g, t, -1, NP - 1, tid - NP));
 }
 
 template <int NP, class T>
 __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
-  constexpr int NN = NP * NP;
-  const int K = p.kpar;
+  constexpr int NN = NP * NP, NF = 2 * NP - 1, RS = NN + 2;   // RS: 16-byte aligned rows
   int b = blockIdx.x;
   const int txi = b % p.ntx;
   b /= p.ntx;
@@ -102,99 +115,139 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
   g.ncol = ox + g.wx;
   g.nrow = oy + g.wy;
   const int T_steps = g.ncol + g.nrow - 1;
+  const int amax = min(p.tx + g.wx, p.ty + g.wy);   // longest anti-diagonal of any tile
 
-  const int tid = threadIdx.x;
-  const int k = tid / NN, q = tid % NN;
-  const int iy = q / NP, ix = q % NP;
-  const bool lane_ok = k < K;
-
-  // shared memory: BinvT[NN][NN] | rbuf[K][NN + 1] | Lt[2][ncol + 1][NP] | Bt[2][ncol][NP]
+  // shared memory: BinvT[NN][NN] | rbuf[amax][RS] | fbuf[2][amax][RS] | Lt[2][ncol+1][NP] |
+  //                Bt[2][ncol][NP] | lbnd[2][NP] | bbnd[2][NP] | rowy[nrow+1] | colx[ncol+1]
   T* BinvT = reinterpret_cast<T*>(sm);
   T* rbuf = BinvT + NN * NN;
-  T* Lt = rbuf + (size_t)K * (NN + 1);
-  T* Bt = Lt + (size_t)2 * (g.ncol + 1) * NP;
+  T* fbuf = rbuf + (size_t)amax * RS;
+  T* Lt = fbuf + (size_t)2 * amax * RS;
+  T* Bt = Lt + (size_t)2 * (p.tx + g.wx + 1) * NP;
+  T* lbnd = Bt + (size_t)2 * (p.tx + g.wx) * NP;
+  T* bbnd = lbnd + 2 * NP;
+  long long* rowy = reinterpret_cast<long long*>(bbnd + 2 * NP);
+  int* colx = reinterpret_cast<int*>(rowy + (p.ty + g.wy + 1));
+  const int LtS = p.tx + g.wx + 1, BtS = p.tx + g.wx;   // per-parity strides (columns)
   for (int i = threadIdx.x; i < NN * NN; i += blockDim.x) {
     const int row = i % NN, col = i / NN;   // BinvT[col][row] = Binv[row][col]
     BinvT[i] = cval<T>(&C.Binv[row * NN + col], &C.Binv_f[row * NN + col], 0);
   }
+  for (int j = threadIdx.x; j <= g.ncol; j += blockDim.x) {
+    const int tc = wrap_cell(g.X0 - g.wx + j - 1, g.ncx);
+    colx[j] = g.sx > 0 ? tc * NP : (g.ncx - 1 - tc) * NP + (NP - 1);
+  }
+  for (int r = threadIdx.x; r <= g.nrow; r += blockDim.x) {
+    const int tr = wrap_cell(g.Y0 - g.wy + r - 1, g.ncy);
+    rowy[r] = (long long)(g.sy > 0 ? tr * NP : (g.ncy - 1 - tr) * NP + (NP - 1)) * g.row;
+  }
+  g.colx = colx;
+  g.rowy = rowy;
+  __syncthreads();
+  // output-cell mapping: thread (k, q) computes node q of cells h1 + k, h1 + k + K, ...
+  const int K = blockDim.x / NN;
+  const int kq = threadIdx.x / NN, qq = threadIdx.x % NN;
+  T creg[NN];
+#pragma unroll
+  for (int i = 0; i < NN; ++i) creg[i] = BinvT[i * NN + qq];
   const T rth = PDG_DC(T, C, rtheta), c1 = PDG_DC(T, C, c1);
   const T th = PDG_DC(T, C, theta), omth = PDG_DC(T, C, omtheta);
   const T kx = PDG_DC(T, C, kx), ky = PDG_DC(T, C, ky);
 
-  auto jlo = [&](int t) { return max(0, t - g.nrow + 1); };
-  auto jhi = [&](int t) { return min(g.ncol - 1, t); };
-
-  // first round
-  int t = 0, base = 0;
-  DiagLoad<T> cur{}, nxt{};
-  diag_fetch<NP, T>(g, t, base + k, iy, ix, lane_ok && base + k <= jhi(t), cur);
-  while (t < T_steps) {
-    const int j = base + k;
-    const bool act = lane_ok && j <= jhi(t);
-    const int r = t - j;
+  diag_stage<NP, T>(g, 0, fbuf, lbnd, bbnd);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int t = 0; t < T_steps; ++t) {
     const int par = t & 1, prv = par ^ 1;
-    // (A) entry q of r_c
-    if (act) {
-      T rv = cur.f * rth;
-      if (ix == 0) {
-        const T lin = (j == 0) ? cur.lb : Lt[((size_t)prv * (g.ncol + 1) + j) * NP + iy];
-        rv = fma(kx, lin, rv);
-      }
-      if (iy == 0) {
-        const T bin = (r == 0) ? cur.bb : Bt[((size_t)prv * g.ncol + j) * NP + ix];
-        rv = fma(ky, bin, rv);
-      }
-      rbuf[k * (NN + 1) + q] = rv;
+    const int jlo = max(0, t - g.nrow + 1), jhi = min(g.ncol - 1, t);
+    const int A = jhi - jlo + 1;
+    const T* fc = fbuf + (size_t)par * amax * RS;
+    // (A) r_c of every cell of the anti-diagonal
+    for (int i = threadIdx.x; i < A * NN; i += blockDim.x) {
+      const int c = i / NN, q = i % NN;
+      const int j = jlo + c, iy = q / NP, ix = q % NP;
+      T rv = fc[c * RS + q] * rth;
+      if (ix == 0) rv = fma(kx, j == 0 ? lbnd[par * NP + iy] : Lt[((size_t)prv * LtS + j) * NP + iy], rv);
+      if (iy == 0) rv = fma(ky, j == t ? bbnd[par * NP + ix] : Bt[((size_t)prv * BtS + j) * NP + ix], rv);
+      rbuf[c * RS + q] = rv;
     }
     __syncthreads();
-    // next round, and its loads
-    int t2 = t, base2 = base + K;
-    if (base2 > jhi(t2)) {
-      t2 = t + 1;
-      base2 = jlo(t2);
-    }
-    if (t2 < T_steps) diag_fetch<NP, T>(g, t2, base2 + k, iy, ix, lane_ok && base2 + k <= jhi(t2), nxt);
-    // (B) output node q
-    if (act) {
-      const T* rc = rbuf + k * (NN + 1);
-      T acc = zero<T>();
-      if constexpr (__is_same(T, double)) {
+    if (t + 1 < T_steps)
+      diag_stage<NP, T>(g, t + 1, fbuf + (size_t)prv * amax * RS, lbnd + prv * NP, bbnd + prv * NP);
+    // (B) outputs.  Cells [jlo, h1) and (h2, jhi] belong to the upwind start (column < wx
+    // or row < wy): only their 2n-1 face nodes are needed.  Cells [h1, h2] are output
+    // cells: every node, with the thread's row of Binv held in registers.
+    const int h1 = max(jlo, min(g.wx, jhi + 1));
+    const int h2 = max(h1 - 1, min(jhi, t - g.wy));
+    auto finish = [&](int j, int q, T acc) {
+      const int c = j - jlo, r = t - j, iy = q / NP, ix = q % NP;
+      const T fo = fc[c * RS + q];
+      const T out = acc - c1 * fo;
+      if (j >= g.wx && r >= g.wy) st(g.fout + diag_off<NP>(g, j, r, iy, ix), out);
+      if (ix == NP - 1 || iy == NP - 1) {
+        const T face = fma(th, out, omth * fo);
+        if (ix == NP - 1) Lt[((size_t)par * LtS + j + 1) * NP + iy] = face;
+        if (iy == NP - 1) Bt[((size_t)par * BtS + j) * NP + ix] = face;
+      }
+    };
+    if (kq < K) {
+      for (int j = h1 + kq; j <= h2; j += K) {
+        const T* rc = rbuf + (j - jlo) * RS;
+        T acc;
+        if constexpr (__is_same(T, double)) {
+          double a[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-        for (int i = 0; i < NN; ++i) acc = fma(BinvT[i * NN + q], rc[i], acc);
+          for (int k = 0; k < NN; ++k) a[k & 3] = fma(creg[k], rc[k], a[k & 3]);
+          acc = (a[0] + a[1]) + (a[2] + a[3]);
+        } else {
+          T bb[NN];
+#pragma unroll
+          for (int k = 0; k < NN; ++k) bb[k] = rc[k];
+          acc = dot_acc<NN>(creg, bb, zero<T>());
+        }
+        finish(j, qq, acc);
+      }
+    }
+    const int n1 = (h1 - jlo) * NF, n2 = (jhi - h2) * NF;
+    for (int i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
+      const int j = i < n1 ? jlo + i / NF : h2 + 1 + (i - n1) / NF;
+      const int q = face_node<NP>(i < n1 ? i % NF : (i - n1) % NF);
+      const T* rc = rbuf + (j - jlo) * RS;
+      T acc;
+      if constexpr (__is_same(T, double)) {
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+        for (int k = 0; k + 1 < NN; k += 2) {
+          a0 = fma(BinvT[k * NN + q], rc[k], a0);
+          a1 = fma(BinvT[(k + 1) * NN + q], rc[k + 1], a1);
+        }
+        if (NN % 2) a0 = fma(BinvT[(NN - 1) * NN + q], rc[NN - 1], a0);
+        acc = a0 + a1;
       } else {
         T a[NN], bb[NN];
 #pragma unroll
-        for (int i = 0; i < NN; ++i) {
-          a[i] = BinvT[i * NN + q];
-          bb[i] = rc[i];
+        for (int k = 0; k < NN; ++k) {
+          a[k] = BinvT[k * NN + q];
+          bb[k] = rc[k];
         }
-        acc = dot_acc<NN>(a, bb, acc);
+        acc = dot_acc<NN>(a, bb, zero<T>());
       }
-      const T out = acc - c1 * cur.f;
-      if (j >= g.wx && r >= g.wy) st(g.fout + diag_off<NP>(g, j, r, iy, ix), out);
-      if (ix == NP - 1 || iy == NP - 1) {
-        const T face = fma(th, out, omth * cur.f);
-        if (ix == NP - 1) Lt[((size_t)par * (g.ncol + 1) + j + 1) * NP + iy] = face;
-        if (iy == NP - 1) Bt[((size_t)par * g.ncol + j) * NP + ix] = face;
-      }
+      finish(j, q, acc);
     }
+    cp_async_wait_all();
     __syncthreads();
-    cur = nxt;
-    t = t2;
-    base = base2;
   }
 }
 
 template <int NP, class T>
-__global__ void __launch_bounds__(512) diag_kernel(const __grid_constant__ PdgDiagPass p) {
+__global__ void __launch_bounds__(512, 1) diag_kernel(const __grid_constant__ PdgDiagPass p) {
   extern __shared__ double sm[];
   diag_body<NP, T>(p, sm);
 }
 
 template <class T>
 int launch_diag_typed(const PdgDiagPass& p, size_t smem, cudaStream_t st) {
-  const int NN = p.n * p.n;
-  const int threads = p.kpar * NN;
+  const int threads = p.threads;
   const int blocks = p.ntx * p.nty * p.npop;
   auto go = [&](auto kern) -> int {
     if (smem > 48 * 1024) {

@@ -94,6 +94,16 @@ struct PdgModel {
 
 enum { PDG_OP_NONE = 0, PDG_OP_T = 1, PDG_OP_C = 2, PDG_OP_TT = 3 };
 
+// Source stage S(delta) applied before and after the collision (see pdg_set_source):
+// theta step of d/dt w = s(w) on (rho, rho u), gravity g and penalisation K(x) (w_s - w).
+struct PdgSrc {
+  int flags;               // PDG_SOURCE_* bits
+  int pad_;
+  const double* kfield;    // K at every point (FP64), when penalising
+  double g[2], ws[3], theta, omtheta, delta;
+  float g_f[2][2], ws_f[3][2], theta_f[1][2], omtheta_f[1][2], delta_f[1][2];
+};
+
 struct PdgPass {
   double* f;
   long long field_stride;  // points per field
@@ -114,6 +124,7 @@ struct PdgPass {
   int periodic;                // 1: periodic lines; 0: inflow boundary data fb
   int dslot;                   // D2Q9 collision: state slot of population 5 (5 or 9)
   const double* fb;            // non-periodic: inflow values [2 sides][m][nlines] (state format)
+  PdgSrc src;                  // source stage around the collision (D2Q9), flags 0 = none
   PdgCoef coef[2];
   PdgModel model;
 };
@@ -130,6 +141,7 @@ struct PdgPassSpec {
   int dslot;      // line pass with C on D2Q9: slot of population 5
   int dslot_in;   // diagonal pass: input slot of population 5 (output: the other set)
   double ddelta;  // diagonal pass: sub-step
+  double sdelta;  // line pass with C: sub-step of the source stages around it (0: none)
   PdgCoef cs[2];
 };
 
@@ -159,7 +171,7 @@ struct PdgDiagPass {
   int npop, n, ncx, ncy;
   long long row;          // points per row (P_x)
   int tx, ty, ntx, nty;   // tile shape and counts
-  int kpar;               // cells processed in parallel per thread group (threads = kpar * n^2)
+  int threads;            // threads per block
   int prec;
   PdgDiagCoef c;
 };

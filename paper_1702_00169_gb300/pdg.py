@@ -35,6 +35,15 @@ class pdg_model_desc(ctypes.Structure):
                 ("theta", ctypes.c_double)]
 
 
+PDG_SOURCE_GRAVITY, PDG_SOURCE_PENALIZATION = 1, 2
+
+
+class pdg_source_desc(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_int), ("reserved", ctypes.c_int), ("gravity", ctypes.c_double * 3),
+                ("K_s", ctypes.c_double), ("kappa", ctypes.c_double), ("x_c", ctypes.c_double * 3),
+                ("w_s", ctypes.c_double * 5), ("theta", ctypes.c_double)]
+
+
 class pdg_info(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("order", ctypes.c_int), ("m", ctypes.c_int), ("nv", ctypes.c_int),
                 ("ncell", ctypes.c_int * 3), ("npts", ctypes.c_int * 3), ("npoints", ctypes.c_longlong),
@@ -63,6 +72,7 @@ _SIGS = {
     "pdg_set_model": (_I, [_P, ctypes.POINTER(pdg_model_desc)]),
     "pdg_set_w": (_I, [_P, _P, _SZ, _I]),
     "pdg_step": (_I, [_P, _D, _I]),
+    "pdg_set_source": (_I, [_P, _P]),
     "pdg_get_w": (_I, [_P, _P, _SZ, _I]),
     "pdg_get_f": (_I, [_P, _P, _SZ, _I]),
     "pdg_set_f": (_I, [_P, _P, _SZ, _I]),
@@ -197,6 +207,21 @@ class Solver:
 
     def step(self, dt, nsteps):
         self._check(pdg_step(self.ctx, dt, nsteps), "pdg_step")
+
+    def set_source(self, gravity=None, K_s=None, kappa=0.0, x_c=(0.0, 0.0), w_s=(1.0, 0.0, 0.0), theta=0.5):
+        """Gravity vector and/or penalisation (K_s, kappa, x_c, w_s); no argument removes it."""
+        d = pdg_source_desc()
+        d.flags = (PDG_SOURCE_GRAVITY if gravity is not None else 0) | \
+                  (PDG_SOURCE_PENALIZATION if K_s is not None else 0)
+        for i in range(3):
+            d.gravity[i] = float(gravity[i]) if gravity is not None and i < len(gravity) else 0.0
+            d.x_c[i] = float(x_c[i]) if i < len(x_c) else 0.0
+        for i in range(5):
+            d.w_s[i] = float(w_s[i]) if i < len(w_s) else 0.0
+        d.K_s = float(K_s or 0.0)
+        d.kappa = float(kappa)
+        d.theta = float(theta)
+        self._check(pdg_set_source(self.ctx, ctypes.byref(d)), "pdg_set_source")
 
     def get_w(self, out=None):
         i = self.info()

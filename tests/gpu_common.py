@@ -29,19 +29,24 @@ def oracle_w0(cfg):
     return W.initial_w(cfg, [mesh.coords1d(a) for a in range(cfg.dim)])
 
 
-def run_oracle(cfg, w0, dt, nsteps, scheme="M2", method="bloch", omega=None):
+def run_oracle(cfg, w0, dt, nsteps, scheme="M2", method="bloch", omega=None, source=None):
+    """source: keyword arguments of oracle.source.Source (and of Solver.set_source)."""
+    from oracle.source import Source
     mesh = oracle_mesh(cfg)
     model = oracle_model(cfg)
     tr = OS.Transporter(mesh, model, theta=cfg.theta, method=method)
     om = cfg.omega if omega is None else omega
-    return OS.run(OS.initial_state(model, w0), tr, model, dt, nsteps, om, scheme)
+    src = None if source is None else Source(**source)
+    return OS.run(OS.initial_state(model, w0), tr, model, dt, nsteps, om, scheme, source=src)
 
 
-def run_gpu(cfg, w0, dt, nsteps, scheme="M2", launch=None, omega=None, stream=None, precision=0):
+def run_gpu(cfg, w0, dt, nsteps, scheme="M2", launch=None, omega=None, stream=None, precision=0, source=None):
     from paper_1702_00169_gb300 import pdg
     import dataclasses
     c = cfg if omega is None else dataclasses.replace(cfg, omega=omega)
     s = pdg.solver_for(c, scheme=scheme, stream=stream, precision=precision)
+    if source is not None:
+        s.set_source(**source)
     if launch:
         for kind, shape in launch.items():
             s.set_launch(kind, *shape)
