@@ -80,6 +80,12 @@ def collision_flops(kind, dim):
     return m * (nv - 1) + 1 + dim + 2 * dim + 3 + dim * (2 + (dim - 1) + 2) + dim * m + 4 * m * nv
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
+# summarised under profiles/ (workload, kernel kind, precision) -> bytes.  Only kernels
+# that have not changed since their capture are listed; the others report null.
+TRAFFIC = {("isothermal_d2q9_64x64x8x8_d3", 3, "fp64"): 287.23e6,
+           ("isothermal_d2q9_64x64x8x8_d3", 3, "df32"): 286.81e6}
+
 SOURCES = {"gravity": dict(gravity=(0.0, -1.0)),
            "penalization": dict(K_s=300.0, kappa=40.0, x_c=(0.25, 0.5), w_s=(1.0, 0.0, 0.0)),
            "both": dict(gravity=(0.0, -1.0), K_s=300.0, kappa=40.0, x_c=(0.25, 0.5), w_s=(1.0, 0.0, 0.0))}
@@ -644,11 +650,15 @@ def main():
     achieved_tflops = flops_launch / (avg_ms * 1e-3) / 1e12
     achieved_gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
     roof = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved_tflops / fp64_peak_tflops, "traffic": None,
+            "frac": achieved_tflops / fp64_peak_tflops,
+            "traffic": TRAFFIC.get((cfg.name, k_dom, args.precision)) if args.source == "none" else None,
             "kernel": kinds[k_dom], "avg_launch_ms": avg_ms, "launches": launches[k_dom],
             "algorithmic_flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
             "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": achieved_gbs / hbm_peak,
-            "peak_note": "FP64 pipe peak = 152 SMs x 2 DFMA/clk x 2 flop x median SM clock under load"}
+            "peak_note": ("FP64 pipe peak = 152 SMs x 2 DFMA/clk x 2 flop x median SM clock under load"
+                          + ("; double-float run: the algorithmic flops are FP64-equivalent operations "
+                             "executed as double-word FP32 arithmetic, so the FP64 pipe is not its bound"
+                             if args.precision == "df32" else ""))}
 
     cpu = None
     if not args.no_cpu_baseline:
