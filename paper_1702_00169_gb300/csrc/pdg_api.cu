@@ -397,6 +397,25 @@ int issue_diag(pdg_ctx* c, const PdgPassSpec& sp) {
   return PDG_OK;
 }
 
+// Single-mesh launch shape: when ceil(nlines / lpb) blocks would leave more than 5 % of
+// the SMs idle in their last round, the block count is rounded up to a multiple of the
+// SM count, the lines are spread evenly over the blocks, and lpb shrinks to the largest
+// share, so that every SM gets the same number of lines and few thread slots stay idle.
+void balance_blocks(PdgPass* p) {
+  const int sms = 152;
+  const int nb0 = (p->nlines + p->lpb - 1) / p->lpb;
+  // keep the plain split (aligned line groups) when the last round of blocks already
+  // keeps 95 % of the SMs busy
+  const long long rounds = ((long long)nb0 + sms - 1) / sms;
+  if (nb0 < sms / 2 || (double)nb0 >= 0.95 * (double)(rounds * sms)) {
+    p->nblocks = nb0;
+    return;
+  }
+  const long long nb = std::min<long long>(((long long)nb0 + sms - 1) / sms * sms, p->nlines);
+  p->nblocks = (int)nb;
+  p->lpb = (int)(((long long)p->nlines + nb - 1) / nb);
+}
+
 int issue_pass(pdg_ctx* c, const PdgPassSpec& sp) {
   if (sp.axis == -2) {
     PDG_CUDA(c, cudaMemcpyAsync(c->f + (long long)PDG_Q9_DIAG * c->npoints,
@@ -408,6 +427,7 @@ int issue_pass(pdg_ctx* c, const PdgPassSpec& sp) {
   PdgPass p;
   const int kind = pass_kind(sp);
   if (int r = make_pass(c, sp, 512, c->launch[kind], &p)) return r;
+  balance_blocks(&p);
   return launch_timed(c, p, kind);
 }
 
@@ -1176,6 +1196,7 @@ int pdg_autotune(pdg_ctx* c, double dt, int reps) {
       int ov[3] = {s.lpb, s.nseg, s.ngroup};
       PdgPass p;
       if ((status = make_pass(c, sp[k], 512, ov, &p))) break;
+      balance_blocks(&p);
       float ms = 0.f;
       status = time_launches(c, reps, [&]() {
         int er = pdg_launch_pass(p, (void*)c->stream);

@@ -851,17 +851,30 @@ __device__ void transport_op_tt(const PdgPass& p, const PdgCoef& C, T* smY, T* s
   }
 }
 
+// Lines [*l0, *l0 + *cnt) of block bid (see PdgPass::nblocks); *cnt <= lpb.
+__device__ __forceinline__ void block_lines(const PdgPass& p, int bid, int* l0, int* cnt) {
+  if (p.nblocks > 0) {
+    const long long a = (long long)bid * p.nlines / p.nblocks;
+    const long long b = (long long)(bid + 1) * p.nlines / p.nblocks;
+    *l0 = (int)a;
+    *cnt = (int)(b - a);
+  } else {
+    *l0 = bid * p.lpb;
+    *cnt = min(p.lpb, p.nlines - *l0);
+  }
+}
+
 template <int MV, class T>
 __device__ void collision_op(const PdgPass& p, int bid) {
   __syncthreads();
   constexpr int NF = NFields<MV>::value;
-  const int LPB = p.lpb;
-  const long long tile = (long long)LPB * p.npl;
+  int l0, cnt;
+  block_lines(p, bid, &l0, &cnt);
+  const long long tile = (long long)cnt * p.npl;
   for (long long idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-    const int l_in = (int)(idx % LPB);
-    const long long tpos = idx / LPB;
-    const int line = bid * LPB + l_in;
-    if (line >= p.nlines) continue;
+    const int l_in = (int)(idx % cnt);
+    const long long tpos = idx / cnt;
+    const int line = l0 + l_in;
     const long long off = line_base(p, line) + tpos * p.stride;
     const int nf = p.model.nf;
     T v[NF];
@@ -894,8 +907,10 @@ __device__ __forceinline__ void pass_body(const PdgPass& p, int bid, double* sm)
   const int l_in = t % LPB;
   const int s = (t / LPB) % S;
   const int grp = t / (LPB * S);
-  const int line = bid * LPB + l_in;
-  const bool active = (t < nthr) && line < p.nlines;
+  int l0, cnt;
+  block_lines(p, bid, &l0, &cnt);
+  const int line = l0 + l_in;
+  const bool active = (t < nthr) && l_in < cnt;
   const int cap = p.ntf * S * LPB;
   T* smY = reinterpret_cast<T*>(sm);
   T* smU = smY + cap;

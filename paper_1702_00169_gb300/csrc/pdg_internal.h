@@ -110,6 +110,9 @@ struct PdgPass {
   long long stride;        // point stride along the line
   long long lineA, s1, s2; // base(l) = (l % lineA) * s1 + (l / lineA) * s2
   int nlines;              // line positions in the pass
+  int nblocks;             // > 0: blocks of the launch, lines spread evenly over them
+                           //      (block b owns lines [b nlines / nblocks, (b+1) nlines / nblocks));
+                           // 0: block b owns lines [b lpb, (b+1) lpb) (batched launches)
   int npl;                 // points per line, P = ncell * n
   int ncell;               // cells per line
   int nseg, lpb, ngroup;   // launch shape

@@ -42,7 +42,7 @@ int launch_pass_t(const PdgPass& p, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
   }
-  const int blocks = (p.nlines + p.lpb - 1) / p.lpb;
+  const int blocks = p.nblocks > 0 ? p.nblocks : (p.nlines + p.lpb - 1) / p.lpb;
   kern<<<blocks, threads, smem, st>>>(p);
   return (int)cudaGetLastError();
 }
