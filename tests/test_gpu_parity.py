@@ -256,3 +256,14 @@ def test_m2kin_scheme(precision, nsteps):
         f_ref = run_oracle(cfg, w0, cfg.dt, nsteps, scheme="M2_kin")
         f = run_gpu(cfg, w0, cfg.dt, nsteps, scheme="M2_kin", precision=precision)
         assert rel_l2(f, f_ref) <= TOL
+
+
+@pytest.mark.parametrize("shape", [None, (8, 4, 2)])
+def test_balanced_line_split(shape):
+    """A pass whose ceil(lines / lpb) blocks would leave SMs idle (700 y-lines, lpb 8 -> 88
+    blocks): the lines are spread evenly over 152 blocks of 4-5 lines; parity unchanged."""
+    cfg = dataclasses.replace(W.SW_D2Q4, n_macro=(70, 14), n_sub=(5, 5), order=1)
+    w0 = oracle_w0(cfg)
+    f_ref = run_oracle(cfg, w0, cfg.dt, 3)
+    f = run_gpu(cfg, w0, cfg.dt, 3, launch=None if shape is None else {0: shape, 1: shape})
+    assert rel_l2(f, f_ref) <= TOL
