@@ -231,8 +231,8 @@ int pdg_set_source(pdg_ctx* ctx, const pdg_source_desc* desc);
  * (L, B: downwind-face values of the upwind neighbours along x and y).  The periodic
  * 2-D recurrence is solved on tiles swept as wavefronts; every tile starts W cells
  * upwind along both axes, W chosen on the host so that the influence of the
- * truncated start (bounded through the entrywise absolute transfer matrices of the
- * face recurrence) is below 2^-56 of the state's magnitude.  dt must be > 0 there
+ * truncated start (bounded by the sum over lattice paths of the face recurrence's
+ * transfer matrices) is below 2^-56 of the state's magnitude.  dt must be > 0 there
  * (PDG_ERR_UNSUPPORTED otherwise, or when no such W <= 128 exists).
  * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_CUDA,
  *         PDG_ERR_UNSUPPORTED.

@@ -51,6 +51,12 @@ struct pdg_ctx {
   int bshape[2][3] = {{0, 0, 0}, {0, 0, 0}};   // shapes inside batched launches (<= 256 threads)
   int dshape[3] = {0, 0, 0};                   // D2Q9 diagonal pass: threads, tile x, tile y
   PdgSrc src{};                                // source stage (flags 0 = none); delta set per pass
+  struct DiagPlan {
+    int order;
+    double nux, nuy, theta;
+    PdgDiagCoef c;
+  };
+  std::vector<DiagPlan> diag_plans;            // planned diagonal sub-steps (a few sizes per run)
   double* kfield = nullptr;                    // penalisation K at every point
   bool timing = false;
   long long t_launches[4] = {0, 0, 0, 0};
@@ -326,9 +332,19 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, PdgDiagPass* out) {
   std::memset(&p, 0, sizeof(p));
   const double nux = 2.0 * c->model.lambda * sp.ddelta / c->h[0];
   const double nuy = 2.0 * c->model.lambda * sp.ddelta / c->h[1];
-  if (pdg_plan_diag(c->order, nux, nuy, c->theta, &p.c))
-    return fail(c, PDG_ERR_UNSUPPORTED,
-                "diagonal transport: no truncation width <= 128 cells for this time step (dt must be > 0)");
+  // plans are cached: the width search costs up to a few ms on the host
+  const PdgDiagCoef* hit = nullptr;
+  for (const auto& e : c->diag_plans)
+    if (e.order == c->order && e.nux == nux && e.nuy == nuy && e.theta == c->theta) hit = &e.c;
+  if (hit) {
+    p.c = *hit;
+  } else {
+    if (pdg_plan_diag(c->order, nux, nuy, c->theta, &p.c))
+      return fail(c, PDG_ERR_UNSUPPORTED,
+                  "diagonal transport: no truncation width <= 128 cells for this time step (dt must be > 0)");
+    if (c->diag_plans.size() >= 8) c->diag_plans.erase(c->diag_plans.begin());
+    c->diag_plans.push_back({c->order, nux, nuy, c->theta, p.c});
+  }
   const int in = sp.dslot_in, outs = sp.dslot_in == PDG_Q9_DIAG ? PDG_Q9_SCRATCH : PDG_Q9_DIAG;
   static const int sx[4] = {+1, -1, -1, +1}, sy[4] = {+1, +1, -1, -1};   // populations 5-8
   p.npop = 4;

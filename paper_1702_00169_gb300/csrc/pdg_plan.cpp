@@ -234,28 +234,56 @@ void pdg_model_constants(PdgModel* m) {
 // of PdgDiagCoef (one dense NN x NN product per cell).
 //
 // Truncation width.  The new face values s_c = (R_c, T_c) (R: nodes (i, n-1), T: nodes
-// (n-1, i)) obey s_c = a_c + A s_{c-x} + B s_{c-y} with A, B the theta-weighted injection
+// (n-1, i)) obey s_c = a_c + A s_{c-x} + B s_{c-y}, A and B the theta-weighted injection
 // columns of B^-1 restricted to the face rows.  A tile swept from W columns upwind starts
-// with the old face values instead of the new ones (error <= 2 max|f| per entry).  With
-// X = (I - |B|)^-1 |A| the error of the column j cells, taken over all rows, is bounded
-// entrywise by X^(j+1) applied to that start error (and likewise for the rows with
-// Y = (I - |A|)^-1 |B|); W is the smallest width whose bound, carried into the cell
-// values, is <= 2^-57 of max|f| for each of the two edges.
-static int diag_width(int m, const double* X, double g) {
-  double v[2 * PDG_MAXN], t[2 * PDG_MAXN];
-  for (int i = 0; i < m; ++i) v[i] = 1.0;
+// with the old face values instead of the new ones (error <= 2 max|f| per entry).  An
+// error entering at row k of the upwind edge reaches the cell of column j, row k + r,
+// through the sum over lattice paths G(j, r) = A G(j-1, r) + B G(j, r-1) of products of A
+// and B (signs kept), so its effect on any cell of column j is bounded by
+// 2 max|f| g sum_r ||G(j, r)||_inf (g: largest gain of a cell value per unit change of the
+// inflow faces).  W is the smallest width for which that bound is <= 2^-57 max|f|, for
+// each of the two edges (rows: A and B exchanged).  Rows are summed up to 256, far past
+// the decay of the terms.
+static int diag_width(int n, const double* A, const double* B, int edge, double g) {
+  const int m = 2 * n, mm = m * m, R = 256;
+  static thread_local double bufA[256 * 4 * PDG_MAXN * PDG_MAXN], bufB[256 * 4 * PDG_MAXN * PDG_MAXN];
+  double* prev = bufA;
+  double* cur = bufB;
+  const double* X = edge == 0 ? A : B;   // step across the edge
+  const double* Y = edge == 0 ? B : A;   // step along the edge
+  for (int i = 0; i < R * mm; ++i) prev[i] = 0.0;
+  for (int s = 0; s < n; ++s) {          // unit error on the faces crossing the edge
+    const int f = edge == 0 ? s : n + s;
+    prev[f * m + f] = 1.0;
+  }
   const double tol = std::ldexp(1.0, -57);
   for (int W = 1; W <= 128; ++W) {
-    double mx = 0.0;
-    for (int i = 0; i < m; ++i) {
-      double acc = 0.0;
-      for (int j = 0; j < m; ++j) acc += X[i * m + j] * v[j];
-      t[i] = acc;
-      if (acc > mx) mx = acc;
+    double total = 0.0;
+    for (int r = 0; r < R; ++r) {
+      double* G = cur + (size_t)r * mm;
+      const double* P = prev + (size_t)r * mm;
+      const double* L = r > 0 ? cur + (size_t)(r - 1) * mm : nullptr;
+      double nrm = 0.0;
+      for (int i = 0; i < m; ++i) {
+        double rs = 0.0;
+        for (int j = 0; j < m; ++j) {
+          double acc = 0.0;
+          for (int k = 0; k < m; ++k) {
+            acc += X[i * m + k] * P[k * m + j];
+            if (L) acc += Y[i * m + k] * L[k * m + j];
+          }
+          G[i * m + j] = acc;
+          rs += std::fabs(acc);
+        }
+        if (rs > nrm) nrm = rs;
+      }
+      total += nrm;
     }
-    for (int i = 0; i < m; ++i) v[i] = t[i];
-    if (!(mx < 1e300)) return -1;
-    if (2.0 * g * mx <= tol) return W;
+    if (!(total < 1e300)) return -1;
+    if (2.0 * g * total <= tol) return W;
+    double* t = prev;
+    prev = cur;
+    cur = t;
   }
   return -1;
 }
@@ -290,14 +318,14 @@ int pdg_plan_diag(int d, double nux, double nuy, double theta, PdgDiagCoef* c) {
   c->c1 = (1.0 - theta) / theta;
   c->kx = nux / w[0];
   c->ky = nuy / w[0];
-  // face transfer matrices (entrywise absolute values), state index s < n: R_s, s >= n: T_{s-n}
+  // face transfer matrices (signed), state index s < n: R_s, s >= n: T_{s-n}
   const int m = 2 * n;
   auto fnode = [&](int s) { return s < n ? s * n + (n - 1) : (n - 1) * n + (s - n); };
   double Ab[4 * PDG_MAXN * PDG_MAXN], Bb[4 * PDG_MAXN * PDG_MAXN];
   for (int s = 0; s < m; ++s)
     for (int t = 0; t < m; ++t) {
-      Ab[s * m + t] = t < n ? std::fabs(theta * c->kx * c->Binv[fnode(s) * NN + t * n]) : 0.0;
-      Bb[s * m + t] = t >= n ? std::fabs(theta * c->ky * c->Binv[fnode(s) * NN + (t - n)]) : 0.0;
+      Ab[s * m + t] = t < n ? theta * c->kx * c->Binv[fnode(s) * NN + t * n] : 0.0;
+      Bb[s * m + t] = t >= n ? theta * c->ky * c->Binv[fnode(s) * NN + (t - n)] : 0.0;
     }
   double g = 0.0;   // largest cell value change per unit change of the inflow faces
   for (int p = 0; p < NN; ++p) {
@@ -306,23 +334,8 @@ int pdg_plan_diag(int d, double nux, double nuy, double theta, PdgDiagCoef* c) {
       acc += std::fabs(theta * c->kx * c->Binv[p * NN + q * n]) + std::fabs(theta * c->ky * c->Binv[p * NN + q]);
     if (acc > g) g = acc;
   }
-  double X[4 * PDG_MAXN * PDG_MAXN], Y[4 * PDG_MAXN * PDG_MAXN];
-  for (int pass = 0; pass < 2; ++pass) {
-    const double* P = pass == 0 ? Ab : Bb;   // the edge's own transfer
-    const double* Q = pass == 0 ? Bb : Ab;   // transfer along the edge
-    double IQ[4 * PDG_MAXN * PDG_MAXN], RHS[4 * PDG_MAXN * PDG_MAXN];
-    for (int i = 0; i < m * m; ++i) {
-      IQ[i] = ((i / m) == (i % m) ? 1.0 : 0.0) - Q[i];
-      RHS[i] = P[i];
-    }
-    if (solve(m, m, IQ, RHS)) return -1;
-    // (I - |Q|)^-1 must be entrywise >= 0 (spectral radius of |Q| below 1)
-    for (int i = 0; i < m * m; ++i)
-      if (RHS[i] < -1e-12) return -1;
-    std::memcpy(pass == 0 ? X : Y, RHS, sizeof(double) * m * m);
-  }
-  c->wx = diag_width(m, X, g);
-  c->wy = diag_width(m, Y, g);
+  c->wx = diag_width(n, Ab, Bb, 0, g);
+  c->wy = diag_width(n, Ab, Bb, 1, g);
   if (c->wx < 0 || c->wy < 0) return -1;
   for (int i = 0; i < NN * NN; ++i) pdg_split(c->Binv[i], c->Binv_f[i]);
   pdg_split(c->rtheta, c->rtheta_f[0]);

@@ -52,7 +52,7 @@ def test_schemes(scheme, nsteps):
     assert rel_l2(f, f_ref) <= TOL
 
 
-@pytest.mark.parametrize("theta,cfl", [(0.7, 1.0), (1.0, 1.0), (0.5, 2.0), (0.5, 0.3)])
+@pytest.mark.parametrize("theta,cfl", [(0.7, 1.0), (1.0, 1.0), (0.5, 2.0), (0.5, 4.0), (0.5, 0.3)])
 def test_theta_and_cfl(theta, cfl):
     cfg = _cfg((3, 5), (5, 3), 3, theta=theta, cfl=cfl)
     w0 = oracle_w0(cfg)
