@@ -15,6 +15,7 @@
 // the x86-64 and aarch64 builds produce identical coefficients.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "pdg_internal.h"
 
@@ -246,9 +247,9 @@ void pdg_model_constants(PdgModel* m) {
 // the decay of the terms.
 static int diag_width(int n, const double* A, const double* B, int edge, double g) {
   const int m = 2 * n, mm = m * m, R = 256;
-  static thread_local double bufA[256 * 4 * PDG_MAXN * PDG_MAXN], bufB[256 * 4 * PDG_MAXN * PDG_MAXN];
-  double* prev = bufA;
-  double* cur = bufB;
+  std::vector<double> bufA((size_t)R * mm), bufB((size_t)R * mm);
+  double* prev = bufA.data();
+  double* cur = bufB.data();
   const double* X = edge == 0 ? A : B;   // step across the edge
   const double* Y = edge == 0 ? B : A;   // step along the edge
   for (int i = 0; i < R * mm; ++i) prev[i] = 0.0;
@@ -297,7 +298,9 @@ int pdg_plan_diag(int d, double nux, double nuy, double theta, PdgDiagCoef* c) {
   if (pdg_plan_gl(d, x, w)) return -1;
   pdg_plan_dmat(n, x, K);
   K[0] += 1.0 / w[0];
-  static thread_local double A[PDG_MAXNN * PDG_MAXNN], R[PDG_MAXNN * PDG_MAXNN];
+  std::vector<double> Av((size_t)PDG_MAXNN * PDG_MAXNN), Rv((size_t)PDG_MAXNN * PDG_MAXNN);
+  double* A = Av.data();
+  double* R = Rv.data();
   for (int p = 0; p < NN; ++p) {
     const int iy = p / n, ix = p % n;
     for (int q = 0; q < NN; ++q) {
