@@ -69,8 +69,8 @@ enum {
                                   - u.u/(2c^2)), c = lambda/sqrt(3), W = 4/9, 1/9, 1/36
                                   (Section 5.1).  The four diagonal velocities couple each
                                   cell to two upwind faces: their transport is the 2-D
-                                  recurrence of pdg_step's documentation.  Periodic meshes
-                                  only; 0 < theta <= 1; dt > 0. */
+                                  recurrence of pdg_step's documentation.  Periodic or
+                                  inflow axes (pdg_set_inflow); 0 < theta <= 1; dt > 0. */
 };
 
 /* Time schemes (Section 3.2 and Section 5.1). */
@@ -233,7 +233,8 @@ int pdg_set_source(pdg_ctx* ctx, const pdg_source_desc* desc);
  * upwind along both axes, W chosen on the host so that the influence of the
  * truncated start (bounded by the sum over lattice paths of the face recurrence's
  * transfer matrices) is below 2^-56 of the state's magnitude.  dt must be > 0 there
- * (PDG_ERR_UNSUPPORTED otherwise, or when no such W <= 128 exists).
+ * (PDG_ERR_UNSUPPORTED otherwise, or when no such W <= 128 exists).  On an inflow axis
+ * the tiles that reach the inflow face start there, from the exact boundary data.
  * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_CUDA,
  *         PDG_ERR_UNSUPPORTED.
  */
@@ -267,6 +268,9 @@ int pdg_set_f(pdg_ctx* ctx, const double* f, size_t len, int on_device);
  *        populations; side 1 = the high face, read by the -lambda e_a populations; lines
  *        are the points of the other axes in C order ([P_z][P_y] for axis 0, [P_z][P_x]
  *        for axis 1, [P_y][P_x] for axis 2); len = 2 * m * lines.
+ *        D2Q9: [2][3][lines], the three populations entering through that face in
+ *        increasing population index (low x face: 1, 5, 8; high x face: 3, 6, 7; low y
+ *        face: 2, 5, 6; high y face: 4, 7, 8); again len = 2 * m * lines (m = 3).
  *   on_device as for pdg_set_w.  Kept until the next pdg_set_inflow or a model change
  *   (which resets it to zero).  Time steps that make |beta| > 1 (dt < 0) are not
  *   supported on inflow axes (pdg_step returns PDG_ERR_UNSUPPORTED).

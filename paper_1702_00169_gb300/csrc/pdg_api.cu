@@ -241,12 +241,15 @@ int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov,
   p.ncell = c->N[axis];
   const int m = c->model.m, nv = c->model.nv;
   if (c->model.kind == PDG_MODEL_ISOTHERMAL_D2Q9) {
-    // populations 1 + axis (+lambda e_axis) and 3 + axis (-lambda e_axis)
+    // populations 1 + axis (+lambda e_axis) and 3 + axis (-lambda e_axis); each is the
+    // first of the three populations entering through its face
     p.ntf = 2;
     p.tfield[0] = 1 + axis;
     p.tdir[0] = +1;
     p.tfield[1] = 3 + axis;
     p.tdir[1] = -1;
+    p.fbnent = 3;
+    p.fbent[0] = p.fbent[1] = 0;
   } else {
     p.ntf = 2 * m;
     for (int k = 0; k < m; ++k) {
@@ -254,7 +257,9 @@ int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov,
       p.tdir[2 * k] = +1;
       p.tfield[2 * k + 1] = k * nv + 2 * axis + 1;
       p.tdir[2 * k + 1] = -1;
+      p.fbent[2 * k] = p.fbent[2 * k + 1] = k;
     }
+    p.fbnent = m;
   }
   p.dslot = sp.dslot;
   p.nops = sp.nops;
@@ -347,13 +352,24 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, PdgDiagPass* out) {
   }
   const int in = sp.dslot_in, outs = sp.dslot_in == PDG_Q9_DIAG ? PDG_Q9_SCRATCH : PDG_Q9_DIAG;
   static const int sx[4] = {+1, -1, -1, +1}, sy[4] = {+1, +1, -1, -1};   // populations 5-8
+  // entry of populations 5-8 among the three entering through their x / y face:
+  // low x {1, 5, 8}, high x {3, 6, 7}, low y {2, 5, 6}, high y {4, 7, 8}
+  static const int xent[4] = {1, 1, 2, 2}, yent[4] = {1, 2, 1, 2};
   p.npop = 4;
   for (int i = 0; i < 4; ++i) {
     p.fin[i] = c->f + (long long)(in + i) * c->npoints;
     p.fout[i] = c->f + (long long)(outs + i) * c->npoints;
     p.sx[i] = sx[i];
     p.sy[i] = sy[i];
+    p.bxside[i] = sx[i] > 0 ? 0 : 1;
+    p.byside[i] = sy[i] > 0 ? 0 : 1;
+    p.bxent[i] = xent[i];
+    p.byent[i] = yent[i];
   }
+  p.perx = c->periodic[0] ? 1 : 0;
+  p.pery = c->periodic[1] ? 1 : 0;
+  p.fbx = c->periodic[0] ? nullptr : c->fb[0];
+  p.fby = c->periodic[1] ? nullptr : c->fb[1];
   p.n = c->n;
   p.ncx = c->N[0];
   p.ncy = c->N[1];
@@ -765,8 +781,6 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
     return fail(c, PDG_ERR_UNSUPPORTED, "shallow water needs dim = 2");
   const bool q9 = d->kind == PDG_MODEL_ISOTHERMAL_D2Q9;
   if (q9 && c->dim != 2) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 needs dim = 2");
-  if (q9 && !(c->periodic[0] && c->periodic[1]))
-    return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 runs on periodic meshes only");
   if (q9 && !(d->theta > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 needs theta > 0");
   PdgModel M{};
   M.kind = d->kind;

@@ -694,9 +694,8 @@ __device__ __forceinline__ int seg_begin(int s, int N, int S) { return (int)(((l
 // Inflow boundary value of transported population phi on line `line` (non-periodic axes).
 template <class T>
 __device__ __forceinline__ T inflow_value(const PdgPass& p, int phi, int line) {
-  const int k = p.tfield[phi] / p.model.nv;
   const int side = p.tdir[phi] > 0 ? 0 : 1;
-  return ld<T>(p.fb + ((long long)(side * p.model.m + k) * p.nlines + line));
+  return ld<T>(p.fb + ((long long)(side * p.fbnent + p.fbent[phi]) * p.nlines + line));
 }
 
 template <int NP, class T>

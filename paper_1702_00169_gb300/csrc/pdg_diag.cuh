@@ -46,6 +46,11 @@ struct DiagGeom {
   int X0, Y0, wx, wy, ncol, nrow;
   const int* colx;         // [ncol + 1]: x of traversal node 0 of region column j - 1
   const long long* rowy;   // [nrow + 1]: offset of traversal node row 0 of region row r - 1
+  // inflow faces: when bx (by) is set the region starts at the domain's inflow face and
+  // the values entering column 0 (row 0) are the boundary data fbx (fby)
+  int bx, by;
+  const double* fbx;       // [P_y] values of this population at its x inflow face
+  const double* fby;       // [P_x] values at its y inflow face
 };
 
 // Offset of node (iy, ix) (traversal orientation) of region cell (j, r), j, r >= -1.
@@ -83,10 +88,25 @@ __device__ __forceinline__ void diag_stage(const DiagGeom& g, int t, T* fb, T* l
     cp_async8(fb + c * RS + q, g.fin + diag_off<NP>(g, j, t - j, q / NP, q % NP));
   }
   const int tid = threadIdx.x;
-  if (jlo == 0 && tid < NP)   // column 0 at row t: +x face of the cell upwind of it
-    cp_async8(lbnd + tid, g.fin + diag_off<NP>(g, -1, t, tid, NP - 1));
-  if (jhi == t && tid >= NP && tid < 2 * NP)   // row 0 at column t: +y face of the cell below
-    cp_async8(bbnd + (tid - NP), g.fin + diag_off<NP>(g, t, -1, NP - 1, tid - NP));
+  if (jlo == 0 && tid < NP) {   // column 0 at row t: +x face of the cell upwind of it
+    if (g.bx) {                 // the inflow face: boundary value at the node's y point
+      const int tr = wrap_cell(g.Y0 - g.wy + t, g.ncy);   // y may be periodic
+      const int pcy = g.sy > 0 ? tr : g.ncy - 1 - tr;
+      cp_async8(lbnd + tid, g.fbx + pcy * NP + (g.sy > 0 ? tid : NP - 1 - tid));
+    } else {
+      cp_async8(lbnd + tid, g.fin + diag_off<NP>(g, -1, t, tid, NP - 1));
+    }
+  }
+  if (jhi == t && tid >= NP && tid < 2 * NP) {   // row 0 at column t: +y face of the cell below
+    const int ix = tid - NP;
+    if (g.by) {
+      const int tc = wrap_cell(g.X0 - g.wx + t, g.ncx);   // x may be periodic
+      const int pcx = g.sx > 0 ? tc : g.ncx - 1 - tc;
+      cp_async8(bbnd + ix, g.fby + pcx * NP + (g.sx > 0 ? ix : NP - 1 - ix));
+    } else {
+      cp_async8(bbnd + ix, g.fin + diag_off<NP>(g, t, -1, NP - 1, ix));
+    }
+  }
 }
 
 template <int NP, class T>
@@ -109,13 +129,19 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
   g.row = p.row;
   g.X0 = txi * p.tx;
   g.Y0 = tyi * p.ty;
-  g.wx = C.wx;
-  g.wy = C.wy;
+  // periodic axis: the truncated start; inflow axis: at most back to the inflow face
+  g.wx = p.perx ? C.wx : min(C.wx, g.X0);
+  g.wy = p.pery ? C.wy : min(C.wy, g.Y0);
+  g.bx = !p.perx && g.X0 - g.wx == 0;
+  g.by = !p.pery && g.Y0 - g.wy == 0;
+  const long long Py = (long long)p.ncy * NP;
+  g.fbx = p.fbx ? p.fbx + (long long)(p.bxside[pop] * 3 + p.bxent[pop]) * Py : nullptr;
+  g.fby = p.fby ? p.fby + (long long)(p.byside[pop] * 3 + p.byent[pop]) * p.row : nullptr;
   const int ox = min(p.tx, p.ncx - g.X0), oy = min(p.ty, p.ncy - g.Y0);
   g.ncol = ox + g.wx;
   g.nrow = oy + g.wy;
   const int T_steps = g.ncol + g.nrow - 1;
-  const int amax = min(p.tx + g.wx, p.ty + g.wy);   // longest anti-diagonal of any tile
+  const int amax = min(p.tx + C.wx, p.ty + C.wy);   // longest anti-diagonal of any tile
 
   // shared memory: BinvT[NN][NN] | rbuf[amax][RS] | fbuf[2][amax][RS] | Lt[2][ncol+1][NP] |
   //                Bt[2][ncol][NP] | lbnd[2][NP] | bbnd[2][NP] | rowy[nrow+1] | colx[ncol+1]
@@ -123,12 +149,12 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
   T* rbuf = BinvT + NN * NN;
   T* fbuf = rbuf + (size_t)amax * RS;
   T* Lt = fbuf + (size_t)2 * amax * RS;
-  T* Bt = Lt + (size_t)2 * (p.tx + g.wx + 1) * NP;
-  T* lbnd = Bt + (size_t)2 * (p.tx + g.wx) * NP;
+  T* Bt = Lt + (size_t)2 * (p.tx + C.wx + 1) * NP;
+  T* lbnd = Bt + (size_t)2 * (p.tx + C.wx) * NP;
   T* bbnd = lbnd + 2 * NP;
   long long* rowy = reinterpret_cast<long long*>(bbnd + 2 * NP);
-  int* colx = reinterpret_cast<int*>(rowy + (p.ty + g.wy + 1));
-  const int LtS = p.tx + g.wx + 1, BtS = p.tx + g.wx;   // per-parity strides (columns)
+  int* colx = reinterpret_cast<int*>(rowy + (p.ty + C.wy + 1));
+  const int LtS = p.tx + C.wx + 1, BtS = p.tx + C.wx;   // per-parity strides (columns)
   for (int i = threadIdx.x; i < NN * NN; i += blockDim.x) {
     const int row = i % NN, col = i / NN;   // BinvT[col][row] = Binv[row][col]
     BinvT[i] = cval<T>(&C.Binv[row * NN + col], &C.Binv_f[row * NN + col], 0);

@@ -126,7 +126,9 @@ struct PdgPass {
   int prec;                    // PDG_PREC_* of the state and arithmetic
   int periodic;                // 1: periodic lines; 0: inflow boundary data fb
   int dslot;                   // D2Q9 collision: state slot of population 5 (5 or 9)
-  const double* fb;            // non-periodic: inflow values [2 sides][m][nlines] (state format)
+  const double* fb;            // non-periodic: inflow values [2 sides][fbnent][nlines] (state format)
+  int fbnent;                  // entries per side of fb (m; 3 for D2Q9)
+  int fbent[2 * PDG_MAXM];     // entry of each transported population within its side
   PdgSrc src;                  // source stage around the collision (D2Q9), flags 0 = none
   PdgCoef coef[2];
   PdgModel model;
@@ -171,6 +173,12 @@ struct PdgDiagPass {
   const double* fin[4];
   double* fout[4];
   int sx[4], sy[4];
+  // inflow axes (per axis: 1 = periodic); boundary data [2 sides][3][lines] (lines = P_y
+  // for the x faces, P_x for the y faces) and each population's side and entry in it
+  int perx, pery;
+  const double* fbx;
+  const double* fby;
+  int bxside[4], bxent[4], byside[4], byent[4];
   int npop, n, ncx, ncy;
   long long row;          // points per row (P_x)
   int tx, ty, ntx, nty;   // tile shape and counts

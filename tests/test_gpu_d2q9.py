@@ -110,8 +110,8 @@ def test_moments_and_checkpoint():
 
 
 def test_unsupported_requests():
-    """dt <= 0, theta = 0 and non-periodic meshes are refused with PDG_ERR_UNSUPPORTED; a
-    batch refuses D2Q9 instances."""
+    """dt <= 0 and theta = 0 are refused with PDG_ERR_UNSUPPORTED; a batch refuses D2Q9
+    instances."""
     from paper_1702_00169_gb300 import pdg
     cfg = _cfg((2, 2), (2, 2), 1)
     w0 = oracle_w0(cfg)
@@ -126,11 +126,6 @@ def test_unsupported_requests():
     with pytest.raises(pdg.PdgError):
         pdg.Batch([s])
     s.close()
-    s2 = pdg.Solver(2, (2, 2), (2, 2), 1, periodic=(True, False))
-    with pytest.raises(pdg.PdgError) as e:
-        s2.set_model("isothermal_d2q9", 1.0)
-    assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
-    s2.close()
 
 
 @pytest.mark.parametrize("precision", [0, 1])

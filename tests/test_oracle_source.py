@@ -116,3 +116,27 @@ def test_m2s_second_order_and_palindrome():
     f = model.feq(w0) + 1e-3 * rng.standard_normal((1, 9) + mesh.shape)
     g = S.m2_step(f, tr, model, dt, om(dt), src)
     np.testing.assert_allclose(S.m2_step(g, tr, model, -dt, om(-dt), src), f, atol=1e-12)
+
+
+def test_hydrostatic_state_time_order():
+    """Section 5.1: at rest under gravity, with the exact hydrostatic state
+    rho_0 exp(-g y / c^2) as initial state and as inflow data on the y faces (x periodic),
+    M_2^s keeps the state to discretisation accuracy, and its error in time is of second
+    order (self-convergence of w at fixed mesh)."""
+    mesh = CartesianMesh(2, (2, 12), 2, periodic=(True, False))
+    model = M.Model(M.ISOTHERMAL_D2Q9, 2, 1.0)
+    g, c2 = 1.0, 1.0 / 3.0
+    Y = mesh.coords1d(1)[:, None] + 0 * mesh.coords1d(0)[None, :]
+    wex = np.stack([np.exp(-g * Y / c2), 0 * Y, 0 * Y])
+    fb = model.feq(wex)
+    tr = S.Transporter(mesh, model, 0.5, "direct", fb=fb)
+    src = Source(gravity=(0.0, -g))
+    T = 0.12
+    sols = []
+    for k in (3, 6, 12, 24):
+        f = S.run(S.initial_state(model, wex), tr, model, T / k, k, 2.0, "M2", source=src)
+        sols.append(model.moments(f))
+    assert np.linalg.norm(sols[-1][0] - wex[0]) / np.linalg.norm(wex[0]) < 1e-3
+    e = [np.linalg.norm(sols[i] - sols[i + 1]) for i in range(3)]
+    r = [e[i] / e[i + 1] for i in range(2)]
+    assert all(3.3 < x < 4.8 for x in r), r
