@@ -456,8 +456,6 @@ def main():
     args = parse_args()
     from paper_1702_00169_gb300 import workloads as W
     cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6, "d2q9": W.D2Q9_ISO}.get(args.workload, W.SW_D2Q4)
-    if args.inflow_x and cfg.kind == "isothermal_d2q9":
-        raise SystemExit("--inflow-x: the D2Q9 path runs on periodic meshes only")
     if args.source != "none" and cfg.kind != "isothermal_d2q9":
         raise SystemExit("--source: sources run on the D2Q9 workload (--workload d2q9)")
     if args.impl == "reference":
@@ -510,9 +508,13 @@ def main():
     if args.inflow_x:
         # inflow data: the initial equilibrium populations at the two x faces
         s.set_w(w0_dev)
-        f0 = s.get_f().reshape((cfg.m, 2 * cfg.dim) + tuple(reversed(cfg.npoints_axis)))
-        fb = np.ascontiguousarray(np.stack([f0[:, 0, ..., 0].reshape(cfg.m, -1),
-                                            f0[:, 1, ..., -1].reshape(cfg.m, -1)]))
+        f0 = s.get_f().reshape((cfg.groups, cfg.nv) + tuple(reversed(cfg.npoints_axis)))
+        if cfg.kind == "isothermal_d2q9":
+            # populations entering through the low x face (1, 5, 8) and the high x face (3, 6, 7)
+            fb = np.ascontiguousarray(np.stack([f0[0, [1, 5, 8], :, 0], f0[0, [3, 6, 7], :, -1]]))
+        else:
+            fb = np.ascontiguousarray(np.stack([f0[:, 0, ..., 0].reshape(cfg.m, -1),
+                                                f0[:, 1, ..., -1].reshape(cfg.m, -1)]))
     torch.cuda.synchronize()
     dev_uuid = None
     try:
