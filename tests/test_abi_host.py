@@ -145,3 +145,51 @@ def test_inflow_validation_host(pdg):
             s.set_inflow(axis, np.zeros(n))
         assert e.value.status == pdg.PDG_ERR_ARG
     s.close()
+
+
+def test_d2q9_and_source_validation(pdg):
+    """D2Q9 model checks and pdg_set_source argument checks (no device memory is touched:
+    the gravity-only source allocates nothing)."""
+    s3 = pdg.Solver(3, (2, 2, 2), (2, 2, 2), 1)
+    with pytest.raises(pdg.PdgError) as e:
+        s3.set_model("isothermal_d2q9", 1.0)
+    assert e.value.status == pdg.PDG_ERR_UNSUPPORTED           # D2Q9 is 2-D
+    s3.close()
+    s = pdg.Solver(2, (2, 2), (2, 2), 2)
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_source(gravity=(0.0, -1.0))
+    assert e.value.status == pdg.PDG_ERR_STATE                 # no model yet
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_model("isothermal_d2q9", 1.0, theta=0.0)
+    assert e.value.status == pdg.PDG_ERR_UNSUPPORTED           # the diagonal form needs theta > 0
+    s.set_model("isothermal_d2q9", 1.0)
+    i = s.info()
+    assert (i.m, i.nv, i.nfields, i.w_len, i.f_len) == (3, 9, 9, 3 * i.npoints, 9 * i.npoints)
+    s.set_source(gravity=(0.0, -1.0))                          # accepted, nothing allocated
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_source(gravity=(0.0, -1.0), theta=1.5)
+    assert e.value.status == pdg.PDG_ERR_ARG
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_source(K_s=-1.0)
+    assert e.value.status == pdg.PDG_ERR_ARG
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_source(gravity=(float("nan"), 0.0))
+    assert e.value.status == pdg.PDG_ERR_ARG
+    s.set_source()                                             # removes the source
+    s.set_model("shallow_water", 8.0)
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_source(gravity=(0.0, -1.0))
+    assert e.value.status == pdg.PDG_ERR_UNSUPPORTED           # sources: D2Q9 only
+    s.close()
+
+
+def test_diagonal_launch_override_validation(pdg):
+    s = pdg.Solver(2, (2, 2), (2, 2), 2)
+    for bad in ((32, 8, 8), (520, 8, 8), (100, 8, 8), (256, 0, 8)):
+        with pytest.raises(pdg.PdgError):
+            s.set_launch(4, *bad)
+    s.set_launch(4, 256, 40, 30)
+    assert s.get_launch(4) == (256, 40, 30)
+    s.set_launch(4, 0, 0, 0)
+    assert s.get_launch(4) == (0, 0, 0)
+    s.close()
