@@ -23,14 +23,36 @@ W = 4/9 (rest), 1/9 (axis), 1/36 (diagonal).  Its second moment is the isotherma
 flux Pi = rho c^2 I + rho u u^T (the paper prints the yy entry without its rho; the
 moment identity fixes it).  Arrays keep the layout (groups, populations, *grid) with
 one group of nine populations.
+
+D3Q19 (one of the lattices of the paper's 3-D scaling runs, Section 4.5; the paper
+prints no 3-D equilibrium): the same polynomial equilibrium for the 3-D isothermal
+Euler variables w = (rho, rho u), c = lambda/sqrt(3), on the velocities 0, the six
+lambda (+-e_a) (order +x, -x, +y, -y, +z, -z) and the twelve lambda (+-e_a +- e_b),
+four per plane in the order xy, xz, yz, each as (+,+), (-,+), (-,-), (+,-); weights
+1/3, 1/18, 1/36.
 """
 import numpy as np
 
-ADVECTION, SHALLOW_WATER, EULER, ISOTHERMAL_D2Q9 = 0, 1, 2, 3
+ADVECTION, SHALLOW_WATER, EULER, ISOTHERMAL_D2Q9, ISOTHERMAL_D3Q19 = 0, 1, 2, 3, 4
 
 D2Q9_XI = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]],
                    dtype=np.float64)
 D2Q9_W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def _d3q19():
+    xi = [[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]]
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        for sa, sb in ((1, 1), (-1, 1), (-1, -1), (1, -1)):
+            v = [0, 0, 0]
+            v[a], v[b] = sa, sb
+            xi.append(v)
+    return np.array(xi, dtype=np.float64)
+
+
+D3Q19_XI = _d3q19()
+D3Q19_W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+LATTICES = {ISOTHERMAL_D2Q9: (D2Q9_XI, D2Q9_W), ISOTHERMAL_D3Q19: (D3Q19_XI, D3Q19_W)}
 
 
 class Model:
@@ -50,24 +72,25 @@ class Model:
             self.m = 3
         elif kind == EULER:
             self.m = self.dim + 2
-        elif kind == ISOTHERMAL_D2Q9:
-            assert self.dim == 2
-            self.m = 3
+        elif kind in LATTICES:
+            assert self.dim == LATTICES[kind][0].shape[1]
+            self.m = self.dim + 1
         else:
             raise ValueError(kind)
-        self.nv = 9 if kind == ISOTHERMAL_D2Q9 else 2 * self.dim
-        self.groups = 1 if kind == ISOTHERMAL_D2Q9 else self.m
+        self.lattice = kind in LATTICES
+        self.nv = len(LATTICES[kind][1]) if self.lattice else 2 * self.dim
+        self.groups = 1 if self.lattice else self.m
 
     @property
     def sound_speed(self):
-        """D2Q9: c = lambda / sqrt(3)."""
+        """D2Q9 / D3Q19: c = lambda / sqrt(3)."""
         return self.lam / np.sqrt(3.0)
 
     def velocities(self):
         """(n_v, D) array: row i is v_i; DnQ2n order +e_1, -e_1, +e_2, -e_2, ...;
         D2Q9 in the order of the module doc."""
-        if self.kind == ISOTHERMAL_D2Q9:
-            return self.lam * D2Q9_XI
+        if self.lattice:
+            return self.lam * LATTICES[self.kind][0]
         V = np.zeros((self.nv, self.dim))
         for a in range(self.dim):
             V[2 * a, a] = self.lam
@@ -77,11 +100,11 @@ class Model:
     def moments(self, f):
         """eq. (2.2) w = P f.  DnQ2n: w_k = sum_i f_{k,i}, f of shape (m, 2D, *grid).
         D2Q9: f of shape (1, 9, *grid), w = (sum_i f_i, sum_i f_i v_i)."""
-        if self.kind == ISOTHERMAL_D2Q9:
+        if self.lattice:
             V = self.velocities()
             g = f[0]
-            return np.stack([np.sum(g, axis=0), np.tensordot(V[:, 0], g, axes=(0, 0)),
-                             np.tensordot(V[:, 1], g, axes=(0, 0))])
+            return np.stack([np.sum(g, axis=0)] + [np.tensordot(V[:, a], g, axes=(0, 0))
+                                                   for a in range(self.dim)])
         return np.sum(f, axis=1)
 
     def flux(self, w):
@@ -89,12 +112,15 @@ class Model:
         D = self.dim
         if self.kind == ADVECTION:
             return np.stack([self.a[a] * w for a in range(D)])
-        if self.kind == ISOTHERMAL_D2Q9:
-            rho, mx, my = w[0], w[1], w[2]
+        if self.lattice:
+            rho, mom = w[0], w[1:]
             c2 = self.sound_speed ** 2
-            qx = np.stack([mx, mx * mx / rho + rho * c2, mx * my / rho])
-            qy = np.stack([my, mx * my / rho, my * my / rho + rho * c2])
-            return np.stack([qx, qy])
+            out = []
+            for a in range(self.dim):
+                comps = [mom[a]] + [mom[a] * mom[b] / rho + (rho * c2 if a == b else 0.0)
+                                    for b in range(self.dim)]
+                out.append(np.stack(comps))
+            return np.stack(out)
         if self.kind == SHALLOW_WATER:
             h, hu, hv = w[0], w[1], w[2]
             u, v = hu / h, hv / h
@@ -120,15 +146,16 @@ class Model:
     def feq(self, w):
         """DnQ2n: f^eq_{k,i} = w_k/(2D) + (v_i . q_k)/(2 lambda^2), shape (m, 2D, *grid).
         D2Q9: the polynomial equilibrium of the module doc, shape (1, 9, *grid)."""
-        if self.kind == ISOTHERMAL_D2Q9:
+        if self.lattice:
+            W = LATTICES[self.kind][1]
             rho = w[0]
-            u = np.stack([w[1] / rho, w[2] / rho])
+            u = [w[1 + a] / rho for a in range(self.dim)]
             c2 = self.sound_speed ** 2
-            uu = u[0] * u[0] + u[1] * u[1]
-            out = np.empty((1, 9) + w.shape[1:])
+            uu = sum(ua * ua for ua in u)
+            out = np.empty((1, self.nv) + w.shape[1:])
             for i, v in enumerate(self.velocities()):
-                uv = u[0] * v[0] + u[1] * v[1]
-                out[0, i] = D2Q9_W[i] * rho * (1.0 + uv / c2 + uv * uv / (2.0 * c2 * c2) - uu / (2.0 * c2))
+                uv = sum(u[a] * v[a] for a in range(self.dim))
+                out[0, i] = W[i] * rho * (1.0 + uv / c2 + uv * uv / (2.0 * c2 * c2) - uu / (2.0 * c2))
             return out
         q = self.flux(w)                                  # (D, m, *grid)
         V = self.velocities()

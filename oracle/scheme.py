@@ -22,7 +22,7 @@ import numpy as np
 
 from .dg import CartesianMesh
 from .source import source_step
-from .transport import DirectTransport, bloch_transport, bloch_transport_2d
+from .transport import DirectTransport, bloch_transport, bloch_transport_2d, bloch_transport_planes
 
 
 def collision(f, model, omega):
@@ -68,8 +68,11 @@ class Transporter:
             nu = 2.0 * abs(v[a]) * delta / self.mesh.h[a]
             return bloch_transport(g, self.mesh.axis_np(a), 1 if v[a] > 0 else -1, self.mesh.d, nu,
                                    self.theta)
-        assert self.mesh.dim == 2
-        return bloch_transport_2d(g, v, self.mesh.h, self.mesh.d, delta, self.theta)
+        if self.mesh.dim == 2:
+            return bloch_transport_2d(g, v, self.mesh.h, self.mesh.d, delta, self.theta)
+        if nz.size == 2:
+            return bloch_transport_planes(g, v, self.mesh.h, self.mesh.d, delta, self.theta)
+        raise NotImplementedError("Fourier form for velocities with three nonzero components")
 
     def __call__(self, f, delta):
         out = np.empty_like(f)

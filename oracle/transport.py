@@ -149,3 +149,21 @@ def bloch_transport_2d(field, v, h, d, delta, theta=0.5):
     if v[0] < 0:
         fn = fn[:, ::-1]
     return np.ascontiguousarray(fn)
+
+
+def bloch_transport_planes(field, v, h, d, delta, theta=0.5):
+    """Solve (*) on a periodic 3-D mesh for a velocity with exactly one zero component c
+    (the edge velocities of D3Q19).  The operator acts along the other two axes only, so
+    every plane of points normal to c is an independent 2-D problem, solved by
+    ``bloch_transport_2d`` (field shape (P_z, P_y, P_x))."""
+    v = np.asarray(v, dtype=np.float64)
+    c = int(np.flatnonzero(v == 0)[0])
+    a, b = [x for x in range(3) if x != c]
+    f = np.asarray(field, dtype=np.float64)
+    out = np.empty_like(f)
+    npc = 2 - c                                  # numpy axis of geometric axis c
+    for k in range(f.shape[npc]):
+        sl = [slice(None)] * 3
+        sl[npc] = k
+        out[tuple(sl)] = bloch_transport_2d(f[tuple(sl)], (v[a], v[b]), (h[a], h[b]), d, delta, theta)
+    return out
