@@ -70,6 +70,11 @@ def collision_flops(kind, dim):
         # quadratic bases (4 x 3); s_x + s_y, s_y - s_x (2); nine e_i (8 adds); W_i rho (3 mul);
         # relaxation (9 x 3)
         return 18 + 1 + 4 + 4 + 12 + 2 + 8 + 3 + 27
+    if kind == "isothermal_d3q19":
+        # rho, j (18 + 3 x 9 adds); 1/rho; s (6 mul); base (6); axis bases (3 x 3) and the
+        # 12 e_i (2 x 6 adds); plane sums (6) and bases (6 x 3), 12 e_i; W_i rho (3 mul);
+        # relaxation (19 x 3)
+        return 45 + 1 + 6 + 6 + 9 + 6 + 6 + 18 + 12 + 3 + 57
     if kind == "shallow_water":
         return collision_flops_sw()
     if kind == "advection":
@@ -96,7 +101,7 @@ def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--workload", default="shallow_water",
-                    choices=["shallow_water", "advection", "euler", "d2q9", "batched", "serving"])
+                    choices=["shallow_water", "advection", "euler", "d2q9", "d3q19", "batched", "serving"])
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=64.0)
@@ -455,7 +460,10 @@ def bench_serving(args):
 def main():
     args = parse_args()
     from paper_1702_00169_gb300 import workloads as W
-    cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6, "d2q9": W.D2Q9_ISO}.get(args.workload, W.SW_D2Q4)
+    cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6, "d2q9": W.D2Q9_ISO,
+           "d3q19": W.D3Q19_ISO}.get(args.workload, W.SW_D2Q4)
+    if args.inflow_x and cfg.kind == "isothermal_d3q19":
+        raise SystemExit("--inflow-x: the D3Q19 path runs on periodic meshes")
     if args.source != "none" and cfg.kind != "isothermal_d2q9":
         raise SystemExit("--source: sources run on the D2Q9 workload (--workload d2q9)")
     if args.impl == "reference":
@@ -472,9 +480,9 @@ def main():
         bench_serving(args)
         return
     if args.steps is None:
-        args.steps = {"euler": 20, "advection": 1000, "d2q9": 100}.get(args.workload, 1000)
+        args.steps = {"euler": 20, "advection": 1000, "d2q9": 100, "d3q19": 10}.get(args.workload, 1000)
     if args.warmup is None:
-        args.warmup = {"euler": 3, "d2q9": 5}.get(args.workload, 20)
+        args.warmup = {"euler": 3, "d2q9": 5, "d3q19": 3}.get(args.workload, 20)
 
     import torch
     ws, rank, local = dist_env()
@@ -562,7 +570,8 @@ def main():
     P = info.npoints
     F = info.nfields
     q9 = cfg.kind == "isothermal_d2q9"
-    pops_line = 2 if q9 else F // cfg.dim     # populations transported by one line pass
+    lattice = cfg.kind.startswith("isothermal")
+    pops_line = 2 if lattice else F // cfg.dim     # populations transported by one line pass
 
     def dominant(kms):
         """Kernel kind with the largest share of the timed region (0, 1 or 3)."""
@@ -570,7 +579,7 @@ def main():
 
     def kernel_work(kind):
         """(algorithmic bytes, algorithmic flops) of one launch of a kernel kind."""
-        if kind == 3:
+        if kind == 3:   # one launch = one plane orientation, four populations
             return 16.0 * 4 * P, 4 * P * diag_flops_per_dof(n)
         if kind == 1:
             return 16.0 * F * P, 2 * pops_line * P * transport_flops_per_dof(n) + P * collision_flops(cfg.kind, cfg.dim)
@@ -637,7 +646,7 @@ def main():
     # ---- roofline of the dominant kernel (from the live CUDA-event timing) ----
     kinds = {0: "transport pass (composed T T on the populations of the other axes)",
              1: "last-axis pass (T, collision, T)",
-             3: "D2Q9 diagonal transport pass (4 populations, tiled 2-D wavefront)"}
+             3: "diagonal transport pass (4 populations of one plane, tiled 2-D wavefront)"}
     k_dom = dominant(kms)
     avg_ms = kms[k_dom] / max(1, launches[k_dom])
     bytes_launch, flops_launch = kernel_work(k_dom)
@@ -672,6 +681,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg.name,
                        "model": ("isothermal Euler via D2Q9 (9 populations, 4 diagonal)" if q9 else
+                                 "isothermal Euler via D3Q19 (19 populations, 12 edge)" if lattice else
                                  f"{cfg.kind} via vectorial D{cfg.dim}Q{2 * cfg.dim} ({cfg.nfields} populations)"),
                        "mesh": (f"{'x'.join(map(str, cfg.n_macro))} macrocells x {'x'.join(map(str, cfg.n_sub))} "
                                 f"subcells, d={cfg.order}, {'x'.join(map(str, cfg.npoints_axis))} GL points, periodic"),

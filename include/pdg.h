@@ -32,7 +32,9 @@
  *                              +x, -x, +y, -y, +z, -z;
  *                              D2Q9 (PDG_MODEL_ISOTHERMAL_D2Q9): [9][P_y][P_x] in the
  *                              velocity order of Section 5.1, lambda (0,0), (1,0), (0,1),
- *                              (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
+ *                              (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1);
+ *                              D3Q19: [19][P_z][P_y][P_x] in the order of
+ *                              PDG_MODEL_ISOTHERMAL_D3Q19.
  */
 #ifndef PDG_H
 #define PDG_H
@@ -63,7 +65,7 @@ enum {
   PDG_MODEL_ADVECTION = 0,     /* m = 1, flux q^a = a_a w                          */
   PDG_MODEL_SHALLOW_WATER = 1, /* D = 2, m = 3, w = (h, hu, hv), gravity g          */
   PDG_MODEL_EULER = 2,         /* D = 2 or 3, m = D + 2, w = (rho, rho u, E), gamma */
-  PDG_MODEL_ISOTHERMAL_D2Q9 = 3 /* D = 2, m = 3, w = (rho, rho u_x, rho u_y), nine
+  PDG_MODEL_ISOTHERMAL_D2Q9 = 3, /* D = 2, m = 3, w = (rho, rho u_x, rho u_y), nine
                                   velocities lambda xi_i (xi in {-1,0,1}^2), equilibrium
                                   f_i = W_i rho (1 + u.v_i/c^2 + (u.v_i)^2/(2c^4)
                                   - u.u/(2c^2)), c = lambda/sqrt(3), W = 4/9, 1/9, 1/36
@@ -71,6 +73,15 @@ enum {
                                   cell to two upwind faces: their transport is the 2-D
                                   recurrence of pdg_step's documentation.  Periodic or
                                   inflow axes (pdg_set_inflow); 0 < theta <= 1; dt > 0. */
+  PDG_MODEL_ISOTHERMAL_D3Q19 = 4 /* D = 3, m = 4, w = (rho, rho u): the D3Q19 lattice of the
+                                  paper's 3-D scaling runs (Section 4.5), velocities 0, the
+                                  six lambda(+-e_a) (+x, -x, +y, -y, +z, -z) and the twelve
+                                  lambda(+-e_a +- e_b) (planes xy, xz, yz, each (+,+), (-,+),
+                                  (-,-), (+,-)); the equilibrium of the D2Q9 model with weights
+                                  1/3, 1/18, 1/36 (reading: the paper prints no 3-D one).
+                                  Each edge velocity acts in planes: its transport is the
+                                  D2Q9 diagonal recurrence on every plane of points.
+                                  Periodic meshes; 0 < theta <= 1; dt > 0. */
 };
 
 /* Time schemes (Section 3.2 and Section 5.1). */
@@ -130,11 +141,11 @@ typedef struct pdg_info {
   int dim;            /* D */
   int order;          /* d (d+1 GL points per cell and axis) */
   int m;              /* conserved variables (0 before pdg_set_model) */
-  int nv;             /* populations per variable, 2D (D2Q9: 9 populations in all) */
+  int nv;             /* populations per variable, 2D (D2Q9 / D3Q19: 9 / 19 in all) */
   int ncell[3];       /* N_a = n_macro_a n_sub_a (1 for absent axes) */
   int npts[3];        /* P_a = N_a (d+1) (1 for absent axes) */
   long long npoints;  /* prod_a P_a */
-  long long nfields;  /* populations in f: m * 2D (D2Q9: 9) */
+  long long nfields;  /* populations in f: m * 2D (D2Q9: 9, D3Q19: 19) */
   long long w_len;    /* m * npoints: doubles in w */
   long long f_len;    /* nfields * npoints: doubles in f */
   double h[3];        /* cell edge per axis */

@@ -134,6 +134,24 @@ int drain_timing(pdg_ctx* c) {
   return PDG_OK;
 }
 
+// Lattice models (one set of populations for all variables): D2Q9 and D3Q19.  Their
+// non-axis populations [diag, diag + ndiag) run in diagonal passes, out of place between
+// slots diag.. and scratch..; norient planes of velocity pairs (a, b).
+struct Lattice {
+  int slots, diag, scratch, ndiag, norient;
+};
+bool lattice_of(int kind, Lattice* L) {
+  if (kind == PDG_MODEL_ISOTHERMAL_D2Q9) {
+    *L = {PDG_Q9_SLOTS, PDG_Q9_DIAG, PDG_Q9_SCRATCH, 4, 1};
+    return true;
+  }
+  if (kind == PDG_MODEL_ISOTHERMAL_D3Q19) {
+    *L = {PDG_Q19_SLOTS, PDG_Q19_DIAG, PDG_Q19_SCRATCH, 12, 3};
+    return true;
+  }
+  return false;
+}
+
 // Launch shape heuristic for one pass (lines per block, segments, field groups)
 // with at most max_threads threads; ov (if ov[0] > 0) forces the shape.
 void choose_shape(const int* ov, int max_threads, int nlines, int ncell, int ntf, int W, int* lpb, int* nseg,
@@ -250,6 +268,14 @@ int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov,
     p.tdir[1] = -1;
     p.fbnent = 3;
     p.fbent[0] = p.fbent[1] = 0;
+  } else if (c->model.kind == PDG_MODEL_ISOTHERMAL_D3Q19) {
+    // populations 1 + 2 axis (+lambda e_axis) and 2 + 2 axis (-lambda e_axis); periodic only
+    p.ntf = 2;
+    p.tfield[0] = 1 + 2 * axis;
+    p.tdir[0] = +1;
+    p.tfield[1] = 2 + 2 * axis;
+    p.tdir[1] = -1;
+    p.fbnent = 1;
   } else {
     p.ntf = 2 * m;
     for (int k = 0; k < m; ++k) {
@@ -329,14 +355,20 @@ int launch_timed(pdg_ctx* c, const PdgPass& p, int kind) {
   return PDG_OK;
 }
 
-// Launch descriptor of a D2Q9 diagonal pass (populations 5-8, slots dslot_in.. -> the
-// other slot set).  The tile counts minimise the swept region of one block (output
-// cells plus the upwind start) times the number of blocks per SM.
-int make_diag(pdg_ctx* c, const PdgPassSpec& sp, PdgDiagPass* out) {
+// Launch descriptor of one orientation o of a diagonal pass: the four populations whose
+// velocity lies in plane (a, b) (D2Q9: 5-8 in the x-y plane; D3Q19: 7 + 4 o .. 10 + 4 o in
+// plane xy, xz, yz), read from slot set dslot_in and written to the other set.  The tile
+// counts minimise the swept region of one block (output cells plus the upwind start)
+// times the number of blocks per SM.
+int make_diag(pdg_ctx* c, const PdgPassSpec& sp, int o, PdgDiagPass* out) {
   PdgDiagPass& p = *out;
   std::memset(&p, 0, sizeof(p));
-  const double nux = 2.0 * c->model.lambda * sp.ddelta / c->h[0];
-  const double nuy = 2.0 * c->model.lambda * sp.ddelta / c->h[1];
+  Lattice L;
+  if (!lattice_of(c->model.kind, &L)) return fail(c, PDG_ERR_ARG, "internal: diagonal pass of a DnQ2n model");
+  static const int oa[3] = {0, 0, 1}, ob[3] = {1, 2, 2};
+  const int ax = oa[o], ay = ob[o], az = 3 - ax - ay;   // az: the plane axis in 3-D
+  const double nux = 2.0 * c->model.lambda * sp.ddelta / c->h[ax];
+  const double nuy = 2.0 * c->model.lambda * sp.ddelta / c->h[ay];
   // plans are cached: the width search costs up to a few ms on the host
   const PdgDiagCoef* hit = nullptr;
   for (const auto& e : c->diag_plans)
@@ -350,15 +382,15 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, PdgDiagPass* out) {
     if (c->diag_plans.size() >= 8) c->diag_plans.erase(c->diag_plans.begin());
     c->diag_plans.push_back({c->order, nux, nuy, c->theta, p.c});
   }
-  const int in = sp.dslot_in, outs = sp.dslot_in == PDG_Q9_DIAG ? PDG_Q9_SCRATCH : PDG_Q9_DIAG;
-  static const int sx[4] = {+1, -1, -1, +1}, sy[4] = {+1, +1, -1, -1};   // populations 5-8
+  const int in = sp.dslot_in, outs = sp.dslot_in == L.diag ? L.scratch : L.diag;
+  static const int sx[4] = {+1, -1, -1, +1}, sy[4] = {+1, +1, -1, -1};   // (+,+) (-,+) (-,-) (+,-)
   // entry of populations 5-8 among the three entering through their x / y face:
   // low x {1, 5, 8}, high x {3, 6, 7}, low y {2, 5, 6}, high y {4, 7, 8}
   static const int xent[4] = {1, 1, 2, 2}, yent[4] = {1, 2, 1, 2};
   p.npop = 4;
   for (int i = 0; i < 4; ++i) {
-    p.fin[i] = c->f + (long long)(in + i) * c->npoints;
-    p.fout[i] = c->f + (long long)(outs + i) * c->npoints;
+    p.fin[i] = c->f + (long long)(in + 4 * o + i) * c->npoints;
+    p.fout[i] = c->f + (long long)(outs + 4 * o + i) * c->npoints;
     p.sx[i] = sx[i];
     p.sy[i] = sy[i];
     p.bxside[i] = sx[i] > 0 ? 0 : 1;
@@ -366,14 +398,18 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, PdgDiagPass* out) {
     p.bxent[i] = xent[i];
     p.byent[i] = yent[i];
   }
-  p.perx = c->periodic[0] ? 1 : 0;
-  p.pery = c->periodic[1] ? 1 : 0;
-  p.fbx = c->periodic[0] ? nullptr : c->fb[0];
-  p.fby = c->periodic[1] ? nullptr : c->fb[1];
+  p.perx = c->periodic[ax] ? 1 : 0;
+  p.pery = c->periodic[ay] ? 1 : 0;
+  p.fbx = c->periodic[ax] ? nullptr : c->fb[ax];
+  p.fby = c->periodic[ay] ? nullptr : c->fb[ay];
   p.n = c->n;
-  p.ncx = c->N[0];
-  p.ncy = c->N[1];
-  p.row = c->P[0];
+  p.ncx = c->N[ax];
+  p.ncy = c->N[ay];
+  const long long stride[3] = {1, c->P[0], (long long)c->P[0] * c->P[1]};
+  p.sa = stride[ax];
+  p.sb = stride[ay];
+  p.sc = c->dim == 3 ? stride[az] : 0;
+  p.nplane = c->dim == 3 ? c->P[az] : 1;
   p.prec = c->model.prec;
   p.threads = c->dshape[0] ? c->dshape[0] : 512;
   const int slots = 152;   // one block per SM per wave (co-resident blocks share its FP64 pipe)
@@ -393,7 +429,7 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, PdgDiagPass* out) {
     for (int nty = 1; nty <= std::min(p.ncy, 64); ++nty) {
       const int ty = (p.ncy + nty - 1) / nty;
       if ((long long)ty * (nty - 1) >= p.ncy) continue;
-      const long long blocks = 4LL * ntx * nty;
+      const long long blocks = 4LL * ntx * nty * p.nplane;
       const long long waves = (blocks + slots - 1) / slots;
       const double region = (double)(tx + p.c.wx) * (double)(ty + p.c.wy), out = (double)tx * ty;
       const double cost = (double)waves * (out + (region - out) * NF / NN + 8.0 * (tx + p.c.wx + ty + p.c.wy));
@@ -411,20 +447,24 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, PdgDiagPass* out) {
 }
 
 int issue_diag(pdg_ctx* c, const PdgPassSpec& sp) {
-  PdgDiagPass p;
-  if (int r = make_diag(c, sp, &p)) return r;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->timing) {
-    e0 = get_event(c);
-    e1 = get_event(c);
-    if (!e0 || !e1) return fail(c, PDG_ERR_CUDA, "cudaEventCreate failed");
-    PDG_CUDA(c, cudaEventRecord(e0, c->stream));
-  }
-  int e = pdg_launch_diag(p, (void*)c->stream);
-  if (e != 0) return cuda_fail(c, (cudaError_t)e, "diag_kernel launch");
-  if (c->timing) {
-    PDG_CUDA(c, cudaEventRecord(e1, c->stream));
-    c->pending.push_back({3, e0, e1});
+  Lattice L;
+  if (!lattice_of(c->model.kind, &L)) return fail(c, PDG_ERR_ARG, "internal: diagonal pass of a DnQ2n model");
+  for (int o = 0; o < L.norient; ++o) {
+    PdgDiagPass p;
+    if (int r = make_diag(c, sp, o, &p)) return r;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+      e0 = get_event(c);
+      e1 = get_event(c);
+      if (!e0 || !e1) return fail(c, PDG_ERR_CUDA, "cudaEventCreate failed");
+      PDG_CUDA(c, cudaEventRecord(e0, c->stream));
+    }
+    int e = pdg_launch_diag(p, (void*)c->stream);
+    if (e != 0) return cuda_fail(c, (cudaError_t)e, "diag_kernel launch");
+    if (c->timing) {
+      PDG_CUDA(c, cudaEventRecord(e1, c->stream));
+      c->pending.push_back({3, e0, e1});
+    }
   }
   return PDG_OK;
 }
@@ -450,9 +490,11 @@ void balance_blocks(PdgPass* p) {
 
 int issue_pass(pdg_ctx* c, const PdgPassSpec& sp) {
   if (sp.axis == -2) {
-    PDG_CUDA(c, cudaMemcpyAsync(c->f + (long long)PDG_Q9_DIAG * c->npoints,
-                                c->f + (long long)PDG_Q9_SCRATCH * c->npoints,
-                                sizeof(double) * 4 * (size_t)c->npoints, cudaMemcpyDeviceToDevice, c->stream));
+    Lattice L;
+    if (!lattice_of(c->model.kind, &L)) return fail(c, PDG_ERR_ARG, "internal: copy of a DnQ2n model");
+    PDG_CUDA(c, cudaMemcpyAsync(c->f + (long long)L.diag * c->npoints, c->f + (long long)L.scratch * c->npoints,
+                                sizeof(double) * L.ndiag * (size_t)c->npoints, cudaMemcpyDeviceToDevice,
+                                c->stream));
     return PDG_OK;
   }
   if (sp.axis < 0) return issue_diag(c, sp);
@@ -563,8 +605,9 @@ int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSp
 // collision reads them where they are, and a final copy returns them to slots 5-8.
 int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
   if (int r = build_line_schedule(c, dt, nsteps, out)) return r;
-  if (c->model.kind != PDG_MODEL_ISOTHERMAL_D2Q9 || nsteps <= 0) return PDG_OK;
-  if (!(dt > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 diagonal transport needs dt > 0");
+  Lattice Lat;
+  if (!lattice_of(c->model.kind, &Lat) || nsteps <= 0) return PDG_OK;
+  if (!(dt > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "diagonal transport needs dt > 0");
   if (c->src.flags && c->scheme == PDG_SCHEME_M2KIN)
     return fail(c, PDG_ERR_UNSUPPORTED, "sources are defined for M2 and M2_collapsed");
   // diagonal sub-steps of each transport segment, in order
@@ -588,7 +631,7 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
   }
   std::vector<PdgPassSpec> res;
   res.reserve(out.size() + 3 * seg.size() + 1);
-  int slot = PDG_Q9_DIAG;
+  int slot = Lat.diag;
   size_t ci = 0;
   auto diag = [&](double delta) {
     PdgPassSpec d;
@@ -597,7 +640,7 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
     d.ddelta = delta;
     d.dslot_in = slot;
     res.push_back(d);
-    slot = (slot == PDG_Q9_DIAG) ? PDG_Q9_SCRATCH : PDG_Q9_DIAG;
+    slot = (slot == Lat.diag) ? Lat.scratch : Lat.diag;
   };
   for (auto sp : out) {
     if (pass_kind(sp)) {
@@ -611,7 +654,7 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
   }
   if (ci + 1 != seg.size()) return fail(c, PDG_ERR_ARG, "internal: schedule segments");
   for (double dl : seg[ci]) diag(dl);
-  if (slot != PDG_Q9_DIAG) {
+  if (slot != Lat.diag) {
     PdgPassSpec cp;
     std::memset(&cp, 0, sizeof(cp));
     cp.axis = -2;   // copy slots 9-12 back to 5-8
@@ -623,7 +666,8 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
 
 // State slots of the current model (D2Q9: nine populations and four scratch slots).
 long long state_slots(const pdg_ctx* c) {
-  return c->model.kind == PDG_MODEL_ISOTHERMAL_D2Q9 ? PDG_Q9_SLOTS : (long long)c->model.nf;
+  Lattice L;
+  return lattice_of(c->model.kind, &L) ? L.slots : (long long)c->model.nf;
 }
 
 // Allocate the kinetic state for the current model if it does not fit yet.
@@ -768,7 +812,7 @@ int pdg_create_mesh(pdg_ctx** out, int dim, const int n_macro[3], const int n_su
 
 int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   if (!c || !d) return PDG_ERR_ARG;
-  if (d->kind < PDG_MODEL_ADVECTION || d->kind > PDG_MODEL_ISOTHERMAL_D2Q9)
+  if (d->kind < PDG_MODEL_ADVECTION || d->kind > PDG_MODEL_ISOTHERMAL_D3Q19)
     return fail(c, PDG_ERR_ARG, "unknown model kind");
   if (d->scheme != PDG_SCHEME_M2 && d->scheme != PDG_SCHEME_M2_COLLAPSED && d->scheme != PDG_SCHEME_M2KIN)
     return fail(c, PDG_ERR_ARG, "unknown scheme");
@@ -779,21 +823,26 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   if (!(d->theta >= 0.0 && d->theta <= 1.0)) return fail(c, PDG_ERR_ARG, "theta must be in [0, 1]");
   if (d->kind == PDG_MODEL_SHALLOW_WATER && c->dim != 2)
     return fail(c, PDG_ERR_UNSUPPORTED, "shallow water needs dim = 2");
-  const bool q9 = d->kind == PDG_MODEL_ISOTHERMAL_D2Q9;
+  const bool q9 = d->kind == PDG_MODEL_ISOTHERMAL_D2Q9, q19 = d->kind == PDG_MODEL_ISOTHERMAL_D3Q19;
+  const bool lat = q9 || q19;
   if (q9 && c->dim != 2) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 needs dim = 2");
-  if (q9 && !(d->theta > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 needs theta > 0");
+  if (q19 && c->dim != 3) return fail(c, PDG_ERR_UNSUPPORTED, "D3Q19 needs dim = 3");
+  if (q19 && !(c->periodic[0] && c->periodic[1] && c->periodic[2]))
+    return fail(c, PDG_ERR_UNSUPPORTED, "D3Q19 runs on periodic meshes");
+  if (lat && !(d->theta > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "diagonal velocities need theta > 0");
   PdgModel M{};
   M.kind = d->kind;
   M.dim = c->dim;
-  M.m = d->kind == PDG_MODEL_ADVECTION ? 1 : ((d->kind == PDG_MODEL_SHALLOW_WATER || q9) ? 3 : c->dim + 2);
-  M.nv = q9 ? 9 : 2 * c->dim;
-  M.nf = q9 ? 9 : M.m * M.nv;
+  M.m = d->kind == PDG_MODEL_ADVECTION ? 1
+        : (d->kind == PDG_MODEL_SHALLOW_WATER ? 3 : (lat ? c->dim + 1 : c->dim + 2));
+  M.nv = q9 ? 9 : (q19 ? 19 : 2 * c->dim);
+  M.nf = lat ? M.nv : M.m * M.nv;
   M.lambda = d->lambda;
   M.omega = d->omega;
   for (int a = 0; a < 3; ++a) M.a[a] = d->a[a];
   M.gravity = d->gravity;
   M.gamma = d->gamma;
-  for (int i = 0; i < M.nv && !q9; ++i) {
+  for (int i = 0; i < M.nv && !lat; ++i) {
     const double s = (i % 2 == 0) ? 1.0 : -1.0;
     M.cadv[i] = 1.0 / (2.0 * c->dim) + s * d->a[i / 2] / (2.0 * d->lambda);
   }
@@ -1285,7 +1334,8 @@ int pdg_batch_create(pdg_batch** out, int n, pdg_ctx* const* ctxs, void* cuda_st
   if (n < 1 || !ctxs) return PDG_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i] || !ctxs[i]->has_model) return PDG_ERR_STATE;
-    if (ctxs[i]->model.kind == PDG_MODEL_ISOTHERMAL_D2Q9) return PDG_ERR_UNSUPPORTED;
+    Lattice L;
+    if (lattice_of(ctxs[i]->model.kind, &L)) return PDG_ERR_UNSUPPORTED;
   }
   pdg_batch* b = new (std::nothrow) pdg_batch();
   if (!b) return PDG_ERR_OOM;
@@ -1359,8 +1409,9 @@ int batch_prepare(pdg_batch* b, const double* dt, const int* nsteps) {
   for (int i = 0; i < n; ++i) {
     pdg_ctx* c = b->inst[i];
     if (!c->has_state) return bfail(b, PDG_ERR_STATE, "batch instance without state");
-    if (c->model.kind == PDG_MODEL_ISOTHERMAL_D2Q9)
-      return bfail(b, PDG_ERR_UNSUPPORTED, "D2Q9 instances run through pdg_step only");
+    Lattice L;
+    if (lattice_of(c->model.kind, &L))
+      return bfail(b, PDG_ERR_UNSUPPORTED, "D2Q9 / D3Q19 instances run through pdg_step only");
     if (nsteps[i] < 0 || !std::isfinite(dt[i])) return bfail(b, PDG_ERR_ARG, "bad dt or nsteps");
     std::vector<PdgPassSpec> sched;
     if (int r = build_schedule(c, dt[i], nsteps[i], sched)) return bfail(b, r, c->err);

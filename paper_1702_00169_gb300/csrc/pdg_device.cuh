@@ -20,7 +20,7 @@ namespace pdgdev {
 #define PDG_PREFETCH_DIST 2   // cells ahead prefetched into L2 on strided sweeps
 #endif
 
-enum { MV_ADV = 0, MV_SW = 1, MV_EU1 = 2, MV_EU2 = 3, MV_EU3 = 4, MV_NONE = 5, MV_D2Q9 = 6 };
+enum { MV_ADV = 0, MV_SW = 1, MV_EU1 = 2, MV_EU2 = 3, MV_EU3 = 4, MV_NONE = 5, MV_D2Q9 = 6, MV_D3Q19 = 7 };
 
 // ---------------------------------------------------------------------------
 // Double-float arithmetic.  Error-free transformations (all with explicit
@@ -390,6 +390,79 @@ struct Collide<MV_D2Q9, T> {
   }
 };
 
+// D3Q19 (order of PDG_Q19_*): f^eq_i = W_i rho e_i with the same e as D2Q9 per velocity,
+// s = 3 j / rho.  Edge velocities of plane (a, b) in the order (+,+), (-,+), (-,-), (+,-)
+// have s.xi = +-(s_a + s_b), +-(s_b - s_a).
+template <class T>
+__device__ __forceinline__ void d3q19_e(T rho, T jx, T jy, T jz, const PdgModel& M, T* e) {
+  const T three = from_double<T>(3.0);
+  const T ir = recip(rho);
+  const T s[3] = {three * (jx * ir), three * (jy * ir), three * (jz * ir)};
+  const T half = PDG_K(T, M, PDG_K_HALF);
+  const T base = from_double<T>(1.0) - PDG_K(T, M, PDG_K_SIXTH) * fma(s[0], s[0], fma(s[1], s[1], s[2] * s[2]));
+  e[0] = base;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T q = fma(half * s[a], s[a], base);
+    e[1 + 2 * a] = q + s[a];
+    e[2 + 2 * a] = q - s[a];
+  }
+  const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    const T t1 = s[pa[o]] + s[pb[o]], t2 = s[pb[o]] - s[pa[o]];
+    const T q1 = fma(half * t1, t1, base), q2 = fma(half * t2, t2, base);
+    e[7 + 4 * o] = q1 + t1;
+    e[8 + 4 * o] = q2 + t2;
+    e[9 + 4 * o] = q1 - t1;
+    e[10 + 4 * o] = q2 - t2;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void d3q19_moments(const T* v, T* rho, T* jx, T* jy, T* jz) {
+  *rho = ((((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) +
+          (((v[8] + v[9]) + (v[10] + v[11])) + ((v[12] + v[13]) + (v[14] + v[15])))) + ((v[16] + v[17]) + v[18]);
+  // x: axis 1 - 2; xy edges 7 - 8 - 9 + 10; xz edges 11 - 12 - 13 + 14
+  *jx = (v[1] - v[2]) + ((v[7] - v[8]) + (v[10] - v[9])) + ((v[11] - v[12]) + (v[14] - v[13]));
+  // y: axis 3 - 4; xy edges 7 + 8 - 9 - 10; yz edges 15 - 16 - 17 + 18
+  *jy = (v[3] - v[4]) + ((v[7] + v[8]) - (v[9] + v[10])) + ((v[15] - v[16]) + (v[18] - v[17]));
+  // z: axis 5 - 6; xz edges 11 + 12 - 13 - 14; yz edges 15 + 16 - 17 - 18
+  *jz = (v[5] - v[6]) + ((v[11] + v[12]) - (v[13] + v[14])) + ((v[15] + v[16]) - (v[17] + v[18]));
+}
+
+template <class T>
+struct Collide<MV_D3Q19, T> {
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) {
+    T rho, jx, jy, jz;
+    d3q19_moments<T>(v, &rho, &jx, &jy, &jz);
+    T e[19];
+    d3q19_e<T>(rho, jx, jy, jz, M, e);
+    const T a0 = PDG_K(T, M, PDG_K_Q9W0) * rho, a1 = PDG_K(T, M, PDG_K_Q9W1) * rho;
+    const T a2 = PDG_K(T, M, PDG_K_Q9W2) * rho;
+    const T om1 = PDG_K(T, M, PDG_K_OM1);
+    if constexpr (!__is_same(T, double)) {
+      v[0] = relax(om1, v[0], a0 * e[0]);
+#pragma unroll
+      for (int i = 1; i < 7; ++i) v[i] = relax(om1, v[i], a1 * e[i]);
+#pragma unroll
+      for (int i = 7; i < 19; ++i) v[i] = relax(om1, v[i], a2 * e[i]);
+    } else if (M.omega == 2.0) {
+      v[0] = fma(a0, e[0], -v[0]);
+#pragma unroll
+      for (int i = 1; i < 7; ++i) v[i] = fma(a1, e[i], -v[i]);
+#pragma unroll
+      for (int i = 7; i < 19; ++i) v[i] = fma(a2, e[i], -v[i]);
+    } else {
+      v[0] = fma(om1, v[0], a0 * e[0]);
+#pragma unroll
+      for (int i = 1; i < 7; ++i) v[i] = fma(om1, v[i], a1 * e[i]);
+#pragma unroll
+      for (int i = 7; i < 19; ++i) v[i] = fma(om1, v[i], a2 * e[i]);
+    }
+  }
+};
+
 template <class T>
 struct Collide<MV_NONE, T> {
   static __device__ __forceinline__ void run(T*, const PdgModel&) {}
@@ -409,12 +482,14 @@ template <> struct NFields<MV_EU3> { static constexpr int value = 30; };
 template <> struct NFields<MV_ADV> { static constexpr int value = 6; };
 template <> struct NFields<MV_NONE> { static constexpr int value = 1; };
 template <> struct NFields<MV_D2Q9> { static constexpr int value = 9; };
+template <> struct NFields<MV_D3Q19> { static constexpr int value = 19; };
 
 // State slot of population k at collision time (D2Q9: the diagonal populations 5-8 sit
 // in slots dslot..dslot+3, see PDG_Q9_SLOTS).
 template <int MV>
 __device__ __forceinline__ int coll_slot(int k, int dslot) {
   if constexpr (MV == MV_D2Q9) return k < PDG_Q9_DIAG ? k : dslot + (k - PDG_Q9_DIAG);
+  if constexpr (MV == MV_D3Q19) return k < PDG_Q19_DIAG ? k : dslot + (k - PDG_Q19_DIAG);
   return k;
 }
 

@@ -9,7 +9,7 @@ size_t pdg_diag_smem(const PdgDiagPass& p) {
   const size_t ncol = (size_t)p.tx + p.c.wx, nrow = (size_t)p.ty + p.c.wy;
   const size_t amax = ncol < nrow ? ncol : nrow;
   return sizeof(double) * (NN * NN + 3 * amax * (NN + 2) + 2 * (ncol + 1) * p.n + 2 * ncol * p.n + 4 * (size_t)p.n) +
-         sizeof(long long) * (nrow + 1) + sizeof(int) * (ncol + 1);
+         sizeof(long long) * (nrow + 1 + ncol + 1);
 }
 
 int pdg_launch_diag(const PdgDiagPass& p, void* stream) {

@@ -42,9 +42,9 @@ struct DiagGeom {
   const double* fin;
   double* fout;
   int sx, sy, ncx, ncy;
-  long long row;
+  long long sa, sb;        // point strides along the plane's axes a ("x") and b ("y")
   int X0, Y0, wx, wy, ncol, nrow;
-  const int* colx;         // [ncol + 1]: x of traversal node 0 of region column j - 1
+  const long long* colx;   // [ncol + 1]: offset of traversal node 0 of region column j - 1
   const long long* rowy;   // [nrow + 1]: offset of traversal node row 0 of region row r - 1
   // inflow faces: when bx (by) is set the region starts at the domain's inflow face and
   // the values entering column 0 (row 0) are the boundary data fbx (fby)
@@ -56,7 +56,7 @@ struct DiagGeom {
 // Offset of node (iy, ix) (traversal orientation) of region cell (j, r), j, r >= -1.
 template <int NP>
 __device__ __forceinline__ long long diag_off(const DiagGeom& g, int j, int r, int iy, int ix) {
-  return g.rowy[r + 1] + (long long)(g.sy * iy) * g.row + g.colx[j + 1] + g.sx * ix;
+  return g.rowy[r + 1] + (long long)(g.sy * iy) * g.sb + g.colx[j + 1] + (long long)(g.sx * ix) * g.sa;
 }
 
 // Asynchronous 8-byte copy global -> shared (cp.async, cached in L1) and its fences.
@@ -112,7 +112,10 @@ __device__ __forceinline__ void diag_stage(const DiagGeom& g, int t, T* fb, T* l
 template <int NP, class T>
 __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
   constexpr int NN = NP * NP, NF = 2 * NP - 1, RS = NN + 2;   // RS: 16-byte aligned rows
+  // block order: plane fastest (neighbouring planes share cache sectors), then tiles
   int b = blockIdx.x;
+  const int plane = b % p.nplane;
+  b /= p.nplane;
   const int txi = b % p.ntx;
   b /= p.ntx;
   const int tyi = b % p.nty;
@@ -120,13 +123,14 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
   const PdgDiagCoef& C = p.c;
 
   DiagGeom g;
-  g.fin = p.fin[pop];
-  g.fout = p.fout[pop];
+  g.fin = p.fin[pop] + (long long)plane * p.sc;
+  g.fout = p.fout[pop] + (long long)plane * p.sc;
   g.sx = p.sx[pop];
   g.sy = p.sy[pop];
   g.ncx = p.ncx;
   g.ncy = p.ncy;
-  g.row = p.row;
+  g.sa = p.sa;
+  g.sb = p.sb;
   g.X0 = txi * p.tx;
   g.Y0 = tyi * p.ty;
   // periodic axis: the truncated start; inflow axis: at most back to the inflow face
@@ -134,9 +138,9 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
   g.wy = p.pery ? C.wy : min(C.wy, g.Y0);
   g.bx = !p.perx && g.X0 - g.wx == 0;
   g.by = !p.pery && g.Y0 - g.wy == 0;
-  const long long Py = (long long)p.ncy * NP;
+  const long long Py = (long long)p.ncy * NP, Px = (long long)p.ncx * NP;
   g.fbx = p.fbx ? p.fbx + (long long)(p.bxside[pop] * 3 + p.bxent[pop]) * Py : nullptr;
-  g.fby = p.fby ? p.fby + (long long)(p.byside[pop] * 3 + p.byent[pop]) * p.row : nullptr;
+  g.fby = p.fby ? p.fby + (long long)(p.byside[pop] * 3 + p.byent[pop]) * Px : nullptr;
   const int ox = min(p.tx, p.ncx - g.X0), oy = min(p.ty, p.ncy - g.Y0);
   g.ncol = ox + g.wx;
   g.nrow = oy + g.wy;
@@ -145,6 +149,7 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
 
   // shared memory: BinvT[NN][NN] | rbuf[amax][RS] | fbuf[2][amax][RS] | Lt[2][ncol+1][NP] |
   //                Bt[2][ncol][NP] | lbnd[2][NP] | bbnd[2][NP] | rowy[nrow+1] | colx[ncol+1]
+  //                (rowy, colx: 64-bit offsets)
   T* BinvT = reinterpret_cast<T*>(sm);
   T* rbuf = BinvT + NN * NN;
   T* fbuf = rbuf + (size_t)amax * RS;
@@ -153,7 +158,7 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
   T* lbnd = Bt + (size_t)2 * (p.tx + C.wx) * NP;
   T* bbnd = lbnd + 2 * NP;
   long long* rowy = reinterpret_cast<long long*>(bbnd + 2 * NP);
-  int* colx = reinterpret_cast<int*>(rowy + (p.ty + C.wy + 1));
+  long long* colx = rowy + (p.ty + C.wy + 1);
   const int LtS = p.tx + C.wx + 1, BtS = p.tx + C.wx;   // per-parity strides (columns)
   for (int i = threadIdx.x; i < NN * NN; i += blockDim.x) {
     const int row = i % NN, col = i / NN;   // BinvT[col][row] = Binv[row][col]
@@ -161,11 +166,11 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
   }
   for (int j = threadIdx.x; j <= g.ncol; j += blockDim.x) {
     const int tc = wrap_cell(g.X0 - g.wx + j - 1, g.ncx);
-    colx[j] = g.sx > 0 ? tc * NP : (g.ncx - 1 - tc) * NP + (NP - 1);
+    colx[j] = (long long)(g.sx > 0 ? tc * NP : (g.ncx - 1 - tc) * NP + (NP - 1)) * g.sa;
   }
   for (int r = threadIdx.x; r <= g.nrow; r += blockDim.x) {
     const int tr = wrap_cell(g.Y0 - g.wy + r - 1, g.ncy);
-    rowy[r] = (long long)(g.sy > 0 ? tr * NP : (g.ncy - 1 - tr) * NP + (NP - 1)) * g.row;
+    rowy[r] = (long long)(g.sy > 0 ? tr * NP : (g.ncy - 1 - tr) * NP + (NP - 1)) * g.sb;
   }
   g.colx = colx;
   g.rowy = rowy;
@@ -274,13 +279,14 @@ __global__ void __launch_bounds__(512, 1) diag_kernel(const __grid_constant__ Pd
 template <class T>
 int launch_diag_typed(const PdgDiagPass& p, size_t smem, cudaStream_t st) {
   const int threads = p.threads;
-  const int blocks = p.ntx * p.nty * p.npop;
+  const long long blocks = (long long)p.ntx * p.nty * p.npop * p.nplane;
+  if (blocks > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
   auto go = [&](auto kern) -> int {
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return (int)e;
     }
-    kern<<<blocks, threads, smem, st>>>(p);
+    kern<<<(unsigned)blocks, threads, smem, st>>>(p);
     return (int)cudaGetLastError();
   };
   switch (p.n) {

@@ -64,7 +64,8 @@ enum {
   PDG_K_CADV = 6,   // omega (1/(2D) + s_i a_axis / (2 lambda)), 6 entries
   PDG_K_N = 12
 };
-// D2Q9 reuses the advection slots: omega W_0, omega W_axis, omega W_diag, 1/6, 1/lambda, lambda.
+// D2Q9 and D3Q19 reuse the advection slots: omega W_0, omega W_axis, omega W_diag (edge),
+// 1/6, 1/lambda, lambda.
 enum { PDG_K_Q9W0 = 6, PDG_K_Q9W1 = 7, PDG_K_Q9W2 = 8, PDG_K_SIXTH = 9, PDG_K_ILAM = 10, PDG_K_LAM = 11 };
 
 // D2Q9 state slots: populations 0-8 in the velocity order of Section 5.1, then four
@@ -74,6 +75,11 @@ enum { PDG_K_Q9W0 = 6, PDG_K_Q9W1 = 7, PDG_K_Q9W2 = 8, PDG_K_SIXTH = 9, PDG_K_IL
 #define PDG_Q9_SLOTS 13
 #define PDG_Q9_DIAG 5
 #define PDG_Q9_SCRATCH 9
+// D3Q19: populations 0-18 (rest, six axis, twelve edge velocities: four per plane xy, xz,
+// yz), then twelve scratch slots for the edge populations 7-18.
+#define PDG_Q19_SLOTS 31
+#define PDG_Q19_DIAG 7
+#define PDG_Q19_SCRATCH 19
 
 struct PdgModel {
   int kind;      // PDG_MODEL_*
@@ -166,9 +172,10 @@ struct PdgDiagCoef {
   float rtheta_f[1][2], c1_f[1][2], theta_f[1][2], omtheta_f[1][2], kx_f[1][2], ky_f[1][2];
 };
 
-// Launch descriptor of a diagonal pass: npop populations (traversal signs sx, sy) on an
-// ncx x ncy periodic cell grid; tiles of tx x ty output cells, each swept from wx
-// columns and wy rows upwind.
+// Launch descriptor of a diagonal pass: npop populations whose velocity has components
+// along two axes a ("x") and b ("y") (traversal signs sx, sy), on an ncx x ncy cell grid
+// of the (a, b) plane, repeated over nplane planes of points along the remaining axis;
+// tiles of tx x ty output cells, each swept from wx columns and wy rows upwind.
 struct PdgDiagPass {
   const double* fin[4];
   double* fout[4];
@@ -180,7 +187,9 @@ struct PdgDiagPass {
   const double* fby;
   int bxside[4], bxent[4], byside[4], byent[4];
   int npop, n, ncx, ncy;
-  long long row;          // points per row (P_x)
+  long long sa, sb;       // point strides along a and b
+  long long sc;           // point stride between planes
+  int nplane;             // planes (points along the third axis; 1 in 2-D)
   int tx, ty, ntx, nty;   // tile shape and counts
   int threads;            // threads per block
   int prec;

@@ -85,6 +85,43 @@ __global__ void get_w_q9_kernel(const double* __restrict__ f, double* __restrict
   }
 }
 
+// D3Q19: w = (rho, rho u) in slots 0-3 -> f = f^eq(w) in slots 0-18.
+template <class T>
+__global__ void set_feq_q19_kernel(double* __restrict__ f, long long P, const __grid_constant__ PdgModel M1) {
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+       pt += (long long)gridDim.x * blockDim.x) {
+    const T rho = from_double<T>(f[pt]);
+    const T ilam = PDG_K(T, M1, PDG_K_ILAM);
+    const T jx = from_double<T>(f[P + pt]) * ilam, jy = from_double<T>(f[2 * P + pt]) * ilam;
+    const T jz = from_double<T>(f[3 * P + pt]) * ilam;
+    T e[19];
+    d3q19_e<T>(rho, jx, jy, jz, M1, e);
+    const T a0 = PDG_K(T, M1, PDG_K_Q9W0) * rho, a1 = PDG_K(T, M1, PDG_K_Q9W1) * rho;
+    const T a2 = PDG_K(T, M1, PDG_K_Q9W2) * rho;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) st(f + (long long)i * P + pt, (i == 0 ? a0 : (i < 7 ? a1 : a2)) * e[i]);
+  }
+}
+
+// D3Q19: w = P f = (sum f_i, lambda sum f_i xi_i).
+template <class T>
+__global__ void get_w_q19_kernel(const double* __restrict__ f, double* __restrict__ w, long long P,
+                                 const __grid_constant__ PdgModel M) {
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+       pt += (long long)gridDim.x * blockDim.x) {
+    T v[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) v[i] = ld<T>(f + (long long)i * P + pt);
+    T rho, jx, jy, jz;
+    d3q19_moments<T>(v, &rho, &jx, &jy, &jz);
+    const T lam = PDG_K(T, M, PDG_K_LAM);
+    w[pt] = to_double(rho);
+    w[P + pt] = to_double(lam * jx);
+    w[2 * P + pt] = to_double(lam * jy);
+    w[3 * P + pt] = to_double(lam * jz);
+  }
+}
+
 __global__ void convert_kernel(double* __restrict__ f, long long n, int to_df) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -117,6 +154,7 @@ int pdg_model_variant(const PdgModel& m) {
     case PDG_MODEL_SHALLOW_WATER: return MV_SW;
     case PDG_MODEL_EULER: return m.dim == 1 ? MV_EU1 : (m.dim == 2 ? MV_EU2 : MV_EU3);
     case PDG_MODEL_ISOTHERMAL_D2Q9: return MV_D2Q9;
+    case PDG_MODEL_ISOTHERMAL_D3Q19: return MV_D3Q19;
   }
   return -1;
 }
@@ -143,12 +181,25 @@ int pdg_launch_set_feq(double* f, long long P, const PdgModel& m, void* stream) 
       else
         set_feq_q9_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
       return (int)cudaGetLastError();
+    case MV_D3Q19:
+      if (m1.prec == PDG_PREC_DF32)
+        set_feq_q19_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+      else
+        set_feq_q19_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+      return (int)cudaGetLastError();
   }
   return (int)cudaErrorInvalidValue;
 }
 
 int pdg_launch_get_w(const double* f, double* w, long long P, const PdgModel& m, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
+  if (m.kind == PDG_MODEL_ISOTHERMAL_D3Q19) {
+    if (m.prec == PDG_PREC_DF32)
+      get_w_q19_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+    else
+      get_w_q19_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+    return (int)cudaGetLastError();
+  }
   if (m.kind == PDG_MODEL_ISOTHERMAL_D2Q9) {
     if (m.prec == PDG_PREC_DF32)
       get_w_q9_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);

@@ -213,9 +213,10 @@ void pdg_model_constants(PdgModel* m) {
   m->k[PDG_K_HALFG] = 0.5 * m->gravity;
   m->k[PDG_K_GM1] = m->gamma - 1.0;
   m->k[PDG_K_HALF] = 0.5;
-  if (m->kind == 3) {  // D2Q9: lattice weights of Section 5.1
-    m->k[PDG_K_Q9W0] = om * (4.0 / 9.0);
-    m->k[PDG_K_Q9W1] = om * (1.0 / 9.0);
+  if (m->kind == 3 || m->kind == 4) {  // D2Q9 (Section 5.1) / D3Q19 lattice weights
+    const bool q19 = m->kind == 4;
+    m->k[PDG_K_Q9W0] = om * (q19 ? 1.0 / 3.0 : 4.0 / 9.0);
+    m->k[PDG_K_Q9W1] = om * (q19 ? 1.0 / 18.0 : 1.0 / 9.0);
     m->k[PDG_K_Q9W2] = om * (1.0 / 36.0);
     m->k[PDG_K_SIXTH] = 1.0 / 6.0;
     m->k[PDG_K_ILAM] = 1.0 / m->lambda;

@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpdg.so")
 
 PDG_OK = 0
 PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA, PDG_ERR_STATE, PDG_ERR_TIMEOUT, PDG_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
-PDG_MODEL_ADVECTION, PDG_MODEL_SHALLOW_WATER, PDG_MODEL_EULER, PDG_MODEL_ISOTHERMAL_D2Q9 = 0, 1, 2, 3
+PDG_MODEL_ADVECTION, PDG_MODEL_SHALLOW_WATER, PDG_MODEL_EULER = 0, 1, 2
+PDG_MODEL_ISOTHERMAL_D2Q9, PDG_MODEL_ISOTHERMAL_D3Q19 = 3, 4
 PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED, PDG_SCHEME_M2KIN = 0, 1, 2
 PDG_PREC_FP64 = 0
 PDG_PREC_DF32 = 1
@@ -24,7 +25,7 @@ PRECISION = {"fp64": PDG_PREC_FP64, "df32": PDG_PREC_DF32}
 PDG_OPT_COMPOSE_TT = 1
 
 KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER,
-        "isothermal_d2q9": PDG_MODEL_ISOTHERMAL_D2Q9}
+        "isothermal_d2q9": PDG_MODEL_ISOTHERMAL_D2Q9, "isothermal_d3q19": PDG_MODEL_ISOTHERMAL_D3Q19}
 SCHEME = {"M2": PDG_SCHEME_M2, "M2_collapsed": PDG_SCHEME_M2_COLLAPSED, "M2_kin": PDG_SCHEME_M2KIN}
 
 

@@ -21,6 +21,8 @@ synthetic and drawn from ``numpy.random.default_rng(seed)``):
 * isothermal D2Q9 (the model of the paper's Euler-with-gravity test, without the
   source): rho = 1 + 0.05 F_rho, u_a = 0.05 F_a with independent fields built like
   F above; w = (rho, rho u_x, rho u_y); lambda = 1 (sound speed 1/sqrt(3), Mach <= 0.09).
+* isothermal D3Q19 (a lattice of the paper's 3-D scaling runs): the same recipe in 3-D
+  (|k|_inf <= 2), w = (rho, rho u).
 """
 import math
 from dataclasses import dataclass, field
@@ -28,7 +30,7 @@ from typing import Tuple
 
 import numpy as np
 
-KINDS = ("advection", "shallow_water", "euler", "isothermal_d2q9")
+KINDS = ("advection", "shallow_water", "euler", "isothermal_d2q9", "isothermal_d3q19")
 
 
 @dataclass
@@ -52,17 +54,18 @@ class Config:
 
     @property
     def m(self):
-        return {"advection": 1, "shallow_water": 3, "euler": self.dim + 2, "isothermal_d2q9": 3}[self.kind]
+        return {"advection": 1, "shallow_water": 3, "euler": self.dim + 2, "isothermal_d2q9": 3,
+                "isothermal_d3q19": 4}[self.kind]
 
     @property
     def groups(self):
         """Leading axis of f: conserved variables (DnQ2n) or one set of nine (D2Q9)."""
-        return 1 if self.kind == "isothermal_d2q9" else self.m
+        return 1 if self.kind.startswith("isothermal") else self.m
 
     @property
     def nv(self):
-        """Populations per group: 2D (DnQ2n) or 9 (D2Q9)."""
-        return 9 if self.kind == "isothermal_d2q9" else 2 * self.dim
+        """Populations per group: 2D (DnQ2n), 9 (D2Q9) or 19 (D3Q19)."""
+        return {"isothermal_d2q9": 9, "isothermal_d3q19": 19}.get(self.kind, 2 * self.dim)
 
     @property
     def ncells(self):
@@ -112,7 +115,10 @@ EULER_D3Q6 = Config("euler_d3q6_32c3x4c3_d2", "euler", 3, (32, 32, 32), (4, 4, 4
 D2Q9_ISO = Config("isothermal_d2q9_64x64x8x8_d3", "isothermal_d2q9", 2, (64, 64), (8, 8), 3,
                   lam=1.0, steps=20, seed=6)
 
-CONFIGS = {c.name: c for c in (ADVECTION_D2Q4, SW_D2Q4, EULER_D3Q6, D2Q9_ISO)}
+D3Q19_ISO = Config("isothermal_d3q19_32c3x4c3_d2", "isothermal_d3q19", 3, (32, 32, 32), (4, 4, 4), 2,
+                   lam=1.0, steps=10, seed=7)
+
+CONFIGS = {c.name: c for c in (ADVECTION_D2Q4, SW_D2Q4, EULER_D3Q6, D2Q9_ISO, D3Q19_ISO)}
 
 
 def _grid(coords):
@@ -193,9 +199,10 @@ def initial_w(cfg, coords):
         p = 1.0
         E = p / (cfg.gamma - 1.0) + 0.5 * rho * sum(ua * ua for ua in u)
         return np.stack([rho] + [rho * ua for ua in u] + [E]).astype(np.float64)
-    if cfg.kind == "isothermal_d2q9":
-        Fr = _normalised_field(rng, D, 16, 4, 256)
-        Fu = [_normalised_field(rng, D, 16, 4, 256) for _ in range(D)]
+    if cfg.kind in ("isothermal_d2q9", "isothermal_d3q19"):
+        kmax, ref = (4, 256) if D == 2 else (2, 48)
+        Fr = _normalised_field(rng, D, 16, kmax, ref)
+        Fu = [_normalised_field(rng, D, 16, kmax, ref) for _ in range(D)]
         rho = np.broadcast_to(1.0 + 0.05 * Fr(X), shape)
         u = [np.broadcast_to(0.05 * Fu[a](X), shape) for a in range(D)]
         return np.stack([rho] + [rho * ua for ua in u]).astype(np.float64)
