@@ -17,9 +17,11 @@ dg          Generic D-dimensional assembly of the transport matrix L_h on an
             with the cofactor formula eq. (3.6).
 transport   The theta / Crank-Nicolson transport step (eq. (3.11)
             transport_cn, with the weight theta of Section 5.1), solved
-            (a) directly with a sparse LU and (b) by a Bloch/FFT closed form.
-models      Velocity sets (D2Q4 / D3Q6), the moment map P (eq. (2.2)), the
-            macroscopic fluxes and the equilibrium f_eq.
+            (a) directly with a sparse LU and (b) by a Bloch/FFT closed form
+            (per line, per 2-D mode, per 3-D mode).
+models      Velocity sets (DnQ2n, D2Q9, D3Q15, D3Q19, D3Q27), the moment map P
+            (eq. (2.2)), the macroscopic fluxes and the equilibrium f_eq.
+source      The source stage S_2 of M2^s (Section 3.2): gravity, penalisation.
 scheme      Collision integrator (eq. (3.12) collision_cn) and the palindromic
             step M2 = T(dt/2) C(dt) T(dt/2) of Section 3.2, in the naive order.
 

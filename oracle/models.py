@@ -30,29 +30,51 @@ Euler variables w = (rho, rho u), c = lambda/sqrt(3), on the velocities 0, the s
 lambda (+-e_a) (order +x, -x, +y, -y, +z, -z) and the twelve lambda (+-e_a +- e_b),
 four per plane in the order xy, xz, yz, each as (+,+), (-,+), (-,-), (+,-); weights
 1/3, 1/18, 1/36.
+
+D3Q15 and D3Q27 (the other two lattices of the Section 4.5 scaling runs; again no
+equilibrium is printed): the same polynomial equilibrium and c = lambda/sqrt(3) on
+  D3Q15: 0, the six axis velocities, the eight corners lambda (+-1, +-1, +-1);
+         weights 2/9, 1/9, 1/72;
+  D3Q27: 0, the six axis velocities, the twelve edges of D3Q19, the eight corners;
+         weights 8/27, 2/27, 1/54, 1/216
+(the standard weights that make the lattice moments isotropic up to fourth order).
+Corners are ordered z = +1 first, then z = -1, each as (x, y) = (+,+), (-,+), (-,-), (+,-).
 """
 import numpy as np
 
 ADVECTION, SHALLOW_WATER, EULER, ISOTHERMAL_D2Q9, ISOTHERMAL_D3Q19 = 0, 1, 2, 3, 4
+ISOTHERMAL_D3Q15, ISOTHERMAL_D3Q27 = 5, 6
 
 D2Q9_XI = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]],
                    dtype=np.float64)
 D2Q9_W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 
 
-def _d3q19():
-    xi = [[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]]
+_REST_AXIS = [[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]]
+
+
+def _edges():
+    xi = []
     for a, b in ((0, 1), (0, 2), (1, 2)):
         for sa, sb in ((1, 1), (-1, 1), (-1, -1), (1, -1)):
             v = [0, 0, 0]
             v[a], v[b] = sa, sb
             xi.append(v)
-    return np.array(xi, dtype=np.float64)
+    return xi
 
 
-D3Q19_XI = _d3q19()
+def _corners():
+    return [[sx, sy, sz] for sz in (1, -1) for sx, sy in ((1, 1), (-1, 1), (-1, -1), (1, -1))]
+
+
+D3Q19_XI = np.array(_REST_AXIS + _edges(), dtype=np.float64)
 D3Q19_W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
-LATTICES = {ISOTHERMAL_D2Q9: (D2Q9_XI, D2Q9_W), ISOTHERMAL_D3Q19: (D3Q19_XI, D3Q19_W)}
+D3Q15_XI = np.array(_REST_AXIS + _corners(), dtype=np.float64)
+D3Q15_W = np.array([2 / 9] + [1 / 9] * 6 + [1 / 72] * 8)
+D3Q27_XI = np.array(_REST_AXIS + _edges() + _corners(), dtype=np.float64)
+D3Q27_W = np.array([8 / 27] + [2 / 27] * 6 + [1 / 54] * 12 + [1 / 216] * 8)
+LATTICES = {ISOTHERMAL_D2Q9: (D2Q9_XI, D2Q9_W), ISOTHERMAL_D3Q19: (D3Q19_XI, D3Q19_W),
+            ISOTHERMAL_D3Q15: (D3Q15_XI, D3Q15_W), ISOTHERMAL_D3Q27: (D3Q27_XI, D3Q27_W)}
 
 
 class Model:
@@ -83,7 +105,7 @@ class Model:
 
     @property
     def sound_speed(self):
-        """D2Q9 / D3Q19: c = lambda / sqrt(3)."""
+        """D2Q9 / D3Q15 / D3Q19 / D3Q27: c = lambda / sqrt(3)."""
         return self.lam / np.sqrt(3.0)
 
     def velocities(self):

@@ -22,7 +22,7 @@ import numpy as np
 
 from .dg import CartesianMesh
 from .source import source_step
-from .transport import DirectTransport, bloch_transport, bloch_transport_2d, bloch_transport_planes
+from .transport import DirectTransport, bloch_transport, bloch_transport_2d, bloch_transport_3d, bloch_transport_planes
 
 
 def collision(f, model, omega):
@@ -36,8 +36,9 @@ class Transporter:
 
     method = "direct": sparse LU of the assembled eq. (3.7) system (tiny meshes);
     method = "bloch":  Fourier closed form (any size): per line for axis-aligned
-                       velocities, per 2-D mode for the diagonal D2Q9 velocities;
-                       the rest velocity of D2Q9 is not transported.
+                       velocities, per 2-D mode for the diagonal D2Q9 velocities and
+                       (plane by plane) the D3Q19 edges, per 3-D mode for the corners
+                       of D3Q15 / D3Q27; rest velocities are not transported.
     """
 
     def __init__(self, mesh, model, theta=0.5, method="direct", fb=None):
@@ -72,7 +73,7 @@ class Transporter:
             return bloch_transport_2d(g, v, self.mesh.h, self.mesh.d, delta, self.theta)
         if nz.size == 2:
             return bloch_transport_planes(g, v, self.mesh.h, self.mesh.d, delta, self.theta)
-        raise NotImplementedError("Fourier form for velocities with three nonzero components")
+        return bloch_transport_3d(g, v, self.mesh.h, self.mesh.d, delta, self.theta)
 
     def __call__(self, f, delta):
         out = np.empty_like(f)
