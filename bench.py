@@ -62,6 +62,13 @@ def diag_flops_per_dof(n):
     return 2.0 * n * n + 1.0 + 2.0 + 8.0 / n
 
 
+def corner_flops_per_dof(n):
+    """D3Q15 / D3Q27 corner transport, per DOF (n^3 nodes per cell): the dense Binv row
+    (n^3 FMA), r = f/theta (1 mul), the -c1 f term (1 FMA), the three face injections and
+    the three published faces (6 n^2 FMA per cell)."""
+    return 2.0 * n ** 3 + 1.0 + 2.0 + 12.0 / n
+
+
 def collision_flops(kind, dim):
     """Algorithmic flops of the collision at one point (FMA = 2)."""
     nv = 2 * dim
@@ -75,6 +82,15 @@ def collision_flops(kind, dim):
         # 12 e_i (2 x 6 adds); plane sums (6) and bases (6 x 3), 12 e_i; W_i rho (3 mul);
         # relaxation (19 x 3)
         return 45 + 1 + 6 + 6 + 9 + 6 + 6 + 18 + 12 + 3 + 57
+    if kind in ("isothermal_d3q15", "isothermal_d3q27"):
+        # moments (q - 1 adds for rho; each j_a sums 2 axis, 8 corner and (D3Q27) 8 edge
+        # populations); 1/rho; s (6); base (6); axis factors (3 x 3); D3Q27 edges as in
+        # D3Q19 (6 x 3 + 12); corner sums t (8), q (4 x 3), e (8); W_i rho (4 mul);
+        # relaxation (q x 3)
+        q = 27 if kind == "isothermal_d3q27" else 15
+        edges = 30 if q == 27 else 0
+        j_adds = 3 * (17 if q == 27 else 9)
+        return (q - 1) + j_adds + 1 + 6 + 6 + 9 + edges + 8 + 12 + 8 + 4 + 3 * q
     if kind == "shallow_water":
         return collision_flops_sw()
     if kind == "advection":
@@ -101,7 +117,8 @@ def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--workload", default="shallow_water",
-                    choices=["shallow_water", "advection", "euler", "d2q9", "d3q19", "batched", "serving"])
+                    choices=["shallow_water", "advection", "euler", "d2q9", "d3q19", "d3q15", "d3q27", "batched",
+                             "serving"])
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=64.0)
@@ -218,10 +235,11 @@ from paper_1702_00169_gb300 import workloads as W
 from oracle import models as OM, scheme as OS
 from oracle.dg import CartesianMesh
 cfg = W.CONFIGS[{cfg_name!r}]
-cfg = cfg.scaled(n_macro=tuple(min(8, x) for x in cfg.n_macro))
+cfg = cfg.scaled(n_macro=tuple(min(8 if cfg.dim < 3 else 2, x) for x in cfg.n_macro))
 mesh = CartesianMesh(cfg.dim, cfg.ncells, cfg.order, lengths=cfg.lengths[:cfg.dim])
 kind = {{"advection": OM.ADVECTION, "shallow_water": OM.SHALLOW_WATER, "euler": OM.EULER,
-        "isothermal_d2q9": OM.ISOTHERMAL_D2Q9}}[cfg.kind]
+        "isothermal_d2q9": OM.ISOTHERMAL_D2Q9, "isothermal_d3q19": OM.ISOTHERMAL_D3Q19,
+        "isothermal_d3q15": OM.ISOTHERMAL_D3Q15, "isothermal_d3q27": OM.ISOTHERMAL_D3Q27}}[cfg.kind]
 model = OM.Model(kind, cfg.dim, cfg.lam, a=cfg.a[:cfg.dim], gravity=cfg.gravity, gamma=cfg.gamma)
 w0 = W.initial_w(cfg, [mesh.coords1d(a) for a in range(cfg.dim)])
 tr = OS.Transporter(mesh, model, theta=cfg.theta, method="bloch")
@@ -461,9 +479,9 @@ def main():
     args = parse_args()
     from paper_1702_00169_gb300 import workloads as W
     cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6, "d2q9": W.D2Q9_ISO,
-           "d3q19": W.D3Q19_ISO}.get(args.workload, W.SW_D2Q4)
-    if args.inflow_x and cfg.kind == "isothermal_d3q19":
-        raise SystemExit("--inflow-x: the D3Q19 path runs on periodic meshes")
+           "d3q19": W.D3Q19_ISO, "d3q15": W.D3Q15_ISO, "d3q27": W.D3Q27_ISO}.get(args.workload, W.SW_D2Q4)
+    if args.inflow_x and cfg.kind in ("isothermal_d3q19", "isothermal_d3q15", "isothermal_d3q27"):
+        raise SystemExit("--inflow-x: the D3Qq paths run on periodic meshes")
     if args.source != "none" and cfg.kind != "isothermal_d2q9":
         raise SystemExit("--source: sources run on the D2Q9 workload (--workload d2q9)")
     if args.impl == "reference":
@@ -480,9 +498,10 @@ def main():
         bench_serving(args)
         return
     if args.steps is None:
-        args.steps = {"euler": 20, "advection": 1000, "d2q9": 100, "d3q19": 10}.get(args.workload, 1000)
+        args.steps = {"euler": 20, "advection": 1000, "d2q9": 100, "d3q19": 10, "d3q15": 4,
+                      "d3q27": 4}.get(args.workload, 1000)
     if args.warmup is None:
-        args.warmup = {"euler": 3, "d2q9": 5, "d3q19": 3}.get(args.workload, 20)
+        args.warmup = {"euler": 3, "d2q9": 5, "d3q19": 3, "d3q15": 3, "d3q27": 3}.get(args.workload, 20)
 
     import torch
     ws, rank, local = dist_env()
@@ -574,13 +593,15 @@ def main():
     pops_line = 2 if lattice else F // cfg.dim     # populations transported by one line pass
 
     def dominant(kms):
-        """Kernel kind with the largest share of the timed region (0, 1 or 3)."""
-        return max((0, 1, 3), key=lambda k: kms[k])
+        """Kernel kind with the largest share of the timed region (0, 1, 3 or 4)."""
+        return max((0, 1, 3, 4), key=lambda k: kms[k])
 
     def kernel_work(kind):
         """(algorithmic bytes, algorithmic flops) of one launch of a kernel kind."""
         if kind == 3:   # one launch = one plane orientation, four populations
             return 16.0 * 4 * P, 4 * P * diag_flops_per_dof(n)
+        if kind == 4:   # one launch = the eight corner populations
+            return 16.0 * 8 * P, 8 * P * corner_flops_per_dof(n)
         if kind == 1:
             return 16.0 * F * P, 2 * pops_line * P * transport_flops_per_dof(n) + P * collision_flops(cfg.kind, cfg.dim)
         return 16.0 * pops_line * P, 2 * pops_line * P * transport_flops_per_dof(n)
@@ -646,7 +667,8 @@ def main():
     # ---- roofline of the dominant kernel (from the live CUDA-event timing) ----
     kinds = {0: "transport pass (composed T T on the populations of the other axes)",
              1: "last-axis pass (T, collision, T)",
-             3: "diagonal transport pass (4 populations of one plane, tiled 2-D wavefront)"}
+             3: "diagonal transport pass (4 populations of one plane, tiled 2-D wavefront)",
+             4: "corner transport pass (8 populations, boxes swept as layer-by-layer wavefronts)"}
     k_dom = dominant(kms)
     avg_ms = kms[k_dom] / max(1, launches[k_dom])
     bytes_launch, flops_launch = kernel_work(k_dom)
@@ -681,7 +703,11 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg.name,
                        "model": ("isothermal Euler via D2Q9 (9 populations, 4 diagonal)" if q9 else
-                                 "isothermal Euler via D3Q19 (19 populations, 12 edge)" if lattice else
+                                 "isothermal Euler via D3Q19 (19 populations, 12 edge)"
+                                 if cfg.kind == "isothermal_d3q19" else
+                                 "isothermal Euler via D3Q15 (15 populations, 8 corner)"
+                                 if cfg.kind == "isothermal_d3q15" else
+                                 "isothermal Euler via D3Q27 (27 populations, 12 edge, 8 corner)" if lattice else
                                  f"{cfg.kind} via vectorial D{cfg.dim}Q{2 * cfg.dim} ({cfg.nfields} populations)"),
                        "mesh": (f"{'x'.join(map(str, cfg.n_macro))} macrocells x {'x'.join(map(str, cfg.n_sub))} "
                                 f"subcells, d={cfg.order}, {'x'.join(map(str, cfg.npoints_axis))} GL points, periodic"),

@@ -33,8 +33,8 @@
  *                              D2Q9 (PDG_MODEL_ISOTHERMAL_D2Q9): [9][P_y][P_x] in the
  *                              velocity order of Section 5.1, lambda (0,0), (1,0), (0,1),
  *                              (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1);
- *                              D3Q19: [19][P_z][P_y][P_x] in the order of
- *                              PDG_MODEL_ISOTHERMAL_D3Q19.
+ *                              D3Q19, D3Q15, D3Q27: [19 / 15 / 27][P_z][P_y][P_x] in
+ *                              the orders of PDG_MODEL_ISOTHERMAL_D3Q19 / _D3Q15 / _D3Q27.
  */
 #ifndef PDG_H
 #define PDG_H
@@ -73,7 +73,7 @@ enum {
                                   cell to two upwind faces: their transport is the 2-D
                                   recurrence of pdg_step's documentation.  Periodic or
                                   inflow axes (pdg_set_inflow); 0 < theta <= 1; dt > 0. */
-  PDG_MODEL_ISOTHERMAL_D3Q19 = 4 /* D = 3, m = 4, w = (rho, rho u): the D3Q19 lattice of the
+  PDG_MODEL_ISOTHERMAL_D3Q19 = 4, /* D = 3, m = 4, w = (rho, rho u): the D3Q19 lattice of the
                                   paper's 3-D scaling runs (Section 4.5), velocities 0, the
                                   six lambda(+-e_a) (+x, -x, +y, -y, +z, -z) and the twelve
                                   lambda(+-e_a +- e_b) (planes xy, xz, yz, each (+,+), (-,+),
@@ -82,6 +82,20 @@ enum {
                                   Each edge velocity acts in planes: its transport is the
                                   D2Q9 diagonal recurrence on every plane of points.
                                   Periodic meshes; 0 < theta <= 1; dt > 0. */
+  PDG_MODEL_ISOTHERMAL_D3Q15 = 5, /* D = 3, m = 4, w = (rho, rho u): the D3Q15 lattice of
+                                  Section 4.5: velocities 0, the six lambda(+-e_a) and the
+                                  eight corners lambda(+-1, +-1, +-1), ordered z = +1 first,
+                                  then z = -1, each as (x, y) = (+,+), (-,+), (-,-), (+,-);
+                                  the same equilibrium with weights 2/9, 1/9, 1/72.  A corner
+                                  velocity couples each cell to three upwind faces: its
+                                  transport is the 3-D recurrence of pdg_step's
+                                  documentation.  Periodic meshes; degree <= 3;
+                                  0 < theta <= 1; dt > 0. */
+  PDG_MODEL_ISOTHERMAL_D3Q27 = 6 /* D = 3, m = 4, w = (rho, rho u): the D3Q27 lattice of
+                                  Section 4.5: the nineteen velocities of D3Q19 in its order,
+                                  then the eight corners in the order of D3Q15; weights 8/27,
+                                  2/27, 1/54, 1/216.  Periodic meshes; degree <= 3;
+                                  0 < theta <= 1; dt > 0. */
 };
 
 /* Time schemes (Section 3.2 and Section 5.1). */
@@ -246,6 +260,13 @@ int pdg_set_source(pdg_ctx* ctx, const pdg_source_desc* desc);
  * transfer matrices) is below 2^-56 of the state's magnitude.  dt must be > 0 there
  * (PDG_ERR_UNSUPPORTED otherwise, or when no such W <= 128 exists).  On an inflow axis
  * the tiles that reach the inflow face start there, from the exact boundary data.
+ * D3Q15 / D3Q27 corner velocities v = lambda (s_x, s_y, s_z): the same form with three
+ * upwind faces, B = I + theta (nu_x I(x)I(x)K + nu_y I(x)K(x)I + nu_z K(x)I(x)I) on the
+ * n^3 nodes of a cell; boxes of cells are swept layer by layer along z, each layer as a
+ * 2-D wavefront, every box starting W cells upwind along all three axes (bound 2^-57 per
+ * upwind boundary; W <= 64, otherwise PDG_ERR_UNSUPPORTED).  The first step with a new
+ * (dt, scheme) plan copies the corner coefficients to the device (a few tens of KB, in
+ * memory allocated by pdg_set_model).
  * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_CUDA,
  *         PDG_ERR_UNSUPPORTED.
  */
@@ -342,7 +363,8 @@ int pdg_synchronize(pdg_ctx* ctx);
  *   kind 0 = transport pass (axes before the last; T or T T, no collision)
  *   kind 1 = last-axis pass (T, fused collision, T)
  *   kind 2 = state kernels (set_w / get_w)
- *   kind 3 = D2Q9 diagonal transport pass
+ *   kind 3 = diagonal transport pass (D2Q9 diagonals, D3Q19 / D3Q27 edges)
+ *   kind 4 = corner transport pass (D3Q15 / D3Q27)
  * pdg_timing_enable(ctx, 1) resets the counters.  pdg_timing_read fills up to
  * max_kinds entries of launches[] and ms[] and synchronises the stream.
  */
@@ -357,6 +379,8 @@ int pdg_timing_read(pdg_ctx* ctx, long long* launches, double* ms, int max_kinds
  *   ngroup field groups per block (>= 1).
  * kind 4 = D2Q9 diagonal pass: lpb = threads per block (a multiple of 32, 64..512),
  *   nseg x ngroup = output cells per tile along x and y (>= 1; the tile counts follow).
+ * kind 5 = D3Q15 / D3Q27 corner pass: lpb = threads per block (a multiple of 32, 64..512,
+ *   at least (d+1)^3), nseg = output cells per box along x and y, ngroup = along z.
  * All zeros restores the built-in heuristic.  Used by the autotuners.
  * Errors: PDG_ERR_ARG.
  */
@@ -374,7 +398,7 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
 enum { PDG_OPT_COMPOSE_TT = 1 };
 int pdg_set_option(pdg_ctx* ctx, int option, int value);
 
-/* pdg_get_launch -- read the launch shape override of a kind 0..4 (zeros = heuristic). */
+/* pdg_get_launch -- read the launch shape override of a kind 0..5 (zeros = heuristic). */
 int pdg_get_launch(const pdg_ctx* ctx, int kind, int* lpb, int* nseg, int* ngroup);
 
 /*

@@ -19,7 +19,8 @@ OBJDIR = os.path.join(ROOT, "_build", "obj")
 LIB = os.path.join(LIBDIR, "libpdg.so")
 
 SOURCES = ["pdg_batch_df.cu", "pdg_batch.cu", "pdg_kernels_df.cu", "pdg_kernels.cu", "pdg_diag_df.cu",
-           "pdg_diag.cu", "pdg_api.cu", "pdg_noalloc.cu", "pdg_server.cu", "pdg_plan.cpp"]
+           "pdg_diag.cu", "pdg_corner_df.cu", "pdg_corner.cu", "pdg_api.cu", "pdg_noalloc.cu", "pdg_server.cu",
+           "pdg_plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I", os.path.join(ROOT, "include")]

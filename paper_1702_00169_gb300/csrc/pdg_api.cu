@@ -57,10 +57,21 @@ struct pdg_ctx {
     PdgDiagCoef c;
   };
   std::vector<DiagPlan> diag_plans;            // planned diagonal sub-steps (a few sizes per run)
+  // corner sub-steps (D3Q15 / D3Q27): host plans and their B^-1 in cbuf (device memory
+  // allocated by pdg_set_model, PDG_CORNER_PLANS slots of FP64 and double-float copies)
+  struct CornerPlan {
+    int order;
+    double nu[3], theta;
+    PdgCornerCoef c;
+    int slot;
+  };
+  std::vector<CornerPlan> corner_plans;
+  char* cbuf = nullptr;
+  int cshape[4] = {0, 0, 0, 0};                // corner pass: threads, box x, y, z (0 = heuristic)
   double* kfield = nullptr;                    // penalisation K at every point
   bool timing = false;
-  long long t_launches[4] = {0, 0, 0, 0};
-  double t_ms[4] = {0, 0, 0, 0};
+  long long t_launches[5] = {0, 0, 0, 0, 0};   // per kind: 0 line, 1 line + C, 2 state, 3 diag, 4 corner
+  double t_ms[5] = {0, 0, 0, 0, 0};
   std::vector<PdgTimedLaunch> pending;
   std::vector<cudaEvent_t> event_pool;
   std::string err;
@@ -134,23 +145,37 @@ int drain_timing(pdg_ctx* c) {
   return PDG_OK;
 }
 
-// Lattice models (one set of populations for all variables): D2Q9 and D3Q19.  Their
-// non-axis populations [diag, diag + ndiag) run in diagonal passes, out of place between
-// slots diag.. and scratch..; norient planes of velocity pairs (a, b).
+// Lattice models (one set of populations for all variables): D2Q9, D3Q19, D3Q15, D3Q27.
+// Their non-axis populations [diag, diag + ndiag) run in diagonal passes, out of place
+// between slots diag.. and scratch..: first norient planes of four edge velocities (a, b),
+// then ncorner corner velocities.
 struct Lattice {
-  int slots, diag, scratch, ndiag, norient;
+  int slots, diag, scratch, ndiag, norient, ncorner;
 };
 bool lattice_of(int kind, Lattice* L) {
   if (kind == PDG_MODEL_ISOTHERMAL_D2Q9) {
-    *L = {PDG_Q9_SLOTS, PDG_Q9_DIAG, PDG_Q9_SCRATCH, 4, 1};
+    *L = {PDG_Q9_SLOTS, PDG_Q9_DIAG, PDG_Q9_SCRATCH, 4, 1, 0};
     return true;
   }
   if (kind == PDG_MODEL_ISOTHERMAL_D3Q19) {
-    *L = {PDG_Q19_SLOTS, PDG_Q19_DIAG, PDG_Q19_SCRATCH, 12, 3};
+    *L = {PDG_Q19_SLOTS, PDG_Q19_DIAG, PDG_Q19_SCRATCH, 12, 3, 0};
+    return true;
+  }
+  if (kind == PDG_MODEL_ISOTHERMAL_D3Q15) {
+    *L = {PDG_Q15_SLOTS, PDG_Q15_DIAG, PDG_Q15_SCRATCH, 8, 0, 8};
+    return true;
+  }
+  if (kind == PDG_MODEL_ISOTHERMAL_D3Q27) {
+    *L = {PDG_Q27_SLOTS, PDG_Q27_DIAG, PDG_Q27_SCRATCH, 20, 3, 8};
     return true;
   }
   return false;
 }
+
+// Corner coefficient slots in pdg_ctx::cbuf: FP64 B^-1 (64 x 64 at most) then its
+// double-float copy, per slot.
+#define PDG_CORNER_PLANS 4
+constexpr size_t kCornerSlotBytes = 64 * 64 * (sizeof(double) + 2 * sizeof(float));
 
 // Launch shape heuristic for one pass (lines per block, segments, field groups)
 // with at most max_threads threads; ov (if ov[0] > 0) forces the shape.
@@ -268,7 +293,8 @@ int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov,
     p.tdir[1] = -1;
     p.fbnent = 3;
     p.fbent[0] = p.fbent[1] = 0;
-  } else if (c->model.kind == PDG_MODEL_ISOTHERMAL_D3Q19) {
+  } else if (c->model.kind == PDG_MODEL_ISOTHERMAL_D3Q19 || c->model.kind == PDG_MODEL_ISOTHERMAL_D3Q15 ||
+             c->model.kind == PDG_MODEL_ISOTHERMAL_D3Q27) {
     // populations 1 + 2 axis (+lambda e_axis) and 2 + 2 axis (-lambda e_axis); periodic only
     p.ntf = 2;
     p.tfield[0] = 1 + 2 * axis;
@@ -446,9 +472,145 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, int o, PdgDiagPass* out) {
   return PDG_OK;
 }
 
+// Launch descriptor of the corner pass of a diagonal sub-step: the eight corner populations
+// (slots diag + 4 norient ..), read from slot set dslot_in and written to the other set.
+// The box counts minimise the swept volume per SM (output cells plus the upwind start,
+// and a per-step overhead of about 8 cells) within the shared-memory budget.
+int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPass* out) {
+  PdgCornerPass& p = *out;
+  std::memset(&p, 0, sizeof(p));
+  double nu[3];
+  for (int a = 0; a < 3; ++a) nu[a] = 2.0 * c->model.lambda * sp.ddelta / c->h[a];
+  const pdg_ctx::CornerPlan* hit = nullptr;
+  for (const auto& e : c->corner_plans)
+    if (e.order == c->order && e.nu[0] == nu[0] && e.nu[1] == nu[1] && e.nu[2] == nu[2] && e.theta == c->theta)
+      hit = &e;
+  if (!hit) {
+    if (!c->cbuf) return fail(c, PDG_ERR_STATE, "internal: corner coefficients not allocated");
+    pdg_ctx::CornerPlan pl;
+    pl.order = c->order;
+    for (int a = 0; a < 3; ++a) pl.nu[a] = nu[a];
+    pl.theta = c->theta;
+    std::vector<double> binv(64 * 64);
+    std::vector<float> binv_f(2 * 64 * 64);
+    if (pdg_plan_corner(c->order, nu[0], nu[1], nu[2], c->theta, &pl.c, binv.data(), binv_f.data()))
+      return fail(c, PDG_ERR_UNSUPPORTED,
+                  "corner transport: no start width <= 64 cells for this time step (dt must be > 0)");
+    // reuse the oldest slot when all are taken (the stream orders the upload after the
+    // launches that read the old coefficients)
+    int slot = (int)c->corner_plans.size();
+    if (slot >= PDG_CORNER_PLANS) {
+      slot = c->corner_plans.front().slot;
+      c->corner_plans.erase(c->corner_plans.begin());
+    }
+    pl.slot = slot;
+    char* base = c->cbuf + (size_t)slot * kCornerSlotBytes;
+    const size_t NN = (size_t)c->n * c->n * c->n;
+    PDG_CUDA(c, cudaMemcpyAsync(base, binv.data(), sizeof(double) * NN * NN, cudaMemcpyHostToDevice, c->stream));
+    PDG_CUDA(c, cudaMemcpyAsync(base + sizeof(double) * 64 * 64, binv_f.data(), sizeof(float) * 2 * NN * NN,
+                                cudaMemcpyHostToDevice, c->stream));
+    // pageable sources: the copies above return once the data are staged
+    c->corner_plans.push_back(pl);
+    hit = &c->corner_plans.back();
+  }
+  p.c = hit->c;
+  const char* base = c->cbuf + (size_t)hit->slot * kCornerSlotBytes;
+  p.binv = reinterpret_cast<const double*>(base);
+  p.binv_f = reinterpret_cast<const float*>(base + sizeof(double) * 64 * 64);
+  const int in = sp.dslot_in, outs = sp.dslot_in == L.diag ? L.scratch : L.diag;
+  const int c0 = 4 * L.norient;   // first corner among the moving populations
+  static const int sx[8] = {+1, -1, -1, +1, +1, -1, -1, +1}, sy[8] = {+1, +1, -1, -1, +1, +1, -1, -1};
+  static const int sz[8] = {+1, +1, +1, +1, -1, -1, -1, -1};
+  p.npop = 8;
+  for (int i = 0; i < 8; ++i) {
+    p.fin[i] = c->f + (long long)(in + c0 + i) * c->npoints;
+    p.fout[i] = c->f + (long long)(outs + c0 + i) * c->npoints;
+    p.sx[i] = sx[i];
+    p.sy[i] = sy[i];
+    p.sz[i] = sz[i];
+  }
+  p.n = c->n;
+  p.ncx = c->N[0];
+  p.ncy = c->N[1];
+  p.ncz = c->N[2];
+  p.sa = 1;
+  p.sb = c->P[0];
+  p.sc = (long long)c->P[0] * c->P[1];
+  p.prec = c->model.prec;
+  p.threads = c->cshape[0] ? c->cshape[0] : 512;
+  if (c->cshape[0]) {
+    p.tx = std::min(c->cshape[1], p.ncx);
+    p.ty = std::min(c->cshape[2], p.ncy);
+    p.tz = std::min(c->cshape[3], p.ncz);
+    p.ntx = (p.ncx + p.tx - 1) / p.tx;
+    p.nty = (p.ncy + p.ty - 1) / p.ty;
+    p.ntz = (p.ncz + p.tz - 1) / p.tz;
+  } else {
+    const int slots = 152;
+    double best = 1e300;
+    auto tiles = [](int N, int cap) {   // candidate (count, size) pairs with a non-empty last box
+      std::vector<std::pair<int, int>> v;
+      for (int k = 1; k <= std::min(N, cap); ++k) {
+        const int t = (N + k - 1) / k;
+        if ((long long)t * (k - 1) >= N) continue;
+        if (!v.empty() && v.back().second == t) continue;
+        v.push_back({k, t});
+      }
+      return v;
+    };
+    const auto TX = tiles(p.ncx, 64), TY = tiles(p.ncy, 64), TZ = tiles(p.ncz, 64);
+    for (auto [ntx, tx] : TX)
+      for (auto [nty, ty] : TY) {
+        PdgCornerPass q = p;
+        q.tx = tx;
+        q.ty = ty;
+        q.tz = p.ncz;
+        if (pdg_corner_smem(q) > 200 * 1024) continue;
+        for (auto [ntz, tz] : TZ) {
+          const long long blocks = 8LL * ntx * nty * ntz;
+          const long long waves = (blocks + slots - 1) / slots;
+          const double layer = (double)(tx + p.c.wx) * (double)(ty + p.c.wy);
+          const double steps = (double)(tx + p.c.wx + ty + p.c.wy);
+          const double cost = (double)waves * (double)(tz + p.c.wz) * (layer + 8.0 * steps);
+          if (cost < best) {
+            best = cost;
+            p.tx = tx;
+            p.ty = ty;
+            p.tz = tz;
+            p.ntx = ntx;
+            p.nty = nty;
+            p.ntz = ntz;
+          }
+        }
+      }
+    if (best == 1e300) return fail(c, PDG_ERR_UNSUPPORTED, "corner box too large for shared memory");
+  }
+  if (pdg_corner_smem(p) > 200 * 1024) return fail(c, PDG_ERR_UNSUPPORTED, "corner box too large");
+  if (p.threads < (int)(c->n * c->n * c->n) || p.threads > 512)
+    return fail(c, PDG_ERR_ARG, "corner pass: threads per block below the nodes of a cell");
+  return PDG_OK;
+}
+
 int issue_diag(pdg_ctx* c, const PdgPassSpec& sp) {
   Lattice L;
   if (!lattice_of(c->model.kind, &L)) return fail(c, PDG_ERR_ARG, "internal: diagonal pass of a DnQ2n model");
+  if (L.ncorner) {
+    PdgCornerPass p;
+    if (int r = make_corner(c, sp, L, &p)) return r;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+      e0 = get_event(c);
+      e1 = get_event(c);
+      if (!e0 || !e1) return fail(c, PDG_ERR_CUDA, "cudaEventCreate failed");
+      PDG_CUDA(c, cudaEventRecord(e0, c->stream));
+    }
+    int e = pdg_launch_corner(p, (void*)c->stream);
+    if (e != 0) return cuda_fail(c, (cudaError_t)e, "corner_kernel launch");
+    if (c->timing) {
+      PDG_CUDA(c, cudaEventRecord(e1, c->stream));
+      c->pending.push_back({4, e0, e1});
+    }
+  }
   for (int o = 0; o < L.norient; ++o) {
     PdgDiagPass p;
     if (int r = make_diag(c, sp, o, &p)) return r;
@@ -812,7 +974,7 @@ int pdg_create_mesh(pdg_ctx** out, int dim, const int n_macro[3], const int n_su
 
 int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   if (!c || !d) return PDG_ERR_ARG;
-  if (d->kind < PDG_MODEL_ADVECTION || d->kind > PDG_MODEL_ISOTHERMAL_D3Q19)
+  if (d->kind < PDG_MODEL_ADVECTION || d->kind > PDG_MODEL_ISOTHERMAL_D3Q27)
     return fail(c, PDG_ERR_ARG, "unknown model kind");
   if (d->scheme != PDG_SCHEME_M2 && d->scheme != PDG_SCHEME_M2_COLLAPSED && d->scheme != PDG_SCHEME_M2KIN)
     return fail(c, PDG_ERR_ARG, "unknown scheme");
@@ -824,18 +986,21 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   if (d->kind == PDG_MODEL_SHALLOW_WATER && c->dim != 2)
     return fail(c, PDG_ERR_UNSUPPORTED, "shallow water needs dim = 2");
   const bool q9 = d->kind == PDG_MODEL_ISOTHERMAL_D2Q9, q19 = d->kind == PDG_MODEL_ISOTHERMAL_D3Q19;
-  const bool lat = q9 || q19;
+  const bool q15 = d->kind == PDG_MODEL_ISOTHERMAL_D3Q15, q27 = d->kind == PDG_MODEL_ISOTHERMAL_D3Q27;
+  const bool q3d = q19 || q15 || q27, lat = q9 || q3d;
   if (q9 && c->dim != 2) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 needs dim = 2");
-  if (q19 && c->dim != 3) return fail(c, PDG_ERR_UNSUPPORTED, "D3Q19 needs dim = 3");
-  if (q19 && !(c->periodic[0] && c->periodic[1] && c->periodic[2]))
-    return fail(c, PDG_ERR_UNSUPPORTED, "D3Q19 runs on periodic meshes");
+  if (q3d && c->dim != 3) return fail(c, PDG_ERR_UNSUPPORTED, "D3Q15 / D3Q19 / D3Q27 need dim = 3");
+  if (q3d && !(c->periodic[0] && c->periodic[1] && c->periodic[2]))
+    return fail(c, PDG_ERR_UNSUPPORTED, "D3Q15 / D3Q19 / D3Q27 run on periodic meshes");
+  if ((q15 || q27) && c->n > PDG_MAXN_CORNER)
+    return fail(c, PDG_ERR_UNSUPPORTED, "D3Q15 / D3Q27 support degrees 1 to 3");
   if (lat && !(d->theta > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "diagonal velocities need theta > 0");
   PdgModel M{};
   M.kind = d->kind;
   M.dim = c->dim;
   M.m = d->kind == PDG_MODEL_ADVECTION ? 1
         : (d->kind == PDG_MODEL_SHALLOW_WATER ? 3 : (lat ? c->dim + 1 : c->dim + 2));
-  M.nv = q9 ? 9 : (q19 ? 19 : 2 * c->dim);
+  M.nv = q9 ? 9 : (q19 ? 19 : (q15 ? 15 : (q27 ? 27 : 2 * c->dim)));
   M.nf = lat ? M.nv : M.m * M.nv;
   M.lambda = d->lambda;
   M.omega = d->omega;
@@ -848,6 +1013,15 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   }
   M.prec = d->precision;
   pdg_model_constants(&M);
+  if ((q15 || q27) && !c->cbuf) {
+    cudaError_t e = cudaMalloc((void**)&c->cbuf, PDG_CORNER_PLANS * kCornerSlotBytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->cbuf = nullptr;
+      return fail(c, PDG_ERR_OOM, std::string("corner coefficients: ") + cudaGetErrorString(e));
+    }
+  }
+  c->corner_plans.clear();
   // a different number of fields or a different state format invalidates the state
   if (c->has_model && (c->model.m != M.m || c->model.nf != M.nf || c->model.prec != M.prec)) {
     c->has_state = false;
@@ -1100,7 +1274,7 @@ int pdg_timing_enable(pdg_ctx* c, int enable) {
     if (r) return r;
   }
   c->timing = enable != 0;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     c->t_launches[k] = 0;
     c->t_ms[k] = 0.0;
   }
@@ -1112,7 +1286,7 @@ int pdg_timing_read(pdg_ctx* c, long long* launches, double* ms, int max_kinds) 
   PDG_CUDA(c, cudaStreamSynchronize(c->stream));
   int r = drain_timing(c);
   if (r) return r;
-  for (int k = 0; k < max_kinds && k < 4; ++k) {
+  for (int k = 0; k < max_kinds && k < 5; ++k) {
     if (launches) launches[k] = c->t_launches[k];
     if (ms) ms[k] = c->t_ms[k];
   }
@@ -1120,7 +1294,19 @@ int pdg_timing_read(pdg_ctx* c, long long* launches, double* ms, int max_kinds) 
 }
 
 int pdg_set_launch(pdg_ctx* c, int kind, int lpb, int nseg, int ngroup) {
-  if (!c || kind < 0 || kind > 4) return PDG_ERR_ARG;
+  if (!c || kind < 0 || kind > 5) return PDG_ERR_ARG;
+  if (kind == 5) {
+    if (lpb == 0 && nseg == 0 && ngroup == 0) {
+      c->cshape[0] = c->cshape[1] = c->cshape[2] = c->cshape[3] = 0;
+      return PDG_OK;
+    }
+    if (lpb < 64 || lpb > 512 || lpb % 32 || nseg < 1 || ngroup < 1)
+      return fail(c, PDG_ERR_ARG, "bad corner launch shape");
+    c->cshape[0] = lpb;
+    c->cshape[1] = c->cshape[2] = nseg;
+    c->cshape[3] = ngroup;
+    return PDG_OK;
+  }
   if (kind == 4) {
     if (lpb == 0 && nseg == 0 && ngroup == 0) {
       c->dshape[0] = c->dshape[1] = c->dshape[2] = 0;
@@ -1161,6 +1347,7 @@ int pdg_destroy(pdg_ctx* c) {
   }
   if (c->wstage) cudaFree(c->wstage);
   if (c->kfield) cudaFree(c->kfield);
+  if (c->cbuf) cudaFree(c->cbuf);
   free_inflow(c);
   delete c;
   return PDG_OK;
@@ -1311,7 +1498,13 @@ int pdg_set_option(pdg_ctx* c, int option, int value) {
 }
 
 int pdg_get_launch(const pdg_ctx* c, int kind, int* lpb, int* nseg, int* ngroup) {
-  if (!c || kind < 0 || kind > 4 || !lpb || !nseg || !ngroup) return PDG_ERR_ARG;
+  if (!c || kind < 0 || kind > 5 || !lpb || !nseg || !ngroup) return PDG_ERR_ARG;
+  if (kind == 5) {
+    *lpb = c->cshape[0];
+    *nseg = c->cshape[1];
+    *ngroup = c->cshape[3];
+    return PDG_OK;
+  }
   const int* slot = kind < 2 ? c->launch[kind] : (kind < 4 ? c->bshape[kind - 2] : c->dshape);
   *lpb = slot[0];
   *nseg = slot[1];
@@ -1411,7 +1604,7 @@ int batch_prepare(pdg_batch* b, const double* dt, const int* nsteps) {
     if (!c->has_state) return bfail(b, PDG_ERR_STATE, "batch instance without state");
     Lattice L;
     if (lattice_of(c->model.kind, &L))
-      return bfail(b, PDG_ERR_UNSUPPORTED, "D2Q9 / D3Q19 instances run through pdg_step only");
+      return bfail(b, PDG_ERR_UNSUPPORTED, "lattice (D2Q9 / D3Qq) instances run through pdg_step only");
     if (nsteps[i] < 0 || !std::isfinite(dt[i])) return bfail(b, PDG_ERR_ARG, "bad dt or nsteps");
     std::vector<PdgPassSpec> sched;
     if (int r = build_schedule(c, dt[i], nsteps[i], sched)) return bfail(b, r, c->err);

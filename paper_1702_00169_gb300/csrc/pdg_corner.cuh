@@ -1,0 +1,262 @@
+// Transport of the corner populations of D3Q15 / D3Q27 (velocities lambda (+-1, +-1, +-1)).
+//
+// Section 3.1, eq. (3.7) on a Cartesian cell splits into one line operator per axis, so
+// the theta step of eq. (3.11) couples cell c to the NEW values on the downwind faces of
+// its three upwind neighbours (traversal orientation: -x, -y and -z):
+//   fn_c = Binv r_c - c1 f_c,   r_c = f_c / theta + kx S_x Lt + ky S_y Bt + kz S_z Zt
+// (PdgCornerCoef).  The faces obey a 3-D recurrence, periodic along all three axes: the
+// analogue of the macrocell wavefronts of Section 4.2 on a cyclic mesh.
+//
+// Exact solve by truncated boxes.  A block owns a box of tx x ty x tz output cells of one
+// population and sweeps the region that starts wx columns, wy rows and wz layers upwind of
+// it.  At the region's three upwind boundaries the new face values are replaced by the old
+// ones; the host chose the widths so that this start changes no output cell by more than
+// 2^-57 of max|f| per boundary (pdg_plan_corner).  The region is swept layer by layer
+// along z; inside a layer, column j handles row t - j at step t (a skewed 2-D wavefront:
+// every cell of an anti-diagonal is independent).  The +x and +y faces pass between the
+// steps of a layer through shared memory (double-buffered by step parity); the +z face of
+// every cell of the layer's region stays in shared memory until the cell above reads it.
+// No block waits on another block.  Reads come from the input slots and writes go to the
+// output slots, so overlapping regions of neighbouring boxes never see a new value.
+//
+// Work split per step: (A) the block builds r_c for every cell of the anti-diagonal in
+// shared memory, (B) the threads of a cell form its n^3 output nodes as dot products with
+// r_c (Binv sits in shared memory transposed, so the threads of a cell read consecutive
+// words; the FP64 pipe, not shared memory, bounds this loop).  The state of the next
+// anti-diagonal is copied into shared memory with cp.async while (B) runs.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pdg_diag.cuh"
+
+namespace pdgdev {
+
+struct CornerGeom {
+  const double* fin;
+  double* fout;
+  int sx, sy, sz;
+  long long sa, sb, sc;
+  int ncol, nrow, nlay, wx, wy, wz;
+  const long long* colx;   // [ncol + 1]: offset of traversal node 0 of region column j - 1
+  const long long* rowy;   // [nrow + 1]
+  const long long* layz;   // [nlay + 1]
+};
+
+// Offset of node (iz, iy, ix) (traversal orientation) of region cell (j, r, k), j, r, k >= -1.
+__device__ __forceinline__ long long corner_off(const CornerGeom& g, int j, int r, int k, int iz, int iy, int ix) {
+  return g.layz[k + 1] + (long long)(g.sz * iz) * g.sc + g.rowy[r + 1] + (long long)(g.sy * iy) * g.sb +
+         g.colx[j + 1] + (long long)(g.sx * ix) * g.sa;
+}
+
+// Stage the state of every cell of anti-diagonal t of layer k (all n^3 nodes) and, on the
+// region's upwind x and y edges, the old face values entering it.
+template <int NP>
+__device__ __forceinline__ void corner_stage(const CornerGeom& g, int k, int t, double* fb, double* lbnd,
+                                             double* bbnd) {
+  constexpr int NF = NP * NP, NN = NF * NP, RS = (NN + 1) & ~1;
+  const int jlo = max(0, t - g.nrow + 1), jhi = min(g.ncol - 1, t);
+  const int A = jhi - jlo + 1;
+  for (int i = threadIdx.x; i < A * NN; i += blockDim.x) {
+    const int c = i / NN, q = i % NN;
+    const int j = jlo + c;
+    cp_async8(fb + c * RS + q, g.fin + corner_off(g, j, t - j, k, q / NF, (q / NP) % NP, q % NP));
+  }
+  const int tid = threadIdx.x;
+  if (jlo == 0 && tid < NF)   // column 0 at row t: +x face of the cell upwind of it
+    cp_async8(lbnd + tid, g.fin + corner_off(g, -1, t, k, tid / NP, tid % NP, NP - 1));
+  if (jhi == t && tid >= NF && tid < 2 * NF) {   // row 0 at column t: +y face of the cell below
+    const int u = tid - NF;
+    cp_async8(bbnd + u, g.fin + corner_off(g, t, -1, k, u / NP, NP - 1, u % NP));
+  }
+}
+
+template <int NP, class T>
+__device__ __forceinline__ void corner_body(const PdgCornerPass& p, double* sm) {
+  constexpr int NF = NP * NP, NN = NF * NP, RS = (NN + 1) & ~1;   // RS: 16-byte aligned rows
+  int b = blockIdx.x;
+  const int txi = b % p.ntx;
+  b /= p.ntx;
+  const int tyi = b % p.nty;
+  b /= p.nty;
+  const int tzi = b % p.ntz;
+  const int pop = b / p.ntz;
+  const PdgCornerCoef& C = p.c;
+
+  CornerGeom g;
+  g.fin = p.fin[pop];
+  g.fout = p.fout[pop];
+  g.sx = p.sx[pop];
+  g.sy = p.sy[pop];
+  g.sz = p.sz[pop];
+  g.sa = p.sa;
+  g.sb = p.sb;
+  g.sc = p.sc;
+  g.wx = C.wx;
+  g.wy = C.wy;
+  g.wz = C.wz;
+  const int X0 = txi * p.tx, Y0 = tyi * p.ty, Z0 = tzi * p.tz;
+  g.ncol = min(p.tx, p.ncx - X0) + g.wx;
+  g.nrow = min(p.ty, p.ncy - Y0) + g.wy;
+  g.nlay = min(p.tz, p.ncz - Z0) + g.wz;
+  const int T_steps = g.ncol + g.nrow - 1;
+  const int CM = p.tx + C.wx, RM = p.ty + C.wy;   // column / row capacities of any box
+  const int amax = min(CM, RM);                                     // longest anti-diagonal
+
+  // shared memory: BinvT[NN][NN] | rbuf[amax][RS] | fbuf[2][amax][RS] | Lt[2][CM+1][NF] |
+  //                Bt[2][CM][NF] | Zt[RM][CM][NF] | lbnd[2][NF] | bbnd[2][NF] |
+  //                colx[CM+1] | rowy[RM+1] | layz[tz+wz+1] (64-bit offsets)
+  T* BinvT = reinterpret_cast<T*>(sm);
+  T* rbuf = BinvT + NN * NN;
+  T* fbuf = rbuf + (size_t)amax * RS;
+  T* Lt = fbuf + (size_t)2 * amax * RS;
+  T* Bt = Lt + (size_t)2 * (CM + 1) * NF;
+  T* Zt = Bt + (size_t)2 * CM * NF;
+  T* lbnd = Zt + (size_t)RM * CM * NF;
+  T* bbnd = lbnd + 2 * NF;
+  long long* colx = reinterpret_cast<long long*>(bbnd + 2 * NF);
+  long long* rowy = colx + (CM + 1);
+  long long* layz = rowy + (RM + 1);
+  const int LtS = CM + 1, BtS = CM;
+  for (int i = threadIdx.x; i < NN * NN; i += blockDim.x) {
+    const int row = i % NN, col = i / NN;   // BinvT[col][row] = Binv[row][col]
+    if constexpr (__is_same(T, double)) {
+      BinvT[i] = p.binv[row * NN + col];
+    } else {
+      const float* bf = p.binv_f + 2 * (row * NN + col);
+      BinvT[i] = T{bf[0], bf[1]};
+    }
+  }
+  for (int j = threadIdx.x; j <= g.ncol; j += blockDim.x) {
+    const int tc = wrap_cell(X0 - g.wx + j - 1, p.ncx);
+    colx[j] = (long long)(g.sx > 0 ? tc * NP : (p.ncx - 1 - tc) * NP + (NP - 1)) * g.sa;
+  }
+  for (int r = threadIdx.x; r <= g.nrow; r += blockDim.x) {
+    const int tr = wrap_cell(Y0 - g.wy + r - 1, p.ncy);
+    rowy[r] = (long long)(g.sy > 0 ? tr * NP : (p.ncy - 1 - tr) * NP + (NP - 1)) * g.sb;
+  }
+  for (int k = threadIdx.x; k <= g.nlay; k += blockDim.x) {
+    const int tl = wrap_cell(Z0 - g.wz + k - 1, p.ncz);
+    layz[k] = (long long)(g.sz > 0 ? tl * NP : (p.ncz - 1 - tl) * NP + (NP - 1)) * g.sc;
+  }
+  g.colx = colx;
+  g.rowy = rowy;
+  g.layz = layz;
+  __syncthreads();
+  // the region's lower z boundary: old +z faces of the layer below the region
+  for (int i = threadIdx.x; i < g.nrow * g.ncol * NF; i += blockDim.x) {
+    const int cell = i / NF, u = i % NF;
+    const int r = cell / g.ncol, j = cell % g.ncol;
+    cp_async8(reinterpret_cast<double*>(Zt + ((size_t)r * CM + j) * NF + u),
+              g.fin + corner_off(g, j, r, -1, NP - 1, u / NP, u % NP));
+  }
+  const T rth = PDG_DC(T, C, rtheta), c1 = PDG_DC(T, C, c1);
+  const T th = PDG_DC(T, C, theta), omth = PDG_DC(T, C, omtheta);
+  const T kx = PDG_DC(T, C, kx), ky = PDG_DC(T, C, ky), kz = PDG_DC(T, C, kz);
+  // output mapping: thread (kq, qq) computes node qq of cells jlo + kq, jlo + kq + K, ...
+  const int K = blockDim.x / NN;
+  const int kq = threadIdx.x / NN, qq = threadIdx.x % NN;
+  const int qz = qq / NF, qy = (qq / NP) % NP, qx = qq % NP;
+
+  corner_stage<NP>(g, 0, 0, reinterpret_cast<double*>(fbuf), reinterpret_cast<double*>(lbnd),
+                   reinterpret_cast<double*>(bbnd));
+  cp_async_wait_all();
+  __syncthreads();
+  int s = 0;   // steps so far (all layers): the parity of the double buffers
+  for (int k = 0; k < g.nlay; ++k) {
+    const bool out_layer = k >= g.wz;
+    for (int t = 0; t < T_steps; ++t, ++s) {
+      const int par = s & 1, prv = par ^ 1;
+      const int jlo = max(0, t - g.nrow + 1), jhi = min(g.ncol - 1, t);
+      const int A = jhi - jlo + 1;
+      const T* fc = fbuf + (size_t)par * amax * RS;
+      // (A) r_c of every cell of the anti-diagonal
+      for (int i = threadIdx.x; i < A * NN; i += blockDim.x) {
+        const int c = i / NN, q = i % NN;
+        const int j = jlo + c, r = t - j;
+        const int iz = q / NF, iy = (q / NP) % NP, ix = q % NP;
+        T rv = fc[c * RS + q] * rth;
+        if (ix == 0)
+          rv = fma(kx, j == 0 ? lbnd[par * NF + iz * NP + iy] : Lt[((size_t)prv * LtS + j) * NF + iz * NP + iy], rv);
+        if (iy == 0)
+          rv = fma(ky, r == 0 ? bbnd[par * NF + iz * NP + ix] : Bt[((size_t)prv * BtS + j) * NF + iz * NP + ix], rv);
+        if (iz == 0) rv = fma(kz, Zt[((size_t)r * CM + j) * NF + iy * NP + ix], rv);
+        rbuf[c * RS + q] = rv;
+      }
+      __syncthreads();
+      {   // stage the next anti-diagonal (the first one of the next layer after the last)
+        double* nf = reinterpret_cast<double*>(fbuf + (size_t)prv * amax * RS);
+        double* nl = reinterpret_cast<double*>(lbnd + prv * NF);
+        double* nb = reinterpret_cast<double*>(bbnd + prv * NF);
+        if (t + 1 < T_steps) corner_stage<NP>(g, k, t + 1, nf, nl, nb);
+        else if (k + 1 < g.nlay) corner_stage<NP>(g, k + 1, 0, nf, nl, nb);
+      }
+      // (B) every node of every cell of the anti-diagonal; only output cells are stored
+      if (kq < K) {
+        for (int j = jlo + kq; j <= jhi; j += K) {
+          const int c = j - jlo, r = t - j;
+          const T* rc = rbuf + c * RS;
+          T acc;
+          if constexpr (__is_same(T, double)) {
+            double a[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int m = 0; m < NN; ++m) a[m & 3] = fma(BinvT[m * NN + qq], rc[m], a[m & 3]);
+            acc = (a[0] + a[1]) + (a[2] + a[3]);
+          } else {
+            // compensated dot product (see dot_acc): exact high products and sums, the
+            // rounding errors and cross terms gathered in one FP32 accumulator
+            float S = 0.0f, L = 0.0f;
+#pragma unroll 8
+            for (int m = 0; m < NN; ++m) {
+              const T a = BinvT[m * NN + qq], bv = rc[m];
+              const dd pr = dd_two_prod(a.hi, bv.hi);
+              const float cross = __fmaf_rn(a.hi, bv.lo, __fmul_rn(a.lo, bv.hi));
+              const dd sm2 = dd_two_sum(S, pr.hi);
+              S = sm2.hi;
+              L = __fadd_rn(L, __fadd_rn(sm2.lo, __fadd_rn(pr.lo, cross)));
+            }
+            acc = dd_fast_two_sum(S, L);
+          }
+          const T fo = fc[c * RS + qq];
+          const T outv = acc - c1 * fo;
+          if (out_layer && j >= g.wx && r >= g.wy) st(g.fout + corner_off(g, j, r, k, qz, qy, qx), outv);
+          if (qx == NP - 1 || qy == NP - 1 || qz == NP - 1) {
+            const T face = fma(th, outv, omth * fo);
+            if (qx == NP - 1) Lt[((size_t)par * LtS + j + 1) * NF + qz * NP + qy] = face;
+            if (qy == NP - 1) Bt[((size_t)par * BtS + j) * NF + qz * NP + qx] = face;
+            if (qz == NP - 1) Zt[((size_t)r * CM + j) * NF + qy * NP + qx] = face;
+          }
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
+  }
+}
+
+template <int NP, class T>
+__global__ void __launch_bounds__(512, 1) corner_kernel(const __grid_constant__ PdgCornerPass p) {
+  extern __shared__ double sm[];
+  corner_body<NP, T>(p, sm);
+}
+
+template <class T>
+int launch_corner_typed(const PdgCornerPass& p, size_t smem, cudaStream_t st) {
+  const long long blocks = (long long)p.ntx * p.nty * p.ntz * p.npop;
+  if (blocks > 0x7fffffffLL || blocks < 1) return (int)cudaErrorInvalidConfiguration;
+  auto go = [&](auto kern) -> int {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return (int)e;
+    }
+    kern<<<(unsigned)blocks, p.threads, smem, st>>>(p);
+    return (int)cudaGetLastError();
+  };
+  switch (p.n) {
+    case 2: return go(corner_kernel<2, T>);
+    case 3: return go(corner_kernel<3, T>);
+    case 4: return go(corner_kernel<4, T>);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace pdgdev

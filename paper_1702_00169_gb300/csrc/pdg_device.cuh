@@ -20,7 +20,8 @@ namespace pdgdev {
 #define PDG_PREFETCH_DIST 2   // cells ahead prefetched into L2 on strided sweeps
 #endif
 
-enum { MV_ADV = 0, MV_SW = 1, MV_EU1 = 2, MV_EU2 = 3, MV_EU3 = 4, MV_NONE = 5, MV_D2Q9 = 6, MV_D3Q19 = 7 };
+enum { MV_ADV = 0, MV_SW = 1, MV_EU1 = 2, MV_EU2 = 3, MV_EU3 = 4, MV_NONE = 5, MV_D2Q9 = 6, MV_D3Q19 = 7,
+       MV_D3Q15 = 8, MV_D3Q27 = 9 };
 
 // ---------------------------------------------------------------------------
 // Double-float arithmetic.  Error-free transformations (all with explicit
@@ -463,6 +464,109 @@ struct Collide<MV_D3Q19, T> {
   }
 };
 
+// Corner velocities (D3Q15 / D3Q27) in the order (s_x, s_y, s_z) = (+,+,+), (-,+,+), (-,-,+),
+// (+,-,+), (+,+,-), (-,+,-), (-,-,-), (+,-,-): sums of the eight populations c[0..7]
+// (mass and the three first moments) and their equilibrium factors e_i (s.xi_i = +-t_1..t_4,
+// t_1 = s_x + s_y + s_z, t_2 = s_y + s_z - s_x, t_3 = s_z - s_x - s_y, t_4 = s_x + s_z - s_y).
+template <class T>
+__device__ __forceinline__ void corner_moments(const T* c, T* rho, T* jx, T* jy, T* jz) {
+  *rho = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+  *jx = ((c[0] - c[1]) + (c[3] - c[2])) + ((c[4] - c[5]) + (c[7] - c[6]));
+  *jy = ((c[0] + c[1]) - (c[2] + c[3])) + ((c[4] + c[5]) - (c[6] + c[7]));
+  *jz = ((c[0] + c[1]) + (c[2] + c[3])) - ((c[4] + c[5]) + (c[6] + c[7]));
+}
+
+template <class T>
+__device__ __forceinline__ void corner_e(T sx, T sy, T sz, T base, T half, T* e) {
+  const T t1 = (sx + sy) + sz, t2 = (sy + sz) - sx, t3 = sz - (sx + sy), t4 = (sx + sz) - sy;
+  const T q1 = fma(half * t1, t1, base), q2 = fma(half * t2, t2, base);
+  const T q3 = fma(half * t3, t3, base), q4 = fma(half * t4, t4, base);
+  e[0] = q1 + t1;
+  e[1] = q2 + t2;
+  e[2] = q3 + t3;
+  e[3] = q4 + t4;
+  e[4] = q3 - t3;
+  e[5] = q4 - t4;
+  e[6] = q1 - t1;
+  e[7] = q2 - t2;
+}
+
+// D3Q15 / D3Q27 relaxation: populations 0 (rest), 1-6 (axis), then (D3Q27) 7-18 (edges as in
+// D3Q19), then the eight corners; f^eq_i = W_i rho e_i with s = 3 j / rho.
+template <class T, bool EDGES>
+__device__ __forceinline__ void d3q_corner_lattice_collide(T* v, const PdgModel& M) {
+  constexpr int C0 = EDGES ? 19 : 7;
+  T rho, jx, jy, jz;
+  if constexpr (EDGES) {
+    d3q19_moments<T>(v, &rho, &jx, &jy, &jz);
+  } else {
+    rho = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + v[6]);
+    jx = v[1] - v[2];
+    jy = v[3] - v[4];
+    jz = v[5] - v[6];
+  }
+  {
+    T cr, cx, cy, cz;
+    corner_moments<T>(v + C0, &cr, &cx, &cy, &cz);
+    rho = rho + cr;
+    jx = jx + cx;
+    jy = jy + cy;
+    jz = jz + cz;
+  }
+  T e[19], ec[8];
+  d3q19_e<T>(rho, jx, jy, jz, M, e);   // e[0], the axis and (D3Q27) the edge factors
+  {
+    const T three = from_double<T>(3.0);
+    const T ir = recip(rho);
+    const T half = PDG_K(T, M, PDG_K_HALF);
+    corner_e<T>(three * (jx * ir), three * (jy * ir), three * (jz * ir), e[0], half, ec);
+  }
+  const T a0 = PDG_K(T, M, PDG_K_Q9W0) * rho, a1 = PDG_K(T, M, PDG_K_Q9W1) * rho;
+  const T a2 = PDG_K(T, M, PDG_K_Q9W2) * rho, a3 = PDG_K(T, M, PDG_K_Q9W3) * rho;
+  const T om1 = PDG_K(T, M, PDG_K_OM1);
+  if constexpr (!__is_same(T, double)) {
+    v[0] = relax(om1, v[0], a0 * e[0]);
+#pragma unroll
+    for (int i = 1; i < 7; ++i) v[i] = relax(om1, v[i], a1 * e[i]);
+    if constexpr (EDGES) {
+#pragma unroll
+      for (int i = 7; i < 19; ++i) v[i] = relax(om1, v[i], a2 * e[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[C0 + i] = relax(om1, v[C0 + i], a3 * ec[i]);
+  } else if (M.omega == 2.0) {
+    v[0] = fma(a0, e[0], -v[0]);
+#pragma unroll
+    for (int i = 1; i < 7; ++i) v[i] = fma(a1, e[i], -v[i]);
+    if constexpr (EDGES) {
+#pragma unroll
+      for (int i = 7; i < 19; ++i) v[i] = fma(a2, e[i], -v[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[C0 + i] = fma(a3, ec[i], -v[C0 + i]);
+  } else {
+    v[0] = fma(om1, v[0], a0 * e[0]);
+#pragma unroll
+    for (int i = 1; i < 7; ++i) v[i] = fma(om1, v[i], a1 * e[i]);
+    if constexpr (EDGES) {
+#pragma unroll
+      for (int i = 7; i < 19; ++i) v[i] = fma(om1, v[i], a2 * e[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[C0 + i] = fma(om1, v[C0 + i], a3 * ec[i]);
+  }
+}
+
+template <class T>
+struct Collide<MV_D3Q15, T> {
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) { d3q_corner_lattice_collide<T, false>(v, M); }
+};
+
+template <class T>
+struct Collide<MV_D3Q27, T> {
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) { d3q_corner_lattice_collide<T, true>(v, M); }
+};
+
 template <class T>
 struct Collide<MV_NONE, T> {
   static __device__ __forceinline__ void run(T*, const PdgModel&) {}
@@ -483,6 +587,8 @@ template <> struct NFields<MV_ADV> { static constexpr int value = 6; };
 template <> struct NFields<MV_NONE> { static constexpr int value = 1; };
 template <> struct NFields<MV_D2Q9> { static constexpr int value = 9; };
 template <> struct NFields<MV_D3Q19> { static constexpr int value = 19; };
+template <> struct NFields<MV_D3Q15> { static constexpr int value = 15; };
+template <> struct NFields<MV_D3Q27> { static constexpr int value = 27; };
 
 // State slot of population k at collision time (D2Q9: the diagonal populations 5-8 sit
 // in slots dslot..dslot+3, see PDG_Q9_SLOTS).
@@ -490,6 +596,8 @@ template <int MV>
 __device__ __forceinline__ int coll_slot(int k, int dslot) {
   if constexpr (MV == MV_D2Q9) return k < PDG_Q9_DIAG ? k : dslot + (k - PDG_Q9_DIAG);
   if constexpr (MV == MV_D3Q19) return k < PDG_Q19_DIAG ? k : dslot + (k - PDG_Q19_DIAG);
+  if constexpr (MV == MV_D3Q15) return k < PDG_Q15_DIAG ? k : dslot + (k - PDG_Q15_DIAG);
+  if constexpr (MV == MV_D3Q27) return k < PDG_Q27_DIAG ? k : dslot + (k - PDG_Q27_DIAG);
   return k;
 }
 

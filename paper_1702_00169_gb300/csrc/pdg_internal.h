@@ -62,11 +62,12 @@ enum {
   PDG_K_GM1 = 4,    // gamma - 1
   PDG_K_HALF = 5,   // 1/2
   PDG_K_CADV = 6,   // omega (1/(2D) + s_i a_axis / (2 lambda)), 6 entries
-  PDG_K_N = 12
+  PDG_K_N = 13
 };
-// D2Q9 and D3Q19 reuse the advection slots: omega W_0, omega W_axis, omega W_diag (edge),
-// 1/6, 1/lambda, lambda.
-enum { PDG_K_Q9W0 = 6, PDG_K_Q9W1 = 7, PDG_K_Q9W2 = 8, PDG_K_SIXTH = 9, PDG_K_ILAM = 10, PDG_K_LAM = 11 };
+// The lattice models reuse the advection slots: omega W_0, omega W_axis, omega W_diag
+// (edge), 1/6, 1/lambda, lambda, and one more slot for omega W_corner (D3Q15 / D3Q27).
+enum { PDG_K_Q9W0 = 6, PDG_K_Q9W1 = 7, PDG_K_Q9W2 = 8, PDG_K_SIXTH = 9, PDG_K_ILAM = 10, PDG_K_LAM = 11,
+       PDG_K_Q9W3 = 12 };
 
 // D2Q9 state slots: populations 0-8 in the velocity order of Section 5.1, then four
 // scratch slots.  The diagonal transport (populations 5-8) is computed out of place,
@@ -80,6 +81,16 @@ enum { PDG_K_Q9W0 = 6, PDG_K_Q9W1 = 7, PDG_K_Q9W2 = 8, PDG_K_SIXTH = 9, PDG_K_IL
 #define PDG_Q19_SLOTS 31
 #define PDG_Q19_DIAG 7
 #define PDG_Q19_SCRATCH 19
+// D3Q15: populations 0-14 (rest, six axis, eight corners), then eight scratch slots for
+// the corner populations 7-14.
+#define PDG_Q15_SLOTS 23
+#define PDG_Q15_DIAG 7
+#define PDG_Q15_SCRATCH 15
+// D3Q27: populations 0-26 (rest, six axis, twelve edges as in D3Q19, eight corners), then
+// twenty scratch slots for populations 7-26.
+#define PDG_Q27_SLOTS 47
+#define PDG_Q27_DIAG 7
+#define PDG_Q27_SCRATCH 27
 
 struct PdgModel {
   int kind;      // PDG_MODEL_*
@@ -196,6 +207,37 @@ struct PdgDiagPass {
   PdgDiagCoef c;
 };
 
+// Coefficients of one corner sub-step (velocity lambda (+-1, +-1, +-1)) on an n^3-node
+// cell (node p = (iz n + iy) n + ix, traversal orientation: the upwind neighbours are at
+// -x, -y and -z):
+//   fn = Binv r - c1 f,  r = f / theta + kx S_x Lt + ky S_y Bt + kz S_z Zt,
+//   Binv = (I + theta (nu_x I(x)I(x)K + nu_y I(x)K(x)I + nu_z K(x)I(x)I))^-1,
+// Lt, Bt, Zt the theta-weighted values on the +x / +y / +z faces of the upwind
+// neighbours (n^2 each), entering the nodes with ix = 0 / iy = 0 / iz = 0.  Binv itself
+// (up to 64 x 64) lives in device memory (PdgCornerPass::binv).
+#define PDG_MAXN_CORNER 4
+struct PdgCornerCoef {
+  double rtheta, c1, theta, omtheta, kx, ky, kz;
+  int wx, wy, wz;   // upwind start widths (cells) along x, y, z
+  float rtheta_f[1][2], c1_f[1][2], theta_f[1][2], omtheta_f[1][2], kx_f[1][2], ky_f[1][2], kz_f[1][2];
+};
+
+// Launch descriptor of a corner pass: npop (<= 8) populations with traversal signs
+// (sx, sy, sz) on an ncx x ncy x ncz periodic cell grid, in tiles of tx x ty x tz output
+// cells, each swept from wx columns, wy rows and wz layers upwind.
+struct PdgCornerPass {
+  const double* fin[8];
+  double* fout[8];
+  int sx[8], sy[8], sz[8];
+  int npop, n, ncx, ncy, ncz;
+  long long sa, sb, sc;            // point strides along x, y, z
+  int tx, ty, tz, ntx, nty, ntz;   // tile shape and counts
+  int threads, prec;
+  const double* binv;              // device: NN x NN row-major (FP64)
+  const float* binv_f;             // device: NN x NN (hi, lo) pairs (double-float)
+  PdgCornerCoef c;
+};
+
 // ---- read-only view of a context for entry points outside pdg_api.cu ----
 #include <cuda_runtime.h>
 #include <string>
@@ -249,6 +291,16 @@ void pdg_model_constants(PdgModel* m);
 // halo / warm-up widths of the truncated tile start (influence <= 2^-56).  Returns 0, or
 // -1 when the theta system is singular or no width <= 128 meets the bound.
 int pdg_plan_diag(int d, double nux, double nuy, double theta, PdgDiagCoef* c);
+// Corner sub-step coefficients for degree d <= 3, nu_x, nu_y, nu_z > 0, 0 < theta <= 1:
+// fills c, binv[NN * NN] and binv_f[NN * NN * 2] (NN = (d+1)^3) and the start widths
+// (influence <= 2^-57 per upwind face set).  Returns 0, or -1 when the system is singular
+// or no width <= 64 meets the bound.
+int pdg_plan_corner(int d, double nux, double nuy, double nuz, double theta, PdgCornerCoef* c, double* binv,
+                    float* binv_f);
+
+// ---- kernels (pdg_corner.cu) ----
+int pdg_launch_corner(const PdgCornerPass& p, void* stream);
+size_t pdg_corner_smem(const PdgCornerPass& p);
 
 // ---- kernels (pdg_diag.cu) ----
 int pdg_launch_diag(const PdgDiagPass& p, void* stream);

@@ -122,6 +122,60 @@ __global__ void get_w_q19_kernel(const double* __restrict__ f, double* __restric
   }
 }
 
+// D3Q15 / D3Q27: w = (rho, rho u) in slots 0-3 -> f = f^eq(w).  rho goes to the rest
+// population and +-j_a/2 to the two axis populations of axis a (moments (rho, j) exactly);
+// one relaxation with omega = 1 (M1) then returns f^eq with the sweep's own arithmetic.
+template <class T, bool EDGES>
+__global__ void set_feq_corner_kernel(double* __restrict__ f, long long P, const __grid_constant__ PdgModel M1) {
+  constexpr int NV = EDGES ? 27 : 15;
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+       pt += (long long)gridDim.x * blockDim.x) {
+    const T ilam = PDG_K(T, M1, PDG_K_ILAM), hf = from_double<T>(0.5);
+    T v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = zero<T>();
+    v[0] = from_double<T>(f[pt]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T ja = from_double<T>(f[(a + 1) * P + pt]) * ilam * hf;
+      v[1 + 2 * a] = ja;
+      v[2 + 2 * a] = -ja;
+    }
+    d3q_corner_lattice_collide<T, EDGES>(v, M1);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) st(f + (long long)i * P + pt, v[i]);
+  }
+}
+
+// D3Q15 / D3Q27: w = P f = (sum f_i, lambda sum f_i xi_i).
+template <class T, bool EDGES>
+__global__ void get_w_corner_kernel(const double* __restrict__ f, double* __restrict__ w, long long P,
+                                    const __grid_constant__ PdgModel M) {
+  constexpr int NV = EDGES ? 27 : 15, C0 = EDGES ? 19 : 7;
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+       pt += (long long)gridDim.x * blockDim.x) {
+    T v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = ld<T>(f + (long long)i * P + pt);
+    T rho, jx, jy, jz;
+    if constexpr (EDGES) {
+      d3q19_moments<T>(v, &rho, &jx, &jy, &jz);
+    } else {
+      rho = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + v[6]);
+      jx = v[1] - v[2];
+      jy = v[3] - v[4];
+      jz = v[5] - v[6];
+    }
+    T cr, cx, cy, cz;
+    corner_moments<T>(v + C0, &cr, &cx, &cy, &cz);
+    const T lam = PDG_K(T, M, PDG_K_LAM);
+    w[pt] = to_double(rho + cr);
+    w[P + pt] = to_double(lam * (jx + cx));
+    w[2 * P + pt] = to_double(lam * (jy + cy));
+    w[3 * P + pt] = to_double(lam * (jz + cz));
+  }
+}
+
 __global__ void convert_kernel(double* __restrict__ f, long long n, int to_df) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -155,6 +209,8 @@ int pdg_model_variant(const PdgModel& m) {
     case PDG_MODEL_EULER: return m.dim == 1 ? MV_EU1 : (m.dim == 2 ? MV_EU2 : MV_EU3);
     case PDG_MODEL_ISOTHERMAL_D2Q9: return MV_D2Q9;
     case PDG_MODEL_ISOTHERMAL_D3Q19: return MV_D3Q19;
+    case PDG_MODEL_ISOTHERMAL_D3Q15: return MV_D3Q15;
+    case PDG_MODEL_ISOTHERMAL_D3Q27: return MV_D3Q27;
   }
   return -1;
 }
@@ -187,6 +243,18 @@ int pdg_launch_set_feq(double* f, long long P, const PdgModel& m, void* stream) 
       else
         set_feq_q19_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
       return (int)cudaGetLastError();
+    case MV_D3Q15:
+      if (m1.prec == PDG_PREC_DF32)
+        set_feq_corner_kernel<dd, false><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+      else
+        set_feq_corner_kernel<double, false><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+      return (int)cudaGetLastError();
+    case MV_D3Q27:
+      if (m1.prec == PDG_PREC_DF32)
+        set_feq_corner_kernel<dd, true><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+      else
+        set_feq_corner_kernel<double, true><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+      return (int)cudaGetLastError();
   }
   return (int)cudaErrorInvalidValue;
 }
@@ -198,6 +266,17 @@ int pdg_launch_get_w(const double* f, double* w, long long P, const PdgModel& m,
       get_w_q19_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
     else
       get_w_q19_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+    return (int)cudaGetLastError();
+  }
+  if (m.kind == PDG_MODEL_ISOTHERMAL_D3Q15 || m.kind == PDG_MODEL_ISOTHERMAL_D3Q27) {
+    const bool q27 = m.kind == PDG_MODEL_ISOTHERMAL_D3Q27;
+    if (m.prec == PDG_PREC_DF32) {
+      if (q27) get_w_corner_kernel<dd, true><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+      else get_w_corner_kernel<dd, false><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+    } else {
+      if (q27) get_w_corner_kernel<double, true><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+      else get_w_corner_kernel<double, false><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+    }
     return (int)cudaGetLastError();
   }
   if (m.kind == PDG_MODEL_ISOTHERMAL_D2Q9) {

@@ -58,6 +58,8 @@ int launch_pass_np(const PdgPass& p, cudaStream_t st) {
     case MV_EU3: return launch_pass_t<NP, MV_EU3, T>(p, st);
     case MV_D2Q9: return launch_pass_t<NP, MV_D2Q9, T>(p, st);
     case MV_D3Q19: return launch_pass_t<NP, MV_D3Q19, T>(p, st);
+    case MV_D3Q15: return launch_pass_t<NP, MV_D3Q15, T>(p, st);
+    case MV_D3Q27: return launch_pass_t<NP, MV_D3Q27, T>(p, st);
   }
   return (int)cudaErrorInvalidValue;
 }

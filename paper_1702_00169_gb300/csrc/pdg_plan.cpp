@@ -14,6 +14,7 @@
 // Everything is computed in double with FP contraction disabled (build flag), so
 // the x86-64 and aarch64 builds produce identical coefficients.
 #include <cmath>
+#include <utility>
 #include <cstring>
 #include <vector>
 
@@ -213,11 +214,17 @@ void pdg_model_constants(PdgModel* m) {
   m->k[PDG_K_HALFG] = 0.5 * m->gravity;
   m->k[PDG_K_GM1] = m->gamma - 1.0;
   m->k[PDG_K_HALF] = 0.5;
-  if (m->kind == 3 || m->kind == 4) {  // D2Q9 (Section 5.1) / D3Q19 lattice weights
-    const bool q19 = m->kind == 4;
-    m->k[PDG_K_Q9W0] = om * (q19 ? 1.0 / 3.0 : 4.0 / 9.0);
-    m->k[PDG_K_Q9W1] = om * (q19 ? 1.0 / 18.0 : 1.0 / 9.0);
-    m->k[PDG_K_Q9W2] = om * (1.0 / 36.0);
+  if (m->kind >= 3 && m->kind <= 6) {  // lattice weights: rest, axis, edge, corner
+    // D2Q9 (Section 5.1), D3Q19, D3Q15, D3Q27
+    static const double W[4][4] = {{4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0, 0.0},
+                                   {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0, 0.0},
+                                   {2.0 / 9.0, 1.0 / 9.0, 0.0, 1.0 / 72.0},
+                                   {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0}};
+    const double* w = W[m->kind - 3];
+    m->k[PDG_K_Q9W0] = om * w[0];
+    m->k[PDG_K_Q9W1] = om * w[1];
+    m->k[PDG_K_Q9W2] = om * w[2];
+    m->k[PDG_K_Q9W3] = om * w[3];
     m->k[PDG_K_SIXTH] = 1.0 / 6.0;
     m->k[PDG_K_ILAM] = 1.0 / m->lambda;
     m->k[PDG_K_LAM] = m->lambda;
@@ -348,5 +355,150 @@ int pdg_plan_diag(int d, double nux, double nuy, double theta, PdgDiagCoef* c) {
   pdg_split(c->omtheta, c->omtheta_f[0]);
   pdg_split(c->kx, c->kx_f[0]);
   pdg_split(c->ky, c->ky_f[0]);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Corner velocities (D3Q15 / D3Q27).  eq. (3.7) splits by axis on a Cartesian cell (as for
+// the diagonal velocities above), so for v = lambda (s_x, s_y, s_z), in the traversal
+// orientation,
+//   B fn_c = (I - (1-theta) K3) f_c + k_x S_x Lt + k_y S_y Bt + k_z S_z Zt,
+//   K3 = nu_x I(x)I(x)K + nu_y I(x)K(x)I + nu_z K(x)I(x)I,  B = I + theta K3,
+// on the node vector p = (iz n + iy) n + ix, and B^-1 (I - (1-theta) K3) = B^-1/theta - c1 I.
+//
+// Start widths.  The theta-weighted values on the three downwind faces of a cell,
+// s_c = (R_c, T_c, U_c) (R: nodes (iz, iy, n-1), T: (iz, n-1, ix), U: (n-1, iy, ix)), obey
+// s_c = a_c + X_x R_{c-x} + X_y T_{c-y} + X_z U_{c-z}, X_a = theta k_a (rows of B^-1 at the
+// face nodes, columns at the nodes the face a enters).  A region swept from W cells
+// upwind along x starts from the old face values on its x edge (error <= 2 max|f| per
+// entry); an error entering there reaches the cell W columns downwind, r rows and k
+// layers along the edge, through the signed lattice-path sum
+//   G(j, r, k) = X_x G(j-1, r, k) + X_y G(j, r-1, k) + X_z G(j, r, k-1),
+// so the effect on any cell of that column is at most 2 max|f| g sum_{r,k} ||G(W, r, k)||_inf
+// (g: largest change of a cell value per unit change of its inflow faces).  W is the
+// smallest width for which this is <= 2^-57 max|f|, for each of the three edges (the y and
+// z edges exchange the roles of the directions).  The sums run over r, k < 48, far past
+// the decay of the terms; the plan is refused when the last row or layer of the sum still
+// carries more than 2^-67 of the total.
+static int corner_width(int n, const std::vector<double>& X, int edge, double g) {
+  const int nn = n * n, m = 3 * nn, R = 48, RR = R * R;
+  const size_t msz = (size_t)m * nn;
+  std::vector<double> bufA((size_t)RR * msz, 0.0), bufB((size_t)RR * msz, 0.0);
+  double* prev = bufA.data();
+  double* cur = bufB.data();
+  const int dir[3] = {edge, (edge + 1) % 3, (edge + 2) % 3};   // across, along 1, along 2
+  for (int c = 0; c < nn; ++c) prev[(size_t)(edge * nn + c) * nn + c] = 1.0;
+  const double tol = std::ldexp(1.0, -57);
+  // acc += X_a (block a of the face state of G)
+  auto apply = [&](int a, const double* G, double* acc) {
+    const double* Xa = X.data() + (size_t)a * m * nn;
+    for (int s = 0; s < m; ++s) {
+      double* out = acc + (size_t)s * nn;
+      for (int t = 0; t < nn; ++t) {
+        const double x = Xa[s * nn + t];
+        if (x == 0.0) continue;
+        const double* row = G + (size_t)(a * nn + t) * nn;
+        for (int c = 0; c < nn; ++c) out[c] += x * row[c];
+      }
+    }
+  };
+  for (int W = 1; W <= 64; ++W) {
+    double total = 0.0, rim = 0.0;
+    for (int r = 0; r < R; ++r)
+      for (int k = 0; k < R; ++k) {
+        double* G = cur + (size_t)(r * R + k) * msz;
+        for (size_t i = 0; i < msz; ++i) G[i] = 0.0;
+        apply(dir[0], prev + (size_t)(r * R + k) * msz, G);
+        if (r > 0) apply(dir[1], cur + (size_t)((r - 1) * R + k) * msz, G);
+        if (k > 0) apply(dir[2], cur + (size_t)(r * R + k - 1) * msz, G);
+        double nrm = 0.0;
+        for (int s = 0; s < m; ++s) {
+          double rs = 0.0;
+          for (int c = 0; c < nn; ++c) rs += std::fabs(G[(size_t)s * nn + c]);
+          if (rs > nrm) nrm = rs;
+        }
+        total += nrm;
+        if (r == R - 1 || k == R - 1) rim += nrm;
+      }
+    if (!(total < 1e300)) return -1;
+    if (2.0 * g * total <= tol) return 2.0 * g * rim <= std::ldexp(tol, -10) ? W : -1;
+    std::swap(prev, cur);
+  }
+  return -1;
+}
+
+int pdg_plan_corner(int d, double nux, double nuy, double nuz, double theta, PdgCornerCoef* c, double* binv,
+                    float* binv_f) {
+  const int n = d + 1, nn = n * n, NN = nn * n;
+  if (n < 2 || n > PDG_MAXN_CORNER || !(theta > 0.0 && theta <= 1.0) || !(nux > 0.0) || !(nuy > 0.0) ||
+      !(nuz > 0.0) || !std::isfinite(nux) || !std::isfinite(nuy) || !std::isfinite(nuz))
+    return -1;
+  double x[PDG_MAXN], w[PDG_MAXN], K[PDG_MAXN * PDG_MAXN];
+  if (pdg_plan_gl(d, x, w)) return -1;
+  pdg_plan_dmat(n, x, K);
+  K[0] += 1.0 / w[0];
+  std::vector<double> A((size_t)NN * NN), R((size_t)NN * NN);
+  for (int p = 0; p < NN; ++p) {
+    const int iz = p / nn, iy = (p / n) % n, ix = p % n;
+    for (int q = 0; q < NN; ++q) {
+      const int jz = q / nn, jy = (q / n) % n, jx = q % n;
+      double k3 = 0.0;
+      if (iz == jz && iy == jy) k3 += nux * K[ix * n + jx];
+      if (iz == jz && ix == jx) k3 += nuy * K[iy * n + jy];
+      if (iy == jy && ix == jx) k3 += nuz * K[iz * n + jz];
+      A[(size_t)p * NN + q] = (p == q ? 1.0 : 0.0) + theta * k3;
+      R[(size_t)p * NN + q] = (p == q ? 1.0 : 0.0);
+    }
+  }
+  if (solve(NN, NN, A.data(), R.data())) return -1;
+  std::memset(c, 0, sizeof(*c));
+  for (int i = 0; i < NN * NN; ++i) {
+    binv[i] = R[i];
+    pdg_split(R[i], binv_f + 2 * i);
+  }
+  c->theta = theta;
+  c->omtheta = 1.0 - theta;
+  c->rtheta = 1.0 / theta;
+  c->c1 = (1.0 - theta) / theta;
+  c->kx = nux / w[0];
+  c->ky = nuy / w[0];
+  c->kz = nuz / w[0];
+  const double ka[3] = {c->kx, c->ky, c->kz};
+  auto idx = [&](int iz, int iy, int ix) { return (iz * n + iy) * n + ix; };
+  auto fnode = [&](int s) {
+    const int a = s / nn, u = (s % nn) / n, v = s % n;
+    return a == 0 ? idx(u, v, n - 1) : (a == 1 ? idx(u, n - 1, v) : idx(n - 1, u, v));
+  };
+  auto inj = [&](int a, int t) {
+    const int u = t / n, v = t % n;
+    return a == 0 ? idx(u, v, 0) : (a == 1 ? idx(u, 0, v) : idx(0, u, v));
+  };
+  const int m = 3 * nn;
+  std::vector<double> X((size_t)3 * m * nn);
+  for (int a = 0; a < 3; ++a)
+    for (int s = 0; s < m; ++s)
+      for (int t = 0; t < nn; ++t)
+        X[((size_t)a * m + s) * nn + t] = theta * ka[a] * R[(size_t)fnode(s) * NN + inj(a, t)];
+  double g = 0.0;
+  for (int p = 0; p < NN; ++p) {
+    double acc = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int t = 0; t < nn; ++t) acc += std::fabs(theta * ka[a] * R[(size_t)p * NN + inj(a, t)]);
+    if (acc > g) g = acc;
+  }
+  c->wx = corner_width(n, X, 0, g);
+  // equal Courant numbers: the three edges are images of each other under a permutation
+  // of the axes, which maps the node and face orderings onto each other
+  const bool cubic = nux == nuy && nuy == nuz;
+  c->wy = cubic ? c->wx : corner_width(n, X, 1, g);
+  c->wz = cubic ? c->wx : corner_width(n, X, 2, g);
+  if (c->wx < 0 || c->wy < 0 || c->wz < 0) return -1;
+  pdg_split(c->rtheta, c->rtheta_f[0]);
+  pdg_split(c->c1, c->c1_f[0]);
+  pdg_split(c->theta, c->theta_f[0]);
+  pdg_split(c->omtheta, c->omtheta_f[0]);
+  pdg_split(c->kx, c->kx_f[0]);
+  pdg_split(c->ky, c->ky_f[0]);
+  pdg_split(c->kz, c->kz_f[0]);
   return 0;
 }

@@ -18,6 +18,7 @@ PDG_OK = 0
 PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA, PDG_ERR_STATE, PDG_ERR_TIMEOUT, PDG_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 PDG_MODEL_ADVECTION, PDG_MODEL_SHALLOW_WATER, PDG_MODEL_EULER = 0, 1, 2
 PDG_MODEL_ISOTHERMAL_D2Q9, PDG_MODEL_ISOTHERMAL_D3Q19 = 3, 4
+PDG_MODEL_ISOTHERMAL_D3Q15, PDG_MODEL_ISOTHERMAL_D3Q27 = 5, 6
 PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED, PDG_SCHEME_M2KIN = 0, 1, 2
 PDG_PREC_FP64 = 0
 PDG_PREC_DF32 = 1
@@ -25,7 +26,8 @@ PRECISION = {"fp64": PDG_PREC_FP64, "df32": PDG_PREC_DF32}
 PDG_OPT_COMPOSE_TT = 1
 
 KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER,
-        "isothermal_d2q9": PDG_MODEL_ISOTHERMAL_D2Q9, "isothermal_d3q19": PDG_MODEL_ISOTHERMAL_D3Q19}
+        "isothermal_d2q9": PDG_MODEL_ISOTHERMAL_D2Q9, "isothermal_d3q19": PDG_MODEL_ISOTHERMAL_D3Q19,
+        "isothermal_d3q15": PDG_MODEL_ISOTHERMAL_D3Q15, "isothermal_d3q27": PDG_MODEL_ISOTHERMAL_D3Q27}
 SCHEME = {"M2": PDG_SCHEME_M2, "M2_collapsed": PDG_SCHEME_M2_COLLAPSED, "M2_kin": PDG_SCHEME_M2KIN}
 
 
@@ -257,10 +259,10 @@ class Solver:
 
     def timing_read(self):
         """Per kernel kind (0 line pass, 1 line pass with collision, 2 state kernels,
-        3 D2Q9 diagonal pass): launches and summed ms."""
-        la = (ctypes.c_longlong * 4)()
-        ms = (ctypes.c_double * 4)()
-        self._check(pdg_timing_read(self.ctx, ctypes.addressof(la), ctypes.addressof(ms), 4), "pdg_timing_read")
+        3 diagonal pass, 4 corner pass): launches and summed ms."""
+        la = (ctypes.c_longlong * 5)()
+        ms = (ctypes.c_double * 5)()
+        self._check(pdg_timing_read(self.ctx, ctypes.addressof(la), ctypes.addressof(ms), 5), "pdg_timing_read")
         return list(la), list(ms)
 
     def set_launch(self, kind, lpb, nseg, ngroup):

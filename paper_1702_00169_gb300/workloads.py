@@ -21,8 +21,8 @@ synthetic and drawn from ``numpy.random.default_rng(seed)``):
 * isothermal D2Q9 (the model of the paper's Euler-with-gravity test, without the
   source): rho = 1 + 0.05 F_rho, u_a = 0.05 F_a with independent fields built like
   F above; w = (rho, rho u_x, rho u_y); lambda = 1 (sound speed 1/sqrt(3), Mach <= 0.09).
-* isothermal D3Q19 (a lattice of the paper's 3-D scaling runs): the same recipe in 3-D
-  (|k|_inf <= 2), w = (rho, rho u).
+* isothermal D3Q19, D3Q15, D3Q27 (the lattices of the paper's 3-D scaling runs): the
+  same recipe in 3-D (|k|_inf <= 2), w = (rho, rho u).
 """
 import math
 from dataclasses import dataclass, field
@@ -30,7 +30,8 @@ from typing import Tuple
 
 import numpy as np
 
-KINDS = ("advection", "shallow_water", "euler", "isothermal_d2q9", "isothermal_d3q19")
+KINDS = ("advection", "shallow_water", "euler", "isothermal_d2q9", "isothermal_d3q19", "isothermal_d3q15",
+         "isothermal_d3q27")
 
 
 @dataclass
@@ -55,7 +56,7 @@ class Config:
     @property
     def m(self):
         return {"advection": 1, "shallow_water": 3, "euler": self.dim + 2, "isothermal_d2q9": 3,
-                "isothermal_d3q19": 4}[self.kind]
+                "isothermal_d3q19": 4, "isothermal_d3q15": 4, "isothermal_d3q27": 4}[self.kind]
 
     @property
     def groups(self):
@@ -64,8 +65,9 @@ class Config:
 
     @property
     def nv(self):
-        """Populations per group: 2D (DnQ2n), 9 (D2Q9) or 19 (D3Q19)."""
-        return {"isothermal_d2q9": 9, "isothermal_d3q19": 19}.get(self.kind, 2 * self.dim)
+        """Populations per group: 2D (DnQ2n), 9 (D2Q9), 15 / 19 / 27 (D3Qq)."""
+        return {"isothermal_d2q9": 9, "isothermal_d3q19": 19, "isothermal_d3q15": 15,
+                "isothermal_d3q27": 27}.get(self.kind, 2 * self.dim)
 
     @property
     def ncells(self):
@@ -117,8 +119,12 @@ D2Q9_ISO = Config("isothermal_d2q9_64x64x8x8_d3", "isothermal_d2q9", 2, (64, 64)
 
 D3Q19_ISO = Config("isothermal_d3q19_32c3x4c3_d2", "isothermal_d3q19", 3, (32, 32, 32), (4, 4, 4), 2,
                    lam=1.0, steps=10, seed=7)
+D3Q15_ISO = Config("isothermal_d3q15_32c3x4c3_d2", "isothermal_d3q15", 3, (32, 32, 32), (4, 4, 4), 2,
+                   lam=1.0, steps=4, seed=8)
+D3Q27_ISO = Config("isothermal_d3q27_32c3x4c3_d2", "isothermal_d3q27", 3, (32, 32, 32), (4, 4, 4), 2,
+                   lam=1.0, steps=4, seed=9)
 
-CONFIGS = {c.name: c for c in (ADVECTION_D2Q4, SW_D2Q4, EULER_D3Q6, D2Q9_ISO, D3Q19_ISO)}
+CONFIGS = {c.name: c for c in (ADVECTION_D2Q4, SW_D2Q4, EULER_D3Q6, D2Q9_ISO, D3Q19_ISO, D3Q15_ISO, D3Q27_ISO)}
 
 
 def _grid(coords):
@@ -199,7 +205,7 @@ def initial_w(cfg, coords):
         p = 1.0
         E = p / (cfg.gamma - 1.0) + 0.5 * rho * sum(ua * ua for ua in u)
         return np.stack([rho] + [rho * ua for ua in u] + [E]).astype(np.float64)
-    if cfg.kind in ("isothermal_d2q9", "isothermal_d3q19"):
+    if cfg.kind.startswith("isothermal"):
         kmax, ref = (4, 256) if D == 2 else (2, 48)
         Fr = _normalised_field(rng, D, 16, kmax, ref)
         Fu = [_normalised_field(rng, D, 16, kmax, ref) for _ in range(D)]

@@ -7,7 +7,8 @@ from oracle import scheme as OS
 from oracle.dg import CartesianMesh
 
 ORACLE_KIND = {"advection": OM.ADVECTION, "shallow_water": OM.SHALLOW_WATER, "euler": OM.EULER,
-               "isothermal_d2q9": OM.ISOTHERMAL_D2Q9, "isothermal_d3q19": OM.ISOTHERMAL_D3Q19}
+               "isothermal_d2q9": OM.ISOTHERMAL_D2Q9, "isothermal_d3q19": OM.ISOTHERMAL_D3Q19,
+               "isothermal_d3q15": OM.ISOTHERMAL_D3Q15, "isothermal_d3q27": OM.ISOTHERMAL_D3Q27}
 
 
 def rel_l2(a, b):
