@@ -21,6 +21,9 @@ LIB = os.path.join(LIBDIR, "libpdg.so")
 SOURCES = ["pdg_batch_df.cu", "pdg_batch.cu", "pdg_kernels_df.cu", "pdg_kernels.cu", "pdg_diag_df.cu",
            "pdg_diag.cu", "pdg_corner_df.cu", "pdg_corner.cu", "pdg_api.cu", "pdg_noalloc.cu", "pdg_server.cu",
            "pdg_plan.cpp"]
+# pass-kernel instantiations: one object per (number type, group of model variants)
+INSTANCES = [("pdg_pass_inst.cu", f"pdg_pass_t{t}_g{g}", [f"-DPDG_INST_T={t}", f"-DPDG_INST_GROUP={g}"])
+             for t in (1, 0) for g in (3, 2, 1, 0)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I", os.path.join(ROOT, "include")]
@@ -33,9 +36,10 @@ def nvcc():
     raise RuntimeError("nvcc not found")
 
 
-def _compile(src):
-    obj = os.path.join(OBJDIR, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc()] + ARCH + COMMON + ["-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(job):
+    src, name, defs = job if isinstance(job, tuple) else (job, os.path.splitext(job)[0], [])
+    obj = os.path.join(OBJDIR, name + ".o")
+    cmd = [nvcc()] + ARCH + COMMON + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cpp"):
         cmd = [nvcc()] + COMMON + ["-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -47,8 +51,9 @@ def _compile(src):
 def build(verbose=False):
     os.makedirs(OBJDIR, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(_compile, SOURCES))
+    jobs = INSTANCES + SOURCES   # the slowest objects first
+    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        objs = list(ex.map(_compile, jobs))
     tmp = LIB + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -67,6 +67,8 @@ struct pdg_ctx {
   };
   std::vector<CornerPlan> corner_plans;
   char* cbuf = nullptr;
+  double* czt = nullptr;                       // corner pass: per-block +z face scratch
+  size_t czt_cap = 0;                          // its capacity (8-byte words)
   int cshape[4] = {0, 0, 0, 0};                // corner pass: threads, box x, y, z (0 = heuristic)
   double* kfield = nullptr;                    // penalisation K at every point
   bool timing = false;
@@ -546,7 +548,10 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
     p.nty = (p.ncy + p.ty - 1) / p.ty;
     p.ntz = (p.ncz + p.tz - 1) / p.tz;
   } else {
-    const int slots = 152;
+    // cost of one block in node dot products: output cells (all NN nodes) and start cells
+    // (NFF face nodes) of every layer, plus about 4 cells of overhead per wavefront step;
+    // one block per SM (512 threads at ~86 registers)
+    const double NN = (double)c->n * c->n * c->n, NFF = NN - (double)(c->n - 1) * (c->n - 1) * (c->n - 1);
     double best = 1e300;
     auto tiles = [](int N, int cap) {   // candidate (count, size) pairs with a non-empty last box
       std::vector<std::pair<int, int>> v;
@@ -560,18 +565,20 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
     };
     const auto TX = tiles(p.ncx, 64), TY = tiles(p.ncy, 64), TZ = tiles(p.ncz, 64);
     for (auto [ntx, tx] : TX)
-      for (auto [nty, ty] : TY) {
-        PdgCornerPass q = p;
-        q.tx = tx;
-        q.ty = ty;
-        q.tz = p.ncz;
-        if (pdg_corner_smem(q) > 200 * 1024) continue;
+      for (auto [nty, ty] : TY)
         for (auto [ntz, tz] : TZ) {
+          PdgCornerPass q = p;
+          q.tx = tx;
+          q.ty = ty;
+          q.tz = tz;
+          if (pdg_corner_smem(q) > 200 * 1024) continue;
           const long long blocks = 8LL * ntx * nty * ntz;
-          const long long waves = (blocks + slots - 1) / slots;
-          const double layer = (double)(tx + p.c.wx) * (double)(ty + p.c.wy);
+          const long long waves = (blocks + 151) / 152;
+          const double region = (double)(tx + p.c.wx) * (double)(ty + p.c.wy), out = (double)tx * ty;
           const double steps = (double)(tx + p.c.wx + ty + p.c.wy);
-          const double cost = (double)waves * (double)(tz + p.c.wz) * (layer + 8.0 * steps);
+          const double work = tz * (out * NN + (region - out) * NFF) + p.c.wz * region * NFF +
+                              (double)(tz + p.c.wz) * 4.0 * NN * steps;
+          const double cost = (double)waves * work;
           if (cost < best) {
             best = cost;
             p.tx = tx;
@@ -582,12 +589,25 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
             p.ntz = ntz;
           }
         }
-      }
     if (best == 1e300) return fail(c, PDG_ERR_UNSUPPORTED, "corner box too large for shared memory");
   }
   if (pdg_corner_smem(p) > 200 * 1024) return fail(c, PDG_ERR_UNSUPPORTED, "corner box too large");
-  if (p.threads < (int)(c->n * c->n * c->n) || p.threads > 512)
-    return fail(c, PDG_ERR_ARG, "corner pass: threads per block below the nodes of a cell");
+  if (p.threads < 64 || p.threads > 512) return fail(c, PDG_ERR_ARG, "corner pass: threads per block");
+  // +z face scratch of the launch (grown on demand; cudaFree waits for the device)
+  const size_t words = pdg_corner_scratch(p);
+  if (words > c->czt_cap) {
+    if (c->czt) cudaFree(c->czt);
+    c->czt = nullptr;
+    c->czt_cap = 0;
+    cudaError_t e = cudaMalloc((void**)&c->czt, sizeof(double) * words);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->czt = nullptr;
+      return fail(c, PDG_ERR_OOM, std::string("corner face scratch: ") + cudaGetErrorString(e));
+    }
+    c->czt_cap = words;
+  }
+  p.zt = c->czt;
   return PDG_OK;
 }
 
@@ -1348,6 +1368,7 @@ int pdg_destroy(pdg_ctx* c) {
   if (c->wstage) cudaFree(c->wstage);
   if (c->kfield) cudaFree(c->kfield);
   if (c->cbuf) cudaFree(c->cbuf);
+  if (c->czt) cudaFree(c->czt);
   free_inflow(c);
   delete c;
   return PDG_OK;

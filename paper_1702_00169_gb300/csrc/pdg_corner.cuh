@@ -15,15 +15,21 @@
 // along z; inside a layer, column j handles row t - j at step t (a skewed 2-D wavefront:
 // every cell of an anti-diagonal is independent).  The +x and +y faces pass between the
 // steps of a layer through shared memory (double-buffered by step parity); the +z face of
-// every cell of the layer's region stays in shared memory until the cell above reads it.
+// every cell of the layer's region is kept until the cell above reads it.
 // No block waits on another block.  Reads come from the input slots and writes go to the
 // output slots, so overlapping regions of neighbouring boxes never see a new value.
 //
 // Work split per step: (A) the block builds r_c for every cell of the anti-diagonal in
-// shared memory, (B) the threads of a cell form its n^3 output nodes as dot products with
-// r_c (Binv sits in shared memory transposed, so the threads of a cell read consecutive
-// words; the FP64 pipe, not shared memory, bounds this loop).  The state of the next
-// anti-diagonal is copied into shared memory with cp.async while (B) runs.
+// shared memory, (B) the threads form the output nodes as dot products with r_c (Binv sits
+// in shared memory transposed, so the threads of a cell read consecutive words; the FP64
+// pipe, not shared memory, bounds this loop): all n^3 nodes of an output cell, only the
+// face nodes of a cell of the upwind start.  The state of the next anti-diagonal (and the
+// +z faces it reads) is copied into shared memory with cp.async while (B) runs.
+//
+// Memory: the +z faces of a layer (one face per cell of the region, the largest per-block
+// array) live in a global scratch slice of the block (PdgCornerPass::zt, L2-resident),
+// which keeps shared memory for the staging buffers and lets boxes grow; each entry is
+// written one layer before it is staged again, with many barriers in between.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -34,6 +40,7 @@ namespace pdgdev {
 struct CornerGeom {
   const double* fin;
   double* fout;
+  double* zt;              // this block's +z faces: [nrow][ncol][n^2] (global scratch)
   int sx, sy, sz;
   long long sa, sb, sc;
   int ncol, nrow, nlay, wx, wy, wz;
@@ -48,18 +55,27 @@ __device__ __forceinline__ long long corner_off(const CornerGeom& g, int j, int 
          g.colx[j + 1] + (long long)(g.sx * ix) * g.sa;
 }
 
-// Stage the state of every cell of anti-diagonal t of layer k (all n^3 nodes) and, on the
-// region's upwind x and y edges, the old face values entering it.
+// Row of one cell in the staging buffers: its n^3 state values, then the n^2 values on the
+// +z face of the cell below it (the face it reads), padded to 16 bytes.
+template <int NP>
+struct CornerRow {
+  static constexpr int NF = NP * NP, NN = NF * NP, RS = (NN + NF + 1) & ~1;
+};
+
+// Stage the state and the entering +z faces of every cell of anti-diagonal t of layer k,
+// and, on the region's upwind x and y edges, the old face values entering it.
 template <int NP>
 __device__ __forceinline__ void corner_stage(const CornerGeom& g, int k, int t, double* fb, double* lbnd,
                                              double* bbnd) {
-  constexpr int NF = NP * NP, NN = NF * NP, RS = (NN + 1) & ~1;
+  constexpr int NF = CornerRow<NP>::NF, NN = CornerRow<NP>::NN, RS = CornerRow<NP>::RS;
   const int jlo = max(0, t - g.nrow + 1), jhi = min(g.ncol - 1, t);
   const int A = jhi - jlo + 1;
-  for (int i = threadIdx.x; i < A * NN; i += blockDim.x) {
-    const int c = i / NN, q = i % NN;
-    const int j = jlo + c;
-    cp_async8(fb + c * RS + q, g.fin + corner_off(g, j, t - j, k, q / NF, (q / NP) % NP, q % NP));
+  for (int i = threadIdx.x; i < A * (NN + NF); i += blockDim.x) {
+    const int c = i / (NN + NF), q = i % (NN + NF);
+    const int j = jlo + c, r = t - j;
+    const double* src = q < NN ? g.fin + corner_off(g, j, r, k, q / NF, (q / NP) % NP, q % NP)
+                               : g.zt + ((long long)r * g.ncol + j) * NF + (q - NN);
+    cp_async8(fb + c * RS + q, src);
   }
   const int tid = threadIdx.x;
   if (jlo == 0 && tid < NF)   // column 0 at row t: +x face of the cell upwind of it
@@ -72,7 +88,8 @@ __device__ __forceinline__ void corner_stage(const CornerGeom& g, int k, int t, 
 
 template <int NP, class T>
 __device__ __forceinline__ void corner_body(const PdgCornerPass& p, double* sm) {
-  constexpr int NF = NP * NP, NN = NF * NP, RS = (NN + 1) & ~1;   // RS: 16-byte aligned rows
+  constexpr int NF = CornerRow<NP>::NF, NN = CornerRow<NP>::NN, RS = CornerRow<NP>::RS;
+  constexpr int NFF = NN - (NP - 1) * (NP - 1) * (NP - 1);   // nodes on the three downwind faces
   int b = blockIdx.x;
   const int txi = b % p.ntx;
   b /= p.ntx;
@@ -81,6 +98,8 @@ __device__ __forceinline__ void corner_body(const PdgCornerPass& p, double* sm) 
   const int tzi = b % p.ntz;
   const int pop = b / p.ntz;
   const PdgCornerCoef& C = p.c;
+  const int CM = p.tx + C.wx, RM = p.ty + C.wy;   // column / row capacities of any box
+  const int amax = min(CM, RM);                   // longest anti-diagonal
 
   CornerGeom g;
   g.fin = p.fin[pop];
@@ -98,24 +117,23 @@ __device__ __forceinline__ void corner_body(const PdgCornerPass& p, double* sm) 
   g.ncol = min(p.tx, p.ncx - X0) + g.wx;
   g.nrow = min(p.ty, p.ncy - Y0) + g.wy;
   g.nlay = min(p.tz, p.ncz - Z0) + g.wz;
+  g.zt = p.zt + (long long)blockIdx.x * RM * CM * NF;
   const int T_steps = g.ncol + g.nrow - 1;
-  const int CM = p.tx + C.wx, RM = p.ty + C.wy;   // column / row capacities of any box
-  const int amax = min(CM, RM);                                     // longest anti-diagonal
 
   // shared memory: BinvT[NN][NN] | rbuf[amax][RS] | fbuf[2][amax][RS] | Lt[2][CM+1][NF] |
-  //                Bt[2][CM][NF] | Zt[RM][CM][NF] | lbnd[2][NF] | bbnd[2][NF] |
+  //                Bt[2][CM][NF] | lbnd[2][NF] | bbnd[2][NF] | fnode[NFF] (int) |
   //                colx[CM+1] | rowy[RM+1] | layz[tz+wz+1] (64-bit offsets)
   T* BinvT = reinterpret_cast<T*>(sm);
   T* rbuf = BinvT + NN * NN;
   T* fbuf = rbuf + (size_t)amax * RS;
   T* Lt = fbuf + (size_t)2 * amax * RS;
   T* Bt = Lt + (size_t)2 * (CM + 1) * NF;
-  T* Zt = Bt + (size_t)2 * CM * NF;
-  T* lbnd = Zt + (size_t)RM * CM * NF;
+  T* lbnd = Bt + (size_t)2 * CM * NF;
   T* bbnd = lbnd + 2 * NF;
   long long* colx = reinterpret_cast<long long*>(bbnd + 2 * NF);
   long long* rowy = colx + (CM + 1);
   long long* layz = rowy + (RM + 1);
+  int* fnode = reinterpret_cast<int*>(layz + (p.tz + C.wz + 1));
   const int LtS = CM + 1, BtS = CM;
   for (int i = threadIdx.x; i < NN * NN; i += blockDim.x) {
     const int row = i % NN, col = i / NN;   // BinvT[col][row] = Binv[row][col]
@@ -125,6 +143,11 @@ __device__ __forceinline__ void corner_body(const PdgCornerPass& p, double* sm) 
       const float* bf = p.binv_f + 2 * (row * NN + col);
       BinvT[i] = T{bf[0], bf[1]};
     }
+  }
+  if (threadIdx.x == 0) {   // the face nodes, in node order
+    int f = 0;
+    for (int q = 0; q < NN; ++q)
+      if (q % NP == NP - 1 || (q / NP) % NP == NP - 1 || q / NF == NP - 1) fnode[f++] = q;
   }
   for (int j = threadIdx.x; j <= g.ncol; j += blockDim.x) {
     const int tc = wrap_cell(X0 - g.wx + j - 1, p.ncx);
@@ -146,16 +169,12 @@ __device__ __forceinline__ void corner_body(const PdgCornerPass& p, double* sm) 
   for (int i = threadIdx.x; i < g.nrow * g.ncol * NF; i += blockDim.x) {
     const int cell = i / NF, u = i % NF;
     const int r = cell / g.ncol, j = cell % g.ncol;
-    cp_async8(reinterpret_cast<double*>(Zt + ((size_t)r * CM + j) * NF + u),
-              g.fin + corner_off(g, j, r, -1, NP - 1, u / NP, u % NP));
+    g.zt[i] = g.fin[corner_off(g, j, r, -1, NP - 1, u / NP, u % NP)];
   }
+  __syncthreads();
   const T rth = PDG_DC(T, C, rtheta), c1 = PDG_DC(T, C, c1);
-  const T th = PDG_DC(T, C, theta), omth = PDG_DC(T, C, omtheta);
+  const T th = PDG_DC(T, C, theta);
   const T kx = PDG_DC(T, C, kx), ky = PDG_DC(T, C, ky), kz = PDG_DC(T, C, kz);
-  // output mapping: thread (kq, qq) computes node qq of cells jlo + kq, jlo + kq + K, ...
-  const int K = blockDim.x / NN;
-  const int kq = threadIdx.x / NN, qq = threadIdx.x % NN;
-  const int qz = qq / NF, qy = (qq / NP) % NP, qx = qq % NP;
 
   corner_stage<NP>(g, 0, 0, reinterpret_cast<double*>(fbuf), reinterpret_cast<double*>(lbnd),
                    reinterpret_cast<double*>(bbnd));
@@ -179,7 +198,7 @@ __device__ __forceinline__ void corner_body(const PdgCornerPass& p, double* sm) 
           rv = fma(kx, j == 0 ? lbnd[par * NF + iz * NP + iy] : Lt[((size_t)prv * LtS + j) * NF + iz * NP + iy], rv);
         if (iy == 0)
           rv = fma(ky, r == 0 ? bbnd[par * NF + iz * NP + ix] : Bt[((size_t)prv * BtS + j) * NF + iz * NP + ix], rv);
-        if (iz == 0) rv = fma(kz, Zt[((size_t)r * CM + j) * NF + iy * NP + ix], rv);
+        if (iz == 0) rv = fma(kz, fc[c * RS + NN + iy * NP + ix], rv);
         rbuf[c * RS + q] = rv;
       }
       __syncthreads();
@@ -190,41 +209,64 @@ __device__ __forceinline__ void corner_body(const PdgCornerPass& p, double* sm) 
         if (t + 1 < T_steps) corner_stage<NP>(g, k, t + 1, nf, nl, nb);
         else if (k + 1 < g.nlay) corner_stage<NP>(g, k + 1, 0, nf, nl, nb);
       }
-      // (B) every node of every cell of the anti-diagonal; only output cells are stored
-      if (kq < K) {
-        for (int j = jlo + kq; j <= jhi; j += K) {
-          const int c = j - jlo, r = t - j;
-          const T* rc = rbuf + c * RS;
-          T acc;
-          if constexpr (__is_same(T, double)) {
-            double a[4] = {0.0, 0.0, 0.0, 0.0};
+      // (B) output cells [h1, h2] (columns >= wx, rows >= wy, in a layer >= wz): every node;
+      // the cells of the upwind start: only their face nodes.  Items are (cell, node)
+      // pairs, output cells first, consecutive threads on consecutive nodes of a cell.
+      int h1 = jhi + 1, h2 = jhi;
+      if (out_layer) {
+        h1 = max(jlo, min(g.wx, jhi + 1));
+        h2 = max(h1 - 1, min(jhi, t - g.wy));
+      }
+      const int nout = (h2 - h1 + 1) * NN, nlo = (h1 - jlo) * NFF;
+      const int items = nout + (A * NFF - (h2 - h1 + 1) * NFF);
+      for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        int j, q;
+        if (it < nout) {
+          j = h1 + it / NN;
+          q = it % NN;
+        } else if (it - nout < nlo) {
+          j = jlo + (it - nout) / NFF;
+          q = fnode[(it - nout) % NFF];
+        } else {
+          j = h2 + 1 + (it - nout - nlo) / NFF;
+          q = fnode[(it - nout - nlo) % NFF];
+        }
+        const int c = j - jlo, r = t - j;
+        const T* rc = rbuf + c * RS;
+        T acc;
+        if constexpr (__is_same(T, double)) {
+          // two chains: the FP64 pipe (2 DFMA per SM and clock) hides their latency
+          double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-            for (int m = 0; m < NN; ++m) a[m & 3] = fma(BinvT[m * NN + qq], rc[m], a[m & 3]);
-            acc = (a[0] + a[1]) + (a[2] + a[3]);
-          } else {
-            // compensated dot product (see dot_acc): exact high products and sums, the
-            // rounding errors and cross terms gathered in one FP32 accumulator
-            float S = 0.0f, L = 0.0f;
+          for (int m = 0; m + 1 < NN; m += 2) {
+            a0 = fma(BinvT[m * NN + q], rc[m], a0);
+            a1 = fma(BinvT[(m + 1) * NN + q], rc[m + 1], a1);
+          }
+          if (NN % 2) a0 = fma(BinvT[(NN - 1) * NN + q], rc[NN - 1], a0);
+          acc = a0 + a1;
+        } else {
+          // compensated dot product (see dot_acc): exact high products and sums, the
+          // rounding errors and cross terms gathered in one FP32 accumulator
+          float S = 0.0f, L = 0.0f;
 #pragma unroll 8
-            for (int m = 0; m < NN; ++m) {
-              const T a = BinvT[m * NN + qq], bv = rc[m];
-              const dd pr = dd_two_prod(a.hi, bv.hi);
-              const float cross = __fmaf_rn(a.hi, bv.lo, __fmul_rn(a.lo, bv.hi));
-              const dd sm2 = dd_two_sum(S, pr.hi);
-              S = sm2.hi;
-              L = __fadd_rn(L, __fadd_rn(sm2.lo, __fadd_rn(pr.lo, cross)));
-            }
-            acc = dd_fast_two_sum(S, L);
+          for (int m = 0; m < NN; ++m) {
+            const T a = BinvT[m * NN + q], bv = rc[m];
+            const dd pr = dd_two_prod(a.hi, bv.hi);
+            const float cross = __fmaf_rn(a.hi, bv.lo, __fmul_rn(a.lo, bv.hi));
+            const dd sm2 = dd_two_sum(S, pr.hi);
+            S = sm2.hi;
+            L = __fadd_rn(L, __fadd_rn(sm2.lo, __fadd_rn(pr.lo, cross)));
           }
-          const T fo = fc[c * RS + qq];
-          const T outv = acc - c1 * fo;
-          if (out_layer && j >= g.wx && r >= g.wy) st(g.fout + corner_off(g, j, r, k, qz, qy, qx), outv);
-          if (qx == NP - 1 || qy == NP - 1 || qz == NP - 1) {
-            const T face = fma(th, outv, omth * fo);
-            if (qx == NP - 1) Lt[((size_t)par * LtS + j + 1) * NF + qz * NP + qy] = face;
-            if (qy == NP - 1) Bt[((size_t)par * BtS + j) * NF + qz * NP + qx] = face;
-            if (qz == NP - 1) Zt[((size_t)r * CM + j) * NF + qy * NP + qx] = face;
-          }
+          acc = dd_fast_two_sum(S, L);
+        }
+        const int qz = q / NF, qy = (q / NP) % NP, qx = q % NP;
+        if (it < nout) st(g.fout + corner_off(g, j, r, k, qz, qy, qx), acc - c1 * fc[c * RS + q]);
+        if (qx == NP - 1 || qy == NP - 1 || qz == NP - 1) {
+          // theta fn + (1 - theta) f = theta (Binv r) - (1 - theta) f + (1 - theta) f
+          const T face = th * acc;
+          if (qx == NP - 1) Lt[((size_t)par * LtS + j + 1) * NF + qz * NP + qy] = face;
+          if (qy == NP - 1) Bt[((size_t)par * BtS + j) * NF + qz * NP + qx] = face;
+          if (qz == NP - 1) st(g.zt + ((long long)r * g.ncol + j) * NF + qy * NP + qx, face);
         }
       }
       cp_async_wait_all();

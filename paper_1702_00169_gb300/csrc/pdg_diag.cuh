@@ -21,7 +21,8 @@
 // builds r_c for every cell of it in shared memory, (B) the block forms the output
 // nodes as dot products with r_c (Binv sits in shared memory transposed, so the threads
 // of a cell read consecutive words).  The cells of the upwind start only pass faces on,
-// so (B) computes just their 2n-1 face nodes.  The state of the next anti-diagonal is
+// so (B) computes just their 2n-1 face nodes.  The face value passed on is
+// theta fn + (1 - theta) f = theta (Binv r_c): one product per face node.  The state of the next anti-diagonal is
 // copied into shared memory with cp.async while (B) runs (double-buffered by parity).
 #pragma once
 #include <cuda_runtime.h>
@@ -182,7 +183,7 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
 #pragma unroll
   for (int i = 0; i < NN; ++i) creg[i] = BinvT[i * NN + qq];
   const T rth = PDG_DC(T, C, rtheta), c1 = PDG_DC(T, C, c1);
-  const T th = PDG_DC(T, C, theta), omth = PDG_DC(T, C, omtheta);
+  const T th = PDG_DC(T, C, theta);
   const T kx = PDG_DC(T, C, kx), ky = PDG_DC(T, C, ky);
 
   diag_stage<NP, T>(g, 0, fbuf, lbnd, bbnd);
@@ -212,11 +213,10 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
     const int h2 = max(h1 - 1, min(jhi, t - g.wy));
     auto finish = [&](int j, int q, T acc) {
       const int c = j - jlo, r = t - j, iy = q / NP, ix = q % NP;
-      const T fo = fc[c * RS + q];
-      const T out = acc - c1 * fo;
-      if (j >= g.wx && r >= g.wy) st(g.fout + diag_off<NP>(g, j, r, iy, ix), out);
+      if (j >= g.wx && r >= g.wy) st(g.fout + diag_off<NP>(g, j, r, iy, ix), acc - c1 * fc[c * RS + q]);
       if (ix == NP - 1 || iy == NP - 1) {
-        const T face = fma(th, out, omth * fo);
+        // theta fn + (1 - theta) f = theta (Binv r) - (1 - theta) f + (1 - theta) f
+        const T face = th * acc;
         if (ix == NP - 1) Lt[((size_t)par * LtS + j + 1) * NP + iy] = face;
         if (iy == NP - 1) Bt[((size_t)par * BtS + j) * NP + ix] = face;
       }
@@ -226,10 +226,15 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
         const T* rc = rbuf + (j - jlo) * RS;
         T acc;
         if constexpr (__is_same(T, double)) {
-          double a[4] = {0.0, 0.0, 0.0, 0.0};
+          // two chains: the FP64 pipe (2 DFMA per SM and clock) hides their latency
+          double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-          for (int k = 0; k < NN; ++k) a[k & 3] = fma(creg[k], rc[k], a[k & 3]);
-          acc = (a[0] + a[1]) + (a[2] + a[3]);
+          for (int k = 0; k + 1 < NN; k += 2) {
+            a0 = fma(creg[k], rc[k], a0);
+            a1 = fma(creg[k + 1], rc[k + 1], a1);
+          }
+          if (NN % 2) a0 = fma(creg[NN - 1], rc[NN - 1], a0);
+          acc = a0 + a1;
         } else {
           T bb[NN];
 #pragma unroll

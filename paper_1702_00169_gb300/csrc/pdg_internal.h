@@ -235,6 +235,7 @@ struct PdgCornerPass {
   int threads, prec;
   const double* binv;              // device: NN x NN row-major (FP64)
   const float* binv_f;             // device: NN x NN (hi, lo) pairs (double-float)
+  double* zt;                      // device scratch: per block [ty + wy][tx + wx][n^2] +z faces
   PdgCornerCoef c;
 };
 
@@ -301,6 +302,8 @@ int pdg_plan_corner(int d, double nux, double nuy, double nuz, double theta, Pdg
 // ---- kernels (pdg_corner.cu) ----
 int pdg_launch_corner(const PdgCornerPass& p, void* stream);
 size_t pdg_corner_smem(const PdgCornerPass& p);
+// 8-byte words of the +z face scratch (PdgCornerPass::zt) of a launch
+size_t pdg_corner_scratch(const PdgCornerPass& p);
 
 // ---- kernels (pdg_diag.cu) ----
 int pdg_launch_diag(const PdgDiagPass& p, void* stream);

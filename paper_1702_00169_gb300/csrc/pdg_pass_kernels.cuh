@@ -1,5 +1,6 @@
-// Pass kernel and its launcher, instantiated once per number type (FP64 in
-// pdg_kernels.cu, double-float in pdg_kernels_df.cu) so the two compile in parallel.
+// Pass kernel and its launcher.  The kernels are instantiated in pdg_pass_inst.cu (one
+// object per group of model variants and number type); pdg_kernels.cu and
+// pdg_kernels_df.cu hold the dispatch by number type.
 //
 // pass_kernel<NP, MV, T> runs one "pass" over whole periodic lines of one axis:
 // a short list of operations chosen from
@@ -47,30 +48,49 @@ int launch_pass_t(const PdgPass& p, cudaStream_t st) {
   return (int)cudaGetLastError();
 }
 
-template <int NP, class T>
-int launch_pass_np(const PdgPass& p, cudaStream_t st) {
-  switch (p.mv) {
-    case MV_NONE: return launch_pass_t<NP, MV_NONE, T>(p, st);
-    case MV_ADV: return launch_pass_t<NP, MV_ADV, T>(p, st);
-    case MV_SW: return launch_pass_t<NP, MV_SW, T>(p, st);
-    case MV_EU1: return launch_pass_t<NP, MV_EU1, T>(p, st);
-    case MV_EU2: return launch_pass_t<NP, MV_EU2, T>(p, st);
-    case MV_EU3: return launch_pass_t<NP, MV_EU3, T>(p, st);
-    case MV_D2Q9: return launch_pass_t<NP, MV_D2Q9, T>(p, st);
-    case MV_D3Q19: return launch_pass_t<NP, MV_D3Q19, T>(p, st);
-    case MV_D3Q15: return launch_pass_t<NP, MV_D3Q15, T>(p, st);
-    case MV_D3Q27: return launch_pass_t<NP, MV_D3Q27, T>(p, st);
+// All degrees of one model variant.  Explicitly instantiated per (variant, number type) in
+// pdg_pass_inst.cu, which is compiled once per group of variants (build.py), so the
+// instantiations compile in parallel; every other translation unit sees the extern
+// declarations below.
+template <int MV, class T>
+int launch_pass_mv(const PdgPass& p, cudaStream_t st) {
+  switch (p.ncell > 0 ? p.npl / p.ncell : 0) {
+    case 2: return launch_pass_t<2, MV, T>(p, st);
+    case 3: return launch_pass_t<3, MV, T>(p, st);
+    case 4: return launch_pass_t<4, MV, T>(p, st);
+    case 5: return launch_pass_t<5, MV, T>(p, st);
   }
   return (int)cudaErrorInvalidValue;
 }
 
+#define PDG_PASS_EXTERN(MV)                                                       \
+  extern template int launch_pass_mv<MV, double>(const PdgPass&, cudaStream_t); \
+  extern template int launch_pass_mv<MV, dd>(const PdgPass&, cudaStream_t);
+PDG_PASS_EXTERN(MV_NONE)
+PDG_PASS_EXTERN(MV_ADV)
+PDG_PASS_EXTERN(MV_SW)
+PDG_PASS_EXTERN(MV_EU1)
+PDG_PASS_EXTERN(MV_EU2)
+PDG_PASS_EXTERN(MV_EU3)
+PDG_PASS_EXTERN(MV_D2Q9)
+PDG_PASS_EXTERN(MV_D3Q19)
+PDG_PASS_EXTERN(MV_D3Q15)
+PDG_PASS_EXTERN(MV_D3Q27)
+#undef PDG_PASS_EXTERN
+
 template <class T>
 int launch_pass_typed(const PdgPass& p, cudaStream_t st) {
-  switch (p.ncell > 0 ? p.npl / p.ncell : 0) {
-    case 2: return launch_pass_np<2, T>(p, st);
-    case 3: return launch_pass_np<3, T>(p, st);
-    case 4: return launch_pass_np<4, T>(p, st);
-    case 5: return launch_pass_np<5, T>(p, st);
+  switch (p.mv) {
+    case MV_NONE: return launch_pass_mv<MV_NONE, T>(p, st);
+    case MV_ADV: return launch_pass_mv<MV_ADV, T>(p, st);
+    case MV_SW: return launch_pass_mv<MV_SW, T>(p, st);
+    case MV_EU1: return launch_pass_mv<MV_EU1, T>(p, st);
+    case MV_EU2: return launch_pass_mv<MV_EU2, T>(p, st);
+    case MV_EU3: return launch_pass_mv<MV_EU3, T>(p, st);
+    case MV_D2Q9: return launch_pass_mv<MV_D2Q9, T>(p, st);
+    case MV_D3Q19: return launch_pass_mv<MV_D3Q19, T>(p, st);
+    case MV_D3Q15: return launch_pass_mv<MV_D3Q15, T>(p, st);
+    case MV_D3Q27: return launch_pass_mv<MV_D3Q27, T>(p, st);
   }
   return (int)cudaErrorInvalidValue;
 }
