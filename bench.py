@@ -133,6 +133,9 @@ def parse_args():
     ap.add_argument("--scheme", default="M2", choices=["M2", "M2_collapsed", "M2_kin"])
     ap.add_argument("--inflow-x", action="store_true",
                     help="x axis with inflow boundaries (f^b = f^eq of the initial state at the faces)")
+    ap.add_argument("--n-macro", type=int, default=None,
+                    help="macrocells per axis instead of the workload's (a smaller case of the same "
+                         "workload, e.g. for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=20)
@@ -265,12 +268,12 @@ print(json.dumps({{"value": cfg.dofs * {sample_steps} / el, "dofs": cfg.dofs, "s
                        f"on {d['mesh']} ({d['dofs']} DOF), {d['seconds']:.1f} s, 1 thread")}
 
 
-def run_reference(args, cfg):
+def run_reference(args, cfg, base_name):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     # each reference step = one M2 step of the oracle on a bounded sample of the workload
-    res = cpu_baseline(cfg.name, max(1, args.steps), max(1, args.warmup))
+    res = cpu_baseline(base_name, max(1, args.steps), max(1, args.warmup))
     value = res["value"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
@@ -480,6 +483,10 @@ def main():
     from paper_1702_00169_gb300 import workloads as W
     cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6, "d2q9": W.D2Q9_ISO,
            "d3q19": W.D3Q19_ISO, "d3q15": W.D3Q15_ISO, "d3q27": W.D3Q27_ISO}.get(args.workload, W.SW_D2Q4)
+    base_name = cfg.name   # the oracle's sample is drawn from the named workload
+    if args.n_macro:
+        cfg = cfg.scaled(n_macro=(args.n_macro,) * cfg.dim,
+                         name=f"{cfg.name}_n{args.n_macro}" if args.n_macro != cfg.n_macro[0] else cfg.name)
     if args.inflow_x and cfg.kind in ("isothermal_d3q19", "isothermal_d3q15", "isothermal_d3q27"):
         raise SystemExit("--inflow-x: the D3Qq paths run on periodic meshes")
     if args.source != "none" and cfg.kind != "isothermal_d2q9":
@@ -489,7 +496,7 @@ def main():
             args.steps = 20
         if args.warmup is None:
             args.warmup = 3
-        run_reference(args, cfg)
+        run_reference(args, cfg, base_name)
         return
     if args.workload == "batched":
         bench_batched(args)
@@ -696,7 +703,7 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = cpu_baseline(cfg.name, args.cpu_sample_steps)
+        cpu = cpu_baseline(base_name, args.cpu_sample_steps)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
