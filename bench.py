@@ -102,11 +102,11 @@ def collision_flops(kind, dim):
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
-# summarised under profiles/ (workload, kernel kind, precision) -> bytes.  Only kernels
-# that have not changed since their capture are listed; the others report null.
-TRAFFIC = {("shallow_water_d2q4_64x64x8x8_d3", 1, "fp64"): 1551.61e6,   # autotuned shapes 8,4,6
-           ("isothermal_d2q9_64x64x8x8_d3", 3, "fp64"): 287.23e6,
-           ("isothermal_d2q9_64x64x8x8_d3", 3, "df32"): 286.81e6}
+# summarised under profiles/: (workload, kernel kind, precision, launch shape) -> bytes.
+# The launch shape is (lines per block, segments, field groups) of that pass kind, or None
+# for the diagonal / corner passes (shape chosen by the host planner).  Only kernels that
+# have not changed since their capture are listed; the others report null.
+TRAFFIC = {("shallow_water_d2q4_64x64x8x8_d3", 1, "fp64", (8, 4, 6)): 1551.61e6}
 
 SOURCES = {"gravity": dict(gravity=(0.0, -1.0)),
            "penalization": dict(K_s=300.0, kappa=40.0, x_c=(0.25, 0.5), w_s=(1.0, 0.0, 0.0)),
@@ -616,6 +616,7 @@ def main():
     # ---- device-resident run (FP64) ----
     ms, launches, kms, clocks, w_end = timed_run(s)
     shape0, shape1 = s.get_launch(0), s.get_launch(1)
+    s_shape = {0: shape0, 1: shape1}
     finite = bool(np.all(np.isfinite(w_end)))
 
     dofs = cfg.dofs
@@ -692,7 +693,9 @@ def main():
     achieved_gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
     roof = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
             "frac": achieved_tflops / fp64_peak_tflops,
-            "traffic": TRAFFIC.get((cfg.name, k_dom, args.precision)) if args.source == "none" else None,
+            "traffic": (TRAFFIC.get((cfg.name, k_dom, args.precision,
+                                     tuple(s_shape[k_dom]) if k_dom in (0, 1) else None))
+                        if args.source == "none" else None),
             "kernel": kinds[k_dom], "avg_launch_ms": avg_ms, "launches": launches[k_dom],
             "algorithmic_flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
             "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": achieved_gbs / hbm_peak,

@@ -432,42 +432,10 @@ __device__ __forceinline__ void d3q19_moments(const T* v, T* rho, T* jx, T* jy, 
   *jz = (v[5] - v[6]) + ((v[11] + v[12]) - (v[13] + v[14])) + ((v[15] + v[16]) - (v[17] + v[18]));
 }
 
-template <class T>
-struct Collide<MV_D3Q19, T> {
-  static __device__ __forceinline__ void run(T* v, const PdgModel& M) {
-    T rho, jx, jy, jz;
-    d3q19_moments<T>(v, &rho, &jx, &jy, &jz);
-    T e[19];
-    d3q19_e<T>(rho, jx, jy, jz, M, e);
-    const T a0 = PDG_K(T, M, PDG_K_Q9W0) * rho, a1 = PDG_K(T, M, PDG_K_Q9W1) * rho;
-    const T a2 = PDG_K(T, M, PDG_K_Q9W2) * rho;
-    const T om1 = PDG_K(T, M, PDG_K_OM1);
-    if constexpr (!__is_same(T, double)) {
-      v[0] = relax(om1, v[0], a0 * e[0]);
-#pragma unroll
-      for (int i = 1; i < 7; ++i) v[i] = relax(om1, v[i], a1 * e[i]);
-#pragma unroll
-      for (int i = 7; i < 19; ++i) v[i] = relax(om1, v[i], a2 * e[i]);
-    } else if (M.omega == 2.0) {
-      v[0] = fma(a0, e[0], -v[0]);
-#pragma unroll
-      for (int i = 1; i < 7; ++i) v[i] = fma(a1, e[i], -v[i]);
-#pragma unroll
-      for (int i = 7; i < 19; ++i) v[i] = fma(a2, e[i], -v[i]);
-    } else {
-      v[0] = fma(om1, v[0], a0 * e[0]);
-#pragma unroll
-      for (int i = 1; i < 7; ++i) v[i] = fma(om1, v[i], a1 * e[i]);
-#pragma unroll
-      for (int i = 7; i < 19; ++i) v[i] = fma(om1, v[i], a2 * e[i]);
-    }
-  }
-};
-
 // Corner velocities (D3Q15 / D3Q27) in the order (s_x, s_y, s_z) = (+,+,+), (-,+,+), (-,-,+),
-// (+,-,+), (+,+,-), (-,+,-), (-,-,-), (+,-,-): sums of the eight populations c[0..7]
-// (mass and the three first moments) and their equilibrium factors e_i (s.xi_i = +-t_1..t_4,
-// t_1 = s_x + s_y + s_z, t_2 = s_y + s_z - s_x, t_3 = s_z - s_x - s_y, t_4 = s_x + s_z - s_y).
+// (+,-,+), (+,+,-), (-,+,-), (-,-,-), (+,-,-): sums of the eight populations c[0..7] (mass
+// and the three first moments).  Their s.xi_i are +-t_1..t_4 (pairs (0,6), (1,7), (2,4),
+// (3,5)), t_1 = s_x + s_y + s_z, t_2 = s_y + s_z - s_x, t_3 = s_z - s_x - s_y, t_4 = s_x + s_z - s_y.
 template <class T>
 __device__ __forceinline__ void corner_moments(const T* c, T* rho, T* jx, T* jy, T* jz) {
   *rho = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
@@ -476,36 +444,26 @@ __device__ __forceinline__ void corner_moments(const T* c, T* rho, T* jx, T* jy,
   *jz = ((c[0] + c[1]) + (c[2] + c[3])) - ((c[4] + c[5]) + (c[6] + c[7]));
 }
 
-template <class T>
-__device__ __forceinline__ void corner_e(T sx, T sy, T sz, T base, T half, T* e) {
-  const T t1 = (sx + sy) + sz, t2 = (sy + sz) - sx, t3 = sz - (sx + sy), t4 = (sx + sz) - sy;
-  const T q1 = fma(half * t1, t1, base), q2 = fma(half * t2, t2, base);
-  const T q3 = fma(half * t3, t3, base), q4 = fma(half * t4, t4, base);
-  e[0] = q1 + t1;
-  e[1] = q2 + t2;
-  e[2] = q3 + t3;
-  e[3] = q4 + t4;
-  e[4] = q3 - t3;
-  e[5] = q4 - t4;
-  e[6] = q1 - t1;
-  e[7] = q2 - t2;
-}
-
-// D3Q15 / D3Q27 relaxation: populations 0 (rest), 1-6 (axis), then (D3Q27) 7-18 (edges as in
-// D3Q19), then the eight corners; f^eq_i = W_i rho e_i with s = 3 j / rho.
-template <class T, bool EDGES>
-__device__ __forceinline__ void d3q_corner_lattice_collide(T* v, const PdgModel& M) {
-  constexpr int C0 = EDGES ? 19 : 7;
-  T rho, jx, jy, jz;
+// 3-D lattice collision (D3Q19: EDGES; D3Q15: CORNERS; D3Q27: both).  Populations 0 (rest),
+// 1-6 (axis), then the twelve edges (order of PDG_Q19_*), then the eight corners;
+// f^eq_i = W_i rho e_i with s = 3 j / rho (see d3q19_e and corner_moments).  Each equilibrium
+// factor is formed right where its population is relaxed, so that only the populations
+// and a few scalars stay live (the pass kernels run at most 128 registers per thread).
+template <class T, bool EDGES, bool CORNERS>
+__device__ __forceinline__ void d3q_lattice_collide(T* v, const PdgModel& M) {
+  constexpr int E0 = 7, C0 = EDGES ? 19 : 7;
+  T rho = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + v[6]);
+  T jx = v[1] - v[2], jy = v[3] - v[4], jz = v[5] - v[6];
   if constexpr (EDGES) {
-    d3q19_moments<T>(v, &rho, &jx, &jy, &jz);
-  } else {
-    rho = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + v[6]);
-    jx = v[1] - v[2];
-    jy = v[3] - v[4];
-    jz = v[5] - v[6];
+    rho = rho + ((((v[E0] + v[E0 + 1]) + (v[E0 + 2] + v[E0 + 3])) + ((v[E0 + 4] + v[E0 + 5]) + (v[E0 + 6] + v[E0 + 7]))) +
+                 ((v[E0 + 8] + v[E0 + 9]) + (v[E0 + 10] + v[E0 + 11])));
+    // x: xy edges 0 - 1 - 2 + 3, xz edges 4 - 5 - 6 + 7; y: xy 0 + 1 - 2 - 3, yz 8 - 9 - 10 + 11;
+    // z: xz 4 + 5 - 6 - 7, yz 8 + 9 - 10 - 11 (edge indices relative to population 7)
+    jx = jx + (((v[E0] - v[E0 + 1]) + (v[E0 + 3] - v[E0 + 2])) + ((v[E0 + 4] - v[E0 + 5]) + (v[E0 + 7] - v[E0 + 6])));
+    jy = jy + (((v[E0] + v[E0 + 1]) - (v[E0 + 2] + v[E0 + 3])) + ((v[E0 + 8] - v[E0 + 9]) + (v[E0 + 11] - v[E0 + 10])));
+    jz = jz + (((v[E0 + 4] + v[E0 + 5]) - (v[E0 + 6] + v[E0 + 7])) + ((v[E0 + 8] + v[E0 + 9]) - (v[E0 + 10] + v[E0 + 11])));
   }
-  {
+  if constexpr (CORNERS) {
     T cr, cx, cy, cz;
     corner_moments<T>(v + C0, &cr, &cx, &cy, &cz);
     rho = rho + cr;
@@ -513,58 +471,65 @@ __device__ __forceinline__ void d3q_corner_lattice_collide(T* v, const PdgModel&
     jy = jy + cy;
     jz = jz + cz;
   }
-  T e[19], ec[8];
-  d3q19_e<T>(rho, jx, jy, jz, M, e);   // e[0], the axis and (D3Q27) the edge factors
-  {
-    const T three = from_double<T>(3.0);
-    const T ir = recip(rho);
-    const T half = PDG_K(T, M, PDG_K_HALF);
-    corner_e<T>(three * (jx * ir), three * (jy * ir), three * (jz * ir), e[0], half, ec);
-  }
-  const T a0 = PDG_K(T, M, PDG_K_Q9W0) * rho, a1 = PDG_K(T, M, PDG_K_Q9W1) * rho;
-  const T a2 = PDG_K(T, M, PDG_K_Q9W2) * rho, a3 = PDG_K(T, M, PDG_K_Q9W3) * rho;
+  const T three = from_double<T>(3.0);
+  const T ir = recip(rho);
+  const T sx = three * (jx * ir), sy = three * (jy * ir), sz = three * (jz * ir);
+  const T half = PDG_K(T, M, PDG_K_HALF);
+  const T base = from_double<T>(1.0) - PDG_K(T, M, PDG_K_SIXTH) * fma(sx, sx, fma(sy, sy, sz * sz));
   const T om1 = PDG_K(T, M, PDG_K_OM1);
-  if constexpr (!__is_same(T, double)) {
-    v[0] = relax(om1, v[0], a0 * e[0]);
-#pragma unroll
-    for (int i = 1; i < 7; ++i) v[i] = relax(om1, v[i], a1 * e[i]);
-    if constexpr (EDGES) {
-#pragma unroll
-      for (int i = 7; i < 19; ++i) v[i] = relax(om1, v[i], a2 * e[i]);
+  const bool two = M.omega == 2.0;
+  // v_i <- omega W_i rho e_i + (1 - omega) v_i  (a = omega W_i rho)
+  auto upd = [&](int i, T a, T e) {
+    if constexpr (!__is_same(T, double)) {
+      v[i] = relax(om1, v[i], a * e);
+    } else {
+      v[i] = two ? fma(a, e, -v[i]) : fma(om1, v[i], a * e);
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[C0 + i] = relax(om1, v[C0 + i], a3 * ec[i]);
-  } else if (M.omega == 2.0) {
-    v[0] = fma(a0, e[0], -v[0]);
-#pragma unroll
-    for (int i = 1; i < 7; ++i) v[i] = fma(a1, e[i], -v[i]);
-    if constexpr (EDGES) {
-#pragma unroll
-      for (int i = 7; i < 19; ++i) v[i] = fma(a2, e[i], -v[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[C0 + i] = fma(a3, ec[i], -v[C0 + i]);
-  } else {
-    v[0] = fma(om1, v[0], a0 * e[0]);
-#pragma unroll
-    for (int i = 1; i < 7; ++i) v[i] = fma(om1, v[i], a1 * e[i]);
-    if constexpr (EDGES) {
-#pragma unroll
-      for (int i = 7; i < 19; ++i) v[i] = fma(om1, v[i], a2 * e[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[C0 + i] = fma(om1, v[C0 + i], a3 * ec[i]);
+  };
+  // one velocity pair +-t: e = q +- t, q = base + t^2 / 2
+  auto pair = [&](int ip, int im, T a, T t) {
+    const T q = fma(half * t, t, base);
+    upd(ip, a, q + t);
+    upd(im, a, q - t);
+  };
+  upd(0, PDG_K(T, M, PDG_K_Q9W0) * rho, base);
+  {
+    const T a1 = PDG_K(T, M, PDG_K_Q9W1) * rho;
+    pair(1, 2, a1, sx);
+    pair(3, 4, a1, sy);
+    pair(5, 6, a1, sz);
+  }
+  if constexpr (EDGES) {   // plane (a, b): (+,+) / (-,-) carry s_a + s_b, (-,+) / (+,-) carry s_b - s_a
+    const T a2 = PDG_K(T, M, PDG_K_Q9W2) * rho;
+    pair(E0 + 0, E0 + 2, a2, sx + sy);
+    pair(E0 + 1, E0 + 3, a2, sy - sx);
+    pair(E0 + 4, E0 + 6, a2, sx + sz);
+    pair(E0 + 5, E0 + 7, a2, sz - sx);
+    pair(E0 + 8, E0 + 10, a2, sy + sz);
+    pair(E0 + 9, E0 + 11, a2, sz - sy);
+  }
+  if constexpr (CORNERS) {   // the corner order of corner_moments
+    const T a3 = PDG_K(T, M, PDG_K_Q9W3) * rho;
+    pair(C0 + 0, C0 + 6, a3, (sx + sy) + sz);
+    pair(C0 + 1, C0 + 7, a3, (sy + sz) - sx);
+    pair(C0 + 2, C0 + 4, a3, sz - (sx + sy));
+    pair(C0 + 3, C0 + 5, a3, (sx + sz) - sy);
   }
 }
 
 template <class T>
+struct Collide<MV_D3Q19, T> {
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) { d3q_lattice_collide<T, true, false>(v, M); }
+};
+
+template <class T>
 struct Collide<MV_D3Q15, T> {
-  static __device__ __forceinline__ void run(T* v, const PdgModel& M) { d3q_corner_lattice_collide<T, false>(v, M); }
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) { d3q_lattice_collide<T, false, true>(v, M); }
 };
 
 template <class T>
 struct Collide<MV_D3Q27, T> {
-  static __device__ __forceinline__ void run(T* v, const PdgModel& M) { d3q_corner_lattice_collide<T, true>(v, M); }
+  static __device__ __forceinline__ void run(T* v, const PdgModel& M) { d3q_lattice_collide<T, true, true>(v, M); }
 };
 
 template <class T>

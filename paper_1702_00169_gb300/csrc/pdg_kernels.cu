@@ -141,7 +141,7 @@ __global__ void set_feq_corner_kernel(double* __restrict__ f, long long P, const
       v[1 + 2 * a] = ja;
       v[2 + 2 * a] = -ja;
     }
-    d3q_corner_lattice_collide<T, EDGES>(v, M1);
+    d3q_lattice_collide<T, EDGES, true>(v, M1);
 #pragma unroll
     for (int i = 0; i < NV; ++i) st(f + (long long)i * P + pt, v[i]);
   }

@@ -34,18 +34,32 @@ __global__ void __launch_bounds__(512) pass_kernel(const __grid_constant__ PdgPa
   pass_body<NP, MV, T>(p, blockIdx.x, sm);
 }
 
+// The 3-D lattices (15 to 27 populations live in the collision): the same body, compiled
+// for one block of 512 threads per SM, so that ptxas may use all 128 registers a thread
+// can have there instead of spilling.
+template <int NP, int MV, class T>
+__global__ void __launch_bounds__(512, 1) pass_kernel_lat(const __grid_constant__ PdgPass p) {
+  extern __shared__ double sm[];
+  pass_body<NP, MV, T>(p, blockIdx.x, sm);
+}
+
 template <int NP, int MV, class T>
 int launch_pass_t(const PdgPass& p, cudaStream_t st) {
   const int threads = p.lpb * p.nseg * p.ngroup;
   const size_t smem = sizeof(double) * 3 * (size_t)p.ntf * p.nseg * p.lpb;
-  auto kern = pass_kernel<NP, MV, T>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-  }
   const int blocks = p.nblocks > 0 ? p.nblocks : (p.nlines + p.lpb - 1) / p.lpb;
-  kern<<<blocks, threads, smem, st>>>(p);
-  return (int)cudaGetLastError();
+  auto go = [&](auto kern) -> int {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return (int)e;
+    }
+    kern<<<blocks, threads, smem, st>>>(p);
+    return (int)cudaGetLastError();
+  };
+  if constexpr (MV == MV_D3Q19 || MV == MV_D3Q15 || MV == MV_D3Q27)
+    return go(pass_kernel_lat<NP, MV, T>);
+  else
+    return go(pass_kernel<NP, MV, T>);
 }
 
 // All degrees of one model variant.  Explicitly instantiated per (variant, number type) in
