@@ -106,7 +106,8 @@ def collision_flops(kind, dim):
 # The launch shape is (lines per block, segments, field groups) of that pass kind, or None
 # for the diagonal / corner passes (shape chosen by the host planner).  Only kernels that
 # have not changed since their capture are listed; the others report null.
-TRAFFIC = {("shallow_water_d2q4_64x64x8x8_d3", 1, "fp64", (8, 4, 6)): 1551.61e6}
+TRAFFIC = {("shallow_water_d2q4_64x64x8x8_d3", 1, "fp64", (8, 4, 6)): 1551.61e6,
+           ("isothermal_d2q9_64x64x8x8_d3", 3, "fp64", None): 279.41e6}
 
 SOURCES = {"gravity": dict(gravity=(0.0, -1.0)),
            "penalization": dict(K_s=300.0, kappa=40.0, x_c=(0.25, 0.5), w_s=(1.0, 0.0, 0.0)),
