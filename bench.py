@@ -735,7 +735,12 @@ def main():
                        "launch_shapes": {"autotuned": not args.no_autotune and not args.shapes,
                                          "transport_pass": list(shape0),
                                          "last_axis_pass": list(shape1)}},
-            "gpu_launches": int(sum(launches)), "roofline": roof, "clocks": clocks,
+            "gpu_launches": int(sum(launches)),
+            "kernels": {name: {"launches": int(launches[k]), "avg_ms": kms[k] / launches[k],
+                               "share": kms[k] / max(1e-12, sum(kms))}
+                        for k, name in ((0, "transport pass"), (1, "last-axis pass"), (2, "state kernels"),
+                                        (3, "diagonal pass"), (4, "corner pass")) if launches[k]},
+            "roofline": roof, "clocks": clocks,
             "e2e": e2e, "cpu_baseline": cpu, "mixed": mixed, "state_finite": finite}
     print(json.dumps(line), flush=True)
     if ws > 1:
