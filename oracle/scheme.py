@@ -13,6 +13,14 @@ Section 3.2:
       each C_2(dt/2).
   With a source (oracle.source): M_2^s(dt) = T_2(dt/2) S_2(dt/2) C_2(dt) S_2(dt/2) T_2(dt/2)
       (Section 3.2), also in the collapsed form of Section 5.1.
+  M_4^kin(dt) = M_2^kin(g1 dt) M_2^kin(g2 dt) M_2^kin(g1 dt): Section 3.2 states that
+      palindromic compositions of M_2^kin reach any even order without giving one; this is
+      the symmetric triple jump (H. Yoshida, Phys. Lett. A 150 (1990) 262), whose
+      coefficients solve 2 g1 + g2 = 1 and 2 g1^3 + g2^3 = 0:
+      g1 = 1 / (2 - 2^(1/3)), g2 = 1 - 2 g1 (negative).  It is fourth order when the
+      composed step is time-symmetric (eq. (3.13)), which M_2^kin is at omega = 2
+      (C_2 is then an involution); its negative sub-step runs the transport backwards,
+      which is stable only for moderate Courant numbers.
 
 The steps are applied in the naive order: every population is transported
 along its own velocity, then the collision acts on all populations, then every
@@ -100,8 +108,9 @@ def source_collision(f, transporter, model, dt, omega, source=None):
 
 
 def run(f0, transporter, model, dt, nsteps, omega, scheme="M2", source=None):
-    """nsteps palindromic steps from f0.  scheme: "M2", "M2_collapsed" (Section 5.1) or
-    "M2_kin" (Section 3.2); source: an oracle.source.Source (M2 and M2_collapsed)."""
+    """nsteps palindromic steps from f0.  scheme: "M2", "M2_collapsed" (Section 5.1),
+    "M2_kin" (Section 3.2) or "M4_kin" (the triple jump of M2_kin); source: an
+    oracle.source.Source (M2 and M2_collapsed)."""
     f = np.array(f0, dtype=np.float64, copy=True)
     if nsteps <= 0:
         return f
@@ -119,13 +128,30 @@ def run(f0, transporter, model, dt, nsteps, omega, scheme="M2", source=None):
         raise ValueError("sources are defined for M2 and M2_collapsed (Section 3.2, Section 5.1)")
     if scheme == "M2_kin":
         for _ in range(nsteps):
-            f = transporter(f, 0.25 * dt)
-            f = collision(f, model, omega)
-            f = transporter(f, 0.5 * dt)
-            f = collision(f, model, omega)
-            f = transporter(f, 0.25 * dt)
+            f = m2kin_step(f, transporter, model, dt, omega)
+        return f
+    if scheme == "M4_kin":
+        g1, g2 = triple_jump()
+        for _ in range(nsteps):
+            for g in (g1, g2, g1):
+                f = m2kin_step(f, transporter, model, g * dt, omega)
         return f
     raise ValueError(scheme)
+
+
+def m2kin_step(f, transporter, model, dt, omega):
+    """M_2^kin(dt) = T_2(dt/4) C_2(dt/2) T_2(dt/2) C_2(dt/2) T_2(dt/4) (Section 3.2)."""
+    f = transporter(f, 0.25 * dt)
+    f = collision(f, model, omega)
+    f = transporter(f, 0.5 * dt)
+    f = collision(f, model, omega)
+    return transporter(f, 0.25 * dt)
+
+
+def triple_jump():
+    """Coefficients (g1, g2) of the symmetric triple jump M(g1 dt) M(g2 dt) M(g1 dt)."""
+    g1 = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+    return g1, 1.0 - 2.0 * g1
 
 
 def initial_state(model, w0):

@@ -195,3 +195,45 @@ def test_m2kin_second_order(d):
     errs = [_advection_error(d, N, "M2_kin") for N in (8, 16, 32)]
     slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(slopes > 1.8) and slopes[-1] > 1.9, (errs, slopes)
+
+
+def test_triple_jump_coefficients():
+    """The order conditions of the symmetric triple jump: consistency 2 g1 + g2 = 1 and
+    cancellation of the third-order error term 2 g1^3 + g2^3 = 0 (g2 < 0)."""
+    g1, g2 = S.triple_jump()
+    assert abs(2 * g1 + g2 - 1.0) < 1e-15
+    assert abs(2 * g1 ** 3 + g2 ** 3) < 1e-14
+    assert g2 < 0 < g1
+
+
+def test_m4kin_time_symmetric_and_conservative():
+    """omega = 2: M4^kin(-dt) M4^kin(dt) = I (composition of time-symmetric steps), and
+    the weighted totals of w are kept."""
+    rng = np.random.default_rng(63)
+    model = M.Model(M.SHALLOW_WATER, 2, 8.0)
+    mesh = CartesianMesh(2, (3, 2), 2)
+    f = model.feq(_sw_state(mesh, rng)) + 1e-3 * rng.standard_normal((3, 4) + mesh.shape)
+    tr = S.Transporter(mesh, model, method="bloch")
+    dt = 0.2 * min(mesh.h) / model.lam
+    g = S.run(f, tr, model, dt, 1, 2.0, "M4_kin")
+    np.testing.assert_allclose(S.run(g, tr, model, -dt, 1, 2.0, "M4_kin"), f, atol=1e-12)
+    np.testing.assert_allclose(S.weighted_total(mesh, model.moments(g)), S.weighted_total(mesh, model.moments(f)),
+                               rtol=0, atol=1e-13)
+
+
+def test_m4kin_fourth_order_in_time():
+    """Fixed mesh, dt halved: successive differences of w shrink by about 2^4 for the
+    triple jump (2^2 for M2^kin itself), on the advection workload at omega = 2."""
+    import dataclasses
+    from paper_1702_00169_gb300 import workloads as W
+    cfg = dataclasses.replace(W.ADVECTION_D2Q4, n_macro=(4, 4), n_sub=(2, 2), order=3)
+    mesh = CartesianMesh(2, cfg.ncells, cfg.order)
+    model = M.Model(M.ADVECTION, 2, cfg.lam, a=cfg.a[:2])
+    w0 = W.initial_w(cfg, [mesh.coords1d(a) for a in range(2)])
+    tr = S.Transporter(mesh, model, 0.5, "bloch")
+    T = 0.05
+    for scheme, lo, hi in (("M2_kin", 3.7, 4.3), ("M4_kin", 13.0, 19.0)):
+        res = [model.moments(S.run(S.initial_state(model, w0), tr, model, T / N, N, 2.0, scheme))
+               for N in (8, 16, 32)]
+        e = [np.abs(res[0] - res[1]).max(), np.abs(res[1] - res[2]).max()]
+        assert lo < e[0] / e[1] < hi, (scheme, e)
