@@ -131,9 +131,12 @@ def parse_args():
     ap.add_argument("--source", default="none", choices=["none", "gravity", "penalization", "both"],
                     help="d2q9 workload: source stages S(dt/2) C S(dt/2) (gravity g = -1 e_y; "
                          "penalisation K_s = 300, kappa = 40 at (0.25, 0.5), w_s = (1, 0, 0))")
-    ap.add_argument("--scheme", default="M2", choices=["M2", "M2_collapsed", "M2_kin"])
+    ap.add_argument("--scheme", default="M2", choices=["M2", "M2_collapsed", "M2_kin", "M4_kin"])
     ap.add_argument("--inflow-x", action="store_true",
                     help="x axis with inflow boundaries (f^b = f^eq of the initial state at the faces)")
+    ap.add_argument("--cfl", type=float, default=None,
+                    help="Courant number of dt = cfl h / lambda instead of the workload's (M4_kin needs "
+                         "moderate values: its middle sub-step runs backwards)")
     ap.add_argument("--n-macro", type=int, default=None,
                     help="macrocells per axis instead of the workload's (a smaller case of the same "
                          "workload, e.g. for profiler captures)")
@@ -485,6 +488,9 @@ def main():
     cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6, "d2q9": W.D2Q9_ISO,
            "d3q19": W.D3Q19_ISO, "d3q15": W.D3Q15_ISO, "d3q27": W.D3Q27_ISO}.get(args.workload, W.SW_D2Q4)
     base_name = cfg.name   # the oracle's sample is drawn from the named workload
+    if args.cfl:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, cfl=args.cfl)
     if args.n_macro:
         cfg = cfg.scaled(n_macro=(args.n_macro,) * cfg.dim,
                          name=f"{cfg.name}_n{args.n_macro}" if args.n_macro != cfg.n_macro[0] else cfg.name)

@@ -102,9 +102,17 @@ enum {
 enum {
   PDG_SCHEME_M2 = 0,          /* T(dt/2) C(dt) T(dt/2) per step                   */
   PDG_SCHEME_M2_COLLAPSED = 1, /* consecutive half transports merged into T(dt)   */
-  PDG_SCHEME_M2KIN = 2         /* T(dt/4) C(dt/2) T(dt/2) C(dt/2) T(dt/4): second order
+  PDG_SCHEME_M2KIN = 2,        /* T(dt/4) C(dt/2) T(dt/2) C(dt/2) T(dt/4): second order
                                   also as tau -> 0 (Section 3.2); omega is the weight of
                                   each C(dt/2) */
+  PDG_SCHEME_M4KIN = 3         /* M2KIN(g1 dt) M2KIN(g2 dt) M2KIN(g1 dt), g1 = 1/(2 - 2^(1/3)),
+                                  g2 = 1 - 2 g1 < 0: the symmetric triple jump of M2^kin,
+                                  fourth order when M2^kin is time-symmetric (omega = 2);
+                                  Section 3.2 states that palindromic compositions of M2^kin
+                                  give any even order.  The middle sub-step runs backwards
+                                  (anti-dissipative): stable for moderate Courant numbers
+                                  only.  DnQ2n models on periodic axes (an inflow axis
+                                  refuses the backward step); no sources. */
 };
 
 /* State format and arithmetic. */
@@ -245,7 +253,8 @@ int pdg_set_source(pdg_ctx* ctx, const pdg_source_desc* desc);
  * (I - theta delta L_h) F^new = (I + (1-theta) delta L_h) F^old of eq. (3.11),
  * solved exactly on the periodic mesh, and C eq. (3.12).  With
  * PDG_SCHEME_M2_COLLAPSED the interior half transports are merged into T(dt)
- * (collapsed Strang of Section 5.1); PDG_SCHEME_M2KIN advances M2^kin steps.
+ * (collapsed Strang of Section 5.1); PDG_SCHEME_M2KIN advances M2^kin steps,
+ * PDG_SCHEME_M4KIN steps of its triple-jump composition.
  * Asynchronous on the context stream.
  * dt may be negative (time-symmetric use).  nsteps = 0 is a no-op.
  * D2Q9 diagonal velocities v = lambda (s_x, s_y): on a Cartesian cell eq. (3.7) splits

@@ -785,7 +785,7 @@ int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSp
 // just before the line pass that holds the next collision (transports of different
 // populations commute); each diagonal pass swaps the slot set of populations 5-8, the
 // collision reads them where they are, and a final copy returns them to slots 5-8.
-int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+int build_schedule_one(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
   if (int r = build_line_schedule(c, dt, nsteps, out)) return r;
   Lattice Lat;
   if (!lattice_of(c->model.kind, &Lat) || nsteps <= 0) return PDG_OK;
@@ -844,6 +844,30 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
   }
   out.swap(res);
   return PDG_OK;
+}
+
+// The pass list of nsteps steps of the context's scheme.  M4^kin (PDG_SCHEME_M4KIN) is the
+// triple jump M2^kin(g1 dt) M2^kin(g2 dt) M2^kin(g1 dt) per step (Section 3.2: palindromic
+// compositions of M2^kin; H. Yoshida, Phys. Lett. A 150 (1990)), g1 = 1/(2 - 2^(1/3)),
+// g2 = 1 - 2 g1 < 0: three M2^kin schedules per step, the middle one backwards in time.
+int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+  if (c->scheme != PDG_SCHEME_M4KIN) return build_schedule_one(c, dt, nsteps, out);
+  Lattice L;
+  if (lattice_of(c->model.kind, &L))
+    return fail(c, PDG_ERR_UNSUPPORTED, "M4^kin has a backward sub-step: not available for diagonal velocities");
+  if (c->src.flags) return fail(c, PDG_ERR_UNSUPPORTED, "sources are defined for M2 and M2_collapsed");
+  const double g1 = 1.0 / (2.0 - std::cbrt(2.0)), g2 = 1.0 - 2.0 * g1;
+  out.clear();
+  std::vector<PdgPassSpec> part;
+  c->scheme = PDG_SCHEME_M2KIN;
+  int r = PDG_OK;
+  for (int s = 0; s < nsteps && r == PDG_OK; ++s)
+    for (double g : {g1, g2, g1}) {
+      if ((r = build_schedule_one(c, g * dt, 1, part)) != PDG_OK) break;
+      out.insert(out.end(), part.begin(), part.end());
+    }
+  c->scheme = PDG_SCHEME_M4KIN;
+  return r;
 }
 
 // State slots of the current model (D2Q9: nine populations and four scratch slots).
@@ -996,7 +1020,8 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   if (!c || !d) return PDG_ERR_ARG;
   if (d->kind < PDG_MODEL_ADVECTION || d->kind > PDG_MODEL_ISOTHERMAL_D3Q27)
     return fail(c, PDG_ERR_ARG, "unknown model kind");
-  if (d->scheme != PDG_SCHEME_M2 && d->scheme != PDG_SCHEME_M2_COLLAPSED && d->scheme != PDG_SCHEME_M2KIN)
+  if (d->scheme != PDG_SCHEME_M2 && d->scheme != PDG_SCHEME_M2_COLLAPSED && d->scheme != PDG_SCHEME_M2KIN &&
+      d->scheme != PDG_SCHEME_M4KIN)
     return fail(c, PDG_ERR_ARG, "unknown scheme");
   if (d->precision != PDG_PREC_FP64 && d->precision != PDG_PREC_DF32)
     return fail(c, PDG_ERR_UNSUPPORTED, "precision not available");
@@ -1155,7 +1180,7 @@ int pdg_set_source(pdg_ctx* c, const pdg_source_desc* d) {
   }
   if (c->model.kind != PDG_MODEL_ISOTHERMAL_D2Q9)
     return fail(c, PDG_ERR_UNSUPPORTED, "sources are available for the D2Q9 model");
-  if (c->scheme == PDG_SCHEME_M2KIN)
+  if (c->scheme == PDG_SCHEME_M2KIN || c->scheme == PDG_SCHEME_M4KIN)
     return fail(c, PDG_ERR_UNSUPPORTED, "sources are defined for M2 and M2_collapsed");
   if (d->flags & ~(PDG_SOURCE_GRAVITY | PDG_SOURCE_PENALIZATION)) return fail(c, PDG_ERR_ARG, "unknown source flag");
   if (!(d->theta >= 0.0 && d->theta <= 1.0)) return fail(c, PDG_ERR_ARG, "source theta must be in [0, 1]");

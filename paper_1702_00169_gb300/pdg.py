@@ -19,7 +19,7 @@ PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA, PDG_ERR_STATE, PDG_ERR_TIMEOUT, PDG_ERR_
 PDG_MODEL_ADVECTION, PDG_MODEL_SHALLOW_WATER, PDG_MODEL_EULER = 0, 1, 2
 PDG_MODEL_ISOTHERMAL_D2Q9, PDG_MODEL_ISOTHERMAL_D3Q19 = 3, 4
 PDG_MODEL_ISOTHERMAL_D3Q15, PDG_MODEL_ISOTHERMAL_D3Q27 = 5, 6
-PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED, PDG_SCHEME_M2KIN = 0, 1, 2
+PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED, PDG_SCHEME_M2KIN, PDG_SCHEME_M4KIN = 0, 1, 2, 3
 PDG_PREC_FP64 = 0
 PDG_PREC_DF32 = 1
 PRECISION = {"fp64": PDG_PREC_FP64, "df32": PDG_PREC_DF32}
@@ -28,7 +28,8 @@ PDG_OPT_COMPOSE_TT = 1
 KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER,
         "isothermal_d2q9": PDG_MODEL_ISOTHERMAL_D2Q9, "isothermal_d3q19": PDG_MODEL_ISOTHERMAL_D3Q19,
         "isothermal_d3q15": PDG_MODEL_ISOTHERMAL_D3Q15, "isothermal_d3q27": PDG_MODEL_ISOTHERMAL_D3Q27}
-SCHEME = {"M2": PDG_SCHEME_M2, "M2_collapsed": PDG_SCHEME_M2_COLLAPSED, "M2_kin": PDG_SCHEME_M2KIN}
+SCHEME = {"M2": PDG_SCHEME_M2, "M2_collapsed": PDG_SCHEME_M2_COLLAPSED, "M2_kin": PDG_SCHEME_M2KIN,
+          "M4_kin": PDG_SCHEME_M4KIN}
 
 
 class pdg_model_desc(ctypes.Structure):
