@@ -275,7 +275,11 @@ int pdg_set_source(pdg_ctx* ctx, const pdg_source_desc* desc);
  * 2-D wavefront, every box starting W cells upwind along all three axes (bound 2^-57 per
  * upwind boundary; W <= 64, otherwise PDG_ERR_UNSUPPORTED).  The first step with a new
  * (dt, scheme) plan copies the corner coefficients to the device (a few tens of KB, in
- * memory allocated by pdg_set_model).
+ * memory allocated by pdg_set_model).  The corner pass keeps the +z faces of each box in
+ * a device scratch buffer (n^2 doubles per cell of a box's region, tens of MB at 384^3
+ * points); the first step that needs a larger one allocates it with cudaMalloc (after a
+ * cudaFree of the old one, which waits for the device), so issue a first step before
+ * any stream capture.
  * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_CUDA,
  *         PDG_ERR_UNSUPPORTED.
  */
