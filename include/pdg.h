@@ -479,13 +479,21 @@ const char* pdg_batch_last_error(const pdg_batch* batch);
  * pdg_server_create -- budget in bytes of resident kinetic state, chunk of steps per
  *   iteration (>= 1), use_graph as in pdg_batch_step, CUDA stream (NULL = default).
  * pdg_server_submit -- validate and enqueue a request; *id receives its id (> 0).
- *   Errors: PDG_ERR_ARG (bad request, w0 length, larger than the budget), PDG_ERR_OOM.
+ *   Errors: PDG_ERR_ARG (bad request, w0 length, larger than the budget), PDG_ERR_OOM,
+ *   PDG_ERR_UNSUPPORTED (lattice models: they run through pdg_step only).
  * pdg_server_iterate -- one admission / batched chunk / retirement round (synchronous).
+ *   A request whose admission fails (its state cannot be allocated, e.g. the device holds
+ *   less free memory than the budget) fails alone: it leaves the queue, pdg_server_result
+ *   returns its status, and the other requests are served.
+ * pdg_server_cancel -- drop a waiting or resident request between iterations (its state is
+ *   freed); pdg_server_result then returns PDG_ERR_STATE for it.
+ *   Errors: PDG_ERR_STATE (no waiting or resident request with this id), PDG_ERR_ARG.
  * pdg_server_pending -- waiting and resident counts.
  * pdg_server_poll -- up to max finished requests not yet polled: ids, arrival,
  *   admission and completion times; *count receives how many were written.
  * pdg_server_result -- copy the final w of a finished request (once; then released).
- *   Errors: PDG_ERR_STATE (unknown, unfinished or already fetched id), PDG_ERR_ARG.
+ *   Errors: PDG_ERR_STATE (unknown, unfinished, cancelled or already fetched id),
+ *   PDG_ERR_ARG, or the status of a request whose admission failed (e.g. PDG_ERR_OOM).
  * pdg_server_stats -- iterations, DOF-updates done, requests completed, peak resident bytes.
  * pdg_server_destroy -- free everything, including unfinished requests.
  */
@@ -512,10 +520,19 @@ int pdg_server_pending(const pdg_server* server, int* n_waiting, int* n_resident
 int pdg_server_poll(pdg_server* server, long long* ids, double* t_arrival, double* t_admit, double* t_done,
                     int max, int* count);
 int pdg_server_result(pdg_server* server, long long id, double* w, size_t len);
+int pdg_server_cancel(pdg_server* server, long long id);
 int pdg_server_stats(const pdg_server* server, long long* iterations, long long* dof_updates,
                      long long* completed, size_t* peak_bytes);
 int pdg_server_destroy(pdg_server* server);
 const char* pdg_server_last_error(const pdg_server* server);
+
+/*
+ * pdg_debug_fail_allocs -- host-side fault injection for tests: the next n device
+ * allocations of kinetic states (any context, this process) fail as if the device were
+ * out of memory, without calling the CUDA allocator; n = 0 disarms.  The failing call
+ * returns PDG_ERR_OOM and leaves its context as it was.  Errors: PDG_ERR_ARG (n < 0).
+ */
+int pdg_debug_fail_allocs(int n);
 
 /* pdg_destroy -- free the context and its device memory (NULL is a no-op). */
 int pdg_destroy(pdg_ctx* ctx);

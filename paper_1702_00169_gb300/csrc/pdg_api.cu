@@ -12,6 +12,8 @@
 // The collapsed scheme of Section 5.1 merges interior half steps into T(dt).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -881,8 +883,9 @@ int ensure_state(pdg_ctx* c) {
   const long long need = state_slots(c) * c->npoints;
   if (need <= c->f_cap) return PDG_OK;
   double* nf = nullptr;
-  cudaError_t e = c->async_alloc ? cudaMallocAsync((void**)&nf, sizeof(double) * (size_t)need, c->stream)
-                                 : cudaMalloc((void**)&nf, sizeof(double) * (size_t)need);
+  cudaError_t e = pdg_fault_take_alloc() ? cudaErrorMemoryAllocation   // injected on the host (tests)
+                  : c->async_alloc ? cudaMallocAsync((void**)&nf, sizeof(double) * (size_t)need, c->stream)
+                                   : cudaMalloc((void**)&nf, sizeof(double) * (size_t)need);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, e == cudaErrorMemoryAllocation ? PDG_ERR_OOM : PDG_ERR_CUDA,
@@ -927,6 +930,17 @@ void free_inflow(pdg_ctx* c) {
 }
 
 }  // namespace
+
+// Host-side fault injection: the next n state allocations fail as if the device were out
+// of memory (pdg_debug_fail_allocs).
+static std::atomic<int> g_fail_allocs{0};
+
+int pdg_fault_take_alloc() {
+  int n = g_fail_allocs.load();
+  while (n > 0 && !g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+  }
+  return n > 0 ? 1 : 0;
+}
 
 bool pdg_internal_view(const pdg_ctx* c, PdgStateView* v) {
   if (!c || !c->has_state || !c->f) return false;
@@ -977,6 +991,12 @@ const char* pdg_status_string(int s) {
 }
 
 const char* pdg_last_error(const pdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int pdg_debug_fail_allocs(int n) {
+  if (n < 0) return PDG_ERR_ARG;
+  g_fail_allocs.store(n);
+  return PDG_OK;
+}
 
 int pdg_create_mesh(pdg_ctx** out, int dim, const int n_macro[3], const int n_sub[3], int order,
                     const double length[3], unsigned periodic_mask, void* cuda_stream) {

@@ -263,6 +263,10 @@ int pdg_internal_set_w_async(pdg_ctx* c, const double* w_host_pinned);
 struct pdg_batch;
 int pdg_internal_batch_set(pdg_batch* b, int n, pdg_ctx* const* ctxs);
 
+// Host-side fault injection (pdg_debug_fail_allocs): 1 when the caller's device allocation
+// must fail as out of memory (the counter of injected failures is decremented).
+int pdg_fault_take_alloc();
+
 // Capacity (doubles) of the static staging array of pdg_get_w_noalloc (8 MiB).
 #define PDG_NOALLOC_W_MAX (1LL << 20)
 

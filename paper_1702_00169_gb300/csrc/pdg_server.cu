@@ -51,8 +51,10 @@ struct pdg_server {
   std::vector<Req*> resident;
   std::deque<Done> done;                                    // not yet polled
   std::unordered_map<long long, std::vector<double>> results;  // not yet fetched
+  std::unordered_map<long long, int> failed;                   // admission failed: status (not yet fetched)
+  std::unordered_map<long long, char> cancelled;               // cancelled ids (not yet fetched)
   pdg_batch* batch = nullptr;
-  long long iterations = 0, dof_updates = 0, admitted = 0, completed = 0;
+  long long iterations = 0, dof_updates = 0, admitted = 0, completed = 0, nfailed = 0, ncancelled = 0;
   std::string err;
 };
 
@@ -115,6 +117,8 @@ int pdg_server_submit(pdg_server* s, const pdg_request* req, long long* id) {
   if (req->dim < 1 || req->dim > 3 || req->order < 1 || req->order > 4 || req->nsteps < 0 ||
       !(req->dt == req->dt))
     return sfail(s, PDG_ERR_ARG, "bad request");
+  if (req->model.kind >= PDG_MODEL_ISOTHERMAL_D2Q9)
+    return sfail(s, PDG_ERR_UNSUPPORTED, "lattice models (D2Q9 / D3Qq) run through pdg_step only");
   // sizes through a throw-away context (no device work)
   pdg_ctx* probe = nullptr;
   int st = pdg_create_mesh(&probe, req->dim, req->n_macro, req->n_sub, req->order, nullptr,
@@ -158,8 +162,12 @@ int pdg_server_iterate(pdg_server* s, int* n_resident, int* n_done) {
     if (s->resident_bytes + r->state_bytes > s->budget) break;
     s->waiting.pop_front();
     if (int st = start_req(s, r)) {
+      // the request fails alone (e.g. the device is out of memory beyond the budget): its
+      // status is kept for pdg_server_result and the others are served
+      s->failed[r->id] = st;
+      s->nfailed++;
       free_req(r);
-      return st;
+      continue;
     }
     r->t_admit = now_s(s);
     s->resident_bytes += r->state_bytes;
@@ -252,8 +260,44 @@ int pdg_server_poll(pdg_server* s, long long* ids, double* t_arrival, double* t_
   return PDG_OK;
 }
 
+int pdg_server_cancel(pdg_server* s, long long id) {
+  if (!s) return PDG_ERR_ARG;
+  for (auto it = s->waiting.begin(); it != s->waiting.end(); ++it)
+    if ((*it)->id == id) {
+      free_req(*it);
+      s->waiting.erase(it);
+      s->cancelled[id] = 1;
+      s->ncancelled++;
+      return PDG_OK;
+    }
+  for (size_t i = 0; i < s->resident.size(); ++i)
+    if (s->resident[i]->id == id) {
+      // between iterations no launch of the server is in flight; pdg_destroy frees the
+      // stream-ordered state after the server stream's pending work
+      Req* r = s->resident[i];
+      s->resident_bytes -= r->state_bytes;
+      s->resident.erase(s->resident.begin() + (long)i);
+      free_req(r);
+      s->cancelled[id] = 1;
+      s->ncancelled++;
+      return PDG_OK;
+    }
+  return sfail(s, PDG_ERR_STATE, "no waiting or resident request with this id");
+}
+
 int pdg_server_result(pdg_server* s, long long id, double* w, size_t len) {
   if (!s || !w) return PDG_ERR_ARG;
+  auto fit = s->failed.find(id);
+  if (fit != s->failed.end()) {
+    const int st = fit->second;
+    s->failed.erase(fit);
+    return sfail(s, st, "request " + std::to_string(id) + " failed at admission");
+  }
+  auto cit = s->cancelled.find(id);
+  if (cit != s->cancelled.end()) {
+    s->cancelled.erase(cit);
+    return sfail(s, PDG_ERR_STATE, "request " + std::to_string(id) + " was cancelled");
+  }
   auto it = s->results.find(id);
   if (it == s->results.end()) return sfail(s, PDG_ERR_STATE, "no result for this id (not finished or fetched)");
   if (it->second.size() != len) return sfail(s, PDG_ERR_ARG, "result length mismatch");

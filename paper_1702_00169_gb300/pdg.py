@@ -105,9 +105,11 @@ _SIGS = {
     "pdg_server_pending": (_I, [_P, _P, _P]),
     "pdg_server_poll": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "pdg_server_result": (_I, [_P, ctypes.c_longlong, _P, _SZ]),
+    "pdg_server_cancel": (_I, [_P, ctypes.c_longlong]),
     "pdg_server_stats": (_I, [_P, _P, _P, _P, _P]),
     "pdg_server_destroy": (_I, [_P]),
     "pdg_server_last_error": (ctypes.c_char_p, [_P]),
+    "pdg_debug_fail_allocs": (_I, [_I]),
     "pdg_destroy": (_I, [_P]),
     "pdg_last_error": (ctypes.c_char_p, [_P]),
     "pdg_status_string": (ctypes.c_char_p, [_I]),
@@ -411,6 +413,9 @@ class Server:
         out = np.empty(w_len)
         self._check(pdg_server_result(self.s, rid, out.ctypes.data, w_len), "pdg_server_result")
         return out
+
+    def cancel(self, rid):
+        self._check(pdg_server_cancel(self.s, rid), "pdg_server_cancel")
 
     def stats(self):
         it, du, co = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
