@@ -81,7 +81,7 @@ enum {
                                   1/3, 1/18, 1/36 (reading: the paper prints no 3-D one).
                                   Each edge velocity acts in planes: its transport is the
                                   D2Q9 diagonal recurrence on every plane of points.
-                                  Periodic meshes; 0 < theta <= 1; dt > 0. */
+                                  Periodic or inflow axes; 0 < theta <= 1; dt > 0. */
   PDG_MODEL_ISOTHERMAL_D3Q15 = 5, /* D = 3, m = 4, w = (rho, rho u): the D3Q15 lattice of
                                   Section 4.5: velocities 0, the six lambda(+-e_a) and the
                                   eight corners lambda(+-1, +-1, +-1), ordered z = +1 first,
@@ -89,12 +89,12 @@ enum {
                                   the same equilibrium with weights 2/9, 1/9, 1/72.  A corner
                                   velocity couples each cell to three upwind faces: its
                                   transport is the 3-D recurrence of pdg_step's
-                                  documentation.  Periodic meshes; degree <= 3;
+                                  documentation.  Periodic or inflow axes; degree <= 3;
                                   0 < theta <= 1; dt > 0. */
   PDG_MODEL_ISOTHERMAL_D3Q27 = 6 /* D = 3, m = 4, w = (rho, rho u): the D3Q27 lattice of
                                   Section 4.5: the nineteen velocities of D3Q19 in its order,
                                   then the eight corners in the order of D3Q15; weights 8/27,
-                                  2/27, 1/54, 1/216.  Periodic meshes; degree <= 3;
+                                  2/27, 1/54, 1/216.  Periodic or inflow axes; degree <= 3;
                                   0 < theta <= 1; dt > 0. */
 };
 
@@ -313,9 +313,12 @@ int pdg_set_f(pdg_ctx* ctx, const double* f, size_t len, int on_device);
  *        populations; side 1 = the high face, read by the -lambda e_a populations; lines
  *        are the points of the other axes in C order ([P_z][P_y] for axis 0, [P_z][P_x]
  *        for axis 1, [P_y][P_x] for axis 2); len = 2 * m * lines.
- *        D2Q9: [2][3][lines], the three populations entering through that face in
- *        increasing population index (low x face: 1, 5, 8; high x face: 3, 6, 7; low y
- *        face: 2, 5, 6; high y face: 4, 7, 8); again len = 2 * m * lines (m = 3).
+ *        Lattice models: [2][q_f][lines], the q_f populations entering through that face
+ *        (xi_a > 0 at the low face, xi_a < 0 at the high face) in increasing population
+ *        index; len = 2 * q_f * lines.  D2Q9: q_f = 3 (low x face: 1, 5, 8; high x face:
+ *        3, 6, 7; low y face: 2, 5, 6; high y face: 4, 7, 8).  D3Q19 and D3Q15: q_f = 5
+ *        (low x face: 1, 7, 10, 11, 14 in both orders); D3Q27: q_f = 9 (low x face: 1, 7,
+ *        10, 11, 14, 19, 22, 23, 26).
  *   on_device as for pdg_set_w.  Kept until the next pdg_set_inflow or a model change
  *   (which resets it to zero).  Time steps that make |beta| > 1 (dt < 0) are not
  *   supported on inflow axes (pdg_step returns PDG_ERR_UNSUPPORTED).

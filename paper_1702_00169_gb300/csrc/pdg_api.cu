@@ -176,6 +176,91 @@ bool lattice_of(int kind, Lattice* L) {
   return false;
 }
 
+// Unit velocities xi_i of the lattice models in population order (the orders of pdg.h):
+// components (x, y, z); nullptr for the DnQ2n models.
+struct LatticeTables {
+  int q9[9][3], q19[19][3], q15[15][3], q27[27][3];
+};
+LatticeTables make_lattice_tables() {
+  LatticeTables t{};
+  // rest, +-x, +-y, +-z; edges by plane xy, xz, yz; corners z = +1 then z = -1
+  const int q9[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                        {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+  const int axis[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+  const int sa[4] = {1, -1, -1, 1}, sb[4] = {1, 1, -1, -1};
+  const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+  int edge[12][3] = {}, corner[8][3] = {};
+  for (int o = 0; o < 3; ++o)
+    for (int k = 0; k < 4; ++k) {
+      edge[4 * o + k][pa[o]] = sa[k];
+      edge[4 * o + k][pb[o]] = sb[k];
+    }
+  for (int h = 0; h < 2; ++h)
+    for (int k = 0; k < 4; ++k) {
+      corner[4 * h + k][0] = sa[k];
+      corner[4 * h + k][1] = sb[k];
+      corner[4 * h + k][2] = h == 0 ? 1 : -1;
+    }
+  for (int i = 0; i < 9; ++i)
+    for (int a = 0; a < 3; ++a) t.q9[i][a] = q9[i][a];
+  for (int i = 0; i < 7; ++i)
+    for (int a = 0; a < 3; ++a) t.q19[i][a] = t.q15[i][a] = t.q27[i][a] = axis[i][a];
+  for (int i = 0; i < 12; ++i)
+    for (int a = 0; a < 3; ++a) t.q19[7 + i][a] = t.q27[7 + i][a] = edge[i][a];
+  for (int i = 0; i < 8; ++i)
+    for (int a = 0; a < 3; ++a) {
+      t.q15[7 + i][a] = corner[i][a];
+      t.q27[19 + i][a] = corner[i][a];
+    }
+  return t;
+}
+
+// Unit velocities xi_i of the lattice models in population order (the orders of pdg.h):
+// components (x, y, z); nullptr for the DnQ2n models.
+const int* lattice_xi(int kind, int* q) {
+  static const LatticeTables t = make_lattice_tables();
+  switch (kind) {
+    case PDG_MODEL_ISOTHERMAL_D2Q9: *q = 9; return &t.q9[0][0];
+    case PDG_MODEL_ISOTHERMAL_D3Q19: *q = 19; return &t.q19[0][0];
+    case PDG_MODEL_ISOTHERMAL_D3Q15: *q = 15; return &t.q15[0][0];
+    case PDG_MODEL_ISOTHERMAL_D3Q27: *q = 27; return &t.q27[0][0];
+  }
+  *q = 0;
+  return nullptr;
+}
+
+// Inflow data entries per face side: the conserved variables of a DnQ2n model (its +-e_a
+// population of each variable), or for a lattice the populations entering through the face.
+int inflow_entries(const PdgModel& m) {
+  int q = 0;
+  const int* xi = lattice_xi(m.kind, &q);
+  if (!xi) return m.m;
+  int n = 0;
+  for (int i = 0; i < q; ++i) n += xi[3 * i] > 0;
+  return n;
+}
+
+// Entry of lattice population i in the data of the face normal to `axis` that it enters
+// through (low face for xi_axis > 0, high face for < 0): its rank among the populations
+// entering through that face, in population order.
+int inflow_entry(int kind, int axis, int i) {
+  int q = 0;
+  const int* xi = lattice_xi(kind, &q);
+  const int s = xi[3 * i + axis];
+  int e = 0;
+  for (int j = 0; j < i; ++j) e += xi[3 * j + axis] == s;
+  return e;
+}
+
+// Stride, in the line index of the face normal to axis A (C order over the other axes, x
+// fastest), of the point coordinate along axis b != A.
+long long face_line_stride(const pdg_ctx* c, int A, int b) {
+  long long st = 1;
+  for (int a = 0; a < b; ++a)
+    if (a != A) st *= c->P[a];
+  return st;
+}
+
 // Corner coefficient slots in pdg_ctx::cbuf: FP64 B^-1 (64 x 64 at most) then its
 // double-float copy, per slot.
 #define PDG_CORNER_PLANS 4
@@ -299,13 +384,15 @@ int make_pass(pdg_ctx* c, const PdgPassSpec& sp, int max_threads, const int* ov,
     p.fbent[0] = p.fbent[1] = 0;
   } else if (c->model.kind == PDG_MODEL_ISOTHERMAL_D3Q19 || c->model.kind == PDG_MODEL_ISOTHERMAL_D3Q15 ||
              c->model.kind == PDG_MODEL_ISOTHERMAL_D3Q27) {
-    // populations 1 + 2 axis (+lambda e_axis) and 2 + 2 axis (-lambda e_axis); periodic only
+    // populations 1 + 2 axis (+lambda e_axis) and 2 + 2 axis (-lambda e_axis); each is the
+    // first of the populations entering through its face
     p.ntf = 2;
     p.tfield[0] = 1 + 2 * axis;
     p.tdir[0] = +1;
     p.tfield[1] = 2 + 2 * axis;
     p.tdir[1] = -1;
-    p.fbnent = 1;
+    p.fbnent = inflow_entries(c->model);
+    p.fbent[0] = p.fbent[1] = 0;
   } else {
     p.ntf = 2 * m;
     for (int k = 0; k < m; ++k) {
@@ -414,24 +501,29 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, int o, PdgDiagPass* out) {
   }
   const int in = sp.dslot_in, outs = sp.dslot_in == L.diag ? L.scratch : L.diag;
   static const int sx[4] = {+1, -1, -1, +1}, sy[4] = {+1, +1, -1, -1};   // (+,+) (-,+) (-,-) (+,-)
-  // entry of populations 5-8 among the three entering through their x / y face:
-  // low x {1, 5, 8}, high x {3, 6, 7}, low y {2, 5, 6}, high y {4, 7, 8}
-  static const int xent[4] = {1, 1, 2, 2}, yent[4] = {1, 2, 1, 2};
   p.npop = 4;
   for (int i = 0; i < 4; ++i) {
+    const int pop = L.diag + 4 * o + i;   // population index (slots diag.. hold it or scratch..)
     p.fin[i] = c->f + (long long)(in + 4 * o + i) * c->npoints;
     p.fout[i] = c->f + (long long)(outs + 4 * o + i) * c->npoints;
     p.sx[i] = sx[i];
     p.sy[i] = sy[i];
     p.bxside[i] = sx[i] > 0 ? 0 : 1;
     p.byside[i] = sy[i] > 0 ? 0 : 1;
-    p.bxent[i] = xent[i];
-    p.byent[i] = yent[i];
+    p.bxent[i] = inflow_entry(c->model.kind, ax, pop);
+    p.byent[i] = inflow_entry(c->model.kind, ay, pop);
   }
   p.perx = c->periodic[ax] ? 1 : 0;
   p.pery = c->periodic[ay] ? 1 : 0;
   p.fbx = c->periodic[ax] ? nullptr : c->fb[ax];
   p.fby = c->periodic[ay] ? nullptr : c->fb[ay];
+  p.nent = inflow_entries(c->model);
+  p.fbx_lines = c->npoints / c->P[ax];
+  p.fby_lines = c->npoints / c->P[ay];
+  p.fbx_ls = face_line_stride(c, ax, ay);
+  p.fby_ls = face_line_stride(c, ay, ax);
+  p.fbx_ps = c->dim == 3 ? face_line_stride(c, ax, az) : 0;
+  p.fby_ps = c->dim == 3 ? face_line_stride(c, ay, az) : 0;
   p.n = c->n;
   p.ncx = c->N[ax];
   p.ncy = c->N[ay];
@@ -540,6 +632,18 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
   p.sa = 1;
   p.sb = c->P[0];
   p.sc = (long long)c->P[0] * c->P[1];
+  p.nent = inflow_entries(c->model);
+  const int* sgn[3] = {sx, sy, sz};
+  for (int a = 0; a < 3; ++a) {
+    p.per[a] = c->periodic[a] ? 1 : 0;
+    p.fb[a] = c->periodic[a] ? nullptr : c->fb[a];
+    p.flines[a] = c->npoints / c->P[a];
+    for (int b = 0; b < 3; ++b) p.fls[a][b] = b == a ? 0 : face_line_stride(c, a, b);
+    for (int i = 0; i < 8; ++i) {
+      p.bside[a][i] = sgn[a][i] > 0 ? 0 : 1;
+      p.bent[a][i] = inflow_entry(c->model.kind, a, L.diag + c0 + i);
+    }
+  }
   p.prec = c->model.prec;
   p.threads = c->cshape[0] ? c->cshape[0] : 512;
   if (c->cshape[0]) {
@@ -910,7 +1014,7 @@ long long lines_of(const pdg_ctx* c, int a) { return c->npoints / c->P[a]; }
 int ensure_inflow(pdg_ctx* c) {
   for (int a = 0; a < c->dim; ++a) {
     if (c->periodic[a] || c->fb[a]) continue;
-    const size_t n = 2 * (size_t)c->model.m * (size_t)lines_of(c, a);
+    const size_t n = 2 * (size_t)inflow_entries(c->model) * (size_t)lines_of(c, a);
     cudaError_t e = cudaMalloc((void**)&c->fb[a], sizeof(double) * n);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->fb[a], 0, sizeof(double) * n, c->stream);
     if (e != cudaSuccess) {
@@ -1055,8 +1159,6 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   const bool q3d = q19 || q15 || q27, lat = q9 || q3d;
   if (q9 && c->dim != 2) return fail(c, PDG_ERR_UNSUPPORTED, "D2Q9 needs dim = 2");
   if (q3d && c->dim != 3) return fail(c, PDG_ERR_UNSUPPORTED, "D3Q15 / D3Q19 / D3Q27 need dim = 3");
-  if (q3d && !(c->periodic[0] && c->periodic[1] && c->periodic[2]))
-    return fail(c, PDG_ERR_UNSUPPORTED, "D3Q15 / D3Q19 / D3Q27 run on periodic meshes");
   if ((q15 || q27) && c->n > PDG_MAXN_CORNER)
     return fail(c, PDG_ERR_UNSUPPORTED, "D3Q15 / D3Q27 support degrees 1 to 3");
   if (lat && !(d->theta > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "diagonal velocities need theta > 0");
@@ -1269,7 +1371,7 @@ int pdg_set_inflow(pdg_ctx* c, int axis, const double* fb, size_t len, int on_de
   if (!c->has_model) return fail(c, PDG_ERR_STATE, "pdg_set_inflow before pdg_set_model");
   if (axis < 0 || axis >= c->dim || c->periodic[axis]) return fail(c, PDG_ERR_ARG, "axis is not an inflow axis");
   if (!fb) return fail(c, PDG_ERR_ARG, "fb is NULL");
-  const size_t need = 2 * (size_t)c->model.m * (size_t)lines_of(c, axis);
+  const size_t need = 2 * (size_t)inflow_entries(c->model) * (size_t)lines_of(c, axis);
   if (len != need) return fail(c, PDG_ERR_ARG, "inflow data length mismatch");
   if (int r = ensure_inflow(c)) return r;
   PDG_CUDA(c, cudaMemcpyAsync(c->fb[axis], fb, sizeof(double) * need,

@@ -44,6 +44,14 @@ struct CornerGeom {
   int sx, sy, sz;
   long long sa, sb, sc;
   int ncol, nrow, nlay, wx, wy, wz;
+  int X0, Y0, Z0, ncx, ncy, ncz;
+  // inflow starts: the region begins at the domain's inflow face of that axis, and the
+  // values entering its first column (row, layer) are this population's boundary data
+  int bx, by, bz;
+  const double* fbx;
+  const double* fby;
+  const double* fbz;
+  long long fls[3][3];
   const long long* colx;   // [ncol + 1]: offset of traversal node 0 of region column j - 1
   const long long* rowy;   // [nrow + 1]
   const long long* layz;   // [nlay + 1]
@@ -53,6 +61,23 @@ struct CornerGeom {
 __device__ __forceinline__ long long corner_off(const CornerGeom& g, int j, int r, int k, int iz, int iy, int ix) {
   return g.layz[k + 1] + (long long)(g.sz * iz) * g.sc + g.rowy[r + 1] + (long long)(g.sy * iy) * g.sb +
          g.colx[j + 1] + (long long)(g.sx * ix) * g.sa;
+}
+
+// Point coordinates (along x, y, z) of traversal node i of region column j, row r, layer k.
+template <int NP>
+__device__ __forceinline__ long long corner_px(const CornerGeom& g, int j, int i) {
+  const int tc = wrap_cell(g.X0 - g.wx + j, g.ncx);
+  return g.sx > 0 ? (long long)tc * NP + i : (long long)(g.ncx - 1 - tc) * NP + (NP - 1 - i);
+}
+template <int NP>
+__device__ __forceinline__ long long corner_py(const CornerGeom& g, int r, int i) {
+  const int tc = wrap_cell(g.Y0 - g.wy + r, g.ncy);
+  return g.sy > 0 ? (long long)tc * NP + i : (long long)(g.ncy - 1 - tc) * NP + (NP - 1 - i);
+}
+template <int NP>
+__device__ __forceinline__ long long corner_pz(const CornerGeom& g, int k, int i) {
+  const int tc = wrap_cell(g.Z0 - g.wz + k, g.ncz);
+  return g.sz > 0 ? (long long)tc * NP + i : (long long)(g.ncz - 1 - tc) * NP + (NP - 1 - i);
 }
 
 // Row of one cell in the staging buffers: its n^3 state values, then the n^2 values on the
@@ -78,11 +103,19 @@ __device__ __forceinline__ void corner_stage(const CornerGeom& g, int k, int t, 
     cp_async8(fb + c * RS + q, src);
   }
   const int tid = threadIdx.x;
-  if (jlo == 0 && tid < NF)   // column 0 at row t: +x face of the cell upwind of it
-    cp_async8(lbnd + tid, g.fin + corner_off(g, -1, t, k, tid / NP, tid % NP, NP - 1));
+  if (jlo == 0 && tid < NF) {   // column 0 at row t: +x face of the cell upwind of it
+    const int iz = tid / NP, iy = tid % NP;
+    if (g.bx)                   // the inflow face: boundary value at the node's (y, z) point
+      cp_async8(lbnd + tid, g.fbx + corner_py<NP>(g, t, iy) * g.fls[0][1] + corner_pz<NP>(g, k, iz) * g.fls[0][2]);
+    else
+      cp_async8(lbnd + tid, g.fin + corner_off(g, -1, t, k, iz, iy, NP - 1));
+  }
   if (jhi == t && tid >= NF && tid < 2 * NF) {   // row 0 at column t: +y face of the cell below
-    const int u = tid - NF;
-    cp_async8(bbnd + u, g.fin + corner_off(g, t, -1, k, u / NP, NP - 1, u % NP));
+    const int u = tid - NF, iz = u / NP, ix = u % NP;
+    if (g.by)
+      cp_async8(bbnd + u, g.fby + corner_px<NP>(g, t, ix) * g.fls[1][0] + corner_pz<NP>(g, k, iz) * g.fls[1][2]);
+    else
+      cp_async8(bbnd + u, g.fin + corner_off(g, t, -1, k, iz, NP - 1, ix));
   }
 }
 
@@ -110,10 +143,28 @@ __device__ __forceinline__ void corner_body(const PdgCornerPass& p, double* sm) 
   g.sa = p.sa;
   g.sb = p.sb;
   g.sc = p.sc;
-  g.wx = C.wx;
-  g.wy = C.wy;
-  g.wz = C.wz;
   const int X0 = txi * p.tx, Y0 = tyi * p.ty, Z0 = tzi * p.tz;
+  // periodic axis: the truncated start; inflow axis: at most back to the inflow face
+  g.wx = p.per[0] ? C.wx : min(C.wx, X0);
+  g.wy = p.per[1] ? C.wy : min(C.wy, Y0);
+  g.wz = p.per[2] ? C.wz : min(C.wz, Z0);
+  g.bx = !p.per[0] && X0 - g.wx == 0;
+  g.by = !p.per[1] && Y0 - g.wy == 0;
+  g.bz = !p.per[2] && Z0 - g.wz == 0;
+  g.X0 = X0;
+  g.Y0 = Y0;
+  g.Z0 = Z0;
+  g.ncx = p.ncx;
+  g.ncy = p.ncy;
+  g.ncz = p.ncz;
+  const double* fbs[3];
+  for (int a = 0; a < 3; ++a) {
+    fbs[a] = p.fb[a] ? p.fb[a] + (long long)(p.bside[a][pop] * p.nent + p.bent[a][pop]) * p.flines[a] : nullptr;
+    for (int b = 0; b < 3; ++b) g.fls[a][b] = p.fls[a][b];
+  }
+  g.fbx = fbs[0];
+  g.fby = fbs[1];
+  g.fbz = fbs[2];
   g.ncol = min(p.tx, p.ncx - X0) + g.wx;
   g.nrow = min(p.ty, p.ncy - Y0) + g.wy;
   g.nlay = min(p.tz, p.ncz - Z0) + g.wz;
@@ -165,11 +216,13 @@ __device__ __forceinline__ void corner_body(const PdgCornerPass& p, double* sm) 
   g.rowy = rowy;
   g.layz = layz;
   __syncthreads();
-  // the region's lower z boundary: old +z faces of the layer below the region
+  // the region's lower z boundary: old +z faces of the layer below the region, or at the
+  // inflow face the boundary values at the nodes' (x, y) points
   for (int i = threadIdx.x; i < g.nrow * g.ncol * NF; i += blockDim.x) {
     const int cell = i / NF, u = i % NF;
     const int r = cell / g.ncol, j = cell % g.ncol;
-    g.zt[i] = g.fin[corner_off(g, j, r, -1, NP - 1, u / NP, u % NP)];
+    g.zt[i] = g.bz ? g.fbz[corner_px<NP>(g, j, u % NP) * g.fls[2][0] + corner_py<NP>(g, r, u / NP) * g.fls[2][1]]
+                   : g.fin[corner_off(g, j, r, -1, NP - 1, u / NP, u % NP)];
   }
   __syncthreads();
   const T rth = PDG_DC(T, C, rtheta), c1 = PDG_DC(T, C, c1);

@@ -50,8 +50,9 @@ struct DiagGeom {
   // inflow faces: when bx (by) is set the region starts at the domain's inflow face and
   // the values entering column 0 (row 0) are the boundary data fbx (fby)
   int bx, by;
-  const double* fbx;       // [P_y] values of this population at its x inflow face
-  const double* fby;       // [P_x] values at its y inflow face
+  const double* fbx;       // values of this population at its x inflow face (this plane)
+  const double* fby;       // values at its y inflow face
+  long long fbx_ls, fby_ls;   // line-index stride of the point coordinate along y (x) there
 };
 
 // Offset of node (iy, ix) (traversal orientation) of region cell (j, r), j, r >= -1.
@@ -93,7 +94,7 @@ __device__ __forceinline__ void diag_stage(const DiagGeom& g, int t, T* fb, T* l
     if (g.bx) {                 // the inflow face: boundary value at the node's y point
       const int tr = wrap_cell(g.Y0 - g.wy + t, g.ncy);   // y may be periodic
       const int pcy = g.sy > 0 ? tr : g.ncy - 1 - tr;
-      cp_async8(lbnd + tid, g.fbx + pcy * NP + (g.sy > 0 ? tid : NP - 1 - tid));
+      cp_async8(lbnd + tid, g.fbx + (long long)(pcy * NP + (g.sy > 0 ? tid : NP - 1 - tid)) * g.fbx_ls);
     } else {
       cp_async8(lbnd + tid, g.fin + diag_off<NP>(g, -1, t, tid, NP - 1));
     }
@@ -103,7 +104,7 @@ __device__ __forceinline__ void diag_stage(const DiagGeom& g, int t, T* fb, T* l
     if (g.by) {
       const int tc = wrap_cell(g.X0 - g.wx + t, g.ncx);   // x may be periodic
       const int pcx = g.sx > 0 ? tc : g.ncx - 1 - tc;
-      cp_async8(bbnd + ix, g.fby + pcx * NP + (g.sx > 0 ? ix : NP - 1 - ix));
+      cp_async8(bbnd + ix, g.fby + (long long)(pcx * NP + (g.sx > 0 ? ix : NP - 1 - ix)) * g.fby_ls);
     } else {
       cp_async8(bbnd + ix, g.fin + diag_off<NP>(g, t, -1, NP - 1, ix));
     }
@@ -139,9 +140,12 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
   g.wy = p.pery ? C.wy : min(C.wy, g.Y0);
   g.bx = !p.perx && g.X0 - g.wx == 0;
   g.by = !p.pery && g.Y0 - g.wy == 0;
-  const long long Py = (long long)p.ncy * NP, Px = (long long)p.ncx * NP;
-  g.fbx = p.fbx ? p.fbx + (long long)(p.bxside[pop] * 3 + p.bxent[pop]) * Py : nullptr;
-  g.fby = p.fby ? p.fby + (long long)(p.byside[pop] * 3 + p.byent[pop]) * Px : nullptr;
+  g.fbx = p.fbx ? p.fbx + (long long)(p.bxside[pop] * p.nent + p.bxent[pop]) * p.fbx_lines + plane * p.fbx_ps
+                : nullptr;
+  g.fby = p.fby ? p.fby + (long long)(p.byside[pop] * p.nent + p.byent[pop]) * p.fby_lines + plane * p.fby_ps
+                : nullptr;
+  g.fbx_ls = p.fbx_ls;
+  g.fby_ls = p.fby_ls;
   const int ox = min(p.tx, p.ncx - g.X0), oy = min(p.ty, p.ncy - g.Y0);
   g.ncol = ox + g.wx;
   g.nrow = oy + g.wy;

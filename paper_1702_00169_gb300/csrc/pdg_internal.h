@@ -191,12 +191,16 @@ struct PdgDiagPass {
   const double* fin[4];
   double* fout[4];
   int sx[4], sy[4];
-  // inflow axes (per axis: 1 = periodic); boundary data [2 sides][3][lines] (lines = P_y
-  // for the x faces, P_x for the y faces) and each population's side and entry in it
+  // inflow axes (per axis: 1 = periodic); boundary data [2 sides][nent][lines] of the faces
+  // normal to a ("x") and b ("y") and each population's side and entry in it.  A point of
+  // such a face has line index (coordinate along the other plane axis) * f?_ls +
+  // (plane index) * f?_ps; f?_lines = lines of the face (the entry stride).
   int perx, pery;
   const double* fbx;
   const double* fby;
   int bxside[4], bxent[4], byside[4], byent[4];
+  int nent;
+  long long fbx_lines, fby_lines, fbx_ls, fbx_ps, fby_ls, fby_ps;
   int npop, n, ncx, ncy;
   long long sa, sb;       // point strides along a and b
   long long sc;           // point stride between planes
@@ -236,6 +240,14 @@ struct PdgCornerPass {
   const double* binv;              // device: NN x NN row-major (FP64)
   const float* binv_f;             // device: NN x NN (hi, lo) pairs (double-float)
   double* zt;                      // device scratch: per block [ty + wy][tx + wx][n^2] +z faces
+  // inflow axes (per axis a: per[a] = 1 periodic); boundary data fb[a] = [2 sides][nent][lines]
+  // of the faces normal to a, each population's side and entry there; a face point's line
+  // index is sum over the other axes b of (point coordinate along b) * fls[a][b]
+  int per[3];
+  const double* fb[3];
+  int bside[3][8], bent[3][8];
+  int nent;
+  long long flines[3], fls[3][3];
   PdgCornerCoef c;
 };
 

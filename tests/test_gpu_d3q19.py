@@ -96,9 +96,9 @@ def test_moments_checkpoint_and_refusals():
     with pytest.raises(pdg.PdgError):
         pdg.Batch([s])
     s.close()
-    s2 = pdg.Solver(3, (2, 2, 2), (2, 2, 2), 1, periodic=(True, False, True))
-    with pytest.raises(pdg.PdgError) as e:
-        s2.set_model("isothermal_d3q19", 1.0)
+    s2 = pdg.Solver(3, (2, 2, 2), (2, 2, 2), 1)
+    with pytest.raises(pdg.PdgError) as e:       # the D3Q lattices need dim = 3
+        s2.set_model("isothermal_d2q9", 1.0)
     assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
     s2.close()
 

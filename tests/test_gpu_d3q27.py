@@ -119,11 +119,6 @@ def test_moments_checkpoint_and_refusals(lat):
     assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
     s.close()
     kind = cfg.kind
-    s2 = pdg.Solver(3, (2, 2, 2), (2, 2, 2), 1, periodic=(True, False, True))
-    with pytest.raises(pdg.PdgError) as e:
-        s2.set_model(kind, 1.0)
-    assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
-    s2.close()
     s3 = pdg.Solver(3, (1, 1, 1), (2, 2, 2), 4)
     with pytest.raises(pdg.PdgError) as e:
         s3.set_model(kind, 1.0)
