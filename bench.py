@@ -69,6 +69,17 @@ def corner_flops_per_dof(n):
     return 2.0 * n ** 3 + 1.0 + 2.0 + 12.0 / n
 
 
+def lattice_xi_x(kind):
+    """x components of the unit lattice velocities in the population orders of pdg.h."""
+    if kind == "isothermal_d2q9":
+        return [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    axis = [0, 1, -1, 0, 0, 0, 0]
+    edges = [1, -1, -1, 1, 1, -1, -1, 1, 0, 0, 0, 0]     # planes xy, xz (x first), yz
+    corners = [1, -1, -1, 1, 1, -1, -1, 1]
+    return {"isothermal_d3q19": axis + edges, "isothermal_d3q15": axis + corners,
+            "isothermal_d3q27": axis + edges + corners}[kind]
+
+
 def collision_flops(kind, dim):
     """Algorithmic flops of the collision at one point (FMA = 2)."""
     nv = 2 * dim
@@ -494,8 +505,6 @@ def main():
     if args.n_macro:
         cfg = cfg.scaled(n_macro=(args.n_macro,) * cfg.dim,
                          name=f"{cfg.name}_n{args.n_macro}" if args.n_macro != cfg.n_macro[0] else cfg.name)
-    if args.inflow_x and cfg.kind in ("isothermal_d3q19", "isothermal_d3q15", "isothermal_d3q27"):
-        raise SystemExit("--inflow-x: the D3Qq paths run on periodic meshes")
     if args.source != "none" and cfg.kind != "isothermal_d2q9":
         raise SystemExit("--source: sources run on the D2Q9 workload (--workload d2q9)")
     if args.impl == "reference":
@@ -550,9 +559,14 @@ def main():
         # inflow data: the initial equilibrium populations at the two x faces
         s.set_w(w0_dev)
         f0 = s.get_f().reshape((cfg.groups, cfg.nv) + tuple(reversed(cfg.npoints_axis)))
-        if cfg.kind == "isothermal_d2q9":
-            # populations entering through the low x face (1, 5, 8) and the high x face (3, 6, 7)
-            fb = np.ascontiguousarray(np.stack([f0[0, [1, 5, 8], :, 0], f0[0, [3, 6, 7], :, -1]]))
+        if cfg.kind.startswith("isothermal"):
+            # the populations entering through the low x face (xi_x > 0) and the high x face
+            # (xi_x < 0), in population order, at that face's points
+            sx = lattice_xi_x(cfg.kind)
+            lo = [i for i in range(cfg.nv) if sx[i] > 0]
+            hi = [i for i in range(cfg.nv) if sx[i] < 0]
+            fb = np.ascontiguousarray(np.stack([f0[0, lo, ..., 0].reshape(len(lo), -1),
+                                                f0[0, hi, ..., -1].reshape(len(hi), -1)]))
         else:
             fb = np.ascontiguousarray(np.stack([f0[:, 0, ..., 0].reshape(cfg.m, -1),
                                                 f0[:, 1, ..., -1].reshape(cfg.m, -1)]))
