@@ -152,6 +152,9 @@ def parse_args():
     ap.add_argument("--n-macro", type=int, default=None,
                     help="macrocells per axis instead of the workload's (a smaller case of the same "
                          "workload, e.g. for profiler captures)")
+    ap.add_argument("--graph", action="store_true",
+                    help="time pdg_step replaying a captured CUDA graph (PDG_OPT_GRAPH); the roofline "
+                         "and kernel figures come from a run with direct launches")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=20)
@@ -582,25 +585,33 @@ def main():
         if ws > 1:
             torch.distributed.barrier()
 
-    def timed_run(sv):
+    def timed_run(sv, graph=False):
         """W untimed steps, then K steps between CUDA events on the context stream, with
-        per-kernel event timing and clock sampling inside the timed region."""
+        per-kernel event timing and clock sampling inside the timed region.  graph: the K
+        steps replay a CUDA graph captured by one untimed run of K steps (per-kernel timing
+        is off in graph replay: launches and kms come back as zeros)."""
         sv.set_w(w0_dev)
         if fb is not None:
             sv.set_inflow(0, fb)
-        if args.shapes:
+        if graph:
+            pass                            # the launch shapes of the plain run stay
+        elif args.shapes:
             for kind, sh in enumerate(args.shapes.split("/")):
                 sv.set_launch(kind, *[int(x) for x in sh.split(",")])
         elif not args.no_autotune:
             sv.autotune(cfg.dt, reps=3)     # launch shapes picked on a scratch copy (untimed)
         sv.step(cfg.dt, args.warmup)
+        if graph:
+            sv.set_option(pdg.PDG_OPT_GRAPH, 1)
+            sv.step(cfg.dt, args.steps)     # capture (and run) the K-step graph, untimed
         sv.synchronize()
         sampler = ClockSampler(dev_uuid)
         barrier()
         torch.cuda.synchronize()
         sampler.start()
         time.sleep(0.4)
-        sv.timing_enable(True)
+        if not graph:
+            sv.timing_enable(True)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
@@ -612,6 +623,8 @@ def main():
         barrier()
         launches, kms = sv.timing_read()
         sv.timing_enable(False)
+        if graph:
+            sv.set_option(pdg.PDG_OPT_GRAPH, 0)
         return ev0.elapsed_time(ev1), launches, kms, clk, sv.get_w()
 
     n = cfg.order + 1
@@ -637,6 +650,14 @@ def main():
 
     # ---- device-resident run (FP64) ----
     ms, launches, kms, clocks, w_end = timed_run(s)
+    graph_run = None
+    if args.graph:
+        # the headline run replays one CUDA graph per K steps; per-kernel timing (roofline,
+        # launch counts) comes from the plain run above
+        ms_g, _, _, clocks_g, _ = timed_run(s, graph=True)
+        graph_run = {"ms_per_step_plain": ms / args.steps,
+                     "note": "one CUDA graph of K steps replayed; bitwise the direct launches (tests/test_gpu_graph.py)"}
+        ms, clocks = ms_g, clocks_g
     shape0, shape1 = s.get_launch(0), s.get_launch(1)
     s_shape = {0: shape0, 1: shape1}
     finite = bool(np.all(np.isfinite(w_end)))
@@ -763,6 +784,8 @@ def main():
                                         (3, "diagonal pass"), (4, "corner pass")) if launches[k]},
             "roofline": roof, "clocks": clocks,
             "e2e": e2e, "cpu_baseline": cpu, "mixed": mixed, "state_finite": finite}
+    if graph_run:
+        line["graph_replay"] = graph_run
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -409,9 +409,16 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
  *     composed sweep, fn = E^2 f + (E q) z + q z', with a 2x2 inflow recurrence; the
  *     same operator, about 27 % fewer operations per cell at degree 3, results equal
  *     up to rounding.  0 runs them as two sweeps.
+ *   PDG_OPT_GRAPH (default 0): pdg_step captures its launches for (dt, nsteps) into a CUDA
+ *     graph on a private stream and replays it while dt, nsteps and the configuration stay
+ *     the same (any set_model / set_w reallocation / set_inflow / set_source / set_launch /
+ *     set_option / autotune call forces a new capture); the replay is ordered after the
+ *     work already on the context stream, and that stream waits for it.  The same
+ *     launches, bitwise the same results, fewer launch overheads for small meshes.  Plans
+ *     and scratch are prepared before the capture.  Ignored while kernel timing is on.
  * Errors: PDG_ERR_ARG (unknown option).
  */
-enum { PDG_OPT_COMPOSE_TT = 1 };
+enum { PDG_OPT_COMPOSE_TT = 1, PDG_OPT_GRAPH = 2 };
 int pdg_set_option(pdg_ctx* ctx, int option, int value);
 
 /* pdg_get_launch -- read the launch shape override of a kind 0..5 (zeros = heuristic). */

@@ -70,6 +70,16 @@ struct pdg_ctx {
   std::vector<CornerPlan> corner_plans;
   char* cbuf = nullptr;
   double* czt = nullptr;                       // corner pass: per-block +z face scratch
+  // CUDA-graph replay of pdg_step (PDG_OPT_GRAPH): the captured step sequence, its key
+  // (dt, nsteps, configuration generation) and the private capture / replay stream
+  bool use_graph = false;
+  unsigned long long gen = 0;                  // bumped by every call that changes the passes
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double g_dt = 0.0;
+  int g_nsteps = -1;
+  unsigned long long g_gen = ~0ULL;
+  cudaEvent_t g_in = nullptr, g_out = nullptr;
   size_t czt_cap = 0;                          // its capacity (8-byte words)
   int cshape[4] = {0, 0, 0, 0};                // corner pass: threads, box x, y, z (0 = heuristic)
   double* kfield = nullptr;                    // penalisation K at every point
@@ -986,6 +996,7 @@ long long state_slots(const pdg_ctx* c) {
 int ensure_state(pdg_ctx* c) {
   const long long need = state_slots(c) * c->npoints;
   if (need <= c->f_cap) return PDG_OK;
+  c->gen++;
   double* nf = nullptr;
   cudaError_t e = pdg_fault_take_alloc() ? cudaErrorMemoryAllocation   // injected on the host (tests)
                   : c->async_alloc ? cudaMallocAsync((void**)&nf, sizeof(double) * (size_t)need, c->stream)
@@ -1142,6 +1153,7 @@ int pdg_create_mesh(pdg_ctx** out, int dim, const int n_macro[3], const int n_su
 
 int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   if (!c || !d) return PDG_ERR_ARG;
+  c->gen++;
   if (d->kind < PDG_MODEL_ADVECTION || d->kind > PDG_MODEL_ISOTHERMAL_D3Q27)
     return fail(c, PDG_ERR_ARG, "unknown model kind");
   if (d->scheme != PDG_SCHEME_M2 && d->scheme != PDG_SCHEME_M2_COLLAPSED && d->scheme != PDG_SCHEME_M2KIN &&
@@ -1295,6 +1307,7 @@ int pdg_get_w(pdg_ctx* c, double* out, size_t len, int on_device) {
 
 int pdg_set_source(pdg_ctx* c, const pdg_source_desc* d) {
   if (!c) return PDG_ERR_ARG;
+  c->gen++;
   if (!c->has_model) return fail(c, PDG_ERR_STATE, "pdg_set_source before pdg_set_model");
   if (!d || d->flags == 0) {
     c->src.flags = 0;
@@ -1354,13 +1367,71 @@ int pdg_set_source(pdg_ctx* c, const pdg_source_desc* d) {
   return PDG_OK;
 }
 
+// Capture the passes of (dt, nsteps) into a CUDA graph on the private stream.  Plans,
+// coefficient uploads and scratch allocations happen first, outside the capture (the
+// corner passes' plans are made by a dry make_corner), so the graph holds launches and
+// device-to-device copies only.
+int capture_steps(pdg_ctx* c, double dt, int nsteps, const std::vector<PdgPassSpec>& sched) {
+  Lattice L;
+  if (lattice_of(c->model.kind, &L) && L.ncorner)
+    for (const auto& sp : sched)
+      if (sp.axis == -1) {
+        PdgCornerPass p;
+        if (int r = make_corner(c, sp, L, &p)) return r;
+      }
+  if (!c->gstream) PDG_CUDA(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+  if (!c->g_in) PDG_CUDA(c, cudaEventCreateWithFlags(&c->g_in, cudaEventDisableTiming));
+  if (!c->g_out) PDG_CUDA(c, cudaEventCreateWithFlags(&c->g_out, cudaEventDisableTiming));
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  // (the corner uploads above went to the context stream, which every replay waits for)
+  PDG_CUDA(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+  cudaStream_t user = c->stream;
+  c->stream = c->gstream;
+  int r = PDG_OK;
+  for (const auto& sp : sched)
+    if ((r = issue_pass(c, sp)) != PDG_OK) break;
+  c->stream = user;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
+  if (r != PDG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->gexec = nullptr;
+    return cuda_fail(c, e, "graph capture of pdg_step");
+  }
+  c->g_dt = dt;
+  c->g_nsteps = nsteps;
+  c->g_gen = c->gen;
+  return PDG_OK;
+}
+
 int pdg_step(pdg_ctx* c, double dt, int nsteps) {
   if (!c) return PDG_ERR_ARG;
   if (!c->has_state) return fail(c, PDG_ERR_STATE, "pdg_step before pdg_set_w / pdg_set_f");
   if (nsteps < 0 || !std::isfinite(dt)) return fail(c, PDG_ERR_ARG, "bad dt or nsteps");
   if (nsteps == 0) return PDG_OK;
+  const bool graph = c->use_graph && !c->timing;
+  if (graph && c->gexec && c->g_gen == c->gen && c->g_dt == dt && c->g_nsteps == nsteps) {
+    PDG_CUDA(c, cudaEventRecord(c->g_in, c->stream));
+    PDG_CUDA(c, cudaStreamWaitEvent(c->gstream, c->g_in, 0));
+    PDG_CUDA(c, cudaGraphLaunch(c->gexec, c->gstream));
+    PDG_CUDA(c, cudaEventRecord(c->g_out, c->gstream));
+    PDG_CUDA(c, cudaStreamWaitEvent(c->stream, c->g_out, 0));
+    return PDG_OK;
+  }
   std::vector<PdgPassSpec> sched;
   if (int r = build_schedule(c, dt, nsteps, sched)) return r;
+  if (graph) {
+    if (int r = capture_steps(c, dt, nsteps, sched)) return r;
+    return pdg_step(c, dt, nsteps);   // replay
+  }
   for (const auto& sp : sched)
     if (int r = issue_pass(c, sp)) return r;
   return PDG_OK;
@@ -1368,6 +1439,7 @@ int pdg_step(pdg_ctx* c, double dt, int nsteps) {
 
 int pdg_set_inflow(pdg_ctx* c, int axis, const double* fb, size_t len, int on_device) {
   if (!c) return PDG_ERR_ARG;
+  c->gen++;
   if (!c->has_model) return fail(c, PDG_ERR_STATE, "pdg_set_inflow before pdg_set_model");
   if (axis < 0 || axis >= c->dim || c->periodic[axis]) return fail(c, PDG_ERR_ARG, "axis is not an inflow axis");
   if (!fb) return fail(c, PDG_ERR_ARG, "fb is NULL");
@@ -1462,6 +1534,7 @@ int pdg_timing_read(pdg_ctx* c, long long* launches, double* ms, int max_kinds) 
 
 int pdg_set_launch(pdg_ctx* c, int kind, int lpb, int nseg, int ngroup) {
   if (!c || kind < 0 || kind > 5) return PDG_ERR_ARG;
+  c->gen++;
   if (kind == 5) {
     if (lpb == 0 && nseg == 0 && ngroup == 0) {
       c->cshape[0] = c->cshape[1] = c->cshape[2] = c->cshape[3] = 0;
@@ -1516,6 +1589,13 @@ int pdg_destroy(pdg_ctx* c) {
   if (c->kfield) cudaFree(c->kfield);
   if (c->cbuf) cudaFree(c->cbuf);
   if (c->czt) cudaFree(c->czt);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gstream) {
+    cudaStreamSynchronize(c->gstream);
+    cudaStreamDestroy(c->gstream);
+  }
+  if (c->g_in) cudaEventDestroy(c->g_in);
+  if (c->g_out) cudaEventDestroy(c->g_out);
   free_inflow(c);
   delete c;
   return PDG_OK;
@@ -1598,6 +1678,7 @@ int representative_specs(pdg_ctx* c, double dt, PdgPassSpec* sp, bool* have) {
 extern "C" {
 
 int pdg_autotune(pdg_ctx* c, double dt, int reps) {
+  if (c) c->gen++;
   if (!c) return PDG_ERR_ARG;
   if (!c->has_state) return fail(c, PDG_ERR_STATE, "pdg_autotune needs a state (pdg_set_w)");
   if (!std::isfinite(dt) || dt == 0.0 || reps < 1) return fail(c, PDG_ERR_ARG, "bad dt or reps");
@@ -1657,9 +1738,13 @@ int pdg_autotune(pdg_ctx* c, double dt, int reps) {
 
 int pdg_set_option(pdg_ctx* c, int option, int value) {
   if (!c) return PDG_ERR_ARG;
+  c->gen++;
   switch (option) {
     case PDG_OPT_COMPOSE_TT:
       c->compose = value != 0;
+      return PDG_OK;
+    case PDG_OPT_GRAPH:
+      c->use_graph = value != 0;
       return PDG_OK;
   }
   return fail(c, PDG_ERR_ARG, "unknown option");
