@@ -415,7 +415,8 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
  *     set_option / autotune call forces a new capture); the replay is ordered after the
  *     work already on the context stream, and that stream waits for it.  The same
  *     launches, bitwise the same results, fewer launch overheads for small meshes.  Plans
- *     and scratch are prepared before the capture.  Ignored while kernel timing is on.
+ *     and scratch are prepared before the capture.  Ignored while kernel timing is on;
+ *     not to be combined with a capture of the context stream by the caller.
  * Errors: PDG_ERR_ARG (unknown option).
  */
 enum { PDG_OPT_COMPOSE_TT = 1, PDG_OPT_GRAPH = 2 };
