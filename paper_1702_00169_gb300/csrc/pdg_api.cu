@@ -80,6 +80,9 @@ struct pdg_ctx {
   int g_nsteps = -1;
   unsigned long long g_gen = ~0ULL;
   cudaEvent_t g_in = nullptr, g_out = nullptr;
+  // auxiliary streams of the diagonal launches of a 3-D lattice sub-step (issue_diag)
+  cudaStream_t dstream[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t dfork = nullptr, djoin[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t czt_cap = 0;                          // its capacity (8-byte words)
   int cshape[4] = {0, 0, 0, 0};                // corner pass: threads, box x, y, z (0 = heuristic)
   double* kfield = nullptr;                    // penalisation K at every point
@@ -727,43 +730,53 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
   return PDG_OK;
 }
 
+// The diagonal launches of one sub-step (the corner pass first, then the edge planes) act
+// on disjoint populations.  With more than one, they fork from the context stream onto
+// the context's auxiliary streams and join back, so the last partial wave of one overlaps
+// the next (events only: a graph capture records them as parallel branches).  Their
+// descriptors, and the corner plans' uploads on the context stream, come before the fork.
 int issue_diag(pdg_ctx* c, const PdgPassSpec& sp) {
   Lattice L;
   if (!lattice_of(c->model.kind, &L)) return fail(c, PDG_ERR_ARG, "internal: diagonal pass of a DnQ2n model");
-  if (L.ncorner) {
-    PdgCornerPass p;
-    if (int r = make_corner(c, sp, L, &p)) return r;
+  PdgCornerPass cp;
+  PdgDiagPass dp[3];
+  if (L.ncorner)
+    if (int r = make_corner(c, sp, L, &cp)) return r;
+  for (int o = 0; o < L.norient; ++o)
+    if (int r = make_diag(c, sp, o, &dp[o])) return r;
+  const int nl = L.norient + (L.ncorner ? 1 : 0);
+  const bool fork = nl > 1;
+  if (fork) {
+    for (int i = 0; i < nl; ++i) {
+      if (!c->dstream[i]) PDG_CUDA(c, cudaStreamCreateWithFlags(&c->dstream[i], cudaStreamNonBlocking));
+      if (!c->djoin[i]) PDG_CUDA(c, cudaEventCreateWithFlags(&c->djoin[i], cudaEventDisableTiming));
+    }
+    if (!c->dfork) PDG_CUDA(c, cudaEventCreateWithFlags(&c->dfork, cudaEventDisableTiming));
+    PDG_CUDA(c, cudaEventRecord(c->dfork, c->stream));
+    for (int i = 0; i < nl; ++i) PDG_CUDA(c, cudaStreamWaitEvent(c->dstream[i], c->dfork, 0));
+  }
+  for (int i = 0; i < nl; ++i) {
+    const bool corner = L.ncorner && i == 0;
+    cudaStream_t st = fork ? c->dstream[i] : c->stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->timing) {
       e0 = get_event(c);
       e1 = get_event(c);
       if (!e0 || !e1) return fail(c, PDG_ERR_CUDA, "cudaEventCreate failed");
-      PDG_CUDA(c, cudaEventRecord(e0, c->stream));
+      PDG_CUDA(c, cudaEventRecord(e0, st));
     }
-    int e = pdg_launch_corner(p, (void*)c->stream);
-    if (e != 0) return cuda_fail(c, (cudaError_t)e, "corner_kernel launch");
+    const int e = corner ? pdg_launch_corner(cp, (void*)st) : pdg_launch_diag(dp[i - (L.ncorner ? 1 : 0)], (void*)st);
+    if (e != 0) return cuda_fail(c, (cudaError_t)e, corner ? "corner_kernel launch" : "diag_kernel launch");
     if (c->timing) {
-      PDG_CUDA(c, cudaEventRecord(e1, c->stream));
-      c->pending.push_back({4, e0, e1});
+      PDG_CUDA(c, cudaEventRecord(e1, st));
+      c->pending.push_back({corner ? 4 : 3, e0, e1});
     }
   }
-  for (int o = 0; o < L.norient; ++o) {
-    PdgDiagPass p;
-    if (int r = make_diag(c, sp, o, &p)) return r;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (c->timing) {
-      e0 = get_event(c);
-      e1 = get_event(c);
-      if (!e0 || !e1) return fail(c, PDG_ERR_CUDA, "cudaEventCreate failed");
-      PDG_CUDA(c, cudaEventRecord(e0, c->stream));
+  if (fork)
+    for (int i = 0; i < nl; ++i) {
+      PDG_CUDA(c, cudaEventRecord(c->djoin[i], c->dstream[i]));
+      PDG_CUDA(c, cudaStreamWaitEvent(c->stream, c->djoin[i], 0));
     }
-    int e = pdg_launch_diag(p, (void*)c->stream);
-    if (e != 0) return cuda_fail(c, (cudaError_t)e, "diag_kernel launch");
-    if (c->timing) {
-      PDG_CUDA(c, cudaEventRecord(e1, c->stream));
-      c->pending.push_back({3, e0, e1});
-    }
-  }
   return PDG_OK;
 }
 
@@ -1596,6 +1609,14 @@ int pdg_destroy(pdg_ctx* c) {
   }
   if (c->g_in) cudaEventDestroy(c->g_in);
   if (c->g_out) cudaEventDestroy(c->g_out);
+  for (int i = 0; i < 4; ++i) {
+    if (c->dstream[i]) {
+      cudaStreamSynchronize(c->dstream[i]);
+      cudaStreamDestroy(c->dstream[i]);
+    }
+    if (c->djoin[i]) cudaEventDestroy(c->djoin[i]);
+  }
+  if (c->dfork) cudaEventDestroy(c->dfork);
   free_inflow(c);
   delete c;
   return PDG_OK;
