@@ -193,3 +193,66 @@ def test_diagonal_launch_override_validation(pdg):
     s.set_launch(4, 0, 0, 0)
     assert s.get_launch(4) == (0, 0, 0)
     s.close()
+
+
+def test_corner_launch_override_and_options(pdg):
+    """Launch kind 5 (corner boxes) and the options, validated on the host."""
+    s = pdg.Solver(3, (2, 2, 2), (2, 2, 2), 2)
+    for bad in ((32, 8, 8), (520, 8, 8), (100, 8, 8), (256, 0, 8), (256, 8, 0)):
+        with pytest.raises(pdg.PdgError):
+            s.set_launch(5, *bad)
+    s.set_launch(5, 256, 12, 7)
+    assert s.get_launch(5) == (256, 12, 7)
+    s.set_launch(5, 0, 0, 0)
+    assert s.get_launch(5) == (0, 0, 0)
+    with pytest.raises(pdg.PdgError):
+        s.set_launch(6, 256, 8, 8)
+    s.set_option(pdg.PDG_OPT_GRAPH, 1)
+    s.set_option(pdg.PDG_OPT_GRAPH, 0)
+    s.set_option(pdg.PDG_OPT_COMPOSE_TT, 1)
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_option(99, 1)
+    assert e.value.status == pdg.PDG_ERR_ARG
+    s.close()
+
+
+def test_lattice_3d_model_checks_and_inflow_lengths(pdg):
+    """D3Q19 on an inflow mesh: accepted; its inflow data hold the five populations
+    entering through each face (2 x 5 x lines); M4^kin is refused for lattices only when
+    stepping (it needs a backward diagonal sub-step)."""
+    s = pdg.Solver(3, (2, 1, 1), (1, 2, 1), 1, periodic=(False, True, True))
+    s.set_model("isothermal_d3q19", 1.0)
+    i = s.info()
+    assert (i.m, i.nv, i.nfields) == (4, 19, 19)
+    lines = i.npoints // i.npts[0]
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_inflow(0, np.zeros(2 * 4 * lines))                 # m entries: wrong for a lattice
+    assert e.value.status == pdg.PDG_ERR_ARG
+    s.close()
+    s2 = pdg.Solver(2, (2, 2), (2, 2), 3)
+    with pytest.raises(pdg.PdgError) as e:
+        s2.set_model("isothermal_d3q27", 1.0)                     # 3-D lattices need dim = 3
+    assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
+    s2.close()
+
+
+def test_server_host_paths(pdg):
+    """Server calls that need no device: unknown ids, fault-injection arguments, lattice
+    requests refused at submission."""
+    import dataclasses
+    from paper_1702_00169_gb300 import workloads as W
+    assert pdg.pdg_debug_fail_allocs(-1) == pdg.PDG_ERR_ARG
+    assert pdg.pdg_debug_fail_allocs(0) == pdg.PDG_OK
+    srv = pdg.Server(1 << 20)
+    with pytest.raises(pdg.PdgError) as e:
+        srv.cancel(12345)
+    assert e.value.status == pdg.PDG_ERR_STATE
+    with pytest.raises(pdg.PdgError) as e:
+        srv.result(12345, 4)
+    assert e.value.status == pdg.PDG_ERR_STATE
+    cfg = dataclasses.replace(W.D2Q9_ISO, n_macro=(1, 1), n_sub=(2, 2), order=1)
+    with pytest.raises(pdg.PdgError) as e:
+        srv.submit(cfg, np.zeros(cfg.m * cfg.npoints), 2, t_arrival=0.0)
+    assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
+    assert srv.pending() == (0, 0)
+    srv.close()
