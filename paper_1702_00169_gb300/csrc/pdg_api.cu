@@ -546,8 +546,12 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, int o, PdgDiagPass* out) {
   p.sc = c->dim == 3 ? stride[az] : 0;
   p.nplane = c->dim == 3 ? c->P[az] : 1;
   p.prec = c->model.prec;
-  p.threads = c->dshape[0] ? c->dshape[0] : 512;
-  const int slots = 152;   // one block per SM per wave (co-resident blocks share its FP64 pipe)
+  // cells of at most 9 nodes (degree <= 2) carry little work between the two barriers of
+  // a wavefront step: two 256-thread blocks per SM then overlap one block's barriers with
+  // the other's FP64 work; larger cells keep one 512-thread block per SM
+  const bool small_cells = c->n * c->n <= 9;
+  p.threads = c->dshape[0] ? c->dshape[0] : (small_cells ? 256 : 512);
+  const int slots = p.threads <= 256 ? 304 : 152;   // blocks per wave
   const double NN = (double)c->n * c->n, NF = 2.0 * c->n - 1.0;
   double best = 1e300;
   if (c->dshape[0]) {
