@@ -38,7 +38,7 @@ METRIC = "kinetic DOF-updates/s"
 UNIT = "DOF-updates/s"
 
 # Algorithmic per-unit figures of the dominant kernel (the last-axis pass:
-# T(dt/2), collision, T(dt/2)); see the design doc for the derivation.
+# T(dt/2), collision, T(dt/2)), counted from the operations each step must do:
 #   bytes: every population of every point read once and written once = 16 B per DOF.
 #   flops per transported DOF per sub-step (degree d, n = d+1): E row (n FMA) + inflow
 #     term (1 FMA) + per cell the z combination (2 flops) -> 2n + 2 + 2/n flops.
