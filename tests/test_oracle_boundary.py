@@ -107,3 +107,18 @@ def test_m2_constant_equilibrium_with_matching_inflow():
     tr = S.Transporter(m, model, method="direct", fb=f0)
     f = S.run(f0, tr, model, 0.5 * m.h[0] / model.lam, 3, 2.0)
     np.testing.assert_allclose(f, f0, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind,q", [(M.ISOTHERMAL_D3Q19, 19), (M.ISOTHERMAL_D3Q15, 15), (M.ISOTHERMAL_D3Q27, 27)])
+def test_3d_lattice_constant_equilibrium_with_matching_inflow(kind, q):
+    """The 3-D lattices on a box with inflow faces on every axis: boundary data f^b =
+    f^eq(w_c) keep the constant equilibrium under M2 (edge and corner velocities included;
+    the oracle the 3-D inflow GPU tests compare with)."""
+    model = M.Model(kind, 3, 1.0)
+    m = CartesianMesh(3, (2, 2, 3), 1, periodic=(False, False, False))
+    w = np.array([1.05, 0.02, -0.01, 0.03]).reshape(4, 1, 1, 1) * np.ones(m.shape)
+    f0 = S.initial_state(model, w)
+    assert f0.shape == (1, q) + m.shape
+    tr = S.Transporter(m, model, method="direct", fb=f0)
+    f = S.run(f0, tr, model, 0.5 * min(m.h) / model.lam, 2, 2.0)
+    np.testing.assert_allclose(f, f0, rtol=1e-13, atol=1e-13)
