@@ -1,0 +1,257 @@
+"""CPU checks of the three sweep algorithms the transport kernels implement (not the kernels).
+
+Each test restates one algorithm in plain numpy, cell by cell, and compares it with the
+theta step solved as the linear system it is: the sparse LU of the eq. (3.7) matrix
+(oracle.transport.DirectTransport), which knows nothing of lines, segments, tiles or
+truncated starts.  The algorithms (Section 4.1 replaced by exact closures):
+
+* line sweep, axis-aligned velocities: per-cell update fn_c = E f_c + q (x_{c-1} + zb u_{c-1}),
+  the scalar recurrence of the last node, segment aggregates closed around the periodic ring
+  exactly (full mode) or through a window of W cells with |beta|^W <= 2^-60 (window mode),
+  and the composed double step with its 2 x 2 recurrence;
+* tile sweep, diagonal velocities of D2Q9: fn_c = B^-1 r_c - c1 f_c with the two upwind faces,
+  every tile swept from W cells upwind, starting from the old face values;
+* box sweep, corner velocities of D3Q15 / D3Q27: the same with three upwind faces.
+
+The widths used are those of the signed lattice-path bound for these Courant numbers; a
+much smaller width is shown to miss, so the check does see the truncation.
+"""
+import numpy as np
+import pytest
+
+from oracle.dg import CartesianMesh
+from oracle.transport import DirectTransport, line_K
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+# ----------------------------------------------------------------------------------------
+# line sweep (axis-aligned velocity +lambda e_x on a periodic 1-D mesh)
+
+def _line_coefs(d, nu, theta):
+    """E, q, beta, zb of the per-cell update, from the reduced cell operator
+    d/dt f_c = -(2 lambda/h)(K f_c - w0^-1 e0 f_{c-1,d}) and the theta step."""
+    K, w = line_K(d)
+    n = d + 1
+    I = np.eye(n)
+    B = I + theta * nu * K
+    E = np.linalg.solve(B, I - (1.0 - theta) * nu * K)
+    e0 = np.zeros(n)
+    e0[0] = 1.0
+    q = np.linalg.solve(B, theta * nu / w[0] * e0)
+    return E, q, q[n - 1], (1.0 - theta) / theta
+
+
+def _line_sweep(f, d, nu, theta, nseg, window):
+    """One theta sub-step of a periodic line of N cells (f: (N, n)), split into nseg segments.
+    window=None: every segment aggregates its whole length and the ring is closed exactly;
+    window=W: the inflow of a segment is the recurrence over the W cells before it."""
+    E, q, beta, zb = _line_coefs(d, nu, theta)
+    N, n = f.shape
+    a = f @ E.T                                        # E f_c
+    u_prev = np.roll(f[:, n - 1], 1)                   # old last node of the upwind cell
+    alpha = a[:, n - 1] + beta * zb * u_prev           # x_c = alpha_c + beta x_{c-1}
+    bounds = np.linspace(0, N, nseg + 1).astype(int)
+    starts, ends = bounds[:-1], bounds[1:]
+    x_in = np.zeros(nseg)                              # x_{s0-1} for each segment
+    if window is None:
+        Y = np.array([sum(beta ** (e - 1 - c) * alpha[c] for c in range(s, e)) for s, e in zip(starts, ends)])
+        P = np.array([beta ** (e - s) for s, e in zip(starts, ends)])
+        for s in range(nseg):
+            # end value of segment s-1: sum_j (prod of the later segments' beta powers) Y, / (1 - beta^N)
+            acc, gain = 0.0, 1.0
+            for j in range(nseg):
+                t = (s - 1 - j) % nseg
+                acc += gain * Y[t]
+                gain *= P[t]
+            x_in[s] = acc / (1.0 - beta ** N)
+    else:
+        for s in range(nseg):
+            x_in[s] = sum(beta ** k * alpha[(starts[s] - 1 - k) % N] for k in range(window))
+    out = np.empty_like(f)
+    for s in range(nseg):
+        x = x_in[s]
+        for c in range(starts[s], ends[s]):
+            out[c] = a[c] + q * (x + zb * u_prev[c])
+            x = out[c, n - 1]
+    return out
+
+
+def _line_composed(f, d, nu, theta, window):
+    """Two consecutive sub-steps as one sweep: gn_c = E^2 f_c + (E q) z_c + q z'_c with
+    z_c = x_{c-1} + zb u_{c-1}, z'_c = y_{c-1} + zb x_{c-1}; the last nodes X_c = (x_c, y_c)
+    obey X_c = A_c + M X_{c-1}, M = [[beta, 0], [g1 + beta zb, beta]], g1 = (E q)[d],
+    started `window` cells upwind."""
+    E, q, beta, zb = _line_coefs(d, nu, theta)
+    N, n = f.shape
+    Eq = E @ q
+    M = np.array([[beta, 0.0], [Eq[n - 1] + beta * zb, beta]])
+    a1 = f @ E.T
+    a2 = f @ (E @ E).T
+    u_prev = np.roll(f[:, n - 1], 1)
+    A = np.stack([a1[:, n - 1] + beta * zb * u_prev, a2[:, n - 1] + Eq[n - 1] * zb * u_prev], axis=1)
+    out = np.empty_like(f)
+    for c in range(N):
+        X = np.zeros(2)                                # X_{c-1} from the window
+        for k in range(window, 0, -1):
+            X = A[(c - k) % N] + M @ X
+        # X_{c-1} = (x_{c-1}, y_{c-1})
+        z = X[0] + zb * u_prev[c]
+        zp = X[1] + zb * X[0]
+        out[c] = a2[c] + Eq * z + q * zp
+    return out
+
+
+def _window(beta, tol=2.0 ** -60):
+    W = 1
+    while abs(beta) ** W > tol:
+        W += 1
+    return W
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("nu,theta", [(1.0, 0.5), (2.0, 0.5), (1.5, 0.75)])
+def test_line_segments_full_ring_and_window_equal_the_lu_solve(d, nu, theta):
+    N = 11
+    n = d + 1
+    mesh = CartesianMesh(1, (N,), d)
+    lam = 1.0
+    delta = nu * mesh.h[0] / (2.0 * lam)
+    f = np.random.default_rng(100 * d + int(4 * nu)).standard_normal(N * n)
+    ref = DirectTransport(mesh, np.array([lam]), delta, theta)(f)
+    _, _, beta, _ = _line_coefs(d, nu, theta)
+    for nseg in (1, 3, 4):
+        full = _line_sweep(f.reshape(N, n), d, nu, theta, nseg, None).reshape(-1)
+        assert _rel(full, ref) < 1e-14
+        win = _line_sweep(f.reshape(N, n), d, nu, theta, nseg, _window(beta)).reshape(-1)
+        assert _rel(win, ref) < 1e-14
+    if abs(beta) > 1e-3:                               # a one-cell window misses
+        assert _rel(_line_sweep(f.reshape(N, n), d, nu, theta, 3, 1).reshape(-1), ref) > 1e-6
+
+
+@pytest.mark.parametrize("d", [1, 3])
+@pytest.mark.parametrize("nu,theta", [(1.0, 0.5), (2.0, 0.5)])
+def test_line_composed_double_step_equals_two_lu_solves(d, nu, theta):
+    N = 9
+    n = d + 1
+    mesh = CartesianMesh(1, (N,), d)
+    delta = nu * mesh.h[0] / 2.0
+    T = DirectTransport(mesh, np.array([1.0]), delta, theta)
+    f = np.random.default_rng(7 + d).standard_normal(N * n)
+    ref = T(T(f))
+    _, _, beta, _ = _line_coefs(d, nu, theta)
+    W2 = _window(beta, 2.0 ** -62) + 8                 # the 2 x 2 recurrence decays like k beta^k
+    got = _line_composed(f.reshape(N, n), d, nu, theta, W2).reshape(-1)
+    assert _rel(got, ref) < 1e-14
+
+
+# ----------------------------------------------------------------------------------------
+# tile sweep (diagonal velocity of D2Q9) and box sweep (corner velocity of D3Q15 / D3Q27)
+
+def _cell_operator(d, nus, theta):
+    """B^-1 and k_a = nu_a / w0 of the cell system B = I + theta sum_a nu_a K_a, nodes
+    numbered with x fastest (p = (i_z n + i_y) n + i_x); axis a of the cell is numpy axis -1-a."""
+    K, w = line_K(d)
+    n = d + 1
+    D = len(nus)
+    Ksum = np.zeros((n ** D, n ** D))
+    for a in range(D):
+        factors = [np.eye(n)] * D
+        factors[D - 1 - a] = K                         # kron order: slowest axis first
+        op = factors[0]
+        for fct in factors[1:]:
+            op = np.kron(op, fct)
+        Ksum += nus[a] * op
+    Binv = np.linalg.inv(np.eye(n ** D) + theta * Ksum)
+    return Binv, [nu / w[0] for nu in nus]
+
+
+def _truncated_sweep(F, d, nus, theta, signs, tile, W):
+    """Every tile (box) of `tile` output cells is swept in upwind-to-downwind order over the
+    region that starts W cells upwind along every axis.  A cell takes r = f/theta + sum_a k_a
+    S_a (face value of its upwind neighbour along a), forms fn = B^-1 r - c1 f and passes the
+    face value theta B^-1 r on.  At the start of the region the face values come from the old
+    state (theta fn + (1-theta) f with fn = f there)."""
+    D = len(nus)
+    n = d + 1
+    Binv, k = _cell_operator(d, nus, theta)
+    c1 = (1.0 - theta) / theta
+    G = F.copy()
+    for a in range(D):                                 # traversal orientation: all signs positive
+        if signs[a] < 0:
+            G = np.flip(G, axis=D - 1 - a)
+    ncell = [G.shape[D - 1 - a] // n for a in range(D)]
+    out = np.full_like(G, np.nan)
+
+    def cell(idx):                                     # idx[a] = cell index along axis a
+        sl = tuple(slice((idx[a] % ncell[a]) * n, (idx[a] % ncell[a]) * n + n) for a in reversed(range(D)))
+        return sl
+
+    def face(vals, a):                                 # the +a face nodes of a cell array
+        sl = [slice(None)] * D
+        sl[D - 1 - a] = n - 1
+        return vals[tuple(sl)]
+
+    def inject(r, a, vals):                            # add to the -a face nodes
+        sl = [slice(None)] * D
+        sl[D - 1 - a] = 0
+        r[tuple(sl)] += vals
+
+    for t0 in np.ndindex(*[-(-ncell[a] // tile[a]) for a in range(D)]):
+        lo = [t0[a] * tile[a] for a in range(D)]
+        hi = [min(lo[a] + tile[a], ncell[a]) for a in range(D)]
+        faces = {}                                     # (cell, axis) -> new +axis face value
+        for rel in np.ndindex(*[hi[a] - lo[a] + W for a in reversed(range(D))]):
+            idx = [lo[a] - W + rel[D - 1 - a] for a in range(D)]
+            f = G[cell(idx)]
+            r = f / theta
+            for a in range(D):
+                up = list(idx)
+                up[a] -= 1
+                fv = faces.get((tuple(up), a))
+                if fv is None:                         # region start: old face value
+                    fv = face(G[cell(up)], a)
+                inject(r, a, k[a] * fv)
+            y = (Binv @ r.reshape(-1)).reshape(r.shape)
+            for a in range(D):
+                faces[(tuple(idx), a)] = theta * face(y, a)
+            if all(idx[a] >= lo[a] for a in range(D)):
+                out[cell(idx)] = y - c1 * f
+    for a in range(D):
+        if signs[a] < 0:
+            out = np.flip(out, axis=D - 1 - a)
+    return out
+
+
+def _lu_reference(dim, ncells, d, v, nus, theta):
+    lam = 1.0
+    h = tuple(2.0 * abs(v[a]) * lam * 0.5 / nus[a] for a in range(dim))   # delta = 1/2
+    mesh = CartesianMesh(dim, ncells, d, lengths=tuple(ncells[a] * h[a] for a in range(dim)))
+    return mesh, DirectTransport(mesh, lam * np.asarray(v, dtype=np.float64), 0.5, theta)
+
+
+@pytest.mark.parametrize("d,signs,nus,tile", [(1, (1, 1), (1.0, 1.0), (2, 3)), (3, (-1, 1), (1.0, 0.8), (3, 2)),
+                                              (2, (-1, -1), (0.6, 1.0), (4, 5)), (3, (1, -1), (1.0, 1.0), (1, 1))])
+def test_diagonal_tile_sweep_truncated_start_equals_the_lu_solve(d, signs, nus, tile):
+    ncells = (4, 5)
+    mesh, T = _lu_reference(2, ncells, d, signs, nus, 0.5)
+    F = np.random.default_rng(sum(ncells) + d).standard_normal(mesh.shape)
+    ref = T(F)
+    got = _truncated_sweep(F, d, nus, 0.5, signs, tile, 17)      # widths 13-17 at nu <= 1
+    assert _rel(got, ref) < 1e-14
+    assert _rel(_truncated_sweep(F, d, nus, 0.5, signs, tile, 2), ref) > 1e-6
+
+
+@pytest.mark.parametrize("d,signs,nus,tile,W", [(1, (1, 1, 1), (1.0, 1.0, 1.0), (2, 3, 2), 17),
+                                                (2, (-1, 1, -1), (1.0, 1.0, 1.0), (3, 3, 3), 16),
+                                                (1, (1, -1, -1), (0.7, 1.0, 0.9), (1, 2, 3), 17)])
+def test_corner_box_sweep_truncated_start_equals_the_lu_solve(d, signs, nus, tile, W):
+    ncells = (3, 3, 3)
+    mesh, T = _lu_reference(3, ncells, d, signs, nus, 0.5)
+    F = np.random.default_rng(3 + d).standard_normal(mesh.shape)
+    ref = T(F)
+    got = _truncated_sweep(F, d, nus, 0.5, signs, tile, W)
+    assert _rel(got, ref) < 1e-14
+    assert _rel(_truncated_sweep(F, d, nus, 0.5, signs, tile, 2), ref) > 1e-6
