@@ -538,6 +538,27 @@ int pdg_server_destroy(pdg_server* server);
 const char* pdg_server_last_error(const pdg_server* server);
 
 /*
+ * pdg_plan_sweep -- the truncated-start plan of the wavefront sweeps, for inspection and
+ * tests (host only: needs no context and no GPU).  ncomp = 2: the tile sweep of velocities
+ * with two nonzero components (D2Q9 diagonals, D3Q19 / D3Q27 edges, Section 4.1's
+ * wavefronts cut into independent tiles); ncomp = 3: the box sweep of the corner velocities
+ * of D3Q15 / D3Q27.
+ *   d       DG degree: 1..4 (ncomp 2), 1..3 (ncomp 3)
+ *   nu      ncomp Courant numbers nu_a = 2 |v_a| delta / h_a (> 0, finite), in the order of
+ *           the velocity's nonzero axes
+ *   theta   weight of the theta step, in (0, 1]
+ *   widths  receives ncomp ints: the cells every tile / box is swept from upwind along each
+ *           axis, the smallest widths whose signed lattice-path bound on the error of the
+ *           truncated start is <= 2^-57 max |f| per upwind edge
+ *   binv    NULL, or (d+1)^(2 ncomp) doubles: the inverse of the cell system
+ *           B = I + theta sum_a nu_a K_a of eq. (3.7) split by axis (K = Dm + w_0^{-1} e_0 e_0^T
+ *           acting along axis a), row-major, nodes numbered with x fastest
+ * Errors: PDG_ERR_ARG (ncomp, d, nu or theta out of range, NULL nu / widths),
+ * PDG_ERR_UNSUPPORTED (no width within the limit: 128 cells for tiles, 64 for boxes).
+ */
+int pdg_plan_sweep(int ncomp, int d, const double* nu, double theta, int* widths, double* binv);
+
+/*
  * pdg_debug_fail_allocs -- host-side fault injection for tests: the next n device
  * allocations of kinetic states (any context, this process) fail as if the device were
  * out of memory, without calling the CUDA allocator; n = 0 disarms.  The failing call

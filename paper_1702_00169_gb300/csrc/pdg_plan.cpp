@@ -18,6 +18,7 @@
 #include <cstring>
 #include <vector>
 
+#include "pdg.h"
 #include "pdg_internal.h"
 
 // Legendre P_k(x) and its derivative by the three-term recurrence.
@@ -501,4 +502,34 @@ int pdg_plan_corner(int d, double nux, double nuy, double nuz, double theta, Pdg
   pdg_split(c->ky, c->ky_f[0]);
   pdg_split(c->kz, c->kz_f[0]);
   return 0;
+}
+
+// Inspection entry point of the tile and box plans (declared in pdg.h).
+int pdg_plan_sweep(int ncomp, int d, const double* nu, double theta, int* widths, double* binv) {
+  if (!nu || !widths || (ncomp != 2 && ncomp != 3)) return PDG_ERR_ARG;
+  if (d < 1 || d + 1 > (ncomp == 2 ? PDG_MAXN : PDG_MAXN_CORNER)) return PDG_ERR_ARG;
+  if (!(theta > 0.0 && theta <= 1.0)) return PDG_ERR_ARG;
+  for (int a = 0; a < ncomp; ++a)
+    if (!(nu[a] > 0.0) || !std::isfinite(nu[a])) return PDG_ERR_ARG;
+  const int n = d + 1;
+  if (ncomp == 2) {
+    std::vector<PdgDiagCoef> c(1);
+    if (pdg_plan_diag(d, nu[0], nu[1], theta, c.data())) return PDG_ERR_UNSUPPORTED;
+    widths[0] = c[0].wx;
+    widths[1] = c[0].wy;
+    if (binv)
+      for (int i = 0; i < n * n * n * n; ++i) binv[i] = c[0].Binv[i];
+    return PDG_OK;
+  }
+  const int NN = n * n * n;
+  PdgCornerCoef c;
+  std::vector<double> b((size_t)NN * NN);
+  std::vector<float> bf((size_t)NN * NN * 2);
+  if (pdg_plan_corner(d, nu[0], nu[1], nu[2], theta, &c, b.data(), bf.data())) return PDG_ERR_UNSUPPORTED;
+  widths[0] = c.wx;
+  widths[1] = c.wy;
+  widths[2] = c.wz;
+  if (binv)
+    for (int i = 0; i < NN * NN; ++i) binv[i] = b[i];
+  return PDG_OK;
 }

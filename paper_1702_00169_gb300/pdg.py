@@ -111,6 +111,7 @@ _SIGS = {
     "pdg_server_destroy": (_I, [_P]),
     "pdg_server_last_error": (ctypes.c_char_p, [_P]),
     "pdg_debug_fail_allocs": (_I, [_I]),
+    "pdg_plan_sweep": (_I, [_I, _I, _P, _D, _P, _P]),
     "pdg_destroy": (_I, [_P]),
     "pdg_last_error": (ctypes.c_char_p, [_P]),
     "pdg_status_string": (ctypes.c_char_p, [_I]),
@@ -128,6 +129,19 @@ class PdgError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{pdg_status_string(status).decode()}: {msg}")
         self.status = status
+
+
+def plan_sweep(d, nu, theta=0.5):
+    """pdg_plan_sweep: (widths, binv) of the tile (len(nu) == 2) or box (len(nu) == 3) sweep."""
+    nu = np.ascontiguousarray(nu, dtype=np.float64)
+    nc = nu.size
+    widths = (ctypes.c_int * nc)()
+    nn = (d + 1) ** nc
+    binv = np.zeros((nn, nn))
+    st = pdg_plan_sweep(nc, d, nu.ctypes.data, theta, ctypes.addressof(widths), binv.ctypes.data)
+    if st != PDG_OK:
+        raise PdgError(st, f"pdg_plan_sweep(ncomp={nc}, d={d}, nu={nu.tolist()}, theta={theta})")
+    return list(widths), binv
 
 
 def _ptr(x, want_device):

@@ -14,8 +14,12 @@ truncated starts.  The algorithms (Section 4.1 replaced by exact closures):
 * box sweep, corner velocities of D3Q15 / D3Q27: the same with three upwind faces.
 
 The widths used are those of the signed lattice-path bound for these Courant numbers; a
-much smaller width is shown to miss, so the check does see the truncation.
+much smaller width is shown to miss, so the check does see the truncation.  The last tests
+take the cell inverse and the widths from the library's host planner (pdg_plan_sweep, no GPU)
+and run them through the same algorithm.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -170,12 +174,13 @@ def _cell_operator(d, nus, theta):
 
 def _truncated_sweep(F, d, nus, theta, signs, tile, W):
     """Every tile (box) of `tile` output cells is swept in upwind-to-downwind order over the
-    region that starts W cells upwind along every axis.  A cell takes r = f/theta + sum_a k_a
+    region that starts W[a] cells upwind along axis a (W: one int for all axes, or a list).  A cell takes r = f/theta + sum_a k_a
     S_a (face value of its upwind neighbour along a), forms fn = B^-1 r - c1 f and passes the
     face value theta B^-1 r on.  At the start of the region the face values come from the old
     state (theta fn + (1-theta) f with fn = f there)."""
     D = len(nus)
     n = d + 1
+    W = [W] * D if np.isscalar(W) else list(W)
     Binv, k = _cell_operator(d, nus, theta)
     c1 = (1.0 - theta) / theta
     G = F.copy()
@@ -203,8 +208,8 @@ def _truncated_sweep(F, d, nus, theta, signs, tile, W):
         lo = [t0[a] * tile[a] for a in range(D)]
         hi = [min(lo[a] + tile[a], ncell[a]) for a in range(D)]
         faces = {}                                     # (cell, axis) -> new +axis face value
-        for rel in np.ndindex(*[hi[a] - lo[a] + W for a in reversed(range(D))]):
-            idx = [lo[a] - W + rel[D - 1 - a] for a in range(D)]
+        for rel in np.ndindex(*[hi[a] - lo[a] + W[a] for a in reversed(range(D))]):
+            idx = [lo[a] - W[a] + rel[D - 1 - a] for a in range(D)]
             f = G[cell(idx)]
             r = f / theta
             for a in range(D):
@@ -255,3 +260,64 @@ def test_corner_box_sweep_truncated_start_equals_the_lu_solve(d, signs, nus, til
     got = _truncated_sweep(F, d, nus, 0.5, signs, tile, W)
     assert _rel(got, ref) < 1e-14
     assert _rel(_truncated_sweep(F, d, nus, 0.5, signs, tile, 2), ref) > 1e-6
+
+
+# ----------------------------------------------------------------------------------------
+# the library's host planner (pdg_plan_sweep; host code, no GPU): its cell inverse and its
+# widths, run through the algorithm above
+
+@pytest.fixture(scope="module")
+def pdg():
+    from paper_1702_00169_gb300 import build as B
+    if not os.path.exists(B.LIB):
+        B.build()
+    from paper_1702_00169_gb300 import pdg as P
+    return P
+
+
+@pytest.mark.parametrize("d,nus,theta", [(1, (1.0, 0.8), 0.5), (2, (0.6, 1.0), 0.75), (3, (2.0, 2.0), 0.5),
+                                         (4, (1.0, 1.0), 1.0), (1, (1.0, 0.7, 0.9), 0.5),
+                                         (2, (1.0, 1.0, 1.0), 0.75), (3, (0.5, 1.0, 2.0), 0.5)])
+def test_planner_cell_inverse(pdg, d, nus, theta):
+    """B^-1 of the planner = numpy's inverse of I + theta sum_a nu_a K_a (K from the oracle)."""
+    _, binv = pdg.plan_sweep(d, nus, theta)
+    ref, _ = _cell_operator(d, nus, theta)
+    assert np.max(np.abs(binv - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("d,signs,nus,theta,tile", [
+    (1, (1, -1), (1.0, 0.8), 0.5, (2, 3)), (2, (-1, -1), (2.0, 2.0), 0.5, (3, 4)),
+    (3, (1, 1), (1.0, 1.0), 0.75, (2, 2)), (4, (-1, 1), (0.6, 1.0), 1.0, (4, 5)),
+    (1, (1, -1, 1), (1.0, 0.7, 0.9), 0.5, (3, 1, 2)), (2, (-1, -1, -1), (1.0, 1.0, 1.0), 0.75, (3, 3, 3)),
+    (1, (1, 1, -1), (2.0, 2.0, 2.0), 0.5, (3, 3, 3))])
+def test_planner_widths_make_the_truncated_sweep_exact(pdg, d, signs, nus, theta, tile):
+    """The widths of the library's planner, used by the tile / box sweep above, reproduce the
+    LU solve to rounding; a third of them does not."""
+    widths, _ = pdg.plan_sweep(d, nus, theta)
+    D = len(nus)
+    ncells = (4, 5) if D == 2 else (3, 3, 3)
+    mesh, T = _lu_reference(D, ncells, d, signs, nus, theta)
+    F = np.random.default_rng(11 * d + D).standard_normal(mesh.shape)
+    ref = T(F)
+    assert _rel(_truncated_sweep(F, d, nus, theta, signs, tile, widths), ref) < 1e-14
+    assert _rel(_truncated_sweep(F, d, nus, theta, signs, tile, [w // 3 for w in widths]), ref) > 1e-12
+
+
+def test_planner_widths_and_refusals(pdg):
+    """Box widths at equal Courant numbers 1 and 2 (theta = 1/2), tile widths in 12..17 at
+    nu <= 1; refusals: boxes at nu = 4 (no width <= 64), degree and argument ranges."""
+    assert [pdg.plan_sweep(d, [1.0] * 3)[0][0] for d in (1, 2, 3)] == [17, 16, 16]
+    assert [pdg.plan_sweep(d, [2.0] * 3)[0][0] for d in (1, 2, 3)] == [27, 25, 24]
+    for d in (1, 2, 3, 4):
+        for nus in ((1.0, 1.0), (1.0, 0.8), (0.6, 1.0)):
+            assert all(12 <= w <= 17 for w in pdg.plan_sweep(d, nus)[0])
+    for args, status in [((1, [4.0] * 3), pdg.PDG_ERR_UNSUPPORTED), ((4, [1.0] * 3), pdg.PDG_ERR_ARG),
+                         ((0, [1.0, 1.0]), pdg.PDG_ERR_ARG), ((5, [1.0, 1.0]), pdg.PDG_ERR_ARG),
+                         ((1, [1.0, 0.0]), pdg.PDG_ERR_ARG), ((1, [1.0]), pdg.PDG_ERR_ARG),
+                         ((1, [1.0, -1.0]), pdg.PDG_ERR_ARG)]:
+        with pytest.raises(pdg.PdgError) as e:
+            pdg.plan_sweep(*args)
+        assert e.value.status == status
+    with pytest.raises(pdg.PdgError) as e:
+        pdg.plan_sweep(1, [1.0, 1.0], theta=0.0)
+    assert e.value.status == pdg.PDG_ERR_ARG
