@@ -1,0 +1,126 @@
+"""Mutation check of the host planner's CPU tests (no GPU).
+
+The host planner (csrc/pdg_plan.cpp: Gauss-Lobatto rule, derivative matrix, per-cell line
+coefficients, the tile and box cell inverses and their truncation widths) runs on the CPU,
+and `tests/test_abi_host.py` and `tests/test_sweep_algorithms.py` check what it returns
+through the C ABI.  Each case plants one plausible mistake in a copy of pdg_plan.cpp,
+compiles that copy, links it with the library's other objects into a private library, and
+runs those two test files against it; the case passes when they fail (pytest exit 1).  The
+unmodified copy, linked the same way, must pass them first.  Nothing of the repository's
+own library or sources is modified.
+
+What these CPU tests cannot see (the window lengths of the line recurrences, the ratio
+(1-theta)/theta, the composed-step coefficients: values that only reach the kernels) is
+covered by the GPU parity tests instead, and is not planted here.
+"""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PKG = "paper_1702_00169_gb300"
+PINS = ["test_abi_host.py", "test_sweep_algorithms.py"]
+
+# (id, text, replacement), the text occurring once in pdg_plan.cpp
+MUTATIONS = [
+    ("legendre_recurrence_denominator", "(j - 1.0) * p0) / j;", "(j - 1.0) * p0) / (j + 1.0);"),
+    ("gl_weight_square_dropped", "w[j] = 2.0 / (d * (d + 1.0) * p * p);", "w[j] = 2.0 / (d * (d + 1.0) * p);"),
+    ("gl_nodes_reversed", "x[j] = -s; x[d - j] = s;", "x[j] = s; x[d - j] = -s;"),
+    ("derivative_matrix_transposed", "Dm[j * n + i] = v;", "Dm[i * n + j] = v;"),
+    ("line_lifting_at_wrong_end", "K[0] += 1.0 / w[0];\n  // A = B", "K[n * n - 1] += 1.0 / w[0];\n  // A = B"),
+    ("line_explicit_weight", "R[r * k + j] = id - (1.0 - theta) * nu * K[r * n + j];",
+     "R[r * k + j] = id - theta * nu * K[r * n + j];"),
+    ("line_inflow_theta_dropped", "R[r * k + n] = (r == 0) ? theta * nu / w[0] : 0.0;",
+     "R[r * k + n] = (r == 0) ? nu / w[0] : 0.0;"),
+    ("tile_courant_numbers_swapped", "if (iy == jy) k2 += nux * K[ix * n + jx];",
+     "if (iy == jy) k2 += nuy * K[ix * n + jx];"),
+    ("box_z_courant_number", "if (iy == jy && ix == jx) k3 += nuz * K[iz * n + jz];",
+     "if (iy == jy && ix == jx) k3 += nuy * K[iz * n + jz];"),
+    ("tile_width_tolerance", "const double tol = std::ldexp(1.0, -57);\n  for (int W = 1; W <= 128",
+     "const double tol = std::ldexp(1.0, -27);\n  for (int W = 1; W <= 128"),
+    ("box_width_tolerance", "const double tol = std::ldexp(1.0, -57);\n  // acc",
+     "const double tol = std::ldexp(1.0, -27);\n  // acc"),
+    ("box_width_cubic_shortcut_always", "const bool cubic = nux == nuy && nuy == nuz;", "const bool cubic = true;"),
+    ("tile_width_edge_roles", "const double* X = edge == 0 ? A : B;", "const double* X = A;"),
+]
+
+
+def _objects(B):
+    objs = [os.path.join(B.OBJDIR, f) for f in sorted(os.listdir(B.OBJDIR)) if f.endswith(".o")]
+    return [o for o in objs if os.path.basename(o) != "pdg_plan.o"]
+
+
+def _prepare(dst):
+    for sub in ("oracle", "include"):
+        shutil.copytree(os.path.join(ROOT, sub), os.path.join(dst, sub), ignore=shutil.ignore_patterns("__pycache__"))
+    os.makedirs(os.path.join(dst, PKG, "lib"))
+    for f in ("__init__.py", "pdg.py", "build.py", "workloads.py"):
+        shutil.copy(os.path.join(ROOT, PKG, f), os.path.join(dst, PKG, f))
+    os.makedirs(os.path.join(dst, "tests"))
+    for f in ["conftest.py", "golden_util.py"] + PINS:
+        shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(dst, "tests", "golden"))
+
+
+def _build_and_test(B, dst, src_text):
+    src = os.path.join(dst, "pdg_plan.cpp")
+    with open(src, "w") as fh:
+        fh.write(src_text)
+    obj = os.path.join(dst, "pdg_plan.o")
+    inc = ["-I", B.CSRC]                              # pdg_internal.h beside the original
+    r = subprocess.run([B.nvcc()] + B.COMMON + inc + ["-x", "c++", "-c", src, "-o", obj],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        return "compile", r.stderr[-1500:]
+    lib = os.path.join(dst, PKG, "lib", "libpdg.so")
+    r = subprocess.run([B.nvcc()] + B.ARCH + ["-shared", "-o", lib] + _objects(B) + [obj] +
+                       ["-lcudart_static", "-lrt", "-lpthread", "-ldl"], capture_output=True, text=True)
+    if r.returncode != 0:
+        return "link", r.stderr[-1500:]
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1", PYTHONPATH=dst)
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
+    cmd += [os.path.join("tests", f) for f in PINS]
+    r = subprocess.run(cmd, cwd=dst, env=env, capture_output=True, text=True, timeout=900)
+    shutil.rmtree(os.path.join(dst, PKG, "lib"))      # about 55 MB each
+    return r.returncode, (r.stdout + r.stderr)[-1500:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    from paper_1702_00169_gb300 import build as B
+    if not os.path.exists(B.LIB) or not os.path.isdir(B.OBJDIR) or len(_objects(B)) < 10:
+        B.build()
+    with open(os.path.join(B.CSRC, "pdg_plan.cpp")) as fh:
+        original = fh.read()
+    base = str(tmp_path_factory.mktemp("planner_mutants"))
+
+    def job(case):
+        name, old, new = case
+        dst = os.path.join(base, name)
+        _prepare(dst)
+        if case[0] == "_unmodified":
+            return name, _build_and_test(B, dst, original)
+        count = original.count(old)
+        if count != 1:
+            return name, ("text", count)
+        return name, _build_and_test(B, dst, original.replace(old, new))
+
+    cases = [("_unmodified", "", "")] + MUTATIONS
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        return dict(ex.map(job, cases))
+
+
+def test_unmodified_planner_passes(outcomes):
+    rc, tail = outcomes["_unmodified"]
+    assert rc == 0, tail
+
+
+@pytest.mark.parametrize("case", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_planner_mistake_is_caught(outcomes, case):
+    rc, tail = outcomes[case[0]]
+    assert rc != "text", f"the text to mutate occurs {tail} times in pdg_plan.cpp"
+    assert rc == 1, f"planted mistake not caught ({rc}):\n{tail}"

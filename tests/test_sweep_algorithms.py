@@ -303,6 +303,23 @@ def test_planner_widths_make_the_truncated_sweep_exact(pdg, d, signs, nus, theta
     assert _rel(_truncated_sweep(F, d, nus, theta, signs, tile, [w // 3 for w in widths]), ref) > 1e-12
 
 
+def test_planner_widths_follow_a_permutation_of_the_axes(pdg):
+    """The cell problem is symmetric under a permutation of the axes (with its Courant
+    numbers), so the widths are permuted with them: boxes for all six permutations, tiles
+    for the swap."""
+    import itertools
+    for d in (1, 2):
+        for nus in ((1.0, 0.7, 0.9), (0.5, 1.0, 2.0)):
+            base = pdg.plan_sweep(d, list(nus))[0]
+            assert len(set(base)) > 1
+            for perm in itertools.permutations(range(3)):
+                assert pdg.plan_sweep(d, [nus[p] for p in perm])[0] == [base[p] for p in perm]
+    for d in (1, 2, 3, 4):
+        for nus in ((1.0, 0.6), (2.0, 1.3)):
+            a = pdg.plan_sweep(d, list(nus))[0]
+            assert a != a[::-1] and pdg.plan_sweep(d, list(nus[::-1]))[0] == a[::-1]
+
+
 def test_planner_widths_and_refusals(pdg):
     """Box widths at equal Courant numbers 1 and 2 (theta = 1/2), tile widths in 12..17 at
     nu <= 1; refusals: boxes at nu = 4 (no width <= 64), degree and argument ranges."""
