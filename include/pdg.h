@@ -538,6 +538,30 @@ int pdg_server_destroy(pdg_server* server);
 const char* pdg_server_last_error(const pdg_server* server);
 
 /*
+ * pdg_plan_line -- the line plan of an axis-aligned velocity, for inspection and tests (host
+ * only: needs no context and no GPU).  With the line reduction of eq. (3.7) and the theta
+ * step of eq. (3.11), for degree d, Courant number nu = 2 lambda delta / h and weight theta,
+ * the update of cell c is
+ *     fn_c = E f_c + q (za x_{c-1} + zb u_{c-1}),
+ * x and u the new and old values of the last node of the upwind cell, and the last node
+ * obeys the recurrence x_c = alpha_c + beta x_{c-1}.
+ *   d        1..4
+ *   nu       finite (negative for delta < 0)
+ *   theta    in [0, 1]
+ *   E        NULL or n*n doubles (n = d + 1), row-major: B^{-1}(I - (1-theta) nu K),
+ *            B = I + theta nu K, K = Dm + w_0^{-1} e_0 e_0^T
+ *   q        NULL or n doubles: the inflow vector
+ *   scalars  NULL or 4 doubles: beta, za, zb, and gamma1, the coupling of the composed double
+ *            step (its second last-node value gains gamma1 x_{c-1}; gamma1 = (E q)_d za + q_d zb)
+ *   windows  NULL or 2 ints: W, the window of the recurrence in its stable direction
+ *            (|r|^W <= 2^-60 with r = beta, or 1/beta when |beta| > 1; 1 when beta = 0), and
+ *            W2, that of the composed double step (|beta|^W2 <= 2^-60 and
+ *            W2 |gamma1| |beta|^(W2-1) <= 2^-60; 0 when |beta| >= 1, where it is not composed)
+ * Errors: PDG_ERR_ARG (d, nu or theta out of range, or a singular cell system).
+ */
+int pdg_plan_line(int d, double nu, double theta, double* E, double* q, double* scalars, int* windows);
+
+/*
  * pdg_plan_sweep -- the truncated-start plan of the wavefront sweeps, for inspection and
  * tests (host only: needs no context and no GPU).  ncomp = 2: the tile sweep of velocities
  * with two nonzero components (D2Q9 diagonals, D3Q19 / D3Q27 edges, Section 4.1's

@@ -504,6 +504,30 @@ int pdg_plan_corner(int d, double nux, double nuy, double nuz, double theta, Pdg
   return 0;
 }
 
+// Inspection entry point of the line plan (declared in pdg.h).
+int pdg_plan_line(int d, double nu, double theta, double* E, double* q, double* scalars, int* windows) {
+  if (d < 1 || d + 1 > PDG_MAXN || !(theta >= 0.0 && theta <= 1.0) || !std::isfinite(nu)) return PDG_ERR_ARG;
+  PdgCoef c;
+  if (pdg_plan_coef(d, nu, theta, &c)) return PDG_ERR_ARG;
+  const int n = d + 1;
+  const int W2 = pdg_plan_compose(n, &c);
+  if (E)
+    for (int i = 0; i < n * n; ++i) E[i] = c.E[i];
+  if (q)
+    for (int i = 0; i < n; ++i) q[i] = c.q[i];
+  if (scalars) {
+    scalars[0] = c.beta;
+    scalars[1] = c.za;
+    scalars[2] = c.zb;
+    scalars[3] = c.gamma1;
+  }
+  if (windows) {
+    windows[0] = pdg_plan_window(std::fabs(c.beta) > 1.0 ? 1.0 / c.beta : c.beta);
+    windows[1] = W2;
+  }
+  return PDG_OK;
+}
+
 // Inspection entry point of the tile and box plans (declared in pdg.h).
 int pdg_plan_sweep(int ncomp, int d, const double* nu, double theta, int* widths, double* binv) {
   if (!nu || !widths || (ncomp != 2 && ncomp != 3)) return PDG_ERR_ARG;

@@ -112,6 +112,7 @@ _SIGS = {
     "pdg_server_last_error": (ctypes.c_char_p, [_P]),
     "pdg_debug_fail_allocs": (_I, [_I]),
     "pdg_plan_sweep": (_I, [_I, _I, _P, _D, _P, _P]),
+    "pdg_plan_line": (_I, [_I, _D, _D, _P, _P, _P, _P]),
     "pdg_destroy": (_I, [_P]),
     "pdg_last_error": (ctypes.c_char_p, [_P]),
     "pdg_status_string": (ctypes.c_char_p, [_I]),
@@ -129,6 +130,19 @@ class PdgError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{pdg_status_string(status).decode()}: {msg}")
         self.status = status
+
+
+def plan_line(d, nu, theta=0.5):
+    """pdg_plan_line: dict with E, q, beta, za, zb, gamma1, W, W2 of the line plan."""
+    n = d + 1
+    E = np.zeros((n, n))
+    q = np.zeros(n)
+    sc = np.zeros(4)
+    win = (ctypes.c_int * 2)()
+    st = pdg_plan_line(d, nu, theta, E.ctypes.data, q.ctypes.data, sc.ctypes.data, ctypes.addressof(win))
+    if st != PDG_OK:
+        raise PdgError(st, f"pdg_plan_line(d={d}, nu={nu}, theta={theta})")
+    return {"E": E, "q": q, "beta": sc[0], "za": sc[1], "zb": sc[2], "gamma1": sc[3], "W": win[0], "W2": win[1]}
 
 
 def plan_sweep(d, nu, theta=0.5):

@@ -9,8 +9,9 @@ runs those two test files against it; the case passes when they fail (pytest exi
 unmodified copy, linked the same way, must pass them first.  Nothing of the repository's
 own library or sources is modified.
 
-What these CPU tests cannot see (the window lengths of the line recurrences, the ratio
-(1-theta)/theta, the composed-step coefficients: values that only reach the kernels) is
+The line plan (coefficients, ratio (1-theta)/theta, windows, composed-step coupling) is
+visible through pdg_plan_line and the tile / box plans through pdg_plan_sweep.  What only
+the kernels see (the squared matrix E^2 of the composed step, the float-pair splits) is
 covered by the GPU parity tests instead, and is not planted here.
 """
 import os
@@ -46,6 +47,13 @@ MUTATIONS = [
      "const double tol = std::ldexp(1.0, -27);\n  // acc"),
     ("box_width_cubic_shortcut_always", "const bool cubic = nux == nuy && nuy == nuz;", "const bool cubic = true;"),
     ("tile_width_edge_roles", "const double* X = edge == 0 ? A : B;", "const double* X = A;"),
+    ("line_ratio_inverted", "c->zb = (1.0 - theta) / theta;", "c->zb = theta / (1.0 - theta);"),
+    ("line_window_tolerance", "std::ceil(-60.0 * std::log(2.0) / std::log(a))",
+     "std::ceil(-30.0 * std::log(2.0) / std::log(a))"),
+    ("composed_coupling_term_dropped", "c->gamma1 = c->Eq[n - 1] * c->za + c->q[n - 1] * c->zb;",
+     "c->gamma1 = c->Eq[n - 1] * c->za;"),
+    ("composed_window_ignores_coupling", "if (bK <= tol && (double)K * g * bk <= tol) return K;",
+     "if (bK <= tol) return K;"),
 ]
 
 

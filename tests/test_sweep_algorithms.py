@@ -338,3 +338,57 @@ def test_planner_widths_and_refusals(pdg):
     with pytest.raises(pdg.PdgError) as e:
         pdg.plan_sweep(1, [1.0, 1.0], theta=0.0)
     assert e.value.status == pdg.PDG_ERR_ARG
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("nu,theta", [(1.0, 0.5), (2.0, 0.5), (1.5, 0.75), (1.0, 1.0), (-0.7, 0.5), (0.4, 0.0)])
+def test_planner_line_plan(pdg, d, nu, theta):
+    """E, q, beta, za, zb and gamma1 of the library's line plan = the numpy derivation; the
+    windows are the smallest that meet their 2^-60 rules."""
+    r = pdg.plan_line(d, nu, theta)
+    n = d + 1
+    K, w = line_K(d)
+    if theta > 0:
+        E, q, beta, zb = _line_coefs(d, nu, theta)
+        za = 1.0
+    else:                                              # explicit step: inflow from the old value only
+        E, q = np.eye(n) - nu * K, np.eye(n)[0] * nu / w[0]
+        beta, za, zb = 0.0, 0.0, 1.0
+    # backward steps (nu < 0) make B ill-conditioned: both sides round differently there
+    atol = (1e-14 if nu > 0 else 1e-12) * max(1.0, np.max(np.abs(E)))
+    np.testing.assert_allclose(r["E"], E, rtol=0, atol=atol)
+    np.testing.assert_allclose(r["q"], q, rtol=0, atol=atol)
+    assert abs(r["beta"] - beta) <= atol
+    assert (r["za"], r["zb"]) == (za, pytest.approx(zb, rel=1e-15))
+    g1 = (E @ q)[n - 1] * za + q[n - 1] * zb
+    assert abs(r["gamma1"] - g1) <= 10 * atol * max(1.0, abs(g1))
+    tol = 2.0 ** -60
+    rr = abs(1.0 / beta) if abs(beta) > 1.0 else abs(beta)
+    W = r["W"]
+    assert rr ** W <= tol and (W == 1 or rr ** (W - 1) > tol)
+
+    def ok2(k):
+        return abs(beta) ** k <= tol and k * abs(g1) * abs(beta) ** (k - 1) <= tol
+    if abs(beta) >= 1.0:
+        assert r["W2"] == 0
+    elif beta == 0.0:
+        assert r["W2"] in (1, 2)
+    else:
+        assert ok2(r["W2"]) and not ok2(r["W2"] - 1)
+
+
+@pytest.mark.parametrize("d", [1, 3, 4])
+@pytest.mark.parametrize("nu,theta", [(1.0, 0.5), (2.0, 0.5), (1.0, 1.0)])
+def test_planner_line_windows_make_the_sweep_exact(pdg, d, nu, theta):
+    """The library's windows W (single step, 3 segments) and W2 (composed double step), used
+    by the line algorithms above, reproduce the LU solves to rounding."""
+    N = 9
+    n = d + 1
+    mesh = CartesianMesh(1, (N,), d)
+    T = DirectTransport(mesh, np.array([1.0]), nu * mesh.h[0] / 2.0, theta)
+    f = np.random.default_rng(31 + d).standard_normal(N * n)
+    r = pdg.plan_line(d, nu, theta)
+    one = _line_sweep(f.reshape(N, n), d, nu, theta, 3, r["W"]).reshape(-1)
+    assert _rel(one, T(f)) < 1e-14
+    two = _line_composed(f.reshape(N, n), d, nu, theta, r["W2"]).reshape(-1)
+    assert _rel(two, T(T(f))) < 1e-14
