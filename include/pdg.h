@@ -349,6 +349,28 @@ int pdg_get_info(const pdg_ctx* ctx, pdg_info* info);
 int pdg_get_line_coefs(const pdg_ctx* ctx, int axis, double delta, double* E, double* q, double* beta);
 
 /*
+ * pdg_get_schedule -- the pass list pdg_step(ctx, dt, nsteps) would issue, for inspection
+ * and tests (host only: builds the list and launches nothing; needs a model, no state).
+ * Section 3.2's compositions (M2, the collapsed form of Section 5.1, M2^kin, M4^kin) are
+ * issued as passes over the axes: transports of different populations commute, so the
+ * transports of each axis between two collisions are grouped into line passes, and the
+ * collision is fused in the pass of the last axis.  Pass i is written as 8 ints at
+ * ints[8 i] and 10 doubles at dbls[10 i]:
+ *   ints   kind (0 line pass, 1 diagonal sub-step: the tile / box launches of every
+ *          velocity with several nonzero components, 2 copy of those populations back to
+ *          their home slots), axis (line pass; -1 / -2 otherwise), nops and op[4] (line pass:
+ *          1 = transport T, 2 = collision C, in order), slot (line pass: where the collision
+ *          reads the diagonal populations; diagonal sub-step: the slot set it reads)
+ *   dbls   per op o of a line pass, 2 o and 2 o + 1: E[0][0] and beta of the transport's line
+ *          plan (as pdg_plan_line returns them for its sub-step; 0 for C); 8: the sub-step of a
+ *          diagonal sub-step; 9: the sub-step of the source stages around a collision (0: none)
+ *   npasses receives the number of passes.  ints = dbls = NULL queries the count only.
+ * Errors: PDG_ERR_STATE (no model), PDG_ERR_ARG (NULL npasses, nsteps < 0, dt not finite,
+ * max_passes below the count, a singular step), PDG_ERR_UNSUPPORTED (as pdg_step).
+ */
+int pdg_get_schedule(pdg_ctx* ctx, double dt, int nsteps, int* ints, double* dbls, int max_passes, int* npasses);
+
+/*
  * pdg_get_w_noalloc -- pdg_get_w into HOST memory without allocating device memory.
  * The paper has no counterpart: this entry point exists for callers that cannot let
  * the library call cudaMalloc (a pooled or custom allocator owns the device budget,

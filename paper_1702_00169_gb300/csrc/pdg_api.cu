@@ -1516,6 +1516,43 @@ int pdg_get_line_coefs(const pdg_ctx* c, int axis, double delta, double* E, doub
   return PDG_OK;
 }
 
+int pdg_get_schedule(pdg_ctx* c, double dt, int nsteps, int* ints, double* dbls, int max_passes, int* npasses) {
+  if (!c || !npasses || nsteps < 0 || max_passes < 0 || !std::isfinite(dt)) return PDG_ERR_ARG;
+  if (!c->has_model) return PDG_ERR_STATE;
+  std::vector<PdgPassSpec> sched;
+  if (int r = build_schedule(c, dt, nsteps, sched)) return r;
+  *npasses = (int)sched.size();
+  if (!ints && !dbls) return PDG_OK;
+  if (!ints || !dbls || (int)sched.size() > max_passes) return PDG_ERR_ARG;
+  static_assert(PDG_MAXOPS <= 4, "four operation slots per pass");
+  for (size_t i = 0; i < sched.size(); ++i) {
+    const PdgPassSpec& sp = sched[i];
+    int* I = ints + 8 * i;
+    double* X = dbls + 10 * i;
+    for (int k = 0; k < 8; ++k) I[k] = 0;
+    for (int k = 0; k < 10; ++k) X[k] = 0.0;
+    I[0] = sp.axis >= 0 ? 0 : (sp.axis == -1 ? 1 : 2);
+    I[1] = sp.axis;
+    if (sp.axis >= 0) {
+      I[2] = sp.nops;
+      for (int o = 0; o < sp.nops; ++o) {
+        I[3 + o] = sp.op[o];
+        if (sp.op[o] == PDG_OP_T) {
+          const PdgCoef& cf = sp.cs[sp.opcoef[o]];
+          X[2 * o] = cf.E[0];
+          X[2 * o + 1] = cf.beta;
+        }
+      }
+      I[7] = sp.dslot;
+      X[9] = sp.sdelta;
+    } else if (sp.axis == -1) {
+      I[7] = sp.dslot_in;
+      X[8] = sp.ddelta;
+    }
+  }
+  return PDG_OK;
+}
+
 int pdg_synchronize(pdg_ctx* c) {
   if (!c) return PDG_ERR_ARG;
   PDG_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -85,6 +85,7 @@ _SIGS = {
     "pdg_set_inflow": (_I, [_P, _I, _P, _SZ, _I]),
     "pdg_get_info": (_I, [_P, ctypes.POINTER(pdg_info)]),
     "pdg_get_line_coefs": (_I, [_P, _I, _D, _P, _P, _P]),
+    "pdg_get_schedule": (_I, [_P, _D, _I, _P, _P, _I, _P]),
     "pdg_get_w_noalloc": (_I, [_P, _P, _SZ]),
     "pdg_synchronize": (_I, [_P]),
     "pdg_timing_enable": (_I, [_P, _I]),
@@ -282,6 +283,25 @@ class Solver:
         self._check(pdg_get_line_coefs(self.ctx, axis, delta, E.ctypes.data, q.ctypes.data, b.ctypes.data),
                     "pdg_get_line_coefs")
         return E.reshape(n, n), q, float(b[0])
+
+    def schedule(self, dt, nsteps):
+        """pdg_get_schedule: list of passes, each a dict (kind, axis, ops, fingerprints of the
+        transports' line plans as (E00, beta), slot, diagonal sub-step, source sub-step)."""
+        cnt = ctypes.c_int(0)
+        self._check(pdg_get_schedule(self.ctx, dt, nsteps, None, None, 0, ctypes.byref(cnt)), "pdg_get_schedule")
+        n = cnt.value
+        ints = np.zeros(8 * max(n, 1), dtype=np.int32)
+        dbls = np.zeros(10 * max(n, 1))
+        self._check(pdg_get_schedule(self.ctx, dt, nsteps, ints.ctypes.data, dbls.ctypes.data, n,
+                                     ctypes.byref(cnt)), "pdg_get_schedule")
+        out = []
+        for i in range(n):
+            I, X = ints[8 * i:8 * i + 8], dbls[10 * i:10 * i + 10]
+            nops = int(I[2])
+            out.append({"kind": int(I[0]), "axis": int(I[1]), "ops": [int(v) for v in I[3:3 + nops]],
+                        "plans": [(float(X[2 * o]), float(X[2 * o + 1])) for o in range(nops)],
+                        "slot": int(I[7]), "ddelta": float(X[8]), "sdelta": float(X[9])})
+        return out
 
     def synchronize(self):
         self._check(pdg_synchronize(self.ctx), "pdg_synchronize")
