@@ -2,8 +2,6 @@
 configuration bench.py times (autotuned shapes), against the oracle where it can
 follow (a few steps through the per-line Bloch solver) and through properties that
 hold at any size otherwise.  The two precisions are both checked."""
-import dataclasses
-
 import numpy as np
 import pytest
 

@@ -1,6 +1,4 @@
 """Pins of oracle.quadrature (Section 3.1: GL points, weights, nodal basis)."""
-import math
-
 import numpy as np
 import pytest
 
