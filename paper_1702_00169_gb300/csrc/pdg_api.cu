@@ -1923,9 +1923,6 @@ int batch_prepare(pdg_batch* b, const double* dt, const int* nsteps) {
     if (nsteps[i] < 0 || !std::isfinite(dt[i])) return bfail(b, PDG_ERR_ARG, "bad dt or nsteps");
     std::vector<PdgPassSpec> sched;
     if (int r = build_schedule(c, dt[i], nsteps[i], sched)) return bfail(b, r, c->err);
-    int prev_kind = -1, prev_nops = -1, prev_idx = -1;
-    const PdgCoef* prev_cs = nullptr;
-    (void)prev_cs;
     for (const auto& sp : sched) {
       const int kind = pass_kind(sp);
       PdgPass p;
@@ -1943,13 +1940,7 @@ int batch_prepare(pdg_batch* b, const double* dt, const int* nsteps) {
       }
       plist[i].push_back(idx);
       pblocks[i].push_back((p.nlines + p.lpb - 1) / p.lpb);
-      prev_kind = kind;
-      prev_nops = sp.nops;
-      prev_idx = idx;
     }
-    (void)prev_kind;
-    (void)prev_nops;
-    (void)prev_idx;
   }
   size_t nst = 0;
   for (int i = 0; i < n; ++i) nst = std::max(nst, plist[i].size());
