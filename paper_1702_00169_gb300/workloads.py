@@ -20,7 +20,8 @@ synthetic and drawn from ``numpy.random.default_rng(seed)``):
   E = p/(gamma-1) + rho |u|^2 / 2.
 * isothermal D2Q9 (the model of the paper's Euler-with-gravity test, without the
   source): rho = 1 + 0.05 F_rho, u_a = 0.05 F_a with independent fields built like
-  F above; w = (rho, rho u_x, rho u_y); lambda = 1 (sound speed 1/sqrt(3), Mach <= 0.09).
+  F above; w = (rho, rho u_x, rho u_y); lambda = 1 (sound speed 1/sqrt(3); Mach number at
+  most 0.05 sqrt(3 D) max|F_a|, about 0.1 on the workload grids).
 * isothermal D3Q19, D3Q15, D3Q27 (the lattices of the paper's 3-D scaling runs): the
   same recipe in 3-D (|k|_inf <= 2), w = (rho, rho u).
 """
