@@ -280,8 +280,13 @@ int pdg_set_source(pdg_ctx* ctx, const pdg_source_desc* desc);
  * points); the first step that needs a larger one allocates it with cudaMalloc (after a
  * cudaFree of the old one, which waits for the device), so issue a first step before
  * any stream capture.
- * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_CUDA,
- *         PDG_ERR_UNSUPPORTED.
+ * Host memory: the call first builds its pass list on the host, about 2.3 KB per pass
+ * (D passes per step for M2 and the collapsed form, about 2D for M2^kin and 6D for M4^kin,
+ * plus one per diagonal sub-step of the lattices); a list that cannot be allocated fails
+ * the call with PDG_ERR_OOM before anything is issued.  Split runs of millions of steps into
+ * several calls (with PDG_SCHEME_M2_COLLAPSED each call is its own collapsed run).
+ * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_OOM,
+ *         PDG_ERR_CUDA, PDG_ERR_UNSUPPORTED.
  */
 int pdg_step(pdg_ctx* ctx, double dt, int nsteps);
 
@@ -366,7 +371,8 @@ int pdg_get_line_coefs(const pdg_ctx* ctx, int axis, double delta, double* E, do
  *          diagonal sub-step; 9: the sub-step of the source stages around a collision (0: none)
  *   npasses receives the number of passes.  ints = dbls = NULL queries the count only.
  * Errors: PDG_ERR_STATE (no model), PDG_ERR_ARG (NULL npasses, nsteps < 0, dt not finite,
- * max_passes below the count, a singular step), PDG_ERR_UNSUPPORTED (as pdg_step).
+ * max_passes below the count, a singular step), PDG_ERR_OOM (no host memory for the list, as
+ * pdg_step), PDG_ERR_UNSUPPORTED (as pdg_step).
  */
 int pdg_get_schedule(pdg_ctx* ctx, double dt, int nsteps, int* ints, double* dbls, int max_passes, int* npasses);
 

@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -839,6 +840,7 @@ int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSp
   out.clear();
   if (nsteps <= 0) return PDG_OK;
   const int D = c->dim, L = D - 1;
+  out.reserve((2 * (size_t)nsteps + 1) * (size_t)D);   // at least the passes of every scheme
   PdgCoef half[3], full[3];
   for (int a = 0; a < D; ++a) {
     if (plan_line_coef(c, a, 0.5 * dt, &half[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
@@ -994,13 +996,34 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
   std::vector<PdgPassSpec> part;
   c->scheme = PDG_SCHEME_M2KIN;
   int r = PDG_OK;
-  for (int s = 0; s < nsteps && r == PDG_OK; ++s)
-    for (double g : {g1, g2, g1}) {
-      if ((r = build_schedule_one(c, g * dt, 1, part)) != PDG_OK) break;
-      out.insert(out.end(), part.begin(), part.end());
-    }
+  try {
+    out.reserve(3 * (size_t)nsteps * 3 * (size_t)c->dim);
+    for (int s = 0; s < nsteps && r == PDG_OK; ++s)
+      for (double g : {g1, g2, g1}) {
+        if ((r = build_schedule_one(c, g * dt, 1, part)) != PDG_OK) break;
+        out.insert(out.end(), part.begin(), part.end());
+      }
+  } catch (...) {
+    c->scheme = PDG_SCHEME_M4KIN;
+    throw;
+  }
   c->scheme = PDG_SCHEME_M4KIN;
   return r;
+}
+
+// build_schedule for the C entry points: the pass list lives in host memory (about 2.3 KB
+// per pass, a few passes per step), and a failed allocation is reported as PDG_ERR_OOM
+// instead of letting the exception cross the C ABI.
+int build_schedule_checked(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+  try {
+    return build_schedule(c, dt, nsteps, out);
+  } catch (const std::bad_alloc&) {
+    std::vector<PdgPassSpec>().swap(out);
+    return fail(c, PDG_ERR_OOM, "no host memory for the pass list of this many steps: split the call");
+  } catch (const std::length_error&) {
+    std::vector<PdgPassSpec>().swap(out);
+    return fail(c, PDG_ERR_OOM, "no host memory for the pass list of this many steps: split the call");
+  }
 }
 
 // State slots of the current model (D2Q9: nine populations and four scratch slots).
@@ -1444,7 +1467,7 @@ int pdg_step(pdg_ctx* c, double dt, int nsteps) {
     return PDG_OK;
   }
   std::vector<PdgPassSpec> sched;
-  if (int r = build_schedule(c, dt, nsteps, sched)) return r;
+  if (int r = build_schedule_checked(c, dt, nsteps, sched)) return r;
   if (graph) {
     if (int r = capture_steps(c, dt, nsteps, sched)) return r;
     return pdg_step(c, dt, nsteps);   // replay
@@ -1520,7 +1543,8 @@ int pdg_get_schedule(pdg_ctx* c, double dt, int nsteps, int* ints, double* dbls,
   if (!c || !npasses || nsteps < 0 || max_passes < 0 || !std::isfinite(dt)) return PDG_ERR_ARG;
   if (!c->has_model) return PDG_ERR_STATE;
   std::vector<PdgPassSpec> sched;
-  if (int r = build_schedule(c, dt, nsteps, sched)) return r;
+  if (int r = build_schedule_checked(c, dt, nsteps, sched)) return r;
+  if (sched.size() > (size_t)0x7fffffff) return fail(c, PDG_ERR_ARG, "more passes than an int counts");
   *npasses = (int)sched.size();
   if (!ints && !dbls) return PDG_OK;
   if (!ints || !dbls || (int)sched.size() > max_passes) return PDG_ERR_ARG;
@@ -1721,7 +1745,7 @@ int time_launches(pdg_ctx* c, int reps, LaunchFn fn, float* ms) {
 // Representative pass specs of kind 0 and 1 for time step dt.
 int representative_specs(pdg_ctx* c, double dt, PdgPassSpec* sp, bool* have) {
   std::vector<PdgPassSpec> sched;
-  if (int r = build_schedule(c, dt, 2, sched)) return r;
+  if (int r = build_schedule_checked(c, dt, 2, sched)) return r;
   have[0] = have[1] = false;
   for (const auto& s : sched) {
     if (s.axis < 0) continue;   // diagonal passes and copies have no line shape
@@ -1922,7 +1946,7 @@ int batch_prepare(pdg_batch* b, const double* dt, const int* nsteps) {
       return bfail(b, PDG_ERR_UNSUPPORTED, "lattice (D2Q9 / D3Qq) instances run through pdg_step only");
     if (nsteps[i] < 0 || !std::isfinite(dt[i])) return bfail(b, PDG_ERR_ARG, "bad dt or nsteps");
     std::vector<PdgPassSpec> sched;
-    if (int r = build_schedule(c, dt[i], nsteps[i], sched)) return bfail(b, r, c->err);
+    if (int r = build_schedule_checked(c, dt[i], nsteps[i], sched)) return bfail(b, r, c->err);
     for (const auto& sp : sched) {
       const int kind = pass_kind(sp);
       PdgPass p;

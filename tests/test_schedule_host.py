@@ -185,3 +185,30 @@ def test_schedule_refusals_and_arguments(pdg):
     assert e.value.status == pdg.PDG_ERR_UNSUPPORTED            # sources: M2 and collapsed only
     assert len(s.schedule(0.01, 2)) > 0
     s.close()
+
+
+def _overcommit_refuses_huge_requests():
+    try:
+        with open("/proc/sys/vm/overcommit_memory") as fh:
+            return fh.read().strip() in ("0", "2")
+    except OSError:
+        return False
+
+
+@pytest.mark.skipif(not _overcommit_refuses_huge_requests(),
+                    reason="needs a kernel that refuses allocations far beyond its memory")
+@pytest.mark.parametrize("scheme", ["M2", "M4_kin"])
+def test_pass_list_beyond_host_memory_fails_cleanly(pdg, scheme):
+    """2^31 - 1 steps need tens of TB of pass list: the call returns PDG_ERR_OOM at once (no
+    exception crosses the C ABI), and the context keeps working, its scheme unchanged."""
+    s = pdg.Solver(3, (2, 2, 2), (2, 2, 2), 1)
+    s.set_model("euler", 5.0, scheme=scheme)
+    with pytest.raises(pdg.PdgError) as e:
+        s.schedule(0.01, 2 ** 31 - 1)
+    assert e.value.status == pdg.PDG_ERR_OOM
+    sched = s.schedule(0.01, 2)
+    ev = classes_from_schedule(sched, 3, False)
+    info = s.info()
+    for a in range(3):
+        check_line_class(pdg, ev[a], expected(scheme, 0.01, 2), 1, 5.0, info.h[a], 0.5)
+    s.close()
