@@ -212,3 +212,25 @@ def test_pass_list_beyond_host_memory_fails_cleanly(pdg, scheme):
     for a in range(3):
         check_line_class(pdg, ev[a], expected(scheme, 0.01, 2), 1, 5.0, info.h[a], 0.5)
     s.close()
+
+
+def test_failed_calls_leave_the_context_unchanged(pdg):
+    """A refused pdg_set_model / pdg_set_source keeps the model, scheme and source that were
+    set before (seen through pdg_get_info and the pass list)."""
+    s = pdg.Solver(2, (3, 2), (2, 2), 2)
+    s.set_model("isothermal_d2q9", 1.0, scheme="M2_collapsed", theta=0.75)
+    s.set_source(gravity=(0.0, -1.0))
+    info0 = bytes(s.info())
+    sched0 = s.schedule(0.01, 3)
+    for kw in ({"theta": 1.5}, {"omega": 0.0}, {"scheme": 7}, {"theta": 0.0}):
+        with pytest.raises(pdg.PdgError):
+            s.set_model("isothermal_d2q9", 1.0, **kw)
+    with pytest.raises(pdg.PdgError):
+        s.set_model("isothermal_d3q19", 1.0)                     # a 3-D lattice on a 2-D mesh
+    assert bytes(s.info()) == info0
+    assert s.schedule(0.01, 3) == sched0
+    with pytest.raises(pdg.PdgError):
+        s.set_source(gravity=(0.0, -1.0), theta=1.5)
+    assert bytes(s.info()) == info0
+    assert s.schedule(0.01, 3) == sched0
+    s.close()
