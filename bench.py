@@ -1,21 +1,32 @@
 #!/usr/bin/env python3
-"""Benchmark of the PDG hot path: kinetic DOF-updates/s on the shallow-water D2Q4 workload.
+"""Benchmark of the PDG hot path: kinetic DOF-updates/s, FP64 against the mixed-precision
+form, as a fraction of the roofline, with the batched and serving forms beside it.
 
-Workload (one GPU): 2-D shallow water (g = 9.81) through the vectorial D2Q4 kinetic
-model (12 populations), periodic unit square, 64x64 macrocells x 8x8 subcells,
-DG degree 3 (4 GL points per cell and axis: 2048 x 2048 points), theta = 1/2,
-omega = 2, dt = h / lambda, lambda = 8; seeded smooth initial height, zero velocity.
-One benchmark step = one palindromic step M2(dt) = T(dt/2) C(dt) T(dt/2) over the
-whole state (50,331,648 kinetic DOF).  DOF-update = one population value at one GL
-point advanced through one full step.
+Default workload (one GPU): 3-D compressible Euler (gamma = 1.4) through the vectorial
+D3Q6 kinetic model (30 populations), periodic unit cube, 32^3 macrocells x 4^3 subcells,
+DG degree 2 (3 GL points per cell and axis: 384^3 points, 1,698,693,120 kinetic DOF,
+13.6 GB of FP64 state), theta = 1/2, omega = 2, dt = h / lambda, lambda = 5; seeded
+smooth density and velocity fields, pressure 1.  One benchmark step = one palindromic
+step M2(dt) = T(dt/2) C(dt) T(dt/2) over the whole state.  DOF-update = one population
+value at one GL point advanced through one full step.  The state is larger than L2, so
+no L2 flush is needed between steps.
 
-Output: ONE JSON line (rank 0).  `value` is measured with the state resident in
-HBM; `e2e` times the same run through the C ABI with host buffers (pdg_set_w from
-pinned host memory, pdg_step, pdg_get_w to host).  The state (403 MB) is larger
-than L2 (126 MB), so no L2 flush is needed between steps.
+Output: ONE JSON line (rank 0).
+  value       FP64, state resident in HBM, K steps between CUDA events on the context
+              stream, no per-kernel timing inside that region;
+  roofline    the dominant kernel, from a second K-step run with per-kernel CUDA events;
+  mixed       the double-float form (FP32-pair state and arithmetic), timed the same way,
+              with its error against the FP64 run;
+  e2e         the same metric through the C ABI with host buffers (pdg_set_w from pinned
+              host memory, pdg_step, pdg_get_w to host) inside the timed region;
+  cpu_baseline  the FP64 oracle on every host core (one replica of a bounded sample per
+              core), measured, not scaled;
+  batched / serving  the batched form (256 shallow-water meshes) and the serving form
+              (Poisson stream, continuous batching, p50/p99 and a sweep of arrival rates),
+              on the default workload only (--no-forms skips them).
 
-`--impl reference` times the FP64 CPU oracle (the only reference this method has:
-the paper ships no code) on a bounded sample of the same workload.
+`--impl reference` times the FP64 CPU oracle (the only reference this method has: the
+paper ships no code) on a bounded sample of the same workload, one replica per host core.
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no
 collective on the data path); value = sum over ranks / max time.
 """
@@ -129,10 +140,11 @@ SOURCES = {"gravity": dict(gravity=(0.0, -1.0)),
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--workload", default="shallow_water",
+    ap.add_argument("--workload", default="euler",
                     choices=["shallow_water", "advection", "euler", "d2q9", "d3q19", "d3q15", "d3q27", "batched",
                              "serving"])
-    ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--requests", type=int, default=1000,
+                    help="serving: requests in the Poisson stream at --rate")
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--chunk", type=int, default=10)
@@ -157,7 +169,18 @@ def parse_args():
                          "and kernel figures come from a run with direct launches")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample-steps", type=int, default=20)
+    ap.add_argument("--cpu-sample-steps", type=int, default=None,
+                    help="oracle steps per core in cpu_baseline (default: about 10 s of work)")
+    ap.add_argument("--cpu-cores", type=int, default=None,
+                    help="oracle replicas in cpu_baseline / --impl reference (default: every host core)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default workload: skip the batched and serving sub-objects")
+    ap.add_argument("--sweep-requests", type=int, default=100,
+                    help="serving: requests per arrival rate of the latency sweep (0: no sweep)")
+    ap.add_argument("--serial", action="store_true",
+                    help="serving: also time every request alone (serial FIFO baseline; as long as the stream)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="print the measured FP64 / FP32 multiply-add throughput and HBM copy rate, and exit")
     ap.add_argument("--no-mixed", action="store_true", help="skip the double-float measurement")
     ap.add_argument("--shapes", default=None,
                     help="fixed launch shapes 'lpb,nseg,ngroup/lpb,nseg,ngroup' for the transport and "
@@ -246,18 +269,26 @@ class ClockSampler:
         return out
 
 
-def cpu_baseline(cfg_name, sample_steps, warmup_steps=1):
-    """Time the FP64 oracle (single thread) on a bounded sample of the workload, in a
-    fresh process (no CUDA there; BLAS/OpenMP pinned to one thread)."""
-    code = f"""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# Oracle sample of each workload for the CPU timings: macrocells per axis (the subcells and
+# the degree stay the workload's).  About 0.3 s per oracle step on one core.
+ORACLE_SAMPLE_MACRO = {2: 8, 3: 4}
+
+_REPLICA = r"""
 import json, sys, time
-sys.path.insert(0, {ROOT!r})
+sys.path.insert(0, {root!r})
 import numpy as np
 from paper_1702_00169_gb300 import workloads as W
 from oracle import models as OM, scheme as OS
 from oracle.dg import CartesianMesh
-cfg = W.CONFIGS[{cfg_name!r}]
-cfg = cfg.scaled(n_macro=tuple(min(8 if cfg.dim < 3 else 2, x) for x in cfg.n_macro))
+cfg = W.CONFIGS[{name!r}]
+cfg = cfg.scaled(n_macro=tuple(min({nm}, x) for x in cfg.n_macro))
 mesh = CartesianMesh(cfg.dim, cfg.ncells, cfg.order, lengths=cfg.lengths[:cfg.dim])
 kind = {{"advection": OM.ADVECTION, "shallow_water": OM.SHALLOW_WATER, "euler": OM.EULER,
         "isothermal_d2q9": OM.ISOTHERMAL_D2Q9, "isothermal_d3q19": OM.ISOTHERMAL_D3Q19,
@@ -266,50 +297,134 @@ model = OM.Model(kind, cfg.dim, cfg.lam, a=cfg.a[:cfg.dim], gravity=cfg.gravity,
 w0 = W.initial_w(cfg, [mesh.coords1d(a) for a in range(cfg.dim)])
 tr = OS.Transporter(mesh, model, theta=cfg.theta, method="bloch")
 f = OS.initial_state(model, w0)
-for _ in range(max(1, {warmup_steps})):
+for _ in range({warmup}):
     f = OS.m2_step(f, tr, model, cfg.dt, cfg.omega)
-t0 = time.perf_counter()
-for _ in range({sample_steps}):
+print("READY", flush=True)
+sys.stdin.readline()
+t0 = time.time()
+for _ in range({steps}):
     f = OS.m2_step(f, tr, model, cfg.dt, cfg.omega)
-el = time.perf_counter() - t0
-print(json.dumps({{"value": cfg.dofs * {sample_steps} / el, "dofs": cfg.dofs, "steps": {sample_steps},
-                  "seconds": el, "mesh": "%s macrocells x %s subcells, d=%d" % (
+t1 = time.time()
+print(json.dumps({{"t0": t0, "t1": t1, "dofs": cfg.dofs, "finite": bool(np.all(np.isfinite(f))),
+                  "mesh": "%s macrocells x %s subcells, d=%d" % (
                       "x".join(map(str, cfg.n_macro)), "x".join(map(str, cfg.n_sub)), cfg.order)}}))
 """
+
+
+def oracle_replicas(cfg_name, dim, steps, warmup, cores=None):
+    """Time the FP64 oracle on every host core: one process per core, each advancing its own
+    copy of a bounded sample of the workload (macrocells per axis capped at
+    ORACLE_SAMPLE_MACRO[dim]) through `warmup` untimed and `steps` timed M2 steps.  The timed
+    steps start together (every process reports after its warm-up and waits for a common go);
+    the wall time runs from the first start to the last process's end.  Returns the measured figures
+    of that sample (nothing is scaled to the full workload)."""
+    cores = cores or host_cores()
+    nm = ORACLE_SAMPLE_MACRO.get(dim, 4)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-500:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 numpy oracle (Bloch/FFT transport), {d['steps']} M2 steps of the same model "
-                       f"on {d['mesh']} ({d['dofs']} DOF), {d['seconds']:.1f} s, 1 thread")}
+    code = _REPLICA.format(root=ROOT, name=cfg_name, nm=nm, warmup=warmup, steps=steps)
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdin=subprocess.PIPE, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env) for _ in range(cores)]
+    for p in procs:            # every replica has set up and warmed up
+        p.stdout.readline()
+    for p in procs:            # common start
+        try:
+            p.stdin.write("go\n")
+            p.stdin.flush()
+        except OSError:
+            pass
+    outs = []
+    err = None
+    for p in procs:
+        try:
+            o, e = p.communicate(timeout=1800)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            o, e = p.communicate()
+        if p.returncode != 0:
+            err = (e or "")[-500:]
+            continue
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    if not outs or err:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": err or "no output"}
+    t0 = min(d["t0"] for d in outs)
+    t1 = max(d["t1"] for d in outs)
+    wall = t1 - t0
+    dofs = outs[0]["dofs"]
+    late = max(d["t0"] for d in outs) - t0
+    return {"value": len(outs) * dofs * steps / wall, "unit": UNIT, "cores": len(outs), "kind": "oracle",
+            "ms_per_step": 1e3 * wall / steps, "seconds": wall, "steps": steps, "sample_dofs": dofs,
+            "start_spread_s": late, "finite": all(d["finite"] for d in outs),
+            "sample": (f"FP64 numpy oracle (Bloch/FFT transport), {len(outs)} processes (one per host core), each "
+                       f"advancing its own copy of the workload's model on {outs[0]['mesh']} ({dofs} DOF) through "
+                       f"{steps} timed M2 steps after {warmup} untimed; wall time {wall:.1f} s from the common "
+                       f"start to the last process's end; value = {len(outs)} x {dofs} x {steps} / wall")}
+
+
+def cpu_baseline(cfg_name, dim, steps=None, cores=None):
+    """The oracle on all host cores, about 10 s of work per core (see oracle_replicas)."""
+    if steps is None:
+        steps = 30 if dim == 3 else 20
+    return oracle_replicas(cfg_name, dim, steps, 1, cores)
 
 
 def run_reference(args, cfg, base_name):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    # each reference step = one M2 step of the oracle on a bounded sample of the workload
-    res = cpu_baseline(base_name, max(1, args.steps), max(1, args.warmup))
-    value = res["value"]
+    # each reference step = one M2 step of the oracle on the bounded sample, on every core
+    res = oracle_replicas(base_name, cfg.dim, max(1, args.steps), max(1, args.warmup), args.cpu_cores)
+    value = res.get("value")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res.get("ms_per_step"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": cfg.name, "reference": "FP64 CPU oracle (the paper ships no code)"},
+            "data": "synthetic",
+            "config": {"workload": cfg.name, "reference": "FP64 CPU oracle (the paper ships no code)",
+                       "sample": res.get("sample"), "sample_dofs": res.get("sample_dofs"),
+                       "ms_per_step": "measured wall time per M2 step of the sample on all cores (not scaled)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": res.get("cores"), "kind": "oracle",
                              "sample": res.get("sample")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    if value:
-        line["ms_per_step"] = 1e3 * cfg.dofs / value
+    if res.get("error"):
+        line["error"] = res["error"]
     print(json.dumps(line), flush=True)
+
+
+def measure_peaks(stream=None):
+    """Measured FP64 / FP32 multiply-add throughput (pdg_measure_fma_peak) and a device copy
+    rate (read + write bytes of a 4 GiB torch copy, best of 5)."""
+    import torch
+    from paper_1702_00169_gb300 import pdg
+    out = {}
+    try:
+        out["fp64_tflops"] = pdg.measure_fma_peak(True, stream)[0]
+        out["fp32_tflops"] = pdg.measure_fma_peak(False, stream)[0]
+    except Exception as e:  # noqa: BLE001 - reported in the line
+        out["error"] = str(e)
+    a = torch.empty(1 << 29, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1.0)
+    best = 1e30
+    for _ in range(6):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    out["copy_gbs"] = 2.0 * a.numel() * 8 / (best * 1e-3) / 1e9
+    del a, b
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_batched(args):
     """256 independent shallow-water meshes (8..96 macrocells per axis x 4x4 subcells,
-    degrees 1-4, per-instance dt at CFL 1) advanced by persistent batched launches
-    replayed from a CUDA graph; compared with the same instances stepped one by one."""
+    degrees 1-4, per-instance dt at CFL 1) advanced by persistent batched launches replayed
+    from a CUDA graph, FP64 and double-float; compared with the same instances stepped one
+    by one through pdg_step, each with its own autotuned launch shapes and its K-step CUDA
+    graph replayed, so that the ratio measures batching alone.  Returns a dict."""
     import torch
     from paper_1702_00169_gb300 import pdg
     from paper_1702_00169_gb300 import workloads as W
@@ -356,49 +471,51 @@ def bench_batched(args):
     ms, launches, tune_s, clocks = timed(b, True)
     err_d = float(np.sqrt(sum(np.sum((sv.get_w() - wd) ** 2) for sv, wd in zip(sol[:16], w_d))
                           / sum(np.sum(sv.get_w() ** 2) for sv in sol[:16])))
-    # same instances one after the other through pdg_step (heuristic shapes, no graph)
+    finite = all(bool(np.all(np.isfinite(sv.get_w()))) for sv in sol[:8])
+    b.close()
+    # the same instances one by one: autotuned shapes, a captured K-step graph each (untimed
+    # set-up), then the K-step replays of all instances back to back between two events
+    t0 = time.perf_counter()
+    for sv, dt in zip(sol, dts):
+        if not args.no_autotune:
+            sv.autotune(dt, reps=1)
+        sv.set_option(pdg.PDG_OPT_GRAPH, 1)
+        sv.step(dt, K)
+    tune_serial = time.perf_counter() - t0
+    torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    for sv, dt in zip(sol, dts):
-        sv.step(dt, 1)
-    torch.cuda.synchronize()
     ev0.record(stream)
     for sv, dt in zip(sol, dts):
         sv.step(dt, K)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms_serial = ev0.elapsed_time(ev1)
-    finite = all(bool(np.all(np.isfinite(sv.get_w()))) for sv in sol[:8])
-    b.close()
     for sv in sol:
         sv.close()
-    value = dofs * K / (ms * 1e-3)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": K,
-            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+    return {"value": dofs * K / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms, "steps": K, "dtype": "f64",
             "config": {"workload": "batched_shallow_water_256", "instances": len(insts), "dof": dofs,
                        "mesh": "M x M macrocells, M ~ U{8..96}, 4x4 subcells, d ~ U{1..4} (seed 4)",
                        "dt": "per instance, CFL 1", "graph": True, "autotuned": not args.no_autotune,
                        "autotune_s": tune_s, "l2": "18 GB state >> L2"},
             "gpu_launches": launches, "clocks": clocks,
-            "serial": {"value": dofs * K / (ms_serial * 1e-3), "ms": ms_serial,
-                       "note": "same instances, pdg_step one after the other, heuristic shapes"},
-            "speedup_vs_serial": ms_serial / ms, "state_finite": finite,
+            "one_by_one": {"value": dofs * K / (ms_serial * 1e-3), "ms": ms_serial, "setup_s": tune_serial,
+                           "note": "each instance alone through pdg_step: its own autotuned shapes, its K-step "
+                                   "CUDA graph replayed, instances back to back"},
+            "speedup_vs_one_by_one": ms_serial / ms, "state_finite": finite,
             "mixed": {"precision": "df32", "value": dofs * K / (ms_d * 1e-3), "speedup_vs_fp64": ms / ms_d,
                       "rel_l2_w_vs_fp64": err_d, "note": "same batch, double-float state and arithmetic; error over "
-                                                         "the first 16 instances after the 2 x K steps"}}
-    print(json.dumps(line), flush=True)
+                                                         "the first 16 instances after warm-up + K steps"}}
 
 
-def bench_serving(args):
-    """Poisson stream of 2-D advection / shallow-water solves served with continuous
-    batching under a device-memory budget; latency = completion - arrival."""
+def _serve_stream(reqs, args, stream, with_clocks=False):
+    """Serve one request stream [(t_arrival, cfg, nsteps)] through a fresh pdg server with
+    continuous batching (arrivals follow their times on the server clock).  Latency =
+    completion - arrival, queue wait = admission - arrival."""
     import queue
     import torch
     from paper_1702_00169_gb300 import pdg
     from paper_1702_00169_gb300 import workloads as W
-    reqs = W.serving_requests(n=args.requests, rate=args.rate)
-    stream = torch.cuda.Stream()
 
     def coords(cfg):
         # GL coordinates from the library's own quadrature (a throw-away context)
@@ -427,8 +544,9 @@ def bench_serving(args):
     lat, work, ids = [], {}, {}
     nxt = None
     submitted = 0
-    sampler = ClockSampler(str(torch.cuda.get_device_properties(0).uuid))
-    sampler.start()
+    sampler = ClockSampler(str(torch.cuda.get_device_properties(0).uuid)) if with_clocks else None
+    if sampler:
+        sampler.start()
     while len(lat) < len(reqs):
         now = srv.now() - t0
         while submitted < len(reqs):
@@ -454,54 +572,105 @@ def bench_serving(args):
             lat.append((tc - ta, tb - ta, rid))
             srv.result(rid, ids[rid].m * ids[rid].npoints)
     makespan = srv.now() - t0
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     st = srv.stats()
     srv.close()
+    th.join(timeout=5)
     total = sum(work.values())
     L = np.array([x[0] for x in lat])
     Q = np.array([x[1] for x in lat])
-    # serial FIFO baseline: service time of every request alone through pdg_step, then the
-    # single-server queue on the same arrival times
-    service = []
-    for t, cfg, ns in reqs:
-        sv = pdg.solver_for(cfg, stream=stream.cuda_stream)
-        sv.set_w(np.ascontiguousarray(W.initial_w(cfg, [sv.points(a) for a in range(cfg.dim)]).reshape(-1)))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sv.step(cfg.dt, ns)
-        e1.record(stream)
-        e1.synchronize()
-        service.append(e0.elapsed_time(e1) * 1e-3)
-        sv.close()
-    tdone, sl = 0.0, []
-    for (t, cfg, ns), sv_t in zip(reqs, service):
-        tdone = max(t, tdone) + sv_t
-        sl.append(tdone - t)
-    sl = np.array(sl)
-    line = {"metric": METRIC, "value": total / makespan, "unit": UNIT, "n_gpus": 1, "steps": len(reqs),
-            "warmup": 1, "ms_per_step": 1e3 * makespan / len(reqs), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "serving_poisson", "requests": len(reqs), "rate_req_s": args.rate,
-                       "budget_gb": args.budget_gb, "chunk_steps": args.chunk,
-                       "mix": "50/50 advection D2Q4 / shallow water D2Q4, M ~ U{16..128} macrocells, 4x4 subcells, "
-                              "d ~ U{1..4}, steps log-uniform [10, 1000] (seed 5)",
-                       "step": "one request served"},
+    return {"requests": len(reqs), "value": total / makespan, "makespan_s": makespan, "dof_updates": total,
             "latency_s": {"p50": float(np.percentile(L, 50)), "p99": float(np.percentile(L, 99)),
-                          "mean": float(L.mean()), "queue_p50": float(np.percentile(Q, 50))},
-            "makespan_s": makespan, "dof_updates": total, "server": st, "clocks": clocks,
-            "offered_dof_updates_per_s": total / max(1e-9, reqs[-1][0]),
-            "serial": {"value": total / float(np.sum(service)), "latency_p50_s": float(np.percentile(sl, 50)),
-                       "latency_p99_s": float(np.percentile(sl, 99)),
-                       "note": "each request alone through pdg_step, FIFO single-server queue on the same arrivals"}}
-    print(json.dumps(line), flush=True)
+                          "mean": float(L.mean()), "queue_p50": float(np.percentile(Q, 50)),
+                          "queue_p99": float(np.percentile(Q, 99))},
+            "offered_dof_updates_per_s": total / max(1e-9, reqs[-1][0]), "server": st, "clocks": clocks}
+
+
+def bench_serving(args, serial=False):
+    """Poisson stream of 2-D advection / shallow-water solves served with continuous
+    batching under a device-memory budget (the stream at --rate, default 1000 requests at
+    200 req/s), then a sweep of arrival rates on the first --sweep-requests requests of the
+    same stream (rates at 1/4, 1/2, 3/4 and 1 of the capacity the first run measured), and
+    the highest swept rate whose p99 latency stays within twice the p99 at the lowest rate.
+    serial: also time every request alone through pdg_step (single-server FIFO on the same
+    arrivals).  Returns a dict."""
+    import torch
+    from paper_1702_00169_gb300 import pdg
+    from paper_1702_00169_gb300 import workloads as W
+    stream = torch.cuda.Stream()
+    reqs = W.serving_requests(n=args.requests, rate=args.rate)
+    main = _serve_stream(reqs, args, stream, with_clocks=True)
+    out = {"value": main["value"], "unit": UNIT, "dtype": "f64",
+           "config": {"workload": "serving_poisson", "requests": len(reqs), "rate_req_s": args.rate,
+                      "budget_gb": args.budget_gb, "chunk_steps": args.chunk,
+                      "mix": "50/50 advection D2Q4 / shallow water D2Q4, M ~ U{16..128} macrocells, 4x4 subcells, "
+                             "d ~ U{1..4}, steps log-uniform [10, 1000] (seed 5)"},
+           "stream": main}
+    if args.sweep_requests > 0:
+        sub = W.serving_requests(n=args.sweep_requests, rate=1.0)
+        mean_work = float(np.mean([c.dofs * ns for _, c, ns in sub]))
+        cap = main["value"] / mean_work          # requests per second the server sustained
+        sweep = []
+        for frac in (0.25, 0.5, 0.75, 1.0):
+            r = frac * cap
+            res = _serve_stream(W.serving_requests(n=args.sweep_requests, rate=r), args, stream)
+            sweep.append({"rate_req_s": r, "fraction_of_capacity": frac, "value": res["value"],
+                          "p50_s": res["latency_s"]["p50"], "p99_s": res["latency_s"]["p99"],
+                          "queue_p99_s": res["latency_s"]["queue_p99"], "makespan_s": res["makespan_s"]})
+        bound = 2.0 * sweep[0]["p99_s"]
+        ok = [x["rate_req_s"] for x in sweep if x["p99_s"] <= bound]
+        out["rate_sweep"] = {"requests_per_rate": args.sweep_requests, "capacity_req_s": cap,
+                             "mean_dof_updates_per_request": mean_work, "points": sweep,
+                             "p99_bound_s": bound,
+                             "max_rate_bounded_p99_req_s": max(ok) if ok else None,
+                             "criterion": "highest swept rate whose p99 latency is at most twice the p99 at "
+                                          "1/4 of the capacity (where requests rarely queue)"}
+    if serial:
+        service = []
+        for t, cfg, ns in reqs:
+            sv = pdg.solver_for(cfg, stream=stream.cuda_stream)
+            sv.set_w(np.ascontiguousarray(W.initial_w(cfg, [sv.points(a) for a in range(cfg.dim)]).reshape(-1)))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv.step(cfg.dt, ns)
+            e1.record(stream)
+            e1.synchronize()
+            service.append(e0.elapsed_time(e1) * 1e-3)
+            sv.close()
+        tdone, sl = 0.0, []
+        for (t, cfg, ns), sv_t in zip(reqs, service):
+            tdone = max(t, tdone) + sv_t
+            sl.append(tdone - t)
+        sl = np.array(sl)
+        out["serial"] = {"value": main["dof_updates"] / float(np.sum(service)),
+                         "latency_p50_s": float(np.percentile(sl, 50)),
+                         "latency_p99_s": float(np.percentile(sl, 99)),
+                         "note": "each request alone through pdg_step (plain FP64, heuristic shapes), single-server "
+                                 "FIFO on the same arrivals"}
+    return out
+
+
+def _line_for_form(args, sub, workload):
+    """A standalone JSON line for --workload batched / serving."""
+    steps = sub.get("steps", sub.get("config", {}).get("requests"))
+    line = {"metric": METRIC, "value": sub["value"], "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": steps if workload == "batched" else 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
+    line.update(sub)
+    if workload == "batched":
+        line["ms_per_step"] = sub["ms_per_call"] / sub["steps"]
+    else:
+        line["ms_per_step"] = 1e3 * sub["stream"]["makespan_s"] / sub["config"]["requests"]
+        line["clocks"] = sub["stream"]["clocks"]
+    return line
 
 
 def main():
     args = parse_args()
     from paper_1702_00169_gb300 import workloads as W
-    cfg = {"advection": W.ADVECTION_D2Q4, "euler": W.EULER_D3Q6, "d2q9": W.D2Q9_ISO,
-           "d3q19": W.D3Q19_ISO, "d3q15": W.D3Q15_ISO, "d3q27": W.D3Q27_ISO}.get(args.workload, W.SW_D2Q4)
+    cfg = {"advection": W.ADVECTION_D2Q4, "shallow_water": W.SW_D2Q4, "euler": W.EULER_D3Q6, "d2q9": W.D2Q9_ISO,
+           "d3q19": W.D3Q19_ISO, "d3q15": W.D3Q15_ISO, "d3q27": W.D3Q27_ISO}.get(args.workload, W.EULER_D3Q6)
     base_name = cfg.name   # the oracle's sample is drawn from the named workload
     if args.cfl:
         import dataclasses
@@ -518,11 +687,16 @@ def main():
             args.warmup = 3
         run_reference(args, cfg, base_name)
         return
-    if args.workload == "batched":
-        bench_batched(args)
+    if args.peaks:
+        import torch
+        torch.cuda.set_device(0)
+        pk = measure_peaks()
+        nominal = torch.cuda.get_device_properties(0).multi_processor_count * 2 * 2 * 2070e6 / 1e12
+        print(json.dumps({"peaks": pk, "fp64_nominal_tflops_at_2070mhz": nominal}), flush=True)
         return
-    if args.workload == "serving":
-        bench_serving(args)
+    if args.workload in ("batched", "serving"):
+        sub = bench_batched(args) if args.workload == "batched" else bench_serving(args, serial=True)
+        print(json.dumps(_line_for_form(args, sub, args.workload)), flush=True)
         return
     if args.steps is None:
         args.steps = {"euler": 20, "advection": 1000, "d2q9": 100, "d3q19": 10, "d3q15": 4,
@@ -574,32 +748,34 @@ def main():
         else:
             fb = np.ascontiguousarray(np.stack([f0[:, 0, ..., 0].reshape(cfg.m, -1),
                                                 f0[:, 1, ..., -1].reshape(cfg.m, -1)]))
+        del f0
     torch.cuda.synchronize()
     dev_uuid = None
     try:
         dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
         pass
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
 
-    def timed_run(sv, graph=False):
+    def timed_run(sv, per_kernel=False, graph=False):
         """W untimed steps, then K steps between CUDA events on the context stream, with
-        per-kernel event timing and clock sampling inside the timed region.  graph: the K
-        steps replay a CUDA graph captured by one untimed run of K steps (per-kernel timing
-        is off in graph replay: launches and kms come back as zeros)."""
+        clock sampling around them.  per_kernel: CUDA events around every launch as well
+        (the roofline run; the headline run has none).  graph: the K steps replay a CUDA
+        graph captured by one untimed run of K steps."""
         sv.set_w(w0_dev)
         if fb is not None:
             sv.set_inflow(0, fb)
-        if graph:
-            pass                            # the launch shapes of the plain run stay
-        elif args.shapes:
-            for kind, sh in enumerate(args.shapes.split("/")):
-                sv.set_launch(kind, *[int(x) for x in sh.split(",")])
-        elif not args.no_autotune:
-            sv.autotune(cfg.dt, reps=3)     # launch shapes picked on a scratch copy (untimed)
+        if not getattr(sv, "_bench_tuned", False) and not graph:
+            if args.shapes:
+                for kind, sh in enumerate(args.shapes.split("/")):
+                    sv.set_launch(kind, *[int(x) for x in sh.split(",")])
+            elif not args.no_autotune:
+                sv.autotune(cfg.dt, reps=3)     # launch shapes picked on a scratch copy (untimed)
+            sv._bench_tuned = True
         sv.step(cfg.dt, args.warmup)
         if graph:
             sv.set_option(pdg.PDG_OPT_GRAPH, 1)
@@ -610,7 +786,7 @@ def main():
         torch.cuda.synchronize()
         sampler.start()
         time.sleep(0.4)
-        if not graph:
+        if per_kernel:
             sv.timing_enable(True)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -621,11 +797,11 @@ def main():
         torch.cuda.synchronize()
         clk = sampler.stop()
         barrier()
-        launches, kms = sv.timing_read()
+        launches, kms = sv.timing_read() if per_kernel else ([0] * 5, [0.0] * 5)
         sv.timing_enable(False)
         if graph:
             sv.set_option(pdg.PDG_OPT_GRAPH, 0)
-        return ev0.elapsed_time(ev1), launches, kms, clk, sv.get_w()
+        return ev0.elapsed_time(ev1), launches, kms, clk
 
     n = cfg.order + 1
     P = info.npoints
@@ -648,51 +824,69 @@ def main():
             return 16.0 * F * P, 2 * pops_line * P * transport_flops_per_dof(n) + P * collision_flops(cfg.kind, cfg.dim)
         return 16.0 * pops_line * P, 2 * pops_line * P * transport_flops_per_dof(n)
 
-    # ---- device-resident run (FP64) ----
-    ms, launches, kms, clocks, w_end = timed_run(s)
+    dofs = cfg.dofs
+    # ---- FP64 (or --precision), state resident in HBM: headline, then per-kernel timing ----
+    ms, _, _, clocks = timed_run(s)
+    w_end = s.get_w()
+    finite = bool(np.all(np.isfinite(w_end)))
+    ms_k, launches, kms, clocks_k = timed_run(s, per_kernel=True)
     graph_run = None
     if args.graph:
-        # the headline run replays one CUDA graph per K steps; per-kernel timing (roofline,
-        # launch counts) comes from the plain run above
-        ms_g, _, _, clocks_g, _ = timed_run(s, graph=True)
-        graph_run = {"ms_per_step_plain": ms / args.steps,
+        ms_g, _, _, clocks_g = timed_run(s, graph=True)
+        graph_run = {"ms_per_step_direct": ms / args.steps,
                      "note": "one CUDA graph of K steps replayed; bitwise the direct launches (tests/test_gpu_graph.py)"}
         ms, clocks = ms_g, clocks_g
     shape0, shape1 = s.get_launch(0), s.get_launch(1)
     s_shape = {0: shape0, 1: shape1}
-    finite = bool(np.all(np.isfinite(w_end)))
-
-    dofs = cfg.dofs
     ms_max, units = aggregate_ranks(ms, dofs * args.steps)
     value = units / (ms_max * 1e-3)
 
     # ---- the same run in double-float precision (FP32-pair state and arithmetic) ----
     mixed = None
     if not args.no_mixed and args.precision == "fp64":
+        s.close()                       # one state at a time on the device
+        s = None
         sd = solver("df32")
-        ms_d, launches_d, kms_d, clocks_d, w_end_d = timed_run(sd)
+        ms_d, _, _, clocks_d = timed_run(sd)
+        w_end_d = sd.get_w()
+        _, launches_d, kms_d, _ = timed_run(sd, per_kernel=True)
         sd.close()
         k_d = dominant(kms_d)
         avg_d = kms_d[k_d] / max(1, launches_d[k_d])
         bytes_d = kernel_work(k_d)[0]
+        ms_d_max, units_d = aggregate_ranks(ms_d, dofs * args.steps)
         mixed = {"precision": "df32 (FP32-pair state and double-word arithmetic on the FP32 pipes)",
-                 "value": aggregate_ranks(ms_d, dofs * args.steps)[1] / (aggregate_ranks(ms_d, 0)[0] * 1e-3),
-                 "ms_per_step": ms_d / args.steps,
-                 "speedup_vs_fp64": ms / ms_d,
+                 "value": units_d / (ms_d_max * 1e-3),
+                 "ms_per_step": ms_d_max / args.steps,
+                 "speedup_vs_fp64": ms_max / ms_d_max,
                  "rel_l2_w_vs_fp64_after_steps": float(np.linalg.norm(w_end_d - w_end) / np.linalg.norm(w_end)),
+                 "steps_compared": args.warmup + args.steps,
                  "dominant_kernel_avg_ms": avg_d,
                  "hbm_achieved_gbs": bytes_d / (avg_d * 1e-3) / 1e9, "clocks": clocks_d,
+                 "kernels": {name: {"launches": int(launches_d[k]), "avg_ms": kms_d[k] / launches_d[k],
+                                    "share": kms_d[k] / max(1e-12, sum(kms_d))}
+                             for k, name in ((0, "transport pass"), (1, "last-axis pass"), (2, "state kernels"),
+                                             (3, "diagonal pass"), (4, "corner pass")) if launches_d[k]},
                  "gpu_launches": int(sum(launches_d))}
+        del w_end_d
 
     # ---- end-to-end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
+        if s is not None:
+            s.close()
+            s = None
+        del w0_dev
+        torch.cuda.empty_cache()
         w_host = torch.from_numpy(w0).pin_memory()
         w_out = torch.empty_like(w_host).pin_memory()
         s2 = solver("fp64")
         s2.set_w(w_host)
         if fb is not None:
             s2.set_inflow(0, fb)
+        if args.shapes or not args.no_autotune:
+            for kind in (0, 1):
+                s2.set_launch(kind, *s_shape[kind])
         s2.step(cfg.dt, 2)
         s2.get_w(w_out)
         barrier()
@@ -707,15 +901,18 @@ def main():
         nbytes = w0.nbytes
         e2e = {"value": units_e2e / el_max, "unit": UNIT,
                "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
-               "note": "one pdg_set_w (host) + pdg_step(K) + pdg_get_w (host) per timed run; bytes amortised over K"}
-    s.close()
+               "note": "one pdg_set_w (pinned host) + pdg_step(K) + pdg_get_w (pinned host) per timed run; "
+                       "bytes amortised over K"}
+        del w_host, w_out
+    if s is not None:
+        s.close()
 
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel (from the live CUDA-event timing) ----
+    # ---- roofline of the dominant kernel (from the per-kernel CUDA-event run) ----
     kinds = {0: "transport pass (composed T T on the populations of the other axes)",
              1: "last-axis pass (T, collision, T)",
              3: "diagonal transport pass (4 populations of one plane, tiled 2-D wavefront)",
@@ -729,31 +926,37 @@ def main():
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # FP64 pipe: 2 DFMA per SM per clock (GB300 nominal 1.25 TFLOP/s at 2.07 GHz, 152 SMs)
-    fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    sm_mhz = clocks_k.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    measured = measure_peaks(stream.cuda_stream)
+    # FP64 pipe: 2 DFMA per SM per clock (GB300 nominal 1.26 TFLOP/s at 2.07 GHz)
+    fp64_peak_tflops = n_sm * 2 * 2 * sm_mhz * 1e6 / 1e12
     achieved_tflops = flops_launch / (avg_ms * 1e-3) / 1e12
     achieved_gbs = bytes_launch / (avg_ms * 1e-3) / 1e9
     roof = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
             "frac": achieved_tflops / fp64_peak_tflops,
+            "peak_measured": measured.get("fp64_tflops"),
+            "frac_of_measured": (achieved_tflops / measured["fp64_tflops"]) if measured.get("fp64_tflops") else None,
             "traffic": (TRAFFIC.get((cfg.name, k_dom, args.precision,
                                      tuple(s_shape[k_dom]) if k_dom in (0, 1) else None))
                         if args.source == "none" else None),
             "kernel": kinds[k_dom], "avg_launch_ms": avg_ms, "launches": launches[k_dom],
             "algorithmic_flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
             "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak, "hbm_frac": achieved_gbs / hbm_peak,
-            "peak_note": ("FP64 pipe peak = 152 SMs x 2 DFMA/clk x 2 flop x median SM clock under load"
+            "timing_run": "a second K-step run with CUDA events around every launch (the headline run has none)",
+            "peak_note": (f"peak = {n_sm} SMs x 2 DFMA/clk x 2 flop x median SM clock under load (nominal); "
+                          "peak_measured = pdg_measure_fma_peak (FP64 FMA chains on every SM), of measured"
                           + ("; double-float run: the algorithmic flops are FP64-equivalent operations "
                              "executed as double-word FP32 arithmetic, so the FP64 pipe is not its bound"
                              if args.precision == "df32" else ""))}
 
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = cpu_baseline(base_name, args.cpu_sample_steps)
+        cpu = cpu_baseline(base_name, cfg.dim, args.cpu_sample_steps, args.cpu_cores)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32x2",
+            "data": "synthetic",
             "config": {"workload": cfg.name,
                        "model": ("isothermal Euler via D2Q9 (9 populations, 4 diagonal)" if q9 else
                                  "isothermal Euler via D3Q19 (19 populations, 12 edge)"
@@ -782,10 +985,14 @@ def main():
                                "share": kms[k] / max(1e-12, sum(kms))}
                         for k, name in ((0, "transport pass"), (1, "last-axis pass"), (2, "state kernels"),
                                         (3, "diagonal pass"), (4, "corner pass")) if launches[k]},
-            "roofline": roof, "clocks": clocks,
+            "per_kernel_run_ms_per_step": ms_k / args.steps,
+            "roofline": roof, "clocks": clocks, "peaks_measured": measured,
             "e2e": e2e, "cpu_baseline": cpu, "mixed": mixed, "state_finite": finite}
     if graph_run:
         line["graph_replay"] = graph_run
+    if args.workload == "euler" and not args.no_forms and ws == 1 and not (args.n_macro or args.cfl):
+        line["batched"] = bench_batched(args)
+        line["serving"] = bench_serving(args, serial=args.serial)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

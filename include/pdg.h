@@ -389,11 +389,16 @@ int pdg_get_schedule(pdg_ctx* ctx, double dt, int nsteps, int* ints, double* dbl
  * Behaviour: writes the whole staged range before copying it (nothing in the array
  * needs to start at zero); synchronises the context stream before returning.  The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  All
+ * with that device current and keeps it for the life of the process; make that first
+ * call before any stream capture.  The kept address assumes the device's primary
+ * context lives as long as the library: a caller that runs cudaDeviceReset must not
+ * call this entry point on that device afterwards (the reset unloads the array).  All
  * calls share the one array: calls whose GPU work overlaps (other contexts on other
  * streams, or other host threads) race on it and must be serialised by the caller.
  * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (NULL, len mismatch, or len greater
- * than 1,048,576: use pdg_get_w), PDG_ERR_UNSUPPORTED (a PDG_PREC_DF32 state), PDG_ERR_CUDA.
+ * than 1,048,576: use pdg_get_w), PDG_ERR_UNSUPPORTED (a PDG_PREC_DF32 state, or a
+ * lattice model: D2Q9, D3Q15, D3Q19, D3Q27, whose w is not a sum of m groups of 2D
+ * populations; use pdg_get_w for those), PDG_ERR_CUDA.
  */
 int pdg_get_w_noalloc(pdg_ctx* ctx, double* out, size_t len);
 
@@ -425,7 +430,10 @@ int pdg_timing_read(pdg_ctx* ctx, long long* launches, double* ms, int max_kinds
  *   nseg x ngroup = output cells per tile along x and y (>= 1; the tile counts follow).
  * kind 5 = D3Q15 / D3Q27 corner pass: lpb = threads per block (a multiple of 32, 64..512,
  *   at least (d+1)^3), nseg = output cells per box along x and y, ngroup = along z.
- * All zeros restores the built-in heuristic.  Used by the autotuners.
+ * kind 6 = the corner box alone: lpb, nseg, ngroup = output cells per box along x, y, z
+ *   (>= 1 each); the threads per block stay as kind 5 set them (512 when unset).
+ * All zeros restores the built-in heuristic (kind 6: the box only).  Used by the
+ * autotuners and by tests that force a box shape.
  * Errors: PDG_ERR_ARG.
  */
 int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
@@ -450,7 +458,7 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
 enum { PDG_OPT_COMPOSE_TT = 1, PDG_OPT_GRAPH = 2 };
 int pdg_set_option(pdg_ctx* ctx, int option, int value);
 
-/* pdg_get_launch -- read the launch shape override of a kind 0..5 (zeros = heuristic). */
+/* pdg_get_launch -- read the launch shape override of a kind 0..6 (zeros = heuristic). */
 int pdg_get_launch(const pdg_ctx* ctx, int kind, int* lpb, int* nseg, int* ngroup);
 
 /*
@@ -609,6 +617,19 @@ int pdg_plan_line(int d, double nu, double theta, double* E, double* q, double* 
  * PDG_ERR_UNSUPPORTED (no width within the limit: 128 cells for tiles, 64 for boxes).
  */
 int pdg_plan_sweep(int ncomp, int d, const double* nu, double theta, int* widths, double* binv);
+
+/*
+ * pdg_measure_fma_peak -- measured multiply-add throughput of the current device, for
+ * the roofline of the arithmetic-bound kernels (no counterpart in the paper: a
+ * measurement utility).  A kernel of 4 blocks of 256 threads per SM runs 8 independent
+ * FMA chains per thread, in FP64 (fp64 != 0, the FP64 pipe that bounds the FP64 passes)
+ * or FP32 (the pipe of the double-float passes); the best of three timed launches after
+ * one warm-up, CUDA events on `stream` (NULL = default stream).
+ *   tflops  receives 2 x FMAs / seconds / 1e12;  ms (may be NULL) the kernel time.
+ * Allocates and frees a small device buffer (stream-ordered).  Synchronises the stream.
+ * Errors: PDG_ERR_ARG (tflops NULL), PDG_ERR_OOM, PDG_ERR_CUDA.
+ */
+int pdg_measure_fma_peak(int fp64, double* tflops, double* ms, void* stream);
 
 /*
  * pdg_debug_fail_allocs -- host-side fault injection for tests: the next n device

@@ -297,7 +297,7 @@ void choose_shape(const int* ov, int max_threads, int nlines, int ncell, int ntf
   if (nlines < L) L = nlines < 1 ? 1 : nlines;
   if (L > max_threads) L = max_threads;
   int G = ntf;
-  const long long target = 152LL * 1024;
+  const long long target = (long long)pdg_sm_count() * 1024;
   long long s_target = (target + (long long)nlines * G - 1) / ((long long)nlines * G);
   int s_max_threads = max_threads / (L * G);
   if (s_max_threads < 1) {
@@ -552,7 +552,7 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, int o, PdgDiagPass* out) {
   // the other's FP64 work; larger cells keep one 512-thread block per SM
   const bool small_cells = c->n * c->n <= 9;
   p.threads = c->dshape[0] ? c->dshape[0] : (small_cells ? 256 : 512);
-  const int slots = p.threads <= 256 ? 304 : 152;   // blocks per wave
+  const int slots = (p.threads <= 256 ? 2 : 1) * pdg_sm_count();   // blocks per wave
   const double NN = (double)c->n * c->n, NF = 2.0 * c->n - 1.0;
   double best = 1e300;
   if (c->dshape[0]) {
@@ -664,7 +664,7 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
   }
   p.prec = c->model.prec;
   p.threads = c->cshape[0] ? c->cshape[0] : 512;
-  if (c->cshape[0]) {
+  if (c->cshape[1]) {
     p.tx = std::min(c->cshape[1], p.ncx);
     p.ty = std::min(c->cshape[2], p.ncy);
     p.tz = std::min(c->cshape[3], p.ncz);
@@ -688,6 +688,7 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
       return v;
     };
     const auto TX = tiles(p.ncx, 64), TY = tiles(p.ncy, 64), TZ = tiles(p.ncz, 64);
+    const long long sms = pdg_sm_count();   // one block per SM
     for (auto [ntx, tx] : TX)
       for (auto [nty, ty] : TY)
         for (auto [ntz, tz] : TZ) {
@@ -697,7 +698,7 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
           q.tz = tz;
           if (pdg_corner_smem(q) > 200 * 1024) continue;
           const long long blocks = 8LL * ntx * nty * ntz;
-          const long long waves = (blocks + 151) / 152;
+          const long long waves = (blocks + sms - 1) / sms;
           const double region = (double)(tx + p.c.wx) * (double)(ty + p.c.wy), out = (double)tx * ty;
           const double steps = (double)(tx + p.c.wx + ty + p.c.wy);
           const double work = tz * (out * NN + (region - out) * NFF) + p.c.wz * region * NFF +
@@ -790,7 +791,7 @@ int issue_diag(pdg_ctx* c, const PdgPassSpec& sp) {
 // SM count, the lines are spread evenly over the blocks, and lpb shrinks to the largest
 // share, so that every SM gets the same number of lines and few thread slots stay idle.
 void balance_blocks(PdgPass* p) {
-  const int sms = 152;
+  const int sms = pdg_sm_count();
   const int nb0 = (p->nlines + p->lpb - 1) / p->lpb;
   // keep the plain split (aligned line groups) when the last round of blocks already
   // keeps 95 % of the SMs busy
@@ -1378,13 +1379,20 @@ int pdg_set_source(pdg_ctx* c, const pdg_source_desc* d) {
   pdg_split(S.theta, S.theta_f[0]);
   pdg_split(S.omtheta, S.omtheta_f[0]);
   if (pen) {
-    // K(x) = K_s exp(-kappa |x - x_c|^2) at the GL points, computed on the host once
+    // K(x) = K_s exp(-kappa |x - x_c|^2) at the GL points, computed on the host once; a
+    // host allocation failure returns PDG_ERR_OOM with the source left unchanged
     std::vector<double> xs[2];
-    for (int a = 0; a < 2; ++a) {
-      xs[a].resize(c->P[a]);
-      if (pdg_get_points(c, a, xs[a].data(), xs[a].size())) return fail(c, PDG_ERR_ARG, "points");
+    std::vector<double> K;
+    try {
+      for (int a = 0; a < 2; ++a) xs[a].resize(c->P[a]);
+      K.resize((size_t)c->npoints);
+    } catch (const std::bad_alloc&) {
+      return fail(c, PDG_ERR_OOM, "no host memory for the penalisation field");
+    } catch (const std::length_error&) {
+      return fail(c, PDG_ERR_OOM, "no host memory for the penalisation field");
     }
-    std::vector<double> K((size_t)c->npoints);
+    for (int a = 0; a < 2; ++a)
+      if (pdg_get_points(c, a, xs[a].data(), xs[a].size())) return fail(c, PDG_ERR_ARG, "points");
     for (int y = 0; y < c->P[1]; ++y) {
       const double dy = xs[1][y] - d->x_c[1];
       for (int x = 0; x < c->P[0]; ++x) {
@@ -1611,8 +1619,19 @@ int pdg_timing_read(pdg_ctx* c, long long* launches, double* ms, int max_kinds) 
 }
 
 int pdg_set_launch(pdg_ctx* c, int kind, int lpb, int nseg, int ngroup) {
-  if (!c || kind < 0 || kind > 5) return PDG_ERR_ARG;
+  if (!c || kind < 0 || kind > 6) return PDG_ERR_ARG;
   c->gen++;
+  if (kind == 6) {   // corner box along x, y, z; the threads stay as kind 5 set them
+    if (lpb == 0 && nseg == 0 && ngroup == 0) {
+      c->cshape[1] = c->cshape[2] = c->cshape[3] = 0;
+      return PDG_OK;
+    }
+    if (lpb < 1 || nseg < 1 || ngroup < 1) return fail(c, PDG_ERR_ARG, "bad corner box shape");
+    c->cshape[1] = lpb;
+    c->cshape[2] = nseg;
+    c->cshape[3] = ngroup;
+    return PDG_OK;
+  }
   if (kind == 5) {
     if (lpb == 0 && nseg == 0 && ngroup == 0) {
       c->cshape[0] = c->cshape[1] = c->cshape[2] = c->cshape[3] = 0;
@@ -1837,7 +1856,13 @@ int pdg_set_option(pdg_ctx* c, int option, int value) {
 }
 
 int pdg_get_launch(const pdg_ctx* c, int kind, int* lpb, int* nseg, int* ngroup) {
-  if (!c || kind < 0 || kind > 5 || !lpb || !nseg || !ngroup) return PDG_ERR_ARG;
+  if (!c || kind < 0 || kind > 6 || !lpb || !nseg || !ngroup) return PDG_ERR_ARG;
+  if (kind == 6) {
+    *lpb = c->cshape[1];
+    *nseg = c->cshape[2];
+    *ngroup = c->cshape[3];
+    return PDG_OK;
+  }
   if (kind == 5) {
     *lpb = c->cshape[0];
     *nseg = c->cshape[1];

@@ -327,6 +327,8 @@ int pdg_launch_diag(const PdgDiagPass& p, void* stream);
 size_t pdg_diag_smem(const PdgDiagPass& p);
 
 // ---- kernels (pdg_kernels.cu) ----
+// Streaming multiprocessors of the current device (152 when no device answers).
+int pdg_sm_count();
 // All return a cudaError_t cast to int.
 int pdg_launch_pass(const PdgPass& p, void* stream);
 int pdg_launch_set_feq(double* f, long long npoints, const PdgModel& m, void* stream);

@@ -1,11 +1,32 @@
 // FP64 instantiation of the pass kernels (see pdg_pass_kernels.cuh), the dispatch by
 // precision, and the state kernels at the API boundary (equilibrium start, moments,
 // FP64 <-> double-float conversion).
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include "pdg_pass_kernels.cuh"
 
 int pdg_launch_pass_df(const PdgPass& p, void* stream);
+
+// Streaming multiprocessors of the current device, read once per device from its
+// properties; 152 (GB300) when no device answers (host-only use of the planners).
+int pdg_sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cached[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return 152;
+  }
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    return 152;
+  }
+  cached[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
 
 namespace {
 using namespace pdgdev;
@@ -186,7 +207,8 @@ __global__ void convert_kernel(double* __restrict__ f, long long n, int to_df) {
 
 int grid_for(long long n, int threads) {
   long long blocks = (n + threads - 1) / threads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  const long long cap = 32LL * pdg_sm_count();
+  if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   return (int)blocks;
 }

@@ -84,7 +84,7 @@ extern "C" int pdg_get_w_noalloc(pdg_ctx* c, double* out, size_t len) {
     return pdg_internal_fail(c, PDG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   const int threads = 256;
   long long blocks = ((long long)v.npoints + threads - 1) / threads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > 32LL * pdg_sm_count()) blocks = 32LL * pdg_sm_count();
   if (blocks < 1) blocks = 1;
   get_w_scratch_kernel<<<(int)blocks, threads, 0, v.stream>>>(v.f, scratch, v.npoints, v.m, v.nv);
   e = cudaGetLastError();

@@ -112,6 +112,7 @@ _SIGS = {
     "pdg_server_destroy": (_I, [_P]),
     "pdg_server_last_error": (ctypes.c_char_p, [_P]),
     "pdg_debug_fail_allocs": (_I, [_I]),
+    "pdg_measure_fma_peak": (_I, [_I, _P, _P, _P]),
     "pdg_plan_sweep": (_I, [_I, _I, _P, _D, _P, _P]),
     "pdg_plan_line": (_I, [_I, _D, _D, _P, _P, _P, _P]),
     "pdg_destroy": (_I, [_P]),
@@ -125,6 +126,17 @@ for _name, (_res, _args) in _SIGS.items():
     globals()[_name] = _fn
 
 EXPORTED = tuple(_SIGS)
+
+
+def measure_fma_peak(fp64=True, stream=None):
+    """pdg_measure_fma_peak: (TFLOP/s, kernel ms) of a multiply-add throughput kernel on the
+    current device, FP64 (fp64=True) or FP32."""
+    t = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    st = pdg_measure_fma_peak(1 if fp64 else 0, ctypes.addressof(t), ctypes.addressof(ms), stream)
+    if st != PDG_OK:
+        raise PdgError(st, "pdg_measure_fma_peak")
+    return t.value, ms.value
 
 
 class PdgError(RuntimeError):

@@ -15,6 +15,33 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
+def max_rel(a, b):
+    """Largest pointwise difference, relative to the largest magnitude of the reference."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def assert_parity(got, ref, tol, what=""):
+    """The parity bar of a GPU result against the oracle, in two parts:
+    the relative L2 error over the whole state (the stated tolerance), and every single
+    value within tol * max|ref| of the oracle's, so that a few wrong values at tile or box
+    starts cannot hide in the norm (a norm dilutes a local error by the square root of the
+    state size)."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    assert got.shape == ref.shape or got.size == ref.size, (what, got.shape, ref.shape)
+    got = got.reshape(ref.shape)
+    assert np.all(np.isfinite(got)), (what, "non-finite values")
+    e2 = rel_l2(got, ref)
+    em = max_rel(got, ref)
+    assert e2 <= tol, (what, "relative L2", e2, tol)
+    if em > tol:
+        idx = np.unravel_index(int(np.argmax(np.abs(got - ref))), ref.shape)
+        raise AssertionError((what, "pointwise", em, tol, "worst index", tuple(int(i) for i in idx)))
+    return e2, em
+
+
 def oracle_mesh(cfg):
     return CartesianMesh(cfg.dim, cfg.ncells, cfg.order, lengths=cfg.lengths[:cfg.dim])
 

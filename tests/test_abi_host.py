@@ -205,8 +205,20 @@ def test_corner_launch_override_and_options(pdg):
     assert s.get_launch(5) == (256, 12, 7)
     s.set_launch(5, 0, 0, 0)
     assert s.get_launch(5) == (0, 0, 0)
+    # kind 6: the box alone (x, y, z may differ); threads stay as kind 5 set them
+    for bad in ((0, 8, 8), (64, 0, 43), (64, 43, -1)):
+        with pytest.raises(pdg.PdgError):
+            s.set_launch(6, *bad)
+    s.set_launch(5, 256, 12, 7)
+    s.set_launch(6, 64, 43, 41)
+    assert s.get_launch(6) == (64, 43, 41)
+    assert s.get_launch(5) == (256, 64, 41)
+    s.set_launch(6, 0, 0, 0)
+    assert s.get_launch(6) == (0, 0, 0)
+    assert s.get_launch(5)[0] == 256
+    s.set_launch(5, 0, 0, 0)
     with pytest.raises(pdg.PdgError):
-        s.set_launch(6, 256, 8, 8)
+        s.set_launch(7, 1, 1, 1)
     s.set_option(pdg.PDG_OPT_GRAPH, 1)
     s.set_option(pdg.PDG_OPT_GRAPH, 0)
     s.set_option(pdg.PDG_OPT_COMPOSE_TT, 1)

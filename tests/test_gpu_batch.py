@@ -9,7 +9,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_common import oracle_w0, rel_l2, run_oracle
+from gpu_common import assert_parity, oracle_w0, run_oracle
 from paper_1702_00169_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -53,7 +53,7 @@ def test_batch_matches_oracle_per_instance():
     b.step([c.dt for c in cfgs], nsteps)
     for s, c, k in zip(sol, cfgs, nsteps):
         f_ref = run_oracle(c, oracle_w0(c), c.dt, k)
-        assert rel_l2(_f(s, c), f_ref) <= TOL, c
+        assert_parity(_f(s, c), f_ref, TOL, c)
     b.close()
     for s in sol:
         s.close()
@@ -108,7 +108,7 @@ def test_batched_kernel_equals_single_kernel_with_same_shape():
     b.step([c.dt], [4])
     b.close()
     np.testing.assert_array_equal(_f(s2, c), _f(s1, c))
-    assert rel_l2(_f(s1, c), run_oracle(c, oracle_w0(c), c.dt, 4)) <= TOL
+    assert_parity(_f(s1, c), run_oracle(c, oracle_w0(c), c.dt, 4), TOL)
     s1.close()
     s2.close()
 
@@ -121,7 +121,7 @@ def test_autotuned_shapes_keep_parity():
     b.autotune([c.dt for c in cfgs], reps=2)
     b.step([c.dt for c in cfgs], [3] * len(cfgs), use_graph=True)
     for s, c in zip(sol, cfgs):
-        assert rel_l2(_f(s, c), run_oracle(c, oracle_w0(c), c.dt, 3)) <= TOL
+        assert_parity(_f(s, c), run_oracle(c, oracle_w0(c), c.dt, 3), TOL)
     b.close()
     c = cfgs[0]
     s = sol[0]
@@ -129,6 +129,6 @@ def test_autotuned_shapes_keep_parity():
     s.autotune(c.dt, reps=2)
     assert s.get_launch(0)[0] > 0 and s.get_launch(1)[0] > 0
     s.step(c.dt, 3)
-    assert rel_l2(_f(s, c), run_oracle(c, oracle_w0(c), c.dt, 3)) <= TOL
+    assert_parity(_f(s, c), run_oracle(c, oracle_w0(c), c.dt, 3), TOL)
     for s in sol:
         s.close()

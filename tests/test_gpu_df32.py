@@ -11,7 +11,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_common import oracle_model, oracle_w0, rel_l2, run_gpu, run_oracle
+from gpu_common import assert_parity, oracle_model, oracle_w0, run_gpu, run_oracle
 from paper_1702_00169_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -24,7 +24,7 @@ def test_advection_workload_df32():
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, cfg.dt, cfg.steps, method="direct")
     f = run_gpu(cfg, w0, cfg.dt, cfg.steps, precision=DF)
-    assert rel_l2(f, f_ref) <= TOL
+    assert_parity(f, f_ref, TOL)
 
 
 @pytest.mark.parametrize("order", [1, 2, 3, 4])
@@ -34,7 +34,7 @@ def test_shallow_water_orders_df32(order, cfl):
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, cfg.dt, 6)
     f = run_gpu(cfg, w0, cfg.dt, 6, precision=DF)
-    assert rel_l2(f, f_ref) <= TOL
+    assert_parity(f, f_ref, TOL)
 
 
 @pytest.mark.parametrize("order", [1, 2, 3, 4])
@@ -46,11 +46,9 @@ def test_negative_time_step_df32(order):
     cfg = dataclasses.replace(W.SW_D2Q4, n_macro=(3, 2), n_sub=(3, 4), order=order)
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, -cfg.dt, 3)
-    e64 = rel_l2(run_gpu(cfg, w0, -cfg.dt, 3), f_ref)
-    e32 = rel_l2(run_gpu(cfg, w0, -cfg.dt, 3, precision=DF), f_ref)
-    print(f"dt<0 d={order}: fp64 {e64:.2e} df32 {e32:.2e}")
-    assert e64 <= TOL
-    assert e32 <= 1e-10
+    e64 = assert_parity(run_gpu(cfg, w0, -cfg.dt, 3), f_ref, TOL)
+    e32 = assert_parity(run_gpu(cfg, w0, -cfg.dt, 3, precision=DF), f_ref, 1e-10)
+    print(f"dt<0 d={order}: fp64 {e64} df32 {e32}")
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (8, 3, 2), (3, 9, 4)])
@@ -59,7 +57,7 @@ def test_launch_shapes_full_ring_df32(shape):
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, cfg.dt, 4)
     f = run_gpu(cfg, w0, cfg.dt, 4, launch={0: shape, 1: shape}, precision=DF)
-    assert rel_l2(f, f_ref) <= TOL
+    assert_parity(f, f_ref, TOL)
 
 
 @pytest.mark.parametrize("theta", [0.0, 0.75, 1.0])
@@ -67,7 +65,7 @@ def test_theta_variants_df32(theta):
     cfl = 0.1 if theta == 0.0 else 2.0
     cfg = dataclasses.replace(W.ADVECTION_D2Q4, n_macro=(3, 4), n_sub=(2, 3), order=3, theta=theta, cfl=cfl)
     w0 = oracle_w0(cfg)
-    assert rel_l2(run_gpu(cfg, w0, cfg.dt, 5, precision=DF), run_oracle(cfg, w0, cfg.dt, 5)) <= TOL
+    assert_parity(run_gpu(cfg, w0, cfg.dt, 5, precision=DF), run_oracle(cfg, w0, cfg.dt, 5), TOL)
 
 
 def test_euler_and_collapsed_df32():
@@ -76,7 +74,7 @@ def test_euler_and_collapsed_df32():
                         (dataclasses.replace(W.SW_D2Q4, n_macro=(2, 3), n_sub=(4, 2), order=2), "M2_collapsed")):
         w0 = oracle_w0(cfg)
         f_ref = run_oracle(cfg, w0, cfg.dt, 3, scheme=scheme)
-        assert rel_l2(run_gpu(cfg, w0, cfg.dt, 3, scheme=scheme, precision=DF), f_ref) <= TOL
+        assert_parity(run_gpu(cfg, w0, cfg.dt, 3, scheme=scheme, precision=DF), f_ref, TOL)
 
 
 def test_shallow_water_100_steps_reduced_df32():
@@ -84,9 +82,8 @@ def test_shallow_water_100_steps_reduced_df32():
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, cfg.dt, cfg.steps)
     f = run_gpu(cfg, w0, cfg.dt, cfg.steps, precision=DF)
-    err = rel_l2(f, f_ref)
-    print(f"df32 SW 100 steps rel L2 = {err:.3e}")
-    assert err <= TOL
+    err = assert_parity(f, f_ref, TOL)
+    print(f"df32 SW 100 steps (rel L2, pointwise) = {err}")
 
 
 def test_checkpoint_roundtrip_exact_and_moments_df32():
@@ -135,7 +132,7 @@ def test_mixed_precision_batch_and_server():
         f = s.get_f()
         np.testing.assert_array_equal(f, ref)
         fr = run_oracle(c, oracle_w0(c), c.dt, 4)
-        assert rel_l2(f.reshape(fr.shape), fr) <= TOL
+        assert_parity(f.reshape(fr.shape), fr, TOL)
     b.close()
     for s in sol:
         s.close()
@@ -150,7 +147,7 @@ def test_mixed_precision_batch_and_server():
     srv.close()
     for rid, (c, pr) in ids.items():
         w_ref = oracle_model(c).moments(run_oracle(c, oracle_w0(c), c.dt, 5))
-        assert rel_l2(got[rid].reshape(w_ref.shape), w_ref) <= TOL
+        assert_parity(got[rid].reshape(w_ref.shape), w_ref, TOL)
 
 
 def test_noalloc_rejects_df32():

@@ -9,7 +9,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_common import oracle_w0, rel_l2, run_oracle
+from gpu_common import assert_parity, oracle_w0, run_oracle
 from paper_1702_00169_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -75,7 +75,7 @@ def test_injected_oom_leaves_context_usable():
     s.step(cfg.dt, 3)
     f = s.get_f().reshape((cfg.m, 4) + tuple(reversed(cfg.npoints_axis)))
     s.close()
-    assert rel_l2(f, run_oracle(cfg, oracle_w0(cfg), cfg.dt, 3)) <= 1e-12
+    assert_parity(f, run_oracle(cfg, oracle_w0(cfg), cfg.dt, 3), 1e-12)
 
 
 def test_server_isolates_failed_admission():

@@ -7,7 +7,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_common import oracle_w0, rel_l2, run_oracle
+from gpu_common import assert_parity, oracle_w0, run_oracle
 from paper_1702_00169_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -57,4 +57,4 @@ def test_graph_recaptures_after_launch_change_and_matches_oracle():
     s.step(cfg.dt, 2)
     f = s.get_f().reshape((cfg.m, 4) + tuple(reversed(cfg.npoints_axis)))
     s.close()
-    assert rel_l2(f, run_oracle(cfg, oracle_w0(cfg), cfg.dt, 4, scheme="M2_kin")) <= 1e-12
+    assert_parity(f, run_oracle(cfg, oracle_w0(cfg), cfg.dt, 4, scheme="M2_kin"), 1e-12)

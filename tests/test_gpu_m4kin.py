@@ -7,7 +7,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_common import oracle_w0, rel_l2, run_gpu, run_oracle
+from gpu_common import assert_parity, oracle_w0, run_gpu, run_oracle
 from paper_1702_00169_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -35,7 +35,7 @@ def test_m4kin_parity(name):
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, cfg.dt, 3, scheme="M4_kin")
     f = run_gpu(cfg, w0, cfg.dt, 3, scheme="M4_kin")
-    assert rel_l2(f, f_ref) <= TOL
+    assert_parity(f, f_ref, TOL)
 
 
 def test_m4kin_df32():
@@ -43,7 +43,7 @@ def test_m4kin_df32():
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, cfg.dt, 3, scheme="M4_kin")
     f = run_gpu(cfg, w0, cfg.dt, 3, scheme="M4_kin", precision=1)
-    assert rel_l2(f, f_ref) <= 1e-10
+    assert_parity(f, f_ref, 1e-10)
 
 
 def test_m4kin_batch_equals_alone_bitwise():

@@ -8,7 +8,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_common import oracle_w0, rel_l2, run_gpu, run_oracle
+from gpu_common import assert_parity, oracle_w0, run_gpu, run_oracle
 from paper_1702_00169_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -69,5 +69,5 @@ def test_random_case(i):
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, cfg.dt, nsteps, scheme=scheme)
     f = run_gpu(cfg, w0, cfg.dt, nsteps, scheme=scheme, precision=precision, launch=launch)
-    err = rel_l2(f, f_ref)
-    assert err <= tol, (name, cfg.n_macro, cfg.n_sub, cfg.order, scheme, cfg.theta, cfg.cfl, precision, launch, err)
+    assert_parity(f, f_ref, tol, (name, cfg.n_macro, cfg.n_sub, cfg.order, scheme, cfg.theta, cfg.cfl, precision,
+                                  launch))

@@ -10,7 +10,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_common import oracle_model, oracle_w0, rel_l2, run_oracle
+from gpu_common import assert_parity, oracle_model, oracle_w0, run_oracle
 from paper_1702_00169_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -70,7 +70,7 @@ def test_mixed_results_equal_alone_and_oracle():
         alone, _ = _run([(cfg, ns)], budget, chunk=4, stagger=False)
         np.testing.assert_array_equal(mixed[i], alone[0])
         w_ref = oracle_model(cfg).moments(run_oracle(cfg, oracle_w0(cfg), cfg.dt, ns))
-        assert rel_l2(mixed[i].reshape(w_ref.shape), w_ref) <= TOL
+        assert_parity(mixed[i].reshape(w_ref.shape), w_ref, TOL)
 
 
 def test_chunking_does_not_change_results():

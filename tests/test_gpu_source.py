@@ -6,7 +6,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_common import oracle_w0, rel_l2, run_gpu, run_oracle
+from gpu_common import assert_parity, oracle_w0, run_gpu, run_oracle
 from paper_1702_00169_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -34,7 +34,7 @@ def test_sources(src, scheme):
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, cfg.dt, 4, scheme=scheme, source=src)
     f = run_gpu(cfg, w0, cfg.dt, 4, scheme=scheme, source=src)
-    assert rel_l2(f, f_ref) <= TOL
+    assert_parity(f, f_ref, TOL)
 
 
 @pytest.mark.parametrize("order", [1, 3, 4])
@@ -44,7 +44,7 @@ def test_source_orders_and_theta(order):
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, cfg.dt, 3, source=src)
     f = run_gpu(cfg, w0, cfg.dt, 3, source=src)
-    assert rel_l2(f, f_ref) <= TOL
+    assert_parity(f, f_ref, TOL)
 
 
 def test_source_df32():
@@ -52,7 +52,7 @@ def test_source_df32():
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, cfg.dt, 5, source=BOTH)
     f = run_gpu(cfg, w0, cfg.dt, 5, source=BOTH, precision=1)
-    assert rel_l2(f, f_ref) <= TOL
+    assert_parity(f, f_ref, TOL)
 
 
 def test_uniform_fall_on_gpu():

@@ -41,11 +41,19 @@ def test_aggregate_ranks_gloo_world2():
 def test_reference_arm_under_torchrun_two_ranks():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr", "127.0.0.1", "--master-port", str(29700 + os.getpid() % 200),
-           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "1"]
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "1",
+           "--cpu-cores", "2"]
+    import time
+    t0 = time.perf_counter()
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    wall = time.perf_counter() - t0
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "DOF-updates/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    # the printed time per step is measured on the sample that ran: K steps of it fit in the run
+    assert d["cpu_baseline"]["cores"] == 2
+    assert 0 < d["ms_per_step"] * d["steps"] / 1e3 < wall
+    assert abs(d["value"] - 2 * d["config"]["sample_dofs"] / (d["ms_per_step"] / 1e3)) <= 1e-9 * d["value"]

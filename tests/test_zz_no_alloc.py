@@ -8,7 +8,6 @@ ABI and checks it against pdg_get_w on two calls in a row, and that sizes beyond
 static array are rejected with a clear error.  It lives in a file collected last and
 passes both alone in a fresh process and after the other GPU tests.
 """
-import ctypes
 import dataclasses
 
 import numpy as np
@@ -74,4 +73,25 @@ def test_noalloc_rejects_sizes_beyond_the_static_array():
     r, _ = _noalloc(s, 7)
     assert r == pdg.PDG_ERR_ARG
     assert np.all(np.isfinite(s.get_w()))
+    s.close()
+
+
+def test_noalloc_refuses_lattice_and_double_float_states():
+    """The static-array read covers FP64 states of the vectorial DnQ2n models; a lattice
+    state (D2Q9 here) and a double-float state are refused with PDG_ERR_UNSUPPORTED, and
+    the regular pdg_get_w still reads them."""
+    from paper_1702_00169_gb300 import pdg
+    q9 = dataclasses.replace(W.D2Q9_ISO, n_macro=(2, 2), n_sub=(2, 2), order=2)
+    s = _solver(q9)
+    n = s.info().w_len
+    r, _ = _noalloc(s, n)
+    assert r == pdg.PDG_ERR_UNSUPPORTED
+    assert np.all(np.isfinite(s.get_w()))
+    s.close()
+    sw = dataclasses.replace(W.SW_D2Q4, n_macro=(2, 2), n_sub=(2, 2), order=2)
+    from gpu_common import oracle_w0
+    s = pdg.solver_for(sw, precision=pdg.PDG_PREC_DF32)
+    s.set_w(np.ascontiguousarray(oracle_w0(sw).reshape(-1)))
+    r, _ = _noalloc(s, s.info().w_len)
+    assert r == pdg.PDG_ERR_UNSUPPORTED
     s.close()
