@@ -185,8 +185,9 @@ def parse_args():
     ap.add_argument("--shapes", default=None,
                     help="fixed launch shapes 'lpb,nseg,ngroup/lpb,nseg,ngroup' for the transport and "
                          "last-axis passes instead of autotuning (reproduces a timed configuration)")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "df32"],
-                    help="precision of the headline run (profiling of the double-float kernels)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df32", "tf32", "tf32_df"],
+                    help="precision of the headline run (profiling of the other forms; tf32 / tf32_df: the "
+                         "tensor-core cell inverse of the D3Q15 / D3Q27 corner sweeps)")
     return ap.parse_args()
 
 
@@ -590,7 +591,7 @@ def bench_serving(args, serial=False):
     """Poisson stream of 2-D advection / shallow-water solves served with continuous
     batching under a device-memory budget (the stream at --rate, default 1000 requests at
     200 req/s), then a sweep of arrival rates on the first --sweep-requests requests of the
-    same stream (rates at 1/4, 1/2, 3/4 and 1 of the capacity the first run measured), and
+    same stream (rates at 1/4, 1/2, 3/4, 1 and 5/4 of the capacity the first run measured), and
     the highest swept rate whose p99 latency stays within twice the p99 at the lowest rate.
     serial: also time every request alone through pdg_step (single-server FIFO on the same
     arrivals).  Returns a dict."""
@@ -611,7 +612,7 @@ def bench_serving(args, serial=False):
         mean_work = float(np.mean([c.dofs * ns for _, c, ns in sub]))
         cap = main["value"] / mean_work          # requests per second the server sustained
         sweep = []
-        for frac in (0.25, 0.5, 0.75, 1.0):
+        for frac in (0.25, 0.5, 0.75, 1.0, 1.25):
             r = frac * cap
             res = _serve_stream(W.serving_requests(n=args.sweep_requests, rate=r), args, stream)
             sweep.append({"rate_req_s": r, "fraction_of_capacity": frac, "value": res["value"],
@@ -870,6 +871,36 @@ def main():
                  "gpu_launches": int(sum(launches_d))}
         del w_end_d
 
+    # ---- the tensor-core forms of the corner sweep (D3Q15 / D3Q27), FP64 state ----
+    tensor_core = None
+    if cfg.kind in ("isothermal_d3q15", "isothermal_d3q27") and args.precision == "fp64" and not args.no_mixed:
+        if s is not None:
+            s.close()
+            s = None
+        tensor_core = {}
+        k4_fp64 = kms[4] / max(1, launches[4])
+        for prec in ("tf32", "tf32_df"):
+            st_ = solver(prec)
+            ms_t, _, _, clocks_t = timed_run(st_)
+            w_end_t = st_.get_w()
+            _, launches_t, kms_t, _ = timed_run(st_, per_kernel=True)
+            st_.close()
+            avg4 = kms_t[4] / max(1, launches_t[4])
+            ms_t_max, units_t = aggregate_ranks(ms_t, dofs * args.steps)
+            tensor_core[prec] = {
+                "precision": ("split-TF32 cell inverse on the tensor cores (tcgen05), one refinement with the "
+                              "residual in " + ("FP64" if prec == "tf32" else "double-float") + "; FP64 state"),
+                "value": units_t / (ms_t_max * 1e-3), "ms_per_step": ms_t_max / args.steps,
+                "speedup_vs_fp64": ms_max / ms_t_max,
+                "rel_l2_w_vs_fp64_after_steps": float(np.linalg.norm(w_end_t - w_end) / np.linalg.norm(w_end)),
+                "corner_pass_avg_ms": avg4, "corner_pass_avg_ms_fp64": k4_fp64,
+                "corner_pass_speedup": k4_fp64 / avg4 if avg4 else None,
+                "corner_pass_algorithmic_tflops": kernel_work(4)[1] / (avg4 * 1e-3) / 1e12 if avg4 else None,
+                "clocks": clocks_t}
+            del w_end_t
+        if mixed is not None:
+            tensor_core["df32_corner_pass_avg_ms"] = mixed["kernels"].get("corner pass", {}).get("avg_ms")
+
     # ---- end-to-end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -988,6 +1019,8 @@ def main():
             "per_kernel_run_ms_per_step": ms_k / args.steps,
             "roofline": roof, "clocks": clocks, "peaks_measured": measured,
             "e2e": e2e, "cpu_baseline": cpu, "mixed": mixed, "state_finite": finite}
+    if tensor_core:
+        line["tensor_core"] = tensor_core
     if graph_run:
         line["graph_replay"] = graph_run
     if args.workload == "euler" and not args.no_forms and ws == 1 and not (args.n_macro or args.cfl):

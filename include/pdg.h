@@ -118,7 +118,7 @@ enum {
 /* State format and arithmetic. */
 enum {
   PDG_PREC_FP64 = 0, /* FP64 storage and FP64 arithmetic on every step */
-  PDG_PREC_DF32 = 1  /* double-float: the state is stored as a pair of FP32 values
+  PDG_PREC_DF32 = 1, /* double-float: the state is stored as a pair of FP32 values
                         (hi + lo, about 48 significant bits, same 8 bytes per value) and
                         every step -- transport, moments, equilibrium, relaxation -- uses
                         double-word arithmetic built from error-free FP32 transformations
@@ -128,6 +128,18 @@ enum {
                         feature: an accuracy/speed trade-off of this implementation
                         (relative L2 vs the FP64 reference <= 1e-12 on the tested
                         workloads). */
+  PDG_PREC_TF32 = 2, /* the precision form of the dense cell inverses on the tensor cores
+                        (D3Q15 / D3Q27 only; the state and every other step stay FP64):
+                        the cell solves x = B^-1 r of the cells on a wavefront of the corner
+                        sweep (B of eq. (3.7) under the theta step of eq. (3.11), Np x Np with
+                        Np = (d+1)^3) run as one (cells x Np) . (Np x Np) product on the
+                        tensor cores (tcgen05, TF32 operands, FP32 accumulation), each
+                        operand split into two TF32 parts (hi + lo), then one refinement:
+                        the residual r - B x in FP64 through the Kronecker sum B, a second
+                        split product for the correction.  Error vs the FP64 path: about
+                        1e-13 per cell solve; the tests hold it to relative L2 <= 1e-10. */
+  PDG_PREC_TF32_DFRES = 3 /* as PDG_PREC_TF32, with the refinement residual in double-float
+                             arithmetic on the FP32 pipes instead of FP64 */
 };
 
 /*
@@ -402,7 +414,10 @@ int pdg_get_schedule(pdg_ctx* ctx, double dt, int nsteps, int* ints, double* dbl
  */
 int pdg_get_w_noalloc(pdg_ctx* ctx, double* out, size_t len);
 
-/* pdg_synchronize -- wait for all work issued on the context stream.  Errors: PDG_ERR_CUDA. */
+/* pdg_synchronize -- wait for all work issued on the context stream.  Errors: PDG_ERR_CUDA,
+ * PDG_ERR_TIMEOUT (a tensor-core corner pass gave up a bounded wait for its tensor-core
+ * work, about one second; the state is incomplete; reported once, also by the host paths
+ * of pdg_get_w / pdg_get_f). */
 int pdg_synchronize(pdg_ctx* ctx);
 
 /*
@@ -453,9 +468,16 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
  *     launches, bitwise the same results, fewer launch overheads for small meshes.  Plans
  *     and scratch are prepared before the capture.  Ignored while kernel timing is on;
  *     not to be combined with a capture of the context stream by the caller.
+ *   PDG_OPT_DEBUG_TC_STALL (default 0): a test switch of the failure path of the
+ *     tensor-core corner pass (PDG_PREC_TF32 / PDG_PREC_TF32_DFRES): its one waiting thread
+ *     watches an mbarrier that nothing arrives on, with a bound of about 0.5 ms, so the
+ *     bounded wait runs out; the pass then records the timeout, waits (boundedly) for its
+ *     tensor-core work in flight, frees its tensor memory and returns, and the next
+ *     synchronising call reports PDG_ERR_TIMEOUT once.  The context stays usable: with the
+ *     switch off, later steps run normally (from the state left by the aborted passes).
  * Errors: PDG_ERR_ARG (unknown option).
  */
-enum { PDG_OPT_COMPOSE_TT = 1, PDG_OPT_GRAPH = 2 };
+enum { PDG_OPT_COMPOSE_TT = 1, PDG_OPT_GRAPH = 2, PDG_OPT_DEBUG_TC_STALL = 3 };
 int pdg_set_option(pdg_ctx* ctx, int option, int value);
 
 /* pdg_get_launch -- read the launch shape override of a kind 0..6 (zeros = heuristic). */

@@ -70,6 +70,10 @@ struct pdg_ctx {
   };
   std::vector<CornerPlan> corner_plans;
   char* cbuf = nullptr;
+  int tc = 0;                                  // corner cell inverse on the tensor cores: 0 off,
+                                               // 1 FP64 residual, 2 double-float residual
+  int* dev_err = nullptr;                      // error word of the tensor-core kernel (in cbuf)
+  int tc_stall = 0;                            // PDG_OPT_DEBUG_TC_STALL
   double* czt = nullptr;                       // corner pass: per-block +z face scratch
   // CUDA-graph replay of pdg_step (PDG_OPT_GRAPH): the captured step sequence, its key
   // (dt, nsteps, configuration generation) and the private capture / replay stream
@@ -136,6 +140,21 @@ int cuda_fail(pdg_ctx* c, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                                  \
     if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
   } while (0)
+
+// After a synchronisation of the context stream: a bounded wait of the tensor-core corner
+// kernel that ran out (its error word set) is reported once as PDG_ERR_TIMEOUT, and the
+// word is cleared.  The state of the steps in flight then is incomplete.
+int check_device_error(pdg_ctx* c) {
+  if (!c->dev_err || !c->tc) return 0;
+  int v = 0;
+  PDG_CUDA(c, cudaMemcpyAsync(&v, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PDG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (!v) return 0;
+  PDG_CUDA(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+  PDG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return fail(c, PDG_ERR_TIMEOUT,
+              "tensor-core corner pass: a bounded wait for the tensor cores ran out; the state is incomplete");
+}
 
 cudaEvent_t get_event(pdg_ctx* c) {
   if (!c->event_pool.empty()) {
@@ -275,10 +294,13 @@ long long face_line_stride(const pdg_ctx* c, int A, int b) {
   return st;
 }
 
-// Corner coefficient slots in pdg_ctx::cbuf: FP64 B^-1 (64 x 64 at most) then its
-// double-float copy, per slot.
+// Corner coefficient slots in pdg_ctx::cbuf: FP64 B^-1 (64 x 64 at most), its
+// double-float copy, then its two TF32 operands of the tensor-core kernel, per slot; after
+// the slots, the tensor-core kernel's error word.
 #define PDG_CORNER_PLANS 4
-constexpr size_t kCornerSlotBytes = 64 * 64 * (sizeof(double) + 2 * sizeof(float));
+constexpr size_t kCornerSlotBytes = 64 * 64 * (sizeof(double) + 2 * sizeof(float) + 2 * sizeof(float));
+constexpr size_t kCornerTcOffset = 64 * 64 * (sizeof(double) + 2 * sizeof(float));
+constexpr size_t kCornerErrBytes = 256;
 
 // Launch shape heuristic for one pass (lines per block, segments, field groups)
 // with at most max_threads threads; ov (if ov[0] > 0) forces the shape.
@@ -623,6 +645,10 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
     PDG_CUDA(c, cudaMemcpyAsync(base, binv.data(), sizeof(double) * NN * NN, cudaMemcpyHostToDevice, c->stream));
     PDG_CUDA(c, cudaMemcpyAsync(base + sizeof(double) * 64 * 64, binv_f.data(), sizeof(float) * 2 * NN * NN,
                                 cudaMemcpyHostToDevice, c->stream));
+    std::vector<float> ops(2 * 64 * 64);
+    const int nops = pdg_corner_tc_operands(c->n, binv.data(), ops.data());
+    PDG_CUDA(c, cudaMemcpyAsync(base + kCornerTcOffset, ops.data(), sizeof(float) * nops, cudaMemcpyHostToDevice,
+                                c->stream));
     // pageable sources: the copies above return once the data are staged
     c->corner_plans.push_back(pl);
     hit = &c->corner_plans.back();
@@ -631,6 +657,10 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
   const char* base = c->cbuf + (size_t)hit->slot * kCornerSlotBytes;
   p.binv = reinterpret_cast<const double*>(base);
   p.binv_f = reinterpret_cast<const float*>(base + sizeof(double) * 64 * 64);
+  p.binv_tc = reinterpret_cast<const float*>(base + kCornerTcOffset);
+  p.tc = c->tc;
+  p.err = c->dev_err;
+  p.stall = c->tc_stall;
   const int in = sp.dslot_in, outs = sp.dslot_in == L.diag ? L.scratch : L.diag;
   const int c0 = 4 * L.norient;   // first corner among the moving populations
   static const int sx[8] = {+1, -1, -1, +1, +1, -1, -1, +1}, sy[8] = {+1, +1, -1, -1, +1, +1, -1, -1};
@@ -663,7 +693,7 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
     }
   }
   p.prec = c->model.prec;
-  p.threads = c->cshape[0] ? c->cshape[0] : 512;
+  p.threads = c->cshape[0] && !p.tc ? c->cshape[0] : 512;   // the tensor-core kernel runs 16 warps
   if (c->cshape[1]) {
     p.tx = std::min(c->cshape[1], p.ncx);
     p.ty = std::min(c->cshape[2], p.ncy);
@@ -697,12 +727,16 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
           q.ty = ty;
           q.tz = tz;
           if (pdg_corner_smem(q) > 200 * 1024) continue;
+          if (p.tc && std::min(tx + p.c.wx, ty + p.c.wy) > 128) continue;
           const long long blocks = 8LL * ntx * nty * ntz;
           const long long waves = (blocks + sms - 1) / sms;
           const double region = (double)(tx + p.c.wx) * (double)(ty + p.c.wy), out = (double)tx * ty;
           const double steps = (double)(tx + p.c.wx + ty + p.c.wy);
-          const double work = tz * (out * NN + (region - out) * NFF) + p.c.wz * region * NFF +
-                              (double)(tz + p.c.wz) * 4.0 * NN * steps;
+          // tensor-core kernel: every cell of the region forms all its nodes and the full
+          // residual (start cells included), and a step carries six barriers and two MMA waits
+          const double work = p.tc ? (double)(tz + p.c.wz) * (region * NN + 16.0 * NN * steps)
+                                   : tz * (out * NN + (region - out) * NFF) + p.c.wz * region * NFF +
+                                         (double)(tz + p.c.wz) * 4.0 * NN * steps;
           const double cost = (double)waves * work;
           if (cost < best) {
             best = cost;
@@ -718,6 +752,8 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
   }
   if (pdg_corner_smem(p) > 200 * 1024) return fail(c, PDG_ERR_UNSUPPORTED, "corner box too large");
   if (p.threads < 64 || p.threads > 512) return fail(c, PDG_ERR_ARG, "corner pass: threads per block");
+  if (p.tc && std::min(p.tx + p.c.wx, p.ty + p.c.wy) > 128)
+    return fail(c, PDG_ERR_UNSUPPORTED, "tensor-core corner pass: more than 128 cells on an anti-diagonal");
   // +z face scratch of the launch (grown on demand; cudaFree waits for the device)
   const size_t words = pdg_corner_scratch(p);
   if (words > c->czt_cap) {
@@ -1200,8 +1236,14 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
   if (d->scheme != PDG_SCHEME_M2 && d->scheme != PDG_SCHEME_M2_COLLAPSED && d->scheme != PDG_SCHEME_M2KIN &&
       d->scheme != PDG_SCHEME_M4KIN)
     return fail(c, PDG_ERR_ARG, "unknown scheme");
-  if (d->precision != PDG_PREC_FP64 && d->precision != PDG_PREC_DF32)
+  if (d->precision != PDG_PREC_FP64 && d->precision != PDG_PREC_DF32 && d->precision != PDG_PREC_TF32 &&
+      d->precision != PDG_PREC_TF32_DFRES)
     return fail(c, PDG_ERR_UNSUPPORTED, "precision not available");
+  const bool tcp = d->precision == PDG_PREC_TF32 || d->precision == PDG_PREC_TF32_DFRES;
+  if (tcp && d->kind != PDG_MODEL_ISOTHERMAL_D3Q15 && d->kind != PDG_MODEL_ISOTHERMAL_D3Q27)
+    return fail(c, PDG_ERR_UNSUPPORTED,
+                "the tensor-core precision forms apply to the dense cell inverses of the corner sweeps "
+                "(D3Q15, D3Q27)");
   if (!(d->lambda > 0.0 && std::isfinite(d->lambda))) return fail(c, PDG_ERR_ARG, "lambda must be > 0");
   if (!std::isfinite(d->omega) || d->omega == 0.0) return fail(c, PDG_ERR_ARG, "omega must be finite and != 0");
   if (!(d->theta >= 0.0 && d->theta <= 1.0)) return fail(c, PDG_ERR_ARG, "theta must be in [0, 1]");
@@ -1231,16 +1273,20 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) {
     const double s = (i % 2 == 0) ? 1.0 : -1.0;
     M.cadv[i] = 1.0 / (2.0 * c->dim) + s * d->a[i / 2] / (2.0 * d->lambda);
   }
-  M.prec = d->precision;
+  // the tensor-core forms keep an FP64 state: every kernel but the corner pass is the FP64 one
+  M.prec = tcp ? PDG_PREC_FP64 : d->precision;
   pdg_model_constants(&M);
   if ((q15 || q27) && !c->cbuf) {
-    cudaError_t e = cudaMalloc((void**)&c->cbuf, PDG_CORNER_PLANS * kCornerSlotBytes);
+    cudaError_t e = cudaMalloc((void**)&c->cbuf, PDG_CORNER_PLANS * kCornerSlotBytes + kCornerErrBytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       c->cbuf = nullptr;
       return fail(c, PDG_ERR_OOM, std::string("corner coefficients: ") + cudaGetErrorString(e));
     }
+    c->dev_err = reinterpret_cast<int*>(c->cbuf + PDG_CORNER_PLANS * kCornerSlotBytes);
+    PDG_CUDA(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
   }
+  c->tc = d->precision == PDG_PREC_TF32 ? 1 : (d->precision == PDG_PREC_TF32_DFRES ? 2 : 0);
   c->corner_plans.clear();
   // a different number of fields or a different state format invalidates the state
   if (c->has_model && (c->model.m != M.m || c->model.nf != M.nf || c->model.prec != M.prec)) {
@@ -1312,7 +1358,10 @@ int pdg_get_f(pdg_ctx* c, double* out, size_t len, int on_device) {
     int e = pdg_launch_convert(c->f, (long long)need, 1, (void*)c->stream);
     if (e) return cuda_fail(c, (cudaError_t)e, "convert launch");
   }
-  if (!on_device) PDG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (!on_device) {
+    PDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (int r = check_device_error(c)) return r;
+  }
   return PDG_OK;
 }
 
@@ -1342,6 +1391,7 @@ int pdg_get_w(pdg_ctx* c, double* out, size_t len, int on_device) {
   if (!on_device) {
     PDG_CUDA(c, cudaMemcpyAsync(out, dst, sizeof(double) * need, cudaMemcpyDeviceToHost, c->stream));
     PDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (int r = check_device_error(c)) return r;
   }
   return PDG_OK;
 }
@@ -1588,7 +1638,7 @@ int pdg_get_schedule(pdg_ctx* c, double dt, int nsteps, int* ints, double* dbls,
 int pdg_synchronize(pdg_ctx* c) {
   if (!c) return PDG_ERR_ARG;
   PDG_CUDA(c, cudaStreamSynchronize(c->stream));
-  return PDG_OK;
+  return check_device_error(c);
 }
 
 int pdg_timing_enable(pdg_ctx* c, int enable) {
@@ -1850,6 +1900,9 @@ int pdg_set_option(pdg_ctx* c, int option, int value) {
       return PDG_OK;
     case PDG_OPT_GRAPH:
       c->use_graph = value != 0;
+      return PDG_OK;
+    case PDG_OPT_DEBUG_TC_STALL:
+      c->tc_stall = value != 0;
       return PDG_OK;
   }
   return fail(c, PDG_ERR_ARG, "unknown option");

@@ -224,6 +224,10 @@ struct PdgCornerCoef {
   double rtheta, c1, theta, omtheta, kx, ky, kz;
   int wx, wy, wz;   // upwind start widths (cells) along x, y, z
   float rtheta_f[1][2], c1_f[1][2], theta_f[1][2], omtheta_f[1][2], kx_f[1][2], ky_f[1][2], kz_f[1][2];
+  // theta nu_a K (n x n, row-major) for a = x, y, z: B x = x + sum_a (theta nu_a K) x along a,
+  // the residual stencil of the tensor-core form (FP64 and as float pairs)
+  double kt[3][PDG_MAXN_CORNER * PDG_MAXN_CORNER];
+  float kt_f[3][PDG_MAXN_CORNER * PDG_MAXN_CORNER][2];
 };
 
 // Launch descriptor of a corner pass: npop (<= 8) populations with traversal signs
@@ -237,8 +241,14 @@ struct PdgCornerPass {
   long long sa, sb, sc;            // point strides along x, y, z
   int tx, ty, tz, ntx, nty, ntz;   // tile shape and counts
   int threads, prec;
+  int tc;                          // 0: FP64 / double-float kernel; 1: tensor-core cell inverse with
+                                   // an FP64 residual; 2: with a double-float residual
   const double* binv;              // device: NN x NN row-major (FP64)
   const float* binv_f;             // device: NN x NN (hi, lo) pairs (double-float)
+  const float* binv_tc;            // device: Binv split into two TF32 MMA operands (tc != 0)
+  int* err;                        // device error word of the tensor-core kernel (tc != 0)
+  int stall;                       // test switch: the MMA wait watches an mbarrier nothing arrives
+                                   // on, with a bound of about 0.5 ms, so it runs out
   double* zt;                      // device scratch: per block [ty + wy][tx + wx][n^2] +z faces
   // inflow axes (per axis a: per[a] = 1 periodic); boundary data fb[a] = [2 sides][nent][lines]
   // of the faces normal to a, each population's side and entry there; a face point's line
@@ -315,9 +325,16 @@ int pdg_plan_diag(int d, double nux, double nuy, double theta, PdgDiagCoef* c);
 int pdg_plan_corner(int d, double nux, double nuy, double nuz, double theta, PdgCornerCoef* c, double* binv,
                     float* binv_f);
 
-// ---- kernels (pdg_corner.cu) ----
+// ---- kernels (pdg_corner.cu, pdg_corner_tc.cu) ----
 int pdg_launch_corner(const PdgCornerPass& p, void* stream);
 size_t pdg_corner_smem(const PdgCornerPass& p);
+int pdg_launch_corner_tc(const PdgCornerPass& p, size_t smem, void* stream);
+size_t pdg_corner_tc_smem(const PdgCornerPass& p);
+// The tensor-core operands of a corner plan: for n = d + 1, NN = n^3, K = NN rounded up to
+// a multiple of 8 and N = max(16, K), two arrays (TF32 high parts, then low parts) of N x K
+// floats each in the MMA's core-matrix layout (pdg_tc.cuh), zero beyond NN.  Returns the
+// number of floats written (2 N K).
+int pdg_corner_tc_operands(int n, const double* binv, float* out);
 // 8-byte words of the +z face scratch (PdgCornerPass::zt) of a launch
 size_t pdg_corner_scratch(const PdgCornerPass& p);
 

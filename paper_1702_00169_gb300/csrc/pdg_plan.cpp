@@ -501,6 +501,12 @@ int pdg_plan_corner(int d, double nux, double nuy, double nuz, double theta, Pdg
   pdg_split(c->kx, c->kx_f[0]);
   pdg_split(c->ky, c->ky_f[0]);
   pdg_split(c->kz, c->kz_f[0]);
+  const double nua[3] = {nux, nuy, nuz};
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < n * n; ++i) {
+      c->kt[a][i] = theta * nua[a] * K[i];
+      pdg_split(c->kt[a][i], c->kt_f[a][i]);
+    }
   return 0;
 }
 

@@ -22,9 +22,12 @@ PDG_MODEL_ISOTHERMAL_D3Q15, PDG_MODEL_ISOTHERMAL_D3Q27 = 5, 6
 PDG_SCHEME_M2, PDG_SCHEME_M2_COLLAPSED, PDG_SCHEME_M2KIN, PDG_SCHEME_M4KIN = 0, 1, 2, 3
 PDG_PREC_FP64 = 0
 PDG_PREC_DF32 = 1
-PRECISION = {"fp64": PDG_PREC_FP64, "df32": PDG_PREC_DF32}
+PDG_PREC_TF32 = 2
+PDG_PREC_TF32_DFRES = 3
+PRECISION = {"fp64": PDG_PREC_FP64, "df32": PDG_PREC_DF32, "tf32": PDG_PREC_TF32, "tf32_df": PDG_PREC_TF32_DFRES}
 PDG_OPT_COMPOSE_TT = 1
 PDG_OPT_GRAPH = 2
+PDG_OPT_DEBUG_TC_STALL = 3
 
 KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER,
         "isothermal_d2q9": PDG_MODEL_ISOTHERMAL_D2Q9, "isothermal_d3q19": PDG_MODEL_ISOTHERMAL_D3Q19,

@@ -22,12 +22,21 @@ def max_rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-def assert_parity(got, ref, tol, what=""):
+# Pointwise bar of time-reversed runs (dt < 0).  The backward theta step is
+# anti-dissipative (the inverse of the forward one, eq. (3.13)), so it amplifies rounding:
+# the oracle alone, given the shallow-water parity case perturbed by one ulp, moves by up to
+# 4.4e-12 max|f| after three backward steps (1.5e-13 to 4.4e-12 for degrees 1-4, against
+# 4e-15 to 9e-15 forward).  Two correct FP64 evaluations that round differently therefore
+# differ by that much pointwise; the relative L2 bar stays 1e-12.
+TOL_POINTWISE_REVERSED = 1e-11
+
+
+def assert_parity(got, ref, tol, what="", tol_pt=None):
     """The parity bar of a GPU result against the oracle, in two parts:
     the relative L2 error over the whole state (the stated tolerance), and every single
-    value within tol * max|ref| of the oracle's, so that a few wrong values at tile or box
-    starts cannot hide in the norm (a norm dilutes a local error by the square root of the
-    state size)."""
+    value within tol * max|ref| of the oracle's (tol_pt * max|ref| when given), so that a
+    few wrong values at tile or box starts cannot hide in the norm (a norm dilutes a local
+    error by the square root of the state size)."""
     got = np.asarray(got)
     ref = np.asarray(ref)
     assert got.shape == ref.shape or got.size == ref.size, (what, got.shape, ref.shape)
@@ -36,9 +45,10 @@ def assert_parity(got, ref, tol, what=""):
     e2 = rel_l2(got, ref)
     em = max_rel(got, ref)
     assert e2 <= tol, (what, "relative L2", e2, tol)
-    if em > tol:
+    tp = tol if tol_pt is None else tol_pt
+    if em > tp:
         idx = np.unravel_index(int(np.argmax(np.abs(got - ref))), ref.shape)
-        raise AssertionError((what, "pointwise", em, tol, "worst index", tuple(int(i) for i in idx)))
+        raise AssertionError((what, "pointwise", em, tp, "worst index", tuple(int(i) for i in idx)))
     return e2, em
 
 

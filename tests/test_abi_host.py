@@ -268,3 +268,22 @@ def test_server_host_paths(pdg):
     assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
     assert srv.pending() == (0, 0)
     srv.close()
+
+
+def test_tensor_core_precisions_only_for_corner_lattices(pdg):
+    """PDG_PREC_TF32 / PDG_PREC_TF32_DFRES apply to the dense cell inverses of the corner
+    sweeps (D3Q15 / D3Q27); every other model refuses them before allocating anything, and a
+    refused call leaves the context without a model."""
+    for dim, kind in ((2, "advection"), (2, "shallow_water"), (3, "euler"), (2, "isothermal_d2q9"),
+                      (3, "isothermal_d3q19")):
+        s = pdg.Solver(dim, (2,) * dim, (2,) * dim, 2)
+        for prec in (pdg.PDG_PREC_TF32, pdg.PDG_PREC_TF32_DFRES):
+            with pytest.raises(pdg.PdgError) as e:
+                s.set_model(kind, 2.0, precision=prec)
+            assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
+            assert "corner" in pdg.pdg_last_error(s.ctx).decode()
+        with pytest.raises(pdg.PdgError) as e:
+            s.set_model(kind, 2.0, precision=4)
+        assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
+        s.close()
+    assert pdg.PRECISION["tf32"] == pdg.PDG_PREC_TF32 == 2 and pdg.PRECISION["tf32_df"] == 3

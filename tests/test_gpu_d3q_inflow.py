@@ -96,3 +96,14 @@ def test_inflow_schemes_df32():
     assert_parity(f, f_ref, TOL)
     f, f_ref = _run(cfg, (True, False, True), 2, scheme="M2_kin")
     assert_parity(f, f_ref, TOL)
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+@pytest.mark.parametrize("lat,periodic", [("q15", (False, True, False)), ("q27", (True, False, True)),
+                                          ("q27", (False, False, False))])
+def test_tensor_core_corner_pass_with_inflow(lat, periodic, precision):
+    """The tensor-core precision forms (split-TF32 cell inverse with an FP64 or a
+    double-float refinement residual) on inflow axes, at the mixed-precision bar 1e-10."""
+    cfg = _cfg(lat, (2, 2, 3), (2, 3, 2), 2)
+    f, f_ref = _run(cfg, periodic, 2, precision=precision)
+    assert_parity(f, f_ref, 1e-10)

@@ -237,3 +237,35 @@ def test_m4kin_fourth_order_in_time():
                for N in (8, 16, 32)]
         e = [np.abs(res[0] - res[1]).max(), np.abs(res[1] - res[2]).max()]
         assert lo < e[0] / e[1] < hi, (scheme, e)
+
+
+def test_backward_steps_amplify_rounding_forward_steps_do_not():
+    """The conditioning behind the pointwise bar of time-reversed GPU runs: the backward theta
+    step (the inverse of the forward one, eq. (3.13)) is anti-dissipative, so a one-ulp
+    perturbation of the input grows to ~1e-12 of max|f| in three backward M2 steps, while
+    three forward steps keep it at ~1e-14.  Two correct FP64 evaluations that round
+    differently can therefore differ pointwise by more than 1e-12 only when run backwards."""
+    import dataclasses
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from gpu_common import TOL_POINTWISE_REVERSED, oracle_mesh, oracle_model, oracle_w0
+    from paper_1702_00169_gb300 import workloads as W
+    worst_b = []
+    for order in (2, 3):
+        cfg = dataclasses.replace(W.SW_D2Q4, n_macro=(3, 2), n_sub=(3, 4), order=order)
+        model = oracle_model(cfg)
+        tr = S.Transporter(oracle_mesh(cfg), model, theta=cfg.theta, method="bloch")
+        f0 = S.initial_state(model, oracle_w0(cfg))
+        rng = np.random.default_rng(order)
+        pert = f0 * (1 + 2.0 ** -52 * rng.standard_normal(f0.shape))
+        for sign, store in ((-1, worst_b), (1, None)):
+            a = S.run(f0, tr, model, sign * cfg.dt, 3, cfg.omega)
+            b = S.run(pert, tr, model, sign * cfg.dt, 3, cfg.omega)
+            e = np.max(np.abs(a - b)) / np.max(np.abs(a))
+            if store is None:
+                assert e < 1e-13, (order, e)
+            else:
+                store.append(e)
+    assert max(worst_b) > 1e-12
+    assert max(worst_b) < 0.5 * TOL_POINTWISE_REVERSED
