@@ -1,0 +1,272 @@
+// The pass schedule of the palindromic compositions.
+//
+// Schedule.  M2(dt) = T(dt/2) C(dt) T(dt/2) (Section 3.2) with T the product of
+// the per-population transports; transports along different axes act on
+// different populations, so they commute exactly.  For D axes with last axis L,
+// nsteps steps are issued as
+//   for a < L: pass_a [T(dt/2)]
+//   repeat nsteps:  pass_L [T(dt/2), C, T(dt/2)]
+//                   for a < L: pass_a [T(dt/2), T(dt/2)]   (last step: [T(dt/2)])
+// which applies to every population exactly the sequence of the naive order.
+// The collapsed scheme of Section 5.1 merges interior half steps into T(dt).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "pdg_ctx.h"
+
+namespace pdgapi {
+
+// Fill the launch-dependent fields of a coefficient set for segments of a line of
+// N cells.  Returns 0, or -1 when the periodic system is singular (|beta| = 1 with
+// beta^N = 1).
+int finish_coef(PdgCoef* C, int N, int S, bool periodic) {
+  const int Lbase = N / S;
+  const double ab = std::fabs(C->beta);
+  C->rev = ab > 1.0 ? 1 : 0;
+  C->gamma = C->rev ? 1.0 / C->beta : 0.0;
+  const double r = C->rev ? C->gamma : C->beta;
+  const int W = pdg_plan_window(r);
+  C->W = W;
+  C->full = (W > Lbase) ? 1 : 0;
+  C->betaL0 = std::pow(r, (double)Lbase);
+  C->betaL1 = std::pow(r, (double)(Lbase + 1));
+  const double rN = std::pow(r, (double)N);
+  if (periodic && !(std::fabs(1.0 - rN) > 1e-12)) return -1;
+  C->inv_ring = periodic ? 1.0 / (1.0 - rN) : 0.0;
+  pdg_coef_split(C);
+  return 0;
+}
+
+// Window of a coefficient set in the stable direction.
+int stable_window(const PdgCoef& C) {
+  const double ab = std::fabs(C.beta);
+  return pdg_plan_window(ab > 1.0 ? 1.0 / C.beta : C.beta);
+}
+
+int plan_line_coef(const pdg_ctx* c, int axis, double delta, PdgCoef* C) {
+  const double nu = 2.0 * c->model.lambda * delta / c->h[axis];
+  return pdg_plan_coef(c->order, nu, c->theta, C);
+}
+
+// Kind of a pass: 0 = transport only, 1 = contains the collision.
+int pass_kind(const PdgPassSpec& sp) {
+  for (int o = 0; o < sp.nops; ++o)
+    if (sp.op[o] == PDG_OP_C) return 1;
+  return 0;
+}
+
+PdgPassSpec spec(int axis, int nops, const int* ops, const int* ci, const PdgCoef* cs, int ncs) {
+  PdgPassSpec sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.axis = axis;
+  sp.nops = nops;
+  for (int o = 0; o < nops; ++o) {
+    sp.op[o] = ops[o];
+    sp.opcoef[o] = ci[o];
+  }
+  sp.ncs = ncs;
+  for (int i = 0; i < ncs; ++i) sp.cs[i] = cs[i];
+  return sp;
+}
+
+// The line passes of nsteps palindromic steps (see the schedule at the top of this file).
+int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+  out.clear();
+  if (nsteps <= 0) return PDG_OK;
+  const int D = c->dim, L = D - 1;
+  out.reserve((2 * (size_t)nsteps + 1) * (size_t)D);   // at least the passes of every scheme
+  PdgCoef half[3], full[3];
+  for (int a = 0; a < D; ++a) {
+    if (plan_line_coef(c, a, 0.5 * dt, &half[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
+    if (plan_line_coef(c, a, dt, &full[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
+    PdgCoef t0 = half[a], t1 = full[a];
+    if (finish_coef(&t0, c->N[a], 1, c->periodic[a]) ||
+        (c->scheme == PDG_SCHEME_M2_COLLAPSED && finish_coef(&t1, c->N[a], 1, c->periodic[a])))
+      return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
+    if (!c->periodic[a] && (t0.rev || (c->scheme == PDG_SCHEME_M2_COLLAPSED && t1.rev)))
+      return fail(c, PDG_ERR_UNSUPPORTED, "time steps with |beta| > 1 on an inflow (non-periodic) axis");
+  }
+  const int T = PDG_OP_T, C = PDG_OP_C;
+  const int z1[1] = {0}, z2[2] = {0, 0}, z3[3] = {0, 0, 0};
+  const int o1[1] = {T}, o2[2] = {T, T}, o3[3] = {T, C, T};
+  if (c->scheme == PDG_SCHEME_M2KIN) {
+    // T(dt/4) C T(dt/2) C T(dt/4) per step.  The collisions split the run into the
+    // transport segments seg_0 = T(q), then alternately T(h) and T(q) T(q) (the trailing
+    // quarter of a step and the leading quarter of the next), and seg_2n = T(q).  Each
+    // collision runs in a last-axis pass together with the last axis' transports around
+    // it; the other axes transport each segment in passes between the collisions.
+    PdgCoef qc[3], hc[3];
+    for (int a = 0; a < D; ++a) {
+      if (plan_line_coef(c, a, 0.25 * dt, &qc[a]) || plan_line_coef(c, a, 0.5 * dt, &hc[a]))
+        return fail(c, PDG_ERR_ARG, "singular transport step");
+      PdgCoef t0 = qc[a], t1 = hc[a];
+      if (finish_coef(&t0, c->N[a], 1, c->periodic[a]) || finish_coef(&t1, c->N[a], 1, c->periodic[a]))
+        return fail(c, PDG_ERR_ARG, "singular periodic transport system (|beta| = 1)");
+      if (!c->periodic[a] && (t0.rev || t1.rev))
+        return fail(c, PDG_ERR_UNSUPPORTED, "time steps with |beta| > 1 on an inflow (non-periodic) axis");
+    }
+    const int nseg = 2 * nsteps + 1;
+    // segment j: number of sub-steps and their coefficient index (0 = quarter, 1 = half)
+    auto seg_n = [&](int j) { return (j == 0 || j == nseg - 1) ? 1 : ((j % 2 == 1) ? 1 : 2); };
+    auto seg_ci = [&](int j) { return (j % 2 == 1) ? 1 : 0; };
+    auto other_axes = [&](int j) {
+      for (int a = 0; a < L; ++a) {
+        PdgCoef cs[2] = {qc[a], hc[a]};
+        const int ops[2] = {T, T}, ci[2] = {seg_ci(j), seg_ci(j)};
+        out.push_back(spec(a, seg_n(j), ops, ci, cs, 2));
+      }
+    };
+    PdgCoef csL[2] = {qc[L], hc[L]};
+    other_axes(0);
+    {
+      const int ops[3] = {T, C, T}, ci[3] = {seg_ci(0), 0, seg_ci(1)};
+      out.push_back(spec(L, 3, ops, ci, csL, 2));
+    }
+    for (int j = 1; j < nseg - 1; ++j) {
+      other_axes(j);
+      int ops[3] = {C, T, T}, ci[3] = {0, seg_ci(j + 1), seg_ci(j + 1)};
+      out.push_back(spec(L, 1 + seg_n(j + 1), ops, ci, csL, 2));
+    }
+    other_axes(nseg - 1);
+    return PDG_OK;
+  }
+  if (c->scheme == PDG_SCHEME_M2) {
+    for (int a = 0; a < L; ++a) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
+    for (int s = 0; s < nsteps; ++s) {
+      out.push_back(spec(L, 3, o3, z3, &half[L], 1));
+      for (int a = 0; a < L; ++a) out.push_back(spec(a, s < nsteps - 1 ? 2 : 1, o2, z2, &half[a], 1));
+    }
+  } else {
+    for (int a = 0; a < L; ++a) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
+    for (int s = 0; s < nsteps; ++s) {
+      PdgCoef cs[2] = {half[L], full[L]};
+      const int ops[2] = {T, C}, ci[2] = {s == 0 ? 0 : 1, 0};
+      out.push_back(spec(L, 2, ops, ci, cs, 2));
+      for (int a = 0; a < L; ++a) out.push_back(spec(a, 1, o1, z1, s < nsteps - 1 ? &full[a] : &half[a], 1));
+    }
+    out.push_back(spec(L, 1, o1, z1, &half[L], 1));
+  }
+  return PDG_OK;
+}
+
+// The full pass list.  D2Q9 adds the diagonal transports: the sub-steps between two
+// collisions (and before the first / after the last) run as diagonal passes issued
+// just before the line pass that holds the next collision (transports of different
+// populations commute); each diagonal pass swaps the slot set of populations 5-8, the
+// collision reads them where they are, and a final copy returns them to slots 5-8.
+int build_schedule_one(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+  if (int r = build_line_schedule(c, dt, nsteps, out)) return r;
+  Lattice Lat;
+  if (!lattice_of(c->model.kind, &Lat) || nsteps <= 0) return PDG_OK;
+  if (!(dt > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "diagonal transport needs dt > 0");
+  if (c->src.flags && c->scheme == PDG_SCHEME_M2KIN)
+    return fail(c, PDG_ERR_UNSUPPORTED, "sources are defined for M2 and M2_collapsed");
+  // diagonal sub-steps of each transport segment, in order
+  std::vector<std::vector<double>> seg;
+  const double h = 0.5 * dt, q = 0.25 * dt;
+  if (c->scheme == PDG_SCHEME_M2) {
+    seg.push_back({h});
+    for (int s = 1; s < nsteps; ++s) seg.push_back({h, h});
+    seg.push_back({h});
+  } else if (c->scheme == PDG_SCHEME_M2_COLLAPSED) {
+    seg.push_back({h});
+    for (int s = 1; s < nsteps; ++s) seg.push_back({dt});
+    seg.push_back({h});
+  } else {
+    seg.push_back({q});
+    for (int s = 0; s < nsteps; ++s) {
+      seg.push_back({h});
+      if (s < nsteps - 1) seg.push_back({q, q});
+    }
+    seg.push_back({q});
+  }
+  std::vector<PdgPassSpec> res;
+  res.reserve(out.size() + 3 * seg.size() + 1);
+  int slot = Lat.diag;
+  size_t ci = 0;
+  auto diag = [&](double delta) {
+    PdgPassSpec d;
+    std::memset(&d, 0, sizeof(d));
+    d.axis = -1;
+    d.ddelta = delta;
+    d.dslot_in = slot;
+    res.push_back(d);
+    slot = (slot == Lat.diag) ? Lat.scratch : Lat.diag;
+  };
+  for (auto sp : out) {
+    if (pass_kind(sp)) {
+      if (ci >= seg.size()) return fail(c, PDG_ERR_ARG, "internal: schedule segments");
+      for (double dl : seg[ci]) diag(dl);
+      ++ci;
+      sp.dslot = slot;
+      sp.sdelta = c->src.flags ? 0.5 * dt : 0.0;   // S(dt/2) C(dt) S(dt/2)
+    }
+    res.push_back(sp);
+  }
+  if (ci + 1 != seg.size()) return fail(c, PDG_ERR_ARG, "internal: schedule segments");
+  for (double dl : seg[ci]) diag(dl);
+  if (slot != Lat.diag) {
+    PdgPassSpec cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.axis = -2;   // copy slots 9-12 back to 5-8
+    res.push_back(cp);
+  }
+  out.swap(res);
+  return PDG_OK;
+}
+
+// The pass list of nsteps steps of the context's scheme.  M4^kin (PDG_SCHEME_M4KIN) is the
+// triple jump M2^kin(g1 dt) M2^kin(g2 dt) M2^kin(g1 dt) per step (Section 3.2: palindromic
+// compositions of M2^kin; H. Yoshida, Phys. Lett. A 150 (1990)), g1 = 1/(2 - 2^(1/3)),
+// g2 = 1 - 2 g1 < 0: three M2^kin schedules per step, the middle one backwards in time.
+int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+  if (c->scheme != PDG_SCHEME_M4KIN) return build_schedule_one(c, dt, nsteps, out);
+  Lattice L;
+  if (lattice_of(c->model.kind, &L))
+    return fail(c, PDG_ERR_UNSUPPORTED, "M4^kin has a backward sub-step: not available for diagonal velocities");
+  if (c->src.flags) return fail(c, PDG_ERR_UNSUPPORTED, "sources are defined for M2 and M2_collapsed");
+  const double g1 = 1.0 / (2.0 - std::cbrt(2.0)), g2 = 1.0 - 2.0 * g1;
+  out.clear();
+  std::vector<PdgPassSpec> part;
+  c->scheme = PDG_SCHEME_M2KIN;
+  int r = PDG_OK;
+  try {
+    out.reserve(3 * (size_t)nsteps * 3 * (size_t)c->dim);
+    for (int s = 0; s < nsteps && r == PDG_OK; ++s)
+      for (double g : {g1, g2, g1}) {
+        if ((r = build_schedule_one(c, g * dt, 1, part)) != PDG_OK) break;
+        out.insert(out.end(), part.begin(), part.end());
+      }
+  } catch (...) {
+    c->scheme = PDG_SCHEME_M4KIN;
+    throw;
+  }
+  c->scheme = PDG_SCHEME_M4KIN;
+  return r;
+}
+
+// build_schedule for the C entry points: the pass list lives in host memory (about 2.3 KB
+// per pass, a few passes per step), and a failed allocation is reported as PDG_ERR_OOM
+// instead of letting the exception cross the C ABI.
+int build_schedule_checked(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+  try {
+    return build_schedule(c, dt, nsteps, out);
+  } catch (const std::bad_alloc&) {
+    std::vector<PdgPassSpec>().swap(out);
+    return fail(c, PDG_ERR_OOM, "no host memory for the pass list of this many steps: split the call");
+  } catch (const std::length_error&) {
+    std::vector<PdgPassSpec>().swap(out);
+    return fail(c, PDG_ERR_OOM, "no host memory for the pass list of this many steps: split the call");
+  }
+}
+
+}  // namespace pdgapi

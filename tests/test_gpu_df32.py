@@ -11,7 +11,7 @@ import dataclasses
 import numpy as np
 import pytest
 
-from gpu_common import TOL_POINTWISE_REVERSED, assert_parity, oracle_model, oracle_w0, run_gpu, run_oracle
+from gpu_common import TOL_POINTWISE_REVERSED, TOL_POINTWISE_REVERSED_DF, assert_parity, oracle_model, oracle_w0, run_gpu, run_oracle
 from paper_1702_00169_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -47,7 +47,7 @@ def test_negative_time_step_df32(order):
     w0 = oracle_w0(cfg)
     f_ref = run_oracle(cfg, w0, -cfg.dt, 3)
     e64 = assert_parity(run_gpu(cfg, w0, -cfg.dt, 3), f_ref, TOL, tol_pt=TOL_POINTWISE_REVERSED)
-    e32 = assert_parity(run_gpu(cfg, w0, -cfg.dt, 3, precision=DF), f_ref, 1e-10)
+    e32 = assert_parity(run_gpu(cfg, w0, -cfg.dt, 3, precision=DF), f_ref, 1e-10, tol_pt=TOL_POINTWISE_REVERSED_DF)
     print(f"dt<0 d={order}: fp64 {e64} df32 {e32}")
 
 

@@ -4,7 +4,7 @@ Two parts of the library run on the host and are checked through the C ABI witho
 the planner (csrc/pdg_plan.cpp: Gauss-Lobatto rule, derivative matrix, per-cell line
 coefficients, windows, the tile and box cell inverses and their truncation widths), checked
 by `tests/test_abi_host.py` and `tests/test_sweep_algorithms.py`, and the pass schedule of
-the palindromic compositions (csrc/pdg_api.cu), checked by `tests/test_schedule_host.py`.
+the palindromic compositions (csrc/pdg_schedule.cu), checked by `tests/test_schedule_host.py`.
 Each case plants one plausible mistake in a copy of one source file, compiles that copy,
 links it with the library's other objects into a private library, and runs the checking
 test files against it; the case passes when they fail (pytest exit 1).  The unmodified
@@ -26,7 +26,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PKG = "paper_1702_00169_gb300"
-PLAN, API = "pdg_plan.cpp", "pdg_api.cu"
+PLAN, API = "pdg_plan.cpp", "pdg_schedule.cu"
 PINS = {PLAN: ["test_abi_host.py", "test_sweep_algorithms.py"], API: ["test_schedule_host.py"]}
 
 # (id, text, replacement[, file]), the text occurring once in the file (default pdg_plan.cpp)
