@@ -149,11 +149,6 @@ struct Shape {
   int lpb, nseg, ngroup;
 };
 
-// Status of a C++ exception that reached an exported entry point (every one of them catches
-// all): PDG_ERR_OOM for a failed host allocation, PDG_ERR_ARG for anything else; the message
-// goes to *err when given.  No exception crosses the C ABI.
-int abi_exception(std::string* err) noexcept;
-
 // Pending injected allocation failures (pdg_debug_fail_allocs).
 extern std::atomic<int> g_fail_allocs;
 

@@ -276,6 +276,12 @@ struct PdgStateView {
 bool pdg_internal_view(const pdg_ctx* c, PdgStateView* v);
 // Records msg as the context's last error and returns code.
 int pdg_internal_fail(pdg_ctx* c, int code, const std::string& msg);
+namespace pdgapi {
+// Status of a C++ exception that reached an exported entry point (every one of them catches
+// all): PDG_ERR_OOM for a failed host allocation, PDG_ERR_ARG for anything else; the message
+// goes to *err when given.  No exception crosses the C ABI.
+int abi_exception(std::string* err) noexcept;
+}  // namespace pdgapi
 // Take the state of c from the stream-ordered pool (no device-wide synchronisation on free).
 void pdg_internal_set_async_alloc(pdg_ctx* c, bool on);
 // pdg_set_w without the final stream synchronisation (pageable sources are staged

@@ -62,7 +62,7 @@ cudaError_t scratch_address(double** out) {
 
 }  // namespace
 
-extern "C" int pdg_get_w_noalloc(pdg_ctx* c, double* out, size_t len) {
+extern "C" int pdg_get_w_noalloc(pdg_ctx* c, double* out, size_t len) try {
   if (!c) return PDG_ERR_ARG;
   PdgStateView v;
   if (!pdg_internal_view(c, &v)) return pdg_internal_fail(c, PDG_ERR_STATE, "no state");
@@ -93,4 +93,6 @@ extern "C" int pdg_get_w_noalloc(pdg_ctx* c, double* out, size_t len) {
   if (e != cudaSuccess)
     return pdg_internal_fail(c, PDG_ERR_CUDA, std::string("pdg_get_w_noalloc: ") + cudaGetErrorString(e));
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(nullptr);
 }

@@ -511,7 +511,7 @@ int pdg_plan_corner(int d, double nux, double nuy, double nuz, double theta, Pdg
 }
 
 // Inspection entry point of the line plan (declared in pdg.h).
-int pdg_plan_line(int d, double nu, double theta, double* E, double* q, double* scalars, int* windows) {
+int pdg_plan_line(int d, double nu, double theta, double* E, double* q, double* scalars, int* windows) try {
   if (d < 1 || d + 1 > PDG_MAXN || !(theta >= 0.0 && theta <= 1.0) || !std::isfinite(nu)) return PDG_ERR_ARG;
   PdgCoef c;
   if (pdg_plan_coef(d, nu, theta, &c)) return PDG_ERR_ARG;
@@ -532,10 +532,12 @@ int pdg_plan_line(int d, double nu, double theta, double* E, double* q, double* 
     windows[1] = W2;
   }
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(nullptr);
 }
 
 // Inspection entry point of the tile and box plans (declared in pdg.h).
-int pdg_plan_sweep(int ncomp, int d, const double* nu, double theta, int* widths, double* binv) {
+int pdg_plan_sweep(int ncomp, int d, const double* nu, double theta, int* widths, double* binv) try {
   if (!nu || !widths || (ncomp != 2 && ncomp != 3)) return PDG_ERR_ARG;
   if (d < 1 || d + 1 > (ncomp == 2 ? PDG_MAXN : PDG_MAXN_CORNER)) return PDG_ERR_ARG;
   if (!(theta > 0.0 && theta <= 1.0)) return PDG_ERR_ARG;
@@ -562,4 +564,6 @@ int pdg_plan_sweep(int ncomp, int d, const double* nu, double theta, int* widths
   if (binv)
     for (int i = 0; i < NN * NN; ++i) binv[i] = b[i];
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(nullptr);
 }

@@ -69,10 +69,12 @@ int measure(double* tflops, double* ms_out, cudaStream_t st) {
 
 }  // namespace
 
-extern "C" int pdg_measure_fma_peak(int fp64, double* tflops, double* ms, void* stream) {
+extern "C" int pdg_measure_fma_peak(int fp64, double* tflops, double* ms, void* stream) try {
   if (!tflops) return PDG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   int r = fp64 ? measure<double>(tflops, ms, st) : measure<float>(tflops, ms, st);
   if (r != PDG_OK) cudaGetLastError();
   return r;
+} catch (...) {
+  return pdgapi::abi_exception(nullptr);
 }

@@ -95,7 +95,7 @@ extern "C" {
 const char* pdg_server_last_error(const pdg_server* s) { return s ? s->err.c_str() : "null server"; }
 
 int pdg_server_create(pdg_server** out, size_t mem_budget_bytes, int chunk_steps, int use_graph,
-                      void* cuda_stream) {
+                      void* cuda_stream) try {
   if (!out) return PDG_ERR_ARG;
   *out = nullptr;
   if (mem_budget_bytes == 0 || chunk_steps < 1) return PDG_ERR_ARG;
@@ -108,11 +108,13 @@ int pdg_server_create(pdg_server** out, size_t mem_budget_bytes, int chunk_steps
   s->t0 = std::chrono::steady_clock::now();
   *out = s;
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(nullptr);
 }
 
 double pdg_server_now(const pdg_server* s) { return s ? now_s(s) : 0.0; }
 
-int pdg_server_submit(pdg_server* s, const pdg_request* req, long long* id) {
+int pdg_server_submit(pdg_server* s, const pdg_request* req, long long* id) try {
   if (!s || !req || !req->w0) return PDG_ERR_ARG;
   if (req->dim < 1 || req->dim > 3 || req->order < 1 || req->order > 4 || req->nsteps < 0 ||
       !(req->dt == req->dt))
@@ -152,9 +154,11 @@ int pdg_server_submit(pdg_server* s, const pdg_request* req, long long* id) {
   s->waiting.push_back(r);
   if (id) *id = r->id;
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(s ? &s->err : nullptr);
 }
 
-int pdg_server_iterate(pdg_server* s, int* n_resident, int* n_done) {
+int pdg_server_iterate(pdg_server* s, int* n_resident, int* n_done) try {
   if (!s) return PDG_ERR_ARG;
   // 1. admission, first come first served, while the memory budget allows
   while (!s->waiting.empty()) {
@@ -234,17 +238,21 @@ int pdg_server_iterate(pdg_server* s, int* n_resident, int* n_done) {
   if (n_resident) *n_resident = (int)s->resident.size();
   if (n_done) *n_done = finished;
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(s ? &s->err : nullptr);
 }
 
-int pdg_server_pending(const pdg_server* s, int* n_waiting, int* n_resident) {
+int pdg_server_pending(const pdg_server* s, int* n_waiting, int* n_resident) try {
   if (!s) return PDG_ERR_ARG;
   if (n_waiting) *n_waiting = (int)s->waiting.size();
   if (n_resident) *n_resident = (int)s->resident.size();
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(nullptr);
 }
 
 int pdg_server_poll(pdg_server* s, long long* ids, double* t_arrival, double* t_admit, double* t_done, int max,
-                    int* count) {
+                    int* count) try {
   if (!s || max < 0 || !count) return PDG_ERR_ARG;
   int n = 0;
   while (n < max && !s->done.empty()) {
@@ -258,9 +266,11 @@ int pdg_server_poll(pdg_server* s, long long* ids, double* t_arrival, double* t_
   }
   *count = n;
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(s ? &s->err : nullptr);
 }
 
-int pdg_server_cancel(pdg_server* s, long long id) {
+int pdg_server_cancel(pdg_server* s, long long id) try {
   if (!s) return PDG_ERR_ARG;
   for (auto it = s->waiting.begin(); it != s->waiting.end(); ++it)
     if ((*it)->id == id) {
@@ -283,9 +293,11 @@ int pdg_server_cancel(pdg_server* s, long long id) {
       return PDG_OK;
     }
   return sfail(s, PDG_ERR_STATE, "no waiting or resident request with this id");
+} catch (...) {
+  return pdgapi::abi_exception(s ? &s->err : nullptr);
 }
 
-int pdg_server_result(pdg_server* s, long long id, double* w, size_t len) {
+int pdg_server_result(pdg_server* s, long long id, double* w, size_t len) try {
   if (!s || !w) return PDG_ERR_ARG;
   auto fit = s->failed.find(id);
   if (fit != s->failed.end()) {
@@ -304,19 +316,23 @@ int pdg_server_result(pdg_server* s, long long id, double* w, size_t len) {
   std::memcpy(w, it->second.data(), sizeof(double) * len);
   s->results.erase(it);
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(s ? &s->err : nullptr);
 }
 
 int pdg_server_stats(const pdg_server* s, long long* iterations, long long* dof_updates, long long* completed,
-                     size_t* peak_bytes) {
+                     size_t* peak_bytes) try {
   if (!s) return PDG_ERR_ARG;
   if (iterations) *iterations = s->iterations;
   if (dof_updates) *dof_updates = s->dof_updates;
   if (completed) *completed = s->completed;
   if (peak_bytes) *peak_bytes = s->peak_bytes;
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(nullptr);
 }
 
-int pdg_server_destroy(pdg_server* s) {
+int pdg_server_destroy(pdg_server* s) try {
   if (!s) return PDG_OK;
   cudaStreamSynchronize(s->stream);
   if (s->batch) pdg_batch_destroy(s->batch);
@@ -325,6 +341,8 @@ int pdg_server_destroy(pdg_server* s) {
   cudaStreamSynchronize(s->stream);
   delete s;
   return PDG_OK;
+} catch (...) {
+  return pdgapi::abi_exception(s ? &s->err : nullptr);
 }
 
 }  // extern "C"

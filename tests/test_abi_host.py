@@ -287,3 +287,26 @@ def test_tensor_core_precisions_only_for_corner_lattices(pdg):
         assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
         s.close()
     assert pdg.PRECISION["tf32"] == pdg.PDG_PREC_TF32 == 2 and pdg.PRECISION["tf32_df"] == 3
+
+
+def test_every_exported_status_function_catches_all_exceptions():
+    """No C++ exception crosses the C ABI: every exported function that returns a status is a
+    function-try-block whose handler maps the exception to a status (a failed host
+    allocation to PDG_ERR_OOM)."""
+    import glob
+    import re
+    csrc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1702_00169_gb300", "csrc")
+    seen = set()
+    for fn in glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cpp")):
+        src = open(fn).read()
+        for m in re.finditer(r'^(?:extern "C" )?int (pdg_[a-z_0-9]+)\(([^{;]*?)\)( try)? \{', src, re.M):
+            name = m.group(1)
+            if name.startswith(("pdg_internal_", "pdg_plan_", "pdg_launch_", "pdg_corner_", "pdg_diag_",
+                                "pdg_batch_threads", "pdg_sm_count", "pdg_fault_take", "pdg_model_variant")) \
+                    and name not in ("pdg_plan_line", "pdg_plan_sweep"):
+                continue
+            assert m.group(3), f"{os.path.basename(fn)}: {name} is not a function-try-block"
+            seen.add(name)
+    header = open(os.path.join(os.path.dirname(csrc), "..", "include", "pdg.h")).read()
+    declared = set(re.findall(r'^int (pdg_[a-z_0-9]+)\(', header, re.M))
+    assert declared <= seen, sorted(declared - seen)
