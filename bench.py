@@ -124,13 +124,16 @@ def collision_flops(kind, dim):
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from the ncu captures
-# summarised under profiles/: (workload, kernel kind, precision, launch shape) -> bytes.
-# The launch shape is (lines per block, segments, field groups) of that pass kind, or None
-# for the diagonal / corner passes (shape chosen by the host planner).  Only kernels that
-# have not changed since their capture are listed; the others report null.
-TRAFFIC = {("shallow_water_d2q4_64x64x8x8_d3", 1, "fp64", (8, 4, 6)): 1551.61e6,
-           ("shallow_water_d2q4_64x64x8x8_d3", 1, "fp64", (8, 16, 2)): 1793.12e6,
-           ("isothermal_d2q9_64x64x8x8_d3", 3, "fp64", None): 279.41e6}
+# summarised under profiles/: (workload, kernel kind, precision, lines per block) -> bytes.
+# Lines per block (the first number of the line-pass launch shape, which sets how much of a
+# block's lines stays in L2 between the operations of a pass) or None for the diagonal /
+# corner passes (shape chosen by the host planner).  Only kernels that have not changed
+# since their capture are listed; the others report null.  The Euler D3Q6 figure was
+# captured at 192^3 points (1.7 GB state, larger than L2) and scaled by the 8 times more
+# points of a 384^3 launch (profiles/pass_kernel_fp64_euler_d3q6_384cube.md).
+TRAFFIC = {("shallow_water_d2q4_64x64x8x8_d3", 1, "fp64", 8): 1793.12e6,
+           ("isothermal_d2q9_64x64x8x8_d3", 3, "fp64", None): 279.41e6,
+           ("euler_d3q6_32c3x4c3_d2", 1, "fp64", 8): 8 * 5092.82e6}
 
 SOURCES = {"gravity": dict(gravity=(0.0, -1.0)),
            "penalization": dict(K_s=300.0, kappa=40.0, x_c=(0.25, 0.5), w_s=(1.0, 0.0, 0.0)),
@@ -968,7 +971,7 @@ def main():
             "peak_measured": measured.get("fp64_tflops"),
             "frac_of_measured": (achieved_tflops / measured["fp64_tflops"]) if measured.get("fp64_tflops") else None,
             "traffic": (TRAFFIC.get((cfg.name, k_dom, args.precision,
-                                     tuple(s_shape[k_dom]) if k_dom in (0, 1) else None))
+                                     s_shape[k_dom][0] if k_dom in (0, 1) else None))
                         if args.source == "none" else None),
             "kernel": kinds[k_dom], "avg_launch_ms": avg_ms, "launches": launches[k_dom],
             "algorithmic_flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
