@@ -188,6 +188,12 @@ def parse_args():
     ap.add_argument("--shapes", default=None,
                     help="fixed launch shapes 'lpb,nseg,ngroup/lpb,nseg,ngroup' for the transport and "
                          "last-axis passes instead of autotuning (reproduces a timed configuration)")
+    ap.add_argument("--resident", type=int, default=0,
+                    help="1: line passes run the line-resident kernel (PDG_OPT_RESIDENT)")
+    ap.add_argument("--caxis", type=int, default=-1,
+                    help="axis whose pass carries the collision (PDG_OPT_COLLISION_AXIS; -1 = last)")
+    ap.add_argument("--rshapes", default=None,
+                    help="line-resident launch shapes 'lpb,nseg,ngroup/lpb,nseg,ngroup' (kinds 7 / 8)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df32", "tf32", "tf32_df"],
                     help="precision of the headline run (profiling of the other forms; tf32 / tf32_df: the "
                          "tensor-core cell inverse of the D3Q15 / D3Q27 corner sweeps)")
@@ -729,6 +735,13 @@ def main():
                      theta=cfg.theta, scheme=args.scheme, precision=pdg.PRECISION[precision])
         if args.source != "none":
             sv.set_source(**SOURCES[args.source])
+        if args.resident:
+            sv.set_option(pdg.PDG_OPT_RESIDENT, 1)
+        if args.caxis >= 0:
+            sv.set_option(pdg.PDG_OPT_COLLISION_AXIS, args.caxis)
+        if args.rshapes:
+            for kind, sh in enumerate(args.rshapes.split("/")):
+                sv.set_launch(7 + kind, *[int(x) for x in sh.split(",")])
         return sv
 
     s = solver(args.precision)
@@ -1011,6 +1024,8 @@ def main():
                               if cfg.dofs * 8 > 126e6 else
                               f"state {cfg.dofs * 8 / 1e6:.1f} MB fits in L2: L2-resident (small parity workload)"),
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                       "collision_axis": args.caxis if args.caxis >= 0 else cfg.dim - 1,
+                       "line_resident": bool(args.resident),
                        "launch_shapes": {"autotuned": not args.no_autotune and not args.shapes,
                                          "transport_pass": list(shape0),
                                          "last_axis_pass": list(shape1)}},

@@ -447,6 +447,9 @@ int pdg_timing_read(pdg_ctx* ctx, long long* launches, double* ms, int max_kinds
  *   at least (d+1)^3), nseg = output cells per box along x and y, ngroup = along z.
  * kind 6 = the corner box alone: lpb, nseg, ngroup = output cells per box along x, y, z
  *   (>= 1 each); the threads per block stay as kind 5 set them (512 when unset).
+ * kind 7 / 8 = the line-resident kernel (PDG_OPT_RESIDENT) for pass kinds 0 / 1: lines per
+ *   block, segments per line, field groups (lpb*nseg*ngroup <= 512); a shape whose staged
+ *   lines exceed ~220 KB of shared memory makes the pass run the streaming kernel.
  * All zeros restores the built-in heuristic (kind 6: the box only).  Used by the
  * autotuners and by tests that force a box shape.
  * Errors: PDG_ERR_ARG.
@@ -475,12 +478,31 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
  *     tensor-core work in flight, frees its tensor memory and returns, and the next
  *     synchronising call reports PDG_ERR_TIMEOUT once.  The context stays usable: with the
  *     switch off, later steps run normally (from the state left by the aborted passes).
- * Errors: PDG_ERR_ARG (unknown option).
+ *   PDG_OPT_RESIDENT (default 0): line passes of periodic axes of the DnQ2n models (no
+ *     source stage) run the line-resident kernel: a block copies its lines -- every
+ *     population the pass touches, over the whole line -- into shared memory, runs the
+ *     pass's operations there and writes the lines back once, so each value crosses DRAM
+ *     once each way per pass and the block requests all of its data at once.  The same
+ *     operations in the same order as the streaming kernel (the segment closure may round
+ *     differently when the launch shape differs).  Passes whose staged lines do not fit
+ *     run the streaming kernel.
+ *   PDG_OPT_COLLISION_AXIS (default -1): the axis whose line pass carries the collision,
+ *     T(dt/2) C T(dt/2); -1 = the last axis.  Transports along different axes commute, so
+ *     any axis gives the same scheme (results equal up to rounding); axis 0 has
+ *     unit-stride lines, which the line-resident kernel stages most cheaply.  Lattice
+ *     models keep the last axis (other values: PDG_ERR_UNSUPPORTED).
+ * Errors: PDG_ERR_ARG (unknown option, axis out of range), PDG_ERR_UNSUPPORTED.
  */
-enum { PDG_OPT_COMPOSE_TT = 1, PDG_OPT_GRAPH = 2, PDG_OPT_DEBUG_TC_STALL = 3 };
+enum {
+  PDG_OPT_COMPOSE_TT = 1,
+  PDG_OPT_GRAPH = 2,
+  PDG_OPT_DEBUG_TC_STALL = 3,
+  PDG_OPT_RESIDENT = 4,
+  PDG_OPT_COLLISION_AXIS = 5
+};
 int pdg_set_option(pdg_ctx* ctx, int option, int value);
 
-/* pdg_get_launch -- read the launch shape override of a kind 0..6 (zeros = heuristic). */
+/* pdg_get_launch -- read the launch shape override of a kind 0..8 (zeros = heuristic). */
 int pdg_get_launch(const pdg_ctx* ctx, int kind, int* lpb, int* nseg, int* ngroup);
 
 /*

@@ -111,6 +111,8 @@ int pdg_set_model(pdg_ctx* c, const pdg_model_desc* d) try {
   if ((q15 || q27) && c->n > PDG_MAXN_CORNER)
     return fail(c, PDG_ERR_UNSUPPORTED, "D3Q15 / D3Q27 support degrees 1 to 3");
   if (lat && !(d->theta > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "diagonal velocities need theta > 0");
+  if (lat && c->caxis >= 0 && c->caxis != c->dim - 1)
+    return fail(c, PDG_ERR_UNSUPPORTED, "lattice models carry the collision in the last-axis pass");
   PdgModel M{};
   M.kind = d->kind;
   M.dim = c->dim;
@@ -508,8 +510,21 @@ int pdg_timing_read(pdg_ctx* c, long long* launches, double* ms, int max_kinds) 
 }
 
 int pdg_set_launch(pdg_ctx* c, int kind, int lpb, int nseg, int ngroup) try {
-  if (!c || kind < 0 || kind > 6) return PDG_ERR_ARG;
+  if (!c || kind < 0 || kind > 8) return PDG_ERR_ARG;
   c->gen++;
+  if (kind == 7 || kind == 8) {   // line-resident kernel, pass kinds 0 / 1
+    int* slot = c->rshape[kind - 7];
+    if (lpb == 0 && nseg == 0 && ngroup == 0) {
+      slot[0] = slot[1] = slot[2] = 0;
+      return PDG_OK;
+    }
+    if (lpb < 1 || nseg < 1 || ngroup < 1 || (long long)lpb * nseg * ngroup > 512)
+      return fail(c, PDG_ERR_ARG, "bad line-resident launch shape");
+    slot[0] = lpb;
+    slot[1] = nseg;
+    slot[2] = ngroup;
+    return PDG_OK;
+  }
   if (kind == 6) {   // corner box along x, y, z; the threads stay as kind 5 set them
     if (lpb == 0 && nseg == 0 && ngroup == 0) {
       c->cshape[1] = c->cshape[2] = c->cshape[3] = 0;
@@ -612,6 +627,17 @@ int pdg_set_option(pdg_ctx* c, int option, int value) try {
     case PDG_OPT_DEBUG_TC_STALL:
       c->tc_stall = value != 0;
       return PDG_OK;
+    case PDG_OPT_RESIDENT:
+      c->resident = value != 0;
+      return PDG_OK;
+    case PDG_OPT_COLLISION_AXIS: {
+      Lattice Lat;
+      if (value < -1 || value >= c->dim) return fail(c, PDG_ERR_ARG, "collision axis out of range");
+      if (value >= 0 && value != c->dim - 1 && c->has_model && lattice_of(c->model.kind, &Lat))
+        return fail(c, PDG_ERR_UNSUPPORTED, "lattice models carry the collision in the last-axis pass");
+      c->caxis = value;
+      return PDG_OK;
+    }
   }
   return fail(c, PDG_ERR_ARG, "unknown option");
 } catch (...) {
@@ -619,7 +645,13 @@ int pdg_set_option(pdg_ctx* c, int option, int value) try {
 }
 
 int pdg_get_launch(const pdg_ctx* c, int kind, int* lpb, int* nseg, int* ngroup) try {
-  if (!c || kind < 0 || kind > 6 || !lpb || !nseg || !ngroup) return PDG_ERR_ARG;
+  if (!c || kind < 0 || kind > 8 || !lpb || !nseg || !ngroup) return PDG_ERR_ARG;
+  if (kind == 7 || kind == 8) {
+    *lpb = c->rshape[kind - 7][0];
+    *nseg = c->rshape[kind - 7][1];
+    *ngroup = c->rshape[kind - 7][2];
+    return PDG_OK;
+  }
   if (kind == 6) {
     *lpb = c->cshape[1];
     *nseg = c->cshape[2];

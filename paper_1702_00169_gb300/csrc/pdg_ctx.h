@@ -61,6 +61,9 @@ struct pdg_ctx {
                                                // 1 FP64 residual, 2 double-float residual
   int* dev_err = nullptr;                      // error word of the tensor-core kernel (in cbuf)
   int tc_stall = 0;                            // PDG_OPT_DEBUG_TC_STALL
+  int resident = 0;                            // PDG_OPT_RESIDENT
+  int rshape[2][3] = {{0, 0, 0}, {0, 0, 0}};   // line-resident shapes per pass kind (0 = heuristic)
+  int caxis = -1;                              // PDG_OPT_COLLISION_AXIS (-1: the last axis)
   double* czt = nullptr;                       // corner pass: per-block +z face scratch
   // CUDA-graph replay of pdg_step (PDG_OPT_GRAPH): the captured step sequence, its key
   // (dt, nsteps, configuration generation) and the private capture / replay stream
@@ -187,6 +190,7 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
 int issue_diag(pdg_ctx* c, const PdgPassSpec& sp);
 void balance_blocks(PdgPass* p);
 int issue_pass(pdg_ctx* c, const PdgPassSpec& sp);
+bool resident_shape(const pdg_ctx* c, const PdgPassSpec& sp, int kind, int* shape);
 int capture_steps(pdg_ctx* c, double dt, int nsteps, const std::vector<PdgPassSpec>& sched);
 int bfail(pdg_batch* b, int code, const std::string& m);
 std::vector<Shape> shape_candidates(int max_threads, int ncell, int ntf, int W);

@@ -143,6 +143,8 @@ struct PdgPass {
   int prec;                    // PDG_PREC_* of the state and arithmetic
   int periodic;                // 1: periodic lines; 0: inflow boundary data fb
   int dslot;                   // D2Q9 collision: state slot of population 5 (5 or 9)
+  int resident;                // 1: the line-resident kernel (the block's lines staged in shared
+                               //    memory for the whole op list; periodic DnQ2n passes)
   const double* fb;            // non-periodic: inflow values [2 sides][fbnent][nlines] (state format)
   int fbnent;                  // entries per side of fb (m; 3 for D2Q9)
   int fbent[2 * PDG_MAXM];     // entry of each transported population within its side

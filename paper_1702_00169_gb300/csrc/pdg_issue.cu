@@ -517,6 +517,57 @@ void balance_blocks(PdgPass* p) {
   p->lpb = (int)(((long long)p->nlines + nb - 1) / nb);
 }
 
+// Launch shape of the line-resident kernel (pass_resident_kernel) for a line pass, or false
+// when the pass runs the streaming kernel: the option is off, the axis has inflow faces,
+// the model is a lattice or has a source stage, or the staged lines of one block would
+// not fit in shared memory.  Shape: the kind's override (launch kinds 7 / 8) or one line
+// per block on unit-stride lines (two when they stay under ~110 KB, two blocks per SM) and
+// four adjacent lines on strided ones (32-byte runs of the fastest axis; fewer when the
+// staged lines pass ~220 KB), segments of about eight cells (never shorter than the
+// transport window), all transported fields in flight, at most 512 threads.
+bool resident_shape(const pdg_ctx* c, const PdgPassSpec& sp, int kind, int* shape) {
+  Lattice Lat;
+  if (!c->resident || sp.axis < 0 || !c->periodic[sp.axis] || c->src.flags || lattice_of(c->model.kind, &Lat))
+    return false;
+  const int axis = sp.axis, npl = c->P[axis], ncell = c->N[axis], ntf = 2 * c->model.m;
+  const size_t nload = kind ? (size_t)c->model.nf : (size_t)ntf;
+  int W = 1;
+  for (int i = 0; i < sp.ncs; ++i) W = std::max(W, stable_window(sp.cs[i]));
+  auto smem = [&](int lpb, int nseg) {
+    return sizeof(double) * (nload * (size_t)lpb * (size_t)(npl + 1) + 3 * (size_t)ntf * nseg * lpb);
+  };
+  const size_t cap = 220 * 1024;
+  int lpb, nseg, ngroup;
+  const int* ov = c->rshape[kind];
+  if (ov[0] > 0) {
+    lpb = ov[0];
+    nseg = std::min(ov[1], ncell);
+    ngroup = std::min(ov[2], ntf);
+  } else {
+    nseg = std::max(1, ncell / 8);
+    if (ncell / nseg < W) nseg = std::max(1, ncell / W);
+    ngroup = ntf;
+    if (axis == 0) {
+      lpb = smem(2, nseg) <= 110 * 1024 ? 2 : 1;
+    } else {
+      lpb = 4;
+      while (lpb > 1 && smem(lpb, nseg) > cap) lpb /= 2;
+    }
+    while (lpb * nseg * ngroup > 512 && ngroup > 1) {
+      int g = ngroup - 1;
+      while (g > 1 && ntf % g) --g;
+      ngroup = g;
+    }
+    while (lpb * nseg * ngroup > 512 && nseg > 1) nseg = (nseg + 1) / 2;
+  }
+  if (lpb < 1 || nseg < 1 || ngroup < 1 || lpb * nseg * ngroup > 512 || smem(lpb, nseg) > cap) return false;
+  if (axis > 0 && lpb < 2 && ov[0] <= 0) return false;   // strided lines: at least 16-byte runs
+  shape[0] = lpb;
+  shape[1] = nseg;
+  shape[2] = ngroup;
+  return true;
+}
+
 int issue_pass(pdg_ctx* c, const PdgPassSpec& sp) {
   if (sp.axis == -2) {
     Lattice L;
@@ -529,7 +580,13 @@ int issue_pass(pdg_ctx* c, const PdgPassSpec& sp) {
   if (sp.axis < 0) return issue_diag(c, sp);
   PdgPass p;
   const int kind = pass_kind(sp);
-  if (int r = make_pass(c, sp, 512, c->launch[kind], &p)) return r;
+  int rs[3];
+  if (resident_shape(c, sp, kind, rs)) {
+    if (int r = make_pass(c, sp, 512, rs, &p)) return r;
+    p.resident = 1;
+  } else {
+    if (int r = make_pass(c, sp, 512, c->launch[kind], &p)) return r;
+  }
   balance_blocks(&p);
   return launch_timed(c, p, kind);
 }

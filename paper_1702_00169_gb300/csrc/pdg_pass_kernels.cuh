@@ -43,11 +43,120 @@ __global__ void __launch_bounds__(512, 1) pass_kernel_lat(const __grid_constant_
   pass_body<NP, MV, T>(p, blockIdx.x, sm);
 }
 
+// Line-resident form of the pass kernel: the block's lines (every field the pass touches,
+// over the whole line length) are copied into shared memory with coalesced cp.async, the op
+// list runs there unchanged (pass_body on a copy of the descriptor, in shared memory, that
+// points at the staged lines), and the lines are written back once.  Each value of the
+// block's lines crosses DRAM once each way, and the block requests all of its data at the
+// start, instead of one cell per thread and sweep step through global memory.  Periodic
+// lines of the DnQ2n models (no inflow data, no lattice slots, no source stage).
+// Shared memory: nload fields x lpb lines x (npl + 1) values (the + 1 puts consecutive
+// lines on different banks), then the segment aggregates of pass_body.
+__device__ __forceinline__ bool pass_has_collision(const PdgPass& p) {
+  for (int o = 0; o < p.nops; ++o)
+    if (p.op[o] == PDG_OP_C) return true;
+  return false;
+}
+
+__device__ __forceinline__ void cp_async8_line(double* smem, const double* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Copies between the block's lines in global memory and their shared-memory image: unit-
+// stride lines with consecutive threads on consecutive points, strided lines with
+// consecutive threads on consecutive lines (adjacent points of the fastest axis).
+template <bool LOAD>
+__device__ __forceinline__ void resident_copy(const PdgPass& p, double* lines, int l0, int cnt, int nload,
+                                              bool all) {
+  const int LS = p.npl + 1;
+  const long long FS = (long long)p.lpb * LS;
+  const long long total = (long long)nload * cnt * p.npl;
+  for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+    int l, pt, j;
+    if (p.stride == 1) {
+      pt = (int)(i % p.npl);
+      const long long r = i / p.npl;
+      l = (int)(r % cnt);
+      j = (int)(r / cnt);
+    } else {
+      l = (int)(i % cnt);
+      const long long r = i / cnt;
+      pt = (int)(r % p.npl);
+      j = (int)(r / p.npl);
+    }
+    const int fld = all ? j : p.tfield[j];
+    double* g = p.f + (long long)fld * p.field_stride + line_base(p, l0 + l) + (long long)pt * p.stride;
+    double* sp = lines + j * FS + (long long)l * LS + pt;
+    if (LOAD)
+      cp_async8_line(sp, g);
+    else
+      *g = *sp;
+  }
+}
+
+template <int NP, int MV, class T>
+__global__ void __launch_bounds__(512) pass_resident_kernel(const __grid_constant__ PdgPass p) {
+  extern __shared__ double sm[];
+  __shared__ PdgPass q;
+  int l0, cnt;
+  block_lines(p, blockIdx.x, &l0, &cnt);
+  const bool all = pass_has_collision(p);
+  const int nload = all ? p.model.nf : p.ntf;
+  const int LS = p.npl + 1;
+  const long long FS = (long long)p.lpb * LS;
+  double* lines = sm;
+  double* aux = sm + (size_t)nload * FS;
+  resident_copy<true>(p, lines, l0, cnt, nload, all);
+  {   // the descriptor, copied word by word by all threads
+    const int* src = reinterpret_cast<const int*>(&p);
+    int* dst = reinterpret_cast<int*>(&q);
+    for (int i = threadIdx.x; i < (int)(sizeof(PdgPass) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    q.f = lines;
+    q.field_stride = FS;
+    q.stride = 1;
+    q.lineA = 0x40000000;
+    q.s1 = LS;
+    q.s2 = 0;
+    q.nlines = cnt;
+    q.nblocks = 0;
+    if (!all)
+      for (int phi = 0; phi < p.ntf; ++phi) q.tfield[phi] = phi;
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  pass_body<NP, MV, T>(q, 0, aux);
+  __syncthreads();
+  resident_copy<false>(p, lines, l0, cnt, nload, all);
+}
+
+// Dynamic shared memory (bytes) of the line-resident kernel for a pass descriptor.
+inline size_t resident_smem(const PdgPass& p, int nf) {
+  bool all = false;
+  for (int o = 0; o < p.nops; ++o)
+    if (p.op[o] == PDG_OP_C) all = true;
+  const size_t nload = all ? (size_t)nf : (size_t)p.ntf;
+  return sizeof(double) * (nload * (size_t)p.lpb * (size_t)(p.npl + 1) + 3 * (size_t)p.ntf * p.nseg * p.lpb);
+}
+
 template <int NP, int MV, class T>
 int launch_pass_t(const PdgPass& p, cudaStream_t st) {
   const int threads = p.lpb * p.nseg * p.ngroup;
-  const size_t smem = sizeof(double) * 3 * (size_t)p.ntf * p.nseg * p.lpb;
   const int blocks = p.nblocks > 0 ? p.nblocks : (p.nlines + p.lpb - 1) / p.lpb;
+  if constexpr (MV != MV_D2Q9 && MV != MV_D3Q19 && MV != MV_D3Q15 && MV != MV_D3Q27) {
+    if (p.resident) {
+      const size_t smem = resident_smem(p, p.model.nf);
+      auto kern = pass_resident_kernel<NP, MV, T>;
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return (int)e;
+      kern<<<blocks, threads, smem, st>>>(p);
+      return (int)cudaGetLastError();
+    }
+  }
+  const size_t smem = sizeof(double) * 3 * (size_t)p.ntf * p.nseg * p.lpb;
   auto go = [&](auto kern) -> int {
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -2,11 +2,12 @@
 //
 // Schedule.  M2(dt) = T(dt/2) C(dt) T(dt/2) (Section 3.2) with T the product of
 // the per-population transports; transports along different axes act on
-// different populations, so they commute exactly.  For D axes with last axis L,
-// nsteps steps are issued as
-//   for a < L: pass_a [T(dt/2)]
+// different populations, so they commute exactly.  With L the axis whose pass carries
+// the collision (the last axis, or the one PDG_OPT_COLLISION_AXIS names), nsteps steps
+// are issued as
+//   for a != L: pass_a [T(dt/2)]
 //   repeat nsteps:  pass_L [T(dt/2), C, T(dt/2)]
-//                   for a < L: pass_a [T(dt/2), T(dt/2)]   (last step: [T(dt/2)])
+//                   for a != L: pass_a [T(dt/2), T(dt/2)]   (last step: [T(dt/2)])
 // which applies to every population exactly the sequence of the naive order.
 // The collapsed scheme of Section 5.1 merges interior half steps into T(dt).
 #include <cuda_runtime.h>
@@ -82,7 +83,7 @@ PdgPassSpec spec(int axis, int nops, const int* ops, const int* ci, const PdgCoe
 int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
   out.clear();
   if (nsteps <= 0) return PDG_OK;
-  const int D = c->dim, L = D - 1;
+  const int D = c->dim, L = (c->caxis >= 0 && c->caxis < D) ? c->caxis : D - 1;
   out.reserve((2 * (size_t)nsteps + 1) * (size_t)D);   // at least the passes of every scheme
   PdgCoef half[3], full[3];
   for (int a = 0; a < D; ++a) {
@@ -119,7 +120,8 @@ int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSp
     auto seg_n = [&](int j) { return (j == 0 || j == nseg - 1) ? 1 : ((j % 2 == 1) ? 1 : 2); };
     auto seg_ci = [&](int j) { return (j % 2 == 1) ? 1 : 0; };
     auto other_axes = [&](int j) {
-      for (int a = 0; a < L; ++a) {
+      for (int a = 0; a < D; ++a) {
+        if (a == L) continue;
         PdgCoef cs[2] = {qc[a], hc[a]};
         const int ops[2] = {T, T}, ci[2] = {seg_ci(j), seg_ci(j)};
         out.push_back(spec(a, seg_n(j), ops, ci, cs, 2));
@@ -140,18 +142,22 @@ int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSp
     return PDG_OK;
   }
   if (c->scheme == PDG_SCHEME_M2) {
-    for (int a = 0; a < L; ++a) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
+    for (int a = 0; a < D; ++a)
+      if (a != L) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
     for (int s = 0; s < nsteps; ++s) {
       out.push_back(spec(L, 3, o3, z3, &half[L], 1));
-      for (int a = 0; a < L; ++a) out.push_back(spec(a, s < nsteps - 1 ? 2 : 1, o2, z2, &half[a], 1));
+      for (int a = 0; a < D; ++a)
+        if (a != L) out.push_back(spec(a, s < nsteps - 1 ? 2 : 1, o2, z2, &half[a], 1));
     }
   } else {
-    for (int a = 0; a < L; ++a) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
+    for (int a = 0; a < D; ++a)
+      if (a != L) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
     for (int s = 0; s < nsteps; ++s) {
       PdgCoef cs[2] = {half[L], full[L]};
       const int ops[2] = {T, C}, ci[2] = {s == 0 ? 0 : 1, 0};
       out.push_back(spec(L, 2, ops, ci, cs, 2));
-      for (int a = 0; a < L; ++a) out.push_back(spec(a, 1, o1, z1, s < nsteps - 1 ? &full[a] : &half[a], 1));
+      for (int a = 0; a < D; ++a)
+        if (a != L) out.push_back(spec(a, 1, o1, z1, s < nsteps - 1 ? &full[a] : &half[a], 1));
     }
     out.push_back(spec(L, 1, o1, z1, &half[L], 1));
   }

@@ -234,3 +234,52 @@ def test_failed_calls_leave_the_context_unchanged(pdg):
     assert bytes(s.info()) == info0
     assert s.schedule(0.01, 3) == sched0
     s.close()
+
+
+@pytest.mark.parametrize("dim,model,lam,lengths,d,theta", CASES[1:], ids=[c[1] for c in CASES[1:]])
+@pytest.mark.parametrize("scheme", ["M2", "M2_collapsed", "M2_kin", "M4_kin"])
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_any_axis_can_carry_the_collision(pdg, dim, model, lam, lengths, d, theta, scheme, nsteps):
+    """PDG_OPT_COLLISION_AXIS: transports along different axes commute, so the pass holding
+    T(dt/2) C T(dt/2) may be any axis' pass; every class still meets the composition."""
+    for ca in range(dim):
+        s = pdg.Solver(dim, (3,) * dim, (2,) * dim, d, lengths=lengths)
+        s.set_model(model, lam, scheme=scheme, theta=theta)
+        s.set_option(pdg.PDG_OPT_COLLISION_AXIS, ca)
+        info = s.info()
+        dt = 0.6 * min(info.h[a] for a in range(dim)) / lam
+        sched = s.schedule(dt, nsteps)
+        assert all(p["axis"] == ca for p in sched if C_OP in p["ops"])
+        assert any(C_OP in p["ops"] for p in sched)
+        ev = classes_from_schedule(sched, dim, False)
+        exp = expected(scheme, dt, nsteps)
+        for a in range(dim):
+            check_line_class(pdg, ev[a], exp, d, lam, info.h[a], theta)
+        s.close()
+
+
+def test_collision_axis_and_resident_options(pdg):
+    s = pdg.Solver(3, (2, 2, 2), (2, 2, 2), 2)
+    for bad in (-2, 3):
+        with pytest.raises(pdg.PdgError) as e:
+            s.set_option(pdg.PDG_OPT_COLLISION_AXIS, bad)
+        assert e.value.status == pdg.PDG_ERR_ARG
+    s.set_option(pdg.PDG_OPT_COLLISION_AXIS, 0)
+    with pytest.raises(pdg.PdgError) as e:        # lattices keep the last axis
+        s.set_model("isothermal_d3q19", 1.0)
+    assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
+    s.set_option(pdg.PDG_OPT_COLLISION_AXIS, -1)
+    s.set_model("isothermal_d3q19", 1.0)
+    with pytest.raises(pdg.PdgError) as e:
+        s.set_option(pdg.PDG_OPT_COLLISION_AXIS, 1)
+    assert e.value.status == pdg.PDG_ERR_UNSUPPORTED
+    s.set_option(pdg.PDG_OPT_COLLISION_AXIS, 2)   # the last axis itself is fine
+    s.set_option(pdg.PDG_OPT_RESIDENT, 1)
+    for bad in ((0, 1, 1), (1, 0, 1), (8, 8, 10)):
+        with pytest.raises(pdg.PdgError):
+            s.set_launch(7, *bad)
+    s.set_launch(8, 1, 16, 10)
+    assert s.get_launch(8) == (1, 16, 10)
+    s.set_launch(8, 0, 0, 0)
+    assert s.get_launch(8) == (0, 0, 0)
+    s.close()
