@@ -218,7 +218,7 @@ def test_corner_launch_override_and_options(pdg):
     assert s.get_launch(5)[0] == 256
     s.set_launch(5, 0, 0, 0)
     with pytest.raises(pdg.PdgError):
-        s.set_launch(7, 1, 1, 1)
+        s.set_launch(9, 1, 1, 1)
     s.set_option(pdg.PDG_OPT_GRAPH, 1)
     s.set_option(pdg.PDG_OPT_GRAPH, 0)
     s.set_option(pdg.PDG_OPT_COMPOSE_TT, 1)
