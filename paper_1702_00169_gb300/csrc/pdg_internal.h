@@ -263,6 +263,15 @@ struct PdgCornerPass {
   PdgCornerCoef c;
 };
 
+// Shared-memory line stride (8-byte words) of the line-resident kernel: the line length
+// rounded up to an even count plus two words at most.  Staged lines then start 16-byte
+// aligned, as lines do in global memory (unit-stride sweeps of even-degree cells move
+// 16-byte pairs), and consecutive lines start on different banks.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int pdg_resident_ls(int npl) { return (npl + 2) & ~1; }
+
 // ---- read-only view of a context for entry points outside pdg_api.cu ----
 #include <cuda_runtime.h>
 #include <string>

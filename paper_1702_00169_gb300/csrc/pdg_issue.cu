@@ -534,7 +534,7 @@ bool resident_shape(const pdg_ctx* c, const PdgPassSpec& sp, int kind, int* shap
   int W = 1;
   for (int i = 0; i < sp.ncs; ++i) W = std::max(W, stable_window(sp.cs[i]));
   auto smem = [&](int lpb, int nseg) {
-    return sizeof(double) * (nload * (size_t)lpb * (size_t)(npl + 1) + 3 * (size_t)ntf * nseg * lpb);
+    return sizeof(double) * (nload * (size_t)lpb * (size_t)pdg_resident_ls(npl) + 3 * (size_t)ntf * nseg * lpb);
   };
   const size_t cap = 220 * 1024;
   int lpb, nseg, ngroup;

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(512, 1) pass_kernel_lat(const __grid_constant_
 // block's lines crosses DRAM once each way, and the block requests all of its data at the
 // start, instead of one cell per thread and sweep step through global memory.  Periodic
 // lines of the DnQ2n models (no inflow data, no lattice slots, no source stage).
-// Shared memory: nload fields x lpb lines x (npl + 1) values (the + 1 puts consecutive
+// Shared memory: nload fields x lpb lines x pdg_resident_ls(npl) values (16-byte aligned
 // lines on different banks), then the segment aggregates of pass_body.
 __device__ __forceinline__ bool pass_has_collision(const PdgPass& p) {
   for (int o = 0; o < p.nops; ++o)
@@ -69,7 +69,7 @@ __device__ __forceinline__ void cp_async8_line(double* smem, const double* gmem)
 template <bool LOAD>
 __device__ __forceinline__ void resident_copy(const PdgPass& p, double* lines, int l0, int cnt, int nload,
                                               bool all) {
-  const int LS = p.npl + 1;
+  const int LS = pdg_resident_ls(p.npl);
   const long long FS = (long long)p.lpb * LS;
   const long long total = (long long)nload * cnt * p.npl;
   for (long long i = threadIdx.x; i < total; i += blockDim.x) {
@@ -97,13 +97,13 @@ __device__ __forceinline__ void resident_copy(const PdgPass& p, double* lines, i
 
 template <int NP, int MV, class T>
 __global__ void __launch_bounds__(512) pass_resident_kernel(const __grid_constant__ PdgPass p) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   __shared__ PdgPass q;
   int l0, cnt;
   block_lines(p, blockIdx.x, &l0, &cnt);
   const bool all = pass_has_collision(p);
   const int nload = all ? p.model.nf : p.ntf;
-  const int LS = p.npl + 1;
+  const int LS = pdg_resident_ls(p.npl);
   const long long FS = (long long)p.lpb * LS;
   double* lines = sm;
   double* aux = sm + (size_t)nload * FS;
@@ -139,7 +139,7 @@ inline size_t resident_smem(const PdgPass& p, int nf) {
   for (int o = 0; o < p.nops; ++o)
     if (p.op[o] == PDG_OP_C) all = true;
   const size_t nload = all ? (size_t)nf : (size_t)p.ntf;
-  return sizeof(double) * (nload * (size_t)p.lpb * (size_t)(p.npl + 1) + 3 * (size_t)p.ntf * p.nseg * p.lpb);
+  return sizeof(double) * (nload * (size_t)p.lpb * (size_t)pdg_resident_ls(p.npl) + 3 * (size_t)p.ntf * p.nseg * p.lpb);
 }
 
 template <int NP, int MV, class T>
