@@ -1048,12 +1048,16 @@ __device__ void collision_op(const PdgPass& p, int bid) {
 // lpb * nseg * ngroup take part in the barriers and in the collision phase only.
 template <int NP, int MV, class T>
 __device__ __forceinline__ void pass_body(const PdgPass& p, int bid, double* sm) {
-  const int LPB = p.lpb, S = p.nseg;
+  const int LPB = p.lpb, S = p.nseg, G = p.ngroup;
   const int t = threadIdx.x;
-  const int nthr = LPB * S * p.ngroup;
-  const int l_in = t % LPB;
-  const int s = (t / LPB) % S;
-  const int grp = t / (LPB * S);
+  const int nthr = LPB * S * G;
+  // thread -> (line, segment, field group): lines fastest (coalesced streaming from global
+  // memory), or field groups fastest (tmap = 1, the line-resident kernel: consecutive
+  // threads then sweep different populations, whose staged copies start on different banks,
+  // instead of segments of one line, which share banks)
+  const int l_in = p.tmap ? t / (G * S) : t % LPB;
+  const int s = p.tmap ? (t / G) % S : (t / LPB) % S;
+  const int grp = p.tmap ? t % G : t / (LPB * S);
   int l0, cnt;
   block_lines(p, bid, &l0, &cnt);
   const int line = l0 + l_in;

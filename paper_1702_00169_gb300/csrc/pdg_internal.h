@@ -145,6 +145,8 @@ struct PdgPass {
   int dslot;                   // D2Q9 collision: state slot of population 5 (5 or 9)
   int resident;                // 1: the line-resident kernel (the block's lines staged in shared
                                //    memory for the whole op list; periodic DnQ2n passes)
+  int tmap;                    // thread map of the transport sweeps: 0 lines fastest, 1 field
+                               //    groups fastest (set by the line-resident kernel)
   const double* fb;            // non-periodic: inflow values [2 sides][fbnent][nlines] (state format)
   int fbnent;                  // entries per side of fb (m; 3 for D2Q9)
   int fbent[2 * PDG_MAXM];     // entry of each transported population within its side

@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(512) pass_resident_kernel(const __grid_constan
     q.s2 = 0;
     q.nlines = cnt;
     q.nblocks = 0;
+    q.tmap = 1;
     if (!all)
       for (int phi = 0; phi < p.ntf; ++phi) q.tfield[phi] = phi;
   }
