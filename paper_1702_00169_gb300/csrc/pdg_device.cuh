@@ -833,8 +833,12 @@ __device__ __forceinline__ void phase_sweep_tt(double* lp, long long dstep, int 
   }
 }
 
+// Offset of line `line` of a pass.  Line indices and lineA are below 2^31 (lineA <= the
+// lines of one axis), so the division runs in 32-bit arithmetic.
 __device__ __forceinline__ long long line_base(const PdgPass& p, int line) {
-  return (long long)(line % p.lineA) * p.s1 + (long long)(line / p.lineA) * p.s2;
+  const unsigned la = (unsigned)min(p.lineA, 0x7fffffffLL);
+  const unsigned u = (unsigned)line;
+  return (long long)(u % la) * p.s1 + (long long)(u / la) * p.s2;
 }
 
 __device__ __forceinline__ int seg_begin(int s, int N, int S) { return (int)(((long long)s * N) / S); }
@@ -1017,10 +1021,10 @@ __device__ void collision_op(const PdgPass& p, int bid) {
   constexpr int NF = NFields<MV>::value;
   int l0, cnt;
   block_lines(p, bid, &l0, &cnt);
-  const long long tile = (long long)cnt * p.npl;
-  for (long long idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-    const int l_in = (int)(idx % cnt);
-    const long long tpos = idx / cnt;
+  const int tile = cnt * p.npl;   // at most lpb * npl points: 32-bit index arithmetic
+  for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+    const int l_in = idx % cnt;
+    const int tpos = idx / cnt;
     const int line = l0 + l_in;
     const long long off = line_base(p, line) + tpos * p.stride;
     const int nf = p.model.nf;

@@ -63,35 +63,45 @@ __device__ __forceinline__ void cp_async8_line(double* smem, const double* gmem)
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 
-// Copies between the block's lines in global memory and their shared-memory image: unit-
-// stride lines with consecutive threads on consecutive points, strided lines with
-// consecutive threads on consecutive lines (adjacent points of the fastest axis).
+// Copies between the block's lines in global memory and their shared-memory image, with
+// no division per element: unit-stride lines with consecutive threads on consecutive
+// points, strided lines with consecutive threads on consecutive lines (adjacent points of
+// the fastest axis; a thread keeps one line and steps along it).
 template <bool LOAD>
 __device__ __forceinline__ void resident_copy(const PdgPass& p, double* lines, int l0, int cnt, int nload,
                                               bool all) {
   const int LS = pdg_resident_ls(p.npl);
   const long long FS = (long long)p.lpb * LS;
-  const long long total = (long long)nload * cnt * p.npl;
-  for (long long i = threadIdx.x; i < total; i += blockDim.x) {
-    int l, pt, j;
-    if (p.stride == 1) {
-      pt = (int)(i % p.npl);
-      const long long r = i / p.npl;
-      l = (int)(r % cnt);
-      j = (int)(r / cnt);
-    } else {
-      l = (int)(i % cnt);
-      const long long r = i / cnt;
-      pt = (int)(r % p.npl);
-      j = (int)(r / p.npl);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (p.stride == 1) {
+    for (int j = 0; j < nload; ++j) {
+      const long long fo = (long long)(all ? j : p.tfield[j]) * p.field_stride;
+      for (int l = 0; l < cnt; ++l) {
+        double* g = p.f + fo + line_base(p, l0 + l);
+        double* sp = lines + j * FS + (long long)l * LS;
+        for (int pt = tid; pt < p.npl; pt += nt) {
+          if (LOAD)
+            cp_async8_line(sp + pt, g + pt);
+          else
+            g[pt] = sp[pt];
+        }
+      }
     }
-    const int fld = all ? j : p.tfield[j];
-    double* g = p.f + (long long)fld * p.field_stride + line_base(p, l0 + l) + (long long)pt * p.stride;
-    double* sp = lines + j * FS + (long long)l * LS + pt;
-    if (LOAD)
-      cp_async8_line(sp, g);
-    else
-      *g = *sp;
+  } else {
+    const int tpl = nt / cnt;                 // threads per line
+    const int l = tid % cnt, t0 = tid / cnt;
+    if (t0 >= tpl) return;
+    const long long lb = line_base(p, l0 + l);
+    for (int j = 0; j < nload; ++j) {
+      double* g = p.f + (long long)(all ? j : p.tfield[j]) * p.field_stride + lb;
+      double* sp = lines + j * FS + (long long)l * LS;
+      for (int pt = t0; pt < p.npl; pt += tpl) {
+        if (LOAD)
+          cp_async8_line(sp + pt, g + (long long)pt * p.stride);
+        else
+          g[(long long)pt * p.stride] = sp[pt];
+      }
+    }
   }
 }
 
