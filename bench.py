@@ -188,6 +188,8 @@ def parse_args():
     ap.add_argument("--shapes", default=None,
                     help="fixed launch shapes 'lpb,nseg,ngroup/lpb,nseg,ngroup' for the transport and "
                          "last-axis passes instead of autotuning (reproduces a timed configuration)")
+    ap.add_argument("--tc-layers", type=int, default=2, choices=[1, 2],
+                    help="tensor-core corner pass: box layers swept together (PDG_OPT_TC_LAYERS)")
     ap.add_argument("--resident", type=int, default=0,
                     help="1: line passes run the line-resident kernel (PDG_OPT_RESIDENT)")
     ap.add_argument("--caxis", type=int, default=-1,
@@ -735,6 +737,8 @@ def main():
                      theta=cfg.theta, scheme=args.scheme, precision=pdg.PRECISION[precision])
         if args.source != "none":
             sv.set_source(**SOURCES[args.source])
+        if precision in ("tf32", "tf32_df"):
+            sv.set_option(pdg.PDG_OPT_TC_LAYERS, args.tc_layers)
         if args.resident:
             sv.set_option(pdg.PDG_OPT_RESIDENT, 1)
         if args.caxis >= 0:

@@ -478,6 +478,11 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
  *     tensor-core work in flight, frees its tensor memory and returns, and the next
  *     synchronising call reports PDG_ERR_TIMEOUT once.  The context stays usable: with the
  *     switch off, later steps run normally (from the state left by the aborted passes).
+ *   PDG_OPT_TC_LAYERS (default 2): box layers the tensor-core corner pass sweeps together
+ *     (PDG_PREC_TF32 / PDG_PREC_TF32_DFRES): 2 = layer k + 1 follows layer k one
+ *     anti-diagonal behind, and the cells of both anti-diagonals share one product (half the
+ *     products and barriers) when they fit its 128 rows; 1 = one layer at a time.  Same
+ *     arithmetic per cell either way.
  *   PDG_OPT_RESIDENT (default 0): line passes of periodic axes of the DnQ2n models (no
  *     source stage) run the line-resident kernel: a block copies its lines -- every
  *     population the pass touches, over the whole line -- into shared memory, runs the
@@ -498,7 +503,8 @@ enum {
   PDG_OPT_GRAPH = 2,
   PDG_OPT_DEBUG_TC_STALL = 3,
   PDG_OPT_RESIDENT = 4,
-  PDG_OPT_COLLISION_AXIS = 5
+  PDG_OPT_COLLISION_AXIS = 5,
+  PDG_OPT_TC_LAYERS = 6
 };
 int pdg_set_option(pdg_ctx* ctx, int option, int value);
 

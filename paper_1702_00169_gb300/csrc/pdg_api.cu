@@ -627,6 +627,10 @@ int pdg_set_option(pdg_ctx* c, int option, int value) try {
     case PDG_OPT_DEBUG_TC_STALL:
       c->tc_stall = value != 0;
       return PDG_OK;
+    case PDG_OPT_TC_LAYERS:
+      if (value != 1 && value != 2) return fail(c, PDG_ERR_ARG, "tensor-core layers: 1 or 2");
+      c->tc_layers = value;
+      return PDG_OK;
     case PDG_OPT_RESIDENT:
       c->resident = value != 0;
       return PDG_OK;

@@ -89,14 +89,17 @@ struct CornerRow {
 
 // Stage the state and the entering +z faces of every cell of anti-diagonal t of layer k,
 // and, on the region's upwind x and y edges, the old face values entering it.
+// stage_z = false: the entering +z faces are left out (a caller that reads them later,
+// directly from the scratch, because the layer below writes them one step before).
 template <int NP>
 __device__ __forceinline__ void corner_stage(const CornerGeom& g, int k, int t, double* fb, double* lbnd,
-                                             double* bbnd) {
+                                             double* bbnd, bool stage_z = true) {
   constexpr int NF = CornerRow<NP>::NF, NN = CornerRow<NP>::NN, RS = CornerRow<NP>::RS;
   const int jlo = max(0, t - g.nrow + 1), jhi = min(g.ncol - 1, t);
   const int A = jhi - jlo + 1;
-  for (int i = threadIdx.x; i < A * (NN + NF); i += blockDim.x) {
-    const int c = i / (NN + NF), q = i % (NN + NF);
+  const int per = stage_z ? NN + NF : NN;
+  for (int i = threadIdx.x; i < A * per; i += blockDim.x) {
+    const int c = i / per, q = i % per;
     const int j = jlo + c, r = t - j;
     const double* src = q < NN ? g.fin + corner_off(g, j, r, k, q / NF, (q / NP) % NP, q % NP)
                                : g.zt + ((long long)r * g.ncol + j) * NF + (q - NN);

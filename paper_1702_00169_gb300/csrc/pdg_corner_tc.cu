@@ -12,12 +12,12 @@ namespace {
 
 template <int NP>
 size_t tc_smem(const PdgCornerPass& p) {
-  return pdgdev::TcSmem<NP>(p.tx + p.c.wx, p.ty + p.c.wy, p.tz + p.c.wz).total;
+  return pdgdev::TcSmem<NP>(p.tx + p.c.wx, p.ty + p.c.wy, p.tz + p.c.wz, p.tc_layers == 2 ? 2 : 1).total;
 }
 
 template <int NP, int RES>
 int go(const PdgCornerPass& p, size_t smem, cudaStream_t st) {
-  auto kern = pdgdev::corner_tc_kernel<NP, RES>;
+  auto kern = p.tc_layers == 2 ? pdgdev::corner_tc_kernel<NP, RES, 2> : pdgdev::corner_tc_kernel<NP, RES, 1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const long long blocks = (long long)p.ntx * p.nty * p.ntz * p.npop;
@@ -49,7 +49,8 @@ size_t pdg_corner_tc_smem(const PdgCornerPass& p) {
 int pdg_launch_corner_tc(const PdgCornerPass& p, size_t smem, void* stream) {
   const long long blocks = (long long)p.ntx * p.nty * p.ntz * p.npop;
   if (blocks > 0x7fffffffLL || blocks < 1) return (int)cudaErrorInvalidConfiguration;
-  if (std::min(p.tx + p.c.wx, p.ty + p.c.wy) > 128 || !p.binv_tc || !p.err) return (int)cudaErrorInvalidValue;
+  const int layers = p.tc_layers == 2 ? 2 : 1;
+  if (layers * std::min(p.tx + p.c.wx, p.ty + p.c.wy) > 128 || !p.binv_tc || !p.err) return (int)cudaErrorInvalidValue;
   cudaStream_t st = (cudaStream_t)stream;
   const int res = p.tc == 2 ? 1 : 0;
   switch (p.n * 2 + res) {

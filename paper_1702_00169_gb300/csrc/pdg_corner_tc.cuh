@@ -9,6 +9,8 @@
 // (M = 128 rows of cells, N = K = the NN nodes padded to 16 / 32 / 64), FP32 accumulation
 // in TMEM, each operand split into two TF32 parts (v = hi + lo, 22 significant bits):
 //   X~ = R_hi Binv_hi + R_lo Binv_hi + R_hi Binv_lo    (relative error ~1e-6)
+// (the FP64 values split into TF32 parts, and FP32 results widened, by integer operations on
+// the bit patterns, which keeps these conversions off the FP64 pipe),
 // then the residual of the cell system, through the Kronecker sum B (1 + 3n FMA per node),
 //   res = r - B x~ = r - x~ - sum_a (theta nu_a K) x~ along axis a
 // in FP64 (RES = 0) or in double-float on the FP32 pipes (RES = 1), a second split
@@ -47,11 +49,12 @@ struct TcShape {
   static constexpr int BOPS = NPAD * KP;                 // floats of one B split
 };
 
-// Shared-memory carve-up of the tensor-core corner kernel (offsets in bytes).
+// Shared-memory carve-up of the tensor-core corner kernel (offsets in bytes) for `layers`
+// box layers swept together (their anti-diagonals' cells share one product).
 template <int NP>
 struct TcSmem {
   size_t aop, bop, rbuf, fbuf, xt, lt, bt, lbnd, bbnd, kt, ktf, colx, rowy, layz, mbar, total;
-  __host__ __device__ TcSmem(int CM, int RM, int LM) {
+  __host__ __device__ TcSmem(int CM, int RM, int LM, int layers) {
     using S = TcShape<NP>;
     constexpr int NF = CornerRow<NP>::NF, NN = CornerRow<NP>::NN, RS = CornerRow<NP>::RS;
     const int amax = CM < RM ? CM : RM;
@@ -64,13 +67,13 @@ struct TcSmem {
     };
     aop = take(sizeof(float) * 2 * S::AOPS, 128);
     bop = take(sizeof(float) * 2 * S::BOPS, 128);
-    rbuf = take(sizeof(double) * amax * NN, 16);
-    fbuf = take(sizeof(double) * 2 * amax * RS, 16);
-    xt = take(sizeof(float) * amax * NN, 16);
-    lt = take(sizeof(double) * 2 * (CM + 1) * NF, 16);
-    bt = take(sizeof(double) * 2 * CM * NF, 16);
-    lbnd = take(sizeof(double) * 2 * NF, 16);
-    bbnd = take(sizeof(double) * 2 * NF, 16);
+    rbuf = take(sizeof(double) * layers * amax * NN, 16);
+    fbuf = take(sizeof(double) * 2 * layers * amax * RS, 16);
+    xt = take(sizeof(float) * layers * amax * NN, 16);
+    lt = take(sizeof(double) * layers * 2 * (CM + 1) * NF, 16);
+    bt = take(sizeof(double) * layers * 2 * CM * NF, 16);
+    lbnd = take(sizeof(double) * layers * 2 * NF, 16);
+    bbnd = take(sizeof(double) * layers * 2 * NF, 16);
     kt = take(sizeof(double) * 3 * NP * NP, 16);
     ktf = take(sizeof(float) * 2 * 3 * NP * NP, 16);
     colx = take(sizeof(long long) * (CM + 1), 16);
@@ -84,13 +87,16 @@ struct TcSmem {
 // r - (x~ + sum_a Kt_a x~ along a) for node (qz, qy, qx) of one cell; x~ in FP32.
 template <int NP>
 __device__ __forceinline__ double tc_residual(double r, const float* xc, const double* kt, int qz, int qy, int qx) {
-  double s = (double)xc[(qz * NP + qy) * NP + qx];
+  using tc::f64_from_f32_bits;
+  double s = f64_from_f32_bits(xc[(qz * NP + qy) * NP + qx]);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) s = fma(kt[qx * NP + i], (double)xc[(qz * NP + qy) * NP + i], s);
+  for (int i = 0; i < NP; ++i) s = fma(kt[qx * NP + i], f64_from_f32_bits(xc[(qz * NP + qy) * NP + i]), s);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) s = fma(kt[NP * NP + qy * NP + i], (double)xc[(qz * NP + i) * NP + qx], s);
+  for (int i = 0; i < NP; ++i)
+    s = fma(kt[NP * NP + qy * NP + i], f64_from_f32_bits(xc[(qz * NP + i) * NP + qx]), s);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) s = fma(kt[2 * NP * NP + qz * NP + i], (double)xc[(i * NP + qy) * NP + qx], s);
+  for (int i = 0; i < NP; ++i)
+    s = fma(kt[2 * NP * NP + qz * NP + i], f64_from_f32_bits(xc[(i * NP + qy) * NP + qx]), s);
   return r - s;
 }
 
@@ -115,10 +121,12 @@ __device__ __forceinline__ dd tc_residual_dd(double r, const float* xc, const fl
 #pragma unroll
   for (int i = 0; i < NP; ++i) term(2, qz, i, xc[(i * NP + qy) * NP + qx]);
   const dd s = dd_fast_two_sum(S, L);
-  return dd_add_accurate(dd_from_double(r), dd{-s.hi, -s.lo});
+  dd rr;
+  tc::split_f64_bits<24>(r, &rr.hi, &rr.lo);
+  return dd_add_accurate(rr, dd{-s.hi, -s.lo});
 }
 
-template <int NP, int RES>
+template <int NP, int RES, int LAYERS>
 __device__ __forceinline__ void corner_tc_body(const PdgCornerPass& p, unsigned char* smem) {
   using S = TcShape<NP>;
   constexpr int NF = CornerRow<NP>::NF, NN = CornerRow<NP>::NN, RS = CornerRow<NP>::RS;
@@ -134,7 +142,7 @@ __device__ __forceinline__ void corner_tc_body(const PdgCornerPass& p, unsigned 
   const PdgCornerCoef& C = p.c;
   const int CM = p.tx + C.wx, RM = p.ty + C.wy;
   const int amax = min(CM, RM);
-  const TcSmem<NP> L(CM, RM, p.tz + C.wz);
+  const TcSmem<NP> L(CM, RM, p.tz + C.wz, LAYERS);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   CornerGeom g;
@@ -175,12 +183,12 @@ __device__ __forceinline__ void corner_tc_body(const PdgCornerPass& p, unsigned 
 
   float* aop = reinterpret_cast<float*>(smem + L.aop);
   float* bop = reinterpret_cast<float*>(smem + L.bop);
-  double* rbuf = reinterpret_cast<double*>(smem + L.rbuf);
-  double* fbuf = reinterpret_cast<double*>(smem + L.fbuf);
-  float* xt = reinterpret_cast<float*>(smem + L.xt);
-  double* Lt = reinterpret_cast<double*>(smem + L.lt);
-  double* Bt = reinterpret_cast<double*>(smem + L.bt);
-  double* lbnd = reinterpret_cast<double*>(smem + L.lbnd);
+  double* rbuf = reinterpret_cast<double*>(smem + L.rbuf);   // [layer][amax][NN]
+  double* fbuf = reinterpret_cast<double*>(smem + L.fbuf);   // [parity][layer][amax][RS]
+  float* xt = reinterpret_cast<float*>(smem + L.xt);         // [layer][amax][NN]
+  double* Lt = reinterpret_cast<double*>(smem + L.lt);       // [layer][parity][CM + 1][NF]
+  double* Bt = reinterpret_cast<double*>(smem + L.bt);       // [layer][parity][CM][NF]
+  double* lbnd = reinterpret_cast<double*>(smem + L.lbnd);   // [layer][parity][NF]
   double* bbnd = reinterpret_cast<double*>(smem + L.bbnd);
   double* kt = reinterpret_cast<double*>(smem + L.kt);
   float* ktf = reinterpret_cast<float*>(smem + L.ktf);
@@ -192,8 +200,13 @@ __device__ __forceinline__ void corner_tc_body(const PdgCornerPass& p, unsigned 
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.mbar + 16);
   int* abort_flag = reinterpret_cast<int*>(smem + L.mbar + 20);
   const int LtS = CM + 1, BtS = CM;
+  auto FB = [&](int par, int ls) { return fbuf + ((size_t)par * LAYERS + ls) * amax * RS; };
+  auto LT = [&](int ls, int par) { return Lt + ((size_t)ls * 2 + par) * LtS * NF; };
+  auto BT = [&](int ls, int par) { return Bt + ((size_t)ls * 2 + par) * BtS * NF; };
+  auto LB = [&](int ls, int par) { return lbnd + ((size_t)ls * 2 + par) * NF; };
+  auto BB = [&](int ls, int par) { return bbnd + ((size_t)ls * 2 + par) * NF; };
 
-  // set-up: TMEM columns for the accumulator, the mbarrier, both A splits zero (the padded
+  // set-up: TMEM columns for the accumulator, the mbarriers, both A splits zero (the padded
   // columns k >= NN stay zero), both B splits from the host's layout, the stencil of B
   if (warp == 0) tc::tmem_alloc(tslot, S::NCOL);
   if (tid == 0) {
@@ -236,7 +249,8 @@ __device__ __forceinline__ void corner_tc_body(const PdgCornerPass& p, unsigned 
   __syncthreads();
   const double rth = C.rtheta, c1 = C.c1, th = C.theta, kx = C.kx, ky = C.ky, kz = C.kz;
 
-  corner_stage<NP>(g, 0, 0, fbuf, lbnd, bbnd);
+  // step s (all groups) uses parity s & 1; the first step stages layer 0's anti-diagonal 0
+  corner_stage<NP>(g, 0, 0, FB(0, 0), LB(0, 0), BB(0, 0));
   cp_async_wait_all();
   __syncthreads();
 
@@ -272,29 +286,52 @@ __device__ __forceinline__ void corner_tc_body(const PdgCornerPass& p, unsigned 
   const uint32_t taddr = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(cc * CW);
   bool aborted = false;
 
+  // Layers k0 .. k0 + nl - 1 are swept together: at group step tau, layer k0 + ls handles
+  // its anti-diagonal tau - ls.  A layer's +z faces come from the layer below: for the first
+  // layer of a group that layer finished in an earlier group and the faces are staged with
+  // the state; for the others it wrote them one step before, after that step's staging, so
+  // they are read from the scratch directly.  Rows of the products: the cells of layer k0's
+  // anti-diagonal, then those of layer k0 + 1.
   int s = 0;
-  for (int k = 0; k < g.nlay && !aborted; ++k) {
-    const bool out_layer = k >= g.wz;
-    for (int t = 0; t < T_steps; ++t, ++s) {
+  for (int k0 = 0; k0 < g.nlay && !aborted; k0 += LAYERS) {
+    const int nl = min(LAYERS, g.nlay - k0);
+    const int tsteps = T_steps + nl - 1;
+    for (int tau = 0; tau < tsteps; ++tau, ++s) {
       const int par = s & 1, prv = par ^ 1;
-      const int jlo = max(0, t - g.nrow + 1), jhi = min(g.ncol - 1, t);
-      const int A = jhi - jlo + 1;
-      const double* fc = fbuf + (size_t)par * amax * RS;
-      // (A) r_c of every cell of the anti-diagonal, kept in FP64 and split into the operand
-      for (int i = tid; i < A * NN; i += blockDim.x) {
+      int jlo[LAYERS], jhi[LAYERS], Acnt[LAYERS], roff[LAYERS];
+      int Atot = 0;
+#pragma unroll
+      for (int ls = 0; ls < LAYERS; ++ls) {
+        const int tt = tau - ls;
+        const bool on = ls < nl && tt >= 0 && tt < T_steps;
+        jlo[ls] = on ? max(0, tt - g.nrow + 1) : 0;
+        jhi[ls] = on ? min(g.ncol - 1, tt) : -1;
+        Acnt[ls] = on ? jhi[ls] - jlo[ls] + 1 : 0;
+        roff[ls] = Atot;
+        Atot += Acnt[ls];
+      }
+      // row c of the products -> (layer slot, cell index in its anti-diagonal)
+      auto row_slot = [&](int c) { return (LAYERS > 1 && c >= Acnt[0]) ? 1 : 0; };
+      // (A) r_c of every cell, kept in FP64 and split into the operand
+      for (int i = tid; i < Atot * NN; i += blockDim.x) {
         const int c = i / NN, q = i % NN;
-        const int j = jlo + c, r = t - j;
+        const int ls = row_slot(c), cl = c - roff[ls], tt = tau - ls;
+        const int j = jlo[ls] + cl, r = tt - j;
         const int iz = q / NF, iy = (q / NP) % NP, ix = q % NP;
-        double rv = fc[c * RS + q] * rth;
+        const double* fc = FB(par, ls);
+        double rv = fc[cl * RS + q] * rth;
         if (ix == 0)
-          rv = fma(kx, j == 0 ? lbnd[par * NF + iz * NP + iy] : Lt[((size_t)prv * LtS + j) * NF + iz * NP + iy], rv);
+          rv = fma(kx, j == 0 ? LB(ls, par)[iz * NP + iy] : LT(ls, prv)[(size_t)j * NF + iz * NP + iy], rv);
         if (iy == 0)
-          rv = fma(ky, r == 0 ? bbnd[par * NF + iz * NP + ix] : Bt[((size_t)prv * BtS + j) * NF + iz * NP + ix], rv);
-        if (iz == 0) rv = fma(kz, fc[c * RS + NN + iy * NP + ix], rv);
-        rbuf[c * NN + q] = rv;
-        const float h = __double2float_rn(rv);
-        const float hi = tc::tf32_rna(h);
-        const float lo = tc::tf32_rna(__double2float_rn(rv - (double)hi));
+          rv = fma(ky, r == 0 ? BB(ls, par)[iz * NP + ix] : BT(ls, prv)[(size_t)j * NF + iz * NP + ix], rv);
+        if (iz == 0) {
+          const double zf = ls == 0 ? fc[cl * RS + NN + iy * NP + ix]
+                                    : g.zt[((long long)r * g.ncol + j) * NF + iy * NP + ix];
+          rv = fma(kz, zf, rv);
+        }
+        rbuf[((size_t)ls * amax + cl) * NN + q] = rv;
+        float hi, lo;
+        tc::split_f64_bits<11>(rv, &hi, &lo);
         const int idx = tc::op_index(c, q, 128);
         aop[idx] = hi;
         aop[S::AOPS + idx] = lo;
@@ -302,12 +339,14 @@ __device__ __forceinline__ void corner_tc_body(const PdgCornerPass& p, unsigned 
       tc::fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) mma_issue();
-      {   // stage the next anti-diagonal (the first one of the next layer after the last)
-        double* nf = fbuf + (size_t)prv * amax * RS;
-        double* nl = lbnd + prv * NF;
-        double* nb = bbnd + prv * NF;
-        if (t + 1 < T_steps) corner_stage<NP>(g, k, t + 1, nf, nl, nb);
-        else if (k + 1 < g.nlay) corner_stage<NP>(g, k + 1, 0, nf, nl, nb);
+      {   // stage the next step: each layer's next anti-diagonal, or the next group's first
+#pragma unroll
+        for (int ls = 0; ls < LAYERS; ++ls) {
+          const int tn = tau + 1 - ls;
+          if (ls < nl && tn >= 0 && tn < T_steps)
+            corner_stage<NP>(g, k0 + ls, tn, FB(prv, ls), LB(ls, prv), BB(ls, prv), ls == 0);
+        }
+        if (tau + 1 == tsteps && k0 + LAYERS < g.nlay) corner_stage<NP>(g, k0 + LAYERS, 0, FB(prv, 0), LB(0, prv), BB(0, prv));
       }
       if (tid == 0) mma_wait();
       __syncthreads();
@@ -319,24 +358,29 @@ __device__ __forceinline__ void corner_tc_body(const PdgCornerPass& p, unsigned 
       tc::fence_after_sync();
       float xr[CW];
       tc::tmem_ld<CW>(taddr, xr);
-      if (trow < A)
+      if (trow < Atot) {
+        const int ls = row_slot(trow), cl = trow - roff[ls];
 #pragma unroll
         for (int e = 0; e < CW; ++e)
-          if (cc * CW + e < NN) xt[trow * NN + cc * CW + e] = xr[e];
+          if (cc * CW + e < NN) xt[((size_t)ls * amax + cl) * NN + cc * CW + e] = xr[e];
+      }
       tc::fence_before_sync();
       __syncthreads();
       // (R) residual r - B x~ of every node, split into the operand
-      for (int i = tid; i < A * NN; i += blockDim.x) {
+      for (int i = tid; i < Atot * NN; i += blockDim.x) {
         const int c = i / NN, q = i % NN;
+        const int ls = row_slot(c), cl = c - roff[ls];
         const int qz = q / NF, qy = (q / NP) % NP, qx = q % NP;
         const int idx = tc::op_index(c, q, 128);
+        const size_t cr = ((size_t)ls * amax + cl) * NN;
         if constexpr (RES == 0) {
-          const double res = tc_residual<NP>(rbuf[c * NN + q], xt + c * NN, kt, qz, qy, qx);
-          const float hi = tc::tf32_rna(__double2float_rn(res));
+          const double res = tc_residual<NP>(rbuf[cr + q], xt + cr, kt, qz, qy, qx);
+          float hi, lo;
+          tc::split_f64_bits<11>(res, &hi, &lo);
           aop[idx] = hi;
-          aop[S::AOPS + idx] = tc::tf32_rna(__double2float_rn(res - (double)hi));
+          aop[S::AOPS + idx] = lo;
         } else {
-          const dd res = tc_residual_dd<NP>(rbuf[c * NN + q], xt + c * NN, ktf, qz, qy, qx);
+          const dd res = tc_residual_dd<NP>(rbuf[cr + q], xt + cr, ktf, qz, qy, qx);
           const float hi = tc::tf32_rna(res.hi);
           aop[idx] = hi;
           aop[S::AOPS + idx] = tc::tf32_rna(__fadd_rn(__fsub_rn(res.hi, hi), res.lo));
@@ -357,25 +401,30 @@ __device__ __forceinline__ void corner_tc_body(const PdgCornerPass& p, unsigned 
       tc::fence_after_sync();
       float dv[CW];
       tc::tmem_ld<CW>(taddr, dv);
-      if (trow < A) {
-        const int c = trow, j = jlo + c, r = t - j;
-        int h1 = jhi + 1, h2 = jhi;
+      if (trow < Atot) {
+        const int ls = row_slot(trow), cl = trow - roff[ls], tt = tau - ls, k = k0 + ls;
+        const int j = jlo[ls] + cl, r = tt - j;
+        const bool out_layer = k >= g.wz;
+        int h1 = jhi[ls] + 1, h2 = jhi[ls];
         if (out_layer) {
-          h1 = max(jlo, min(g.wx, jhi + 1));
-          h2 = max(h1 - 1, min(jhi, t - g.wy));
+          h1 = max(jlo[ls], min(g.wx, jhi[ls] + 1));
+          h2 = max(h1 - 1, min(jhi[ls], tt - g.wy));
         }
         const bool out_cell = j >= h1 && j <= h2;
+        const double* fc = FB(par, ls);
+        double* lt = LT(ls, par);
+        double* bt = BT(ls, par);
 #pragma unroll
         for (int e = 0; e < CW; ++e) {
           const int q = cc * CW + e;
           if (q < NN) {
-            const double x = (double)xr[e] + (double)dv[e];
+            const double x = tc::f64_from_f32_bits(xr[e]) + tc::f64_from_f32_bits(dv[e]);
             const int qz = q / NF, qy = (q / NP) % NP, qx = q % NP;
-            if (out_cell) st(g.fout + corner_off(g, j, r, k, qz, qy, qx), x - c1 * fc[c * RS + q]);
+            if (out_cell) st(g.fout + corner_off(g, j, r, k, qz, qy, qx), x - c1 * fc[cl * RS + q]);
             if (qx == NP - 1 || qy == NP - 1 || qz == NP - 1) {
               const double face = th * x;
-              if (qx == NP - 1) Lt[((size_t)par * LtS + j + 1) * NF + qz * NP + qy] = face;
-              if (qy == NP - 1) Bt[((size_t)par * BtS + j) * NF + qz * NP + qx] = face;
+              if (qx == NP - 1) lt[(size_t)(j + 1) * NF + qz * NP + qy] = face;
+              if (qy == NP - 1) bt[(size_t)j * NF + qz * NP + qx] = face;
               if (qz == NP - 1) st(g.zt + ((long long)r * g.ncol + j) * NF + qy * NP + qx, face);
             }
           }
@@ -396,10 +445,10 @@ __device__ __forceinline__ void corner_tc_body(const PdgCornerPass& p, unsigned 
   }
 }
 
-template <int NP, int RES>
+template <int NP, int RES, int LAYERS>
 __global__ void __launch_bounds__(512, 1) corner_tc_kernel(const __grid_constant__ PdgCornerPass p) {
   extern __shared__ __align__(128) unsigned char tc_smem[];
-  corner_tc_body<NP, RES>(p, tc_smem);
+  corner_tc_body<NP, RES, LAYERS>(p, tc_smem);
 }
 
 }  // namespace pdgdev

@@ -61,6 +61,7 @@ struct pdg_ctx {
                                                // 1 FP64 residual, 2 double-float residual
   int* dev_err = nullptr;                      // error word of the tensor-core kernel (in cbuf)
   int tc_stall = 0;                            // PDG_OPT_DEBUG_TC_STALL
+  int tc_layers = 2;                           // PDG_OPT_TC_LAYERS
   int resident = 0;                            // PDG_OPT_RESIDENT
   int rshape[2][3] = {{0, 0, 0}, {0, 0, 0}};   // line-resident shapes per pass kind (0 = heuristic)
   int caxis = -1;                              // PDG_OPT_COLLISION_AXIS (-1: the last axis)

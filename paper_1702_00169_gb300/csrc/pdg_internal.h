@@ -253,6 +253,8 @@ struct PdgCornerPass {
   int* err;                        // device error word of the tensor-core kernel (tc != 0)
   int stall;                       // test switch: the MMA wait watches an mbarrier nothing arrives
                                    // on, with a bound of about 0.5 ms, so it runs out
+  int tc_layers;                   // tensor-core kernel: box layers swept together (1 or 2; 2 when
+                                   // two anti-diagonals fit the 128 rows of a product)
   double* zt;                      // device scratch: per block [ty + wy][tx + wx][n^2] +z faces
   // inflow axes (per axis a: per[a] = 1 periodic); boundary data fb[a] = [2 sides][nent][lines]
   // of the faces normal to a, each population's side and entry there; a face point's line

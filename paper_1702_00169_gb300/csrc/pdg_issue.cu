@@ -337,6 +337,7 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
   p.tc = c->tc;
   p.err = c->dev_err;
   p.stall = c->tc_stall;
+  p.tc_layers = c->tc ? c->tc_layers : 1;
   const int in = sp.dslot_in, outs = sp.dslot_in == L.diag ? L.scratch : L.diag;
   const int c0 = 4 * L.norient;   // first corner among the moving populations
   static const int sx[8] = {+1, -1, -1, +1, +1, -1, -1, +1}, sy[8] = {+1, +1, -1, -1, +1, +1, -1, -1};
@@ -402,6 +403,7 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
           q.tx = tx;
           q.ty = ty;
           q.tz = tz;
+          if (p.tc && q.tc_layers * std::min(tx + p.c.wx, ty + p.c.wy) > 128) q.tc_layers = 1;
           if (pdg_corner_smem(q) > 200 * 1024) continue;
           if (p.tc && std::min(tx + p.c.wx, ty + p.c.wy) > 128) continue;
           const long long blocks = 8LL * ntx * nty * ntz;
@@ -410,7 +412,7 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
           const double steps = (double)(tx + p.c.wx + ty + p.c.wy);
           // tensor-core kernel: every cell of the region forms all its nodes and the full
           // residual (start cells included), and a step carries six barriers and two MMA waits
-          const double work = p.tc ? (double)(tz + p.c.wz) * (region * NN + 16.0 * NN * steps)
+          const double work = p.tc ? (double)(tz + p.c.wz) * (region * NN + 16.0 * NN * steps / q.tc_layers)
                                    : tz * (out * NN + (region - out) * NFF) + p.c.wz * region * NFF +
                                          (double)(tz + p.c.wz) * 4.0 * NN * steps;
           const double cost = (double)waves * work;
@@ -422,10 +424,13 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
             p.ntx = ntx;
             p.nty = nty;
             p.ntz = ntz;
+            p.tc_layers = q.tc_layers;
           }
         }
     if (best == 1e300) return fail(c, PDG_ERR_UNSUPPORTED, "corner box too large for shared memory");
   }
+  if (p.tc && p.tc_layers * std::min(p.tx + p.c.wx, p.ty + p.c.wy) > 128) p.tc_layers = 1;
+  if (p.tc && pdg_corner_smem(p) > 200 * 1024) p.tc_layers = 1;
   if (pdg_corner_smem(p) > 200 * 1024) return fail(c, PDG_ERR_UNSUPPORTED, "corner box too large");
   if (p.threads < 64 || p.threads > 512) return fail(c, PDG_ERR_ARG, "corner pass: threads per block");
   if (p.tc && std::min(p.tx + p.c.wx, p.ty + p.c.wy) > 128)

@@ -30,6 +30,81 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
+// ---- exact conversions by integer operations on the IEEE bit patterns ----
+// GB300's FP64 pipe runs 1/62 of its FP32 rate, and conversions between FP64 and FP32 use
+// it too; these replace them with integer arithmetic.  Magnitudes below 2^-126 (and zero)
+// map to zero (the scheme's values are O(1): that absolute error, < 2^-126, is far below
+// its rounding); infinities and NaNs are not expected and not handled.
+
+// FP32 value from its parts; a biased exponent <= 0 (below the normal range) gives zero.
+__device__ __forceinline__ float f32_from_parts(unsigned sign, int ebiased, unsigned mant23) {
+  if (ebiased <= 0) return 0.0f;
+  return __uint_as_float((sign << 31) | ((unsigned)ebiased << 23) | mant23);
+}
+
+// Round the nonzero magnitude a (leading bit p < 63) to `bits` significant bits, to nearest
+// with ties away from zero: returns the significand (leading one at bit bits - 1) and adds
+// the carry of a round-up past a power of two to *p.
+template <int bits>
+__device__ __forceinline__ unsigned round_sig(unsigned long long a, int* p) {
+  unsigned long long m;
+  if (*p >= bits) {
+    const int sh = *p - (bits - 1);
+    m = (a + (1ull << (sh - 1))) >> sh;
+    if (m == (1ull << bits)) {
+      m >>= 1;
+      ++*p;
+    }
+  } else {
+    m = a << ((bits - 1) - *p);
+  }
+  return (unsigned)m;
+}
+
+// x = hi + lo exactly, hi = x rounded to `bits` significant bits (nearest, ties away), lo =
+// the remainder rounded to `bits` significant bits the same way (so |x - hi - lo| is about
+// 2^(-2 bits) |x|).  bits = 11: the two TF32 parts of a tensor-core operand; bits = 24: a
+// double-float pair.
+template <int bits>
+__device__ __forceinline__ void split_f64_bits(double x, float* hi, float* lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(u >> 63);
+  const int e = (int)((u >> 52) & 0x7ff);   // biased FP64 exponent
+  if (e <= 1023 - 126) {
+    *hi = 0.0f;
+    *lo = 0.0f;
+    return;
+  }
+  const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // x = M 2^(e - 1075)
+  constexpr int sh = 53 - bits;
+  unsigned long long Mh = (M + (1ull << (sh - 1))) >> sh;
+  const long long R = (long long)M - (long long)(Mh << sh);               // |R| <= 2^(sh - 1)
+  int eh = e;
+  if (Mh == (1ull << bits)) {
+    Mh >>= 1;
+    ++eh;
+  }
+  *hi = f32_from_parts(sign, eh - 1023 + 127, (unsigned)(Mh & ((1ull << (bits - 1)) - 1)) << (24 - bits));
+  if (R == 0) {
+    *lo = 0.0f;
+    return;
+  }
+  const unsigned long long a = (unsigned long long)(R < 0 ? -R : R);
+  int p = 63 - __clzll((long long)a);                                      // a = 1.f 2^p
+  const unsigned ml = round_sig<bits>(a, &p);
+  *lo = f32_from_parts(sign ^ (R < 0 ? 1u : 0u), e - 1075 + p + 127, (ml & ((1u << (bits - 1)) - 1)) << (24 - bits));
+}
+
+// The FP64 value of an FP32 value (exact).
+__device__ __forceinline__ double f64_from_f32_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0) return 0.0;
+  const unsigned long long u = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(e + 896) << 52) |
+                               ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)u);
+}
+
 // Shared-memory matrix descriptor: start address, leading / stride byte offsets (all
 // multiples of 16 bytes), descriptor version 1, no swizzle, base offset 0.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {

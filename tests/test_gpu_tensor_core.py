@@ -132,3 +132,26 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable():
     f = s.get_f().reshape((1, cfg.nv) + w0.shape[1:])
     s.close()
     assert_parity(f, run_oracle(cfg, w0, cfg.dt, 2), TOL_MIXED)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("lat,order", [("q15", 1), ("q27", 2), ("q15", 3)])
+def test_layer_pairs_equal_single_layers_bitwise(prec, lat, order):
+    """PDG_OPT_TC_LAYERS: sweeping two box layers together (layer k + 1 one anti-diagonal
+    behind layer k, both anti-diagonals in one product) changes where a cell's row sits in
+    the product, not its arithmetic: the result is bitwise that of one layer at a time, and
+    both match the oracle.  Odd layer counts leave a last single layer."""
+    from paper_1702_00169_gb300 import pdg
+    cfg = _cfg(lat, (3, 2, 3), (2, 3, 1), order)
+    w0 = oracle_w0(cfg)
+    out = {}
+    for layers in (1, 2):
+        s = pdg.solver_for(cfg, precision=prec)
+        s.set_option(pdg.PDG_OPT_TC_LAYERS, layers)
+        s.set_w(np.ascontiguousarray(w0.reshape(-1)))
+        s.step(cfg.dt, 3)
+        out[layers] = s.get_f()
+        s.close()
+    np.testing.assert_array_equal(out[1], out[2])
+    f_ref = run_oracle(cfg, w0, cfg.dt, 3)
+    assert_parity(out[2].reshape(f_ref.shape), f_ref, TOL_MIXED)

@@ -84,6 +84,7 @@ def _prepare(dst):
     os.makedirs(os.path.join(dst, PKG, "lib"))
     for f in ("__init__.py", "pdg.py", "build.py", "workloads.py"):
         shutil.copy(os.path.join(ROOT, PKG, f), os.path.join(dst, PKG, f))
+    shutil.copytree(os.path.join(ROOT, PKG, "csrc"), os.path.join(dst, PKG, "csrc"))   # read by source checks
     os.makedirs(os.path.join(dst, "tests"))
     for f in ["conftest.py", "golden_util.py"] + sorted({p for v in PINS.values() for p in v}):
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(dst, "tests", f))
