@@ -471,11 +471,13 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
  *     launches, bitwise the same results, fewer launch overheads for small meshes.  Plans
  *     and scratch are prepared before the capture.  Ignored while kernel timing is on;
  *     not to be combined with a capture of the context stream by the caller.
- *   PDG_OPT_DEBUG_TC_STALL (default 0): a test switch of the failure path of the
- *     tensor-core corner pass (PDG_PREC_TF32 / PDG_PREC_TF32_DFRES): its one waiting thread
- *     watches an mbarrier that nothing arrives on, with a bound of about 0.5 ms, so the
- *     bounded wait runs out; the pass then records the timeout, waits (boundedly) for its
- *     tensor-core work in flight, frees its tensor memory and returns, and the next
+ *   PDG_OPT_DEBUG_TC_STALL (default 0): a test switch of the failure path of the bounded
+ *     waits of the corner passes.  Tensor-core form (PDG_PREC_TF32 / PDG_PREC_TF32_DFRES):
+ *     its one waiting thread watches an mbarrier that nothing arrives on, with a bound of
+ *     about 0.5 ms, so the bounded wait runs out; the pass then records the timeout, waits
+ *     (boundedly) for its tensor-core work in flight, frees its tensor memory and returns.
+ *     Hyperplane sweep (PDG_OPT_CORNER_SWEEP): every block waits for a count that no block
+ *     reaches, with the same bound, records the timeout and returns.  Either way the next
  *     synchronising call reports PDG_ERR_TIMEOUT once.  The context stays usable: with the
  *     switch off, later steps run normally (from the state left by the aborted passes).
  *   PDG_OPT_TC_LAYERS (default 2): box layers the tensor-core corner pass sweeps together
@@ -496,6 +498,15 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
  *     any axis gives the same scheme (results equal up to rounding); axis 0 has
  *     unit-stride lines, which the line-resident kernel stages most cheaply.  Lattice
  *     models keep the last axis (other values: PDG_ERR_UNSUPPORTED).
+ *   PDG_OPT_CORNER_SWEEP (default 1): how the corner pass of D3Q15 / D3Q27 (FP64 and
+ *     PDG_PREC_DF32) is organised.  1 = hyperplane sweeps: each corner population sweeps
+ *     the whole mesh once, from one truncated upwind start per periodic axis, cell
+ *     hyperplane by hyperplane (column + row + layer = s), each hyperplane shared by the
+ *     blocks of a cooperative launch that meet at a bounded counter wait after every
+ *     hyperplane (a wait that runs out is reported as PDG_ERR_TIMEOUT at the next
+ *     synchronising call); 0 = boxes: one block per box of output cells with its own
+ *     truncated start, no block waiting on another.  Forced box shapes (pdg_set_launch,
+ *     kind 6) and the tensor-core forms use boxes.  Results agree to rounding.
  * Errors: PDG_ERR_ARG (unknown option, axis out of range), PDG_ERR_UNSUPPORTED.
  */
 enum {
@@ -504,7 +515,8 @@ enum {
   PDG_OPT_DEBUG_TC_STALL = 3,
   PDG_OPT_RESIDENT = 4,
   PDG_OPT_COLLISION_AXIS = 5,
-  PDG_OPT_TC_LAYERS = 6
+  PDG_OPT_TC_LAYERS = 6,
+  PDG_OPT_CORNER_SWEEP = 7
 };
 int pdg_set_option(pdg_ctx* ctx, int option, int value);
 

@@ -19,7 +19,7 @@ OBJDIR = os.path.join(ROOT, "_build", "obj")
 LIB = os.path.join(LIBDIR, "libpdg.so")
 
 SOURCES = ["pdg_batch_df.cu", "pdg_batch.cu", "pdg_kernels_df.cu", "pdg_kernels.cu", "pdg_diag_df.cu",
-           "pdg_diag.cu", "pdg_corner_df.cu", "pdg_corner.cu", "pdg_corner_tc.cu", "pdg_api.cu", "pdg_ctx.cu", "pdg_schedule.cu", "pdg_issue.cu", "pdg_autotune.cu",
+           "pdg_diag.cu", "pdg_corner_df.cu", "pdg_corner.cu", "pdg_corner_tc.cu", "pdg_corner_hp.cu", "pdg_corner_hp_df.cu", "pdg_api.cu", "pdg_ctx.cu", "pdg_schedule.cu", "pdg_issue.cu", "pdg_autotune.cu",
            "pdg_batch_api.cu", "pdg_noalloc.cu", "pdg_probe.cu", "pdg_server.cu",
            "pdg_plan.cpp"]
 # pass-kernel instantiations: one object per (number type, group of model variants)

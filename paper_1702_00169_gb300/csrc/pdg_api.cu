@@ -634,6 +634,9 @@ int pdg_set_option(pdg_ctx* c, int option, int value) try {
     case PDG_OPT_RESIDENT:
       c->resident = value != 0;
       return PDG_OK;
+    case PDG_OPT_CORNER_SWEEP:
+      c->corner_sweep = value != 0;
+      return PDG_OK;
     case PDG_OPT_COLLISION_AXIS: {
       Lattice Lat;
       if (value < -1 || value >= c->dim) return fail(c, PDG_ERR_ARG, "collision axis out of range");

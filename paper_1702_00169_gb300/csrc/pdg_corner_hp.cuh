@@ -1,0 +1,536 @@
+// Transport of the corner populations of D3Q15 / D3Q27 by hyperplane sweeps of the whole
+// periodic domain.
+//
+// The operator is that of pdg_corner.cuh (Section 3.1, eq. (3.7) split by axis, the theta
+// step of eq. (3.11)): fn_c = Binv r_c - c1 f_c, r_c = f_c / theta + kx S_x Lt + ky S_y Bt +
+// kz S_z Zt, the faces passed on being theta (Binv r_c).  A cell depends on its three
+// upwind neighbours only, so the cells of a hyperplane j + r + k = s of the (column, row,
+// layer) grid are independent: the 3-D form of the wavefronts of Section 4.2.
+//
+// Region.  Each population sweeps ONE region: the whole mesh plus, along every periodic
+// axis, the start that begins wx (wy, wz) cells upwind (pdg_plan_corner: starting from the
+// old face values there changes no output cell by more than 2^-57 of max|f| per
+// boundary), or, along an inflow axis, the mesh from its inflow face.  The truncated start
+// is paid once per population instead of once per box: at 128^3 cells and a width of 16
+// the region holds 1.42x the output cells (face nodes only in the start), against about
+// 2x for boxes of one block each.
+//
+// Blocks.  G blocks share a population (a cooperative launch of npop x G blocks, all
+// resident at once).  At step s the cells of hyperplane s, enumerated layer by layer
+// (row inside a layer), are cut into G contiguous ranges of equal work (n^3 nodes per
+// output cell, the face nodes per start cell); a block processes its range in batches
+// of nb cells: (A) r_c of every node of a batch in shared memory, (B) the dot products
+// with Binv (transposed in shared memory) for every node of an output cell and for the
+// face nodes of a start cell, while the next batch is copied in with cp.async.
+//
+// Faces.  The faces a cell passes on go to a global buffer (L2-resident), slot [layer]
+// [row] of the RECEIVING cell, in the half of the step parity that reads it: x faces to
+// (k, r) itself, y faces to (k, r + 1), z faces to (k + 1, r).  Every slot has one
+// writer per step.  After a step the G blocks of the population meet at a counter in
+// global memory (release / acquire at GPU scope); the faces are then read with cp.async.cg
+// (L2, never a stale L1 line: the same addresses were read two steps before).  The
+// region's upwind boundaries read the old face values (or the inflow data) instead.
+//
+// Waits.  A block waits only at that counter, and only for blocks of the same launch
+// (all resident).  The wait is bounded (about two seconds of SM clock): if it runs out,
+// or another block has given up, the block records PDG_HP_ERR_TIMEOUT in the launch's
+// error word and returns; the host reports PDG_ERR_TIMEOUT at the next synchronising
+// call.  Nothing else is in flight at the counter (every copy has been waited for).  The
+// test switch p.stall makes every block wait for a count that no block reaches, with a
+// bound of about 0.5 ms, so that the failure path runs without any fault.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pdg_corner.cuh"
+
+#define PDG_HP_ERR_TIMEOUT 2
+
+namespace pdgdev {
+
+// Shared-memory layout of the hyperplane kernel (8-byte words first, then ints).
+template <int NP>
+struct HpShape {
+  static constexpr int NF = NP * NP, NN = NF * NP;
+  static constexpr int NFF = NN - (NP - 1) * (NP - 1) * (NP - 1);   // face nodes of a cell
+  static constexpr int NN2 = (NN + 1) & ~1, NF2 = (NF + 1) & ~1;     // 16-byte rows
+  static constexpr int RS = NN2 + 3 * NF2;   // staged row: state, then the x, y, z inflow faces
+};
+
+struct HpSmem {
+  size_t binv, stage, rbuf, colx, rowy, layz, rcell, ritem, cr, ck, cit, misc, total;
+  __host__ __device__ HpSmem(int n, int nb, int RX, int RY, int RZ) {
+    const int NF = n * n, NN = NF * n, NN2 = (NN + 1) & ~1, NF2 = (NF + 1) & ~1, RS = NN2 + 3 * NF2;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      o = (o + 15) / 16 * 16;
+      const size_t at = o;
+      o += bytes;
+      return at;
+    };
+    binv = take(sizeof(double) * NN * NN);
+    stage = take(sizeof(double) * 2 * (size_t)nb * RS);
+    rbuf = take(sizeof(double) * (size_t)nb * NN);
+    colx = take(sizeof(long long) * (RX + 1));
+    rowy = take(sizeof(long long) * (RY + 1));
+    layz = take(sizeof(long long) * (RZ + 1));
+    rcell = take(sizeof(int) * (RZ + 1));
+    ritem = take(sizeof(int) * (RZ + 1));
+    cr = take(sizeof(int) * 2 * nb);
+    ck = take(sizeof(int) * 2 * nb);
+    cit = take(sizeof(int) * 2 * (nb + 1));
+    misc = take(sizeof(int) * 96);   // fnode[NFF <= 37], range bounds, abort flag, warp sums
+    total = o;
+  }
+};
+
+// 16-byte copy global -> shared that bypasses L1 (cp.async.cg): face slots written by
+// other blocks since this block last read the same addresses.
+__device__ __forceinline__ void cp_async16_cg(void* smem, const double* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Rows of hyperplane s in layer k: r in [rlo, rhi] (j = s - r - k in [0, RX)); returns the
+// count (0 when the layer does not meet the hyperplane).
+__device__ __forceinline__ int hp_rows(int s, int k, int RX, int RY, int* rlo, int* rhi) {
+  *rlo = max(0, s - k - (RX - 1));
+  *rhi = min(RY - 1, s - k);
+  return max(0, *rhi - *rlo + 1);
+}
+
+// Output rows of layer k on hyperplane s: [olo, ohi] (j >= wx, r >= wy, k >= wz).
+__device__ __forceinline__ int hp_out_rows(int s, int k, int rlo, int rhi, int wx, int wy, int wz, int* olo) {
+  if (k < wz) {
+    *olo = 0;
+    return 0;
+  }
+  *olo = max(rlo, wy);
+  const int ohi = min(rhi, s - k - wx);
+  return max(0, ohi - *olo + 1);
+}
+
+template <int NP, class T>
+__device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned char* smraw) {
+  using S = HpShape<NP>;
+  constexpr int NF = S::NF, NN = S::NN, NFF = S::NFF, NN2 = S::NN2, NF2 = S::NF2, RS = S::RS;
+  constexpr int NT = 512;
+  const int G = p.hg, nb = p.hnb;
+  const int pop = blockIdx.x / G, gi = blockIdx.x % G;
+  const PdgCornerCoef& C = p.c;
+  const int tid = threadIdx.x;
+
+  CornerGeom g;
+  g.fin = p.fin[pop];
+  g.fout = p.fout[pop];
+  g.sx = p.sx[pop];
+  g.sy = p.sy[pop];
+  g.sz = p.sz[pop];
+  g.sa = p.sa;
+  g.sb = p.sb;
+  g.sc = p.sc;
+  g.wx = p.per[0] ? C.wx : 0;
+  g.wy = p.per[1] ? C.wy : 0;
+  g.wz = p.per[2] ? C.wz : 0;
+  g.bx = !p.per[0];
+  g.by = !p.per[1];
+  g.bz = !p.per[2];
+  g.X0 = g.Y0 = g.Z0 = 0;
+  g.ncx = p.ncx;
+  g.ncy = p.ncy;
+  g.ncz = p.ncz;
+  const double* fbs[3];
+  for (int a = 0; a < 3; ++a) {
+    fbs[a] = p.fb[a] ? p.fb[a] + (long long)(p.bside[a][pop] * p.nent + p.bent[a][pop]) * p.flines[a] : nullptr;
+    for (int b = 0; b < 3; ++b) g.fls[a][b] = p.fls[a][b];
+  }
+  g.fbx = fbs[0];
+  g.fby = fbs[1];
+  g.fbz = fbs[2];
+  const int RX = p.ncx + g.wx, RY = p.ncy + g.wy, RZ = p.ncz + g.wz;
+  g.ncol = RX;
+  g.nrow = RY;
+  g.nlay = RZ;
+  g.zt = nullptr;
+
+  const HpSmem L(NP, nb, RX, RY, RZ);
+  T* BinvT = reinterpret_cast<T*>(smraw + L.binv);
+  T* stage = reinterpret_cast<T*>(smraw + L.stage);   // 8-byte words (FP64 or a float pair)
+  T* rbuf = reinterpret_cast<T*>(smraw + L.rbuf);
+  long long* colx = reinterpret_cast<long long*>(smraw + L.colx);
+  long long* rowy = reinterpret_cast<long long*>(smraw + L.rowy);
+  long long* layz = reinterpret_cast<long long*>(smraw + L.layz);
+  int* rcell = reinterpret_cast<int*>(smraw + L.rcell);
+  int* ritem = reinterpret_cast<int*>(smraw + L.ritem);
+  int* cr = reinterpret_cast<int*>(smraw + L.cr);
+  int* ck = reinterpret_cast<int*>(smraw + L.ck);
+  int* cit = reinterpret_cast<int*>(smraw + L.cit);
+  int* misc = reinterpret_cast<int*>(smraw + L.misc);
+  int* fnode = misc;            // [NFF]
+  int* range = misc + 40;       // [2]: this block's cells [range[0], range[1]) of the step
+  volatile int* abort_flag = misc + 42;
+  int* wsum = misc + 48;        // [16]: per-warp sums
+  int* wsum2 = misc + 64;       // [16]
+
+  for (int i = tid; i < NN * NN; i += NT) {
+    const int row = i % NN, col = i / NN;   // BinvT[col][row] = Binv[row][col]
+    if constexpr (__is_same(T, double)) {
+      BinvT[i] = p.binv[row * NN + col];
+    } else {
+      const float* bf = p.binv_f + 2 * (row * NN + col);
+      BinvT[i] = T{bf[0], bf[1]};
+    }
+  }
+  if (tid == 0) {
+    int f = 0;
+    for (int q = 0; q < NN; ++q)
+      if (q % NP == NP - 1 || (q / NP) % NP == NP - 1 || q / NF == NP - 1) fnode[f++] = q;
+    *abort_flag = 0;
+  }
+  for (int j = tid; j <= RX; j += NT) {
+    const int tc = wrap_cell(j - 1 - g.wx, p.ncx);
+    colx[j] = (long long)(g.sx > 0 ? tc * NP : (p.ncx - 1 - tc) * NP + (NP - 1)) * g.sa;
+  }
+  for (int r = tid; r <= RY; r += NT) {
+    const int tr = wrap_cell(r - 1 - g.wy, p.ncy);
+    rowy[r] = (long long)(g.sy > 0 ? tr * NP : (p.ncy - 1 - tr) * NP + (NP - 1)) * g.sb;
+  }
+  for (int k = tid; k <= RZ; k += NT) {
+    const int tl = wrap_cell(k - 1 - g.wz, p.ncz);
+    layz[k] = (long long)(g.sz > 0 ? tl * NP : (p.ncz - 1 - tl) * NP + (NP - 1)) * g.sc;
+  }
+  g.colx = colx;
+  g.rowy = rowy;
+  g.layz = layz;
+  __syncthreads();
+
+  const T rth = PDG_DC(T, C, rtheta), c1 = PDG_DC(T, C, c1);
+  const T th = PDG_DC(T, C, theta);
+  const T kx = PDG_DC(T, C, kx), ky = PDG_DC(T, C, ky), kz = PDG_DC(T, C, kz);
+  // face slots of this population: [parity][face a][layer][row][NF2]
+  const long long slab = (long long)RZ * RY * NF2;
+  double* hf = p.hface + (long long)pop * 6 * slab;
+  unsigned* bar = p.hbar + pop;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int NS = RX + RY + RZ - 2;
+
+  // cells [c0, c0 + cnt) of the step (c0 relative to the hyperplane's enumeration): their
+  // coordinates, and the start of each cell's items (n^3 for an output cell, NFF else)
+  auto batch_info = [&](int s, int c0, int cnt, int buf) {
+    int items = 0;
+    if (tid < cnt) {
+      const int c = c0 + tid;
+      int lo = 0, hi = RZ - 1;   // the layer: last k with rcell[k] <= c
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rcell[mid] <= c) lo = mid;
+        else hi = mid - 1;
+      }
+      int rlo, rhi;
+      hp_rows(s, lo, RX, RY, &rlo, &rhi);
+      const int r = rlo + (c - rcell[lo]);
+      cr[buf * nb + tid] = r;
+      ck[buf * nb + tid] = lo;
+      const int j = s - r - lo;
+      items = (j >= g.wx && r >= g.wy && lo >= g.wz) ? NN : NFF;
+    }
+    // exclusive scan of items over the batch (cnt <= nb <= 512)
+    int v = items;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += u;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < warp; ++w) base += wsum[w];
+    if (tid < cnt) cit[buf * (nb + 1) + tid] = base + v - items;
+    if (tid == cnt - 1) cit[buf * (nb + 1) + cnt] = base + v;
+  };
+
+  // copy the state and the inflow faces of the batch's cells into stage[buf]
+  auto stage_batch = [&](int s, int cnt, int buf) {
+    double* sb = reinterpret_cast<double*>(stage + (size_t)buf * nb * RS);
+    const int par = s & 1;
+    constexpr int per = NN + 3 * NF2;
+    for (int i = tid; i < cnt * per; i += NT) {
+      const int c = i / per, e = i % per;
+      const int r = cr[buf * nb + c], k = ck[buf * nb + c], j = s - r - k;
+      double* row = sb + (size_t)c * RS;
+      if (e < NN) {
+        cp_async8(row + e, g.fin + corner_off(g, j, r, k, e / NF, (e / NP) % NP, e % NP));
+        continue;
+      }
+      const int a = (e - NN) / NF2, u = (e - NN) % NF2;
+      double* dst = row + NN2 + a * NF2 + u;
+      const bool edge = a == 0 ? j == 0 : (a == 1 ? r == 0 : k == 0);
+      if (!edge) {
+        if ((u & 1) == 0) cp_async16_cg(dst, hf + ((long long)(par * 3 + a) * RZ + k) * RY * NF2 + (long long)r * NF2 + u);
+        continue;
+      }
+      if (u >= NF) continue;
+      const int u1 = u / NP, u2 = u % NP;
+      const double* src;
+      if (a == 0) {   // +x face of the cell upwind of column 0: node (iz, iy) = (u1, u2)
+        src = g.bx ? g.fbx + corner_py<NP>(g, r, u2) * g.fls[0][1] + corner_pz<NP>(g, k, u1) * g.fls[0][2]
+                   : g.fin + corner_off(g, -1, r, k, u1, u2, NP - 1);
+      } else if (a == 1) {   // +y face below row 0: node (iz, ix) = (u1, u2)
+        src = g.by ? g.fby + corner_px<NP>(g, j, u2) * g.fls[1][0] + corner_pz<NP>(g, k, u1) * g.fls[1][2]
+                   : g.fin + corner_off(g, j, -1, k, u1, NP - 1, u2);
+      } else {   // +z face under layer 0: node (iy, ix) = (u1, u2)
+        src = g.bz ? g.fbz + corner_px<NP>(g, j, u2) * g.fls[2][0] + corner_py<NP>(g, r, u1) * g.fls[2][1]
+                   : g.fin + corner_off(g, j, r, -1, NP - 1, u1, u2);
+      }
+      cp_async8(dst, src);
+    }
+  };
+
+  for (int s = 0; s < NS; ++s) {
+    // (0) cells and items of hyperplane s per layer, exclusive prefix over the layers
+    {
+      const int per_t = (RZ + NT - 1) / NT, k0 = tid * per_t;
+      int cs = 0, is = 0;
+      for (int k = k0; k < min(RZ, k0 + per_t); ++k) {
+        int rlo, rhi, olo;
+        const int n = hp_rows(s, k, RX, RY, &rlo, &rhi);
+        const int no = n ? hp_out_rows(s, k, rlo, rhi, g.wx, g.wy, g.wz, &olo) : 0;
+        cs += n;
+        is += n * NFF + no * (NN - NFF);
+      }
+      int vc = cs, vi = is;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int uc = __shfl_up_sync(0xffffffffu, vc, d), ui = __shfl_up_sync(0xffffffffu, vi, d);
+        if (lane >= d) {
+          vc += uc;
+          vi += ui;
+        }
+      }
+      if (lane == 31) {
+        wsum[warp] = vc;
+        wsum2[warp] = vi;
+      }
+      __syncthreads();
+      int bc = 0, bi = 0;
+      for (int w = 0; w < warp; ++w) {
+        bc += wsum[w];
+        bi += wsum2[w];
+      }
+      int pc = bc + vc - cs, pi = bi + vi - is;   // exclusive prefixes at k0
+      for (int k = k0; k < min(RZ, k0 + per_t); ++k) {
+        rcell[k] = pc;
+        ritem[k] = pi;
+        int rlo, rhi, olo;
+        const int n = hp_rows(s, k, RX, RY, &rlo, &rhi);
+        const int no = n ? hp_out_rows(s, k, rlo, rhi, g.wx, g.wy, g.wz, &olo) : 0;
+        pc += n;
+        pi += n * NFF + no * (NN - NFF);
+      }
+      if (tid == NT - 1) {
+        rcell[RZ] = pc;
+        ritem[RZ] = pi;
+      }
+      __syncthreads();
+    }
+    // (1) this block's cells: those whose first item lies in [I gi / G, I (gi + 1) / G)
+    if (tid < 2) {
+      const long long I = ritem[RZ];
+      const int P = (int)(I * (gi + tid) / G);
+      int c = rcell[RZ];
+      if (P < I) {
+        int lo = 0, hi = RZ - 1;   // layer with ritem[k] <= P < ritem[k + 1]
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (ritem[mid] <= P) lo = mid;
+          else hi = mid - 1;
+        }
+        int rlo, rhi, olo;
+        hp_rows(s, lo, RX, RY, &rlo, &rhi);
+        const int no = hp_out_rows(s, lo, rlo, rhi, g.wx, g.wy, g.wz, &olo);
+        // first row r of the layer whose first item is >= P
+        int a = rlo, b = rhi + 1;
+        while (a < b) {
+          const int m = (a + b) >> 1;
+          const int before_out = no ? max(0, min(m, olo + no) - olo) : 0;
+          const int start = ritem[lo] + (m - rlo) * NFF + before_out * (NN - NFF);
+          if (start >= P) b = m;
+          else a = m + 1;
+        }
+        c = rcell[lo] + (a - rlo);
+      }
+      range[tid] = c;
+    }
+    __syncthreads();
+    const int cb = range[0], ce = range[1];
+    const int nbat = (ce - cb + nb - 1) / nb;
+    if (nbat > 0) {
+      batch_info(s, cb, min(nb, ce - cb), 0);
+      __syncthreads();
+      stage_batch(s, min(nb, ce - cb), 0);
+    }
+    for (int bI = 0; bI < nbat; ++bI) {
+      const int buf = bI & 1;
+      const int c0 = cb + bI * nb, cnt = min(nb, ce - c0);
+      cp_async_wait_all();
+      __syncthreads();
+      // (A) r_c of every node of the batch
+      const T* sb = stage + (size_t)buf * nb * RS;
+      for (int i = tid; i < cnt * NN; i += NT) {
+        const int c = i / NN, q = i % NN;
+        const int iz = q / NF, iy = (q / NP) % NP, ix = q % NP;
+        const T* row = sb + (size_t)c * RS;
+        T rv = row[q] * rth;
+        if (ix == 0) rv = fma(kx, row[NN2 + iz * NP + iy], rv);
+        if (iy == 0) rv = fma(ky, row[NN2 + NF2 + iz * NP + ix], rv);
+        if (iz == 0) rv = fma(kz, row[NN2 + 2 * NF2 + iy * NP + ix], rv);
+        rbuf[(size_t)c * NN + q] = rv;
+      }
+      const bool more = bI + 1 < nbat;
+      if (more) batch_info(s, c0 + nb, min(nb, ce - c0 - nb), buf ^ 1);   // has its own barrier
+      __syncthreads();
+      if (more) stage_batch(s, min(nb, ce - c0 - nb), buf ^ 1);
+      // (B) items of the batch: every node of an output cell, the face nodes of a start cell
+      const int* itb = cit + buf * (nb + 1);
+      const int nitems = itb[cnt];
+      const int par1 = (s + 1) & 1;
+      for (int it = tid; it < nitems; it += NT) {
+        int lo = 0, hi = cnt - 1;   // the cell: last c with itb[c] <= it
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (itb[mid] <= it) lo = mid;
+          else hi = mid - 1;
+        }
+        const int c = lo, loc = it - itb[c];
+        const bool out = itb[c + 1] - itb[c] == NN;
+        const int q = out ? loc : fnode[loc];
+        const T* rc = rbuf + (size_t)c * NN;
+        T acc;
+        if constexpr (__is_same(T, double)) {
+          double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+          for (int m = 0; m + 1 < NN; m += 2) {
+            a0 = fma(BinvT[m * NN + q], rc[m], a0);
+            a1 = fma(BinvT[(m + 1) * NN + q], rc[m + 1], a1);
+          }
+          if (NN % 2) a0 = fma(BinvT[(NN - 1) * NN + q], rc[NN - 1], a0);
+          acc = a0 + a1;
+        } else {
+          float Sh = 0.0f, Ll = 0.0f;
+#pragma unroll 8
+          for (int m = 0; m < NN; ++m) {
+            const T a = BinvT[m * NN + q], bv = rc[m];
+            const dd pr = dd_two_prod(a.hi, bv.hi);
+            const float cross = __fmaf_rn(a.hi, bv.lo, __fmul_rn(a.lo, bv.hi));
+            const dd sm2 = dd_two_sum(Sh, pr.hi);
+            Sh = sm2.hi;
+            Ll = __fadd_rn(Ll, __fadd_rn(sm2.lo, __fadd_rn(pr.lo, cross)));
+          }
+          acc = dd_fast_two_sum(Sh, Ll);
+        }
+        const int r = cr[buf * nb + c], k = ck[buf * nb + c], j = s - r - k;
+        const int qz = q / NF, qy = (q / NP) % NP, qx = q % NP;
+        if (out) st(g.fout + corner_off(g, j, r, k, qz, qy, qx), acc - c1 * sb[(size_t)c * RS + q]);
+        if (qx == NP - 1 || qy == NP - 1 || qz == NP - 1) {
+          const T face = th * acc;
+          if (qx == NP - 1 && j + 1 < RX)
+            st(hf + ((long long)(par1 * 3 + 0) * RZ + k) * RY * NF2 + (long long)r * NF2 + qz * NP + qy, face);
+          if (qy == NP - 1 && r + 1 < RY)
+            st(hf + ((long long)(par1 * 3 + 1) * RZ + k) * RY * NF2 + (long long)(r + 1) * NF2 + qz * NP + qx, face);
+          if (qz == NP - 1 && k + 1 < RZ)
+            st(hf + ((long long)(par1 * 3 + 2) * RZ + k + 1) * RY * NF2 + (long long)r * NF2 + qy * NP + qx, face);
+        }
+      }
+    }
+    // (2) the population's blocks meet: every face of step s is written before any block
+    // reads it at step s + 1 (none is in flight: the copies were waited for above)
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(bar, 1u);
+      // test switch (p.stall): a count no block reaches, with a bound of about 0.5 ms
+      const unsigned target = p.stall ? 0xffffffffu : (unsigned)G * (unsigned)(s + 1);
+      const long long limit = p.stall ? 1000000LL : 4000000000LL;
+      const long long t0 = clock64();
+      int ok = 1;
+      while (ld_acquire_gpu(bar) < target) {
+        if (*(volatile int*)p.err != 0 || clock64() - t0 > limit) {
+          atomicCAS(p.err, 0, PDG_HP_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+      if (!ok) *abort_flag = 1;
+    }
+    __syncthreads();
+    if (*abort_flag) return;
+  }
+}
+
+template <int NP, class T>
+__global__ void __launch_bounds__(512, 1) corner_hp_kernel(const __grid_constant__ PdgCornerPass p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  corner_hp_body<NP, T>(p, smraw);
+}
+
+// Blocks of the kernel for n that fit one SM with smem bytes of shared memory.
+template <class T>
+int hp_blocks_per_sm(int n, size_t smem) {
+  auto occ = [&](auto kern) -> int {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 512, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return b;
+  };
+  switch (n) {
+    case 2: return occ(corner_hp_kernel<2, T>);
+    case 3: return occ(corner_hp_kernel<3, T>);
+    case 4: return occ(corner_hp_kernel<4, T>);
+  }
+  return 0;
+}
+
+// Cooperative launch of npop x hg blocks of 512 threads (the host sized hg so that all are
+// resident).
+template <class T>
+int launch_corner_hp_typed(const PdgCornerPass& p, size_t smem, cudaStream_t st) {
+  auto go = [&](auto kern) -> int {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaMemsetAsync(p.hbar, 0, sizeof(unsigned) * 8, st);
+    if (e != cudaSuccess) return (int)e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(p.npop * p.hg));
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, p);
+    return (int)e;
+  };
+  switch (p.n) {
+    case 2: return go(corner_hp_kernel<2, T>);
+    case 3: return go(corner_hp_kernel<3, T>);
+    case 4: return go(corner_hp_kernel<4, T>);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace pdgdev

@@ -53,19 +53,23 @@ int cuda_fail(pdg_ctx* c, cudaError_t e, const char* what) {
   return fail(c, PDG_ERR_CUDA, m);
 }
 
-// After a synchronisation of the context stream: a bounded wait of the tensor-core corner
-// kernel that ran out (its error word set) is reported once as PDG_ERR_TIMEOUT, and the
-// word is cleared.  The state of the steps in flight then is incomplete.
+// After a synchronisation of the context stream: a bounded wait of a corner kernel that
+// ran out (its error word set: the tensor-core kernel's wait for its products, or the
+// hyperplane kernel's wait for the other blocks of its population) is reported once as
+// PDG_ERR_TIMEOUT, and the word is cleared.  The state of the steps in flight then is
+// incomplete.
 int check_device_error(pdg_ctx* c) {
-  if (!c->dev_err || !c->tc) return 0;
+  if (!c->dev_err) return 0;
   int v = 0;
   PDG_CUDA(c, cudaMemcpyAsync(&v, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PDG_CUDA(c, cudaStreamSynchronize(c->stream));
   if (!v) return 0;
   PDG_CUDA(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
   PDG_CUDA(c, cudaStreamSynchronize(c->stream));
-  return fail(c, PDG_ERR_TIMEOUT,
-              "tensor-core corner pass: a bounded wait for the tensor cores ran out; the state is incomplete");
+  return fail(c, PDG_ERR_TIMEOUT, v == 2 ? "corner pass: a bounded wait for the other blocks of a hyperplane ran "
+                                           "out; the state is incomplete"
+                                         : "tensor-core corner pass: a bounded wait for the tensor cores ran out; "
+                                           "the state is incomplete");
 }
 
 cudaEvent_t get_event(pdg_ctx* c) {

@@ -62,10 +62,12 @@ struct pdg_ctx {
   int* dev_err = nullptr;                      // error word of the tensor-core kernel (in cbuf)
   int tc_stall = 0;                            // PDG_OPT_DEBUG_TC_STALL
   int tc_layers = 2;                           // PDG_OPT_TC_LAYERS
+  int corner_sweep = 1;                        // PDG_OPT_CORNER_SWEEP (1 hyperplanes, 0 boxes)
   int resident = 0;                            // PDG_OPT_RESIDENT
   int rshape[2][3] = {{0, 0, 0}, {0, 0, 0}};   // line-resident shapes per pass kind (0 = heuristic)
   int caxis = -1;                              // PDG_OPT_COLLISION_AXIS (-1: the last axis)
-  double* czt = nullptr;                       // corner pass: per-block +z face scratch
+  double* czt = nullptr;                       // corner pass: per-block +z face scratch (boxes) or
+                                               // the face slots of the hyperplane sweep
   // CUDA-graph replay of pdg_step (PDG_OPT_GRAPH): the captured step sequence, its key
   // (dt, nsteps, configuration generation) and the private capture / replay stream
   bool use_graph = false;

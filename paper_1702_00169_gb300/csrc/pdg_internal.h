@@ -256,6 +256,12 @@ struct PdgCornerPass {
   int tc_layers;                   // tensor-core kernel: box layers swept together (1 or 2; 2 when
                                    // two anti-diagonals fit the 128 rows of a product)
   double* zt;                      // device scratch: per block [ty + wy][tx + wx][n^2] +z faces
+  // hyperplane sweep of the whole region (hyper != 0; pdg_corner_hp.cuh): hg blocks per
+  // population in a cooperative launch, batches of hnb cells, face slots hface
+  // ([npop][2][3][nlay][nrow][n^2 rounded to even]) and one step counter per population
+  int hyper, hg, hnb;
+  double* hface;
+  unsigned* hbar;
   // inflow axes (per axis a: per[a] = 1 periodic); boundary data fb[a] = [2 sides][nent][lines]
   // of the faces normal to a, each population's side and entry there; a face point's line
   // index is sum over the other axes b of (point coordinate along b) * fls[a][b]
@@ -351,6 +357,11 @@ int pdg_launch_corner(const PdgCornerPass& p, void* stream);
 size_t pdg_corner_smem(const PdgCornerPass& p);
 int pdg_launch_corner_tc(const PdgCornerPass& p, size_t smem, void* stream);
 size_t pdg_corner_tc_smem(const PdgCornerPass& p);
+// Hyperplane form (pdg_corner_hp.cu): launch, shared memory of a block, and how many of
+// its blocks fit one SM (0 when none does).
+int pdg_launch_corner_hp(const PdgCornerPass& p, size_t smem, void* stream);
+size_t pdg_corner_hp_smem(const PdgCornerPass& p);
+int pdg_corner_hp_blocks_per_sm(const PdgCornerPass& p, size_t smem);
 // The tensor-core operands of a corner plan: for n = d + 1, NN = n^3, K = NN rounded up to
 // a multiple of 8 and N = max(16, K), two arrays (TF32 high parts, then low parts) of N x K
 // floats each in the MMA's core-matrix layout (pdg_tc.cuh), zero beyond NN.  Returns the

@@ -284,6 +284,70 @@ int make_diag(pdg_ctx* c, const PdgPassSpec& sp, int o, PdgDiagPass* out) {
   return PDG_OK;
 }
 
+// The hyperplane form of the corner pass (pdg_corner_hp.cuh): batch size, blocks per
+// population and the face slots.  Returns 1 when planned, 0 when the form does not apply
+// here (the caller plans boxes), -1 on a failed allocation (the context error is set).
+int plan_corner_hyper(pdg_ctx* c, PdgCornerPass* pp) {
+  PdgCornerPass& p = *pp;
+  int dev = 0, coop = 0;   // cooperative launches (every GB300 has them)
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
+    coop = 0;
+  cudaGetLastError();
+  if (!coop || !c->dev_err) return 0;
+  const int RX = p.ncx + (p.per[0] ? p.c.wx : 0), RY = p.ncy + (p.per[1] ? p.c.wy : 0);
+  const int RZ = p.ncz + (p.per[2] ? p.c.wz : 0);
+  const long long NN = (long long)p.n * p.n * p.n, NF2 = ((long long)p.n * p.n + 1) & ~1LL;
+  if ((long long)RY * RZ * NN >= (1LL << 30)) return 0;   // item counts of a step in 32 bits
+  p.hyper = 1;
+  p.threads = 512;
+  p.hnb = p.n == 2 ? 256 : (p.n == 3 ? 128 : 64);
+  while (p.hnb > 16 && pdg_corner_smem(p) > 220 * 1024) p.hnb /= 2;
+  if (pdg_corner_smem(p) > 220 * 1024) {
+    p.hyper = 0;
+    return 0;
+  }
+  // blocks per population: all resident (cooperative launch), and no more than the
+  // largest hyperplane has cells for (about 32 cells per block)
+  long long maxcells = 0;
+  for (int s = 0; s < RX + RY + RZ - 2; ++s) {
+    long long n = 0;
+    for (int k = 0; k < RZ; ++k) {
+      const int rlo = std::max(0, s - k - (RX - 1)), rhi = std::min(RY - 1, s - k);
+      if (rhi >= rlo) n += rhi - rlo + 1;
+    }
+    maxcells = std::max(maxcells, n);
+  }
+  const int per_sm = pdg_corner_hp_blocks_per_sm(p, pdg_corner_smem(p));
+  if (per_sm < 1) {
+    p.hyper = 0;
+    return 0;
+  }
+  const long long resident = (long long)per_sm * pdg_sm_count();
+  long long G = std::min<long long>(resident / p.npop, std::max<long long>(1, maxcells / 32));
+  if (G < 1) {
+    p.hyper = 0;
+    return 0;
+  }
+  p.hg = (int)G;
+  const size_t words = (size_t)p.npop * 6 * RZ * RY * NF2;
+  if (words > c->czt_cap) {
+    if (c->czt) cudaFree(c->czt);
+    c->czt = nullptr;
+    c->czt_cap = 0;
+    cudaError_t e = cudaMalloc((void**)&c->czt, sizeof(double) * words);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->czt = nullptr;
+      fail(c, PDG_ERR_OOM, std::string("corner face slots: ") + cudaGetErrorString(e));
+      return -1;
+    }
+    c->czt_cap = words;
+  }
+  p.hface = c->czt;
+  p.hbar = reinterpret_cast<unsigned*>(c->dev_err + 16);
+  return 1;
+}
+
 // Launch descriptor of the corner pass of a diagonal sub-step: the eight corner populations
 // (slots diag + 4 norient ..), read from slot set dslot_in and written to the other set.
 // The box counts minimise the swept volume per SM (output cells plus the upwind start,
@@ -371,6 +435,13 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
   }
   p.prec = c->model.prec;
   p.threads = c->cshape[0] && !p.tc ? c->cshape[0] : 512;   // the tensor-core kernel runs 16 warps
+  // hyperplane sweep of the whole region (default; not for forced box shapes or the
+  // tensor-core form), when its tables fit shared memory and its blocks can all be resident
+  if (c->corner_sweep && !p.tc && !c->cshape[1]) {
+    int r = plan_corner_hyper(c, &p);
+    if (r < 0) return fail(c, PDG_ERR_UNSUPPORTED, "internal: corner hyperplane plan");
+    if (r == 1) return PDG_OK;
+  }
   if (c->cshape[1]) {
     p.tx = std::min(c->cshape[1], p.ncx);
     p.ty = std::min(c->cshape[2], p.ncy);

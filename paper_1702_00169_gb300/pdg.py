@@ -31,6 +31,7 @@ PDG_OPT_DEBUG_TC_STALL = 3
 PDG_OPT_RESIDENT = 4
 PDG_OPT_COLLISION_AXIS = 5
 PDG_OPT_TC_LAYERS = 6
+PDG_OPT_CORNER_SWEEP = 7
 
 KIND = {"advection": PDG_MODEL_ADVECTION, "shallow_water": PDG_MODEL_SHALLOW_WATER, "euler": PDG_MODEL_EULER,
         "isothermal_d2q9": PDG_MODEL_ISOTHERMAL_D2Q9, "isothermal_d3q19": PDG_MODEL_ISOTHERMAL_D3Q19,
