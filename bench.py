@@ -190,6 +190,8 @@ def parse_args():
                          "last-axis passes instead of autotuning (reproduces a timed configuration)")
     ap.add_argument("--tc-layers", type=int, default=2, choices=[1, 2],
                     help="tensor-core corner pass: box layers swept together (PDG_OPT_TC_LAYERS)")
+    ap.add_argument("--corner-sweep", type=int, default=1, choices=[0, 1],
+                    help="corner pass of D3Q15 / D3Q27: 1 hyperplanes, 0 boxes (PDG_OPT_CORNER_SWEEP)")
     ap.add_argument("--resident", type=int, default=0,
                     help="1: line passes run the line-resident kernel (PDG_OPT_RESIDENT)")
     ap.add_argument("--caxis", type=int, default=-1,
@@ -739,6 +741,8 @@ def main():
             sv.set_source(**SOURCES[args.source])
         if precision in ("tf32", "tf32_df"):
             sv.set_option(pdg.PDG_OPT_TC_LAYERS, args.tc_layers)
+        if not args.corner_sweep:
+            sv.set_option(pdg.PDG_OPT_CORNER_SWEEP, 0)
         if args.resident:
             sv.set_option(pdg.PDG_OPT_RESIDENT, 1)
         if args.caxis >= 0:
@@ -1030,6 +1034,7 @@ def main():
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                        "collision_axis": args.caxis if args.caxis >= 0 else cfg.dim - 1,
                        "line_resident": bool(args.resident),
+                       "corner_sweep": "hyperplanes" if args.corner_sweep else "boxes",
                        "launch_shapes": {"autotuned": not args.no_autotune and not args.shapes,
                                          "transport_pass": list(shape0),
                                          "last_axis_pass": list(shape1)}},

@@ -20,8 +20,11 @@
 // (row inside a layer), are cut into G contiguous ranges of equal work (n^3 nodes per
 // output cell, the face nodes per start cell); a block processes its range in batches
 // of nb cells: (A) r_c of every node of a batch in shared memory, (B) the dot products
-// with Binv (transposed in shared memory) for every node of an output cell and for the
-// face nodes of a start cell, while the next batch is copied in with cp.async.
+// with Binv (row-major in shared memory, rows padded so that the 16-byte pair loads of
+// neighbouring nodes fall on different banks) for every node of an output cell and for
+// the face nodes of a start cell, while the next batch is copied in with cp.async.  The
+// first batch of the next hyperplane is planned and its state copied in before the blocks
+// meet (the state does not depend on the other blocks; the faces do).
 //
 // Faces.  The faces a cell passes on go to a global buffer (L2-resident), slot [layer]
 // [row] of the RECEIVING cell, in the half of the step parity that reads it: x faces to
@@ -35,9 +38,10 @@
 // (all resident).  The wait is bounded (about two seconds of SM clock): if it runs out,
 // or another block has given up, the block records PDG_HP_ERR_TIMEOUT in the launch's
 // error word and returns; the host reports PDG_ERR_TIMEOUT at the next synchronising
-// call.  Nothing else is in flight at the counter (every copy has been waited for).  The
-// test switch p.stall makes every block wait for a count that no block reaches, with a
-// bound of about 0.5 ms, so that the failure path runs without any fault.
+// call.  The copies in flight at the counter (the next state) are waited for before the
+// block returns.  The test switch p.stall makes every block wait for a count that no
+// block reaches, with a bound of about 0.5 ms, so that the failure path runs without
+// any fault.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -47,19 +51,21 @@
 
 namespace pdgdev {
 
-// Shared-memory layout of the hyperplane kernel (8-byte words first, then ints).
+// Shared-memory layout of the hyperplane kernel.
 template <int NP>
 struct HpShape {
   static constexpr int NF = NP * NP, NN = NF * NP;
   static constexpr int NFF = NN - (NP - 1) * (NP - 1) * (NP - 1);   // face nodes of a cell
   static constexpr int NN2 = (NN + 1) & ~1, NF2 = (NF + 1) & ~1;     // 16-byte rows
   static constexpr int RS = NN2 + 3 * NF2;   // staged row: state, then the x, y, z inflow faces
+  static constexpr int BS = NN2 + ((NN2 / 2) % 2 == 0 ? 2 : 0);   // Binv row stride: odd in 16-byte units
 };
 
 struct HpSmem {
-  size_t binv, stage, rbuf, colx, rowy, layz, rcell, ritem, cr, ck, cit, misc, total;
+  size_t binv, stage, rbuf, off0, nodeoff, colx, rowy, layz, rcell, ritem, cr, ck, cit, icell, misc, total;
   __host__ __device__ HpSmem(int n, int nb, int RX, int RY, int RZ) {
     const int NF = n * n, NN = NF * n, NN2 = (NN + 1) & ~1, NF2 = (NF + 1) & ~1, RS = NN2 + 3 * NF2;
+    const int BS = NN2 + ((NN2 / 2) % 2 == 0 ? 2 : 0);
     size_t o = 0;
     auto take = [&](size_t bytes) {
       o = (o + 15) / 16 * 16;
@@ -67,9 +73,11 @@ struct HpSmem {
       o += bytes;
       return at;
     };
-    binv = take(sizeof(double) * NN * NN);
+    binv = take(sizeof(double) * NN * BS);
     stage = take(sizeof(double) * 2 * (size_t)nb * RS);
-    rbuf = take(sizeof(double) * (size_t)nb * NN);
+    rbuf = take(sizeof(double) * (size_t)nb * NN2);
+    off0 = take(sizeof(long long) * 2 * nb);
+    nodeoff = take(sizeof(long long) * NN);
     colx = take(sizeof(long long) * (RX + 1));
     rowy = take(sizeof(long long) * (RY + 1));
     layz = take(sizeof(long long) * (RZ + 1));
@@ -78,6 +86,7 @@ struct HpSmem {
     cr = take(sizeof(int) * 2 * nb);
     ck = take(sizeof(int) * 2 * nb);
     cit = take(sizeof(int) * 2 * (nb + 1));
+    icell = take(sizeof(unsigned short) * 2 * (size_t)nb * NN);   // cell of each item of a batch
     misc = take(sizeof(int) * 96);   // fnode[NFF <= 37], range bounds, abort flag, warp sums
     total = o;
   }
@@ -115,10 +124,17 @@ __device__ __forceinline__ int hp_out_rows(int s, int k, int rlo, int rhi, int w
   return max(0, ohi - *olo + 1);
 }
 
+// Two consecutive 8-byte words of shared memory (16-byte aligned) in one load.
+__device__ __forceinline__ void ld_pair(const double* p, double& a, double& b) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a = v.x;
+  b = v.y;
+}
+
 template <int NP, class T>
 __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned char* smraw) {
   using S = HpShape<NP>;
-  constexpr int NF = S::NF, NN = S::NN, NFF = S::NFF, NN2 = S::NN2, NF2 = S::NF2, RS = S::RS;
+  constexpr int NF = S::NF, NN = S::NN, NFF = S::NFF, NN2 = S::NN2, NF2 = S::NF2, RS = S::RS, BS = S::BS;
   constexpr int NT = 512;
   const int G = p.hg, nb = p.hnb;
   const int pop = blockIdx.x / G, gi = blockIdx.x % G;
@@ -159,9 +175,11 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   g.zt = nullptr;
 
   const HpSmem L(NP, nb, RX, RY, RZ);
-  T* BinvT = reinterpret_cast<T*>(smraw + L.binv);
-  T* stage = reinterpret_cast<T*>(smraw + L.stage);   // 8-byte words (FP64 or a float pair)
-  T* rbuf = reinterpret_cast<T*>(smraw + L.rbuf);
+  T* Bq = reinterpret_cast<T*>(smraw + L.binv);        // Binv[q][m] at q * BS + m
+  T* stage = reinterpret_cast<T*>(smraw + L.stage);    // 8-byte words (FP64 or a float pair)
+  T* rbuf = reinterpret_cast<T*>(smraw + L.rbuf);      // r of cell c at c * NN2
+  long long* off0 = reinterpret_cast<long long*>(smraw + L.off0);        // node (0, 0, 0) of a cell
+  long long* nodeoff = reinterpret_cast<long long*>(smraw + L.nodeoff);  // node q from node 0
   long long* colx = reinterpret_cast<long long*>(smraw + L.colx);
   long long* rowy = reinterpret_cast<long long*>(smraw + L.rowy);
   long long* layz = reinterpret_cast<long long*>(smraw + L.layz);
@@ -170,6 +188,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   int* cr = reinterpret_cast<int*>(smraw + L.cr);
   int* ck = reinterpret_cast<int*>(smraw + L.ck);
   int* cit = reinterpret_cast<int*>(smraw + L.cit);
+  unsigned short* icell = reinterpret_cast<unsigned short*>(smraw + L.icell);
   int* misc = reinterpret_cast<int*>(smraw + L.misc);
   int* fnode = misc;            // [NFF]
   int* range = misc + 40;       // [2]: this block's cells [range[0], range[1]) of the step
@@ -177,15 +196,17 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   int* wsum = misc + 48;        // [16]: per-warp sums
   int* wsum2 = misc + 64;       // [16]
 
-  for (int i = tid; i < NN * NN; i += NT) {
-    const int row = i % NN, col = i / NN;   // BinvT[col][row] = Binv[row][col]
+  for (int i = tid; i < NN * BS; i += NT) {
+    const int q = i / BS, m = i % BS;
     if constexpr (__is_same(T, double)) {
-      BinvT[i] = p.binv[row * NN + col];
+      Bq[i] = m < NN ? p.binv[q * NN + m] : 0.0;
     } else {
-      const float* bf = p.binv_f + 2 * (row * NN + col);
-      BinvT[i] = T{bf[0], bf[1]};
+      Bq[i] = m < NN ? T{p.binv_f[2 * (q * NN + m)], p.binv_f[2 * (q * NN + m) + 1]} : T{0.0f, 0.0f};
     }
   }
+  for (int q = tid; q < NN; q += NT)
+    nodeoff[q] = (long long)(g.sz * (q / NF)) * g.sc + (long long)(g.sy * ((q / NP) % NP)) * g.sb +
+                 (long long)(g.sx * (q % NP)) * g.sa;
   if (tid == 0) {
     int f = 0;
     for (int q = 0; q < NN; ++q)
@@ -209,9 +230,12 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   g.layz = layz;
   __syncthreads();
 
-  const T rth = PDG_DC(T, C, rtheta), c1 = PDG_DC(T, C, c1);
+  // theta r_c = f_c + theta kx S_x Lt + ... is what the block forms: its product with
+  // Binv is the face value theta (Binv r_c) itself, and fn = (Binv (theta r) - (1 - theta) f)
+  // / theta
+  const T rth = PDG_DC(T, C, rtheta), omth = PDG_DC(T, C, omtheta);
   const T th = PDG_DC(T, C, theta);
-  const T kx = PDG_DC(T, C, kx), ky = PDG_DC(T, C, ky), kz = PDG_DC(T, C, kz);
+  const T tkx = th * PDG_DC(T, C, kx), tky = th * PDG_DC(T, C, ky), tkz = th * PDG_DC(T, C, kz);
   // face slots of this population: [parity][face a][layer][row][NF2]
   const long long slab = (long long)RZ * RY * NF2;
   double* hf = p.hface + (long long)pop * 6 * slab;
@@ -219,126 +243,53 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   const int lane = tid & 31, warp = tid >> 5;
   const int NS = RX + RY + RZ - 2;
 
-  // cells [c0, c0 + cnt) of the step (c0 relative to the hyperplane's enumeration): their
-  // coordinates, and the start of each cell's items (n^3 for an output cell, NFF else)
-  auto batch_info = [&](int s, int c0, int cnt, int buf) {
-    int items = 0;
-    if (tid < cnt) {
-      const int c = c0 + tid;
-      int lo = 0, hi = RZ - 1;   // the layer: last k with rcell[k] <= c
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (rcell[mid] <= c) lo = mid;
-        else hi = mid - 1;
-      }
-      int rlo, rhi;
-      hp_rows(s, lo, RX, RY, &rlo, &rhi);
-      const int r = rlo + (c - rcell[lo]);
-      cr[buf * nb + tid] = r;
-      ck[buf * nb + tid] = lo;
-      const int j = s - r - lo;
-      items = (j >= g.wx && r >= g.wy && lo >= g.wz) ? NN : NFF;
+  // (0) cells and items of hyperplane s per layer, exclusive prefixes over the layers
+  // (rcell, ritem), then (1) this block's cells: those whose first item lies in
+  // [I gi / G, I (gi + 1) / G) (range).  Barriers inside; rcell / ritem are overwritten.
+  auto plan_step = [&](int s) {
+    const int per_t = (RZ + NT - 1) / NT, k0 = tid * per_t;
+    int cs = 0, is = 0;
+    for (int k = k0; k < min(RZ, k0 + per_t); ++k) {
+      int rlo, rhi, olo;
+      const int n = hp_rows(s, k, RX, RY, &rlo, &rhi);
+      const int no = n ? hp_out_rows(s, k, rlo, rhi, g.wx, g.wy, g.wz, &olo) : 0;
+      cs += n;
+      is += n * NFF + no * (NN - NFF);
     }
-    // exclusive scan of items over the batch (cnt <= nb <= 512)
-    int v = items;
+    int vc = cs, vi = is;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, v, d);
-      if (lane >= d) v += u;
+      const int uc = __shfl_up_sync(0xffffffffu, vc, d), ui = __shfl_up_sync(0xffffffffu, vi, d);
+      if (lane >= d) {
+        vc += uc;
+        vi += ui;
+      }
     }
-    if (lane == 31) wsum[warp] = v;
+    if (lane == 31) {
+      wsum[warp] = vc;
+      wsum2[warp] = vi;
+    }
     __syncthreads();
-    int base = 0;
-    for (int w = 0; w < warp; ++w) base += wsum[w];
-    if (tid < cnt) cit[buf * (nb + 1) + tid] = base + v - items;
-    if (tid == cnt - 1) cit[buf * (nb + 1) + cnt] = base + v;
-  };
-
-  // copy the state and the inflow faces of the batch's cells into stage[buf]
-  auto stage_batch = [&](int s, int cnt, int buf) {
-    double* sb = reinterpret_cast<double*>(stage + (size_t)buf * nb * RS);
-    const int par = s & 1;
-    constexpr int per = NN + 3 * NF2;
-    for (int i = tid; i < cnt * per; i += NT) {
-      const int c = i / per, e = i % per;
-      const int r = cr[buf * nb + c], k = ck[buf * nb + c], j = s - r - k;
-      double* row = sb + (size_t)c * RS;
-      if (e < NN) {
-        cp_async8(row + e, g.fin + corner_off(g, j, r, k, e / NF, (e / NP) % NP, e % NP));
-        continue;
-      }
-      const int a = (e - NN) / NF2, u = (e - NN) % NF2;
-      double* dst = row + NN2 + a * NF2 + u;
-      const bool edge = a == 0 ? j == 0 : (a == 1 ? r == 0 : k == 0);
-      if (!edge) {
-        if ((u & 1) == 0) cp_async16_cg(dst, hf + ((long long)(par * 3 + a) * RZ + k) * RY * NF2 + (long long)r * NF2 + u);
-        continue;
-      }
-      if (u >= NF) continue;
-      const int u1 = u / NP, u2 = u % NP;
-      const double* src;
-      if (a == 0) {   // +x face of the cell upwind of column 0: node (iz, iy) = (u1, u2)
-        src = g.bx ? g.fbx + corner_py<NP>(g, r, u2) * g.fls[0][1] + corner_pz<NP>(g, k, u1) * g.fls[0][2]
-                   : g.fin + corner_off(g, -1, r, k, u1, u2, NP - 1);
-      } else if (a == 1) {   // +y face below row 0: node (iz, ix) = (u1, u2)
-        src = g.by ? g.fby + corner_px<NP>(g, j, u2) * g.fls[1][0] + corner_pz<NP>(g, k, u1) * g.fls[1][2]
-                   : g.fin + corner_off(g, j, -1, k, u1, NP - 1, u2);
-      } else {   // +z face under layer 0: node (iy, ix) = (u1, u2)
-        src = g.bz ? g.fbz + corner_px<NP>(g, j, u2) * g.fls[2][0] + corner_py<NP>(g, r, u1) * g.fls[2][1]
-                   : g.fin + corner_off(g, j, r, -1, NP - 1, u1, u2);
-      }
-      cp_async8(dst, src);
+    int bc = 0, bi = 0;
+    for (int w = 0; w < warp; ++w) {
+      bc += wsum[w];
+      bi += wsum2[w];
     }
-  };
-
-  for (int s = 0; s < NS; ++s) {
-    // (0) cells and items of hyperplane s per layer, exclusive prefix over the layers
-    {
-      const int per_t = (RZ + NT - 1) / NT, k0 = tid * per_t;
-      int cs = 0, is = 0;
-      for (int k = k0; k < min(RZ, k0 + per_t); ++k) {
-        int rlo, rhi, olo;
-        const int n = hp_rows(s, k, RX, RY, &rlo, &rhi);
-        const int no = n ? hp_out_rows(s, k, rlo, rhi, g.wx, g.wy, g.wz, &olo) : 0;
-        cs += n;
-        is += n * NFF + no * (NN - NFF);
-      }
-      int vc = cs, vi = is;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int uc = __shfl_up_sync(0xffffffffu, vc, d), ui = __shfl_up_sync(0xffffffffu, vi, d);
-        if (lane >= d) {
-          vc += uc;
-          vi += ui;
-        }
-      }
-      if (lane == 31) {
-        wsum[warp] = vc;
-        wsum2[warp] = vi;
-      }
-      __syncthreads();
-      int bc = 0, bi = 0;
-      for (int w = 0; w < warp; ++w) {
-        bc += wsum[w];
-        bi += wsum2[w];
-      }
-      int pc = bc + vc - cs, pi = bi + vi - is;   // exclusive prefixes at k0
-      for (int k = k0; k < min(RZ, k0 + per_t); ++k) {
-        rcell[k] = pc;
-        ritem[k] = pi;
-        int rlo, rhi, olo;
-        const int n = hp_rows(s, k, RX, RY, &rlo, &rhi);
-        const int no = n ? hp_out_rows(s, k, rlo, rhi, g.wx, g.wy, g.wz, &olo) : 0;
-        pc += n;
-        pi += n * NFF + no * (NN - NFF);
-      }
-      if (tid == NT - 1) {
-        rcell[RZ] = pc;
-        ritem[RZ] = pi;
-      }
-      __syncthreads();
+    int pc = bc + vc - cs, pi = bi + vi - is;   // exclusive prefixes at k0
+    for (int k = k0; k < min(RZ, k0 + per_t); ++k) {
+      rcell[k] = pc;
+      ritem[k] = pi;
+      int rlo, rhi, olo;
+      const int n = hp_rows(s, k, RX, RY, &rlo, &rhi);
+      const int no = n ? hp_out_rows(s, k, rlo, rhi, g.wx, g.wy, g.wz, &olo) : 0;
+      pc += n;
+      pi += n * NFF + no * (NN - NFF);
     }
-    // (1) this block's cells: those whose first item lies in [I gi / G, I (gi + 1) / G)
+    if (tid == NT - 1) {
+      rcell[RZ] = pc;
+      ritem[RZ] = pi;
+    }
+    __syncthreads();
     if (tid < 2) {
       const long long I = ritem[RZ];
       const int P = (int)(I * (gi + tid) / G);
@@ -353,8 +304,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
         int rlo, rhi, olo;
         hp_rows(s, lo, RX, RY, &rlo, &rhi);
         const int no = hp_out_rows(s, lo, rlo, rhi, g.wx, g.wy, g.wz, &olo);
-        // first row r of the layer whose first item is >= P
-        int a = rlo, b = rhi + 1;
+        int a = rlo, b = rhi + 1;   // first row of the layer whose first item is >= P
         while (a < b) {
           const int m = (a + b) >> 1;
           const int before_out = no ? max(0, min(m, olo + no) - olo) : 0;
@@ -367,64 +317,160 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
       range[tid] = c;
     }
     __syncthreads();
-    const int cb = range[0], ce = range[1];
-    const int nbat = (ce - cb + nb - 1) / nb;
-    if (nbat > 0) {
-      batch_info(s, cb, min(nb, ce - cb), 0);
-      __syncthreads();
-      stage_batch(s, min(nb, ce - cb), 0);
+  };
+
+  // cells [c0, c0 + cnt) of hyperplane s into table buffer buf: coordinates, offset of
+  // node 0, the start of each cell's items (n^3 for an output cell, NFF else) and the
+  // cell of every item.  One barrier inside; the tables are complete after the caller's
+  // next barrier.
+  auto batch_info = [&](int s, int c0, int cnt, int buf) {
+    int items = 0;
+    if (tid < cnt) {
+      const int c = c0 + tid;
+      int lo = 0, hi = RZ - 1;   // the layer: last k with rcell[k] <= c
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rcell[mid] <= c) lo = mid;
+        else hi = mid - 1;
+      }
+      int rlo, rhi;
+      hp_rows(s, lo, RX, RY, &rlo, &rhi);
+      const int r = rlo + (c - rcell[lo]);
+      const int j = s - r - lo;
+      cr[buf * nb + tid] = r;
+      ck[buf * nb + tid] = lo;
+      off0[buf * nb + tid] = layz[lo + 1] + rowy[r + 1] + colx[j + 1];
+      items = (j >= g.wx && r >= g.wy && lo >= g.wz) ? NN : NFF;
     }
-    for (int bI = 0; bI < nbat; ++bI) {
-      const int buf = bI & 1;
+    int v = items;   // exclusive scan of items over the batch (cnt <= nb <= 512)
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += u;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < warp; ++w) base += wsum[w];
+    if (tid < cnt) {
+      cit[buf * (nb + 1) + tid] = base + v - items;
+      unsigned short* ic = icell + (size_t)buf * nb * NN + (base + v - items);
+      for (int i = 0; i < items; ++i) ic[i] = (unsigned short)tid;
+    }
+    if (tid == cnt - 1) cit[buf * (nb + 1) + cnt] = base + v;
+  };
+
+  // copy the state (what & 1) and the inflow faces (what & 2) of the batch's cells into
+  // stage[buf]; the faces of hyperplane s must be complete (after the blocks met)
+  auto stage_batch = [&](int s, int cnt, int buf, int what) {
+    double* sb = reinterpret_cast<double*>(stage + (size_t)buf * nb * RS);
+    const int par = s & 1;
+    if (what & 1)
+      for (int i = tid; i < cnt * NN; i += NT) {
+        const int c = i / NN, e = i % NN;
+        cp_async8(sb + (size_t)c * RS + e, g.fin + off0[buf * nb + c] + nodeoff[e]);
+      }
+    if (what & 2) {
+      constexpr int per = 3 * NF2;
+      for (int i = tid; i < cnt * per; i += NT) {
+        const int c = i / per, e = i % per;
+        const int a = e / NF2, u = e % NF2;
+        const int r = cr[buf * nb + c], k = ck[buf * nb + c], j = s - r - k;
+        double* dst = sb + (size_t)c * RS + NN2 + e;
+        const bool edge = a == 0 ? j == 0 : (a == 1 ? r == 0 : k == 0);
+        if (!edge) {
+          if ((u & 1) == 0)
+            cp_async16_cg(dst, hf + ((long long)(par * 3 + a) * RZ + k) * RY * NF2 + (long long)r * NF2 + u);
+          continue;
+        }
+        if (u >= NF) continue;
+        const int u1 = u / NP, u2 = u % NP;
+        const double* src;
+        if (a == 0) {   // +x face of the cell upwind of column 0: node (iz, iy) = (u1, u2)
+          src = g.bx ? g.fbx + corner_py<NP>(g, r, u2) * g.fls[0][1] + corner_pz<NP>(g, k, u1) * g.fls[0][2]
+                     : g.fin + corner_off(g, -1, r, k, u1, u2, NP - 1);
+        } else if (a == 1) {   // +y face below row 0: node (iz, ix) = (u1, u2)
+          src = g.by ? g.fby + corner_px<NP>(g, j, u2) * g.fls[1][0] + corner_pz<NP>(g, k, u1) * g.fls[1][2]
+                     : g.fin + corner_off(g, j, -1, k, u1, NP - 1, u2);
+        } else {   // +z face under layer 0: node (iy, ix) = (u1, u2)
+          src = g.bz ? g.fbz + corner_px<NP>(g, j, u2) * g.fls[2][0] + corner_py<NP>(g, r, u1) * g.fls[2][1]
+                     : g.fin + corner_off(g, j, r, -1, NP - 1, u1, u2);
+        }
+        cp_async8(dst, src);
+      }
+    }
+  };
+
+  // Pipeline.  Table and stage buffers alternate with a running batch count (nbt) across
+  // hyperplanes.  Before the blocks meet after hyperplane s, the block has planned
+  // hyperplane s + 1, filled the tables of its first batch and started copying that
+  // batch's state; after the meeting it copies the batch's faces.
+  int nbt = 0;
+  plan_step(0);
+  int cb = range[0], ce = range[1];
+  if (ce > cb) {
+    batch_info(0, cb, min(nb, ce - cb), 0);
+    __syncthreads();
+    stage_batch(0, min(nb, ce - cb), 0, 1);
+  }
+  for (int s = 0; s < NS; ++s) {
+    const int nbat = (ce - cb + nb - 1) / nb;
+    if (nbat > 0) stage_batch(s, min(nb, ce - cb), nbt & 1, 2);
+    for (int bI = 0; bI < nbat; ++bI, ++nbt) {
+      const int buf = nbt & 1;
       const int c0 = cb + bI * nb, cnt = min(nb, ce - c0);
       cp_async_wait_all();
       __syncthreads();
-      // (A) r_c of every node of the batch
+      // (A) theta r_c of every node of the batch
       const T* sb = stage + (size_t)buf * nb * RS;
       for (int i = tid; i < cnt * NN; i += NT) {
         const int c = i / NN, q = i % NN;
         const int iz = q / NF, iy = (q / NP) % NP, ix = q % NP;
         const T* row = sb + (size_t)c * RS;
-        T rv = row[q] * rth;
-        if (ix == 0) rv = fma(kx, row[NN2 + iz * NP + iy], rv);
-        if (iy == 0) rv = fma(ky, row[NN2 + NF2 + iz * NP + ix], rv);
-        if (iz == 0) rv = fma(kz, row[NN2 + 2 * NF2 + iy * NP + ix], rv);
-        rbuf[(size_t)c * NN + q] = rv;
+        T rv = row[q];
+        if (ix == 0) rv = fma(tkx, row[NN2 + iz * NP + iy], rv);
+        if (iy == 0) rv = fma(tky, row[NN2 + NF2 + iz * NP + ix], rv);
+        if (iz == 0) rv = fma(tkz, row[NN2 + 2 * NF2 + iy * NP + ix], rv);
+        rbuf[(size_t)c * NN2 + q] = rv;
       }
       const bool more = bI + 1 < nbat;
       if (more) batch_info(s, c0 + nb, min(nb, ce - c0 - nb), buf ^ 1);   // has its own barrier
       __syncthreads();
-      if (more) stage_batch(s, min(nb, ce - c0 - nb), buf ^ 1);
-      // (B) items of the batch: every node of an output cell, the face nodes of a start cell
+      // (B) items of the batch: every node of an output cell, the face nodes of a start cell;
+      // each thread issues its share of the next batch's copies after its first item
       const int* itb = cit + buf * (nb + 1);
+      const unsigned short* icb = icell + (size_t)buf * nb * NN;
       const int nitems = itb[cnt];
       const int par1 = (s + 1) & 1;
+      bool staged = !more;
       for (int it = tid; it < nitems; it += NT) {
-        int lo = 0, hi = cnt - 1;   // the cell: last c with itb[c] <= it
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (itb[mid] <= it) lo = mid;
-          else hi = mid - 1;
-        }
-        const int c = lo, loc = it - itb[c];
+        const int c = icb[it], loc = it - itb[c];
         const bool out = itb[c + 1] - itb[c] == NN;
         const int q = out ? loc : fnode[loc];
-        const T* rc = rbuf + (size_t)c * NN;
+        const T* rc = rbuf + (size_t)c * NN2;
+        const T* br = Bq + (size_t)q * BS;
         T acc;
         if constexpr (__is_same(T, double)) {
-          double a0 = 0.0, a1 = 0.0;
+          // one chain (one warp per SM sub-partition keeps its FP64 unit busy with a
+          // dependent chain), 16-byte pair loads of Binv[q][m..m+1] and r[m..m+1]
+          double a = 0.0;
 #pragma unroll
           for (int m = 0; m + 1 < NN; m += 2) {
-            a0 = fma(BinvT[m * NN + q], rc[m], a0);
-            a1 = fma(BinvT[(m + 1) * NN + q], rc[m + 1], a1);
+            double b0, b1, x0, x1;
+            ld_pair(br + m, b0, b1);
+            ld_pair(rc + m, x0, x1);
+            a = fma(b0, x0, a);
+            a = fma(b1, x1, a);
           }
-          if (NN % 2) a0 = fma(BinvT[(NN - 1) * NN + q], rc[NN - 1], a0);
-          acc = a0 + a1;
+          if constexpr (NN % 2) a = fma(br[NN - 1], rc[NN - 1], a);
+          acc = a;
         } else {
+          // compensated dot product (see dot_acc): exact high products and sums, the
+          // rounding errors and cross terms gathered in one FP32 accumulator
           float Sh = 0.0f, Ll = 0.0f;
 #pragma unroll 8
           for (int m = 0; m < NN; ++m) {
-            const T a = BinvT[m * NN + q], bv = rc[m];
+            const T a = br[m], bv = rc[m];
             const dd pr = dd_two_prod(a.hi, bv.hi);
             const float cross = __fmaf_rn(a.hi, bv.lo, __fmul_rn(a.lo, bv.hi));
             const dd sm2 = dd_two_sum(Sh, pr.hi);
@@ -433,22 +479,36 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
           }
           acc = dd_fast_two_sum(Sh, Ll);
         }
-        const int r = cr[buf * nb + c], k = ck[buf * nb + c], j = s - r - k;
         const int qz = q / NF, qy = (q / NP) % NP, qx = q % NP;
-        if (out) st(g.fout + corner_off(g, j, r, k, qz, qy, qx), acc - c1 * sb[(size_t)c * RS + q]);
+        if (out) st(g.fout + off0[buf * nb + c] + nodeoff[q], (acc - omth * sb[(size_t)c * RS + q]) * rth);
         if (qx == NP - 1 || qy == NP - 1 || qz == NP - 1) {
-          const T face = th * acc;
-          if (qx == NP - 1 && j + 1 < RX)
-            st(hf + ((long long)(par1 * 3 + 0) * RZ + k) * RY * NF2 + (long long)r * NF2 + qz * NP + qy, face);
-          if (qy == NP - 1 && r + 1 < RY)
-            st(hf + ((long long)(par1 * 3 + 1) * RZ + k) * RY * NF2 + (long long)(r + 1) * NF2 + qz * NP + qx, face);
-          if (qz == NP - 1 && k + 1 < RZ)
-            st(hf + ((long long)(par1 * 3 + 2) * RZ + k + 1) * RY * NF2 + (long long)r * NF2 + qy * NP + qx, face);
+          const int r = cr[buf * nb + c], k = ck[buf * nb + c], j = s - r - k;
+          const T face = acc;
+          double* fx = hf + (long long)par1 * 3 * slab + ((long long)k * RY + r) * NF2;
+          if (qx == NP - 1 && j + 1 < RX) st(fx + qz * NP + qy, face);
+          if (qy == NP - 1 && r + 1 < RY) st(fx + slab + NF2 + qz * NP + qx, face);
+          if (qz == NP - 1 && k + 1 < RZ) st(fx + 2 * slab + (long long)RY * NF2 + qy * NP + qx, face);
+        }
+        if (!staged) {
+          stage_batch(s, min(nb, ce - c0 - nb), buf ^ 1, 3);
+          staged = true;
         }
       }
+      if (!staged) stage_batch(s, min(nb, ce - c0 - nb), buf ^ 1, 3);
     }
-    // (2) the population's blocks meet: every face of step s is written before any block
-    // reads it at step s + 1 (none is in flight: the copies were waited for above)
+    // (2) plan hyperplane s + 1 and start copying the state of its first batch; then the
+    // population's blocks meet: every face of step s is written before any block reads it
+    // at step s + 1
+    if (s + 1 < NS) {
+      plan_step(s + 1);   // its barriers also end this step's work on the tables
+      cb = range[0];
+      ce = range[1];
+      if (ce > cb) {
+        batch_info(s + 1, cb, min(nb, ce - cb), nbt & 1);
+        __syncthreads();
+        stage_batch(s + 1, min(nb, ce - cb), nbt & 1, 1);
+      }
+    }
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -470,7 +530,10 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
       if (!ok) *abort_flag = 1;
     }
     __syncthreads();
-    if (*abort_flag) return;
+    if (*abort_flag) {
+      cp_async_wait_all();   // the next state's copies in flight
+      return;
+    }
   }
 }
 
