@@ -21,9 +21,10 @@
 // builds r_c for every cell of it in shared memory, (B) the block forms the output
 // nodes as dot products with r_c (Binv sits in shared memory transposed, so the threads
 // of a cell read consecutive words).  The cells of the upwind start only pass faces on,
-// so (B) computes just their 2n-1 face nodes.  The face value passed on is
-// theta fn + (1 - theta) f = theta (Binv r_c): one product per face node.  The state of the next anti-diagonal is
-// copied into shared memory with cp.async while (B) runs (double-buffered by parity).
+// so (B) computes just their 2n-1 face nodes.  The block forms theta r_c, whose product
+// with Binv is the face value passed on, theta fn + (1 - theta) f = theta (Binv r_c).  The
+// state of the next anti-diagonal is copied into shared memory with cp.async while (B)
+// runs (double-buffered by parity).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -186,9 +187,12 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
   T creg[NN];
 #pragma unroll
   for (int i = 0; i < NN; ++i) creg[i] = BinvT[i * NN + qq];
-  const T rth = PDG_DC(T, C, rtheta), c1 = PDG_DC(T, C, c1);
+  // the block forms theta r_c = f_c + theta kx S_x Lt + theta ky S_y Bt: its product with
+  // Binv is the face value theta (Binv r_c) itself, and fn = (Binv (theta r) - (1 - theta) f)
+  // / theta
+  const T rth = PDG_DC(T, C, rtheta), omth = PDG_DC(T, C, omtheta);
   const T th = PDG_DC(T, C, theta);
-  const T kx = PDG_DC(T, C, kx), ky = PDG_DC(T, C, ky);
+  const T tkx = th * PDG_DC(T, C, kx), tky = th * PDG_DC(T, C, ky);
 
   diag_stage<NP, T>(g, 0, fbuf, lbnd, bbnd);
   cp_async_wait_all();
@@ -198,13 +202,13 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
     const int jlo = max(0, t - g.nrow + 1), jhi = min(g.ncol - 1, t);
     const int A = jhi - jlo + 1;
     const T* fc = fbuf + (size_t)par * amax * RS;
-    // (A) r_c of every cell of the anti-diagonal
+    // (A) theta r_c of every cell of the anti-diagonal
     for (int i = threadIdx.x; i < A * NN; i += blockDim.x) {
       const int c = i / NN, q = i % NN;
       const int j = jlo + c, iy = q / NP, ix = q % NP;
-      T rv = fc[c * RS + q] * rth;
-      if (ix == 0) rv = fma(kx, j == 0 ? lbnd[par * NP + iy] : Lt[((size_t)prv * LtS + j) * NP + iy], rv);
-      if (iy == 0) rv = fma(ky, j == t ? bbnd[par * NP + ix] : Bt[((size_t)prv * BtS + j) * NP + ix], rv);
+      T rv = fc[c * RS + q];
+      if (ix == 0) rv = fma(tkx, j == 0 ? lbnd[par * NP + iy] : Lt[((size_t)prv * LtS + j) * NP + iy], rv);
+      if (iy == 0) rv = fma(tky, j == t ? bbnd[par * NP + ix] : Bt[((size_t)prv * BtS + j) * NP + ix], rv);
       rbuf[c * RS + q] = rv;
     }
     __syncthreads();
@@ -217,10 +221,10 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
     const int h2 = max(h1 - 1, min(jhi, t - g.wy));
     auto finish = [&](int j, int q, T acc) {
       const int c = j - jlo, r = t - j, iy = q / NP, ix = q % NP;
-      if (j >= g.wx && r >= g.wy) st(g.fout + diag_off<NP>(g, j, r, iy, ix), acc - c1 * fc[c * RS + q]);
+      if (j >= g.wx && r >= g.wy) st(g.fout + diag_off<NP>(g, j, r, iy, ix), (acc - omth * fc[c * RS + q]) * rth);
       if (ix == NP - 1 || iy == NP - 1) {
-        // theta fn + (1 - theta) f = theta (Binv r) - (1 - theta) f + (1 - theta) f
-        const T face = th * acc;
+        // theta fn + (1 - theta) f = theta (Binv r) = Binv (theta r)
+        const T face = acc;
         if (ix == NP - 1) Lt[((size_t)par * LtS + j + 1) * NP + iy] = face;
         if (iy == NP - 1) Bt[((size_t)par * BtS + j) * NP + ix] = face;
       }
@@ -230,15 +234,12 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
         const T* rc = rbuf + (j - jlo) * RS;
         T acc;
         if constexpr (__is_same(T, double)) {
-          // two chains: the FP64 pipe (2 DFMA per SM and clock) hides their latency
-          double a0 = 0.0, a1 = 0.0;
+          // one chain: a dependent DFMA chain per warp keeps its SM sub-partition's FP64
+          // unit busy, so more chains would only add the adds that join them
+          double a = 0.0;
 #pragma unroll
-          for (int k = 0; k + 1 < NN; k += 2) {
-            a0 = fma(creg[k], rc[k], a0);
-            a1 = fma(creg[k + 1], rc[k + 1], a1);
-          }
-          if (NN % 2) a0 = fma(creg[NN - 1], rc[NN - 1], a0);
-          acc = a0 + a1;
+          for (int k = 0; k < NN; ++k) a = fma(creg[k], rc[k], a);
+          acc = a;
         } else {
           T bb[NN];
 #pragma unroll
@@ -255,14 +256,10 @@ __device__ __forceinline__ void diag_body(const PdgDiagPass& p, double* sm) {
       const T* rc = rbuf + (j - jlo) * RS;
       T acc;
       if constexpr (__is_same(T, double)) {
-        double a0 = 0.0, a1 = 0.0;
+        double a = 0.0;
 #pragma unroll
-        for (int k = 0; k + 1 < NN; k += 2) {
-          a0 = fma(BinvT[k * NN + q], rc[k], a0);
-          a1 = fma(BinvT[(k + 1) * NN + q], rc[k + 1], a1);
-        }
-        if (NN % 2) a0 = fma(BinvT[(NN - 1) * NN + q], rc[NN - 1], a0);
-        acc = a0 + a1;
+        for (int k = 0; k < NN; ++k) a = fma(BinvT[k * NN + q], rc[k], a);
+        acc = a;
       } else {
         T a[NN], bb[NN];
 #pragma unroll
