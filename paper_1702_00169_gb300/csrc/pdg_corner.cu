@@ -5,8 +5,8 @@
 int pdg_launch_corner_df(const PdgCornerPass& p, size_t smem, void* stream);
 
 size_t pdg_corner_smem(const PdgCornerPass& p) {
-  if (p.tc) return pdg_corner_tc_smem(p);
   if (p.hyper) return pdg_corner_hp_smem(p);
+  if (p.tc) return pdg_corner_tc_smem(p);
   const size_t n = (size_t)p.n, NF = n * n, NN = NF * n, RS = (NN + NF + 1) & ~(size_t)1;
   const size_t CM = (size_t)p.tx + p.c.wx, RM = (size_t)p.ty + p.c.wy, LM = (size_t)p.tz + p.c.wz;
   const size_t amax = CM < RM ? CM : RM;
@@ -23,8 +23,8 @@ size_t pdg_corner_scratch(const PdgCornerPass& p) {
 
 int pdg_launch_corner(const PdgCornerPass& p, void* stream) {
   const size_t smem = pdg_corner_smem(p);
-  if (p.tc) return pdg_launch_corner_tc(p, smem, stream);
   if (p.hyper) return pdg_launch_corner_hp(p, smem, stream);
+  if (p.tc) return pdg_launch_corner_tc(p, smem, stream);
   if (p.prec == PDG_PREC_DF32) return pdg_launch_corner_df(p, smem, stream);
   return pdgdev::launch_corner_typed<double>(p, smem, (cudaStream_t)stream);
 }

@@ -46,6 +46,7 @@
 #include <cuda_runtime.h>
 
 #include "pdg_corner.cuh"
+#include "pdg_corner_tc.cuh"
 
 #define PDG_HP_ERR_TIMEOUT 2
 
@@ -61,11 +62,17 @@ struct HpShape {
   static constexpr int BS = NN2 + ((NN2 / 2) % 2 == 0 ? 2 : 0);   // Binv row stride: odd in 16-byte units
 };
 
+// tc != 0: the tensor-core form (nb = 128 cells, one product row each) adds, first and
+// 128-byte aligned, the two TF32 splits of the A operand (128 x K) and of Binv (N x K),
+// x~ of the batch, the residual stencil and the mbarriers; it keeps no Binv of its own and
+// no item table.
 struct HpSmem {
+  size_t aop, bop, xt, kt, ktf, mbar;
   size_t binv, stage, rbuf, off0, nodeoff, colx, rowy, layz, rcell, ritem, cr, ck, cit, icell, misc, total;
-  __host__ __device__ HpSmem(int n, int nb, int RX, int RY, int RZ) {
+  __host__ __device__ HpSmem(int n, int nb, int RX, int RY, int RZ, int tc = 0) {
     const int NF = n * n, NN = NF * n, NN2 = (NN + 1) & ~1, NF2 = (NF + 1) & ~1, RS = NN2 + 3 * NF2;
     const int BS = NN2 + ((NN2 / 2) % 2 == 0 ? 2 : 0);
+    const int KP = (NN + 7) & ~7, NPAD = KP < 16 ? 16 : KP;
     size_t o = 0;
     auto take = [&](size_t bytes) {
       o = (o + 15) / 16 * 16;
@@ -73,7 +80,16 @@ struct HpSmem {
       o += bytes;
       return at;
     };
-    binv = take(sizeof(double) * NN * BS);
+    aop = bop = xt = kt = ktf = mbar = 0;
+    if (tc) {
+      aop = take(sizeof(float) * 2 * 128 * KP);
+      bop = take(sizeof(float) * 2 * NPAD * KP);
+      xt = take(sizeof(float) * 128 * NN);
+      kt = take(sizeof(double) * 3 * n * n);
+      ktf = take(sizeof(float) * 2 * 3 * n * n);
+      mbar = take(32);   // mbarrier (8 bytes), an idle mbarrier (8), TMEM base (4)
+    }
+    binv = take(tc ? 0 : sizeof(double) * NN * BS);
     stage = take(sizeof(double) * 2 * (size_t)nb * RS);
     rbuf = take(sizeof(double) * (size_t)nb * NN2);
     off0 = take(sizeof(long long) * 2 * nb);
@@ -86,7 +102,7 @@ struct HpSmem {
     cr = take(sizeof(int) * 2 * nb);
     ck = take(sizeof(int) * 2 * nb);
     cit = take(sizeof(int) * 2 * (nb + 1));
-    icell = take(sizeof(unsigned short) * 2 * (size_t)nb * NN);   // cell of each item of a batch
+    icell = take(tc ? 0 : sizeof(unsigned short) * 2 * (size_t)nb * NN);   // cell of each item of a batch
     misc = take(sizeof(int) * 96);   // fnode[NFF <= 37], range bounds, abort flag, warp sums
     total = o;
   }
@@ -131,7 +147,13 @@ __device__ __forceinline__ void ld_pair(const double* p, double& a, double& b) {
   b = v.y;
 }
 
-template <int NP, class T>
+// TC = 0: FP64 or double-float dot products with Binv (T = double or dd).  TC = 1 / 2: the
+// tensor-core form (T = double, FP64 state): per batch of at most 128 cells, the products
+// X~ = (theta R) Binv^T as three TF32 split products on tcgen05 (rows = cells), the residual
+// theta r - B x~ through the Kronecker sum (TC = 1: FP64; 2: double-float), a second split
+// product for the correction d, and x = x~ + d, the face values (pdg_corner_tc.cuh has the
+// same arithmetic on box anti-diagonals).
+template <int NP, class T, int TC>
 __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned char* smraw) {
   using S = HpShape<NP>;
   constexpr int NF = S::NF, NN = S::NN, NFF = S::NFF, NN2 = S::NN2, NF2 = S::NF2, RS = S::RS, BS = S::BS;
@@ -139,7 +161,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   const int G = p.hg, nb = p.hnb;
   const int pop = blockIdx.x / G, gi = blockIdx.x % G;
   const PdgCornerCoef& C = p.c;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   CornerGeom g;
   g.fin = p.fin[pop];
@@ -174,7 +196,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   g.nlay = RZ;
   g.zt = nullptr;
 
-  const HpSmem L(NP, nb, RX, RY, RZ);
+  const HpSmem L(NP, nb, RX, RY, RZ, TC);
   T* Bq = reinterpret_cast<T*>(smraw + L.binv);        // Binv[q][m] at q * BS + m
   T* stage = reinterpret_cast<T*>(smraw + L.stage);    // 8-byte words (FP64 or a float pair)
   T* rbuf = reinterpret_cast<T*>(smraw + L.rbuf);      // r of cell c at c * NN2
@@ -196,7 +218,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   int* wsum = misc + 48;        // [16]: per-warp sums
   int* wsum2 = misc + 64;       // [16]
 
-  for (int i = tid; i < NN * BS; i += NT) {
+  for (int i = tid; i < (TC ? 0 : NN * BS); i += NT) {
     const int q = i / BS, m = i % BS;
     if constexpr (__is_same(T, double)) {
       Bq[i] = m < NN ? p.binv[q * NN + m] : 0.0;
@@ -228,7 +250,39 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   g.colx = colx;
   g.rowy = rowy;
   g.layz = layz;
+  // tensor-core form: TMEM columns for the accumulator, the mbarriers, both A splits zero
+  // (rows beyond a batch and columns k >= NN stay finite), both Binv splits from the host's
+  // layout, the stencil of B
+  using TS = TcShape<NP>;
+  float* aop = reinterpret_cast<float*>(smraw + L.aop);
+  float* bop = reinterpret_cast<float*>(smraw + L.bop);
+  float* xt = reinterpret_cast<float*>(smraw + L.xt);
+  double* kt = reinterpret_cast<double*>(smraw + L.kt);
+  float* ktf = reinterpret_cast<float*>(smraw + L.ktf);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smraw + L.mbar);
+  uint64_t* idle = mbar + 1;   // no thread or product ever arrives on it (the stall test waits here)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smraw + L.mbar + 16);
+  if constexpr (TC != 0) {
+    if (warp == 0) tc::tmem_alloc(tslot, TS::NCOL);
+    if (tid == 0) {
+      tc::mbar_init(mbar, 1);
+      tc::mbar_init(idle, 1);
+    }
+    for (int i = tid; i < 2 * TS::AOPS; i += NT) aop[i] = 0.0f;
+    for (int i = tid; i < 2 * TS::BOPS; i += NT) bop[i] = p.binv_tc[i];
+    for (int i = tid; i < 3 * NP * NP; i += NT) {
+      kt[i] = p.c.kt[i / (NP * NP)][i % (NP * NP)];
+      ktf[2 * i] = p.c.kt_f[i / (NP * NP)][i % (NP * NP)][0];
+      ktf[2 * i + 1] = p.c.kt_f[i / (NP * NP)][i % (NP * NP)][1];
+    }
+    tc::fence_before_sync();
+  }
   __syncthreads();
+  uint32_t tmem = 0;
+  if constexpr (TC != 0) {
+    tc::fence_after_sync();
+    tmem = *tslot;
+  }
 
   // theta r_c = f_c + theta kx S_x Lt + ... is what the block forms: its product with
   // Binv is the face value theta (Binv r_c) itself, and fn = (Binv (theta r) - (1 - theta) f)
@@ -240,7 +294,6 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   const long long slab = (long long)RZ * RY * NF2;
   double* hf = p.hface + (long long)pop * 6 * slab;
   unsigned* bar = p.hbar + pop;
-  const int lane = tid & 31, warp = tid >> 5;
   const int NS = RX + RY + RZ - 2;
 
   // (0) cells and items of hyperplane s per layer, exclusive prefixes over the layers
@@ -354,8 +407,10 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
     for (int w = 0; w < warp; ++w) base += wsum[w];
     if (tid < cnt) {
       cit[buf * (nb + 1) + tid] = base + v - items;
-      unsigned short* ic = icell + (size_t)buf * nb * NN + (base + v - items);
-      for (int i = 0; i < items; ++i) ic[i] = (unsigned short)tid;
+      if constexpr (TC == 0) {   // the tensor-core form maps one thread row to one cell
+        unsigned short* ic = icell + (size_t)buf * nb * NN + (base + v - items);
+        for (int i = 0; i < items; ++i) ic[i] = (unsigned short)tid;
+      }
     }
     if (tid == cnt - 1) cit[buf * (nb + 1) + cnt] = base + v;
   };
@@ -405,6 +460,39 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   // hyperplanes.  Before the blocks meet after hyperplane s, the block has planned
   // hyperplane s + 1, filled the tables of its first batch and started copying that
   // batch's state; after the meeting it copies the batch's faces.
+  // tensor-core form: one thread issues the three split products of a solve (then commits
+  // them to the mbarrier) and later waits for them, boundedly
+  constexpr uint32_t IDESC = tc::idesc_tf32(128, TS::NPAD);
+  uint32_t phase = 0;
+  auto mma_issue = [&]() {   // tid 0 only
+    tc::fence_after_sync();
+#pragma unroll 1
+    for (int sp = 0; sp < 3; ++sp) {
+      const int sa = sp == 1 ? 1 : 0, sbb = sp == 2 ? 1 : 0;   // (hi, hi), (lo, hi), (hi, lo)
+#pragma unroll 1
+      for (int ks = 0; ks < TS::KP / 8; ++ks) {
+        const uint64_t ad = tc::smem_desc(tc::smem_u32(aop + sa * TS::AOPS) + ks * 2 * 16 * 128, 16 * 128, 128);
+        const uint64_t bd = tc::smem_desc(tc::smem_u32(bop + sbb * TS::BOPS) + ks * 2 * (TS::NPAD / 8) * 128,
+                                          (TS::NPAD / 8) * 128, 128);
+        tc::mma_tf32(tmem, ad, bd, IDESC, (sp | ks) ? 1u : 0u);
+      }
+    }
+    tc::commit(mbar);
+  };
+  auto mma_wait = [&]() {    // tid 0 only; records a timeout for the whole block
+    const bool ok = p.stall ? tc::mbar_wait_bounded(idle, 0, 1000000LL)
+                            : tc::mbar_wait_bounded(mbar, phase & 1, 2000000000LL);
+    ++phase;
+    if (!ok) {
+      *abort_flag = 1;
+      atomicExch(p.err, PDG_TC_ERR_TIMEOUT);
+    }
+  };
+  const int lq = warp & 3, cc = warp >> 2;        // TMEM lane quarter, column block
+  const int trow = 32 * lq + lane;                // this thread's TMEM row (cell of the batch)
+  const uint32_t taddr = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(cc * TS::CW);
+  bool aborted = false;
+
   int nbt = 0;
   plan_step(0);
   int cb = range[0], ce = range[1];
@@ -416,7 +504,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   for (int s = 0; s < NS; ++s) {
     const int nbat = (ce - cb + nb - 1) / nb;
     if (nbat > 0) stage_batch(s, min(nb, ce - cb), nbt & 1, 2);
-    for (int bI = 0; bI < nbat; ++bI, ++nbt) {
+    for (int bI = 0; bI < nbat && !aborted; ++bI, ++nbt) {
       const int buf = nbt & 1;
       const int c0 = cb + bI * nb, cnt = min(nb, ce - c0);
       cp_async_wait_all();
@@ -432,16 +520,99 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
         if (iy == 0) rv = fma(tky, row[NN2 + NF2 + iz * NP + ix], rv);
         if (iz == 0) rv = fma(tkz, row[NN2 + 2 * NF2 + iy * NP + ix], rv);
         rbuf[(size_t)c * NN2 + q] = rv;
+        if constexpr (TC != 0) {   // row c of the A operand: theta r_c split into TF32 parts
+          float hi, lo;
+          tc::split_f64_bits<11>(rv, &hi, &lo);
+          const int idx = tc::op_index(c, q, 128);
+          aop[idx] = hi;
+          aop[TS::AOPS + idx] = lo;
+        }
       }
       const bool more = bI + 1 < nbat;
       if (more) batch_info(s, c0 + nb, min(nb, ce - c0 - nb), buf ^ 1);   // has its own barrier
+      const int par1 = (s + 1) & 1;
+      if constexpr (TC != 0) {
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) mma_issue();
+        if (more) stage_batch(s, min(nb, ce - c0 - nb), buf ^ 1, 3);   // while the products run
+        if (tid == 0) mma_wait();
+        __syncthreads();
+        if (*abort_flag) {
+          aborted = true;
+          break;
+        }
+        // (L1) x~ from TMEM (rows = cells, this warp's block of node columns)
+        tc::fence_after_sync();
+        float xr[TS::CW];
+        tc::tmem_ld<TS::CW>(taddr, xr);
+        if (trow < cnt) {
+#pragma unroll
+          for (int e = 0; e < TS::CW; ++e)
+            if (cc * TS::CW + e < NN) xt[trow * NN + cc * TS::CW + e] = xr[e];
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        // (R) residual theta r - B x~ of every node, split into the operand
+        for (int i = tid; i < cnt * NN; i += NT) {
+          const int c = i / NN, q = i % NN;
+          const int qz = q / NF, qy = (q / NP) % NP, qx = q % NP;
+          const int idx = tc::op_index(c, q, 128);
+          if constexpr (TC == 1) {
+            const double res = tc_residual<NP>(rbuf[(size_t)c * NN2 + q], xt + c * NN, kt, qz, qy, qx);
+            float hi, lo;
+            tc::split_f64_bits<11>(res, &hi, &lo);
+            aop[idx] = hi;
+            aop[TS::AOPS + idx] = lo;
+          } else {
+            const dd res = tc_residual_dd<NP>(rbuf[(size_t)c * NN2 + q], xt + c * NN, ktf, qz, qy, qx);
+            const float hi = tc::tf32_rna(res.hi);
+            aop[idx] = hi;
+            aop[TS::AOPS + idx] = tc::tf32_rna(__fadd_rn(__fsub_rn(res.hi, hi), res.lo));
+          }
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          mma_issue();
+          mma_wait();
+        }
+        __syncthreads();
+        if (*abort_flag) {
+          aborted = true;
+          break;
+        }
+        // (L2) x = x~ + d (= theta Binv r: the face value); outputs and faces
+        tc::fence_after_sync();
+        float dv[TS::CW];
+        tc::tmem_ld<TS::CW>(taddr, dv);
+        if (trow < cnt) {
+          const int r = cr[buf * nb + trow], k = ck[buf * nb + trow], j = s - r - k;
+          const bool out = cit[buf * (nb + 1) + trow + 1] - cit[buf * (nb + 1) + trow] == NN;
+          const long long o0 = off0[buf * nb + trow];
+          double* fx = hf + (long long)par1 * 3 * slab + ((long long)k * RY + r) * NF2;
+#pragma unroll
+          for (int e = 0; e < TS::CW; ++e) {
+            const int q = cc * TS::CW + e;
+            if (q < NN) {
+              const double x = tc::f64_from_f32_bits(xr[e]) + tc::f64_from_f32_bits(dv[e]);
+              const int qz = q / NF, qy = (q / NP) % NP, qx = q % NP;
+              if (out) st(g.fout + o0 + nodeoff[q], (x - omth * sb[(size_t)trow * RS + q]) * rth);
+              if (qx == NP - 1 && j + 1 < RX) st(fx + qz * NP + qy, x);
+              if (qy == NP - 1 && r + 1 < RY) st(fx + slab + NF2 + qz * NP + qx, x);
+              if (qz == NP - 1 && k + 1 < RZ) st(fx + 2 * slab + (long long)RY * NF2 + qy * NP + qx, x);
+            }
+          }
+        }
+        tc::fence_before_sync();
+        continue;
+      }
       __syncthreads();
       // (B) items of the batch: every node of an output cell, the face nodes of a start cell;
       // each thread issues its share of the next batch's copies after its first item
       const int* itb = cit + buf * (nb + 1);
       const unsigned short* icb = icell + (size_t)buf * nb * NN;
       const int nitems = itb[cnt];
-      const int par1 = (s + 1) & 1;
       bool staged = !more;
       for (int it = tid; it < nitems; it += NT) {
         const int c = icb[it], loc = it - itb[c];
@@ -496,6 +667,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
       }
       if (!staged) stage_batch(s, min(nb, ce - c0 - nb), buf ^ 1, 3);
     }
+    if (aborted) break;
     // (2) plan hyperplane s + 1 and start copying the state of its first batch; then the
     // population's blocks meet: every face of step s is written before any block reads it
     // at step s + 1
@@ -531,20 +703,33 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
     }
     __syncthreads();
     if (*abort_flag) {
-      cp_async_wait_all();   // the next state's copies in flight
-      return;
+      aborted = true;
+      break;
+    }
+  }
+  // the copies in flight (after a failed wait: the next state's), then, tensor-core form,
+  // the products in flight after a timed-out wait (bounded) and the TMEM columns
+  if constexpr (TC != 0)
+    if (aborted && tid == 0) tc::mbar_wait_bounded(mbar, (phase - 1) & 1, 2000000000LL);
+  cp_async_wait_all();
+  if constexpr (TC != 0) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+      tc::fence_after_sync();
+      tc::tmem_dealloc(tmem, TS::NCOL);
     }
   }
 }
 
-template <int NP, class T>
+template <int NP, class T, int TC>
 __global__ void __launch_bounds__(512, 1) corner_hp_kernel(const __grid_constant__ PdgCornerPass p) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  corner_hp_body<NP, T>(p, smraw);
+  extern __shared__ __align__(128) unsigned char smraw[];
+  corner_hp_body<NP, T, TC>(p, smraw);
 }
 
 // Blocks of the kernel for n that fit one SM with smem bytes of shared memory.
-template <class T>
+template <class T, int TC>
 int hp_blocks_per_sm(int n, size_t smem) {
   auto occ = [&](auto kern) -> int {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -559,16 +744,17 @@ int hp_blocks_per_sm(int n, size_t smem) {
     return b;
   };
   switch (n) {
-    case 2: return occ(corner_hp_kernel<2, T>);
-    case 3: return occ(corner_hp_kernel<3, T>);
-    case 4: return occ(corner_hp_kernel<4, T>);
+    case 2: return occ(corner_hp_kernel<2, T, TC>);
+    case 3: return occ(corner_hp_kernel<3, T, TC>);
+    case 4:
+      if constexpr (TC == 0) return occ(corner_hp_kernel<4, T, TC>);
   }
   return 0;
 }
 
 // Cooperative launch of npop x hg blocks of 512 threads (the host sized hg so that all are
 // resident).
-template <class T>
+template <class T, int TC>
 int launch_corner_hp_typed(const PdgCornerPass& p, size_t smem, cudaStream_t st) {
   auto go = [&](auto kern) -> int {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -589,9 +775,10 @@ int launch_corner_hp_typed(const PdgCornerPass& p, size_t smem, cudaStream_t st)
     return (int)e;
   };
   switch (p.n) {
-    case 2: return go(corner_hp_kernel<2, T>);
-    case 3: return go(corner_hp_kernel<3, T>);
-    case 4: return go(corner_hp_kernel<4, T>);
+    case 2: return go(corner_hp_kernel<2, T, TC>);
+    case 3: return go(corner_hp_kernel<3, T, TC>);
+    case 4:
+      if constexpr (TC == 0) return go(corner_hp_kernel<4, T, TC>);
   }
   return (int)cudaErrorInvalidValue;
 }

@@ -298,9 +298,14 @@ int plan_corner_hyper(pdg_ctx* c, PdgCornerPass* pp) {
   const int RZ = p.ncz + (p.per[2] ? p.c.wz : 0);
   const long long NN = (long long)p.n * p.n * p.n, NF2 = ((long long)p.n * p.n + 1) & ~1LL;
   if ((long long)RY * RZ * NN >= (1LL << 30)) return 0;   // item counts of a step in 32 bits
+  if (p.tc && p.n > 3) return 0;   // the tensor-core form's batches are 128 cells: degree <= 2 fits
   p.hyper = 1;
   p.threads = 512;
-  p.hnb = p.n == 2 ? 256 : (p.n == 3 ? 128 : 64);
+  p.hnb = p.tc ? 128 : (p.n == 2 ? 256 : (p.n == 3 ? 128 : 64));
+  if (p.tc && pdg_corner_smem(p) > 220 * 1024) {
+    p.hyper = 0;
+    return 0;
+  }
   while (p.hnb > 16 && pdg_corner_smem(p) > 220 * 1024) p.hnb /= 2;
   if (pdg_corner_smem(p) > 220 * 1024) {
     p.hyper = 0;
@@ -435,9 +440,9 @@ int make_corner(pdg_ctx* c, const PdgPassSpec& sp, const Lattice& L, PdgCornerPa
   }
   p.prec = c->model.prec;
   p.threads = c->cshape[0] && !p.tc ? c->cshape[0] : 512;   // the tensor-core kernel runs 16 warps
-  // hyperplane sweep of the whole region (default; not for forced box shapes or the
-  // tensor-core form), when its tables fit shared memory and its blocks can all be resident
-  if (c->corner_sweep && !p.tc && !c->cshape[1]) {
+  // hyperplane sweep of the whole region (default; not for forced box shapes), when its
+  // tables fit shared memory and its blocks can all be resident
+  if (c->corner_sweep && !c->cshape[1]) {
     int r = plan_corner_hyper(c, &p);
     if (r < 0) return fail(c, PDG_ERR_UNSUPPORTED, "internal: corner hyperplane plan");
     if (r == 1) return PDG_OK;

@@ -147,6 +147,7 @@ def test_layer_pairs_equal_single_layers_bitwise(prec, lat, order):
     out = {}
     for layers in (1, 2):
         s = pdg.solver_for(cfg, precision=prec)
+        s.set_option(pdg.PDG_OPT_CORNER_SWEEP, 0)      # layer pairs belong to the box sweep
         s.set_option(pdg.PDG_OPT_TC_LAYERS, layers)
         s.set_w(np.ascontiguousarray(w0.reshape(-1)))
         s.step(cfg.dt, 3)
@@ -155,3 +156,36 @@ def test_layer_pairs_equal_single_layers_bitwise(prec, lat, order):
     np.testing.assert_array_equal(out[1], out[2])
     f_ref = run_oracle(cfg, w0, cfg.dt, 3)
     assert_parity(out[2].reshape(f_ref.shape), f_ref, TOL_MIXED)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("lat,order", [("q15", 1), ("q27", 2), ("q15", 2)])
+def test_hyperplane_and_box_forms_match_the_oracle(prec, lat, order):
+    """The tensor-core form on hyperplanes (default for degree <= 2: batches of up to 128
+    cells of one hyperplane, one product row each) and on box anti-diagonals both reach
+    the oracle within the mixed-precision bar; they differ by the refinement's rounding."""
+    from paper_1702_00169_gb300 import pdg
+    cfg = _cfg(lat, (3, 2, 3), (2, 3, 1), order)
+    w0 = oracle_w0(cfg)
+    f_ref = run_oracle(cfg, w0, cfg.dt, 3)
+    out = {}
+    for sweep in (1, 0):
+        s = pdg.solver_for(cfg, precision=prec)
+        s.set_option(pdg.PDG_OPT_CORNER_SWEEP, sweep)
+        s.set_w(np.ascontiguousarray(w0.reshape(-1)))
+        s.step(cfg.dt, 3)
+        out[sweep] = s.get_f().reshape(f_ref.shape)
+        s.close()
+        assert_parity(out[sweep], f_ref, TOL_MIXED, ("sweep", sweep))
+    assert rel_l2(out[1], out[0]) <= 1e-11
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_hyperplane_form_at_scale(prec):
+    """80 x 50 x 50 cells, d = 2 (D3Q15): 226 hyperplanes, 19 blocks per population, many
+    batches of 128 cells per block and step.  One M2 step, every value against the oracle."""
+    cfg = _cfg("q15", (20, 25, 25), (4, 2, 2), 2)
+    w0 = oracle_w0(cfg)
+    f_ref = run_oracle(cfg, w0, cfg.dt, 1)
+    f = run_gpu(cfg, w0, cfg.dt, 1, precision=prec)
+    assert_parity(f, f_ref, TOL_MIXED)
