@@ -20,6 +20,7 @@ int pdg_corner_hp_blocks_per_sm(const PdgCornerPass& p, size_t smem) {
 
 int pdg_launch_corner_hp(const PdgCornerPass& p, size_t smem, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
+  if (p.hnb < 1 || p.hnb > 512 || (p.hnb & (p.hnb - 1))) return (int)cudaErrorInvalidValue;   // a power of two
   if (p.tc) {   // one product row per cell of a batch of 128; degree <= 2 (K <= 32)
     if (p.hnb != 128 || p.n > 3 || !p.binv_tc || !p.err) return (int)cudaErrorInvalidValue;
     return p.tc == 1 ? pdgdev::launch_corner_hp_typed<double, 1>(p, smem, st)

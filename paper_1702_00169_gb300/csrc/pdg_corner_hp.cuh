@@ -60,6 +60,7 @@ struct HpShape {
   static constexpr int NN2 = (NN + 1) & ~1, NF2 = (NF + 1) & ~1;     // 16-byte rows
   static constexpr int RS = NN2 + 3 * NF2;   // staged row: state, then the x, y, z inflow faces
   static constexpr int BS = NN2 + ((NN2 / 2) % 2 == 0 ? 2 : 0);   // Binv row stride: odd in 16-byte units
+  static constexpr int RB = BS;   // row stride of theta r in shared memory (the same rule)
 };
 
 // tc != 0: the tensor-core form (nb = 128 cells, one product row each) adds, first and
@@ -91,7 +92,7 @@ struct HpSmem {
     }
     binv = take(tc ? 0 : sizeof(double) * NN * BS);
     stage = take(sizeof(double) * 2 * (size_t)nb * RS);
-    rbuf = take(sizeof(double) * (size_t)nb * NN2);
+    rbuf = take(sizeof(double) * (size_t)nb * BS);
     off0 = take(sizeof(long long) * 2 * nb);
     nodeoff = take(sizeof(long long) * NN);
     colx = take(sizeof(long long) * (RX + 1));
@@ -157,6 +158,7 @@ template <int NP, class T, int TC>
 __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned char* smraw) {
   using S = HpShape<NP>;
   constexpr int NF = S::NF, NN = S::NN, NFF = S::NFF, NN2 = S::NN2, NF2 = S::NF2, RS = S::RS, BS = S::BS;
+  constexpr int RB = S::RB;
   constexpr int NT = 512;
   const int G = p.hg, nb = p.hnb;
   const int pop = blockIdx.x / G, gi = blockIdx.x % G;
@@ -199,7 +201,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   const HpSmem L(NP, nb, RX, RY, RZ, TC);
   T* Bq = reinterpret_cast<T*>(smraw + L.binv);        // Binv[q][m] at q * BS + m
   T* stage = reinterpret_cast<T*>(smraw + L.stage);    // 8-byte words (FP64 or a float pair)
-  T* rbuf = reinterpret_cast<T*>(smraw + L.rbuf);      // r of cell c at c * NN2
+  T* rbuf = reinterpret_cast<T*>(smraw + L.rbuf);      // theta r of cell c at c * RB
   long long* off0 = reinterpret_cast<long long*>(smraw + L.off0);        // node (0, 0, 0) of a cell
   long long* nodeoff = reinterpret_cast<long long*>(smraw + L.nodeoff);  // node q from node 0
   long long* colx = reinterpret_cast<long long*>(smraw + L.colx);
@@ -464,16 +466,21 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   // them to the mbarrier) and later waits for them, boundedly
   constexpr uint32_t IDESC = tc::idesc_tf32(128, TS::NPAD);
   uint32_t phase = 0;
+  // descriptors of the operand splits at K-step 0; a K-step of 8 moves the start address by
+  // two core-matrix columns (the address field is the byte address / 16, and shared
+  // memory addresses stay below 2^18 bytes, so the offsets add without a carry)
+  const uint64_t adesc[2] = {tc::smem_desc(tc::smem_u32(aop), 16 * 128, 128),
+                             tc::smem_desc(tc::smem_u32(aop + TS::AOPS), 16 * 128, 128)};
+  const uint64_t bdesc[2] = {tc::smem_desc(tc::smem_u32(bop), (TS::NPAD / 8) * 128, 128),
+                             tc::smem_desc(tc::smem_u32(bop + TS::BOPS), (TS::NPAD / 8) * 128, 128)};
   auto mma_issue = [&]() {   // tid 0 only
     tc::fence_after_sync();
-#pragma unroll 1
-    for (int sp = 0; sp < 3; ++sp) {
-      const int sa = sp == 1 ? 1 : 0, sbb = sp == 2 ? 1 : 0;   // (hi, hi), (lo, hi), (hi, lo)
-#pragma unroll 1
+#pragma unroll
+    for (int sp = 0; sp < 3; ++sp) {   // (hi, hi), (lo, hi), (hi, lo)
+#pragma unroll
       for (int ks = 0; ks < TS::KP / 8; ++ks) {
-        const uint64_t ad = tc::smem_desc(tc::smem_u32(aop + sa * TS::AOPS) + ks * 2 * 16 * 128, 16 * 128, 128);
-        const uint64_t bd = tc::smem_desc(tc::smem_u32(bop + sbb * TS::BOPS) + ks * 2 * (TS::NPAD / 8) * 128,
-                                          (TS::NPAD / 8) * 128, 128);
+        const uint64_t ad = adesc[sp == 1 ? 1 : 0] + (uint64_t)((ks * 2 * 16 * 128) >> 4);
+        const uint64_t bd = bdesc[sp == 2 ? 1 : 0] + (uint64_t)((ks * 2 * (TS::NPAD / 8) * 128) >> 4);
         tc::mma_tf32(tmem, ad, bd, IDESC, (sp | ks) ? 1u : 0u);
       }
     }
@@ -509,20 +516,26 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
       const int c0 = cb + bI * nb, cnt = min(nb, ce - c0);
       cp_async_wait_all();
       __syncthreads();
-      // (A) theta r_c of every node of the batch
+      // (A) theta r_c of every node of the batch.  Item i is node i / nb of cell i % nb (nb a
+      // power of two), so the 32 threads of a warp take one node of 32 cells: the face
+      // terms below are warp-uniform and each FMA runs on full warps (with mixed nodes a
+      // warp would issue all three under masks, each costing the FP64 unit a full warp slot)
       const T* sb = stage + (size_t)buf * nb * RS;
-      for (int i = tid; i < cnt * NN; i += NT) {
-        const int c = i / NN, q = i % NN;
+      constexpr int QG = (NN + 3) / 4;
+      const int lgnb = __ffs(nb) - 1;
+      for (int i = tid; i < (NN << lgnb); i += NT) {
+        const int q = i >> lgnb, c = i & (nb - 1);
+        if (c >= cnt) continue;
         const int iz = q / NF, iy = (q / NP) % NP, ix = q % NP;
         const T* row = sb + (size_t)c * RS;
         T rv = row[q];
         if (ix == 0) rv = fma(tkx, row[NN2 + iz * NP + iy], rv);
         if (iy == 0) rv = fma(tky, row[NN2 + NF2 + iz * NP + ix], rv);
         if (iz == 0) rv = fma(tkz, row[NN2 + 2 * NF2 + iy * NP + ix], rv);
-        rbuf[(size_t)c * NN2 + q] = rv;
+        rbuf[(size_t)c * RB + q] = rv;
         if constexpr (TC != 0) {   // row c of the A operand: theta r_c split into TF32 parts
           float hi, lo;
-          tc::split_f64_bits<11>(rv, &hi, &lo);
+          tc::split_tf32_fast(rv, &hi, &lo);
           const int idx = tc::op_index(c, q, 128);
           aop[idx] = hi;
           aop[TS::AOPS + idx] = lo;
@@ -554,18 +567,19 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
         tc::fence_before_sync();
         __syncthreads();
         // (R) residual theta r - B x~ of every node, split into the operand
-        for (int i = tid; i < cnt * NN; i += NT) {
-          const int c = i / NN, q = i % NN;
+        for (int i = tid; i < QG * 16 * 32; i += NT) {   // i = tc::op_index(c, q, 128)
+          const int c = 8 * ((i >> 5) & 15) + ((i & 31) >> 2), q = 4 * (i >> 9) + (i & 3);
+          if (c >= cnt || q >= NN) continue;
           const int qz = q / NF, qy = (q / NP) % NP, qx = q % NP;
-          const int idx = tc::op_index(c, q, 128);
+          const int idx = i;
           if constexpr (TC == 1) {
-            const double res = tc_residual<NP>(rbuf[(size_t)c * NN2 + q], xt + c * NN, kt, qz, qy, qx);
+            const double res = tc_residual<NP>(rbuf[(size_t)c * RB + q], xt + c * NN, kt, qz, qy, qx);
             float hi, lo;
-            tc::split_f64_bits<11>(res, &hi, &lo);
+            tc::split_tf32_fast(res, &hi, &lo);
             aop[idx] = hi;
             aop[TS::AOPS + idx] = lo;
           } else {
-            const dd res = tc_residual_dd<NP>(rbuf[(size_t)c * NN2 + q], xt + c * NN, ktf, qz, qy, qx);
+            const dd res = tc_residual_dd<NP>(rbuf[(size_t)c * RB + q], xt + c * NN, ktf, qz, qy, qx);
             const float hi = tc::tf32_rna(res.hi);
             aop[idx] = hi;
             aop[TS::AOPS + idx] = tc::tf32_rna(__fadd_rn(__fsub_rn(res.hi, hi), res.lo));
@@ -618,7 +632,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
         const int c = icb[it], loc = it - itb[c];
         const bool out = itb[c + 1] - itb[c] == NN;
         const int q = out ? loc : fnode[loc];
-        const T* rc = rbuf + (size_t)c * NN2;
+        const T* rc = rbuf + (size_t)c * RB;
         const T* br = Bq + (size_t)q * BS;
         T acc;
         if constexpr (__is_same(T, double)) {

@@ -122,7 +122,7 @@ __device__ __forceinline__ dd tc_residual_dd(double r, const float* xc, const fl
   for (int i = 0; i < NP; ++i) term(2, qz, i, xc[(i * NP + qy) * NP + qx]);
   const dd s = dd_fast_two_sum(S, L);
   dd rr;
-  tc::split_f64_bits<24>(r, &rr.hi, &rr.lo);
+  tc::split_dd_fast(r, &rr.hi, &rr.lo);
   return dd_add_accurate(rr, dd{-s.hi, -s.lo});
 }
 

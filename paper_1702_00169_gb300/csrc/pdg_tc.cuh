@@ -95,6 +95,57 @@ __device__ __forceinline__ void split_f64_bits(double x, float* hi, float* lo) {
   *lo = f32_from_parts(sign ^ (R < 0 ? 1u : 0u), e - 1075 + p + 127, (ml & ((1u << (bits - 1)) - 1)) << (24 - bits));
 }
 
+// x truncated to 24 significant bits, as an FP32 value built from the FP64 bit pattern (sign,
+// rebiased exponent, the top 23 mantissa bits); *e gets the FP64 biased exponent and *lw the
+// low 32 bits of the pattern.  Returns false (value 0) outside the normal FP32 range.
+__device__ __forceinline__ bool f32_trunc_bits(double x, float* t, int* e, unsigned* lw) {
+  const unsigned hw = (unsigned)__double2hiint(x);
+  *lw = (unsigned)__double2loint(x);
+  *e = (int)((hw >> 20) & 0x7ffu);
+  if (*e <= 1023 - 127 || *e >= 1023 + 128) {
+    *t = 0.0f;
+    return false;
+  }
+  *t = __uint_as_float((hw & 0x80000000u) | ((unsigned)(*e - 1023 + 127) << 23) | ((hw & 0xfffffu) << 3) |
+                       (*lw >> 29));
+  return true;
+}
+
+// The two TF32 parts of an FP64 value, |x - hi - lo| <= 2^-22 |x| (the precision of
+// split_f64_bits<11>, with far fewer operations): hi = the 24-bit truncation rounded to TF32,
+// lo = the exact FP32 remainder of that truncation rounded to TF32.
+__device__ __forceinline__ void split_tf32_fast(double x, float* hi, float* lo) {
+  float t;
+  int e;
+  unsigned lw;
+  f32_trunc_bits(x, &t, &e, &lw);
+  *hi = tf32_rna(t);
+  *lo = tf32_rna(__fsub_rn(t, *hi));
+}
+
+// An FP64 value as an unevaluated FP32 pair, |x - hi - lo| <= 2^-48 |x| for |x| >= 2^-74
+// (absolute error below 2^-98 under it): hi = the 24-bit truncation, lo = the remaining 29
+// mantissa bits (an integer below 2^29, rounded to FP32) times 2^(e - 1075), the scale an
+// exact power of two.
+__device__ __forceinline__ void split_dd_fast(double x, float* hi, float* lo) {
+  float t;
+  int e;
+  unsigned lw;
+  if (!f32_trunc_bits(x, &t, &e, &lw)) {
+    *hi = 0.0f;
+    *lo = 0.0f;
+    return;
+  }
+  *hi = t;
+  const int se = e - 1075 + 127;
+  if (se <= 0) {
+    *lo = 0.0f;
+    return;
+  }
+  const float m = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), __uint_as_float((unsigned)se << 23));
+  *lo = __double2hiint(x) < 0 ? -m : m;
+}
+
 // The FP64 value of an FP32 value (exact).
 __device__ __forceinline__ double f64_from_f32_bits(float f) {
   const unsigned b = __float_as_uint(f);
