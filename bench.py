@@ -133,7 +133,7 @@ def collision_flops(kind, dim):
 # points of a 384^3 launch (profiles/pass_kernel_fp64_euler_d3q6_384cube.md).
 TRAFFIC = {("shallow_water_d2q4_64x64x8x8_d3", 1, "fp64", 8): 1793.12e6,
            ("isothermal_d2q9_64x64x8x8_d3", 3, "fp64", None): 279.41e6,
-           ("euler_d3q6_32c3x4c3_d2", 1, "fp64", 8): 8 * 5092.82e6}
+           ("euler_d3q6_32c3x4c3_d2", 1, "fp64", 8): 8 * 4895.31e6}
 
 SOURCES = {"gravity": dict(gravity=(0.0, -1.0)),
            "penalization": dict(K_s=300.0, kappa=40.0, x_c=(0.25, 0.5), w_s=(1.0, 0.0, 0.0)),
@@ -913,7 +913,9 @@ def main():
             ms_t_max, units_t = aggregate_ranks(ms_t, dofs * args.steps)
             tensor_core[prec] = {
                 "precision": ("split-TF32 cell inverse on the tensor cores (tcgen05), one refinement with the "
-                              "residual in " + ("FP64" if prec == "tf32" else "double-float") + "; FP64 state"),
+                              "residual in " + ("FP64" if prec == "tf32" else "double-float") + "; FP64 state; " +
+                              ("batches of 128 hyperplane cells per product (degree <= 2)" if args.corner_sweep
+                               else "box anti-diagonals per product")),
                 "value": units_t / (ms_t_max * 1e-3), "ms_per_step": ms_t_max / args.steps,
                 "speedup_vs_fp64": ms_max / ms_t_max,
                 "rel_l2_w_vs_fp64_after_steps": float(np.linalg.norm(w_end_t - w_end) / np.linalg.norm(w_end)),
@@ -971,7 +973,8 @@ def main():
     kinds = {0: "transport pass (composed T T on the populations of the other axes)",
              1: "last-axis pass (T, collision, T)",
              3: "diagonal transport pass (4 populations of one plane, tiled 2-D wavefront)",
-             4: "corner transport pass (8 populations, boxes swept as layer-by-layer wavefronts)"}
+             4: ("corner transport pass (8 populations, cell hyperplanes of the whole mesh, cooperative launch)"
+                 if args.corner_sweep else "corner transport pass (8 populations, boxes swept as layer-by-layer wavefronts)")}
     k_dom = dominant(kms)
     avg_ms = kms[k_dom] / max(1, launches[k_dom])
     bytes_launch, flops_launch = kernel_work(k_dom)
