@@ -392,3 +392,139 @@ def test_planner_line_windows_make_the_sweep_exact(pdg, d, nu, theta):
     assert _rel(one, T(f)) < 1e-14
     two = _line_composed(f.reshape(N, n), d, nu, theta, r["W2"]).reshape(-1)
     assert _rel(two, T(T(f))) < 1e-14
+
+
+# ----------------------------------------------------------------------------------------
+# hyperplane sweep of the corner velocities (the organisation of the default corner kernel):
+# the whole mesh plus one truncated start per axis, swept cell hyperplane by cell hyperplane
+# (column + row + layer = s); each hyperplane's cells, enumerated layer by layer and row
+# inside a layer, are cut into G ranges of equal work (n^3 node dot products per output
+# cell, the face nodes per start cell), each range processed in batches; the faces a cell
+# passes on go to a slot [parity][face][layer][row] of the receiving cell.  The integer
+# arithmetic below is the kernel's (per-layer prefix tables, first cell of a work offset,
+# slot indices); the values are checked against the LU solve, and the bookkeeping by
+# assertions: every cell once per step, every slot written once per step and read one
+# step after it was written.
+
+def _hp_rows(s, k, RX, RY):
+    rlo, rhi = max(0, s - k - (RX - 1)), min(RY - 1, s - k)
+    return max(0, rhi - rlo + 1), rlo, rhi
+
+
+def _hp_out_rows(s, k, rlo, rhi, w):
+    if k < w[2]:
+        return 0, 0
+    olo, ohi = max(rlo, w[1]), min(rhi, s - k - w[0])
+    return max(0, ohi - olo + 1), olo
+
+
+def _hyperplane_sweep(F, d, nus, theta, signs, W, G, nb):
+    n = d + 1
+    NF, NN = n * n, n ** 3
+    NFF = NN - (n - 1) ** 3
+    Binv, k = _cell_operator(d, nus, theta)
+    c1 = (1.0 - theta) / theta
+    Gs = F.copy()
+    for a in range(3):
+        if signs[a] < 0:
+            Gs = np.flip(Gs, axis=2 - a)
+    nc = [Gs.shape[2 - a] // n for a in range(3)]
+    w = list(W)
+    RX, RY, RZ = nc[0] + w[0], nc[1] + w[1], nc[2] + w[2]
+    fnode = [q for q in range(NN) if q % n == n - 1 or (q // n) % n == n - 1 or q // NF == n - 1]
+    assert len(fnode) == NFF
+    out = np.full_like(Gs, np.nan)
+    slots = np.full((2, 3, RZ, RY, NF), np.nan)
+    written = np.full((2, 3, RZ, RY), -10, dtype=np.int64)
+
+    def cell(j, r, kk):
+        cx, cy, cz = (j - w[0]) % nc[0], (r - w[1]) % nc[1], (kk - w[2]) % nc[2]
+        return (slice(cz * n, cz * n + n), slice(cy * n, cy * n + n), slice(cx * n, cx * n + n))
+
+    def old_face(j, r, kk, a):              # +a face of the upwind cell (old state)
+        up = [j, r, kk]
+        up[a] -= 1
+        v = Gs[cell(*up)]
+        return (v[:, :, n - 1], v[:, n - 1, :], v[n - 1, :, :])[a].reshape(-1)
+
+    for s in range(RX + RY + RZ - 2):
+        rcell = np.zeros(RZ + 1, dtype=np.int64)
+        ritem = np.zeros(RZ + 1, dtype=np.int64)
+        for kk in range(RZ):
+            cnt, rlo, rhi = _hp_rows(s, kk, RX, RY)
+            no = _hp_out_rows(s, kk, rlo, rhi, w)[0] if cnt else 0
+            rcell[kk + 1] = rcell[kk] + cnt
+            ritem[kk + 1] = ritem[kk] + cnt * NFF + no * (NN - NFF)
+        items = int(ritem[RZ])
+
+        def first_cell(P):                  # first cell whose first item is >= P
+            if P >= items:
+                return int(rcell[RZ])
+            kk = int(np.searchsorted(ritem, P, side="right")) - 1
+            cnt, rlo, rhi = _hp_rows(s, kk, RX, RY)
+            assert cnt > 0
+            no, olo = _hp_out_rows(s, kk, rlo, rhi, w)
+            for r in range(rlo, rhi + 2):
+                before = max(0, min(r, olo + no) - olo) if no else 0
+                if ritem[kk] + (r - rlo) * NFF + before * (NN - NFF) >= P:
+                    return int(rcell[kk] + r - rlo)
+            raise AssertionError("no first cell")
+
+        seen = np.zeros(int(rcell[RZ]), dtype=np.int64)
+        par, par1 = s & 1, (s + 1) & 1
+        for gi in range(G):
+            cb, ce = first_cell(items * gi // G), first_cell(items * (gi + 1) // G)
+            for c0 in range(cb, ce, nb):
+                for c in range(c0, min(c0 + nb, ce)):
+                    kk = int(np.searchsorted(rcell, c, side="right")) - 1
+                    _, rlo, _ = _hp_rows(s, kk, RX, RY)
+                    r = rlo + c - int(rcell[kk])
+                    j = s - r - kk
+                    assert 0 <= j < RX and 0 <= r < RY
+                    seen[c] += 1
+                    f = Gs[cell(j, r, kk)]
+                    inflow = []
+                    for a, edge in enumerate((j == 0, r == 0, kk == 0)):
+                        if edge:
+                            inflow.append(old_face(j, r, kk, a))
+                        else:
+                            assert written[par, a, kk, r] == s - 1
+                            inflow.append(slots[par, a, kk, r])
+                    tr = f.copy()                                    # theta r
+                    tr[:, :, 0] += theta * k[0] * inflow[0].reshape(n, n)
+                    tr[:, 0, :] += theta * k[1] * inflow[1].reshape(n, n)
+                    tr[0, :, :] += theta * k[2] * inflow[2].reshape(n, n)
+                    is_out = j >= w[0] and r >= w[1] and kk >= w[2]
+                    x = (Binv[fnode] @ tr.reshape(-1)) if not is_out else Binv @ tr.reshape(-1)
+                    if is_out:
+                        sl = cell(j, r, kk)
+                        assert np.isnan(out[sl]).all()
+                        out[sl] = ((x - (1.0 - theta) * f.reshape(-1)) / theta).reshape(n, n, n)
+                        xf = x.reshape(n, n, n)
+                    else:
+                        xf = np.full(NN, np.nan)
+                        xf[fnode] = x
+                        xf = xf.reshape(n, n, n)
+                    for a, (jj, rr, kq, face) in enumerate(((j + 1, r, kk, xf[:, :, n - 1]),
+                                                             (j, r + 1, kk, xf[:, n - 1, :]),
+                                                             (j, r, kk + 1, xf[n - 1, :, :]))):
+                        if jj < RX and rr < RY and kq < RZ:
+                            assert written[par1, a, kq, rr] != s
+                            written[par1, a, kq, rr] = s
+                            slots[par1, a, kq, rr] = face.reshape(-1)
+        assert (seen == 1).all()
+    for a in range(3):
+        if signs[a] < 0:
+            out = np.flip(out, axis=2 - a)
+    return out
+
+
+@pytest.mark.parametrize("d,signs,nus,ncells,W,G,nb", [(1, (1, 1, 1), (1.0, 1.0, 1.0), (3, 4, 2), (17, 17, 17), 3, 16),
+                                                       (2, (-1, 1, -1), (1.0, 1.0, 1.0), (3, 3, 3), (16, 16, 16), 5, 8),
+                                                       (1, (1, -1, -1), (0.7, 1.0, 0.9), (2, 3, 4), (17, 17, 17), 2, 32)])
+def test_corner_hyperplane_sweep_with_face_slots_equals_the_lu_solve(d, signs, nus, ncells, W, G, nb):
+    mesh, T = _lu_reference(3, ncells, d, signs, nus, 0.5)
+    F = np.random.default_rng(7 + d).standard_normal(mesh.shape)
+    ref = T(F)
+    assert _rel(_hyperplane_sweep(F, d, nus, 0.5, signs, W, G, nb), ref) < 1e-14
+    assert _rel(_hyperplane_sweep(F, d, nus, 0.5, signs, (2, 2, 2), G, nb), ref) > 1e-6
