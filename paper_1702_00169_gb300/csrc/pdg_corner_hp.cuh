@@ -427,33 +427,33 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
         const int c = i / NN, e = i % NN;
         cp_async8(sb + (size_t)c * RS + e, g.fin + off0[buf * nb + c] + nodeoff[e]);
       }
-    if (what & 2) {
-      constexpr int per = 3 * NF2;
+    if (what & 2) {   // one item per 16-byte chunk of a face slot
+      constexpr int CH = NF2 / 2, per = 3 * CH;
       for (int i = tid; i < cnt * per; i += NT) {
         const int c = i / per, e = i % per;
-        const int a = e / NF2, u = e % NF2;
+        const int a = e / CH, u0 = 2 * (e % CH);
         const int r = cr[buf * nb + c], k = ck[buf * nb + c], j = s - r - k;
-        double* dst = sb + (size_t)c * RS + NN2 + e;
+        double* dst = sb + (size_t)c * RS + NN2 + a * NF2 + u0;
         const bool edge = a == 0 ? j == 0 : (a == 1 ? r == 0 : k == 0);
         if (!edge) {
-          if ((u & 1) == 0)
-            cp_async16_cg(dst, hf + ((long long)(par * 3 + a) * RZ + k) * RY * NF2 + (long long)r * NF2 + u);
+          cp_async16_cg(dst, hf + ((long long)(par * 3 + a) * RZ + k) * RY * NF2 + (long long)r * NF2 + u0);
           continue;
         }
-        if (u >= NF) continue;
-        const int u1 = u / NP, u2 = u % NP;
-        const double* src;
-        if (a == 0) {   // +x face of the cell upwind of column 0: node (iz, iy) = (u1, u2)
-          src = g.bx ? g.fbx + corner_py<NP>(g, r, u2) * g.fls[0][1] + corner_pz<NP>(g, k, u1) * g.fls[0][2]
-                     : g.fin + corner_off(g, -1, r, k, u1, u2, NP - 1);
-        } else if (a == 1) {   // +y face below row 0: node (iz, ix) = (u1, u2)
-          src = g.by ? g.fby + corner_px<NP>(g, j, u2) * g.fls[1][0] + corner_pz<NP>(g, k, u1) * g.fls[1][2]
-                     : g.fin + corner_off(g, j, -1, k, u1, NP - 1, u2);
-        } else {   // +z face under layer 0: node (iy, ix) = (u1, u2)
-          src = g.bz ? g.fbz + corner_px<NP>(g, j, u2) * g.fls[2][0] + corner_py<NP>(g, r, u1) * g.fls[2][1]
-                     : g.fin + corner_off(g, j, r, -1, NP - 1, u1, u2);
+        for (int u = u0; u < min(u0 + 2, NF); ++u) {   // the region's upwind boundary: old faces
+          const int u1 = u / NP, u2 = u % NP;
+          const double* src;
+          if (a == 0) {   // +x face of the cell upwind of column 0: node (iz, iy) = (u1, u2)
+            src = g.bx ? g.fbx + corner_py<NP>(g, r, u2) * g.fls[0][1] + corner_pz<NP>(g, k, u1) * g.fls[0][2]
+                       : g.fin + corner_off(g, -1, r, k, u1, u2, NP - 1);
+          } else if (a == 1) {   // +y face below row 0: node (iz, ix) = (u1, u2)
+            src = g.by ? g.fby + corner_px<NP>(g, j, u2) * g.fls[1][0] + corner_pz<NP>(g, k, u1) * g.fls[1][2]
+                       : g.fin + corner_off(g, j, -1, k, u1, NP - 1, u2);
+          } else {   // +z face under layer 0: node (iy, ix) = (u1, u2)
+            src = g.bz ? g.fbz + corner_px<NP>(g, j, u2) * g.fls[2][0] + corner_py<NP>(g, r, u1) * g.fls[2][1]
+                       : g.fin + corner_off(g, j, r, -1, NP - 1, u1, u2);
+          }
+          cp_async8(dst + (u - u0), src);
         }
-        cp_async8(dst, src);
       }
     }
   };
@@ -516,16 +516,30 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
       const int c0 = cb + bI * nb, cnt = min(nb, ce - c0);
       cp_async_wait_all();
       __syncthreads();
-      // (A) theta r_c of every node of the batch.  Item i is node i / nb of cell i % nb (nb a
-      // power of two), so the 32 threads of a warp take one node of 32 cells: the face
-      // terms below are warp-uniform and each FMA runs on full warps (with mixed nodes a
-      // warp would issue all three under masks, each costing the FP64 unit a full warp slot)
+      // (A) theta r_c of every node of the batch.  The item order is the one each form ran
+      // fastest with (measured): double-float (T = dd), item i is node i / nb of cell i % nb
+      // (nb a power of two: a warp takes one node of 32 cells, so its face terms are
+      // warp-uniform); FP64, consecutive nodes of a cell; tensor-core form, item i of a group
+      // of 32 is (cell 8 cg + i / 4, node 4 qg + i % 4), whose operand words are consecutive
+      // in the core-matrix layout (i = tc::op_index(c, q, 128), no bank conflict)
       const T* sb = stage + (size_t)buf * nb * RS;
       constexpr int QG = (NN + 3) / 4;
       const int lgnb = __ffs(nb) - 1;
-      for (int i = tid; i < (NN << lgnb); i += NT) {
-        const int q = i >> lgnb, c = i & (nb - 1);
-        if (c >= cnt) continue;
+      constexpr bool by_node = !__is_same(T, double);
+      for (int i = tid; i < (TC ? QG * 16 * 32 : (by_node ? (NN << lgnb) : cnt * NN)); i += NT) {
+        int c, q;
+        if constexpr (TC != 0) {
+          c = 8 * ((i >> 5) & 15) + ((i & 31) >> 2);
+          q = 4 * (i >> 9) + (i & 3);
+          if (c >= cnt || q >= NN) continue;
+        } else if constexpr (by_node) {
+          q = i >> lgnb;
+          c = i & (nb - 1);
+          if (c >= cnt) continue;
+        } else {
+          c = i / NN;
+          q = i % NN;
+        }
         const int iz = q / NF, iy = (q / NP) % NP, ix = q % NP;
         const T* row = sb + (size_t)c * RS;
         T rv = row[q];
@@ -536,9 +550,8 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
         if constexpr (TC != 0) {   // row c of the A operand: theta r_c split into TF32 parts
           float hi, lo;
           tc::split_tf32_fast(rv, &hi, &lo);
-          const int idx = tc::op_index(c, q, 128);
-          aop[idx] = hi;
-          aop[TS::AOPS + idx] = lo;
+          aop[i] = hi;
+          aop[TS::AOPS + i] = lo;
         }
       }
       const bool more = bI + 1 < nbat;
