@@ -298,6 +298,15 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
   unsigned* bar = p.hbar + pop;
   const int NS = RX + RY + RZ - 2;
 
+  // sum of ws[0 .. this warp) (the per-warp partial sums of a block scan): one load per lane
+  // and a butterfly, instead of a serial loop over the earlier warps
+  auto warps_before = [&](const int* ws) {
+    int x = (lane < NT / 32 && lane < warp) ? ws[lane] : 0;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    return x;
+  };
+
   // (0) cells and items of hyperplane s per layer, exclusive prefixes over the layers
   // (rcell, ritem), then (1) this block's cells: those whose first item lies in
   // [I gi / G, I (gi + 1) / G) (range).  Barriers inside; rcell / ritem are overwritten.
@@ -325,11 +334,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
       wsum2[warp] = vi;
     }
     __syncthreads();
-    int bc = 0, bi = 0;
-    for (int w = 0; w < warp; ++w) {
-      bc += wsum[w];
-      bi += wsum2[w];
-    }
+    const int bc = warps_before(wsum), bi = warps_before(wsum2);
     int pc = bc + vc - cs, pi = bi + vi - is;   // exclusive prefixes at k0
     for (int k = k0; k < min(RZ, k0 + per_t); ++k) {
       rcell[k] = pc;
@@ -345,17 +350,16 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
       ritem[RZ] = pi;
     }
     __syncthreads();
-    if (tid < 2) {
+    if (warp < 2) {   // warp 0: the first cell of this block's range, warp 1: of the next
       const long long I = ritem[RZ];
-      const int P = (int)(I * (gi + tid) / G);
+      const int P = (int)(I * (gi + warp) / G);
+      int le = 0;   // layers k with ritem[k] <= P (a non-decreasing table from ritem[0] = 0)
+      for (int k = lane; k < RZ; k += 32) le += ritem[k] <= P ? 1 : 0;
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) le += __shfl_xor_sync(0xffffffffu, le, d);
       int c = rcell[RZ];
-      if (P < I) {
-        int lo = 0, hi = RZ - 1;   // layer with ritem[k] <= P < ritem[k + 1]
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (ritem[mid] <= P) lo = mid;
-          else hi = mid - 1;
-        }
+      if (lane == 0 && P < I) {
+        const int lo = le - 1;   // layer with ritem[k] <= P < ritem[k + 1]
         int rlo, rhi, olo;
         hp_rows(s, lo, RX, RY, &rlo, &rhi);
         const int no = hp_out_rows(s, lo, rlo, rhi, g.wx, g.wy, g.wz, &olo);
@@ -369,7 +373,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
         }
         c = rcell[lo] + (a - rlo);
       }
-      range[tid] = c;
+      if (lane == 0) range[warp] = c;
     }
     __syncthreads();
   };
@@ -405,8 +409,7 @@ __device__ __forceinline__ void corner_hp_body(const PdgCornerPass& p, unsigned 
     }
     if (lane == 31) wsum[warp] = v;
     __syncthreads();
-    int base = 0;
-    for (int w = 0; w < warp; ++w) base += wsum[w];
+    const int base = warps_before(wsum);
     if (tid < cnt) {
       cit[buf * (nb + 1) + tid] = base + v - items;
       if constexpr (TC == 0) {   // the tensor-core form maps one thread row to one cell
