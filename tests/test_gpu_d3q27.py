@@ -1,7 +1,8 @@
 """GPU parity of the D3Q15 and D3Q27 paths: axis populations through the line passes, the
 D3Q27 edge populations through the plane-wise diagonal sweep, and the eight corner
-populations lambda (+-1, +-1, +-1) through the 3-D box sweep (layer-by-layer wavefronts with
-a truncated upwind start), against the oracle's 3-D Fourier form.
+populations lambda (+-1, +-1, +-1) through the 3-D hyperplane sweep (the default) or, where a
+launch shape forces it, the box sweep (layer-by-layer wavefronts), both from a truncated
+upwind start, against the oracle's 3-D Fourier form.
 Bar: relative L2 <= 1e-12 over all populations."""
 import dataclasses
 

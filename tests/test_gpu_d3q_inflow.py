@@ -1,8 +1,8 @@
 """GPU parity of the 3-D lattices (D3Q15, D3Q19, D3Q27) on meshes with inflow axes (eq. (2.6),
 fictitious cells of eq. (3.8)): axis populations through the line passes, edge populations
-through the plane-wise diagonal sweep and corner populations through the box sweep; tiles
-and boxes whose region reaches an inflow face start there from the boundary data, the
-others from their truncated upwind start.  Against the oracle's sparse LU of the assembled
+through the plane-wise diagonal sweep and corner populations through the hyperplane sweep
+(the default; boxes where a launch shape forces them); a region that reaches an inflow face
+starts there from the boundary data, the others from their truncated upwind start.  Against the oracle's sparse LU of the assembled
 system with the same boundary data.  Bar: relative L2 <= 1e-12."""
 import dataclasses
 
