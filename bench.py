@@ -128,12 +128,14 @@ def collision_flops(kind, dim):
 # Lines per block (the first number of the line-pass launch shape, which sets how much of a
 # block's lines stays in L2 between the operations of a pass) or None for the diagonal /
 # corner passes (shape chosen by the host planner).  Only kernels that have not changed
-# since their capture are listed; the others report null.  The Euler D3Q6 figure was
-# captured at 192^3 points (1.7 GB state, larger than L2) and scaled by the 8 times more
-# points of a 384^3 launch (profiles/pass_kernel_fp64_euler_d3q6_384cube.md).
-TRAFFIC = {("shallow_water_d2q4_64x64x8x8_d3", 1, "fp64", 8): 1793.12e6,
-           ("isothermal_d2q9_64x64x8x8_d3", 3, "fp64", None): 279.41e6,
-           ("euler_d3q6_32c3x4c3_d2", 1, "fp64", 8): 8 * 4895.31e6}
+# since their capture are listed; the others report null.  The last-axis passes are those of
+# the schedule with the collision after the composed pair of half steps ([T T, C]).  The
+# Euler D3Q6 figure was captured at 192^3 points (1.7 GB state, larger than L2) and scaled by
+# the 8 times more points of a 384^3 launch (profiles/pass_kernel_fp64_euler_d3q6_384cube.md);
+# the shallow-water one at the workload's own size.
+TRAFFIC = {("shallow_water_d2q4_64x64x8x8_d3", 1, "fp64", 16): 1192.8e6,
+           ("isothermal_d2q9_64x64x8x8_d3", 3, "fp64", None): 279.29e6,
+           ("euler_d3q6_32c3x4c3_d2", 1, "fp64", 16): 8 * 4385.8e6}
 
 SOURCES = {"gravity": dict(gravity=(0.0, -1.0)),
            "penalization": dict(K_s=300.0, kappa=40.0, x_c=(0.25, 0.5), w_s=(1.0, 0.0, 0.0)),

@@ -283,15 +283,22 @@ int pdg_set_source(pdg_ctx* ctx, const pdg_source_desc* desc);
  * the tiles that reach the inflow face start there, from the exact boundary data.
  * D3Q15 / D3Q27 corner velocities v = lambda (s_x, s_y, s_z): the same form with three
  * upwind faces, B = I + theta (nu_x I(x)I(x)K + nu_y I(x)K(x)I + nu_z K(x)I(x)I) on the
- * n^3 nodes of a cell; boxes of cells are swept layer by layer along z, each layer as a
- * 2-D wavefront, every box starting W cells upwind along all three axes (bound 2^-57 per
- * upwind boundary; W <= 64, otherwise PDG_ERR_UNSUPPORTED).  The first step with a new
- * (dt, scheme) plan copies the corner coefficients to the device (a few tens of KB, in
- * memory allocated by pdg_set_model).  The corner pass keeps the +z faces of each box in
- * a device scratch buffer (n^2 doubles per cell of a box's region, tens of MB at 384^3
- * points); the first step that needs a larger one allocates it with cudaMalloc (after a
- * cudaFree of the old one, which waits for the device), so issue a first step before
- * any stream capture.
+ * n^3 nodes of a cell.  By default each corner population sweeps the whole mesh, from a
+ * start W cells upwind along every periodic axis, cell hyperplane by cell hyperplane
+ * (PDG_OPT_CORNER_SWEEP); otherwise boxes of cells are swept layer by layer along z, each
+ * layer as a 2-D wavefront, every box starting W cells upwind along all three axes (bound
+ * 2^-57 per upwind boundary; W <= 64, otherwise PDG_ERR_UNSUPPORTED).  The first step with
+ * a new (dt, scheme) plan copies the corner coefficients to the device (a few tens of KB,
+ * in memory allocated by pdg_set_model).  The corner pass keeps the faces passed between
+ * cells in a device scratch buffer (hyperplanes: 6 slots of n^2 doubles, rounded up to an
+ * even count, per (layer, row) of each population's region, about 80 MB at 384^3 points;
+ * boxes: the +z faces of each box's region); the first step that needs a larger one
+ * allocates it with cudaMalloc (after a cudaFree of the old one, which waits for the
+ * device), so issue a first step before any stream capture.
+ * Pass order (M2): transports of different axes act on different populations and commute,
+ * so between two collisions the trailing T(dt/2) of one step and the leading T(dt/2) of the
+ * next run in one pass per axis (composed, PDG_OPT_COMPOSE_TT), the collision at the end of
+ * the last axis' pass; each population sees the order of the definition.
  * Host memory: the call first builds its pass list on the host, about 2.3 KB per pass
  * (D passes per step for M2 and the collapsed form, about 2D for M2^kin and 6D for M4^kin,
  * plus one per diagonal sub-step of the lattices); a list that cannot be allocated fails
@@ -493,8 +500,10 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
  *     operations in the same order as the streaming kernel (the segment closure may round
  *     differently when the launch shape differs).  Passes whose staged lines do not fit
  *     run the streaming kernel.
- *   PDG_OPT_COLLISION_AXIS (default -1): the axis whose line pass carries the collision,
- *     T(dt/2) C T(dt/2); -1 = the last axis.  Transports along different axes commute, so
+ *   PDG_OPT_COLLISION_AXIS (default -1): the axis whose line pass carries the collision
+ *     (M2: the pair of half steps between two collisions, composed, then the collision,
+ *     T(dt/2) T(dt/2) C; M2^kin: T C T as in Section 3.2); -1 = the last axis.  Transports
+ *     along different axes commute, so
  *     any axis gives the same scheme (results equal up to rounding); axis 0 has
  *     unit-stride lines, which the line-resident kernel stages most cheaply.  Lattice
  *     models keep the last axis (other values: PDG_ERR_UNSUPPORTED).

@@ -2,13 +2,17 @@
 //
 // Schedule.  M2(dt) = T(dt/2) C(dt) T(dt/2) (Section 3.2) with T the product of
 // the per-population transports; transports along different axes act on
-// different populations, so they commute exactly.  With L the axis whose pass carries
-// the collision (the last axis, or the one PDG_OPT_COLLISION_AXIS names), nsteps steps
-// are issued as
-//   for a != L: pass_a [T(dt/2)]
-//   repeat nsteps:  pass_L [T(dt/2), C, T(dt/2)]
-//                   for a != L: pass_a [T(dt/2), T(dt/2)]   (last step: [T(dt/2)])
-// which applies to every population exactly the sequence of the naive order.
+// different populations, so they commute exactly.  Between two collisions every
+// population therefore sees its axis' trailing T(dt/2) of one step and leading T(dt/2) of
+// the next, in that order, whatever the order of the axes.  With L the axis whose pass
+// carries the collision (the last axis, or the one PDG_OPT_COLLISION_AXIS names), nsteps
+// steps are issued as
+//   for a != L: pass_a [T(dt/2)];   pass_L [T(dt/2), C]
+//   repeat nsteps - 1:  for a != L: pass_a [T(dt/2), T(dt/2)];   pass_L [T(dt/2), T(dt/2), C]
+//   for a != L: pass_a [T(dt/2)];   pass_L [T(dt/2)]
+// which applies to every population exactly the sequence of the naive order, and puts
+// every pair of half steps of one axis into one pass (the issue composes it into one
+// T T sweep), the collision at the end of the last axis' pass.
 // The collapsed scheme of Section 5.1 merges interior half steps into T(dt).
 #include <cuda_runtime.h>
 
@@ -98,7 +102,7 @@ int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSp
   }
   const int T = PDG_OP_T, C = PDG_OP_C;
   const int z1[1] = {0}, z2[2] = {0, 0}, z3[3] = {0, 0, 0};
-  const int o1[1] = {T}, o2[2] = {T, T}, o3[3] = {T, C, T};
+  const int o1[1] = {T}, o2[2] = {T, T};
   if (c->scheme == PDG_SCHEME_M2KIN) {
     // T(dt/4) C T(dt/2) C T(dt/4) per step.  The collisions split the run into the
     // transport segments seg_0 = T(q), then alternately T(h) and T(q) T(q) (the trailing
@@ -142,13 +146,18 @@ int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSp
     return PDG_OK;
   }
   if (c->scheme == PDG_SCHEME_M2) {
+    const int otc[2] = {T, C}, ottc[3] = {T, T, C};
     for (int a = 0; a < D; ++a)
       if (a != L) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
-    for (int s = 0; s < nsteps; ++s) {
-      out.push_back(spec(L, 3, o3, z3, &half[L], 1));
+    out.push_back(spec(L, 2, otc, z2, &half[L], 1));
+    for (int s = 1; s < nsteps; ++s) {
       for (int a = 0; a < D; ++a)
-        if (a != L) out.push_back(spec(a, s < nsteps - 1 ? 2 : 1, o2, z2, &half[a], 1));
+        if (a != L) out.push_back(spec(a, 2, o2, z2, &half[a], 1));
+      out.push_back(spec(L, 3, ottc, z3, &half[L], 1));
     }
+    for (int a = 0; a < D; ++a)
+      if (a != L) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
+    out.push_back(spec(L, 1, o1, z1, &half[L], 1));
   } else {
     for (int a = 0; a < D; ++a)
       if (a != L) out.push_back(spec(a, 1, o1, z1, &half[a], 1));

@@ -58,8 +58,10 @@ MUTATIONS = [
     ("composed_window_ignores_coupling", "if (bK <= tol && (double)K * g * bk <= tol) return K;",
      "if (bK <= tol) return K;"),
     # pass schedule of the compositions (Section 3.2, Section 5.1)
-    ("m2_next_leading_half_step_dropped", "out.push_back(spec(a, s < nsteps - 1 ? 2 : 1, o2, z2, &half[a], 1));",
-     "out.push_back(spec(a, 1, o2, z2, &half[a], 1));", API),
+    ("m2_next_leading_half_step_dropped", "if (a != L) out.push_back(spec(a, 2, o2, z2, &half[a], 1));",
+     "if (a != L) out.push_back(spec(a, 1, o2, z2, &half[a], 1));", API),
+    ("m2_collision_dropped_from_last_axis_pass", "out.push_back(spec(L, 3, ottc, z3, &half[L], 1));",
+     "out.push_back(spec(L, 2, ottc, z3, &half[L], 1));", API),
     ("collapsed_interior_step_half", "const int ops[2] = {T, C}, ci[2] = {s == 0 ? 0 : 1, 0};",
      "const int ops[2] = {T, C}, ci[2] = {0, 0};", API),
     ("m2kin_segment_coefficients_swapped", "auto seg_ci = [&](int j) { return (j % 2 == 1) ? 1 : 0; };",
