@@ -515,7 +515,9 @@ int pdg_set_launch(pdg_ctx* ctx, int kind, int lpb, int nseg, int ngroup);
  *     hyperplane (a wait that runs out is reported as PDG_ERR_TIMEOUT at the next
  *     synchronising call); 0 = boxes: one block per box of output cells with its own
  *     truncated start, no block waiting on another.  Forced box shapes (pdg_set_launch,
- *     kind 6) and the tensor-core forms use boxes.  Results agree to rounding.
+ *     kind 6) and the tensor-core forms at degree 3 use boxes; the tensor-core forms at
+ *     degree <= 2 sweep hyperplanes too, one batch of 128 cells per product.  Results
+ *     agree to rounding.
  * Errors: PDG_ERR_ARG (unknown option, axis out of range), PDG_ERR_UNSUPPORTED.
  */
 enum {
