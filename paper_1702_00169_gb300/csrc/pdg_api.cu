@@ -347,15 +347,14 @@ int pdg_step(pdg_ctx* c, double dt, int nsteps) try {
     PDG_CUDA(c, cudaStreamWaitEvent(c->stream, c->g_out, 0));
     return PDG_OK;
   }
-  std::vector<PdgPassSpec> sched;
-  if (int r = build_schedule_checked(c, dt, nsteps, sched)) return r;
   if (graph) {
+    std::vector<PdgPassSpec> sched;
+    if (int r = build_schedule_checked(c, dt, nsteps, sched)) return r;
     if (int r = capture_steps(c, dt, nsteps, sched)) return r;
     return pdg_step(c, dt, nsteps);   // replay
   }
-  for (const auto& sp : sched)
-    if (int r = issue_pass(c, sp)) return r;
-  return PDG_OK;
+  // each pass is issued as it is generated: no pass list is held on the host
+  return emit_schedule(c, dt, nsteps, [c](const PdgPassSpec& sp) { return issue_pass(c, sp); });
 } catch (...) {
   return pdgapi::abi_exception(c ? &c->err : nullptr);
 }

@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <cstddef>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -180,8 +181,11 @@ int stable_window(const PdgCoef& C);
 int plan_line_coef(const pdg_ctx* c, int axis, double delta, PdgCoef* C);
 int pass_kind(const PdgPassSpec& sp);
 PdgPassSpec spec(int axis, int nops, const int* ops, const int* ci, const PdgCoef* cs, int ncs);
-int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out);
-int build_schedule_one(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out);
+// Receives the passes of a schedule in order; a non-zero return (a PDG_ERR_*) stops it.
+using PassSink = std::function<int(const PdgPassSpec&)>;
+int emit_line_schedule(pdg_ctx* c, double dt, int nsteps, const PassSink& sink);
+int emit_schedule_one(pdg_ctx* c, double dt, int nsteps, const PassSink& sink);
+int emit_schedule(pdg_ctx* c, double dt, int nsteps, const PassSink& sink);
 int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out);
 int build_schedule_checked(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out);
 void choose_shape(const int* ov, int max_threads, int nlines, int ncell, int ntf, int W, int* lpb, int* nseg,

@@ -14,6 +14,8 @@
 // every pair of half steps of one axis into one pass (the issue composes it into one
 // T T sweep), the collision at the end of the last axis' pass.
 // The collapsed scheme of Section 5.1 merges interior half steps into T(dt).
+// The passes are generated one at a time into a sink: pdg_step issues each as it comes, so
+// its host memory does not grow with the step count; the other callers collect them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,6 +23,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -83,12 +86,16 @@ PdgPassSpec spec(int axis, int nops, const int* ops, const int* ci, const PdgCoe
   return sp;
 }
 
-// The line passes of nsteps palindromic steps (see the schedule at the top of this file).
-int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
-  out.clear();
+// The line passes of nsteps palindromic steps (see the schedule at the top of this file),
+// in order, into `sink`.  Every argument check comes before the first pass; after a sink
+// error no further pass reaches it and that error is returned.
+int emit_line_schedule(pdg_ctx* c, double dt, int nsteps, const PassSink& sink) {
   if (nsteps <= 0) return PDG_OK;
   const int D = c->dim, L = (c->caxis >= 0 && c->caxis < D) ? c->caxis : D - 1;
-  out.reserve((2 * (size_t)nsteps + 1) * (size_t)D);   // at least the passes of every scheme
+  int rc = PDG_OK;
+  auto put = [&](const PdgPassSpec& sp) {
+    if (rc == PDG_OK) rc = sink(sp);
+  };
   PdgCoef half[3], full[3];
   for (int a = 0; a < D; ++a) {
     if (plan_line_coef(c, a, 0.5 * dt, &half[a])) return fail(c, PDG_ERR_ARG, "singular transport step");
@@ -119,58 +126,58 @@ int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSp
       if (!c->periodic[a] && (t0.rev || t1.rev))
         return fail(c, PDG_ERR_UNSUPPORTED, "time steps with |beta| > 1 on an inflow (non-periodic) axis");
     }
-    const int nseg = 2 * nsteps + 1;
+    const long long nseg = 2LL * nsteps + 1;
     // segment j: number of sub-steps and their coefficient index (0 = quarter, 1 = half)
-    auto seg_n = [&](int j) { return (j == 0 || j == nseg - 1) ? 1 : ((j % 2 == 1) ? 1 : 2); };
-    auto seg_ci = [&](int j) { return (j % 2 == 1) ? 1 : 0; };
-    auto other_axes = [&](int j) {
+    auto seg_n = [&](long long j) { return (j == 0 || j == nseg - 1) ? 1 : ((j % 2 == 1) ? 1 : 2); };
+    auto seg_ci = [&](long long j) { return (j % 2 == 1) ? 1 : 0; };
+    auto other_axes = [&](long long j) {
       for (int a = 0; a < D; ++a) {
         if (a == L) continue;
         PdgCoef cs[2] = {qc[a], hc[a]};
         const int ops[2] = {T, T}, ci[2] = {seg_ci(j), seg_ci(j)};
-        out.push_back(spec(a, seg_n(j), ops, ci, cs, 2));
+        put(spec(a, seg_n(j), ops, ci, cs, 2));
       }
     };
     PdgCoef csL[2] = {qc[L], hc[L]};
     other_axes(0);
     {
       const int ops[3] = {T, C, T}, ci[3] = {seg_ci(0), 0, seg_ci(1)};
-      out.push_back(spec(L, 3, ops, ci, csL, 2));
+      put(spec(L, 3, ops, ci, csL, 2));
     }
-    for (int j = 1; j < nseg - 1; ++j) {
+    for (long long j = 1; j < nseg - 1 && rc == PDG_OK; ++j) {
       other_axes(j);
       int ops[3] = {C, T, T}, ci[3] = {0, seg_ci(j + 1), seg_ci(j + 1)};
-      out.push_back(spec(L, 1 + seg_n(j + 1), ops, ci, csL, 2));
+      put(spec(L, 1 + seg_n(j + 1), ops, ci, csL, 2));
     }
     other_axes(nseg - 1);
-    return PDG_OK;
+    return rc;
   }
   if (c->scheme == PDG_SCHEME_M2) {
     const int otc[2] = {T, C}, ottc[3] = {T, T, C};
     for (int a = 0; a < D; ++a)
-      if (a != L) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
-    out.push_back(spec(L, 2, otc, z2, &half[L], 1));
-    for (int s = 1; s < nsteps; ++s) {
+      if (a != L) put(spec(a, 1, o1, z1, &half[a], 1));
+    put(spec(L, 2, otc, z2, &half[L], 1));
+    for (int s = 1; s < nsteps && rc == PDG_OK; ++s) {
       for (int a = 0; a < D; ++a)
-        if (a != L) out.push_back(spec(a, 2, o2, z2, &half[a], 1));
-      out.push_back(spec(L, 3, ottc, z3, &half[L], 1));
+        if (a != L) put(spec(a, 2, o2, z2, &half[a], 1));
+      put(spec(L, 3, ottc, z3, &half[L], 1));
     }
     for (int a = 0; a < D; ++a)
-      if (a != L) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
-    out.push_back(spec(L, 1, o1, z1, &half[L], 1));
+      if (a != L) put(spec(a, 1, o1, z1, &half[a], 1));
+    put(spec(L, 1, o1, z1, &half[L], 1));
   } else {
     for (int a = 0; a < D; ++a)
-      if (a != L) out.push_back(spec(a, 1, o1, z1, &half[a], 1));
-    for (int s = 0; s < nsteps; ++s) {
+      if (a != L) put(spec(a, 1, o1, z1, &half[a], 1));
+    for (int s = 0; s < nsteps && rc == PDG_OK; ++s) {
       PdgCoef cs[2] = {half[L], full[L]};
       const int ops[2] = {T, C}, ci[2] = {s == 0 ? 0 : 1, 0};
-      out.push_back(spec(L, 2, ops, ci, cs, 2));
+      put(spec(L, 2, ops, ci, cs, 2));
       for (int a = 0; a < D; ++a)
-        if (a != L) out.push_back(spec(a, 1, o1, z1, s < nsteps - 1 ? &full[a] : &half[a], 1));
+        if (a != L) put(spec(a, 1, o1, z1, s < nsteps - 1 ? &full[a] : &half[a], 1));
     }
-    out.push_back(spec(L, 1, o1, z1, &half[L], 1));
+    put(spec(L, 1, o1, z1, &half[L], 1));
   }
-  return PDG_OK;
+  return rc;
 }
 
 // The full pass list.  D2Q9 adds the diagonal transports: the sub-steps between two
@@ -178,64 +185,72 @@ int build_line_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSp
 // just before the line pass that holds the next collision (transports of different
 // populations commute); each diagonal pass swaps the slot set of populations 5-8, the
 // collision reads them where they are, and a final copy returns them to slots 5-8.
-int build_schedule_one(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
-  if (int r = build_line_schedule(c, dt, nsteps, out)) return r;
+int emit_schedule_one(pdg_ctx* c, double dt, int nsteps, const PassSink& sink) {
   Lattice Lat;
-  if (!lattice_of(c->model.kind, &Lat) || nsteps <= 0) return PDG_OK;
+  if (!lattice_of(c->model.kind, &Lat) || nsteps <= 0) return emit_line_schedule(c, dt, nsteps, sink);
   if (!(dt > 0.0)) return fail(c, PDG_ERR_UNSUPPORTED, "diagonal transport needs dt > 0");
   if (c->src.flags && c->scheme == PDG_SCHEME_M2KIN)
     return fail(c, PDG_ERR_UNSUPPORTED, "sources are defined for M2 and M2_collapsed");
-  // diagonal sub-steps of each transport segment, in order
-  std::vector<std::vector<double>> seg;
+  // diagonal sub-steps of transport segment j (the segments between the collisions, in
+  // order): nseg segments, one more than the collisions
   const double h = 0.5 * dt, q = 0.25 * dt;
-  if (c->scheme == PDG_SCHEME_M2) {
-    seg.push_back({h});
-    for (int s = 1; s < nsteps; ++s) seg.push_back({h, h});
-    seg.push_back({h});
-  } else if (c->scheme == PDG_SCHEME_M2_COLLAPSED) {
-    seg.push_back({h});
-    for (int s = 1; s < nsteps; ++s) seg.push_back({dt});
-    seg.push_back({h});
-  } else {
-    seg.push_back({q});
-    for (int s = 0; s < nsteps; ++s) {
-      seg.push_back({h});
-      if (s < nsteps - 1) seg.push_back({q, q});
+  const int scheme = c->scheme;
+  const long long nseg = scheme == PDG_SCHEME_M2KIN ? 2LL * nsteps + 1 : (long long)nsteps + 1;
+  auto seg = [&](long long j, double* dl) -> int {
+    const bool end = j == 0 || j == nseg - 1;
+    if (scheme == PDG_SCHEME_M2) {
+      dl[0] = dl[1] = h;
+      return end ? 1 : 2;
     }
-    seg.push_back({q});
-  }
-  std::vector<PdgPassSpec> res;
-  res.reserve(out.size() + 3 * seg.size() + 1);
+    if (scheme == PDG_SCHEME_M2_COLLAPSED) {
+      dl[0] = end ? h : dt;
+      return 1;
+    }
+    if (end || j % 2 == 0) {       // M2^kin: T(dt/4) at the ends, T(dt/4) T(dt/4) between steps
+      dl[0] = dl[1] = q;
+      return end ? 1 : 2;
+    }
+    dl[0] = h;                     // the middle of a step
+    return 1;
+  };
   int slot = Lat.diag;
-  size_t ci = 0;
+  long long ci = 0;
   auto diag = [&](double delta) {
     PdgPassSpec d;
     std::memset(&d, 0, sizeof(d));
     d.axis = -1;
     d.ddelta = delta;
     d.dslot_in = slot;
-    res.push_back(d);
     slot = (slot == Lat.diag) ? Lat.scratch : Lat.diag;
+    return sink(d);
   };
-  for (auto sp : out) {
+  auto segment = [&](long long j) {
+    double dl[2];
+    const int k = seg(j, dl);
+    for (int i = 0; i < k; ++i)
+      if (int r = diag(dl[i])) return r;
+    return (int)PDG_OK;
+  };
+  int r = emit_line_schedule(c, dt, nsteps, [&](const PdgPassSpec& line) -> int {
+    PdgPassSpec sp = line;
     if (pass_kind(sp)) {
-      if (ci >= seg.size()) return fail(c, PDG_ERR_ARG, "internal: schedule segments");
-      for (double dl : seg[ci]) diag(dl);
+      if (ci >= nseg) return fail(c, PDG_ERR_ARG, "internal: schedule segments");
+      if (int e = segment(ci)) return e;
       ++ci;
       sp.dslot = slot;
       sp.sdelta = c->src.flags ? 0.5 * dt : 0.0;   // S(dt/2) C(dt) S(dt/2)
     }
-    res.push_back(sp);
-  }
-  if (ci + 1 != seg.size()) return fail(c, PDG_ERR_ARG, "internal: schedule segments");
-  for (double dl : seg[ci]) diag(dl);
+    return sink(sp);
+  });
+  if (r) return r;
+  if (ci + 1 != nseg) return fail(c, PDG_ERR_ARG, "internal: schedule segments");
+  if (int e = segment(ci)) return e;
   if (slot != Lat.diag) {
     PdgPassSpec cp;
     std::memset(&cp, 0, sizeof(cp));
     cp.axis = -2;   // copy slots 9-12 back to 5-8
-    res.push_back(cp);
+    return sink(cp);
   }
-  out.swap(res);
   return PDG_OK;
 }
 
@@ -243,23 +258,24 @@ int build_schedule_one(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpe
 // triple jump M2^kin(g1 dt) M2^kin(g2 dt) M2^kin(g1 dt) per step (Section 3.2: palindromic
 // compositions of M2^kin; H. Yoshida, Phys. Lett. A 150 (1990)), g1 = 1/(2 - 2^(1/3)),
 // g2 = 1 - 2 g1 < 0: three M2^kin schedules per step, the middle one backwards in time.
-int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
-  if (c->scheme != PDG_SCHEME_M4KIN) return build_schedule_one(c, dt, nsteps, out);
+// Its steps are all alike, so one step is generated first without a sink to check the
+// arguments of all three sub-steps before any pass is emitted.
+int emit_schedule(pdg_ctx* c, double dt, int nsteps, const PassSink& sink) {
+  if (c->scheme != PDG_SCHEME_M4KIN) return emit_schedule_one(c, dt, nsteps, sink);
   Lattice L;
   if (lattice_of(c->model.kind, &L))
     return fail(c, PDG_ERR_UNSUPPORTED, "M4^kin has a backward sub-step: not available for diagonal velocities");
   if (c->src.flags) return fail(c, PDG_ERR_UNSUPPORTED, "sources are defined for M2 and M2_collapsed");
   const double g1 = 1.0 / (2.0 - std::cbrt(2.0)), g2 = 1.0 - 2.0 * g1;
-  out.clear();
-  std::vector<PdgPassSpec> part;
+  const PassSink none = [](const PdgPassSpec&) { return (int)PDG_OK; };
   c->scheme = PDG_SCHEME_M2KIN;
   int r = PDG_OK;
   try {
-    out.reserve(3 * (size_t)nsteps * 3 * (size_t)c->dim);
+    for (double g : {g1, g2, g1})
+      if (nsteps > 0 && r == PDG_OK) r = emit_schedule_one(c, g * dt, 1, none);
     for (int s = 0; s < nsteps && r == PDG_OK; ++s)
       for (double g : {g1, g2, g1}) {
-        if ((r = build_schedule_one(c, g * dt, 1, part)) != PDG_OK) break;
-        out.insert(out.end(), part.begin(), part.end());
+        if ((r = emit_schedule_one(c, g * dt, 1, sink)) != PDG_OK) break;
       }
   } catch (...) {
     c->scheme = PDG_SCHEME_M4KIN;
@@ -267,6 +283,15 @@ int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& 
   }
   c->scheme = PDG_SCHEME_M4KIN;
   return r;
+}
+
+int build_schedule(pdg_ctx* c, double dt, int nsteps, std::vector<PdgPassSpec>& out) {
+  out.clear();
+  if (nsteps > 0) out.reserve((2 * (size_t)nsteps + 1) * (size_t)c->dim);   // at least the passes of every scheme
+  return emit_schedule(c, dt, nsteps, [&](const PdgPassSpec& sp) {
+    out.push_back(sp);
+    return (int)PDG_OK;
+  });
 }
 
 // build_schedule for the C entry points: the pass list lives in host memory (about 2.3 KB

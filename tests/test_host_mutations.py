@@ -58,18 +58,17 @@ MUTATIONS = [
     ("composed_window_ignores_coupling", "if (bK <= tol && (double)K * g * bk <= tol) return K;",
      "if (bK <= tol) return K;"),
     # pass schedule of the compositions (Section 3.2, Section 5.1)
-    ("m2_next_leading_half_step_dropped", "if (a != L) out.push_back(spec(a, 2, o2, z2, &half[a], 1));",
-     "if (a != L) out.push_back(spec(a, 1, o2, z2, &half[a], 1));", API),
-    ("m2_collision_dropped_from_last_axis_pass", "out.push_back(spec(L, 3, ottc, z3, &half[L], 1));",
-     "out.push_back(spec(L, 2, ottc, z3, &half[L], 1));", API),
+    ("m2_next_leading_half_step_dropped", "if (a != L) put(spec(a, 2, o2, z2, &half[a], 1));",
+     "if (a != L) put(spec(a, 1, o2, z2, &half[a], 1));", API),
+    ("m2_collision_dropped_from_last_axis_pass", "put(spec(L, 3, ottc, z3, &half[L], 1));",
+     "put(spec(L, 2, ottc, z3, &half[L], 1));", API),
     ("collapsed_interior_step_half", "const int ops[2] = {T, C}, ci[2] = {s == 0 ? 0 : 1, 0};",
      "const int ops[2] = {T, C}, ci[2] = {0, 0};", API),
-    ("m2kin_segment_coefficients_swapped", "auto seg_ci = [&](int j) { return (j % 2 == 1) ? 1 : 0; };",
-     "auto seg_ci = [&](int j) { return (j % 2 == 0) ? 1 : 0; };", API),
+    ("m2kin_segment_coefficients_swapped", "auto seg_ci = [&](long long j) { return (j % 2 == 1) ? 1 : 0; };",
+     "auto seg_ci = [&](long long j) { return (j % 2 == 0) ? 1 : 0; };", API),
     ("m2kin_first_pass_trailing_quarter", "ci[3] = {seg_ci(0), 0, seg_ci(1)};", "ci[3] = {seg_ci(0), 0, seg_ci(0)};", API),
     ("m4kin_not_palindromic", "for (double g : {g1, g2, g1}) {", "for (double g : {g1, g1, g2}) {", API),
-    ("diagonal_collapsed_interior_half", "for (int s = 1; s < nsteps; ++s) seg.push_back({dt});",
-     "for (int s = 1; s < nsteps; ++s) seg.push_back({h});", API),
+    ("diagonal_collapsed_interior_half", "dl[0] = end ? h : dt;", "dl[0] = h;", API),
     ("diagonal_home_copy_condition", "if (slot != Lat.diag) {", "if (slot == Lat.diag) {", API),
     ("source_substep_full", "sp.sdelta = c->src.flags ? 0.5 * dt : 0.0;", "sp.sdelta = c->src.flags ? dt : 0.0;", API),
 ]
