@@ -18,7 +18,8 @@ Output: ONE JSON line (rank 0).
   mixed       the double-float form (FP32-pair state and arithmetic), timed the same way,
               with its error against the FP64 run;
   e2e         the same metric through the C ABI with host buffers (pdg_set_w from pinned
-              host memory, pdg_step, pdg_get_w to host) inside the timed region;
+              host memory, pdg_step, pdg_get_w to host) inside the timed region; the
+              median of three such runs;
   cpu_baseline  the FP64 oracle on every host core (one replica of a bounded sample per
               core), measured, not scaled;
   batched / serving  the batched form (256 shallow-water meshes) and the serving form
@@ -948,20 +949,26 @@ def main():
                 s2.set_launch(kind, *s_shape[kind])
         s2.step(cfg.dt, 2)
         s2.get_w(w_out)
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s2.set_w(w_host)
-        s2.step(cfg.dt, args.steps)
-        s2.get_w(w_out)
-        t1 = time.perf_counter()
-        el_max, units_e2e = aggregate_ranks(t1 - t0, dofs * args.steps)
+        # three timed runs, the median reported: a host-to-device copy from pinned memory
+        # occasionally runs at a fraction of its usual rate on a shared host
+        runs = []
+        for _ in range(3):
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2.set_w(w_host)
+            s2.step(cfg.dt, args.steps)
+            s2.get_w(w_out)
+            t1 = time.perf_counter()
+            runs.append(t1 - t0)
+        el_max, units_e2e = aggregate_ranks(sorted(runs)[1], dofs * args.steps)
         s2.close()
         nbytes = w0.nbytes
         e2e = {"value": units_e2e / el_max, "unit": UNIT,
                "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+               "runs_s": [round(r, 4) for r in runs],
                "note": "one pdg_set_w (pinned host) + pdg_step(K) + pdg_get_w (pinned host) per timed run; "
-                       "bytes amortised over K"}
+                       "bytes amortised over K; median of three runs"}
         del w_host, w_out
     if s is not None:
         s.close()
