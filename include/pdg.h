@@ -300,11 +300,13 @@ int pdg_set_source(pdg_ctx* ctx, const pdg_source_desc* desc);
  * next run in one pass per axis (composed, PDG_OPT_COMPOSE_TT), the collision at the end of
  * the last axis' pass; each population sees the order of the definition.
  * Host memory: the passes are generated and issued one at a time, so the host memory of the
- * call does not depend on nsteps; every argument check comes before the first pass is
- * issued.  With PDG_OPT_GRAPH the call first builds its pass list for the capture, about
- * 2.3 KB per pass (D passes per step for M2 and the collapsed form, about 2D for M2^kin and
- * 6D for M4^kin, plus one per diagonal sub-step of the lattices); a list that cannot be
- * allocated fails the call with PDG_ERR_OOM before anything is issued.
+ * call does not depend on nsteps.  The schedule's own checks (time step, scheme, model) come
+ * before the first pass is issued; a pass that cannot be planned (PDG_ERR_UNSUPPORTED) ends
+ * the call after the passes before it.  With PDG_OPT_GRAPH the call first builds its pass
+ * list for the capture, about 2.3 KB per pass (D passes per step for M2 and the collapsed
+ * form, about 2D for M2^kin and 6D for M4^kin, plus one per diagonal sub-step of the
+ * lattices); a list that cannot be allocated fails the call with PDG_ERR_OOM before anything
+ * is issued.
  * Errors: PDG_ERR_STATE (no state), PDG_ERR_ARG (nsteps < 0, non-finite dt), PDG_ERR_OOM,
  *         PDG_ERR_CUDA, PDG_ERR_UNSUPPORTED.
  */
