@@ -283,3 +283,42 @@ def test_collision_axis_and_resident_options(pdg):
     s.set_launch(8, 0, 0, 0)
     assert s.get_launch(8) == (0, 0, 0)
     s.close()
+
+
+@pytest.mark.parametrize("model", ["euler", "isothermal_d2q9", "isothermal_d3q19"])
+@pytest.mark.parametrize("scheme", ["M2", "M2_collapsed", "M2_kin", "M4_kin"])
+def test_long_runs_repeat_one_step_pattern(pdg, model, scheme):
+    """Long runs: the pass lists of 200 and 202 steps share their first and last passes, and
+    their middle repeats with the passes of two steps (two, because the diagonal sub-steps
+    alternate the slot set of the D2Q9 / D3Q19 diagonals).  The class sequences of the
+    200-step list still follow the composition (the diagonal class included), and the D2Q9
+    slots stay consistent."""
+    dim = 2 if model == "isothermal_d2q9" else 3
+    lattice = model.startswith("isothermal")
+    if lattice and scheme == "M4_kin":
+        pytest.skip("M4^kin is refused for diagonal velocities (test_schedule_refusals_and_arguments)")
+    s = pdg.Solver(dim, (2,) * dim, (2,) * dim, 2, lengths=(1.0, 0.7, 1.3)[:dim])
+    s.set_model(model, 1.0 if lattice else 5.0, scheme=scheme)
+    dt, n = 0.01, 200
+    a, b = s.schedule(dt, n), s.schedule(dt, n + 2)
+    k = len(b) - len(a)
+    assert k > 0 and len(a) > 8 * k
+    edge = len(a) // 4
+    assert b[:edge] == a[:edge] and b[-edge:] == a[-edge:]
+    for i in range(2 * k, len(a) - 2 * k):
+        assert a[i] == a[i + k], i
+    for i in range(edge, len(b) - edge - k):
+        assert b[i] == b[i + k], i
+    ev = classes_from_schedule(a, dim, lattice)
+    info = s.info()
+    exp = expected(scheme, dt, n)
+    for ax in range(dim):
+        if not lattice:
+            check_line_class(pdg, ev[ax], exp, 2, 5.0, info.h[ax], 0.5)
+        else:
+            assert [e == "C" for e in ev[ax]] == [e == "C" for e in exp]
+    if lattice:
+        check_diag_class(ev["diag"], exp)
+    if model == "isothermal_d2q9":
+        check_slots(a)
+    s.close()
