@@ -17,6 +17,22 @@
 
 using namespace pdgapi;
 
+namespace {
+// pdg_set_w / pdg_get_w with host buffers: a state of at least kXferChunks * kXferChunkMin
+// points moves in kXferChunks chunks of points, the copy of each chunk overlapping the
+// equilibrium or moment kernel of its neighbour (smaller states: one copy, one kernel).
+constexpr int kXferChunks = 8;
+constexpr long long kXferChunkMin = 1LL << 19;
+static_assert(kXferChunks + 1 <= (int)(sizeof(pdg_ctx::xev) / sizeof(cudaEvent_t)), "one event per chunk and one more");
+
+int ensure_xfer(pdg_ctx* c) {
+  if (!c->xstream) PDG_CUDA(c, cudaStreamCreateWithFlags(&c->xstream, cudaStreamNonBlocking));
+  for (auto& e : c->xev)
+    if (!e) PDG_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return PDG_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char* pdg_status_string(int s) {
@@ -169,6 +185,30 @@ int pdg_set_w(pdg_ctx* c, const double* w, size_t len, int on_device) try {
   if (int r = ensure_state(c)) return r;
   if (int r = ensure_inflow(c)) return r;
   // w_k goes to field slot k; the kernel reads all w_k of a point before writing.
+  if (!on_device && c->npoints >= kXferChunkMin * kXferChunks) {
+    // large host state: chunk j's copies on the private stream, its equilibrium kernel on the
+    // context stream after them, so that the kernel of chunk j runs during the copies of j + 1
+    if (int r = ensure_xfer(c)) return r;
+    const int m = c->model.m;
+    const long long P = c->npoints;
+    PDG_CUDA(c, cudaEventRecord(c->xev[kXferChunks], c->stream));   // earlier work on f first
+    PDG_CUDA(c, cudaStreamWaitEvent(c->xstream, c->xev[kXferChunks], 0));
+    // (a copy from pageable memory may return only once staged: each kernel is issued right
+    // after its chunk's copies, before the next chunk's)
+    for (int j = 0; j < kXferChunks; ++j) {
+      const long long p0 = P * j / kXferChunks, p1 = P * (j + 1) / kXferChunks;
+      for (int k = 0; k < m; ++k)
+        PDG_CUDA(c, cudaMemcpyAsync(c->f + (long long)k * P + p0, w + (long long)k * P + p0,
+                                    sizeof(double) * (size_t)(p1 - p0), cudaMemcpyHostToDevice, c->xstream));
+      PDG_CUDA(c, cudaEventRecord(c->xev[j], c->xstream));
+      PDG_CUDA(c, cudaStreamWaitEvent(c->stream, c->xev[j], 0));
+      int e = pdg_launch_set_feq_range(c->f, P, p0, p1 - p0, c->model, (void*)c->stream);
+      if (e) return cuda_fail(c, (cudaError_t)e, "set_feq launch");
+    }
+    PDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->has_state = true;
+    return PDG_OK;
+  }
   PDG_CUDA(c, cudaMemcpyAsync(c->f, w, sizeof(double) * need,
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   int e = pdg_launch_set_feq(c->f, c->npoints, c->model, (void*)c->stream);
@@ -249,6 +289,35 @@ int pdg_get_w(pdg_ctx* c, double* out, size_t len, int on_device) try {
       c->wstage_cap = (long long)need;
     }
     dst = c->wstage;
+  }
+  if (!on_device && c->npoints >= kXferChunkMin * kXferChunks) {
+    // large host result: chunk j's moment kernel on the context stream, its copies on the
+    // private stream after it, so that the copies of chunk j run during the kernel of j + 1
+    if (int r = ensure_xfer(c)) return r;
+    const int m = c->model.m;
+    const long long P = c->npoints;
+    // the kernel of chunk j + 1 is issued before the copies of chunk j (a copy to pageable
+    // memory may return only once it has completed)
+    auto kernel = [&](int j) -> int {
+      const long long p0 = P * j / kXferChunks, p1 = P * (j + 1) / kXferChunks;
+      int e = pdg_launch_get_w_range(c->f, dst, P, p0, p1 - p0, c->model, (void*)c->stream);
+      if (e) return cuda_fail(c, (cudaError_t)e, "get_w launch");
+      PDG_CUDA(c, cudaEventRecord(c->xev[j], c->stream));
+      return PDG_OK;
+    };
+    if (int r = kernel(0)) return r;
+    for (int j = 0; j < kXferChunks; ++j) {
+      if (j + 1 < kXferChunks)
+        if (int r = kernel(j + 1)) return r;
+      const long long p0 = P * j / kXferChunks, p1 = P * (j + 1) / kXferChunks;
+      PDG_CUDA(c, cudaStreamWaitEvent(c->xstream, c->xev[j], 0));
+      for (int k = 0; k < m; ++k)
+        PDG_CUDA(c, cudaMemcpyAsync(out + (long long)k * P + p0, dst + (long long)k * P + p0,
+                                    sizeof(double) * (size_t)(p1 - p0), cudaMemcpyDeviceToHost, c->xstream));
+    }
+    PDG_CUDA(c, cudaStreamSynchronize(c->xstream));
+    PDG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
   }
   int e = pdg_launch_get_w(c->f, dst, c->npoints, c->model, (void*)c->stream);
   if (e) return cuda_fail(c, (cudaError_t)e, "get_w launch");
@@ -606,6 +675,12 @@ int pdg_destroy(pdg_ctx* c) try {
     if (c->djoin[i]) cudaEventDestroy(c->djoin[i]);
   }
   if (c->dfork) cudaEventDestroy(c->dfork);
+  if (c->xstream) {
+    cudaStreamSynchronize(c->xstream);
+    cudaStreamDestroy(c->xstream);
+  }
+  for (auto e : c->xev)
+    if (e) cudaEventDestroy(e);
   free_inflow(c);
   delete c;
   return PDG_OK;

@@ -79,6 +79,10 @@ struct pdg_ctx {
   int g_nsteps = -1;
   unsigned long long g_gen = ~0ULL;
   cudaEvent_t g_in = nullptr, g_out = nullptr;
+  // host <-> device copies of pdg_set_w / pdg_get_w in chunks of points, overlapped with the
+  // equilibrium and moment kernels of the neighbouring chunks (private stream and events)
+  cudaStream_t xstream = nullptr;
+  cudaEvent_t xev[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // auxiliary streams of the diagonal launches of a 3-D lattice sub-step (issue_diag)
   cudaStream_t dstream[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t dfork = nullptr, djoin[4] = {nullptr, nullptr, nullptr, nullptr};

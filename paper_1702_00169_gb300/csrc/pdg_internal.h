@@ -382,6 +382,11 @@ int pdg_sm_count();
 int pdg_launch_pass(const PdgPass& p, void* stream);
 int pdg_launch_set_feq(double* f, long long npoints, const PdgModel& m, void* stream);
 int pdg_launch_get_w(const double* f, double* w, long long npoints, const PdgModel& m, void* stream);
+// The same on points [p0, p0 + n) of the npoints (field stride npoints).
+int pdg_launch_set_feq_range(double* f, long long npoints, long long p0, long long n, const PdgModel& m,
+                             void* stream);
+int pdg_launch_get_w_range(const double* f, double* w, long long npoints, long long p0, long long n,
+                           const PdgModel& m, void* stream);
 // In-place conversion of n state values between FP64 and double-float (to_df != 0: FP64 -> pair).
 int pdg_launch_convert(double* f, long long n, int to_df, void* stream);
 // Model variant index used by the kernels (MV_* in pdg_device.cuh) for a model / pass.

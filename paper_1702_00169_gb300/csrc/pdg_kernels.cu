@@ -36,10 +36,10 @@ using namespace pdgdev;
 // through one collision with omega = 1 (the model M1 carries the omega = 1 constants),
 // which yields f^eq(w) with the sweep's own arithmetic.
 template <int MV, class T>
-__global__ void set_feq_kernel(double* __restrict__ f, long long P, const __grid_constant__ PdgModel M1) {
+__global__ void set_feq_kernel(double* __restrict__ f, long long P, long long n, const __grid_constant__ PdgModel M1) {
   constexpr int NF = NFields<MV>::value;
   const int m = M1.m, nv = M1.nv;
-  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < n;
        pt += (long long)gridDim.x * blockDim.x) {
     double w[PDG_MAXM];
 #pragma unroll
@@ -57,9 +57,9 @@ __global__ void set_feq_kernel(double* __restrict__ f, long long P, const __grid
 }
 
 template <class T>
-__global__ void get_w_kernel(const double* __restrict__ f, double* __restrict__ w, long long P, int m,
-                             int nv) {
-  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+__global__ void get_w_kernel(const double* __restrict__ f, double* __restrict__ w, long long P, long long n,
+                             int m, int nv) {
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < n;
        pt += (long long)gridDim.x * blockDim.x) {
     for (int k = 0; k < m; ++k) {
       T s = zero<T>();
@@ -72,8 +72,8 @@ __global__ void get_w_kernel(const double* __restrict__ f, double* __restrict__ 
 // D2Q9: w = (rho, rho u_x, rho u_y) in slots 0-2 -> f = f^eq(w) in slots 0-8 (M1 has
 // omega = 1, so the relaxation returns f^eq).
 template <class T>
-__global__ void set_feq_q9_kernel(double* __restrict__ f, long long P, const __grid_constant__ PdgModel M1) {
-  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+__global__ void set_feq_q9_kernel(double* __restrict__ f, long long P, long long n, const __grid_constant__ PdgModel M1) {
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < n;
        pt += (long long)gridDim.x * blockDim.x) {
     const T rho = from_double<T>(f[pt]);
     const T ilam = PDG_K(T, M1, PDG_K_ILAM);
@@ -89,9 +89,9 @@ __global__ void set_feq_q9_kernel(double* __restrict__ f, long long P, const __g
 
 // D2Q9: w = P f = (sum f_i, lambda sum f_i xi_i).
 template <class T>
-__global__ void get_w_q9_kernel(const double* __restrict__ f, double* __restrict__ w, long long P,
+__global__ void get_w_q9_kernel(const double* __restrict__ f, double* __restrict__ w, long long P, long long n,
                                 const __grid_constant__ PdgModel M) {
-  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < n;
        pt += (long long)gridDim.x * blockDim.x) {
     T v[9];
 #pragma unroll
@@ -108,8 +108,8 @@ __global__ void get_w_q9_kernel(const double* __restrict__ f, double* __restrict
 
 // D3Q19: w = (rho, rho u) in slots 0-3 -> f = f^eq(w) in slots 0-18.
 template <class T>
-__global__ void set_feq_q19_kernel(double* __restrict__ f, long long P, const __grid_constant__ PdgModel M1) {
-  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+__global__ void set_feq_q19_kernel(double* __restrict__ f, long long P, long long n, const __grid_constant__ PdgModel M1) {
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < n;
        pt += (long long)gridDim.x * blockDim.x) {
     const T rho = from_double<T>(f[pt]);
     const T ilam = PDG_K(T, M1, PDG_K_ILAM);
@@ -126,9 +126,9 @@ __global__ void set_feq_q19_kernel(double* __restrict__ f, long long P, const __
 
 // D3Q19: w = P f = (sum f_i, lambda sum f_i xi_i).
 template <class T>
-__global__ void get_w_q19_kernel(const double* __restrict__ f, double* __restrict__ w, long long P,
+__global__ void get_w_q19_kernel(const double* __restrict__ f, double* __restrict__ w, long long P, long long n,
                                  const __grid_constant__ PdgModel M) {
-  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < n;
        pt += (long long)gridDim.x * blockDim.x) {
     T v[19];
 #pragma unroll
@@ -147,9 +147,9 @@ __global__ void get_w_q19_kernel(const double* __restrict__ f, double* __restric
 // population and +-j_a/2 to the two axis populations of axis a (moments (rho, j) exactly);
 // one relaxation with omega = 1 (M1) then returns f^eq with the sweep's own arithmetic.
 template <class T, bool EDGES>
-__global__ void set_feq_corner_kernel(double* __restrict__ f, long long P, const __grid_constant__ PdgModel M1) {
+__global__ void set_feq_corner_kernel(double* __restrict__ f, long long P, long long n, const __grid_constant__ PdgModel M1) {
   constexpr int NV = EDGES ? 27 : 15;
-  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < n;
        pt += (long long)gridDim.x * blockDim.x) {
     const T ilam = PDG_K(T, M1, PDG_K_ILAM), hf = from_double<T>(0.5);
     T v[NV];
@@ -170,10 +170,10 @@ __global__ void set_feq_corner_kernel(double* __restrict__ f, long long P, const
 
 // D3Q15 / D3Q27: w = P f = (sum f_i, lambda sum f_i xi_i).
 template <class T, bool EDGES>
-__global__ void get_w_corner_kernel(const double* __restrict__ f, double* __restrict__ w, long long P,
+__global__ void get_w_corner_kernel(const double* __restrict__ f, double* __restrict__ w, long long P, long long n,
                                     const __grid_constant__ PdgModel M) {
   constexpr int NV = EDGES ? 27 : 15, C0 = EDGES ? 19 : 7;
-  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < P;
+  for (long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x; pt < n;
        pt += (long long)gridDim.x * blockDim.x) {
     T v[NV];
 #pragma unroll
@@ -214,11 +214,11 @@ int grid_for(long long n, int threads) {
 }
 
 template <int MV>
-int launch_feq_t(double* f, long long P, const PdgModel& m1, cudaStream_t st) {
+int launch_feq_t(double* f, long long P, long long p0, long long n, const PdgModel& m1, cudaStream_t st) {
   if (m1.prec == PDG_PREC_DF32)
-    set_feq_kernel<MV, dd><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+    set_feq_kernel<MV, dd><<<grid_for(n, 256), 256, 0, st>>>(f + p0, P, n, m1);
   else
-    set_feq_kernel<MV, double><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+    set_feq_kernel<MV, double><<<grid_for(n, 256), 256, 0, st>>>(f + p0, P, n, m1);
   return (int)cudaGetLastError();
 }
 
@@ -243,75 +243,84 @@ int pdg_launch_pass(const PdgPass& p, void* stream) {
 }
 
 int pdg_launch_set_feq(double* f, long long P, const PdgModel& m, void* stream) {
+  return pdg_launch_set_feq_range(f, P, 0, P, m, stream);
+}
+
+int pdg_launch_set_feq_range(double* f, long long P, long long p0, long long n, const PdgModel& m, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   PdgModel m1 = m;
   m1.omega = 1.0;
   pdg_model_constants(&m1);
   switch (pdg_model_variant(m)) {
-    case MV_ADV: return launch_feq_t<MV_ADV>(f, P, m1, st);
-    case MV_SW: return launch_feq_t<MV_SW>(f, P, m1, st);
-    case MV_EU1: return launch_feq_t<MV_EU1>(f, P, m1, st);
-    case MV_EU2: return launch_feq_t<MV_EU2>(f, P, m1, st);
-    case MV_EU3: return launch_feq_t<MV_EU3>(f, P, m1, st);
+    case MV_ADV: return launch_feq_t<MV_ADV>(f, P, p0, n, m1, st);
+    case MV_SW: return launch_feq_t<MV_SW>(f, P, p0, n, m1, st);
+    case MV_EU1: return launch_feq_t<MV_EU1>(f, P, p0, n, m1, st);
+    case MV_EU2: return launch_feq_t<MV_EU2>(f, P, p0, n, m1, st);
+    case MV_EU3: return launch_feq_t<MV_EU3>(f, P, p0, n, m1, st);
     case MV_D2Q9:
       if (m1.prec == PDG_PREC_DF32)
-        set_feq_q9_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+        set_feq_q9_kernel<dd><<<grid_for(n, 256), 256, 0, st>>>(f + p0, P, n, m1);
       else
-        set_feq_q9_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+        set_feq_q9_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(f + p0, P, n, m1);
       return (int)cudaGetLastError();
     case MV_D3Q19:
       if (m1.prec == PDG_PREC_DF32)
-        set_feq_q19_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+        set_feq_q19_kernel<dd><<<grid_for(n, 256), 256, 0, st>>>(f + p0, P, n, m1);
       else
-        set_feq_q19_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+        set_feq_q19_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(f + p0, P, n, m1);
       return (int)cudaGetLastError();
     case MV_D3Q15:
       if (m1.prec == PDG_PREC_DF32)
-        set_feq_corner_kernel<dd, false><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+        set_feq_corner_kernel<dd, false><<<grid_for(n, 256), 256, 0, st>>>(f + p0, P, n, m1);
       else
-        set_feq_corner_kernel<double, false><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+        set_feq_corner_kernel<double, false><<<grid_for(n, 256), 256, 0, st>>>(f + p0, P, n, m1);
       return (int)cudaGetLastError();
     case MV_D3Q27:
       if (m1.prec == PDG_PREC_DF32)
-        set_feq_corner_kernel<dd, true><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+        set_feq_corner_kernel<dd, true><<<grid_for(n, 256), 256, 0, st>>>(f + p0, P, n, m1);
       else
-        set_feq_corner_kernel<double, true><<<grid_for(P, 256), 256, 0, st>>>(f, P, m1);
+        set_feq_corner_kernel<double, true><<<grid_for(n, 256), 256, 0, st>>>(f + p0, P, n, m1);
       return (int)cudaGetLastError();
   }
   return (int)cudaErrorInvalidValue;
 }
 
 int pdg_launch_get_w(const double* f, double* w, long long P, const PdgModel& m, void* stream) {
+  return pdg_launch_get_w_range(f, w, P, 0, P, m, stream);
+}
+
+int pdg_launch_get_w_range(const double* f, double* w, long long P, long long p0, long long n, const PdgModel& m,
+                           void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (m.kind == PDG_MODEL_ISOTHERMAL_D3Q19) {
     if (m.prec == PDG_PREC_DF32)
-      get_w_q19_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+      get_w_q19_kernel<dd><<<grid_for(n, 256), 256, 0, st>>>(f + p0, w + p0, P, n, m);
     else
-      get_w_q19_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+      get_w_q19_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(f + p0, w + p0, P, n, m);
     return (int)cudaGetLastError();
   }
   if (m.kind == PDG_MODEL_ISOTHERMAL_D3Q15 || m.kind == PDG_MODEL_ISOTHERMAL_D3Q27) {
     const bool q27 = m.kind == PDG_MODEL_ISOTHERMAL_D3Q27;
     if (m.prec == PDG_PREC_DF32) {
-      if (q27) get_w_corner_kernel<dd, true><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
-      else get_w_corner_kernel<dd, false><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+      if (q27) get_w_corner_kernel<dd, true><<<grid_for(n, 256), 256, 0, st>>>(f + p0, w + p0, P, n, m);
+      else get_w_corner_kernel<dd, false><<<grid_for(n, 256), 256, 0, st>>>(f + p0, w + p0, P, n, m);
     } else {
-      if (q27) get_w_corner_kernel<double, true><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
-      else get_w_corner_kernel<double, false><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+      if (q27) get_w_corner_kernel<double, true><<<grid_for(n, 256), 256, 0, st>>>(f + p0, w + p0, P, n, m);
+      else get_w_corner_kernel<double, false><<<grid_for(n, 256), 256, 0, st>>>(f + p0, w + p0, P, n, m);
     }
     return (int)cudaGetLastError();
   }
   if (m.kind == PDG_MODEL_ISOTHERMAL_D2Q9) {
     if (m.prec == PDG_PREC_DF32)
-      get_w_q9_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+      get_w_q9_kernel<dd><<<grid_for(n, 256), 256, 0, st>>>(f + p0, w + p0, P, n, m);
     else
-      get_w_q9_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m);
+      get_w_q9_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(f + p0, w + p0, P, n, m);
     return (int)cudaGetLastError();
   }
   if (m.prec == PDG_PREC_DF32)
-    get_w_kernel<dd><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m.m, m.nv);
+    get_w_kernel<dd><<<grid_for(n, 256), 256, 0, st>>>(f + p0, w + p0, P, n, m.m, m.nv);
   else
-    get_w_kernel<double><<<grid_for(P, 256), 256, 0, st>>>(f, w, P, m.m, m.nv);
+    get_w_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(f + p0, w + p0, P, n, m.m, m.nv);
   return (int)cudaGetLastError();
 }
 
