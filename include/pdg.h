@@ -220,7 +220,11 @@ int pdg_set_model(pdg_ctx* ctx, const pdg_model_desc* desc);
  *   on_device  1: w is a device pointer (read on the context stream, asynchronous);
  *              0: w is host memory (copied, then the stream is synchronised)
  * The first pdg_set_w / pdg_set_f after a model change allocates the device state
- * f (f_len doubles, cudaMalloc).
+ * f (f_len doubles, cudaMalloc).  From host memory, a state of at least 8 * 2^19 points is
+ * copied in 8 chunks of points on a private stream of the context (created on first use,
+ * ordered after the work already on the context stream), each chunk's equilibrium kernel
+ * running on the context stream during the next chunk's copy; the result is bitwise that
+ * of one copy and one kernel.
  * Errors: PDG_ERR_STATE (no model), PDG_ERR_ARG (len mismatch, NULL), PDG_ERR_OOM, PDG_ERR_CUDA.
  */
 int pdg_set_w(pdg_ctx* ctx, const double* w, size_t len, int on_device);
@@ -317,7 +321,9 @@ int pdg_step(pdg_ctx* ctx, double dt, int nsteps);
  *   out        layout [m][P_z][P_y][P_x], len = m * npoints doubles
  *   on_device  1: out is a device pointer (written on the context stream, asynchronous);
  *              0: host memory (the stream is synchronised before returning)
- * A host read uses a device staging buffer of len doubles, allocated on first use.
+ * A host read uses a device staging buffer of len doubles, allocated on first use; from a
+ * state of at least 8 * 2^19 points it is copied out in 8 chunks of points on the private
+ * stream of pdg_set_w, each during the moment kernel of the next chunk.
  * Errors: PDG_ERR_STATE, PDG_ERR_ARG, PDG_ERR_OOM, PDG_ERR_CUDA.
  */
 int pdg_get_w(pdg_ctx* ctx, double* out, size_t len, int on_device);
